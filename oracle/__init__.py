@@ -1,0 +1,19 @@
+"""Plain FP64 CPU oracle for the PCEXP Krylov step on DG Euler.
+
+TEST INFRASTRUCTURE ONLY.  Only the test suite, ``__graft_entry__.smoke()``
+and the CPU-baseline leg of ``bench.py`` may import or run anything here;
+the product (the CUDA library and its Python binding) never does, and has no
+CPU fallback.  The oracle shares no code with the CUDA path: it builds its
+own quadrature, basis, face list, flux and Krylov machinery from the paper
+("An Exponential Time-Integrator Scheme for Steady and Unsteady Inviscid
+Flows", Li, Luo, Wang & Ju).  Each function cites the section or equation it
+follows.  Inputs (meshes, seeds) come from the ``workloads`` module, which
+holds no method arithmetic.
+
+Pinned by the ``-m "not gpu"`` tests against closed forms, library routines
+and printed values (Table 1 "timesize", Eq. grow / exp1_grow / rkgrow,
+phi_1(z) = (e^z - 1)/z, dense expm, free-stream preservation, conservation,
+complex-step derivatives and the Appendix flux Jacobian).  Parity unpinned:
+the steady bump-channel march beyond agreement with itself (no printed
+number exists for it).
+"""
