@@ -1,0 +1,336 @@
+#!/usr/bin/env python3
+"""Throughput of the PCEXP Krylov step on GB300: DOF * steps / s.
+
+Workload (default): the subsonic bump channel, 192 x 64 quads split into
+24,576 triangles with +-15% node jitter (seed 1), DG P2 (K = 589,824
+unknowns), Ma 0.5, slip walls and far-field boundaries, PCEXP with local time
+steps at CFL 100 and Krylov dimension m = 30, FP64, starting from the free
+stream.  One step = one PCEXP iteration (residual, two CGS2 Arnoldi
+processes of 30 columns with their J v products, two phi evaluations, the
+corrector residual and J v, both updates).
+
+Usage: python bench.py [--gpus N] [--steps K] [--warmup W] [--impl gb300|reference]
+For N > 1 run under torchrun; every rank runs an independent replica (the
+path is not sharded), so the scaling is weak.
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import os
+import statistics
+import subprocess
+import sys
+import tempfile
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+if ROOT not in sys.path:
+    sys.path.insert(0, ROOT)
+
+METRIC = "PCEXP DOF·steps/s on DG Euler, FP32-mixed vs FP64 at stated error, % HBM peak"
+UNIT = "DOF*steps/s"
+NX, NY, P, M, CFL, SEED = 192, 64, 2, 30, 100.0, 1
+WORKLOAD = "bump2d_192x64_p2_m30_pcexp_localcfl100"
+# bounded CPU samples of the same configuration (a smaller instance of the same channel)
+CPU_SAMPLE = (96, 32)
+REF_SAMPLE = (48, 16)
+
+
+def load_peaks():
+    try:
+        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
+            d = json.load(f)
+        return float(d["hbm_gbs"]), "measured"
+    except Exception:
+        return 6800.0, "fallback"
+
+
+# ----------------------------------------------------------------- CPU oracle
+ORACLE_SNIPPET = r"""
+import json, sys, time
+sys.path.insert(0, {root!r})
+import numpy as np
+import workloads as W
+from oracle.dg import DGOracle
+from oracle import pcexp
+case = W.case_bump2d({nx}, {ny}, {p}, {seed})
+dg = DGOracle(case.mesh, case.p, case.free)
+u = np.zeros((dg.E, dg.nv, dg.N))
+u[:, :, 0] = dg.freestream_state()[None, :] * np.sqrt(dg.area)[:, None]
+u = u.reshape(-1)
+times = []
+for s in range({warm} + {steps}):
+    t0 = time.perf_counter()
+    u, _ = pcexp.steady_step(dg, u, {cfl}, {m})
+    times.append(time.perf_counter() - t0)
+print(json.dumps(dict(K=dg.K, times=times[{warm}:])))
+"""
+
+
+def run_oracle(nx, ny, steps, warm):
+    env = dict(os.environ, OMP_NUM_THREADS="1", OPENBLAS_NUM_THREADS="1", MKL_NUM_THREADS="1",
+               CUDA_VISIBLE_DEVICES="")
+    code = ORACLE_SNIPPET.format(root=ROOT, nx=nx, ny=ny, p=P, seed=SEED, warm=warm, steps=steps, cfl=CFL, m=M)
+    r = subprocess.run([sys.executable, "-c", code], capture_output=True, text=True, env=env)
+    if r.returncode != 0:
+        raise RuntimeError("oracle sample failed:\n" + r.stderr[-2000:])
+    return json.loads(r.stdout.strip().splitlines()[-1])
+
+
+# ------------------------------------------------------------------- clocks
+class ClockSampler:
+    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, device_index: int):
+        self.path = tempfile.mktemp(suffix=".csv")
+        self.proc = None
+        self.dev = device_index
+
+    def start(self):
+        try:
+            self.f = open(self.path, "w")
+            self.proc = subprocess.Popen(["nvidia-smi", "-i", str(self.dev), f"--query-gpu={self.FIELDS}",
+                                          "--format=csv,noheader,nounits", "-lms", "200"],
+                                         stdout=self.f, stderr=subprocess.DEVNULL)
+        except Exception:
+            self.proc = None
+
+    def stop(self):
+        if self.proc is None:
+            return None
+        time.sleep(0.25)
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except Exception:
+            self.proc.kill()
+        self.f.close()
+        rows = []
+        for line in open(self.path):
+            parts = [x.strip() for x in line.split(",")]
+            if len(parts) >= 9:
+                rows.append(parts)
+        os.unlink(self.path)
+        if not rows:
+            return None
+        sm = [float(r[1]) for r in rows if r[1].replace(".", "").isdigit()]
+        smax = max(float(r[2]) for r in rows if r[2].replace(".", "").isdigit())
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        reasons = sorted({names[i] for r in rows for i in range(4) if r[5 + i].lower() == "active"})
+        return {"sm_mhz": statistics.median(sm) if sm else None, "sm_max_mhz": smax, "reasons": reasons,
+                "samples": len(rows)}
+
+
+# ------------------------------------------------------------ algorithmic bytes
+def algorithmic_bytes(kind, T, K, E, F, nfq, m):
+    """Minimum DRAM bytes per launch of a kernel class (per-kernel table)."""
+    g_face = F * (4 * T + 12)  # normal, length, element and local-face ids
+    g_elem = E * (8 * T + 12)  # affine map, sqrt(det), h; face slots
+    G = F * nfq * 4 * T        # face-flux buffer
+    avg_j = (m - 1) / 2.0       # mean column index over one Arnoldi process
+    return {
+        "jvp_face": 2 * K * T + g_face + G,
+        "jvp_elem": 3 * K * T + g_elem + G,
+        "residual_face": K * T + g_face + G,
+        "residual_elem": 2 * K * T + g_elem + G,
+        "cgs_proj": (avg_j + 2) * K * T,
+        "cgs_upd_proj": (avg_j + 3) * K * T,
+        "cgs_upd_norm": (avg_j + 3) * K * T,
+    }.get(kind)
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=20)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="gb300", choices=["gb300", "reference"])
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-mixed", action="store_true")
+    args = ap.parse_args()
+    args.warmup = max(args.warmup, 3)
+
+    rank = int(os.environ.get("RANK", "0"))
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    if args.impl == "reference":
+        return reference_arm(args, rank, world)
+
+    import numpy as np
+    import torch
+
+    import workloads as W
+    from paper_1801_06300_gb300 import build, capi
+
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    torch.cuda.set_device(local)
+    dist = None
+    if world > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl", device_id=torch.device("cuda", local))
+    if rank == 0:
+        build()
+    if dist:
+        dist.barrier()
+    capi.load()
+
+    case = W.case_bump2d(NX, NY, P, SEED)
+    free = case.free
+    flush = torch.empty(64 * 1024 * 1024, dtype=torch.float32, device="cuda")  # 256 MB > L2
+
+    def run(precision, profile):
+        ctx = capi.Context(case.mesh, P, free, precision, m_max=M)
+        for _ in range(args.warmup):
+            ctx.step(capi.PCEXP_SCHEME_PCEXP, capi.PCEXP_DT_LOCAL_CFL, CFL, M, info=False)
+        torch.cuda.synchronize()
+        evs = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(args.steps)]
+        sampler = ClockSampler(local)
+        if dist:
+            dist.barrier()
+        torch.cuda.synchronize()
+        sampler.start()
+        if profile:
+            ctx.profile_enable(True)
+        t0 = time.perf_counter()
+        for s in range(args.steps):
+            flush.zero_()
+            evs[s][0].record()
+            ctx.step(capi.PCEXP_SCHEME_PCEXP, capi.PCEXP_DT_LOCAL_CFL, CFL, M, info=False)
+            evs[s][1].record()
+        torch.cuda.synchronize()
+        wall = time.perf_counter() - t0
+        if dist:
+            dist.barrier()
+        clocks = sampler.stop()
+        ms = sum(a.elapsed_time(b) for a, b in evs)
+        prof = ctx.profile_read() if profile else None
+        if profile:
+            ctx.profile_enable(False)
+        state = ctx.get_state()
+        return ctx, ms, wall, prof, clocks, state
+
+    ctx64, ms64, wall64, prof, clocks, state64 = run(capi.PCEXP_FP64, True)
+    K = ctx64.K
+    ms_max = ms64
+    if dist:
+        t = torch.tensor([ms64], device="cuda", dtype=torch.float64)
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        ms_max = float(t.item())
+    value = K * args.steps * world / (ms_max / 1e3)
+
+    # end to end through the public API with host buffers (pinned), copies inside the timed region
+    hin = torch.empty(K, dtype=torch.float64, pin_memory=True).numpy()
+    hout = torch.empty(K, dtype=torch.float64, pin_memory=True).numpy()
+    ctx64.get_state(hin)
+    torch.cuda.synchronize()
+    if dist:
+        dist.barrier()
+    t0 = time.perf_counter()
+    for s in range(args.steps):
+        ctx64.set_state(hin)
+        ctx64.step(capi.PCEXP_SCHEME_PCEXP, capi.PCEXP_DT_LOCAL_CFL, CFL, M, info=False)
+        ctx64.get_state(hout)
+        hin, hout = hout, hin
+    torch.cuda.synchronize()
+    e2e_s = time.perf_counter() - t0
+    if dist:
+        t = torch.tensor([e2e_s], device="cuda", dtype=torch.float64)
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        e2e_s = float(t.item())
+    e2e_value = K * args.steps * world / e2e_s
+
+    # FP32-mixed form on the same workload.  Accuracy: one step from the same state in
+    # both forms (the steady march at CFL 100 amplifies any 1e-7 difference to 1e-2
+    # within a few steps, so multi-step state differences measure that, not FP32).
+    mixed = None
+    if not args.no_mixed:
+        ctx32, ms32, wall32, prof32, _, state32 = run(capi.PCEXP_FP32_MIXED, True)
+        s0 = np.ascontiguousarray(state64)
+        ctx64.set_state(s0)
+        ctx64.step(capi.PCEXP_SCHEME_PCEXP, capi.PCEXP_DT_LOCAL_CFL, CFL, M, info=False)
+        a = ctx64.get_state()
+        ctx32.set_state(s0)
+        ctx32.step(capi.PCEXP_SCHEME_PCEXP, capi.PCEXP_DT_LOCAL_CFL, CFL, M, info=False)
+        b = ctx32.get_state()
+        mixed = {"value": K * args.steps * world / (ms32 / 1e3), "ms_per_step": ms32 / args.steps,
+                 "speedup_vs_fp64": ms64 / ms32,
+                 "one_step_state_rel_l2_vs_fp64": float(np.linalg.norm(b - a) / np.linalg.norm(a)),
+                 "one_step_increment_rel_l2_vs_fp64": float(np.linalg.norm((b - s0) - (a - s0)) / np.linalg.norm(a - s0)),
+                 "kernel_ms_per_step": {k: round(v[1] / args.steps, 4) for k, v in prof32.items() if v[0]}}
+        ctx32.close()
+
+    # roofline of the dominant kernel class (by device time in the timed region)
+    hbm, peak_kind = load_peaks()
+    E, F, nfq = case.mesh.n_elem, None, P + 1
+    from paper_1801_06300_gb300.capi import KERNEL_CLASSES  # noqa: F401
+    nfaces = (3 * E + len(case.mesh.btags)) // 2
+    F = nfaces
+    launches = sum(v[0] for v in prof.values())
+    dom = max(prof, key=lambda k: prof[k][1])
+    n_dom, ms_dom = prof[dom]
+    ab = algorithmic_bytes(dom, 8, K, E, F, nfq, M)
+    roof = None
+    if ab is not None and n_dom:
+        achieved = ab / (ms_dom / n_dom / 1e3) / 1e9
+        roof = {"kernel": dom, "bound": "hbm", "achieved": round(achieved, 1), "peak": hbm, "unit": "GB/s",
+                "frac": round(achieved / hbm, 4), "peak_source": peak_kind, "traffic": None,
+                "algorithmic_bytes_per_launch": ab, "avg_launch_us": round(ms_dom / n_dom * 1e3, 2),
+                "time_share": round(ms_dom / sum(v[1] for v in prof.values()), 4)}
+
+    cpu = None
+    if rank == 0 and world == 1 and not args.no_cpu_baseline:
+        r = run_oracle(*CPU_SAMPLE, steps=1, warm=0)
+        cpu = {"value": r["K"] * len(r["times"]) / sum(r["times"]), "unit": UNIT, "cores": 1, "kind": "oracle",
+               "sample": f"1 PCEXP local-step iteration of the same configuration on the "
+                         f"{CPU_SAMPLE[0]}x{CPU_SAMPLE[1]} channel (K={r['K']}), FP64 numpy, 1 thread, "
+                         f"{sum(r['times']):.1f} s"}
+
+    out = {
+        "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
+        "warmup": args.warmup, "ms_per_step": ms_max / args.steps, "higher_is_better": True,
+        "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+        "config": {"workload": WORKLOAD, "mesh": f"{NX}x{NY} split quads, {E} triangles, 15% jitter seed {SEED}",
+                   "p": P, "m": M, "K": K, "scheme": "PCEXP", "time_step": f"local, CFL {CFL:g}",
+                   "precision": "FP64", "l2": "flushed between steps (256 MB write outside the step events)",
+                   "parallelism": f"replicas x{world}"},
+        "e2e": {"value": e2e_value, "unit": UNIT, "h2d_bytes_per_step": K * 8, "d2h_bytes_per_step": K * 8},
+        "gpu_launches": launches,
+        "kernel_ms_per_step": {k: round(v[1] / args.steps, 4) for k, v in prof.items() if v[0]},
+        "roofline": roof,
+        "cpu_baseline": cpu,
+        "fp32_mixed": mixed,
+        "clocks": clocks,
+    }
+    ctx64.close()
+    if rank == 0:
+        print(json.dumps(out))
+    if dist:
+        dist.destroy_process_group()
+
+
+def reference_arm(args, rank, world):
+    """The oracle, as it stands, on the host cores: each step one PCEXP iteration on a
+    bounded sample (the same channel configuration at REF_SAMPLE resolution)."""
+    if rank != 0:
+        return
+    r = run_oracle(*REF_SAMPLE, steps=args.steps, warm=args.warmup)
+    total = sum(r["times"])
+    value = r["K"] * args.steps / total
+    out = {
+        "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
+        "warmup": args.warmup, "ms_per_step": total / args.steps * 1e3, "higher_is_better": True,
+        "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic", "impl": "reference",
+        "config": {"workload": WORKLOAD, "p": P, "m": M, "scheme": "PCEXP", "time_step": f"local, CFL {CFL:g}",
+                   "sample": f"{REF_SAMPLE[0]}x{REF_SAMPLE[1]} channel, K={r['K']}"},
+        "cpu_baseline": {"value": value, "unit": UNIT, "cores": 1, "kind": "oracle",
+                         "sample": f"{args.steps} PCEXP local-step iterations of the same configuration on the "
+                                   f"{REF_SAMPLE[0]}x{REF_SAMPLE[1]} channel (K={r['K']}), FP64 numpy, 1 thread"},
+        "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
+    }
+    print(json.dumps(out))
+
+
+if __name__ == "__main__":
+    main()

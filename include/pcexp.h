@@ -1,0 +1,228 @@
+/*
+ * pcexp.h -- C interface of the GB300 library for the Krylov step of the
+ * predictor-corrector exponential (PCEXP) scheme on the DG discretisation of
+ * the Euler equations (Li, Luo, Wang & Ju, "An Exponential Time-Integrator
+ * Scheme for Steady and Unsteady Inviscid Flows").
+ *
+ * The problem statement follows the paper: a mesh, a DG order p and a state
+ * u (Sec. 4.2, Eq. uexp), a time step dt and a Krylov dimension m give the
+ * state at t + dt (Sec. 2.1, Eq. s9/s10); steady runs march to a residual
+ * drop with the CFL ramp of Eq. cfl (Sec. 5.2).
+ *
+ * Conventions shared by every call
+ *   - Every function returns PCEXP_OK (0) or a negative PCEXP_ERR_* code and
+ *     never aborts the process; pcexp_status_string() names a code.
+ *   - State-shaped arrays hold K = n_elem * n_var * n_basis doubles laid out
+ *     [element][variable][basis function]; variables are (rho, rho u, rho v,
+ *     rho E).  With basis_io == PCEXP_BASIS_PAPER the coefficients are those
+ *     of the paper's element basis (Eq. basis: scaled Cartesian monomials
+ *     about the centroid, orthonormalised by modified Gram-Schmidt,
+ *     Algorithm 1); with PCEXP_BASIS_INTERNAL they are those of the library's
+ *     own orthonormal basis (a reference-triangle orthonormal basis scaled by
+ *     |det A_e|^-1/2).  Both bases are orthonormal, so norms and inner
+ *     products agree in either.
+ *   - on_device != 0: pointers are device pointers read/written on the
+ *     context's stream; otherwise host pointers, copied synchronously.
+ *   - The caller owns every pointer it passes; nothing is retained after a
+ *     call returns.  The library owns its internal device buffers and frees
+ *     them in pcexp_destroy().
+ *   - One context per stream; a context is not thread-safe.
+ *   - Krylov breakdown is not an error: it is reported in pcexp_step_info.
+ */
+#ifndef PCEXP_H
+#define PCEXP_H
+
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+/* ---- status codes ---- */
+#define PCEXP_OK 0
+#define PCEXP_ERR_INVALID_ARG (-1) /* bad pointer, size, order or option */
+#define PCEXP_ERR_MESH (-2)        /* unmatched / non-conforming / inverted mesh */
+#define PCEXP_ERR_CUDA (-3)        /* a CUDA runtime call failed */
+#define PCEXP_ERR_OOM (-4)         /* device allocation failed */
+#define PCEXP_ERR_NONFINITE (-5)   /* a norm, beta or h_{j+1,j} was NaN/Inf */
+#define PCEXP_ERR_TIMEOUT (-6)     /* reserved for bounded device waits */
+#define PCEXP_ERR_UNSUPPORTED (-7) /* valid request this build does not cover */
+
+/* ---- boundary tags (Sec. 4.4, Sec. 5.2) ---- */
+#define PCEXP_BC_SLIP_WALL 1 /* ghost state mirrors the normal velocity */
+#define PCEXP_BC_FARFIELD 2  /* characteristic (Riemann-invariant) ghost state */
+
+/* ---- options ---- */
+#define PCEXP_FP64 0       /* every vector, flux and reduction in FP64 */
+#define PCEXP_FP32_MIXED 1 /* R, J v and the Krylov basis in FP32; reductions,
+                              Hessenberg, phi and the master state in FP64 */
+#define PCEXP_BASIS_PAPER 0
+#define PCEXP_BASIS_INTERNAL 1
+
+#define PCEXP_SCHEME_PCEXP 0 /* Eq. s9 + s10 */
+#define PCEXP_SCHEME_EXP1 1  /* Eq. s9 alone (first stage) */
+
+#define PCEXP_DT_GIVEN 0      /* global dt passed by the caller */
+#define PCEXP_DT_GLOBAL_CFL 1 /* dt = min_e dt_e(CFL), Eq. x3d */
+#define PCEXP_DT_LOCAL_CFL 2  /* local steps: du/dtau = D R(u), D = diag(dt_e(CFL)),
+                                 unit pseudo-step (reading for steady runs) */
+
+#define PCEXP_PROJ_FREESTREAM 0 /* params: none */
+#define PCEXP_PROJ_VORTEX 1     /* params: eps, xc, yc, period (0 = none) */
+#define PCEXP_PROJ_BLOBS 2      /* params: radius, then n x (x, y, a_rho, a_p) */
+
+#define PCEXP_MAX_KRYLOV 32 /* largest supported m (the paper uses m = 30) */
+
+/* Mesh of positively oriented triangles (dim = 2).
+ * coords [n_vert][dim]; elem_vert [n_elem][dim+1]; vert_master [n_vert] maps
+ * each vertex to its periodic master (NULL: no periodic identification);
+ * bface_vert [n_bface][dim] + bface_tag [n_bface] list the tagged boundary
+ * edges.  Edges are matched on master vertices; an edge with no partner and
+ * no tag is a PCEXP_ERR_MESH. */
+typedef struct pcexp_mesh {
+  int32_t dim;
+  int64_t n_vert;
+  const double* coords;
+  int64_t n_elem;
+  const int32_t* elem_vert;
+  const int32_t* vert_master;
+  int64_t n_bface;
+  const int32_t* bface_vert;
+  const int32_t* bface_tag;
+} pcexp_mesh;
+
+/* Free stream (nondimensional): gamma (7/5 in the paper, Sec. 4.1), Mach
+ * number, flow angle in degrees, density and pressure. */
+typedef struct pcexp_physics {
+  double gamma;
+  double mach;
+  double alpha_deg;
+  double rho_inf;
+  double p_inf;
+} pcexp_physics;
+
+typedef struct pcexp_options {
+  int32_t precision;    /* PCEXP_FP64 | PCEXP_FP32_MIXED */
+  int32_t m_max;        /* Krylov storage, 1..PCEXP_MAX_KRYLOV */
+  double breakdown_eta; /* happy breakdown when h_{j+1,j} <= eta ||J v_j||; <=0: default
+                           (1e-12 FP64, 1e-6 FP32-mixed) */
+  int32_t basis_io;     /* PCEXP_BASIS_PAPER | PCEXP_BASIS_INTERNAL */
+} pcexp_options;
+
+typedef struct pcexp_step_info {
+  int32_t krylov_dim[2]; /* Arnoldi dimension reached in each stage (0 if skipped) */
+  double beta[2];        /* ||R_n|| and ||N_* - N_n|| */
+  double dt;             /* dt used (1 for local pseudo-steps) */
+  double res_norm;       /* density residual norm of Eq. cfl at u_n */
+} pcexp_step_info;
+
+typedef struct pcexp_steady_info {
+  int32_t iterations;
+  double res_first; /* ||R(rho_1)|| */
+  double res_last;  /* ||R(rho_n)|| at exit */
+  int32_t converged;
+} pcexp_steady_info;
+
+typedef struct pcexp_ctx pcexp_ctx;
+
+/* Builds faces, geometry, quadrature, bases and device buffers for order p
+ * (0..3).  cuda_stream is a cudaStream_t (NULL: the legacy default stream).
+ * Errors: INVALID_ARG, MESH, CUDA, OOM.  On error *out is NULL. */
+int pcexp_create(pcexp_ctx** out, const pcexp_mesh* mesh, int p,
+                 const pcexp_physics* phys, const pcexp_options* opt, void* cuda_stream);
+
+/* Frees every device buffer of the context.  NULL is a no-op. */
+int pcexp_destroy(pcexp_ctx* ctx);
+
+/* Sizes: number of elements, basis functions per variable, variables and
+ * K = n_elem * n_var * n_basis.  Any output pointer may be NULL. */
+int pcexp_sizes(const pcexp_ctx* ctx, int64_t* n_elem, int32_t* n_basis,
+                int32_t* n_var, int64_t* K);
+
+/* Sets / reads the master state u (K doubles). */
+int pcexp_set_state(pcexp_ctx* ctx, const double* U, int on_device);
+int pcexp_get_state(pcexp_ctx* ctx, double* U, int on_device);
+
+/* L2 projection of an analytic state (PCEXP_PROJ_*) onto the DG space,
+ * written into the master state.  params as listed at PCEXP_PROJ_*. */
+int pcexp_project_state(pcexp_ctx* ctx, int kind, const double* params, int n_params);
+
+/* R(U) of Eq. euler3 (Sec. 4.2): volume term, Roe flux on interior and
+ * periodic faces, Roe flux against the ghost state on boundary faces. */
+int pcexp_residual(pcexp_ctx* ctx, const double* U, double* R, int on_device);
+
+/* J(U) v, the exact directional derivative of R at U (Eq. jac1, jac2),
+ * matrix-free by a tangent-linear kernel. */
+int pcexp_jvp(pcexp_ctx* ctx, const double* U, const double* v, double* Jv, int on_device);
+
+/* Time-step sizes of Eq. x3d at the master state: local != 0 writes n_elem
+ * values dt_e, otherwise one value min_e dt_e. */
+int pcexp_compute_dt(pcexp_ctx* ctx, double cfl, int local, double* dt, int on_device);
+
+/* Arnoldi process (Eq. vm-vm2) for J(U) started from b: V [m+1][K] (column j
+ * = v_{j+1}, same basis as U), H [(m+1) * m] row-major Hessenberg H~_m,
+ * *k = dimension reached (< m on happy breakdown), *beta = ||b||.  Uses
+ * classical Gram-Schmidt run twice (CGS2).  V may be NULL. */
+int pcexp_arnoldi(pcexp_ctx* ctx, const double* U, const double* b, int m,
+                  double* V, double* H, int* k, double* beta, int on_device);
+
+/* phi_1(dt H) e_1 and phi_2(dt H) e_1 (Eq. Phi1, Phi2, final) for the k x k
+ * matrix H (row-major, leading dimension ldh; host arrays), evaluated on the
+ * device in FP64 from the exponential of the augmented matrix
+ * [[dt H, e_1, 0], [0, 0, 1], [0, 0, 0]] by scaling and squaring with a
+ * diagonal Pade approximant.  phi2 may be NULL.  k <= PCEXP_MAX_KRYLOV. */
+int pcexp_phi(pcexp_ctx* ctx, const double* H, int k, int ldh, double dt,
+              double* phi1, double* phi2);
+
+/* One PCEXP (Eq. s9, s10) or EXP1 (Eq. s9) step on the master state with
+ * Krylov dimension m (<= m_max).  dt_mode PCEXP_DT_*: dt_or_cfl is dt for
+ * PCEXP_DT_GIVEN, else the CFL number.  info may be NULL; when given, the
+ * call synchronises the stream to fill it. */
+int pcexp_step(pcexp_ctx* ctx, int scheme, int dt_mode, double dt_or_cfl, int m,
+               pcexp_step_info* info);
+
+/* Steady march with local pseudo-steps and the CFL ramp of Eq. cfl until
+ * ||R(rho_n)|| <= 10^-decades ||R(rho_1)|| or max_iter iterations. */
+int pcexp_march_steady(pcexp_ctx* ctx, int scheme, double cfl_max, double decades,
+                       int max_iter, int m, pcexp_steady_info* info);
+
+/* Diagnostics of the master state: kind 0 = density residual norm of Eq. cfl
+ * (domain volume taken from the mesh), kind 1 = entropy error of
+ * Eq. entropy_error. */
+int pcexp_output(pcexp_ctx* ctx, int kind, double* value);
+
+/* ---- kernel-class timing (diagnostic) ----
+ * With profiling enabled every kernel launch of the context is bracketed by
+ * CUDA events on the context's stream.  pcexp_profile_read synchronises the
+ * stream and returns, for one kernel class, the number of launches and their
+ * summed device time (ms) since profiling was enabled. */
+#define PCEXP_KC_RESIDUAL_FACE 0 /* face Riemann-flux kernel of R(u) */
+#define PCEXP_KC_RESIDUAL_ELEM 1 /* element volume + lift kernel of R(u) */
+#define PCEXP_KC_JVP_FACE 2      /* tangent face kernel of J v */
+#define PCEXP_KC_JVP_ELEM 3      /* tangent element kernel of J v */
+#define PCEXP_KC_CGS_NORM 4      /* ||b|| of the Krylov start vector */
+#define PCEXP_KC_CGS_PROJ 5      /* h = V^T w, ||w|| */
+#define PCEXP_KC_CGS_UPD_PROJ 6  /* w -= V h; h2 = V^T w */
+#define PCEXP_KC_CGS_UPD_NORM 7  /* v_{j+1} = w - V h2; ||v_{j+1}|| */
+#define PCEXP_KC_PHI 8           /* phi of the Hessenberg matrix */
+#define PCEXP_KC_AXPY 9          /* u + sum_i c_i v_i */
+#define PCEXP_KC_DT 10           /* element time steps */
+#define PCEXP_KC_OTHER 11        /* small bookkeeping kernels */
+#define PCEXP_KC_COUNT 12
+int pcexp_profile_enable(pcexp_ctx* ctx, int enable);
+int pcexp_profile_read(pcexp_ctx* ctx, int kernel_class, int64_t* launches, double* ms);
+
+/* Waits for all work queued on the context's stream. */
+int pcexp_synchronize(pcexp_ctx* ctx);
+
+/* Static description of a status code. */
+const char* pcexp_status_string(int status);
+
+/* Human-readable detail of the last error raised on the calling thread
+ * (empty string if none).  Valid until the next call on that thread. */
+const char* pcexp_last_error(void);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* PCEXP_H */

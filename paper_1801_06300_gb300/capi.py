@@ -1,0 +1,273 @@
+"""ctypes binding of include/pcexp.h: the same entry points, argument marshalling only.
+
+Every step of the compute path runs in libpcexp.so.  Arrays may be numpy
+float64 arrays (host, ``on_device=0``) or CUDA torch tensors (``on_device=1``);
+torch is used only for device memory and the stream.
+"""
+from __future__ import annotations
+
+import ctypes as C
+import os
+
+import numpy as np
+
+from .build import LIB, up_to_date
+
+PCEXP_OK = 0
+PCEXP_ERR_INVALID_ARG = -1
+PCEXP_ERR_MESH = -2
+PCEXP_ERR_CUDA = -3
+PCEXP_ERR_OOM = -4
+PCEXP_ERR_NONFINITE = -5
+PCEXP_ERR_TIMEOUT = -6
+PCEXP_ERR_UNSUPPORTED = -7
+PCEXP_BC_SLIP_WALL = 1
+PCEXP_BC_FARFIELD = 2
+PCEXP_FP64 = 0
+PCEXP_FP32_MIXED = 1
+PCEXP_BASIS_PAPER = 0
+PCEXP_BASIS_INTERNAL = 1
+PCEXP_SCHEME_PCEXP = 0
+PCEXP_SCHEME_EXP1 = 1
+PCEXP_DT_GIVEN = 0
+PCEXP_DT_GLOBAL_CFL = 1
+PCEXP_DT_LOCAL_CFL = 2
+PCEXP_PROJ_FREESTREAM = 0
+PCEXP_PROJ_VORTEX = 1
+PCEXP_PROJ_BLOBS = 2
+PCEXP_MAX_KRYLOV = 32
+KERNEL_CLASSES = ["residual_face", "residual_elem", "jvp_face", "jvp_elem", "cgs_norm", "cgs_proj",
+                  "cgs_upd_proj", "cgs_upd_norm", "phi", "axpy", "dt", "other"]
+
+
+class pcexp_mesh(C.Structure):
+    _fields_ = [("dim", C.c_int32), ("n_vert", C.c_int64), ("coords", C.POINTER(C.c_double)),
+                ("n_elem", C.c_int64), ("elem_vert", C.POINTER(C.c_int32)),
+                ("vert_master", C.POINTER(C.c_int32)), ("n_bface", C.c_int64),
+                ("bface_vert", C.POINTER(C.c_int32)), ("bface_tag", C.POINTER(C.c_int32))]
+
+
+class pcexp_physics(C.Structure):
+    _fields_ = [("gamma", C.c_double), ("mach", C.c_double), ("alpha_deg", C.c_double),
+                ("rho_inf", C.c_double), ("p_inf", C.c_double)]
+
+
+class pcexp_options(C.Structure):
+    _fields_ = [("precision", C.c_int32), ("m_max", C.c_int32), ("breakdown_eta", C.c_double),
+                ("basis_io", C.c_int32)]
+
+
+class pcexp_step_info(C.Structure):
+    _fields_ = [("krylov_dim", C.c_int32 * 2), ("beta", C.c_double * 2), ("dt", C.c_double),
+                ("res_norm", C.c_double)]
+
+
+class pcexp_steady_info(C.Structure):
+    _fields_ = [("iterations", C.c_int32), ("res_first", C.c_double), ("res_last", C.c_double),
+                ("converged", C.c_int32)]
+
+
+_P = C.c_void_p
+_D = C.POINTER(C.c_double)
+SIGNATURES = {
+    "pcexp_create": (C.c_int, [C.POINTER(_P), C.POINTER(pcexp_mesh), C.c_int, C.POINTER(pcexp_physics),
+                               C.POINTER(pcexp_options), _P]),
+    "pcexp_destroy": (C.c_int, [_P]),
+    "pcexp_sizes": (C.c_int, [_P, C.POINTER(C.c_int64), C.POINTER(C.c_int32), C.POINTER(C.c_int32),
+                              C.POINTER(C.c_int64)]),
+    "pcexp_set_state": (C.c_int, [_P, _P, C.c_int]),
+    "pcexp_get_state": (C.c_int, [_P, _P, C.c_int]),
+    "pcexp_project_state": (C.c_int, [_P, C.c_int, _D, C.c_int]),
+    "pcexp_residual": (C.c_int, [_P, _P, _P, C.c_int]),
+    "pcexp_jvp": (C.c_int, [_P, _P, _P, _P, C.c_int]),
+    "pcexp_compute_dt": (C.c_int, [_P, C.c_double, C.c_int, _P, C.c_int]),
+    "pcexp_arnoldi": (C.c_int, [_P, _P, _P, C.c_int, _P, _D, C.POINTER(C.c_int), _D, C.c_int]),
+    "pcexp_phi": (C.c_int, [_P, _D, C.c_int, C.c_int, C.c_double, _D, _D]),
+    "pcexp_step": (C.c_int, [_P, C.c_int, C.c_int, C.c_double, C.c_int, C.POINTER(pcexp_step_info)]),
+    "pcexp_march_steady": (C.c_int, [_P, C.c_int, C.c_double, C.c_double, C.c_int, C.c_int,
+                                     C.POINTER(pcexp_steady_info)]),
+    "pcexp_output": (C.c_int, [_P, C.c_int, _D]),
+    "pcexp_synchronize": (C.c_int, [_P]),
+    "pcexp_profile_enable": (C.c_int, [_P, C.c_int]),
+    "pcexp_profile_read": (C.c_int, [_P, C.c_int, C.POINTER(C.c_int64), _D]),
+    "pcexp_status_string": (C.c_char_p, [C.c_int]),
+    "pcexp_last_error": (C.c_char_p, []),
+}
+
+_lib = None
+
+
+def load(path: str | None = None):
+    """Load libpcexp.so (built in-tree by ``build()``); raises if it is missing or stale."""
+    global _lib
+    if _lib is not None:
+        return _lib
+    path = path or LIB
+    if not os.path.exists(path):
+        raise RuntimeError(f"{path} is missing: run paper_1801_06300_gb300.build() (no CPU fallback exists)")
+    if not up_to_date():
+        raise RuntimeError(f"{path} is older than its sources: rebuild with paper_1801_06300_gb300.build()")
+    lib = C.CDLL(path)
+    for name, (res, args) in SIGNATURES.items():
+        fn = getattr(lib, name)
+        fn.restype = res
+        fn.argtypes = args
+    _lib = lib
+    return lib
+
+
+class PcexpError(RuntimeError):
+    def __init__(self, code: int, where: str):
+        lib = load()
+        super().__init__(f"{where}: {lib.pcexp_status_string(code).decode()} ({code}): "
+                         f"{lib.pcexp_last_error().decode()}")
+        self.code = code
+
+
+def check(code: int, where: str):
+    if code != PCEXP_OK:
+        raise PcexpError(code, where)
+
+
+def _ptr(x):
+    """(pointer, on_device) of a numpy float64 array or a CUDA torch tensor."""
+    if isinstance(x, np.ndarray):
+        assert x.dtype == np.float64 and x.flags.c_contiguous
+        return x.ctypes.data_as(C.c_void_p), 0
+    # torch tensor
+    assert x.is_contiguous() and str(x.dtype) == "torch.float64"
+    return C.c_void_p(x.data_ptr()), 1 if x.is_cuda else 0
+
+
+class Context:
+    """Owns one pcexp_ctx; each method is one C call with its arguments marshalled."""
+
+    def __init__(self, mesh, p: int, free, precision: int = PCEXP_FP64, m_max: int = 30,
+                 eta: float = 0.0, basis_io: int = PCEXP_BASIS_PAPER, stream=None):
+        lib = load()
+        self._keep = []
+        coords = np.ascontiguousarray(mesh.coords, np.float64)
+        elems = np.ascontiguousarray(mesh.elems, np.int32)
+        master = np.ascontiguousarray(mesh.vert_master, np.int32)
+        bfv = np.ascontiguousarray(mesh.bfaces, np.int32).reshape(-1)
+        btag = np.ascontiguousarray(mesh.btags, np.int32)
+        self._keep += [coords, elems, master, bfv, btag]
+        ip = lambda a: a.ctypes.data_as(C.POINTER(C.c_int32))  # noqa: E731
+        m = pcexp_mesh(mesh.dim, coords.shape[0], coords.ctypes.data_as(_D), elems.shape[0], ip(elems),
+                       ip(master), btag.shape[0], ip(bfv) if bfv.size else None, ip(btag) if btag.size else None)
+        ph = pcexp_physics(free.gamma, free.mach, free.alpha_deg, free.rho, free.p)
+        op = pcexp_options(precision, m_max, eta, basis_io)
+        if stream is None:
+            try:
+                import torch
+                stream = torch.cuda.current_stream().cuda_stream if torch.cuda.is_available() else 0
+            except ImportError:
+                stream = 0
+        self.ctx = C.c_void_p()
+        check(lib.pcexp_create(C.byref(self.ctx), C.byref(m), p, C.byref(ph), C.byref(op), C.c_void_p(stream)),
+              "pcexp_create")
+        ne, nb, nv, K = C.c_int64(), C.c_int32(), C.c_int32(), C.c_int64()
+        check(lib.pcexp_sizes(self.ctx, C.byref(ne), C.byref(nb), C.byref(nv), C.byref(K)), "pcexp_sizes")
+        self.E, self.nb, self.nv, self.K = ne.value, nb.value, nv.value, K.value
+        self.lib = lib
+
+    def close(self):
+        if getattr(self, "ctx", None) is not None and self.ctx.value:
+            self.lib.pcexp_destroy(self.ctx)
+            self.ctx = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def set_state(self, U):
+        p, dev = _ptr(U)
+        check(self.lib.pcexp_set_state(self.ctx, p, dev), "pcexp_set_state")
+
+    def get_state(self, out=None):
+        out = np.empty(self.K) if out is None else out
+        p, dev = _ptr(out)
+        check(self.lib.pcexp_get_state(self.ctx, p, dev), "pcexp_get_state")
+        return out
+
+    def project_state(self, kind: int, params=()):
+        prm = np.ascontiguousarray(params, np.float64)
+        check(self.lib.pcexp_project_state(self.ctx, kind, prm.ctypes.data_as(_D) if prm.size else None,
+                                           prm.size), "pcexp_project_state")
+
+    def residual(self, U, out=None):
+        out = (np.empty(self.K) if isinstance(U, np.ndarray) else U.new_empty(self.K)) if out is None else out
+        pu, dev = _ptr(U)
+        po, _ = _ptr(out)
+        check(self.lib.pcexp_residual(self.ctx, pu, po, dev), "pcexp_residual")
+        return out
+
+    def jvp(self, U, v, out=None):
+        out = (np.empty(self.K) if isinstance(U, np.ndarray) else U.new_empty(self.K)) if out is None else out
+        pu, dev = _ptr(U)
+        pv, _ = _ptr(v)
+        po, _ = _ptr(out)
+        check(self.lib.pcexp_jvp(self.ctx, pu, pv, po, dev), "pcexp_jvp")
+        return out
+
+    def compute_dt(self, cfl: float, local: bool = False):
+        out = np.empty(self.E if local else 1)
+        check(self.lib.pcexp_compute_dt(self.ctx, cfl, int(local), out.ctypes.data_as(C.c_void_p), 0),
+              "pcexp_compute_dt")
+        return out if local else float(out[0])
+
+    def arnoldi(self, U, b, m: int, want_V: bool = True):
+        V = np.zeros((m + 1, self.K)) if want_V else None
+        H = np.zeros((m + 1) * m)
+        k, beta = C.c_int(), C.c_double()
+        pu, dev = _ptr(U)
+        pb, _ = _ptr(b)
+        check(self.lib.pcexp_arnoldi(self.ctx, pu, pb, m, V.ctypes.data_as(C.c_void_p) if want_V else None,
+                                     H.ctypes.data_as(_D), C.byref(k), C.byref(beta), dev), "pcexp_arnoldi")
+        return V, H.reshape(m + 1, m), k.value, beta.value
+
+    def phi(self, H, dt: float):
+        H = np.ascontiguousarray(H, np.float64)
+        k = H.shape[0]
+        p1, p2 = np.zeros(k), np.zeros(k)
+        check(self.lib.pcexp_phi(self.ctx, H.ctypes.data_as(_D), k, H.shape[1], dt, p1.ctypes.data_as(_D),
+                                 p2.ctypes.data_as(_D)), "pcexp_phi")
+        return p1, p2
+
+    def step(self, scheme: int, dt_mode: int, dt_or_cfl: float, m: int, info: bool = True):
+        inf = pcexp_step_info()
+        check(self.lib.pcexp_step(self.ctx, scheme, dt_mode, dt_or_cfl, m, C.byref(inf) if info else None),
+              "pcexp_step")
+        if not info:
+            return None
+        return dict(k=(inf.krylov_dim[0], inf.krylov_dim[1]), beta=(inf.beta[0], inf.beta[1]), dt=inf.dt,
+                    res_norm=inf.res_norm)
+
+    def march_steady(self, scheme: int, cfl_max: float, decades: float, max_iter: int, m: int):
+        inf = pcexp_steady_info()
+        check(self.lib.pcexp_march_steady(self.ctx, scheme, cfl_max, decades, max_iter, m, C.byref(inf)),
+              "pcexp_march_steady")
+        return dict(iterations=inf.iterations, res_first=inf.res_first, res_last=inf.res_last,
+                    converged=bool(inf.converged))
+
+    def output(self, kind: int = 0) -> float:
+        v = C.c_double()
+        check(self.lib.pcexp_output(self.ctx, kind, C.byref(v)), "pcexp_output")
+        return v.value
+
+    def synchronize(self):
+        check(self.lib.pcexp_synchronize(self.ctx), "pcexp_synchronize")
+
+    def profile_enable(self, on: bool = True):
+        check(self.lib.pcexp_profile_enable(self.ctx, int(on)), "pcexp_profile_enable")
+
+    def profile_read(self):
+        """{class name: (launches, total ms)} since profiling was enabled."""
+        out = {}
+        for i, name in enumerate(KERNEL_CLASSES):
+            n, ms = C.c_int64(), C.c_double()
+            check(self.lib.pcexp_profile_read(self.ctx, i, C.byref(n), C.byref(ms)), "pcexp_profile_read")
+            out[name] = (n.value, ms.value)
+        return out

@@ -1,0 +1,835 @@
+// The C interface of include/pcexp.h: context set-up, basis conversion at the
+// boundary, and the launch sequence of one PCEXP / EXP1 step (Eq. s9, s10).
+//
+// A step never waits for the host: the time step, beta, the Hessenberg matrix,
+// the breakdown flag and the Krylov dimension stay in device memory, and the
+// kernels after a happy breakdown exit at once.  Only pcexp_step with a
+// non-NULL info, the steady march (one 8-byte residual read per iteration)
+// and host-pointer transfers synchronise.
+#include <cmath>
+#include <cstdio>
+#include <cstring>
+#include <string>
+#include <vector>
+
+#include "host_setup.h"
+#include "kernels.h"
+
+using namespace pcexp;
+
+struct pcexp_ctx {
+  int device = 0;
+  cudaStream_t st = nullptr;
+  bool fp32 = false;
+  int p = 0, nb = 0, nq = 0, nfq = 0, nv = 4;
+  int64_t E = 0, F = 0, K = 0, Kp = 0;
+  int m_max = 0;
+  double eta = 0;
+  int basis_io = PCEXP_BASIS_PAPER;
+  double volume = 0;
+  pcexp_physics phys{};
+  Setup host;
+  // device data
+  double* Q = nullptr;
+  int32_t *ef = nullptr, *fel = nullptr, *floc = nullptr;
+  void *geo = nullptr, *fgeo = nullptr, *tabs = nullptr;
+  double* U64[2] = {nullptr, nullptr};
+  void* S32[2] = {nullptr, nullptr};  // FP32 shadows (mixed form only)
+  void *V = nullptr, *w = nullptr, *tmp = nullptr, *delta = nullptr, *G = nullptr, *dte = nullptr;
+  double *io64a = nullptr, *io64b = nullptr;
+  KState* ks = nullptr;
+  StepState* ss = nullptr;
+  double* partials = nullptr;
+  int cur = 0;
+  std::vector<void*> allocs;
+  // kernel-class timing
+  bool prof = false;
+  std::vector<cudaEvent_t> ev_pool;
+  size_t ev_used = 0;
+  std::vector<int> ev_rec;  // (class, start, end) triples of indices into ev_pool
+  double prof_ms[PCEXP_KC_COUNT] = {};
+  int64_t prof_n[PCEXP_KC_COUNT] = {};
+};
+
+namespace {
+
+thread_local std::string g_last_error;
+
+#define PCEXP_CK(...)                                                       \
+  do {                                                                      \
+    cudaError_t _e = (__VA_ARGS__);                                         \
+    if (_e != cudaSuccess) {                                                \
+      g_last_error = std::string(#__VA_ARGS__) + ": " + cudaGetErrorString(_e); \
+      return _e == cudaErrorMemoryAllocation ? PCEXP_ERR_OOM : PCEXP_ERR_CUDA; \
+    }                                                                       \
+  } while (0)
+
+template <class T>
+int dalloc(pcexp_ctx* c, T** p, size_t n) {
+  void* q = nullptr;
+  cudaError_t e = cudaMalloc(&q, n * sizeof(T) + 16);
+  if (e != cudaSuccess) {
+    g_last_error = std::string("cudaMalloc: ") + cudaGetErrorString(e);
+    return PCEXP_ERR_OOM;
+  }
+  c->allocs.push_back(q);
+  e = cudaMemsetAsync(q, 0, n * sizeof(T) + 16, c->st);
+  if (e != cudaSuccess) return PCEXP_ERR_CUDA;
+  *p = reinterpret_cast<T*>(q);
+  return PCEXP_OK;
+}
+
+#define PCEXP_TRY(...)      \
+  do {                      \
+    int _r = (__VA_ARGS__); \
+    if (_r != PCEXP_OK) return _r; \
+  } while (0)
+
+template <class T>
+int upload(pcexp_ctx* c, void** dst, const std::vector<double>& src) {
+  T* d = nullptr;
+  PCEXP_TRY(dalloc(c, &d, src.size() ? src.size() : 1));
+  std::vector<T> tmp(src.begin(), src.end());
+  if (!tmp.empty()) PCEXP_CK(cudaMemcpyAsync(d, tmp.data(), tmp.size() * sizeof(T), cudaMemcpyHostToDevice, c->st));
+  PCEXP_CK(cudaStreamSynchronize(c->st));
+  *dst = d;
+  return PCEXP_OK;
+}
+
+template <class T>
+DGData<T> dgdata(const pcexp_ctx* c) {
+  DGData<T> d;
+  const T* tabs = reinterpret_cast<const T*>(c->tabs);
+  const int nb = c->nb, nq = c->nq, nfq = c->nfq;
+  d.geo = reinterpret_cast<const T*>(c->geo);
+  d.ef = c->ef;
+  d.fel = c->fel;
+  d.floc = c->floc;
+  d.fgeo = reinterpret_cast<const T*>(c->fgeo);
+  d.Bv = tabs;
+  d.Dv = d.Bv + nq * nb;
+  d.Bf = d.Dv + 2 * nq * nb;
+  d.Wf = d.Bf + 3 * nfq * nb;
+  d.Bc = d.Wf + nfq;
+  d.E = c->E;
+  d.F = c->F;
+  const double a = c->phys.alpha_deg * M_PI / 180.0;
+  const double cinf = std::sqrt(c->phys.gamma * c->phys.p_inf / c->phys.rho_inf);
+  d.fs.gamma = (T)c->phys.gamma;
+  d.fs.rho = (T)c->phys.rho_inf;
+  d.fs.p = (T)c->phys.p_inf;
+  d.fs.u = (T)(c->phys.mach * cinf * std::cos(a));
+  d.fs.v = (T)(c->phys.mach * cinf * std::sin(a));
+  d.p = c->p;
+  return d;
+}
+
+// ---- kernel-class timing: events bracket each launch when profiling is on
+int prof_flush(pcexp_ctx* c) {
+  if (c->ev_rec.empty()) {
+    c->ev_used = 0;
+    return PCEXP_OK;
+  }
+  PCEXP_CK(cudaStreamSynchronize(c->st));
+  for (size_t i = 0; i + 2 < c->ev_rec.size(); i += 3) {
+    float ms = 0;
+    PCEXP_CK(cudaEventElapsedTime(&ms, c->ev_pool[c->ev_rec[i + 1]], c->ev_pool[c->ev_rec[i + 2]]));
+    c->prof_ms[c->ev_rec[i]] += ms;
+    c->prof_n[c->ev_rec[i]] += 1;
+  }
+  c->ev_rec.clear();
+  c->ev_used = 0;
+  return PCEXP_OK;
+}
+
+cudaEvent_t* prof_events(pcexp_ctx* c, int n) {
+  if (!c->prof) return nullptr;
+  if (c->ev_used + n > c->ev_pool.size()) {
+    if (c->ev_pool.size() >= 16384) {
+      if (prof_flush(c) != PCEXP_OK) return nullptr;
+    } else {
+      size_t add = c->ev_pool.size() ? c->ev_pool.size() : 1024;
+      for (size_t i = 0; i < add; ++i) {
+        cudaEvent_t e;
+        if (cudaEventCreate(&e) != cudaSuccess) return nullptr;
+        c->ev_pool.push_back(e);
+      }
+    }
+  }
+  cudaEvent_t* e = &c->ev_pool[c->ev_used];
+  c->ev_used += n;
+  return e;
+}
+
+void prof_note(pcexp_ctx* c, int cls, cudaEvent_t* e0, int offset) {
+  if (!e0) return;
+  const int i0 = (int)(e0 - c->ev_pool.data()) + offset;
+  c->ev_rec.push_back(cls);
+  c->ev_rec.push_back(i0);
+  c->ev_rec.push_back(i0 + 1);
+}
+
+// one timed launch of kernel class cls
+#define PCEXP_LAUNCH(c, cls, ...)                                  \
+  do {                                                             \
+    cudaEvent_t* _ev = prof_events(c, 2);                          \
+    if (_ev) cudaEventRecord(_ev[0], (c)->st);                     \
+    cudaError_t _e = (__VA_ARGS__);                                \
+    if (_ev) {                                                     \
+      cudaEventRecord(_ev[1], (c)->st);                            \
+      prof_note(c, cls, _ev, 0);                                   \
+    }                                                              \
+    if (_e != cudaSuccess) {                                       \
+      g_last_error = std::string(#__VA_ARGS__) + ": " + cudaGetErrorString(_e); \
+      return PCEXP_ERR_CUDA;                                       \
+    }                                                              \
+  } while (0)
+
+// the two kernels of one DG operator application (face, element)
+template <class T>
+int dg_apply(pcexp_ctx* c, const DGData<T>& d, const T* u, const T* du, T* out, const T* escale, const int* skip,
+             const double* oscale = nullptr) {
+  cudaEvent_t* ev = prof_events(c, 3);
+  cudaError_t e = launch_dg_operator<T>(d, u, du, out, reinterpret_cast<T*>(c->G), escale, skip, c->st, ev, oscale);
+  if (ev) {
+    prof_note(c, du ? PCEXP_KC_JVP_FACE : PCEXP_KC_RESIDUAL_FACE, ev, 0);
+    prof_note(c, du ? PCEXP_KC_JVP_ELEM : PCEXP_KC_RESIDUAL_ELEM, ev, 1);
+  }
+  if (e != cudaSuccess) {
+    g_last_error = std::string("DG operator launch: ") + cudaGetErrorString(e);
+    return PCEXP_ERR_CUDA;
+  }
+  return PCEXP_OK;
+}
+
+template <class T> T* Vcol(pcexp_ctx* c, int j) { return reinterpret_cast<T*>(c->V) + (int64_t)j * c->Kp; }
+template <class T> T* shadow(pcexp_ctx* c, int i) {
+  return c->fp32 ? reinterpret_cast<T*>(c->S32[i]) : reinterpret_cast<T*>(c->U64[i]);
+}
+
+// Input state-shaped double array (host or device) -> internal basis in T (dst, device).
+template <class T>
+int import_vec(pcexp_ctx* c, const double* src, int on_device, T* dst) {
+  const double* s = src;
+  if (!on_device) {
+    PCEXP_CK(cudaMemcpyAsync(c->io64a, src, c->K * sizeof(double), cudaMemcpyHostToDevice, c->st));
+    s = c->io64a;
+  }
+  if (c->basis_io == PCEXP_BASIS_PAPER) PCEXP_CK(launch_paper_to_internal<T>(s, dst, c->Q, c->E, c->nb, c->nv, c->st));
+  else PCEXP_CK(launch_cast<double, T>(s, dst, c->K, c->st));
+  return PCEXP_OK;
+}
+
+template <class T>
+int export_vec(pcexp_ctx* c, const T* src, double* dst, int on_device) {
+  double* d = on_device ? dst : c->io64b;
+  if (c->basis_io == PCEXP_BASIS_PAPER) PCEXP_CK(launch_internal_to_paper<T>(src, d, c->Q, c->E, c->nb, c->nv, c->st));
+  else PCEXP_CK(launch_cast<T, double>(src, d, c->K, c->st));
+  if (!on_device) {
+    PCEXP_CK(cudaMemcpyAsync(dst, c->io64b, c->K * sizeof(double), cudaMemcpyDeviceToHost, c->st));
+    PCEXP_CK(cudaStreamSynchronize(c->st));
+  }
+  return PCEXP_OK;
+}
+
+template <class T>
+int refresh_shadow(pcexp_ctx* c, int i) {
+  if (c->fp32) PCEXP_CK(launch_cast<double, float>(c->U64[i], reinterpret_cast<float*>(c->S32[i]), c->Kp, c->st));
+  return PCEXP_OK;
+}
+
+// Arnoldi on J(lin) (times escale) started from V[0]; m columns at most.
+template <class T>
+int arnoldi(pcexp_ctx* c, const T* lin, const T* escale, int m) {
+  const DGData<T> d = dgdata<T>(c);
+  T* w = reinterpret_cast<T*>(c->w);
+  T* G = reinterpret_cast<T*>(c->G);
+  T* V = reinterpret_cast<T*>(c->V);
+  (void)G;
+  PCEXP_LAUNCH(c, PCEXP_KC_OTHER, launch_reset_kstate(c->ks, c->st));
+  PCEXP_LAUNCH(c, PCEXP_KC_CGS_NORM, launch_cgs<T>(CGS_NORM, V, c->Kp, c->Kp, 0, V, nullptr, c->ks, c->partials, c->eta, c->st));
+  for (int j = 0; j < m; ++j) {
+    // w = J v_j = s_j J z_j: the basis scale is applied to the output, so every
+    // stored vector stays of the size of ||J|| (no growth like ||J||^j)
+    PCEXP_TRY(dg_apply<T>(c, d, lin, Vcol<T>(c, j), w, escale, &c->ks->done, &c->ks->s[j]));
+    PCEXP_LAUNCH(c, PCEXP_KC_CGS_PROJ, launch_cgs<T>(CGS_PROJ, V, c->Kp, c->Kp, j, w, nullptr, c->ks, c->partials, c->eta, c->st));
+    PCEXP_LAUNCH(c, PCEXP_KC_CGS_UPD_PROJ, launch_cgs<T>(CGS_UPD_PROJ, V, c->Kp, c->Kp, j, w, nullptr, c->ks, c->partials, c->eta, c->st));
+    PCEXP_LAUNCH(c, PCEXP_KC_CGS_UPD_NORM, launch_cgs<T>(CGS_UPD_NORM, V, c->Kp, c->Kp, j, w, Vcol<T>(c, j + 1), c->ks, c->partials, c->eta, c->st));
+  }
+  return PCEXP_OK;
+}
+
+// Stages of Eq. s9 (and s10) once V[0] holds R_n (scaled by escale when given)
+// and ss->dt holds dt.  u_n = U64[cur]; the new state ends in U64[cur] (PCEXP)
+// or U64[1-cur] (EXP1; cur flips).
+template <class T>
+int krylov_stages(pcexp_ctx* c, int scheme, const T* escale, int m) {
+  const DGData<T> d = dgdata<T>(c);
+  const int a = c->cur, b = 1 - c->cur;
+  T* S0 = shadow<T>(c, a);
+  T* S1 = shadow<T>(c, b);
+  T* V = reinterpret_cast<T*>(c->V);
+  T* G = reinterpret_cast<T*>(c->G);
+  T* w = reinterpret_cast<T*>(c->w);
+  T* tmp = reinterpret_cast<T*>(c->tmp);
+  T* delta = reinterpret_cast<T*>(c->delta);
+  // predictor: u_* = u_n + dt phi_1(dt J_n) R_n
+  PCEXP_TRY(arnoldi<T>(c, S0, escale, m));
+  PCEXP_LAUNCH(c, PCEXP_KC_PHI, launch_phi(c->ks, &c->ss->dt, 0.0, 1.0, c->ss, 0, c->st));
+  PCEXP_LAUNCH(c, PCEXP_KC_AXPY, launch_krylov_axpy<T>(c->U64[a], c->U64[b], S1, delta, V, c->Kp, c->Kp, c->ks, c->st));
+  if (scheme == PCEXP_SCHEME_EXP1) {
+    c->cur = b;
+    return PCEXP_OK;
+  }
+  // corrector input N_* - N_n = R(u_*) - R_n - J_n (u_* - u_n)
+  (void)G;
+  PCEXP_TRY(dg_apply<T>(c, d, S1, nullptr, w, escale, nullptr));
+  PCEXP_TRY(dg_apply<T>(c, d, S0, delta, tmp, escale, nullptr));
+  PCEXP_LAUNCH(c, PCEXP_KC_OTHER, launch_combine_corrector<T>(V, w, tmp, c->Kp, c->st));
+  // corrector: u_{n+1} = u_* + dt/2 phi_1(dt J_n) (N_* - N_n)
+  PCEXP_TRY(arnoldi<T>(c, S0, escale, m));
+  PCEXP_LAUNCH(c, PCEXP_KC_PHI, launch_phi(c->ks, &c->ss->dt, 0.0, 0.5, c->ss, 1, c->st));
+  PCEXP_LAUNCH(c, PCEXP_KC_AXPY, launch_krylov_axpy<T>(c->U64[b], c->U64[a], S0, nullptr, V, c->Kp, c->Kp, c->ks, c->st));
+  return PCEXP_OK;
+}
+
+template <class T>
+int step_impl(pcexp_ctx* c, int scheme, int dt_mode, double dt_or_cfl, int m, pcexp_step_info* info) {
+  const DGData<T> d = dgdata<T>(c);
+  T* S0 = shadow<T>(c, c->cur);
+  T* V = reinterpret_cast<T*>(c->V);
+  T* G = reinterpret_cast<T*>(c->G);
+  T* dte = reinterpret_cast<T*>(c->dte);
+  const T* escale = nullptr;
+  PCEXP_CK(cudaMemsetAsync(&c->ss->err, 0, sizeof(int), c->st));
+  (void)G;
+  if (dt_mode == PCEXP_DT_GIVEN) {
+    PCEXP_LAUNCH(c, PCEXP_KC_OTHER, launch_set_dt(c->ss, dt_or_cfl, c->st));
+  } else {
+    PCEXP_LAUNCH(c, PCEXP_KC_DT, launch_local_dt<T>(d, S0, nullptr, dt_or_cfl, dte, &c->ss->dt, c->partials, &c->ss->counter, c->st));
+    if (dt_mode == PCEXP_DT_LOCAL_CFL) {
+      escale = dte;
+      PCEXP_LAUNCH(c, PCEXP_KC_OTHER, launch_set_dt(c->ss, 1.0, c->st));
+    }
+  }
+  PCEXP_TRY(dg_apply<T>(c, d, S0, nullptr, V, nullptr, nullptr));
+  PCEXP_LAUNCH(c, PCEXP_KC_OTHER, launch_density_norm<T>(V, nullptr, c->E, c->nb, c->nv, c->volume, c->ss, c->partials, 0, c->p, 0.0, c->st));
+  if (escale) PCEXP_LAUNCH(c, PCEXP_KC_OTHER, launch_scale_elements<T>(V, escale, c->E, c->nv * c->nb, c->st));
+  PCEXP_TRY(krylov_stages<T>(c, scheme, escale, m));
+  if (info) {
+    StepState h;
+    PCEXP_CK(cudaMemcpyAsync(&h, c->ss, sizeof(h), cudaMemcpyDeviceToHost, c->st));
+    PCEXP_CK(cudaStreamSynchronize(c->st));
+    info->krylov_dim[0] = h.k[0];
+    info->krylov_dim[1] = scheme == PCEXP_SCHEME_EXP1 ? 0 : h.k[1];
+    info->beta[0] = h.beta[0];
+    info->beta[1] = scheme == PCEXP_SCHEME_EXP1 ? 0.0 : h.beta[1];
+    info->dt = h.dt;
+    info->res_norm = h.res_norm;
+    if (h.err) {
+      g_last_error = "non-finite norm, beta or Hessenberg entry";
+      return PCEXP_ERR_NONFINITE;
+    }
+  }
+  return PCEXP_OK;
+}
+
+template <class T>
+int march_impl(pcexp_ctx* c, int scheme, double cfl_max, double decades, int max_iter, int m,
+               pcexp_steady_info* info) {
+  const DGData<T> d = dgdata<T>(c);
+  T* V = reinterpret_cast<T*>(c->V);
+  T* G = reinterpret_cast<T*>(c->G);
+  T* dte = reinterpret_cast<T*>(c->dte);
+  double r1 = -1, rn = -1;
+  int n = 1;
+  bool conv = false;
+  for (; n <= max_iter + 1; ++n) {
+    T* S0 = shadow<T>(c, c->cur);
+    PCEXP_CK(cudaMemsetAsync(&c->ss->err, 0, sizeof(int), c->st));
+    (void)G;
+    PCEXP_TRY(dg_apply<T>(c, d, S0, nullptr, V, nullptr, nullptr));
+    PCEXP_LAUNCH(c, PCEXP_KC_OTHER, launch_density_norm<T>(V, nullptr, c->E, c->nb, c->nv, c->volume, c->ss, c->partials, n, c->p, cfl_max, c->st));
+    StepState h;
+    PCEXP_CK(cudaMemcpyAsync(&h, c->ss, sizeof(h), cudaMemcpyDeviceToHost, c->st));
+    PCEXP_CK(cudaStreamSynchronize(c->st));
+    rn = h.res_norm;
+    if (!std::isfinite(rn)) {
+      g_last_error = "non-finite residual norm";
+      return PCEXP_ERR_NONFINITE;
+    }
+    if (r1 < 0) r1 = rn;
+    if (rn <= r1 * std::pow(10.0, -decades)) {
+      conv = true;
+      break;
+    }
+    if (n > max_iter) break;
+    PCEXP_LAUNCH(c, PCEXP_KC_DT, launch_local_dt<T>(d, S0, &c->ss->cfl, 0.0, dte, &c->ss->dtmin_scratch, c->partials, &c->ss->counter, c->st));
+    PCEXP_LAUNCH(c, PCEXP_KC_OTHER, launch_set_dt(c->ss, 1.0, c->st));
+    PCEXP_LAUNCH(c, PCEXP_KC_OTHER, launch_scale_elements<T>(V, dte, c->E, c->nv * c->nb, c->st));
+    PCEXP_TRY(krylov_stages<T>(c, scheme, dte, m));
+  }
+  if (info) {
+    info->iterations = n - 1;
+    info->res_first = r1;
+    info->res_last = rn;
+    info->converged = conv ? 1 : 0;
+  }
+  return PCEXP_OK;
+}
+
+__global__ void scale_vec_kernel(double* x, const KState* ks, int col, int64_t n) {
+  const double s = ks->s[col];
+  for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) x[i] *= s;
+}
+
+template <class T>
+int arnoldi_abi(pcexp_ctx* c, const double* U, const double* b, int m, double* Vout, double* H, int* k, double* beta,
+                int on_device) {
+  T* lin = reinterpret_cast<T*>(c->delta);
+  PCEXP_TRY(import_vec<T>(c, U, on_device, lin));
+  PCEXP_TRY(import_vec<T>(c, b, on_device, Vcol<T>(c, 0)));
+  PCEXP_TRY(arnoldi<T>(c, lin, nullptr, m));
+  KState hk;
+  PCEXP_CK(cudaMemcpyAsync(&hk, c->ks, sizeof(hk), cudaMemcpyDeviceToHost, c->st));
+  PCEXP_CK(cudaStreamSynchronize(c->st));
+  if (hk.err) {
+    g_last_error = "non-finite Arnoldi quantity";
+    return PCEXP_ERR_NONFINITE;
+  }
+  const int kk = hk.k;
+  if (k) *k = kk;
+  if (beta) *beta = hk.beta;
+  if (H) {
+    for (int i = 0; i <= m; ++i)
+      for (int j = 0; j < m; ++j) H[i * m + j] = (i <= kk && j < kk) ? hk.H[i * MMAX + j] : 0.0;
+  }
+  if (Vout) {
+    const int ncol = hk.done ? kk : kk + 1;
+    for (int j = 0; j <= m; ++j) {
+      double* dst = Vout + (int64_t)j * c->K;
+      if (j < ncol && hk.beta > 0) {
+        double* dd = on_device ? dst : c->io64b;
+        if (c->basis_io == PCEXP_BASIS_PAPER)
+          PCEXP_CK(launch_internal_to_paper<T>(Vcol<T>(c, j), dd, c->Q, c->E, c->nb, c->nv, c->st));
+        else PCEXP_CK(launch_cast<T, double>(Vcol<T>(c, j), dd, c->K, c->st));
+        scale_vec_kernel<<<152 * 4, 256, 0, c->st>>>(dd, c->ks, j, c->K);
+        PCEXP_CK(cudaGetLastError());
+        if (!on_device) {
+          PCEXP_CK(cudaMemcpyAsync(dst, dd, c->K * sizeof(double), cudaMemcpyDeviceToHost, c->st));
+          PCEXP_CK(cudaStreamSynchronize(c->st));
+        }
+      } else if (on_device) {
+        PCEXP_CK(cudaMemsetAsync(dst, 0, c->K * sizeof(double), c->st));
+      } else {
+        std::memset(dst, 0, c->K * sizeof(double));
+      }
+    }
+    PCEXP_CK(cudaStreamSynchronize(c->st));
+  }
+  return PCEXP_OK;
+}
+
+// Host L2 projection of an analytic state onto the internal basis:
+// u_j = sqrt(det) sum_q w^_q U(x_q) phi^_j(xi_q).
+int project_host(pcexp_ctx* c, int kind, const double* prm, int np, std::vector<double>& u) {
+  const Setup& s = c->host;
+  const double g = c->phys.gamma;
+  const double a = c->phys.alpha_deg * M_PI / 180.0;
+  const double cinf = std::sqrt(g * c->phys.p_inf / c->phys.rho_inf);
+  const double u0 = c->phys.mach * cinf * std::cos(a), v0 = c->phys.mach * cinf * std::sin(a);
+  const double rinf = c->phys.rho_inf, pinf = c->phys.p_inf;
+  if (kind == PCEXP_PROJ_VORTEX && np < 4) return PCEXP_ERR_INVALID_ARG;
+  if (kind == PCEXP_PROJ_BLOBS && (np < 1 || (np - 1) % 4)) return PCEXP_ERR_INVALID_ARG;
+  if (kind < 0 || kind > 2) return PCEXP_ERR_INVALID_ARG;
+  u.assign(c->E * c->nv * c->nb, 0.0);
+  for (int64_t e = 0; e < c->E; ++e) {
+    const double sd = s.geo[8 * e + 4];
+    for (int q = 0; q < c->nq; ++q) {
+      const double x = s.xqphys[(e * c->nq + q) * 2], y = s.xqphys[(e * c->nq + q) * 2 + 1];
+      double rho = rinf, uu = u0, vv = v0, p = pinf;
+      if (kind == PCEXP_PROJ_VORTEX) {
+        const double eps = prm[0], period = prm[3];
+        double dx = x - prm[1], dy = y - prm[2];
+        if (period > 0) {
+          dx -= period * std::nearbyint(dx / period);
+          dy -= period * std::nearbyint(dy / period);
+        }
+        const double r2 = dx * dx + dy * dy;
+        const double f = eps / (2 * M_PI) * std::exp(0.5 * (1 - r2));
+        uu = u0 - f * dy;
+        vv = v0 + f * dx;
+        const double Tinf = pinf / rinf;
+        const double T = Tinf - (g - 1) * eps * eps / (8 * g * M_PI * M_PI) * std::exp(1 - r2);
+        rho = rinf * std::pow(T / Tinf, 1.0 / (g - 1));
+        p = rho * T;
+      } else if (kind == PCEXP_PROJ_BLOBS) {
+        const double R = prm[0];
+        for (int b = 0; b < (np - 1) / 4; ++b) {
+          const double* bb = prm + 1 + 4 * b;
+          const double wgt = std::exp(-((x - bb[0]) * (x - bb[0]) + (y - bb[1]) * (y - bb[1])) / (R * R));
+          rho += bb[2] * wgt;
+          p += bb[3] * wgt;
+        }
+      }
+      const double U[4] = {rho, rho * uu, rho * vv, p / (g - 1) + 0.5 * rho * (uu * uu + vv * vv)};
+      for (int v = 0; v < 4; ++v)
+        for (int j = 0; j < c->nb; ++j)
+          u[(e * c->nv + v) * c->nb + j] += sd * s.Wv[q] * U[v] * s.Bv[q * c->nb + j];
+    }
+  }
+  return PCEXP_OK;
+}
+
+int check_ctx(const pcexp_ctx* c) {
+  if (!c) {
+    g_last_error = "null context";
+    return PCEXP_ERR_INVALID_ARG;
+  }
+  cudaError_t e = cudaSetDevice(c->device);
+  if (e != cudaSuccess) {
+    g_last_error = cudaGetErrorString(e);
+    return PCEXP_ERR_CUDA;
+  }
+  return PCEXP_OK;
+}
+
+int create_impl(pcexp_ctx* c, const pcexp_mesh* mesh, int p, const pcexp_physics* phys, const pcexp_options* opt) {
+  std::string msg;
+  int r = build_setup(*mesh, p, c->host, msg);
+  if (r != PCEXP_OK) {
+    g_last_error = msg;
+    return r;
+  }
+  const Setup& s = c->host;
+  c->p = p;
+  c->nb = s.nb;
+  c->nq = s.nq;
+  c->nfq = s.nfq;
+  c->E = s.E;
+  c->F = s.F;
+  c->K = c->E * c->nv * c->nb;
+  c->Kp = (c->K + VPAD - 1) / VPAD * VPAD;
+  c->volume = s.volume;
+  c->phys = *phys;
+  c->fp32 = opt->precision == PCEXP_FP32_MIXED;
+  c->m_max = opt->m_max;
+  c->eta = opt->breakdown_eta > 0 ? opt->breakdown_eta : (c->fp32 ? 1e-6 : 1e-12);
+  c->basis_io = opt->basis_io;
+  // tables
+  std::vector<double> tabs;
+  tabs.insert(tabs.end(), s.Bv.begin(), s.Bv.end());
+  tabs.insert(tabs.end(), s.Dv.begin(), s.Dv.end());
+  tabs.insert(tabs.end(), s.Bf.begin(), s.Bf.end());
+  tabs.insert(tabs.end(), s.Wf.begin(), s.Wf.end());
+  tabs.insert(tabs.end(), s.Bc.begin(), s.Bc.end());
+  const size_t es = c->fp32 ? sizeof(float) : sizeof(double);
+  if (c->fp32) {
+    PCEXP_TRY(upload<float>(c, &c->tabs, tabs));
+    PCEXP_TRY(upload<float>(c, &c->geo, s.geo));
+    PCEXP_TRY(upload<float>(c, &c->fgeo, s.fgeo));
+  } else {
+    PCEXP_TRY(upload<double>(c, &c->tabs, tabs));
+    PCEXP_TRY(upload<double>(c, &c->geo, s.geo));
+    PCEXP_TRY(upload<double>(c, &c->fgeo, s.fgeo));
+  }
+  void* q = nullptr;
+  PCEXP_TRY(upload<double>(c, &q, s.Q));
+  c->Q = reinterpret_cast<double*>(q);
+  PCEXP_TRY(dalloc(c, &c->ef, s.ef.size()));
+  PCEXP_TRY(dalloc(c, &c->fel, s.fel.size() + 2));
+  PCEXP_TRY(dalloc(c, &c->floc, s.floc.size() + 1));
+  PCEXP_CK(cudaMemcpyAsync(c->ef, s.ef.data(), s.ef.size() * 4, cudaMemcpyHostToDevice, c->st));
+  if (s.F) {
+    PCEXP_CK(cudaMemcpyAsync(c->fel, s.fel.data(), s.fel.size() * 4, cudaMemcpyHostToDevice, c->st));
+    PCEXP_CK(cudaMemcpyAsync(c->floc, s.floc.data(), s.floc.size() * 4, cudaMemcpyHostToDevice, c->st));
+  }
+  // state and work vectors
+  const int64_t Kp = c->Kp;
+  for (int i = 0; i < 2; ++i) PCEXP_TRY(dalloc(c, &c->U64[i], Kp));
+  auto valloc = [&](void** p, size_t n) -> int {
+    if (c->fp32) {
+      float* f = nullptr;
+      int rr = dalloc(c, &f, n);
+      *p = f;
+      return rr;
+    }
+    double* d = nullptr;
+    int rr = dalloc(c, &d, n);
+    *p = d;
+    return rr;
+  };
+  if (c->fp32)
+    for (int i = 0; i < 2; ++i) PCEXP_TRY(valloc(&c->S32[i], Kp));
+  PCEXP_TRY(valloc(&c->V, (size_t)(c->m_max + 1) * Kp));
+  PCEXP_TRY(valloc(&c->w, Kp));
+  PCEXP_TRY(valloc(&c->tmp, Kp));
+  PCEXP_TRY(valloc(&c->delta, Kp));
+  PCEXP_TRY(valloc(&c->G, (size_t)(c->F > 0 ? c->F : 1) * c->nfq * 4));
+  PCEXP_TRY(valloc(&c->dte, c->E));
+  PCEXP_TRY(dalloc(c, &c->io64a, Kp));
+  PCEXP_TRY(dalloc(c, &c->io64b, Kp));
+  PCEXP_TRY(dalloc(c, &c->ks, 1));
+  PCEXP_TRY(dalloc(c, &c->ss, 1));
+  PCEXP_TRY(dalloc(c, &c->partials, (size_t)RED_BLOCKS * (MMAX + 2)));
+  (void)es;
+  PCEXP_CK(cudaStreamSynchronize(c->st));
+  // free-stream initial state
+  std::vector<double> u;
+  PCEXP_TRY(project_host(c, PCEXP_PROJ_FREESTREAM, nullptr, 0, u));
+  PCEXP_CK(cudaMemcpyAsync(c->U64[0], u.data(), u.size() * 8, cudaMemcpyHostToDevice, c->st));
+  PCEXP_TRY(refresh_shadow<double>(c, 0));
+  PCEXP_CK(cudaStreamSynchronize(c->st));
+  return PCEXP_OK;
+}
+
+}  // namespace
+
+extern "C" {
+
+int pcexp_create(pcexp_ctx** out, const pcexp_mesh* mesh, int p, const pcexp_physics* phys,
+                 const pcexp_options* opt, void* cuda_stream) {
+  if (!out) return PCEXP_ERR_INVALID_ARG;
+  *out = nullptr;
+  if (!mesh || !phys || !opt) return PCEXP_ERR_INVALID_ARG;
+  if (opt->m_max < 1 || opt->m_max > PCEXP_MAX_KRYLOV) return PCEXP_ERR_INVALID_ARG;
+  if (opt->precision != PCEXP_FP64 && opt->precision != PCEXP_FP32_MIXED) return PCEXP_ERR_INVALID_ARG;
+  if (opt->basis_io != PCEXP_BASIS_PAPER && opt->basis_io != PCEXP_BASIS_INTERNAL) return PCEXP_ERR_INVALID_ARG;
+  if (!(phys->gamma > 1.0) || !(phys->rho_inf > 0) || !(phys->p_inf > 0)) return PCEXP_ERR_INVALID_ARG;
+  pcexp_ctx* c = new pcexp_ctx();
+  cudaGetDevice(&c->device);
+  c->st = reinterpret_cast<cudaStream_t>(cuda_stream);
+  int r = create_impl(c, mesh, p, phys, opt);
+  if (r != PCEXP_OK) {
+    std::string keep = g_last_error;
+    pcexp_destroy(c);
+    g_last_error = keep;
+    return r;
+  }
+  *out = c;
+  return PCEXP_OK;
+}
+
+int pcexp_destroy(pcexp_ctx* c) {
+  if (!c) return PCEXP_OK;
+  cudaSetDevice(c->device);
+  cudaStreamSynchronize(c->st);
+  for (void* p : c->allocs) cudaFree(p);
+  for (cudaEvent_t e : c->ev_pool) cudaEventDestroy(e);
+  delete c;
+  return PCEXP_OK;
+}
+
+int pcexp_sizes(const pcexp_ctx* c, int64_t* n_elem, int32_t* n_basis, int32_t* n_var, int64_t* K) {
+  if (!c) return PCEXP_ERR_INVALID_ARG;
+  if (n_elem) *n_elem = c->E;
+  if (n_basis) *n_basis = c->nb;
+  if (n_var) *n_var = c->nv;
+  if (K) *K = c->K;
+  return PCEXP_OK;
+}
+
+int pcexp_set_state(pcexp_ctx* c, const double* U, int on_device) {
+  PCEXP_TRY(check_ctx(c));
+  if (!U) return PCEXP_ERR_INVALID_ARG;
+  PCEXP_TRY(import_vec<double>(c, U, on_device, c->U64[c->cur]));
+  PCEXP_TRY(refresh_shadow<double>(c, c->cur));
+  PCEXP_CK(cudaStreamSynchronize(c->st));
+  return PCEXP_OK;
+}
+
+int pcexp_get_state(pcexp_ctx* c, double* U, int on_device) {
+  PCEXP_TRY(check_ctx(c));
+  if (!U) return PCEXP_ERR_INVALID_ARG;
+  return export_vec<double>(c, c->U64[c->cur], U, on_device);
+}
+
+int pcexp_project_state(pcexp_ctx* c, int kind, const double* params, int n_params) {
+  PCEXP_TRY(check_ctx(c));
+  if (n_params > 0 && !params) return PCEXP_ERR_INVALID_ARG;
+  std::vector<double> u;
+  PCEXP_TRY(project_host(c, kind, params, n_params, u));
+  PCEXP_CK(cudaMemcpyAsync(c->U64[c->cur], u.data(), u.size() * 8, cudaMemcpyHostToDevice, c->st));
+  PCEXP_TRY(refresh_shadow<double>(c, c->cur));
+  PCEXP_CK(cudaStreamSynchronize(c->st));
+  return PCEXP_OK;
+}
+
+int pcexp_residual(pcexp_ctx* c, const double* U, double* R, int on_device) {
+  PCEXP_TRY(check_ctx(c));
+  if (!U || !R) return PCEXP_ERR_INVALID_ARG;
+  if (c->fp32) {
+    float* in = reinterpret_cast<float*>(c->tmp);
+    float* out = reinterpret_cast<float*>(c->w);
+    PCEXP_TRY(import_vec<float>(c, U, on_device, in));
+    PCEXP_CK(launch_dg_operator<float>(dgdata<float>(c), in, nullptr, out, reinterpret_cast<float*>(c->G), nullptr, nullptr, c->st));
+    PCEXP_TRY(export_vec<float>(c, out, R, on_device));
+  } else {
+    double* in = reinterpret_cast<double*>(c->tmp);
+    double* out = reinterpret_cast<double*>(c->w);
+    PCEXP_TRY(import_vec<double>(c, U, on_device, in));
+    PCEXP_CK(launch_dg_operator<double>(dgdata<double>(c), in, nullptr, out, reinterpret_cast<double*>(c->G), nullptr, nullptr, c->st));
+    PCEXP_TRY(export_vec<double>(c, out, R, on_device));
+  }
+  if (on_device) PCEXP_CK(cudaStreamSynchronize(c->st));
+  return PCEXP_OK;
+}
+
+int pcexp_jvp(pcexp_ctx* c, const double* U, const double* v, double* Jv, int on_device) {
+  PCEXP_TRY(check_ctx(c));
+  if (!U || !v || !Jv) return PCEXP_ERR_INVALID_ARG;
+  if (c->fp32) {
+    float* a = reinterpret_cast<float*>(c->tmp);
+    float* b = reinterpret_cast<float*>(c->delta);
+    float* o = reinterpret_cast<float*>(c->w);
+    PCEXP_TRY(import_vec<float>(c, U, on_device, a));
+    PCEXP_TRY(import_vec<float>(c, v, on_device, b));
+    PCEXP_CK(launch_dg_operator<float>(dgdata<float>(c), a, b, o, reinterpret_cast<float*>(c->G), nullptr, nullptr, c->st));
+    PCEXP_TRY(export_vec<float>(c, o, Jv, on_device));
+  } else {
+    double* a = reinterpret_cast<double*>(c->tmp);
+    double* b = reinterpret_cast<double*>(c->delta);
+    double* o = reinterpret_cast<double*>(c->w);
+    PCEXP_TRY(import_vec<double>(c, U, on_device, a));
+    PCEXP_TRY(import_vec<double>(c, v, on_device, b));
+    PCEXP_CK(launch_dg_operator<double>(dgdata<double>(c), a, b, o, reinterpret_cast<double*>(c->G), nullptr, nullptr, c->st));
+    PCEXP_TRY(export_vec<double>(c, o, Jv, on_device));
+  }
+  if (on_device) PCEXP_CK(cudaStreamSynchronize(c->st));
+  return PCEXP_OK;
+}
+
+int pcexp_compute_dt(pcexp_ctx* c, double cfl, int local, double* dt, int on_device) {
+  PCEXP_TRY(check_ctx(c));
+  if (!dt || !(cfl > 0)) return PCEXP_ERR_INVALID_ARG;
+  if (c->fp32) {
+    float* dte = reinterpret_cast<float*>(c->dte);
+    PCEXP_CK(launch_local_dt<float>(dgdata<float>(c), shadow<float>(c, c->cur), nullptr, cfl, dte, &c->ss->dtmin_scratch,
+                                     c->partials, &c->ss->counter, c->st));
+    if (local) PCEXP_CK(launch_cast<float, double>(dte, c->io64b, c->E, c->st));
+  } else {
+    double* dte = reinterpret_cast<double*>(c->dte);
+    PCEXP_CK(launch_local_dt<double>(dgdata<double>(c), shadow<double>(c, c->cur), nullptr, cfl, dte, &c->ss->dtmin_scratch,
+                                      c->partials, &c->ss->counter, c->st));
+    if (local) PCEXP_CK(cudaMemcpyAsync(c->io64b, dte, c->E * 8, cudaMemcpyDeviceToDevice, c->st));
+  }
+  const double* src = local ? c->io64b : &c->ss->dtmin_scratch;
+  const size_t n = local ? (size_t)c->E : 1;
+  PCEXP_CK(cudaMemcpyAsync(dt, src, n * 8, on_device ? cudaMemcpyDeviceToDevice : cudaMemcpyDeviceToHost, c->st));
+  PCEXP_CK(cudaStreamSynchronize(c->st));
+  return PCEXP_OK;
+}
+
+int pcexp_arnoldi(pcexp_ctx* c, const double* U, const double* b, int m, double* V, double* H, int* k, double* beta,
+                  int on_device) {
+  PCEXP_TRY(check_ctx(c));
+  if (!U || !b || m < 1 || m > c->m_max) return PCEXP_ERR_INVALID_ARG;
+  if (c->fp32) return arnoldi_abi<float>(c, U, b, m, V, H, k, beta, on_device);
+  return arnoldi_abi<double>(c, U, b, m, V, H, k, beta, on_device);
+}
+
+int pcexp_phi(pcexp_ctx* c, const double* H, int k, int ldh, double dt, double* phi1, double* phi2) {
+  PCEXP_TRY(check_ctx(c));
+  if (!H || !phi1 || k < 1 || k > PCEXP_MAX_KRYLOV || ldh < k) return PCEXP_ERR_INVALID_ARG;
+  KState hk;
+  std::memset(&hk, 0, sizeof(hk));
+  for (int i = 0; i < k; ++i)
+    for (int j = 0; j < k; ++j) hk.H[i * MMAX + j] = H[i * ldh + j];
+  for (int i = 0; i <= MMAX; ++i) hk.s[i] = 1.0;
+  hk.k = k;
+  hk.beta = 1.0;
+  PCEXP_CK(cudaMemcpyAsync(c->ks, &hk, sizeof(hk), cudaMemcpyHostToDevice, c->st));
+  PCEXP_CK(launch_phi(c->ks, nullptr, dt, 1.0, nullptr, 0, c->st));
+  PCEXP_CK(cudaMemcpyAsync(&hk, c->ks, sizeof(hk), cudaMemcpyDeviceToHost, c->st));
+  PCEXP_CK(cudaStreamSynchronize(c->st));
+  if (hk.err) return PCEXP_ERR_NONFINITE;
+  for (int i = 0; i < k; ++i) {
+    phi1[i] = hk.y[i];
+    if (phi2) phi2[i] = hk.y2[i];
+  }
+  return PCEXP_OK;
+}
+
+int pcexp_step(pcexp_ctx* c, int scheme, int dt_mode, double dt_or_cfl, int m, pcexp_step_info* info) {
+  PCEXP_TRY(check_ctx(c));
+  if (scheme != PCEXP_SCHEME_PCEXP && scheme != PCEXP_SCHEME_EXP1) return PCEXP_ERR_INVALID_ARG;
+  if (dt_mode < PCEXP_DT_GIVEN || dt_mode > PCEXP_DT_LOCAL_CFL) return PCEXP_ERR_INVALID_ARG;
+  if (m < 1 || m > c->m_max || !(dt_or_cfl > 0) || !std::isfinite(dt_or_cfl)) return PCEXP_ERR_INVALID_ARG;
+  if (c->fp32) return step_impl<float>(c, scheme, dt_mode, dt_or_cfl, m, info);
+  return step_impl<double>(c, scheme, dt_mode, dt_or_cfl, m, info);
+}
+
+int pcexp_march_steady(pcexp_ctx* c, int scheme, double cfl_max, double decades, int max_iter, int m,
+                       pcexp_steady_info* info) {
+  PCEXP_TRY(check_ctx(c));
+  if (scheme != PCEXP_SCHEME_PCEXP && scheme != PCEXP_SCHEME_EXP1) return PCEXP_ERR_INVALID_ARG;
+  if (m < 1 || m > c->m_max || !(cfl_max > 0) || !(decades > 0) || max_iter < 0) return PCEXP_ERR_INVALID_ARG;
+  if (c->fp32) return march_impl<float>(c, scheme, cfl_max, decades, max_iter, m, info);
+  return march_impl<double>(c, scheme, cfl_max, decades, max_iter, m, info);
+}
+
+int pcexp_output(pcexp_ctx* c, int kind, double* value) {
+  PCEXP_TRY(check_ctx(c));
+  if (!value) return PCEXP_ERR_INVALID_ARG;
+  if (kind != 0) return PCEXP_ERR_UNSUPPORTED;
+  if (c->fp32) {
+    float* V = reinterpret_cast<float*>(c->V);
+    PCEXP_CK(launch_dg_operator<float>(dgdata<float>(c), shadow<float>(c, c->cur), nullptr, V, reinterpret_cast<float*>(c->G),
+                                        nullptr, nullptr, c->st));
+    PCEXP_CK(launch_density_norm<float>(V, nullptr, c->E, c->nb, c->nv, c->volume, c->ss, c->partials, 0, c->p, 0.0, c->st));
+  } else {
+    double* V = reinterpret_cast<double*>(c->V);
+    PCEXP_CK(launch_dg_operator<double>(dgdata<double>(c), shadow<double>(c, c->cur), nullptr, V, reinterpret_cast<double*>(c->G),
+                                         nullptr, nullptr, c->st));
+    PCEXP_CK(launch_density_norm<double>(V, nullptr, c->E, c->nb, c->nv, c->volume, c->ss, c->partials, 0, c->p, 0.0, c->st));
+  }
+  StepState h;
+  PCEXP_CK(cudaMemcpyAsync(&h, c->ss, sizeof(h), cudaMemcpyDeviceToHost, c->st));
+  PCEXP_CK(cudaStreamSynchronize(c->st));
+  *value = h.res_norm;
+  return PCEXP_OK;
+}
+
+int pcexp_profile_enable(pcexp_ctx* c, int enable) {
+  PCEXP_TRY(check_ctx(c));
+  PCEXP_TRY(prof_flush(c));
+  for (int i = 0; i < PCEXP_KC_COUNT; ++i) {
+    c->prof_ms[i] = 0;
+    c->prof_n[i] = 0;
+  }
+  c->prof = enable != 0;
+  return PCEXP_OK;
+}
+
+int pcexp_profile_read(pcexp_ctx* c, int kernel_class, int64_t* launches, double* ms) {
+  PCEXP_TRY(check_ctx(c));
+  if (kernel_class < 0 || kernel_class >= PCEXP_KC_COUNT) return PCEXP_ERR_INVALID_ARG;
+  PCEXP_TRY(prof_flush(c));
+  if (launches) *launches = c->prof_n[kernel_class];
+  if (ms) *ms = c->prof_ms[kernel_class];
+  return PCEXP_OK;
+}
+
+int pcexp_synchronize(pcexp_ctx* c) {
+  PCEXP_TRY(check_ctx(c));
+  PCEXP_CK(cudaStreamSynchronize(c->st));
+  return PCEXP_OK;
+}
+
+const char* pcexp_last_error(void) { return g_last_error.c_str(); }
+
+const char* pcexp_status_string(int status) {
+  switch (status) {
+    case PCEXP_OK: return "ok";
+    case PCEXP_ERR_INVALID_ARG: return "invalid argument";
+    case PCEXP_ERR_MESH: return "invalid mesh";
+    case PCEXP_ERR_CUDA: return "CUDA error";
+    case PCEXP_ERR_OOM: return "out of device memory";
+    case PCEXP_ERR_NONFINITE: return "non-finite value";
+    case PCEXP_ERR_TIMEOUT: return "device wait timed out";
+    case PCEXP_ERR_UNSUPPORTED: return "unsupported request";
+  }
+  return "unknown status";
+}
+
+}  // extern "C"

@@ -1,0 +1,414 @@
+// DG operator kernels: the residual R(u) of Eq. euler3 (Sec. 4.2) and its
+// tangent-linear J(u) v (the exact Jacobian of Eq. jac1 / jac2, applied
+// matrix-free), plus the element time-step rule of Eq. x3d.
+//
+// Basis: a reference-triangle orthonormal basis phi^_j mapped affinely and
+// scaled by |det A_e|^-1/2, so it is orthonormal on every element (the mass
+// matrix is the identity, as with the paper's basis).  With x = v0 + A xi:
+//   U(x_q)        = |det A|^-1/2 sum_j phi^_j(xi_q) u_j
+//   volume term   = |det A|^1/2 sum_q w_q sum_d' d phi^_i/d xi_d'(xi_q) Fhat_d'
+//                   with Fhat_d' = sum_d (A^-1)_{d' d} F_d(U(x_q))
+//   face term     = -|det A|^-1/2 sum_q w_q |e| phi^_i(x_q) F~_n(x_q)
+// Two launches per operator: a face kernel (one thread per face point)
+// writes |e| w_q F~_n into the face-flux buffer G; an element kernel (a tile
+// of elements per block, staged in shared memory) adds the volume term and
+// lifts the face fluxes of its three edges.  Every face flux is computed once
+// and every output is written once, in a fixed order (deterministic).
+#include <cfloat>
+
+#include "kernels.h"
+
+namespace pcexp {
+
+template <int P> struct Ord {
+  static constexpr int NB = (P + 1) * (P + 2) / 2;
+  static constexpr int NQ = (P + 1) * (P + 1);
+  static constexpr int NFQ = P + 1;
+  static constexpr int ET = (256 / NQ) > 128 ? 128 : (256 / NQ);  // elements per block
+};
+
+template <class S> struct PartOf;
+template <> struct PartOf<double> { PCEXP_DEV static double get(double x) { return x; } };
+template <> struct PartOf<float> { PCEXP_DEV static float get(float x) { return x; } };
+template <class T> struct PartOf<Tangent<T>> { PCEXP_DEV static T get(Tangent<T> x) { return x.d; } };
+
+// ------------------------------------------------------------------ face kernel
+template <class T, int P, bool TAN>
+__global__ void __launch_bounds__(256) face_kernel(DGData<T> d, const T* __restrict__ u,
+                                                   const T* __restrict__ du, T* __restrict__ G,
+                                                   const int* __restrict__ skip) {
+  using O = Ord<P>;
+  constexpr int NB = O::NB, NFQ = O::NFQ;
+  using S = typename std::conditional<TAN, Tangent<T>, T>::type;
+  __shared__ T sBf[3 * NFQ * NB];
+  __shared__ T sWf[NFQ];
+  if (skip && *skip) return;
+  for (int i = threadIdx.x; i < 3 * NFQ * NB; i += blockDim.x) sBf[i] = d.Bf[i];
+  for (int i = threadIdx.x; i < NFQ; i += blockDim.x) sWf[i] = d.Wf[i];
+  __syncthreads();
+  const int64_t idx = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (idx >= d.F * NFQ) return;
+  const int64_t f = idx / NFQ;
+  const int q = (int)(idx - f * NFQ);
+  const int eL = d.fel[2 * f], eR = d.fel[2 * f + 1];
+  const int loc = d.floc[f];
+  const int fL = loc & 0xff, fR = loc >> 8;
+  const T nx = d.fgeo[4 * f], ny = d.fgeo[4 * f + 1], len = d.fgeo[4 * f + 2];
+  S UL[4], UR[4];
+  {
+    const T isd = T(1) / d.geo[8 * (int64_t)eL + 4];
+    const T* ue = u + (int64_t)eL * 4 * NB;
+    const T* be = sBf + (fL * NFQ + q) * NB;
+#pragma unroll
+    for (int v = 0; v < 4; ++v) {
+      T a = 0, b = 0;
+#pragma unroll
+      for (int j = 0; j < NB; ++j) {
+        a += be[j] * ue[v * NB + j];
+        if constexpr (TAN) b += be[j] * du[(int64_t)eL * 4 * NB + v * NB + j];
+      }
+      if constexpr (TAN) UL[v] = S{a * isd, b * isd};
+      else UL[v] = a * isd;
+    }
+  }
+  if (eR >= 0) {
+    const T isd = T(1) / d.geo[8 * (int64_t)eR + 4];
+    const T* ue = u + (int64_t)eR * 4 * NB;
+    const T* be = sBf + (fR * NFQ + (NFQ - 1 - q)) * NB;  // R traverses the edge backwards
+#pragma unroll
+    for (int v = 0; v < 4; ++v) {
+      T a = 0, b = 0;
+#pragma unroll
+      for (int j = 0; j < NB; ++j) {
+        a += be[j] * ue[v * NB + j];
+        if constexpr (TAN) b += be[j] * du[(int64_t)eR * 4 * NB + v * NB + j];
+      }
+      if constexpr (TAN) UR[v] = S{a * isd, b * isd};
+      else UR[v] = a * isd;
+    }
+  } else if (-eR == PCEXP_BC_SLIP_WALL) {
+    ghost_slip_wall<S, T>(UL, nx, ny, UR);
+  } else {
+    ghost_farfield<S, T>(UL, nx, ny, d.fs, UR);
+  }
+  S Fn[4];
+  roe_flux<S, T>(UL, UR, nx, ny, d.fs.gamma, Fn);
+  const T wl = len * sWf[q];
+  T* g = G + idx * 4;
+#pragma unroll
+  for (int v = 0; v < 4; ++v) g[v] = wl * PartOf<S>::get(Fn[v]);
+}
+
+// --------------------------------------------------------------- element kernel
+template <class T, int P, bool TAN>
+__global__ void __launch_bounds__(256) elem_kernel(DGData<T> d, const T* __restrict__ u,
+                                                   const T* __restrict__ du, const T* __restrict__ G,
+                                                   T* __restrict__ out, const T* __restrict__ escale,
+                                                   const int* __restrict__ skip, const double* __restrict__ oscale) {
+  using O = Ord<P>;
+  constexpr int NB = O::NB, NQ = O::NQ, NFQ = O::NFQ, ET = O::ET, NVB = 4 * NB;
+  using S = typename std::conditional<TAN, Tangent<T>, T>::type;
+  __shared__ T sBv[NQ * NB];
+  __shared__ T sDv[2 * NQ * NB];
+  __shared__ T sBf[3 * NFQ * NB];
+  __shared__ T su[ET * NVB];
+  __shared__ T sdu[TAN ? ET * NVB : 1];
+  __shared__ T sF[ET * NQ * 8];
+  __shared__ T sgeo[ET * 8];
+  if (skip && *skip) return;
+  const int64_t e0 = (int64_t)blockIdx.x * ET;
+  const int ne = (int)((d.E - e0) < ET ? (d.E - e0) : ET);
+  for (int i = threadIdx.x; i < NQ * NB; i += blockDim.x) sBv[i] = d.Bv[i];
+  for (int i = threadIdx.x; i < 2 * NQ * NB; i += blockDim.x) sDv[i] = d.Dv[i];
+  for (int i = threadIdx.x; i < 3 * NFQ * NB; i += blockDim.x) sBf[i] = d.Bf[i];
+  for (int i = threadIdx.x; i < ne * NVB; i += blockDim.x) {
+    su[i] = u[e0 * NVB + i];
+    if constexpr (TAN) sdu[i] = du[e0 * NVB + i];
+  }
+  for (int i = threadIdx.x; i < ne * 8; i += blockDim.x) sgeo[i] = d.geo[e0 * 8 + i];
+  __syncthreads();
+  const T g = d.fs.gamma;
+  const T osc = oscale ? (T)*oscale : T(1);
+  // phase 1: flux at each volume point, mapped to reference directions
+  for (int it = threadIdx.x; it < ne * NQ; it += blockDim.x) {
+    const int el = it / NQ, q = it - el * NQ;
+    const T* ge = sgeo + el * 8;
+    const T isd = T(1) / ge[4];
+    S U[4];
+#pragma unroll
+    for (int v = 0; v < 4; ++v) {
+      T a = 0, b = 0;
+#pragma unroll
+      for (int j = 0; j < NB; ++j) {
+        a += sBv[q * NB + j] * su[el * NVB + v * NB + j];
+        if constexpr (TAN) b += sBv[q * NB + j] * sdu[el * NVB + v * NB + j];
+      }
+      if constexpr (TAN) U[v] = S{a * isd, b * isd};
+      else U[v] = a * isd;
+    }
+    S Fx[4], Fy[4];
+    euler_flux<S, T>(U, g, Fx, Fy);
+    T* fo = sF + (el * NQ + q) * 8;
+#pragma unroll
+    for (int v = 0; v < 4; ++v) {
+      const T fx = PartOf<S>::get(Fx[v]), fy = PartOf<S>::get(Fy[v]);
+      fo[v] = ge[0] * fx + ge[1] * fy;
+      fo[4 + v] = ge[2] * fx + ge[3] * fy;
+    }
+  }
+  __syncthreads();
+  // phase 2: test against grad phi, lift the three face fluxes
+  for (int it = threadIdx.x; it < ne * NVB; it += blockDim.x) {
+    const int el = it / NVB, r = it - el * NVB;
+    const int v = r / NB, i = r - v * NB;
+    const T sd = sgeo[el * 8 + 4];
+    T acc = 0;
+#pragma unroll
+    for (int q = 0; q < NQ; ++q)
+      acc += sDv[q * NB + i] * sF[(el * NQ + q) * 8 + v] + sDv[(NQ + q) * NB + i] * sF[(el * NQ + q) * 8 + 4 + v];
+    acc *= sd;
+    const int64_t e = e0 + el;
+    T lift = 0;
+#pragma unroll
+    for (int k = 0; k < 3; ++k) {
+      const int fs = d.ef[3 * e + k];
+      const int64_t face = fs >> 1;
+      const T* gf = G + face * NFQ * 4;
+      if (fs & 1) {
+#pragma unroll
+        for (int q = 0; q < NFQ; ++q) lift += sBf[(k * NFQ + (NFQ - 1 - q)) * NB + i] * gf[q * 4 + v];
+      } else {
+#pragma unroll
+        for (int q = 0; q < NFQ; ++q) lift -= sBf[(k * NFQ + q) * NB + i] * gf[q * 4 + v];
+      }
+    }
+    acc = (acc + lift / sd) * osc;
+    if (escale) acc *= escale[e];
+    out[e0 * NVB + it] = acc;
+  }
+}
+
+template <class T, int P>
+static cudaError_t dg_op_p(const DGData<T>& d, const T* u, const T* du, T* out, T* G, const T* escale,
+                           const int* skip, const double* oscale, cudaStream_t st, const cudaEvent_t* ev) {
+  using O = Ord<P>;
+  const int64_t nfp = d.F * O::NFQ;
+  if (ev) cudaEventRecord(ev[0], st);
+  if (nfp > 0) {
+    const int64_t nb = (nfp + 255) / 256;
+    if (du) face_kernel<T, P, true><<<(unsigned)nb, 256, 0, st>>>(d, u, du, G, skip);
+    else face_kernel<T, P, false><<<(unsigned)nb, 256, 0, st>>>(d, u, du, G, skip);
+  }
+  if (ev) cudaEventRecord(ev[1], st);
+  const int64_t eb = (d.E + O::ET - 1) / O::ET;
+  if (du) elem_kernel<T, P, true><<<(unsigned)eb, 256, 0, st>>>(d, u, du, G, out, escale, skip, oscale);
+  else elem_kernel<T, P, false><<<(unsigned)eb, 256, 0, st>>>(d, u, du, G, out, escale, skip, oscale);
+  if (ev) cudaEventRecord(ev[2], st);
+  return cudaGetLastError();
+}
+
+template <class T>
+cudaError_t launch_dg_operator(const DGData<T>& d, const T* u, const T* du, T* out, T* G, const T* escale,
+                               const int* skip, cudaStream_t st, const cudaEvent_t* ev, const double* oscale) {
+  switch (d.p) {
+    case 0: return dg_op_p<T, 0>(d, u, du, out, G, escale, skip, oscale, st, ev);
+    case 1: return dg_op_p<T, 1>(d, u, du, out, G, escale, skip, oscale, st, ev);
+    case 2: return dg_op_p<T, 2>(d, u, du, out, G, escale, skip, oscale, st, ev);
+    case 3: return dg_op_p<T, 3>(d, u, du, out, G, escale, skip, oscale, st, ev);
+  }
+  return cudaErrorInvalidValue;
+}
+
+// ------------------------------------------------------------------ time step
+// dt_e = CFL h_e / ((2p+1)(|v| + c)) with v, c at the element centroid (Eq. x3d).
+template <class T, int P>
+__global__ void __launch_bounds__(256) local_dt_kernel(DGData<T> d, const T* __restrict__ u,
+                                                       const double* cfl_dev, double cfl_host,
+                                                       T* __restrict__ dte, double* __restrict__ dtmin,
+                                                       double* __restrict__ partials,
+                                                       unsigned* __restrict__ counter) {
+  constexpr int NB = Ord<P>::NB;
+  __shared__ double red[8];
+  __shared__ bool last;
+  const double cfl = cfl_dev ? *cfl_dev : cfl_host;
+  double mn = DBL_MAX;
+  for (int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; e < d.E; e += (int64_t)gridDim.x * blockDim.x) {
+    const T isd = T(1) / d.geo[8 * e + 4];
+    double U[4];
+    for (int v = 0; v < 4; ++v) {
+      T a = 0;
+      for (int j = 0; j < NB; ++j) a += d.Bc[j] * u[e * 4 * NB + v * NB + j];
+      U[v] = (double)(a * isd);
+    }
+    const double gam = (double)d.fs.gamma;
+    const double ux = U[1] / U[0], uy = U[2] / U[0];
+    const double p = (gam - 1.0) * (U[3] - 0.5 * U[0] * (ux * ux + uy * uy));
+    const double c = sqrt(gam * p / U[0]);
+    const double h = (double)d.geo[8 * e + 5];
+    const double dt = cfl * h / ((2 * d.p + 1) * (sqrt(ux * ux + uy * uy) + c));
+    if (dte) dte[e] = (T)dt;
+    mn = fmin(mn, dt);
+  }
+  for (int o = 16; o > 0; o >>= 1) mn = fmin(mn, __shfl_xor_sync(0xffffffffu, mn, o));
+  if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = mn;
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    double b = red[0];
+    for (int w = 1; w < (int)(blockDim.x >> 5); ++w) b = fmin(b, red[w]);
+    partials[blockIdx.x] = b;
+    __threadfence();
+    last = atomicAdd(counter, 1u) == gridDim.x - 1;
+  }
+  __syncthreads();
+  if (last && threadIdx.x == 0) {
+    double b = DBL_MAX;
+    for (unsigned i = 0; i < gridDim.x; ++i) b = fmin(b, __ldcg(partials + i));
+    *dtmin = b;
+    *counter = 0;
+  }
+}
+
+template <class T>
+cudaError_t launch_local_dt(const DGData<T>& d, const T* u, const double* cfl_dev, double cfl, T* dte,
+                            double* dtmin, double* partials, unsigned* counter, cudaStream_t st) {
+  int64_t nb = (d.E + 255) / 256;
+  if (nb > RED_BLOCKS) nb = RED_BLOCKS;
+  switch (d.p) {
+    case 0: local_dt_kernel<T, 0><<<(unsigned)nb, 256, 0, st>>>(d, u, cfl_dev, cfl, dte, dtmin, partials, counter); break;
+    case 1: local_dt_kernel<T, 1><<<(unsigned)nb, 256, 0, st>>>(d, u, cfl_dev, cfl, dte, dtmin, partials, counter); break;
+    case 2: local_dt_kernel<T, 2><<<(unsigned)nb, 256, 0, st>>>(d, u, cfl_dev, cfl, dte, dtmin, partials, counter); break;
+    case 3: local_dt_kernel<T, 3><<<(unsigned)nb, 256, 0, st>>>(d, u, cfl_dev, cfl, dte, dtmin, partials, counter); break;
+    default: return cudaErrorInvalidValue;
+  }
+  return cudaGetLastError();
+}
+
+// ------------------------------------------------------------ basis conversion
+template <class T>
+__global__ void paper_to_internal_kernel(const double* __restrict__ src, T* __restrict__ dst,
+                                         const double* __restrict__ Q, int64_t E, int nb, int nv) {
+  const int64_t n = E * nv * nb;
+  for (int64_t idx = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; idx < n; idx += (int64_t)gridDim.x * blockDim.x) {
+    const int64_t e = idx / (nv * nb);
+    const int r = (int)(idx - e * nv * nb), v = r / nb, j = r - v * nb;
+    const double* q = Q + e * nb * nb;
+    const double* s = src + e * nv * nb + v * nb;
+    double a = 0;
+    for (int i = 0; i < nb; ++i) a += q[i * nb + j] * s[i];
+    dst[idx] = (T)a;
+  }
+}
+
+template <class T>
+__global__ void internal_to_paper_kernel(const T* __restrict__ src, double* __restrict__ dst,
+                                         const double* __restrict__ Q, int64_t E, int nb, int nv) {
+  const int64_t n = E * nv * nb;
+  for (int64_t idx = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; idx < n; idx += (int64_t)gridDim.x * blockDim.x) {
+    const int64_t e = idx / (nv * nb);
+    const int r = (int)(idx - e * nv * nb), v = r / nb, i = r - v * nb;
+    const double* q = Q + e * nb * nb + i * nb;
+    const T* s = src + e * nv * nb + v * nb;
+    double a = 0;
+    for (int j = 0; j < nb; ++j) a += q[j] * (double)s[j];
+    dst[idx] = a;
+  }
+}
+
+static unsigned grid_for(int64_t n) {
+  int64_t b = (n + 255) / 256;
+  if (b > 152 * 16) b = 152 * 16;
+  return (unsigned)(b < 1 ? 1 : b);
+}
+
+template <class T>
+cudaError_t launch_paper_to_internal(const double* src, T* dst, const double* Q, int64_t E, int nb, int nv, cudaStream_t st) {
+  paper_to_internal_kernel<T><<<grid_for(E * nb * nv), 256, 0, st>>>(src, dst, Q, E, nb, nv);
+  return cudaGetLastError();
+}
+template <class T>
+cudaError_t launch_internal_to_paper(const T* src, double* dst, const double* Q, int64_t E, int nb, int nv, cudaStream_t st) {
+  internal_to_paper_kernel<T><<<grid_for(E * nb * nv), 256, 0, st>>>(src, dst, Q, E, nb, nv);
+  return cudaGetLastError();
+}
+
+template <class T>
+__global__ void scale_elements_kernel(T* __restrict__ x, const T* __restrict__ s, int64_t E, int nvb) {
+  const int64_t n = E * nvb;
+  for (int64_t idx = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; idx < n; idx += (int64_t)gridDim.x * blockDim.x)
+    x[idx] *= s[idx / nvb];
+}
+template <class T>
+cudaError_t launch_scale_elements(T* x, const T* s, int64_t E, int nvb, cudaStream_t st) {
+  scale_elements_kernel<T><<<grid_for(E * nvb), 256, 0, st>>>(x, s, E, nvb);
+  return cudaGetLastError();
+}
+
+// Density residual norm of Eq. cfl with the orthonormal basis:
+// (1/|Omega|) sqrt(sum_e sum_i (R[e][0][i] / s_e)^2); then CFL(n) of Eq. cfl.
+template <class T>
+__global__ void __launch_bounds__(256) density_norm_kernel(const T* __restrict__ R, const T* __restrict__ s,
+                                                           int64_t E, int nb, int nv, double volume,
+                                                           StepState* ss, double* __restrict__ partials,
+                                                           int ramp_n, int p, double cfl_max) {
+  __shared__ double red[8];
+  __shared__ bool last;
+  double acc = 0;
+  const int64_t n = E * nb;
+  for (int64_t idx = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; idx < n; idx += (int64_t)gridDim.x * blockDim.x) {
+    const int64_t e = idx / nb;
+    const int i = (int)(idx - e * nb);
+    double r = (double)R[e * nv * nb + i];
+    if (s) r /= (double)s[e];
+    acc += r * r;
+  }
+  for (int o = 16; o > 0; o >>= 1) acc += __shfl_xor_sync(0xffffffffu, acc, o);
+  if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = acc;
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    double b = 0;
+    for (int w = 0; w < (int)(blockDim.x >> 5); ++w) b += red[w];
+    partials[blockIdx.x] = b;
+    __threadfence();
+    last = atomicAdd(&ss->counter, 1u) == gridDim.x - 1;
+  }
+  __syncthreads();
+  if (last && threadIdx.x == 0) {
+    double b = 0;
+    for (unsigned i = 0; i < gridDim.x; ++i) b += __ldcg(partials + i);
+    const double rn = sqrt(b) / volume;
+    ss->res_norm = rn;
+    if (!isfinite(rn)) ss->err = 1;
+    if (ramp_n > 0) {
+      const double a = rn > 0 ? 1.0 / (rn * rn * rn) : DBL_MAX;
+      const double b2 = 1.0 + (double)(ramp_n - 1) / (2 * p + 1);
+      ss->cfl = fmin(cfl_max, fmax(a, b2));
+    }
+    ss->counter = 0;
+  }
+}
+
+template <class T>
+cudaError_t launch_density_norm(const T* R, const T* s, int64_t E, int nb, int nv, double volume, StepState* ss,
+                                double* partials, int ramp_n, int p, double cfl_max, cudaStream_t st) {
+  int64_t b = (E * nb + 255) / 256;
+  if (b > RED_BLOCKS) b = RED_BLOCKS;
+  density_norm_kernel<T><<<(unsigned)(b < 1 ? 1 : b), 256, 0, st>>>(R, s, E, nb, nv, volume, ss, partials, ramp_n, p, cfl_max);
+  return cudaGetLastError();
+}
+
+#define PCEXP_INST(T)                                                                                         \
+  template cudaError_t launch_dg_operator<T>(const DGData<T>&, const T*, const T*, T*, T*, const T*, const int*, \
+                                             cudaStream_t, const cudaEvent_t*, const double*);                \
+  template cudaError_t launch_local_dt<T>(const DGData<T>&, const T*, const double*, double, T*, double*,      \
+                                          double*, unsigned*, cudaStream_t);                                   \
+  template cudaError_t launch_paper_to_internal<T>(const double*, T*, const double*, int64_t, int, int,        \
+                                                   cudaStream_t);                                              \
+  template cudaError_t launch_internal_to_paper<T>(const T*, double*, const double*, int64_t, int, int,        \
+                                                   cudaStream_t);                                              \
+  template cudaError_t launch_scale_elements<T>(T*, const T*, int64_t, int, cudaStream_t);                     \
+  template cudaError_t launch_density_norm<T>(const T*, const T*, int64_t, int, int, double, StepState*,       \
+                                              double*, int, int, double, cudaStream_t);
+PCEXP_INST(double)
+PCEXP_INST(float)
+
+}  // namespace pcexp

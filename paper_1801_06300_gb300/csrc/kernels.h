@@ -1,0 +1,111 @@
+// Launchers of the device kernels (host-callable), shared by the C API.
+#pragma once
+#include <cstdint>
+#include <cuda_runtime.h>
+
+#include "../../include/pcexp.h"
+#include "physics.cuh"
+
+namespace pcexp {
+
+constexpr int MMAX = 32;        // largest Krylov dimension
+constexpr int RED_BLOCKS = 608;  // blocks of the streaming reductions (4 x 152 SMs)
+constexpr int VPAD = 64;        // vector length padding (elements)
+
+// Device-resident Arnoldi state.  V holds unnormalised vectors z_i with
+// v_i = s_i z_i; the Hessenberg matrix is row-major with leading dimension MMAX.
+struct KState {
+  double H[(MMAX + 1) * MMAX];
+  double s[MMAX + 1];
+  double coef[MMAX + 1];   // Gram-Schmidt update coefficients in units of z_i
+  double acoef[MMAX + 1];  // axpy coefficients (factor * beta * y_i * s_i)
+  double y[MMAX];          // phi_1(dt H_k) e_1
+  double y2[MMAX];         // phi_2(dt H_k) e_1
+  double beta;
+  double wnorm0;
+  int k;
+  int done;
+  int err;
+  unsigned counter;
+};
+
+// Device-resident per-step scalars.
+struct StepState {
+  double dt;        // global dt (or 1 for local pseudo-steps)
+  double cfl;       // CFL number in use
+  double res_norm;  // density residual norm (Eq. cfl)
+  double beta[2];
+  int k[2];
+  int err;
+  unsigned counter;
+  double dtmin_scratch;
+};
+
+// Mesh/geometry/tables on the device, for one scalar type.
+template <class T>
+struct DGData {
+  const T* geo;          // [E][8]
+  const int32_t* ef;     // [E][3]
+  const int32_t* fel;    // [F][2]
+  const int32_t* floc;   // [F]
+  const T* fgeo;         // [F][4]
+  const T* Bv;           // [nq][nb]
+  const T* Dv;           // [2][nq][nb]
+  const T* Bf;           // [3][nfq][nb]
+  const T* Wf;           // [nfq]
+  const T* Bc;           // [nb]
+  int64_t E, F;
+  Free<T> fs;
+  int p;
+};
+
+// ---- DG operator (dg_kernels.cu)
+// out = R(u)  or  out = J(u) du  (du != nullptr); G is face-flux scratch [F][nfq][4].
+// escale (nullable): per-element output factor.  skip (nullable): device flag, nonzero = no-op.
+// ev (nullable): three events recorded before the face kernel, between the
+// two kernels and after the element kernel.  oscale (nullable, device): one
+// more scalar factor on the output (the Krylov basis scale s_j).
+template <class T>
+cudaError_t launch_dg_operator(const DGData<T>& d, const T* u, const T* du, T* out, T* G,
+                               const T* escale, const int* skip, cudaStream_t st,
+                               const cudaEvent_t* ev = nullptr, const double* oscale = nullptr);
+// dt_e = cfl h_e / ((2p+1)(|v_c| + c_c)) -> dte[E]; min over e -> *dtmin (last-block reduction).
+template <class T>
+cudaError_t launch_local_dt(const DGData<T>& d, const T* u, const double* cfl_dev, double cfl,
+                            T* dte, double* dtmin, double* partials, unsigned* counter, cudaStream_t st);
+// basis conversions at the interface (Q_e: paper <- internal)
+template <class T>
+cudaError_t launch_paper_to_internal(const double* src, T* dst, const double* Q, int64_t E, int nb, int nv, cudaStream_t st);
+template <class T>
+cudaError_t launch_internal_to_paper(const T* src, double* dst, const double* Q, int64_t E, int nb, int nv, cudaStream_t st);
+// x[e][:] *= s[e] (block of nvb entries per element)
+template <class T>
+cudaError_t launch_scale_elements(T* x, const T* s, int64_t E, int nvb, cudaStream_t st);
+// density residual norm sqrt(sum (R[e][0][i] / s[e])^2) / volume -> ss->res_norm, then the CFL ramp
+template <class T>
+cudaError_t launch_density_norm(const T* R, const T* s, int64_t E, int nb, int nv, double volume,
+                                StepState* ss, double* partials, int ramp_n, int p, double cfl_max,
+                                cudaStream_t st);
+
+// ---- Krylov (krylov_kernels.cu)
+enum CgsMode { CGS_PROJ = 0, CGS_UPD_PROJ = 1, CGS_UPD_NORM = 2, CGS_NORM = 3 };
+template <class T>
+cudaError_t launch_cgs(int mode, const T* Z, int64_t ldz, int64_t Kp, int j, T* w, T* out,
+                       KState* ks, double* partials, double eta, cudaStream_t st);
+// phi_1/phi_2 of dt H_k (dt from *dt_dev when non-null, else dt) -> ks->y, ks->y2,
+// ks->acoef = factor * dt * beta * y_i * s_i; records k and beta into ss->k[stage], ss->beta[stage].
+cudaError_t launch_phi(KState* ks, const double* dt_dev, double dt, double factor, StepState* ss,
+                       int stage, cudaStream_t st);
+// out64 = base64 + sum_i acoef_i z_i; delta = sum_i acoef_i z_i; shadow = (T) out64
+template <class T>
+cudaError_t launch_krylov_axpy(const double* base64, double* out64, T* shadow, T* delta, const T* Z,
+                               int64_t ldz, int64_t Kp, const KState* ks, cudaStream_t st);
+// a = b - a - c  (corrector input N_* - N_n = R(u_*) - R_n - J_n delta)
+template <class T>
+cudaError_t launch_combine_corrector(T* a, const T* b, const T* c, int64_t Kp, cudaStream_t st);
+template <class Tin, class Tout>
+cudaError_t launch_cast(const Tin* x, Tout* y, int64_t n, cudaStream_t st);
+cudaError_t launch_reset_kstate(KState* ks, cudaStream_t st);
+cudaError_t launch_set_dt(StepState* ss, double dt, cudaStream_t st);
+
+}  // namespace pcexp

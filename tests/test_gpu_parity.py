@@ -1,0 +1,301 @@
+"""CUDA path vs the FP64 oracle, element by element, through the C interface.
+
+FP64 form: relative L2 <= 1e-10 for steps (the stated target) and <= 1e-12 for
+single operator applications.  FP32-mixed form: errors are measured against
+the FP64 oracle and bounded by the FP32 arithmetic (stated per test).
+"""
+import numpy as np
+import pytest
+
+import workloads as W
+
+pytestmark = pytest.mark.gpu
+
+
+def rel(a, b):
+    return float(np.linalg.norm(np.asarray(a) - np.asarray(b)) / max(np.linalg.norm(b), 1e-300))
+
+
+@pytest.fixture(scope="module")
+def capi():
+    from paper_1801_06300_gb300 import build
+    build()
+    from paper_1801_06300_gb300 import capi as c
+    c.load()
+    return c
+
+
+def oracle_dg(mesh, p, free):
+    from oracle.dg import DGOracle
+    return DGOracle(mesh, p, free)
+
+
+def perturbed_state(dg, seed, amp=0.05):
+    u = np.zeros((dg.E, dg.nv, dg.N))
+    u[:, :, 0] = dg.freestream_state()[None, :] * np.sqrt(dg.area)[:, None]
+    r = W.random_coeffs(seed, u.shape)
+    return (u + amp * r * np.abs(u[:, :, :1])).reshape(-1)
+
+
+MESHES = {
+    "periodic": lambda: (W.periodic_square(12, 10.0, 0.15, 21), W.Freestream(0.5, 30.0)),
+    "bump": lambda: (W.bump_channel(16, 6, 0.15, 1), W.Freestream(0.5, 0.0)),
+}
+
+
+@pytest.mark.parametrize("kind", ["periodic", "bump"])
+@pytest.mark.parametrize("p", [0, 1, 2, 3])
+def test_residual_and_jvp_fp64(capi, kind, p):
+    mesh, free = MESHES[kind]()
+    dg = oracle_dg(mesh, p, free)
+    ctx = capi.Context(mesh, p, free, capi.PCEXP_FP64, m_max=4)
+    u = perturbed_state(dg, 100 + p)
+    v = W.random_coeffs(200 + p, (dg.K,))
+    R = ctx.residual(u)
+    Ro = dg.residual(u)
+    assert rel(R, Ro) <= 1e-12
+    Jv = ctx.jvp(u, v)
+    Jo = dg.jvp(u, v)
+    assert rel(Jv, Jo) <= 1e-12
+    ctx.close()
+
+
+@pytest.mark.parametrize("p", [1, 3])
+def test_residual_and_jvp_fp32_mixed(capi, p):
+    mesh, free = MESHES["bump"]()
+    dg = oracle_dg(mesh, p, free)
+    ctx = capi.Context(mesh, p, free, capi.PCEXP_FP32_MIXED, m_max=4)
+    u = perturbed_state(dg, 7)
+    v = W.random_coeffs(8, (dg.K,))
+    # FP32 storage and arithmetic: relative error a few hundred ulp of FP32
+    assert rel(ctx.residual(u), dg.residual(u)) <= 2e-5
+    assert rel(ctx.jvp(u, v), dg.jvp(u, v)) <= 2e-5
+    ctx.close()
+
+
+def test_state_roundtrip_and_projection(capi):
+    from oracle.cases import vortex_state
+    case = W.case_vortex2d_small()
+    dg = oracle_dg(case.mesh, case.p, case.free)
+    ctx = capi.Context(case.mesh, case.p, case.free, capi.PCEXP_FP64, m_max=4)
+    u = perturbed_state(dg, 3)
+    ctx.set_state(u)
+    assert rel(ctx.get_state(), u) <= 1e-14
+    ctx.project_state(capi.PCEXP_PROJ_VORTEX, [case.vortex.eps, *case.vortex.center, 10.0])
+    uo = dg.project(lambda x: vortex_state(x, case.free, case.vortex, period=10.0)).reshape(-1)
+    assert rel(ctx.get_state(), uo) <= 1e-13
+    ctx.close()
+
+
+def test_time_step_rule(capi):
+    mesh, free = MESHES["bump"]()
+    dg = oracle_dg(mesh, 2, free)
+    ctx = capi.Context(mesh, 2, free, capi.PCEXP_FP64, m_max=4)
+    u = perturbed_state(dg, 11)
+    ctx.set_state(u)
+    dte = ctx.compute_dt(3.0, local=True)
+    assert rel(dte, dg.local_dt(u, 3.0)) <= 1e-13
+    assert abs(ctx.compute_dt(3.0) - dte.min()) <= 1e-15 * dte.min()
+    ctx.close()
+
+
+@pytest.mark.parametrize("k,scale", [(1, 0.5), (5, 2.0), (30, 20.0), (32, 300.0)])
+def test_phi_matches_oracle(capi, k, scale):
+    from oracle.krylov import phi_e1
+    rng = np.random.default_rng(k)
+    H = np.triu(rng.standard_normal((k, k)), -1) * scale / np.sqrt(k) - scale * np.eye(k)
+    mesh, free = MESHES["periodic"]()
+    ctx = capi.Context(mesh, 0, free, capi.PCEXP_FP64, m_max=4)
+    p1, p2 = ctx.phi(H, 0.7)
+    o1, o2 = phi_e1(H, 0.7)
+    assert rel(p1, o1) <= 1e-12
+    assert rel(p2, o2) <= 1e-12
+    ctx.close()
+
+
+@pytest.mark.parametrize("m", [1, 7, 30])
+def test_arnoldi_cgs2_matches_oracle(capi, m):
+    from oracle.krylov import arnoldi
+    mesh, free = MESHES["bump"]()
+    dg = oracle_dg(mesh, 1, free)
+    ctx = capi.Context(mesh, 1, free, capi.PCEXP_FP64, m_max=30)
+    u = perturbed_state(dg, 5)
+    b = dg.residual(u)
+    V, H, k, beta = ctx.arnoldi(u, b, m)
+    Vo, Ho, ko, betao, _ = arnoldi(lambda x: dg.jvp(u, x), b, m)
+    assert k == ko == m
+    assert abs(beta - betao) <= 1e-14 * betao
+    assert rel(H[: k + 1, :k], Ho) <= 1e-10
+    assert np.abs(V @ V.T - np.eye(m + 1)).max() <= 1e-12
+    assert rel(V.T, Vo) <= 1e-9
+    ctx.close()
+
+
+def test_arnoldi_zero_start_vector(capi):
+    """beta = ||b|| = 0: no Krylov vector is built (k = 0)."""
+    mesh, free = MESHES["periodic"]()
+    dg = oracle_dg(mesh, 0, free)
+    ctx = capi.Context(mesh, 0, free, capi.PCEXP_FP64, m_max=8)
+    u = perturbed_state(dg, 0, amp=0.0)
+    V, H, k, beta = ctx.arnoldi(u, np.zeros(dg.K), 5)
+    assert k == 0 and beta == 0.0 and not np.any(V)
+    ctx.close()
+
+
+def test_breakdown_truncation_matches_oracle(capi):
+    """With a large breakdown threshold (eta = 0.7; here h_{j+1,j} / ||J v_j|| stays in
+    0.69..0.95) the Krylov process stops early; the truncated H, V and the resulting
+    PCEXP step match the oracle run with the same eta."""
+    eta = 0.7
+    from oracle import pcexp
+    from oracle.krylov import arnoldi
+    mesh, free = MESHES["bump"]()
+    dg = oracle_dg(mesh, 1, free)
+    ctx = capi.Context(mesh, 1, free, capi.PCEXP_FP64, m_max=30, eta=eta)
+    u = perturbed_state(dg, 5)
+    b = W.random_coeffs(1, (dg.K,))
+    V, H, k, beta = ctx.arnoldi(u, b, 30)
+    Vo, Ho, ko, _, brk = arnoldi(lambda x: dg.jvp(u, x), b, 30, eta)
+    assert brk and k == ko and 1 < k < 30
+    assert rel(H[: k + 1, :k], Ho) <= 1e-10
+    assert rel(V[:k].T, Vo[:, :k]) <= 1e-9
+    assert not np.any(V[k + 1:])
+    ctx.set_state(u)
+    g = ctx.step(capi.PCEXP_SCHEME_PCEXP, capi.PCEXP_DT_GIVEN, 0.05, 30)
+    uo, info = pcexp.pcexp_step(u, dg.residual, dg.jvp, 0.05, 30, eta)
+    assert g["k"] == (info["k1"], info["k2"])
+    assert rel(ctx.get_state(), uo) <= 1e-10
+    ctx.close()
+
+
+def test_pcexp_steps_vortex_p1_per_step(capi):
+    """20 PCEXP steps, CFL 5, m = 10 on the 16x16 periodic vortex (512 triangles, P1)."""
+    from oracle import pcexp
+    from oracle.cases import vortex_state
+    case = W.case_vortex2d_small()
+    dg = oracle_dg(case.mesh, case.p, case.free)
+    u0 = dg.project(lambda x: vortex_state(x, case.free, case.vortex, period=10.0)).reshape(-1)
+    ctx = capi.Context(case.mesh, case.p, case.free, capi.PCEXP_FP64, m_max=case.m)
+    ctx.set_state(u0)
+    u = u0.copy()
+    worst = 0.0
+    for n in range(case.steps):
+        dt = float(np.min(dg.local_dt(u, case.cfl)))
+        u, info = pcexp.pcexp_step(u, dg.residual, dg.jvp, dt, case.m)
+        g = ctx.step(capi.PCEXP_SCHEME_PCEXP, capi.PCEXP_DT_GLOBAL_CFL, case.cfl, case.m)
+        assert abs(g["dt"] - dt) <= 1e-13 * dt
+        assert g["k"] == (info["k1"], info["k2"])
+        e = rel(ctx.get_state(), u)
+        worst = max(worst, e)
+        assert e <= 1e-10, (n, e)
+    ctx.close()
+
+
+@pytest.mark.parametrize("scheme", ["pcexp", "exp1"])
+def test_steady_local_steps_bump(capi, scheme):
+    """Local pseudo-steps du/dtau = D R(u) at CFL 50 on a jittered bump channel, P2, m = 20."""
+    from oracle import pcexp
+    mesh, free = W.bump_channel(24, 8, 0.15, 1), W.Freestream(0.5, 0.0)
+    dg = oracle_dg(mesh, 2, free)
+    ctx = capi.Context(mesh, 2, free, capi.PCEXP_FP64, m_max=20)
+    u = perturbed_state(dg, 0, amp=0.0)
+    ctx.set_state(u)
+    sc = capi.PCEXP_SCHEME_PCEXP if scheme == "pcexp" else capi.PCEXP_SCHEME_EXP1
+    for n in range(3):
+        u, info = pcexp.steady_step(dg, u, 50.0, 20, scheme=scheme)
+        ctx.step(sc, capi.PCEXP_DT_LOCAL_CFL, 50.0, 20)
+        assert rel(ctx.get_state(), u) <= 1e-10
+    ctx.close()
+
+
+def test_freestream_step_is_identity(capi):
+    """R(u_inf) = 0 on a periodic mesh: beta = 0 and the step leaves u unchanged."""
+    mesh, free = MESHES["periodic"]()
+    dg = oracle_dg(mesh, 2, free)
+    ctx = capi.Context(mesh, 2, free, capi.PCEXP_FP64, m_max=10)
+    u = perturbed_state(dg, 0, amp=0.0)
+    ctx.set_state(u)
+    g = ctx.step(capi.PCEXP_SCHEME_PCEXP, capi.PCEXP_DT_GLOBAL_CFL, 5.0, 10)
+    assert g["beta"][0] < 1e-12
+    assert rel(ctx.get_state(), u) <= 1e-13
+    ctx.close()
+
+
+def test_full_size_bump_operator_and_step(capi):
+    """Full bump channel (192 x 64 split, 24,576 triangles, P2, K = 589,824): operators
+    element by element, and one PCEXP local-step iteration at m = 30, as timed."""
+    from oracle import pcexp
+    case = W.case_bump2d()
+    dg = oracle_dg(case.mesh, case.p, case.free)
+    ctx = capi.Context(case.mesh, case.p, case.free, capi.PCEXP_FP64, m_max=30)
+    up = perturbed_state(dg, 10)
+    v = W.random_coeffs(9, (dg.K,))
+    assert rel(ctx.residual(up), dg.residual(up)) <= 1e-12
+    assert rel(ctx.jvp(up, v), dg.jvp(up, v)) <= 1e-12
+    u = perturbed_state(dg, 0, amp=0.0)
+    ctx.set_state(u)
+    uo, _ = pcexp.steady_step(dg, u, case.cfl, 30)
+    ctx.step(capi.PCEXP_SCHEME_PCEXP, capi.PCEXP_DT_LOCAL_CFL, case.cfl, 30)
+    assert rel(ctx.get_state(), uo) <= 1e-10
+    ctx.close()
+
+
+def test_fp32_mixed_steps_vortex_error_stated(capi):
+    """FP32-mixed form on the P1 vortex: state error against the FP64 oracle after 20 steps."""
+    from oracle import pcexp
+    from oracle.cases import vortex_state
+    case = W.case_vortex2d_small()
+    dg = oracle_dg(case.mesh, case.p, case.free)
+    u0 = dg.project(lambda x: vortex_state(x, case.free, case.vortex, period=10.0)).reshape(-1)
+    ctx = capi.Context(case.mesh, case.p, case.free, capi.PCEXP_FP32_MIXED, m_max=case.m)
+    ctx.set_state(u0)
+    u = u0.copy()
+    for n in range(case.steps):
+        dt = float(np.min(dg.local_dt(u, case.cfl)))
+        u, _ = pcexp.pcexp_step(u, dg.residual, dg.jvp, dt, case.m)
+        ctx.step(capi.PCEXP_SCHEME_PCEXP, capi.PCEXP_DT_GIVEN, dt, case.m, info=False)
+    e = rel(ctx.get_state(), u)
+    print(f"FP32-mixed relative state error after {case.steps} steps: {e:.3e}")
+    assert e <= 1e-5
+    ctx.close()
+
+
+def test_fp32_mixed_krylov_no_overflow_and_one_step(capi):
+    """FP32-mixed Arnoldi at m = 30 on an operator with ||D J|| ~ 1e2 (stored Krylov
+    vectors must not grow like ||J||^j), and one local-step PCEXP iteration against the
+    FP64 oracle: state error and error of the increment u_{n+1} - u_n."""
+    from oracle import pcexp
+    from oracle.krylov import arnoldi
+    mesh, free = W.bump_channel(24, 8, 0.15, 1), W.Freestream(0.5, 0.0)
+    dg = oracle_dg(mesh, 2, free)
+    ctx = capi.Context(mesh, 2, free, capi.PCEXP_FP32_MIXED, m_max=30)
+    u = perturbed_state(dg, 0, amp=0.0)
+    b = dg.residual(u)
+    sc = np.repeat(dg.local_dt(u, 100.0), dg.nv * dg.N)
+    V, H, k, beta = ctx.arnoldi(u, b, 30)
+    Vo, Ho, ko, _, _ = arnoldi(lambda x: dg.jvp(u, x), b, 30)
+    assert k == 30 and np.all(np.isfinite(H))
+    assert rel(H[:3, :2], Ho[:3, :2]) <= 1e-4
+    assert np.abs(V @ V.T - np.eye(31)).max() <= 1e-4
+    ctx.set_state(u)
+    ctx.step(capi.PCEXP_SCHEME_PCEXP, capi.PCEXP_DT_LOCAL_CFL, 100.0, 30)
+    uo, _ = pcexp.steady_step(dg, u, 100.0, 30)
+    g = ctx.get_state()
+    es, ei = rel(g, uo), rel(g - u, uo - u)
+    print(f"FP32-mixed one step vs FP64 oracle: state {es:.2e}, increment {ei:.2e}")
+    assert es <= 1e-5 and ei <= 1e-3
+    del sc
+    ctx.close()
+
+
+def test_torch_device_pointers(capi):
+    torch = pytest.importorskip("torch")
+    mesh, free = MESHES["periodic"]()
+    dg = oracle_dg(mesh, 2, free)
+    ctx = capi.Context(mesh, 2, free, capi.PCEXP_FP64, m_max=4)
+    u = perturbed_state(dg, 4)
+    ud = torch.from_numpy(u).cuda()
+    R = ctx.residual(ud)
+    torch.cuda.synchronize()
+    assert rel(R.cpu().numpy(), dg.residual(u)) <= 1e-12
+    ctx.close()
