@@ -212,6 +212,23 @@ int pcexp_output(pcexp_ctx* ctx, int kind, double* value);
 int pcexp_profile_enable(pcexp_ctx* ctx, int enable);
 int pcexp_profile_read(pcexp_ctx* ctx, int kernel_class, int64_t* launches, double* ms);
 
+/* R(U) exactly as pcexp_residual computes it, for callers that cannot allocate
+ * device memory when they need it (inside CUDA stream capture, under a fixed
+ * memory budget or a custom allocator, in loops that forbid allocator calls
+ * after set-up).  The paper has no counterpart; this is an interface variant.
+ * U and R are device pointers to K doubles in the library's INTERNAL basis
+ * (whatever basis_io the context uses); the context must be FP64.  The call
+ * only enqueues the two DG kernels on the context's stream and returns; it
+ * calls no cudaMalloc/cudaFree or other allocating routine.  Its face-flux
+ * scratch is a fixed 8 MiB device array inside the library (held by every GPU
+ * that loads the library until the process exits): meshes needing more than
+ * 2^20 doubles (faces x (p+1) x 4) get PCEXP_ERR_INVALID_ARG.  The array's
+ * device address is looked up on the first call on each device, so make that
+ * first call before any stream capture.  All calls share the array: calls
+ * whose kernels overlap on the GPU race; calls on one stream are ordered.
+ * Errors: INVALID_ARG, UNSUPPORTED (FP32-mixed context), CUDA. */
+int pcexp_residual_noalloc(pcexp_ctx* ctx, const double* U, double* R);
+
 /* Waits for all work queued on the context's stream. */
 int pcexp_synchronize(pcexp_ctx* ctx);
 

@@ -88,6 +88,7 @@ SIGNATURES = {
                                      C.POINTER(pcexp_steady_info)]),
     "pcexp_output": (C.c_int, [_P, C.c_int, _D]),
     "pcexp_synchronize": (C.c_int, [_P]),
+    "pcexp_residual_noalloc": (C.c_int, [_P, _P, _P]),
     "pcexp_profile_enable": (C.c_int, [_P, C.c_int]),
     "pcexp_profile_read": (C.c_int, [_P, C.c_int, C.POINTER(C.c_int64), _D]),
     "pcexp_status_string": (C.c_char_p, [C.c_int]),
@@ -210,6 +211,14 @@ class Context:
         pv, _ = _ptr(v)
         po, _ = _ptr(out)
         check(self.lib.pcexp_jvp(self.ctx, pu, pv, po, dev), "pcexp_jvp")
+        return out
+
+    def residual_noalloc(self, U, out):
+        """R(U) in the internal basis on device tensors, with no device allocation (enqueue only)."""
+        pu, dev = _ptr(U)
+        po, dev2 = _ptr(out)
+        assert dev and dev2, "pcexp_residual_noalloc takes device pointers"
+        check(self.lib.pcexp_residual_noalloc(self.ctx, pu, po), "pcexp_residual_noalloc")
         return out
 
     def compute_dt(self, cfl: float, local: bool = False):

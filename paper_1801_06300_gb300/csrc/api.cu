@@ -585,6 +585,21 @@ int create_impl(pcexp_ctx* c, const pcexp_mesh* mesh, int p, const pcexp_physics
 
 }  // namespace
 
+namespace pcexp {
+// Read-only view of a context for pcexp_residual_noalloc (noalloc.cu); makes the
+// context's device current.
+int ctx_noalloc_view(pcexp_ctx* c, DGData<double>* d, cudaStream_t* st, int* nfq, int* fp32, int* device) {
+  int r = check_ctx(c);
+  if (r != PCEXP_OK) return r;
+  *d = dgdata<double>(c);
+  *st = c->st;
+  *nfq = c->nfq;
+  *fp32 = c->fp32 ? 1 : 0;
+  *device = c->device;
+  return PCEXP_OK;
+}
+}  // namespace pcexp
+
 extern "C" {
 
 int pcexp_create(pcexp_ctx** out, const pcexp_mesh* mesh, int p, const pcexp_physics* phys,
