@@ -127,13 +127,15 @@ class ClockSampler:
 # ------------------------------------------------------------ algorithmic bytes
 def algorithmic_bytes(kind, T, K, E, F, nfq, m):
     """Minimum DRAM bytes per launch of a kernel class (per-kernel table)."""
+    nq = nfq * nfq
     g_face = F * (4 * T + 12)  # normal, length, element and local-face ids
     g_elem = E * (8 * T + 12)  # affine map, sqrt(det), h; face slots
     G = F * nfq * 4 * T        # face-flux buffer
     avg_j = (m - 1) / 2.0       # mean column index over one Arnoldi process
     return {
-        "jvp_face": 2 * K * T + g_face + G,
-        "jvp_elem": 3 * K * T + g_elem + G,
+        # J v from the point Jacobians at u_n: read v and the 4x4 blocks, write G / Jv
+        "jvp_face": K * T + 32 * F * nfq * T + F * 12 + G,
+        "jvp_elem": 2 * K * T + 32 * E * nq * T + E * (T + 12) + G,
         "residual_face": K * T + g_face + G,
         "residual_elem": 2 * K * T + g_elem + G,
         "cgs_proj": (avg_j + 2) * K * T,
@@ -149,7 +151,9 @@ def main():
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="gb300", choices=["gb300", "reference"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
-    ap.add_argument("--no-mixed", action="store_true")
+    ap.add_argument("--no-mixed", action="store_true", help="skip the second precision form")
+    ap.add_argument("--precision", default="fp64", choices=["fp64", "fp32"],
+                    help="form of the headline value (the other form is reported beside it)")
     args = ap.parse_args()
     args.warmup = max(args.warmup, 3)
 
@@ -180,38 +184,44 @@ def main():
     free = case.free
     flush = torch.empty(64 * 1024 * 1024, dtype=torch.float32, device="cuda")  # 256 MB > L2
 
-    def run(precision, profile):
-        ctx = capi.Context(case.mesh, P, free, precision, m_max=M)
-        for _ in range(args.warmup):
-            ctx.step(capi.PCEXP_SCHEME_PCEXP, capi.PCEXP_DT_LOCAL_CFL, CFL, M, info=False)
-        torch.cuda.synchronize()
+    def timed_steps(ctx, profile):
+        """K steps after a barrier and a synchronize, L2 flushed before each step outside
+        the step's CUDA events (recorded on the context's stream = torch's current stream)."""
         evs = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(args.steps)]
-        sampler = ClockSampler(local)
         if dist:
             dist.barrier()
         torch.cuda.synchronize()
-        sampler.start()
         if profile:
             ctx.profile_enable(True)
-        t0 = time.perf_counter()
         for s in range(args.steps):
             flush.zero_()
             evs[s][0].record()
             ctx.step(capi.PCEXP_SCHEME_PCEXP, capi.PCEXP_DT_LOCAL_CFL, CFL, M, info=False)
             evs[s][1].record()
         torch.cuda.synchronize()
-        wall = time.perf_counter() - t0
         if dist:
             dist.barrier()
-        clocks = sampler.stop()
         ms = sum(a.elapsed_time(b) for a, b in evs)
         prof = ctx.profile_read() if profile else None
         if profile:
             ctx.profile_enable(False)
-        state = ctx.get_state()
-        return ctx, ms, wall, prof, clocks, state
+        return ms, prof
 
-    ctx64, ms64, wall64, prof, clocks, state64 = run(capi.PCEXP_FP64, True)
+    def run(precision):
+        ctx = capi.Context(case.mesh, P, free, precision, m_max=M)
+        for _ in range(args.warmup):
+            ctx.step(capi.PCEXP_SCHEME_PCEXP, capi.PCEXP_DT_LOCAL_CFL, CFL, M, info=False)
+        torch.cuda.synchronize()
+        sampler = ClockSampler(local)
+        sampler.start()
+        ms, _ = timed_steps(ctx, False)          # the measurement
+        ms_prof, prof = timed_steps(ctx, True)   # per-kernel-class events (adds launch gaps)
+        clocks = sampler.stop()
+        state = ctx.get_state()
+        return ctx, ms, ms_prof, prof, clocks, state
+
+    main_prec = capi.PCEXP_FP64 if args.precision == "fp64" else capi.PCEXP_FP32_MIXED
+    ctx64, ms64, ms64_prof, prof, clocks, state64 = run(main_prec)
     K = ctx64.K
     ms_max = ms64
     if dist:
@@ -245,8 +255,8 @@ def main():
     # both forms (the steady march at CFL 100 amplifies any 1e-7 difference to 1e-2
     # within a few steps, so multi-step state differences measure that, not FP32).
     mixed = None
-    if not args.no_mixed:
-        ctx32, ms32, wall32, prof32, _, state32 = run(capi.PCEXP_FP32_MIXED, True)
+    if not args.no_mixed and args.precision == "fp64":
+        ctx32, ms32, ms32_prof, prof32, _, state32 = run(capi.PCEXP_FP32_MIXED)
         s0 = np.ascontiguousarray(state64)
         ctx64.set_state(s0)
         ctx64.step(capi.PCEXP_SCHEME_PCEXP, capi.PCEXP_DT_LOCAL_CFL, CFL, M, info=False)
@@ -270,7 +280,7 @@ def main():
     launches = sum(v[0] for v in prof.values())
     dom = max(prof, key=lambda k: prof[k][1])
     n_dom, ms_dom = prof[dom]
-    ab = algorithmic_bytes(dom, 8, K, E, F, nfq, M)
+    ab = algorithmic_bytes(dom, 8 if args.precision == "fp64" else 4, K, E, F, nfq, M)
     roof = None
     if ab is not None and n_dom:
         achieved = ab / (ms_dom / n_dom / 1e3) / 1e9
@@ -290,13 +300,15 @@ def main():
     out = {
         "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
         "warmup": args.warmup, "ms_per_step": ms_max / args.steps, "higher_is_better": True,
-        "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+        "scaling": "weak", "vs_baseline": None, "dtype": "f64" if args.precision == "fp64" else "f32+f64",
+        "data": "synthetic",
         "config": {"workload": WORKLOAD, "mesh": f"{NX}x{NY} split quads, {E} triangles, 15% jitter seed {SEED}",
                    "p": P, "m": M, "K": K, "scheme": "PCEXP", "time_step": f"local, CFL {CFL:g}",
-                   "precision": "FP64", "l2": "flushed between steps (256 MB write outside the step events)",
+                   "precision": "FP64" if args.precision == "fp64" else "FP32-mixed", "l2": "flushed between steps (256 MB write outside the step events)",
                    "parallelism": f"replicas x{world}"},
         "e2e": {"value": e2e_value, "unit": UNIT, "h2d_bytes_per_step": K * 8, "d2h_bytes_per_step": K * 8},
         "gpu_launches": launches,
+        "ms_per_step_with_kernel_events": ms64_prof / args.steps,
         "kernel_ms_per_step": {k: round(v[1] / args.steps, 4) for k, v in prof.items() if v[0]},
         "roofline": roof,
         "cpu_baseline": cpu,
@@ -321,7 +333,8 @@ def reference_arm(args, rank, world):
     out = {
         "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
         "warmup": args.warmup, "ms_per_step": total / args.steps * 1e3, "higher_is_better": True,
-        "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic", "impl": "reference",
+        "scaling": "weak", "vs_baseline": None, "dtype": "f64" if args.precision == "fp64" else "f32+f64",
+        "data": "synthetic", "impl": "reference",
         "config": {"workload": WORKLOAD, "p": P, "m": M, "scheme": "PCEXP", "time_step": f"local, CFL {CFL:g}",
                    "sample": f"{REF_SAMPLE[0]}x{REF_SAMPLE[1]} channel, K={r['K']}"},
         "cpu_baseline": {"value": value, "unit": UNIT, "cores": 1, "kind": "oracle",

@@ -198,8 +198,8 @@ int pcexp_output(pcexp_ctx* ctx, int kind, double* value);
  * summed device time (ms) since profiling was enabled. */
 #define PCEXP_KC_RESIDUAL_FACE 0 /* face Riemann-flux kernel of R(u) */
 #define PCEXP_KC_RESIDUAL_ELEM 1 /* element volume + lift kernel of R(u) */
-#define PCEXP_KC_JVP_FACE 2      /* tangent face kernel of J v */
-#define PCEXP_KC_JVP_ELEM 3      /* tangent element kernel of J v */
+#define PCEXP_KC_JVP_FACE 2      /* face kernel of J v (point-Jacobian or tangent form) */
+#define PCEXP_KC_JVP_ELEM 3      /* element kernel of J v */
 #define PCEXP_KC_CGS_NORM 4      /* ||b|| of the Krylov start vector */
 #define PCEXP_KC_CGS_PROJ 5      /* h = V^T w, ||w|| */
 #define PCEXP_KC_CGS_UPD_PROJ 6  /* w -= V h; h2 = V^T w */
@@ -208,7 +208,8 @@ int pcexp_output(pcexp_ctx* ctx, int kind, double* value);
 #define PCEXP_KC_AXPY 9          /* u + sum_i c_i v_i */
 #define PCEXP_KC_DT 10           /* element time steps */
 #define PCEXP_KC_OTHER 11        /* small bookkeeping kernels */
-#define PCEXP_KC_COUNT 12
+#define PCEXP_KC_LINEARIZE 12    /* point Jacobians at u_n (once per step) */
+#define PCEXP_KC_COUNT 13
 int pcexp_profile_enable(pcexp_ctx* ctx, int enable);
 int pcexp_profile_read(pcexp_ctx* ctx, int kernel_class, int64_t* launches, double* ms);
 

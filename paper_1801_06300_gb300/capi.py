@@ -37,7 +37,7 @@ PCEXP_PROJ_VORTEX = 1
 PCEXP_PROJ_BLOBS = 2
 PCEXP_MAX_KRYLOV = 32
 KERNEL_CLASSES = ["residual_face", "residual_elem", "jvp_face", "jvp_elem", "cgs_norm", "cgs_proj",
-                  "cgs_upd_proj", "cgs_upd_norm", "phi", "axpy", "dt", "other"]
+                  "cgs_upd_proj", "cgs_upd_norm", "phi", "axpy", "dt", "other", "linearize"]
 
 
 class pcexp_mesh(C.Structure):

@@ -37,6 +37,7 @@ struct pcexp_ctx {
   void* S32[2] = {nullptr, nullptr};  // FP32 shadows (mixed form only)
   void *V = nullptr, *w = nullptr, *tmp = nullptr, *delta = nullptr, *G = nullptr, *dte = nullptr;
   double *io64a = nullptr, *io64b = nullptr;
+  void *Avol = nullptr, *Bface = nullptr;  // point Jacobians at the linearisation state
   KState* ks = nullptr;
   StepState* ss = nullptr;
   double* partials = nullptr;
@@ -202,6 +203,34 @@ int dg_apply(pcexp_ctx* c, const DGData<T>& d, const T* u, const T* du, T* out, 
   return PCEXP_OK;
 }
 
+template <class T> LinData<T> lindata(pcexp_ctx* c) {
+  return LinData<T>{reinterpret_cast<T*>(c->Avol), reinterpret_cast<T*>(c->Bface)};
+}
+
+template <class T>
+int linearize(pcexp_ctx* c, const DGData<T>& d, const T* u) {
+  PCEXP_LAUNCH(c, PCEXP_KC_LINEARIZE, launch_linearize<T>(d, u, lindata<T>(c), c->st));
+  return PCEXP_OK;
+}
+
+// J(u_lin) dv from the point Jacobians (two kernels: face, element)
+template <class T>
+int jac_apply(pcexp_ctx* c, const DGData<T>& d, const T* dv, T* out, const T* escale, const int* skip,
+              const double* oscale) {
+  cudaEvent_t* ev = prof_events(c, 3);
+  cudaError_t e = launch_jac_apply<T>(d, lindata<T>(c), dv, out, reinterpret_cast<T*>(c->G), escale, skip, oscale,
+                                      c->st, ev);
+  if (ev) {
+    prof_note(c, PCEXP_KC_JVP_FACE, ev, 0);
+    prof_note(c, PCEXP_KC_JVP_ELEM, ev, 1);
+  }
+  if (e != cudaSuccess) {
+    g_last_error = std::string("Jacobian apply launch: ") + cudaGetErrorString(e);
+    return PCEXP_ERR_CUDA;
+  }
+  return PCEXP_OK;
+}
+
 template <class T> T* Vcol(pcexp_ctx* c, int j) { return reinterpret_cast<T*>(c->V) + (int64_t)j * c->Kp; }
 template <class T> T* shadow(pcexp_ctx* c, int i) {
   return c->fp32 ? reinterpret_cast<T*>(c->S32[i]) : reinterpret_cast<T*>(c->U64[i]);
@@ -238,9 +267,10 @@ int refresh_shadow(pcexp_ctx* c, int i) {
   return PCEXP_OK;
 }
 
-// Arnoldi on J(lin) (times escale) started from V[0]; m columns at most.
+// Arnoldi on J (times escale) started from V[0]; m columns at most.  J is the
+// operator linearised by the last linearize() call.
 template <class T>
-int arnoldi(pcexp_ctx* c, const T* lin, const T* escale, int m) {
+int arnoldi(pcexp_ctx* c, const T* escale, int m) {
   const DGData<T> d = dgdata<T>(c);
   T* w = reinterpret_cast<T*>(c->w);
   T* G = reinterpret_cast<T*>(c->G);
@@ -251,7 +281,7 @@ int arnoldi(pcexp_ctx* c, const T* lin, const T* escale, int m) {
   for (int j = 0; j < m; ++j) {
     // w = J v_j = s_j J z_j: the basis scale is applied to the output, so every
     // stored vector stays of the size of ||J|| (no growth like ||J||^j)
-    PCEXP_TRY(dg_apply<T>(c, d, lin, Vcol<T>(c, j), w, escale, &c->ks->done, &c->ks->s[j]));
+    PCEXP_TRY(jac_apply<T>(c, d, Vcol<T>(c, j), w, escale, &c->ks->done, &c->ks->s[j]));
     PCEXP_LAUNCH(c, PCEXP_KC_CGS_PROJ, launch_cgs<T>(CGS_PROJ, V, c->Kp, c->Kp, j, w, nullptr, c->ks, c->partials, c->eta, c->st));
     PCEXP_LAUNCH(c, PCEXP_KC_CGS_UPD_PROJ, launch_cgs<T>(CGS_UPD_PROJ, V, c->Kp, c->Kp, j, w, nullptr, c->ks, c->partials, c->eta, c->st));
     PCEXP_LAUNCH(c, PCEXP_KC_CGS_UPD_NORM, launch_cgs<T>(CGS_UPD_NORM, V, c->Kp, c->Kp, j, w, Vcol<T>(c, j + 1), c->ks, c->partials, c->eta, c->st));
@@ -273,8 +303,10 @@ int krylov_stages(pcexp_ctx* c, int scheme, const T* escale, int m) {
   T* w = reinterpret_cast<T*>(c->w);
   T* tmp = reinterpret_cast<T*>(c->tmp);
   T* delta = reinterpret_cast<T*>(c->delta);
+  // J_n: point Jacobians at u_n, shared by all 2m+1 products of the step
+  PCEXP_TRY(linearize<T>(c, d, S0));
   // predictor: u_* = u_n + dt phi_1(dt J_n) R_n
-  PCEXP_TRY(arnoldi<T>(c, S0, escale, m));
+  PCEXP_TRY(arnoldi<T>(c, escale, m));
   PCEXP_LAUNCH(c, PCEXP_KC_PHI, launch_phi(c->ks, &c->ss->dt, 0.0, 1.0, c->ss, 0, c->st));
   PCEXP_LAUNCH(c, PCEXP_KC_AXPY, launch_krylov_axpy<T>(c->U64[a], c->U64[b], S1, delta, V, c->Kp, c->Kp, c->ks, c->st));
   if (scheme == PCEXP_SCHEME_EXP1) {
@@ -284,10 +316,10 @@ int krylov_stages(pcexp_ctx* c, int scheme, const T* escale, int m) {
   // corrector input N_* - N_n = R(u_*) - R_n - J_n (u_* - u_n)
   (void)G;
   PCEXP_TRY(dg_apply<T>(c, d, S1, nullptr, w, escale, nullptr));
-  PCEXP_TRY(dg_apply<T>(c, d, S0, delta, tmp, escale, nullptr));
+  PCEXP_TRY(jac_apply<T>(c, d, delta, tmp, escale, nullptr, nullptr));
   PCEXP_LAUNCH(c, PCEXP_KC_OTHER, launch_combine_corrector<T>(V, w, tmp, c->Kp, c->st));
   // corrector: u_{n+1} = u_* + dt/2 phi_1(dt J_n) (N_* - N_n)
-  PCEXP_TRY(arnoldi<T>(c, S0, escale, m));
+  PCEXP_TRY(arnoldi<T>(c, escale, m));
   PCEXP_LAUNCH(c, PCEXP_KC_PHI, launch_phi(c->ks, &c->ss->dt, 0.0, 0.5, c->ss, 1, c->st));
   PCEXP_LAUNCH(c, PCEXP_KC_AXPY, launch_krylov_axpy<T>(c->U64[b], c->U64[a], S0, nullptr, V, c->Kp, c->Kp, c->ks, c->st));
   return PCEXP_OK;
@@ -389,7 +421,8 @@ int arnoldi_abi(pcexp_ctx* c, const double* U, const double* b, int m, double* V
   T* lin = reinterpret_cast<T*>(c->delta);
   PCEXP_TRY(import_vec<T>(c, U, on_device, lin));
   PCEXP_TRY(import_vec<T>(c, b, on_device, Vcol<T>(c, 0)));
-  PCEXP_TRY(arnoldi<T>(c, lin, nullptr, m));
+  PCEXP_TRY(linearize<T>(c, dgdata<T>(c), lin));
+  PCEXP_TRY(arnoldi<T>(c, nullptr, m));
   KState hk;
   PCEXP_CK(cudaMemcpyAsync(&hk, c->ks, sizeof(hk), cudaMemcpyDeviceToHost, c->st));
   PCEXP_CK(cudaStreamSynchronize(c->st));
@@ -567,6 +600,8 @@ int create_impl(pcexp_ctx* c, const pcexp_mesh* mesh, int p, const pcexp_physics
   PCEXP_TRY(valloc(&c->delta, Kp));
   PCEXP_TRY(valloc(&c->G, (size_t)(c->F > 0 ? c->F : 1) * c->nfq * 4));
   PCEXP_TRY(valloc(&c->dte, c->E));
+  PCEXP_TRY(valloc(&c->Avol, (size_t)32 * c->E * c->nq));
+  PCEXP_TRY(valloc(&c->Bface, (size_t)32 * (c->F > 0 ? c->F : 1) * c->nfq));
   PCEXP_TRY(dalloc(c, &c->io64a, Kp));
   PCEXP_TRY(dalloc(c, &c->io64b, Kp));
   PCEXP_TRY(dalloc(c, &c->ks, 1));

@@ -219,6 +219,303 @@ cudaError_t launch_dg_operator(const DGData<T>& d, const T* u, const T* du, T* o
   return cudaErrorInvalidValue;
 }
 
+// ------------------------------------------------------- point Jacobians (linearisation)
+// The exact Jacobian of the scheme (Eq. jac1, jac2) is assembled point by point: the
+// volume flux Jacobians dF_d/dU and the Riemann-flux Jacobians dF~/dU_L, dF~/dU_R are
+// evaluated exactly by running the flux code on Jet<T,4> numbers seeded with unit
+// directions (the paper obtains the Riemann-flux Jacobians by AD as well).  Every J v
+// of a PCEXP step is taken at u_n, so the Jacobians are built once per step and each
+// of the 2m+1 products reduces to traces, 4x4 mat-vecs and the test/lift contractions.
+template <class T, int P>
+__global__ void __launch_bounds__(256) linearize_vol_kernel(DGData<T> d, const T* __restrict__ u,
+                                                            T* __restrict__ Avol) {
+  using O = Ord<P>;
+  constexpr int NB = O::NB, NQ = O::NQ;
+  using J4 = Jet<T, 4>;
+  const int64_t n = d.E * NQ;
+  const int64_t idx = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (idx >= n) return;
+  const int64_t e = idx / NQ;
+  const int q = (int)(idx - e * NQ);
+  const T* ge = d.geo + 8 * e;
+  const T isd = T(1) / ge[4];
+  J4 U[4];
+#pragma unroll
+  for (int v = 0; v < 4; ++v) {
+    T a = 0;
+#pragma unroll
+    for (int j = 0; j < NB; ++j) a += d.Bv[q * NB + j] * u[e * 4 * NB + v * NB + j];
+    U[v].v = a * isd;
+#pragma unroll
+    for (int c = 0; c < 4; ++c) U[v].d[c] = (v == c) ? T(1) : T(0);
+  }
+  J4 Fx[4], Fy[4];
+  euler_flux<J4, T>(U, d.fs.gamma, Fx, Fy);
+#pragma unroll
+  for (int v = 0; v < 4; ++v)
+#pragma unroll
+    for (int c = 0; c < 4; ++c) {
+      Avol[(int64_t)(0 * 16 + v * 4 + c) * n + idx] = ge[0] * Fx[v].d[c] + ge[1] * Fy[v].d[c];
+      Avol[(int64_t)(1 * 16 + v * 4 + c) * n + idx] = ge[2] * Fx[v].d[c] + ge[3] * Fy[v].d[c];
+    }
+}
+
+template <class T, int P>
+__global__ void __launch_bounds__(128) linearize_face_kernel(DGData<T> d, const T* __restrict__ u,
+                                                             T* __restrict__ Bface) {
+  using O = Ord<P>;
+  constexpr int NB = O::NB, NFQ = O::NFQ;
+  using J4 = Jet<T, 4>;
+  const int64_t n = d.F * NFQ;
+  const int64_t idx = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (idx >= n) return;
+  const int64_t f = idx / NFQ;
+  const int q = (int)(idx - f * NFQ);
+  const int eL = d.fel[2 * f], eR = d.fel[2 * f + 1];
+  const int loc = d.floc[f];
+  const int fL = loc & 0xff, fR = loc >> 8;
+  const T nx = d.fgeo[4 * f], ny = d.fgeo[4 * f + 1], len = d.fgeo[4 * f + 2];
+  const T wq = len * d.Wf[q];
+  T uL[4], uR[4];
+  const T isdL = T(1) / d.geo[8 * (int64_t)eL + 4];
+  T isdR = T(0);
+#pragma unroll
+  for (int v = 0; v < 4; ++v) {
+    T a = 0;
+#pragma unroll
+    for (int j = 0; j < NB; ++j) a += d.Bf[(fL * NFQ + q) * NB + j] * u[(int64_t)eL * 4 * NB + v * NB + j];
+    uL[v] = a * isdL;
+  }
+  if (eR >= 0) {
+    isdR = T(1) / d.geo[8 * (int64_t)eR + 4];
+#pragma unroll
+    for (int v = 0; v < 4; ++v) {
+      T a = 0;
+#pragma unroll
+      for (int j = 0; j < NB; ++j)
+        a += d.Bf[(fR * NFQ + (NFQ - 1 - q)) * NB + j] * u[(int64_t)eR * 4 * NB + v * NB + j];
+      uR[v] = a * isdR;
+    }
+  }
+#pragma unroll 1
+  for (int side = 0; side < 2; ++side) {
+    J4 L[4], R[4], F[4];
+    if (side == 1 && eR < 0) {
+#pragma unroll
+      for (int k = 0; k < 16; ++k) Bface[(int64_t)(16 + k) * n + idx] = T(0);
+      break;
+    }
+#pragma unroll
+    for (int v = 0; v < 4; ++v) {
+      L[v].v = uL[v];
+#pragma unroll
+      for (int c = 0; c < 4; ++c) L[v].d[c] = (side == 0 && v == c) ? T(1) : T(0);
+    }
+    if (eR >= 0) {
+#pragma unroll
+      for (int v = 0; v < 4; ++v) {
+        R[v].v = uR[v];
+#pragma unroll
+        for (int c = 0; c < 4; ++c) R[v].d[c] = (side == 1 && v == c) ? T(1) : T(0);
+      }
+    } else if (-eR == PCEXP_BC_SLIP_WALL) {
+      ghost_slip_wall<J4, T>(L, nx, ny, R);
+    } else {
+      ghost_farfield<J4, T>(L, nx, ny, d.fs, R);
+    }
+    roe_flux<J4, T>(L, R, nx, ny, d.fs.gamma, F);
+    const T sc = wq * (side == 0 ? isdL : isdR);
+#pragma unroll
+    for (int v = 0; v < 4; ++v)
+#pragma unroll
+      for (int c = 0; c < 4; ++c) Bface[(int64_t)(side * 16 + v * 4 + c) * n + idx] = sc * F[v].d[c];
+  }
+}
+
+template <class T, int P>
+__global__ void __launch_bounds__(256) face_apply_kernel(DGData<T> d, const T* __restrict__ Bface,
+                                                         const T* __restrict__ dv, T* __restrict__ G,
+                                                         const int* __restrict__ skip) {
+  using O = Ord<P>;
+  constexpr int NB = O::NB, NFQ = O::NFQ;
+  __shared__ T sBf[3 * NFQ * NB];
+  if (skip && *skip) return;
+  for (int i = threadIdx.x; i < 3 * NFQ * NB; i += blockDim.x) sBf[i] = d.Bf[i];
+  __syncthreads();
+  const int64_t n = d.F * NFQ;
+  const int64_t idx = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (idx >= n) return;
+  const int64_t f = idx / NFQ;
+  const int q = (int)(idx - f * NFQ);
+  const int eL = d.fel[2 * f], eR = d.fel[2 * f + 1];
+  const int loc = d.floc[f];
+  const int fL = loc & 0xff, fR = loc >> 8;
+  T B[32];
+#pragma unroll
+  for (int k = 0; k < 32; ++k) B[k] = (k < 16 || eR >= 0) ? Bface[(int64_t)k * n + idx] : T(0);
+  T tL[4], tR[4];
+#pragma unroll
+  for (int v = 0; v < 4; ++v) {
+    T a = 0;
+#pragma unroll
+    for (int j = 0; j < NB; ++j) a += sBf[(fL * NFQ + q) * NB + j] * dv[(int64_t)eL * 4 * NB + v * NB + j];
+    tL[v] = a;
+  }
+  if (eR >= 0) {
+#pragma unroll
+    for (int v = 0; v < 4; ++v) {
+      T a = 0;
+#pragma unroll
+      for (int j = 0; j < NB; ++j)
+        a += sBf[(fR * NFQ + (NFQ - 1 - q)) * NB + j] * dv[(int64_t)eR * 4 * NB + v * NB + j];
+      tR[v] = a;
+    }
+  }
+  T* g = G + idx * 4;
+#pragma unroll
+  for (int v = 0; v < 4; ++v) {
+    T a = 0;
+#pragma unroll
+    for (int c = 0; c < 4; ++c) a += B[v * 4 + c] * tL[c];
+    if (eR >= 0) {
+#pragma unroll
+      for (int c = 0; c < 4; ++c) a += B[16 + v * 4 + c] * tR[c];
+    }
+    g[v] = a;
+  }
+}
+
+template <class T, int P>
+__global__ void __launch_bounds__(256) elem_apply_kernel(DGData<T> d, const T* __restrict__ Avol,
+                                                         const T* __restrict__ dv, const T* __restrict__ G,
+                                                         T* __restrict__ out, const T* __restrict__ escale,
+                                                         const int* __restrict__ skip,
+                                                         const double* __restrict__ oscale) {
+  using O = Ord<P>;
+  constexpr int NB = O::NB, NQ = O::NQ, NFQ = O::NFQ, ET = O::ET, NVB = 4 * NB;
+  __shared__ T sBv[NQ * NB];
+  __shared__ T sDv[2 * NQ * NB];
+  __shared__ T sBf[3 * NFQ * NB];
+  __shared__ T sdu[ET * NVB];
+  __shared__ T sF[ET * NQ * 8];
+  __shared__ T ssd[ET];
+  static_assert(ET * NQ <= 256, "one volume point per thread");
+  if (skip && *skip) return;
+  const int64_t e0 = (int64_t)blockIdx.x * ET;
+  const int ne = (int)((d.E - e0) < ET ? (d.E - e0) : ET);
+  const int64_t n = d.E * NQ;
+  // issue this thread's point-Jacobian loads first, so they are in flight while the
+  // block stages its tile of dv in shared memory
+  const int el1 = threadIdx.x / NQ, q1 = threadIdx.x - (threadIdx.x / NQ) * NQ;
+  const bool has_pt = threadIdx.x < ne * NQ;
+  const int64_t pidx = (e0 + el1) * NQ + q1;
+  T A[32];
+#pragma unroll
+  for (int k = 0; k < 32; ++k) A[k] = has_pt ? Avol[(int64_t)k * n + pidx] : T(0);
+  for (int i = threadIdx.x; i < NQ * NB; i += blockDim.x) sBv[i] = d.Bv[i];
+  for (int i = threadIdx.x; i < 2 * NQ * NB; i += blockDim.x) sDv[i] = d.Dv[i];
+  for (int i = threadIdx.x; i < 3 * NFQ * NB; i += blockDim.x) sBf[i] = d.Bf[i];
+  for (int i = threadIdx.x; i < ne * NVB; i += blockDim.x) sdu[i] = dv[e0 * NVB + i];
+  for (int i = threadIdx.x; i < ne; i += blockDim.x) ssd[i] = d.geo[(e0 + i) * 8 + 4];
+  __syncthreads();
+  const T osc = oscale ? (T)*oscale : T(1);
+  // phase 1: trace of dv at this thread's volume point, times the mapped flux Jacobians
+  if (has_pt) {
+    T t[4];
+#pragma unroll
+    for (int v = 0; v < 4; ++v) {
+      T a = 0;
+#pragma unroll
+      for (int j = 0; j < NB; ++j) a += sBv[q1 * NB + j] * sdu[el1 * NVB + v * NB + j];
+      t[v] = a;
+    }
+    T* fo = sF + (el1 * NQ + q1) * 8;
+#pragma unroll
+    for (int dd = 0; dd < 2; ++dd)
+#pragma unroll
+      for (int v = 0; v < 4; ++v) {
+        T a = 0;
+#pragma unroll
+        for (int c = 0; c < 4; ++c) a += A[dd * 16 + v * 4 + c] * t[c];
+        fo[dd * 4 + v] = a;
+      }
+  }
+  __syncthreads();
+  // phase 2: test against grad phi (the sqrt(det) factors cancel), lift the face terms
+  for (int it = threadIdx.x; it < ne * NVB; it += blockDim.x) {
+    const int el = it / NVB, r = it - el * NVB;
+    const int v = r / NB, i = r - v * NB;
+    T acc = 0;
+#pragma unroll
+    for (int q = 0; q < NQ; ++q)
+      acc += sDv[q * NB + i] * sF[(el * NQ + q) * 8 + v] + sDv[(NQ + q) * NB + i] * sF[(el * NQ + q) * 8 + 4 + v];
+    const int64_t e = e0 + el;
+    T lift = 0;
+#pragma unroll
+    for (int k = 0; k < 3; ++k) {
+      const int fs = d.ef[3 * e + k];
+      const int64_t face = fs >> 1;
+      const T* gf = G + face * NFQ * 4;
+      if (fs & 1) {
+#pragma unroll
+        for (int q = 0; q < NFQ; ++q) lift += sBf[(k * NFQ + (NFQ - 1 - q)) * NB + i] * gf[q * 4 + v];
+      } else {
+#pragma unroll
+        for (int q = 0; q < NFQ; ++q) lift -= sBf[(k * NFQ + q) * NB + i] * gf[q * 4 + v];
+      }
+    }
+    acc = (acc + lift / ssd[el]) * osc;
+    if (escale) acc *= escale[e];
+    out[e0 * NVB + it] = acc;
+  }
+}
+
+template <class T, int P>
+static cudaError_t linearize_p(const DGData<T>& d, const T* u, LinData<T> lin, cudaStream_t st) {
+  using O = Ord<P>;
+  const int64_t nv = d.E * O::NQ, nf = d.F * O::NFQ;
+  linearize_vol_kernel<T, P><<<(unsigned)((nv + 255) / 256), 256, 0, st>>>(d, u, lin.Avol);
+  if (nf > 0) linearize_face_kernel<T, P><<<(unsigned)((nf + 127) / 128), 128, 0, st>>>(d, u, lin.Bface);
+  return cudaGetLastError();
+}
+
+template <class T>
+cudaError_t launch_linearize(const DGData<T>& d, const T* u, LinData<T> lin, cudaStream_t st) {
+  switch (d.p) {
+    case 0: return linearize_p<T, 0>(d, u, lin, st);
+    case 1: return linearize_p<T, 1>(d, u, lin, st);
+    case 2: return linearize_p<T, 2>(d, u, lin, st);
+    case 3: return linearize_p<T, 3>(d, u, lin, st);
+  }
+  return cudaErrorInvalidValue;
+}
+
+template <class T, int P>
+static cudaError_t jac_apply_p(const DGData<T>& d, LinData<T> lin, const T* dv, T* out, T* G, const T* escale,
+                               const int* skip, const double* oscale, cudaStream_t st, const cudaEvent_t* ev) {
+  using O = Ord<P>;
+  const int64_t nf = d.F * O::NFQ;
+  if (ev) cudaEventRecord(ev[0], st);
+  if (nf > 0) face_apply_kernel<T, P><<<(unsigned)((nf + 255) / 256), 256, 0, st>>>(d, lin.Bface, dv, G, skip);
+  if (ev) cudaEventRecord(ev[1], st);
+  const int64_t eb = (d.E + O::ET - 1) / O::ET;
+  elem_apply_kernel<T, P><<<(unsigned)eb, 256, 0, st>>>(d, lin.Avol, dv, G, out, escale, skip, oscale);
+  if (ev) cudaEventRecord(ev[2], st);
+  return cudaGetLastError();
+}
+
+template <class T>
+cudaError_t launch_jac_apply(const DGData<T>& d, LinData<T> lin, const T* dv, T* out, T* G, const T* escale,
+                             const int* skip, const double* oscale, cudaStream_t st, const cudaEvent_t* ev) {
+  switch (d.p) {
+    case 0: return jac_apply_p<T, 0>(d, lin, dv, out, G, escale, skip, oscale, st, ev);
+    case 1: return jac_apply_p<T, 1>(d, lin, dv, out, G, escale, skip, oscale, st, ev);
+    case 2: return jac_apply_p<T, 2>(d, lin, dv, out, G, escale, skip, oscale, st, ev);
+    case 3: return jac_apply_p<T, 3>(d, lin, dv, out, G, escale, skip, oscale, st, ev);
+  }
+  return cudaErrorInvalidValue;
+}
+
 // ------------------------------------------------------------------ time step
 // dt_e = CFL h_e / ((2p+1)(|v| + c)) with v, c at the element centroid (Eq. x3d).
 template <class T, int P>
@@ -397,6 +694,9 @@ cudaError_t launch_density_norm(const T* R, const T* s, int64_t E, int nb, int n
 }
 
 #define PCEXP_INST(T)                                                                                         \
+  template cudaError_t launch_linearize<T>(const DGData<T>&, const T*, LinData<T>, cudaStream_t);               \
+  template cudaError_t launch_jac_apply<T>(const DGData<T>&, LinData<T>, const T*, T*, T*, const T*, const int*, \
+                                           const double*, cudaStream_t, const cudaEvent_t*);                  \
   template cudaError_t launch_dg_operator<T>(const DGData<T>&, const T*, const T*, T*, T*, const T*, const int*, \
                                              cudaStream_t, const cudaEvent_t*, const double*);                \
   template cudaError_t launch_local_dt<T>(const DGData<T>&, const T*, const double*, double, T*, double*,      \

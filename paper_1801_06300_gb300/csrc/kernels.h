@@ -59,6 +59,17 @@ struct DGData {
   int p;
 };
 
+// Point Jacobians of the DG operator at a linearisation state u (structure of
+// arrays: entry k of every point is contiguous).
+//   Avol [32][E*nq]:  k = d'*16 + v*4 + c: sum_d (A^-1)_{d'd} dF_d[v]/dU[c] at volume points
+//   Bface[32][F*nfq]: k = s*16 + v*4 + c: |e| w_q / sqrt(det_s) dF~[v]/dU_s[c], s = L (0), R (1),
+//                     the ghost-state chain rule folded into s = L on boundary faces
+template <class T>
+struct LinData {
+  T* Avol;
+  T* Bface;
+};
+
 // ---- DG operator (dg_kernels.cu)
 // out = R(u)  or  out = J(u) du  (du != nullptr); G is face-flux scratch [F][nfq][4].
 // escale (nullable): per-element output factor.  skip (nullable): device flag, nonzero = no-op.
@@ -69,6 +80,13 @@ template <class T>
 cudaError_t launch_dg_operator(const DGData<T>& d, const T* u, const T* du, T* out, T* G,
                                const T* escale, const int* skip, cudaStream_t st,
                                const cudaEvent_t* ev = nullptr, const double* oscale = nullptr);
+// Evaluate the point Jacobians at u (once per linearisation state).
+template <class T>
+cudaError_t launch_linearize(const DGData<T>& d, const T* u, LinData<T> lin, cudaStream_t st);
+// out = J(u) dv from the point Jacobians (same ev / escale / skip / oscale conventions).
+template <class T>
+cudaError_t launch_jac_apply(const DGData<T>& d, LinData<T> lin, const T* dv, T* out, T* G, const T* escale,
+                             const int* skip, const double* oscale, cudaStream_t st, const cudaEvent_t* ev);
 // dt_e = cfl h_e / ((2p+1)(|v_c| + c_c)) -> dte[E]; min over e -> *dtmin (last-block reduction).
 template <class T>
 cudaError_t launch_local_dt(const DGData<T>& d, const T* u, const double* cfl_dev, double cfl,

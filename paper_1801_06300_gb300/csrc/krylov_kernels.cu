@@ -15,37 +15,32 @@
 // Each streaming kernel writes per-block partial sums; the last block to
 // finish (atomic ticket) reduces them in a fixed order and applies the scalar
 // update, so results are deterministic and no extra launch is needed.
-// Partial products are accumulated in FP64 (FP64 form) or in FP32 over 8
-// elements and then in FP64 (FP32-mixed form).
+// Partial products are accumulated in FP64 (FP64 form) or in compensated FP32
+// pairs converted to FP64 once per warp (FP32-mixed form).
+#include <cooperative_groups.h>
 #include <cfloat>
 
 #include "kernels.h"
 
 namespace pcexp {
 
-// Elements per thread per row-loop iteration: 16-byte (double2) loads in FP64;
-// in FP32 two float4 loads for the read-only reductions and one float4 where the
-// kernel also keeps every basis element in registers (update + projection).
-template <class T, int MODE> struct VecN {
-  static constexpr int N = sizeof(T) == 8 ? 2 : ((MODE == CGS_PROJ || MODE == CGS_NORM) ? 8 : 4);
+// Elements per thread per row-loop iteration: one 16-byte load (double2 / float4).
+template <class T> struct VecN {
+  static constexpr int N = 16 / sizeof(T);
 };
 
 template <class T, int VN>
-PCEXP_DEV void load_vec(const T* p, T (&x)[VN], bool stream) {
+PCEXP_DEV void load_vec(const T* p, T (&x)[VN]) {
   if constexpr (sizeof(T) == 8) {
-    static_assert(VN == 2, "FP64 uses double2");
-    double2 a = stream ? __ldcs(reinterpret_cast<const double2*>(p)) : *reinterpret_cast<const double2*>(p);
+    double2 a = *reinterpret_cast<const double2*>(p);
     x[0] = a.x;
     x[1] = a.y;
   } else {
-#pragma unroll
-    for (int h = 0; h < VN / 4; ++h) {
-      float4 a = stream ? __ldcs(reinterpret_cast<const float4*>(p) + h) : reinterpret_cast<const float4*>(p)[h];
-      x[4 * h + 0] = a.x;
-      x[4 * h + 1] = a.y;
-      x[4 * h + 2] = a.z;
-      x[4 * h + 3] = a.w;
-    }
+    float4 a = *reinterpret_cast<const float4*>(p);
+    x[0] = a.x;
+    x[1] = a.y;
+    x[2] = a.z;
+    x[3] = a.w;
   }
 }
 template <class T, int VN>
@@ -53,26 +48,86 @@ PCEXP_DEV void store_vec(T* p, const T (&x)[VN]) {
   if constexpr (sizeof(T) == 8) {
     *reinterpret_cast<double2*>(p) = make_double2(x[0], x[1]);
   } else {
-#pragma unroll
-    for (int h = 0; h < VN / 4; ++h)
-      reinterpret_cast<float4*>(p)[h] = make_float4(x[4 * h], x[4 * h + 1], x[4 * h + 2], x[4 * h + 3]);
+    *reinterpret_cast<float4*>(p) = make_float4(x[0], x[1], x[2], x[3]);
   }
 }
 
-// sum_v a[v] * b[v] in T (FP32 partial over VN elements in the mixed form), returned in FP64
+// Dot-product accumulator.  FP64 form: a double.  FP32-mixed form: an unevaluated
+// float pair hi + lo updated with Knuth's TwoSum, so per-thread sums and the warp
+// shuffle tree run on the FP32 pipe (GB300 has 1/62 the FP64 rate) while keeping
+// about twice FP32 precision; each warp converts to FP64 once per column.
+// Both are 8 bytes, so block partial sums are stored in the same FP64-sized slots; the
+// float pair stays a pair through the block and grid reductions and is converted to
+// FP64 once per column (each FP64 warp instruction costs tens of cycles here).
+template <class T> struct Acc;
+template <> struct Acc<double> {
+  double s;
+  PCEXP_DEV void zero() { s = 0.0; }
+  PCEXP_DEV void add(double x) { s += x; }
+  PCEXP_DEV void add_acc(const Acc& o) { s += o.s; }
+  PCEXP_DEV void add_partner(int o) { s += __shfl_xor_sync(0xffffffffu, s, o); }
+  PCEXP_DEV double value() const { return s; }
+};
+template <> struct Acc<float> {
+  float hi, lo;
+  PCEXP_DEV void zero() { hi = lo = 0.f; }
+  PCEXP_DEV void add(float x) {
+    const float s = hi + x;
+    const float bp = s - hi;
+    lo += (hi - (s - bp)) + (x - bp);
+    hi = s;
+  }
+  PCEXP_DEV void add_acc(const Acc& o) {
+    add(o.hi);
+    lo += o.lo;
+  }
+  PCEXP_DEV void add_partner(int o) {
+    Acc p;
+    p.hi = __shfl_xor_sync(0xffffffffu, hi, o);
+    p.lo = __shfl_xor_sync(0xffffffffu, lo, o);
+    add_acc(p);
+  }
+  PCEXP_DEV double value() const { return (double)hi + (double)lo; }
+};
+static_assert(sizeof(Acc<float>) == 8 && sizeof(Acc<double>) == 8, "partials are 8-byte slots");
+
+// sum_v a[v] * b[v] in T (FMA chain over one 16-byte chunk)
 template <class T, int VN>
-PCEXP_DEV double dot_vec(const T (&a)[VN], const T (&b)[VN]) {
+PCEXP_DEV T dot_vec(const T (&a)[VN], const T (&b)[VN]) {
   T s = 0;
 #pragma unroll
   for (int v = 0; v < VN; ++v) s = fma(a[v], b[v], s);
-  return (double)s;
+  return s;
 }
 
-// Scalar stage logic run by one thread of the last block.
+// Stage logic of the last block: per-column entries in parallel, scalars on thread 0.
 PCEXP_DEV void cgs_finalize(int mode, int j, const double* dots, KState* ks, double eta) {
+  __shared__ int bad;
+  if (threadIdx.x == 0) bad = 0;
+  __syncthreads();
+  if (mode == CGS_PROJ || mode == CGS_UPD_PROJ) {
+    // w = J v_j is already normalised by s_j (applied by the J v kernel)
+    for (int i = threadIdx.x; i <= j; i += blockDim.x) {
+      const double si = ks->s[i];
+      const double h = si * dots[i];
+      if (!isfinite(h)) bad = 1;
+      if (mode == CGS_PROJ) ks->H[i * MMAX + j] = h;
+      else ks->H[i * MMAX + j] += h;
+      ks->coef[i] = si * h;
+    }
+    __syncthreads();
+    if (threadIdx.x == 0) {
+      if (mode == CGS_PROJ) ks->wnorm0 = sqrt(dots[j + 1]);
+      if (bad) {
+        ks->err = 1;
+        ks->done = 1;
+      }
+    }
+    return;
+  }
+  if (threadIdx.x != 0) return;
   if (mode == CGS_NORM) {
-    const double b2 = dots[0];
-    const double beta = sqrt(b2);
+    const double beta = sqrt(dots[0]);
     ks->beta = beta;
     ks->k = 0;
     if (!isfinite(beta)) {
@@ -86,36 +141,17 @@ PCEXP_DEV void cgs_finalize(int mode, int j, const double* dots, KState* ks, dou
     }
     return;
   }
-  // w = J v_j is already normalised by s_j (applied by the J v kernel)
-  if (mode == CGS_PROJ || mode == CGS_UPD_PROJ) {
-    bool ok = true;
-    for (int i = 0; i <= j; ++i) {
-      const double si = ks->s[i];
-      const double h = si * dots[i];
-      ok = ok && isfinite(h);
-      if (mode == CGS_PROJ) ks->H[i * MMAX + j] = h;
-      else ks->H[i * MMAX + j] += h;
-      ks->coef[i] = si * si * dots[i];
-    }
-    if (mode == CGS_PROJ) ks->wnorm0 = sqrt(dots[j + 1]);
-    if (!ok) {
-      ks->err = 1;
-      ks->done = 1;
-    }
-    return;
-  }
   // CGS_UPD_NORM
-  const double nn = sqrt(dots[0]);
-  const double hn = nn;
+  const double hn = sqrt(dots[0]);
   ks->H[(j + 1) * MMAX + j] = hn;
   ks->k = j + 1;
   if (!isfinite(hn)) {
     ks->err = 1;
     ks->done = 1;
-  } else if (nn == 0.0 || hn <= eta * ks->wnorm0) {
+  } else if (hn == 0.0 || hn <= eta * ks->wnorm0) {
     ks->done = 1;  // happy breakdown: K_{j+1} is invariant
   } else {
-    ks->s[j + 1] = 1.0 / nn;
+    ks->s[j + 1] = 1.0 / hn;
   }
 }
 
@@ -123,70 +159,77 @@ template <class T, int NC, int MODE>
 __global__ void __launch_bounds__(256) cgs_kernel(const T* __restrict__ Z, int64_t ldz, int64_t Kp, int j,
                                                   T* __restrict__ w, T* __restrict__ out, KState* ks,
                                                   double* __restrict__ partials, double eta) {
-  constexpr int VN = VecN<T, MODE>::N;
+  constexpr int VN = VecN<T>::N;
   constexpr int NACC = (MODE == CGS_PROJ) ? NC + 1 : (MODE == CGS_UPD_PROJ ? NC : 1);
   __shared__ T scoef[NC > 0 ? NC : 1];
-  __shared__ double red[8][NACC];
+  __shared__ Acc<T> red[8][NACC];
   __shared__ bool last;
   if (ks->done) return;  // breakdown reached earlier: uniform early exit
   const int nc = (MODE == CGS_NORM) ? 0 : j + 1;
   if (MODE == CGS_UPD_PROJ || MODE == CGS_UPD_NORM)
     for (int c = threadIdx.x; c < nc; c += blockDim.x) scoef[c] = (T)ks->coef[c];
   __syncthreads();
-  double acc[NACC];
+  Acc<T> acc[NACC];
 #pragma unroll
-  for (int c = 0; c < NACC; ++c) acc[c] = 0.0;
+  for (int c = 0; c < NACC; ++c) acc[c].zero();
   const int64_t stride = (int64_t)gridDim.x * blockDim.x * VN;
   for (int64_t r = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) * VN; r < Kp; r += stride) {
     T x[VN];
-    load_vec<T, VN>(w + r, x, false);
+    load_vec<T, VN>(w + r, x);
     if constexpr (MODE == CGS_NORM) {
-      acc[0] += dot_vec<T, VN>(x, x);
+      acc[0].add(dot_vec<T, VN>(x, x));
     } else if constexpr (MODE == CGS_PROJ) {
 #pragma unroll
       for (int c = 0; c < NC; ++c) {
         if (c < nc) {
           T z[VN];
-          load_vec<T, VN>(Z + c * ldz + r, z, true);
-          acc[c] += dot_vec<T, VN>(z, x);
+          load_vec<T, VN>(Z + c * ldz + r, z);
+          acc[c].add(dot_vec<T, VN>(z, x));
         }
       }
-      acc[NC] += dot_vec<T, VN>(x, x);
+      acc[NC].add(dot_vec<T, VN>(x, x));
     } else {
-      T zc[NC][VN];
+      // update pass; the projection pass below re-reads the same 16-byte chunks (L1)
 #pragma unroll
       for (int c = 0; c < NC; ++c) {
         if (c < nc) {
-          load_vec<T, VN>(Z + c * ldz + r, zc[c], true);
+          T z[VN];
+          load_vec<T, VN>(Z + c * ldz + r, z);
 #pragma unroll
-          for (int v = 0; v < VN; ++v) x[v] = fma(-scoef[c], zc[c][v], x[v]);
+          for (int v = 0; v < VN; ++v) x[v] = fma(-scoef[c], z[v], x[v]);
         }
       }
       if constexpr (MODE == CGS_UPD_PROJ) {
         store_vec<T, VN>(w + r, x);
 #pragma unroll
-        for (int c = 0; c < NC; ++c)
-          if (c < nc) acc[c] += dot_vec<T, VN>(zc[c], x);
+        for (int c = 0; c < NC; ++c) {
+          if (c < nc) {
+            T z[VN];
+            load_vec<T, VN>(Z + c * ldz + r, z);
+            acc[c].add(dot_vec<T, VN>(z, x));
+          }
+        }
       } else {
         store_vec<T, VN>(out + r, x);
-        acc[0] += dot_vec<T, VN>(x, x);
+        acc[0].add(dot_vec<T, VN>(x, x));
       }
     }
   }
-  // block reduction (fixed order)
+  // block reduction in the accumulator type (fixed order): warp tree, then over warps
   const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5, nw = blockDim.x >> 5;
 #pragma unroll
   for (int c = 0; c < NACC; ++c) {
-    double a = acc[c];
-    for (int o = 16; o > 0; o >>= 1) a += __shfl_xor_sync(0xffffffffu, a, o);
-    if (lane == 0) red[wid][c] = a;
+    for (int o = 16; o > 0; o >>= 1) acc[c].add_partner(o);
+    if (lane == 0) red[wid][c] = acc[c];
   }
   __syncthreads();
   const int nred = (MODE == CGS_PROJ) ? nc + 1 : (MODE == CGS_UPD_PROJ ? nc : 1);
+  Acc<T>* P = reinterpret_cast<Acc<T>*>(partials);
   for (int c = threadIdx.x; c < nred; c += blockDim.x) {
-    double a = 0;
-    for (int q = 0; q < nw; ++q) a += red[q][(MODE == CGS_PROJ && c == nc) ? NC : c];
-    partials[(int64_t)c * gridDim.x + blockIdx.x] = a;
+    const int cc = (MODE == CGS_PROJ && c == nc) ? NC : c;
+    Acc<T> a = red[0][cc];
+    for (int q = 1; q < nw; ++q) a.add_acc(red[q][cc]);
+    P[(int64_t)c * gridDim.x + blockIdx.x] = a;
   }
   __threadfence();
   __syncthreads();
@@ -195,43 +238,79 @@ __global__ void __launch_bounds__(256) cgs_kernel(const T* __restrict__ Z, int64
   if (!last) return;
   __threadfence();
   __shared__ double dots[MMAX + 2];
+  // every lane issues all its partial loads before summing them (fixed order per lane,
+  // fixed shuffle tree), so the serial tail of the last block is one L2 round trip
+  constexpr int PER_LANE = (RED_BLOCKS + 31) / 32;
   for (int c = wid; c < nred; c += nw) {
-    double a = 0;
-    for (unsigned b = lane; b < gridDim.x; b += 32) a += __ldcg(partials + (int64_t)c * gridDim.x + b);
-    for (int o = 16; o > 0; o >>= 1) a += __shfl_xor_sync(0xffffffffu, a, o);
-    if (lane == 0) dots[c] = a;
+    const unsigned long long* pc = reinterpret_cast<const unsigned long long*>(P + (int64_t)c * gridDim.x);
+    unsigned long long pv[PER_LANE];
+#pragma unroll
+    for (int t = 0; t < PER_LANE; ++t) {
+      const unsigned b = lane + 32u * t;
+      pv[t] = b < gridDim.x ? __ldcg(pc + b) : 0ull;
+    }
+    Acc<T> a;
+    a.zero();
+#pragma unroll
+    for (int t = 0; t < PER_LANE; ++t) a.add_acc(*reinterpret_cast<const Acc<T>*>(&pv[t]));
+    for (int o = 16; o > 0; o >>= 1) a.add_partner(o);
+    if (lane == 0) dots[c] = a.value();
   }
   __syncthreads();
-  if (threadIdx.x == 0) {
-    cgs_finalize(MODE, j, dots, ks, eta);
-    ks->counter = 0;
+  cgs_finalize(MODE, j, dots, ks, eta);
+  if (threadIdx.x == 0) ks->counter = 0;
+}
+
+template <class KernelT>
+static unsigned wave_grid(KernelT kernel, int64_t chunks) {
+  static int sms = 0;
+  if (sms == 0) {
+    int dev = 0;
+    cudaGetDevice(&dev);
+    cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+    if (sms <= 0) sms = 152;
   }
+  int occ = 1;
+  cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, kernel, 256, 0);
+  if (occ < 1) occ = 1;
+  int64_t g = (int64_t)sms * occ;
+  const int64_t need = (chunks + 255) / 256;
+  if (g > need) g = need;
+  if (g > RED_BLOCKS) g = RED_BLOCKS;
+  return (unsigned)(g < 1 ? 1 : g);
+}
+
+template <class T, int NC, int MODE>
+static void cgs_launch(const T* Z, int64_t ldz, int64_t Kp, int j, T* w, T* out, KState* ks, double* partials,
+                       double eta, cudaStream_t st) {
+  static unsigned grid_cache = 0;
+  static int64_t kp_cache = -1;
+  if (kp_cache != Kp) {
+    grid_cache = wave_grid(cgs_kernel<T, NC, MODE>, Kp / VecN<T>::N);
+    kp_cache = Kp;
+  }
+  cgs_kernel<T, NC, MODE><<<grid_cache, 256, 0, st>>>(Z, ldz, Kp, j, w, out, ks, partials, eta);
 }
 
 template <class T, int MODE>
 static void cgs_dispatch(int nc, const T* Z, int64_t ldz, int64_t Kp, int j, T* w, T* out, KState* ks,
-                         double* partials, double eta, unsigned grid, cudaStream_t st) {
-  if (nc <= 4) cgs_kernel<T, 4, MODE><<<grid, 256, 0, st>>>(Z, ldz, Kp, j, w, out, ks, partials, eta);
-  else if (nc <= 8) cgs_kernel<T, 8, MODE><<<grid, 256, 0, st>>>(Z, ldz, Kp, j, w, out, ks, partials, eta);
-  else if (nc <= 16) cgs_kernel<T, 16, MODE><<<grid, 256, 0, st>>>(Z, ldz, Kp, j, w, out, ks, partials, eta);
-  else cgs_kernel<T, 32, MODE><<<grid, 256, 0, st>>>(Z, ldz, Kp, j, w, out, ks, partials, eta);
+                         double* partials, double eta, cudaStream_t st) {
+  if (nc <= 4) cgs_launch<T, 4, MODE>(Z, ldz, Kp, j, w, out, ks, partials, eta, st);
+  else if (nc <= 8) cgs_launch<T, 8, MODE>(Z, ldz, Kp, j, w, out, ks, partials, eta, st);
+  else if (nc <= 16) cgs_launch<T, 16, MODE>(Z, ldz, Kp, j, w, out, ks, partials, eta, st);
+  else cgs_launch<T, 32, MODE>(Z, ldz, Kp, j, w, out, ks, partials, eta, st);
 }
 
 template <class T>
 cudaError_t launch_cgs(int mode, const T* Z, int64_t ldz, int64_t Kp, int j, T* w, T* out, KState* ks,
                        double* partials, double eta, cudaStream_t st) {
-  const int64_t per = 256LL * 2;
-  int64_t g = (Kp + per - 1) / per;
-  if (g > RED_BLOCKS) g = RED_BLOCKS;
-  if (g < 1) g = 1;
-  const unsigned grid = (unsigned)g;
   const int nc = j + 1;
   if (nc > MMAX) return cudaErrorInvalidValue;
   switch (mode) {
-    case CGS_NORM: cgs_kernel<T, 0, CGS_NORM><<<grid, 256, 0, st>>>(Z, ldz, Kp, j, w, out, ks, partials, eta); break;
-    case CGS_PROJ: cgs_dispatch<T, CGS_PROJ>(nc, Z, ldz, Kp, j, w, out, ks, partials, eta, grid, st); break;
-    case CGS_UPD_PROJ: cgs_dispatch<T, CGS_UPD_PROJ>(nc, Z, ldz, Kp, j, w, out, ks, partials, eta, grid, st); break;
-    case CGS_UPD_NORM: cgs_dispatch<T, CGS_UPD_NORM>(nc, Z, ldz, Kp, j, w, out, ks, partials, eta, grid, st); break;
+    case CGS_NORM: cgs_launch<T, 0, CGS_NORM>(Z, ldz, Kp, j, w, out, ks, partials, eta, st); break;
+    case CGS_PROJ: cgs_dispatch<T, CGS_PROJ>(nc, Z, ldz, Kp, j, w, out, ks, partials, eta, st); break;
+    case CGS_UPD_PROJ: cgs_dispatch<T, CGS_UPD_PROJ>(nc, Z, ldz, Kp, j, w, out, ks, partials, eta, st); break;
+    case CGS_UPD_NORM: cgs_dispatch<T, CGS_UPD_NORM>(nc, Z, ldz, Kp, j, w, out, ks, partials, eta, st); break;
     default: return cudaErrorInvalidValue;
   }
   return cudaGetLastError();
@@ -243,34 +322,50 @@ cudaError_t launch_cgs(int mode, const T* Z, int64_t ldz, int64_t Kp, int j, T* 
 //   r(X) = N(X) / N(-X),  N(X) = sum_j c_j X^j,  c_j = (16-j)! 8! / (16! j! (8-j)!),
 // applied to X = A / 2^s with ||X||_1 <= 1, where the Pade error is far below
 // FP64 rounding.  Column k of exp(A) holds phi_1(dt H) e_1, column k+1 phi_2(dt H) e_1.
+//
+// FP64 issues at a few instructions per clock per SM on this GPU, so one CTA would
+// spend ~10 us per (m+2)^3 product.  The kernel runs as a cluster of PHI_CTAS CTAs:
+// every CTA keeps a full copy of the matrices in shared memory, computes its share of
+// the rows of each product and writes them into every CTA of the cluster (distributed
+// shared memory), then the cluster barrier publishes them.  The Pade solve factors the
+// denominator redundantly in each CTA and splits the right-hand-side columns.
 constexpr int PN = MMAX + 2;
+constexpr int PHI_CTAS = 8;
 
-__device__ void mat_mul(const double* A, const double* B, double* C, int n) {
-  for (int t = threadIdx.x; t < n * n; t += blockDim.x) {
-    const int i = t / n, jj = t - i * n;
+namespace cg = cooperative_groups;
+
+// C = A B for rows i = rank, rank + PHI_CTAS, ... ; results broadcast to all CTAs.
+__device__ void mat_mul_cluster(cg::cluster_group& cl, const double* A, const double* B, double* C, int n) {
+  const int rank = (int)cl.block_rank();
+  const int nrow = (n - rank + PHI_CTAS - 1) / PHI_CTAS;
+  for (int t = threadIdx.x; t < nrow * n; t += blockDim.x) {
+    const int i = rank + (t / n) * PHI_CTAS, jj = t % n;
     double a = 0;
     for (int l = 0; l < n; ++l) a = fma(A[i * PN + l], B[l * PN + jj], a);
-    C[i * PN + jj] = a;
+#pragma unroll
+    for (int r = 0; r < PHI_CTAS; ++r) cl.map_shared_rank(C, r)[i * PN + jj] = a;
   }
-  __syncthreads();
+  cl.sync();
 }
 
-__global__ void __launch_bounds__(512) phi_kernel(KState* ks, const double* dt_dev, double dt_host,
-                                                  double factor, StepState* ss, int stage) {
+__global__ void __cluster_dims__(PHI_CTAS, 1, 1) __launch_bounds__(256)
+    phi_kernel(KState* ks, const double* dt_dev, double dt_host, double factor, StepState* ss, int stage) {
   extern __shared__ double sm[];
-  double* A = sm;             // X, later the result
+  double* A = sm;             // X = A / 2^s
   double* B2 = A + PN * PN;
   double* B4 = B2 + PN * PN;
   double* B6 = B4 + PN * PN;
-  double* Nm = B6 + PN * PN;  // V + U
+  double* Nm = B6 + PN * PN;  // V + U, then the solution X
   double* Dm = Nm + PN * PN;  // V - U
   double* Tm = Dm + PN * PN;
   __shared__ int s_sq;
   __shared__ int piv_row;
+  cg::cluster_group cl = cg::this_cluster();
+  const int rank = (int)cl.block_rank();
   const int k = ks->k;
   const double dt = dt_dev ? *dt_dev : dt_host;
-  if (k == 0 || ks->err) {
-    if (threadIdx.x == 0) {
+  if (k == 0 || ks->err) {  // uniform across the cluster: no shared-memory traffic happens
+    if (rank == 0 && threadIdx.x == 0) {
       for (int i = 0; i <= MMAX; ++i) ks->acoef[i] = 0.0;
       if (ss) {
         ss->k[stage] = 0;
@@ -292,21 +387,31 @@ __global__ void __launch_bounds__(512) phi_kernel(KState* ks, const double* dt_d
     A[k * PN + k + 1] = 1.0;
   }
   __syncthreads();
-  if (threadIdx.x == 0) {
-    double nrm = 0;
-    for (int jj = 0; jj < n; ++jj) {
-      double c = 0;
-      for (int i = 0; i < n; ++i) c += fabs(A[i * PN + jj]);
-      nrm = fmax(nrm, c);
+  // ||A||_1 from parallel column sums in FP32 (it only selects s; the same arithmetic
+  // in every CTA gives the same s), reduced by warp 0
+  {
+    __shared__ float colsum[PN];
+    for (int jj = threadIdx.x; jj < n; jj += blockDim.x) {
+      float c = 0.f;
+      for (int i = 0; i < n; ++i) c += fabsf((float)A[i * PN + jj]);
+      colsum[jj] = c;
     }
-    int s = 0;
-    if (nrm > 1.0) s = (int)ceil(log2(nrm));
-    if (!isfinite(nrm) || s > 1000) s = -1;
-    s_sq = s;
+    __syncthreads();
+    if (threadIdx.x < 32) {
+      float m = 0.f;
+      for (int jj = threadIdx.x; jj < n; jj += 32) m = fmaxf(m, colsum[jj]);
+      for (int o = 16; o > 0; o >>= 1) m = fmaxf(m, __shfl_xor_sync(0xffffffffu, m, o));
+      if (threadIdx.x == 0) {
+        int s = 0;
+        if (m > 1.0f) s = (int)ceilf(log2f(m)) + 1;  // +1 covers the FP32 estimate
+        if (!(m <= 3.0e38f) || s > 1000) s = -1;     // NaN or overflow
+        s_sq = s;
+      }
+    }
   }
   __syncthreads();
   if (s_sq < 0) {
-    if (threadIdx.x == 0) {
+    if (rank == 0 && threadIdx.x == 0) {
       ks->err = 1;
       if (ss) ss->err = 1;
     }
@@ -317,16 +422,15 @@ __global__ void __launch_bounds__(512) phi_kernel(KState* ks, const double* dt_d
     const int i = t / n, jj = t - i * n;
     A[i * PN + jj] *= sc;
   }
-  __syncthreads();
-  // Pade [8/8] coefficients
+  // every CTA must have finished writing its own A before remote products land in B2
+  cl.sync();
   double c[9];
   c[0] = 1.0;
   for (int jj = 1; jj <= 8; ++jj) c[jj] = c[jj - 1] * (double)(8 - jj + 1) / (double)(jj * (16 - jj + 1));
-  mat_mul(A, A, B2, n);
-  mat_mul(B2, B2, B4, n);
-  mat_mul(B4, B2, B6, n);
-  // B8 into Tm
-  mat_mul(B4, B4, Tm, n);
+  mat_mul_cluster(cl, A, A, B2, n);
+  mat_mul_cluster(cl, B2, B2, B4, n);
+  mat_mul_cluster(cl, B4, B2, B6, n);
+  mat_mul_cluster(cl, B4, B4, Tm, n);  // B8
   // V = c0 I + c2 B2 + c4 B4 + c6 B6 + c8 B8 -> Dm ; W = c1 I + c3 B2 + c5 B4 + c7 B6 -> Nm
   for (int t = threadIdx.x; t < n * n; t += blockDim.x) {
     const int i = t / n, jj = t - i * n;
@@ -335,8 +439,9 @@ __global__ void __launch_bounds__(512) phi_kernel(KState* ks, const double* dt_d
     Dm[o] = c[0] * id + c[2] * B2[o] + c[4] * B4[o] + c[6] * B6[o] + c[8] * Tm[o];
     Nm[o] = c[1] * id + c[3] * B2[o] + c[5] * B4[o] + c[7] * B6[o];
   }
-  __syncthreads();
-  mat_mul(A, Nm, Tm, n);  // U = X W
+  // Tm is overwritten by the next product: all CTAs must be done reading it
+  cl.sync();
+  mat_mul_cluster(cl, A, Nm, Tm, n);  // U = X W
   for (int t = threadIdx.x; t < n * n; t += blockDim.x) {
     const int i = t / n, jj = t - i * n;
     const int o = i * PN + jj;
@@ -345,64 +450,97 @@ __global__ void __launch_bounds__(512) phi_kernel(KState* ks, const double* dt_d
     Dm[o] = V - U;
   }
   __syncthreads();
-  // solve Dm X = Nm (Gaussian elimination, partial pivoting); X overwrites Nm
+  // solve Dm X = Nm: LU with partial pivoting repeated in every CTA (identical),
+  // right-hand-side columns jj = rank, rank + PHI_CTAS, ... in this CTA
+  const int ncol = (n - rank + PHI_CTAS - 1) / PHI_CTAS;
   for (int col = 0; col < n; ++col) {
-    if (threadIdx.x == 0) {
-      int pr = col;
-      double best = fabs(Dm[col * PN + col]);
-      for (int i = col + 1; i < n; ++i) {
-        const double v = fabs(Dm[i * PN + col]);
-        if (v > best) {
-          best = v;
-          pr = i;
+    if (threadIdx.x < 32) {
+      // partial pivoting: largest |Dm[i][col]|, i >= col, by warp argmax on the bit
+      // patterns of |x| (their integer order is the order of the magnitudes)
+      unsigned long long best = 0ull;
+      int bi = col;
+      for (int i = col + threadIdx.x; i < n; i += 32) {
+        const unsigned long long key = (unsigned long long)__double_as_longlong(Dm[i * PN + col]) & 0x7fffffffffffffffull;
+        if (key > best || i == col) {
+          best = key;
+          bi = i;
         }
       }
-      piv_row = pr;
+      for (int o = 16; o > 0; o >>= 1) {
+        const unsigned long long ob = __shfl_xor_sync(0xffffffffu, best, o);
+        const int oi = __shfl_xor_sync(0xffffffffu, bi, o);
+        if (ob > best || (ob == best && oi < bi)) {
+          best = ob;
+          bi = oi;
+        }
+      }
+      if (threadIdx.x == 0) piv_row = bi;
     }
     __syncthreads();
     const int pr = piv_row;
     if (pr != col) {
+      // Dm is private to this CTA; of Nm only this CTA's own columns are touched
       for (int t = threadIdx.x; t < n; t += blockDim.x) {
         double a = Dm[col * PN + t];
         Dm[col * PN + t] = Dm[pr * PN + t];
         Dm[pr * PN + t] = a;
-        double b = Nm[col * PN + t];
-        Nm[col * PN + t] = Nm[pr * PN + t];
-        Nm[pr * PN + t] = b;
+      }
+      for (int t = threadIdx.x; t < ncol; t += blockDim.x) {
+        const int jj = rank + t * PHI_CTAS;
+        double b = Nm[col * PN + jj];
+        Nm[col * PN + jj] = Nm[pr * PN + jj];
+        Nm[pr * PN + jj] = b;
       }
       __syncthreads();
     }
     const double piv = Dm[col * PN + col];
-    for (int t = threadIdx.x; t < (n - col - 1) * n; t += blockDim.x) {
-      const int i = col + 1 + t / n, jj = t % n;
+    const int nr = n - col - 1, w = (n - col - 1) + ncol;  // matrix part, then own RHS columns
+    for (int t = threadIdx.x; t < nr * w; t += blockDim.x) {
+      const int i = col + 1 + t / w, q = t % w;
       const double f = Dm[i * PN + col] / piv;
-      Nm[i * PN + jj] -= f * Nm[col * PN + jj];
-      if (jj > col) Dm[i * PN + jj] -= f * Dm[col * PN + jj];
+      if (q < n - col - 1) {
+        const int jj = col + 1 + q;
+        Dm[i * PN + jj] -= f * Dm[col * PN + jj];
+      } else {
+        const int jj = rank + (q - (n - col - 1)) * PHI_CTAS;
+        Nm[i * PN + jj] -= f * Nm[col * PN + jj];
+      }
     }
     __syncthreads();
-    for (int t = threadIdx.x; t < n - col - 1; t += blockDim.x) Dm[(col + 1 + t) * PN + col] = 0.0;
+    for (int t = threadIdx.x; t < nr; t += blockDim.x) Dm[(col + 1 + t) * PN + col] = 0.0;
     __syncthreads();
   }
   for (int col = n - 1; col >= 0; --col) {
     const double piv = Dm[col * PN + col];
-    for (int t = threadIdx.x; t < n; t += blockDim.x) Nm[col * PN + t] /= piv;
+    for (int t = threadIdx.x; t < ncol; t += blockDim.x) Nm[col * PN + rank + t * PHI_CTAS] /= piv;
     __syncthreads();
-    for (int t = threadIdx.x; t < col * n; t += blockDim.x) {
-      const int i = t / n, jj = t % n;
+    for (int t = threadIdx.x; t < col * ncol; t += blockDim.x) {
+      const int i = t / ncol, jj = rank + (t % ncol) * PHI_CTAS;
       Nm[i * PN + jj] -= Dm[i * PN + col] * Nm[col * PN + jj];
     }
     __syncthreads();
   }
+  // publish this CTA's solution columns to the whole cluster, once every CTA has
+  // finished writing V + U into its own copy of Nm
+  cl.sync();
+  for (int t = threadIdx.x; t < n * ncol; t += blockDim.x) {
+    const int i = t / ncol, jj = rank + (t % ncol) * PHI_CTAS;
+    const double v = Nm[i * PN + jj];
+#pragma unroll
+    for (int r = 0; r < PHI_CTAS; ++r)
+      if (r != rank) cl.map_shared_rank(Nm, r)[i * PN + jj] = v;
+  }
+  cl.sync();
   // squaring
   double* X = Nm;
   double* Y = Tm;
   for (int it = 0; it < s_sq; ++it) {
-    mat_mul(X, X, Y, n);
+    mat_mul_cluster(cl, X, X, Y, n);
     double* t = X;
     X = Y;
     Y = t;
   }
-  if (threadIdx.x == 0) {
+  if (rank == 0 && threadIdx.x == 0) {
     const double beta = ks->beta;
     bool ok = true;
     for (int i = 0; i < k; ++i) {
@@ -431,7 +569,7 @@ cudaError_t launch_phi(KState* ks, const double* dt_dev, double dt, double facto
     if (e != cudaSuccess) return e;
     attr_set = true;
   }
-  phi_kernel<<<1, 512, smem, st>>>(ks, dt_dev, dt, factor, ss, stage);
+  phi_kernel<<<PHI_CTAS, 256, smem, st>>>(ks, dt_dev, dt, factor, ss, stage);
   return cudaGetLastError();
 }
 

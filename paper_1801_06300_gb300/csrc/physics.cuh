@@ -66,9 +66,109 @@ template <class T> PCEXP_DEV Tangent<T> pow_s(Tangent<T> x, T e) {
 }
 template <class S> PCEXP_DEV S select_s(bool c, S a, S b) { return c ? a : b; }
 
-template <class S, class T> PCEXP_DEV S lift_s(T x) { return S(x); }
-template <> PCEXP_DEV Tangent<double> lift_s<Tangent<double>, double>(double x) { return {x, 0.0}; }
-template <> PCEXP_DEV Tangent<float> lift_s<Tangent<float>, float>(float x) { return {x, 0.0f}; }
+
+// ------------------------------------------------- multi-direction tangent (Jacobians)
+// Jet<T, N>: value and its derivatives along N directions; evaluating a flux on
+// Jets seeded with unit directions gives N columns of its exact Jacobian.
+template <class T, int N>
+struct Jet {
+  T v;
+  T d[N];
+};
+template <class T, int N> PCEXP_DEV T val(const Jet<T, N>& x) { return x.v; }
+#define PCEXP_JET_BIN(OP, DEXPR)                                                        \
+  template <class T, int N>                                                             \
+  PCEXP_DEV Jet<T, N> operator OP(const Jet<T, N>& a, const Jet<T, N>& b) {             \
+    Jet<T, N> r;                                                                        \
+    r.v = a.v OP b.v;                                                                   \
+    _Pragma("unroll") for (int k = 0; k < N; ++k) r.d[k] = DEXPR;                       \
+    return r;                                                                           \
+  }
+PCEXP_JET_BIN(+, a.d[k] + b.d[k])
+PCEXP_JET_BIN(-, a.d[k] - b.d[k])
+PCEXP_JET_BIN(*, a.d[k] * b.v + a.v * b.d[k])
+#undef PCEXP_JET_BIN
+template <class T, int N> PCEXP_DEV Jet<T, N> operator/(const Jet<T, N>& a, const Jet<T, N>& b) {
+  Jet<T, N> r;
+  r.v = a.v / b.v;
+  const T ib = T(1) / b.v;
+#pragma unroll
+  for (int k = 0; k < N; ++k) r.d[k] = (a.d[k] - r.v * b.d[k]) * ib;
+  return r;
+}
+template <class T, int N> PCEXP_DEV Jet<T, N> operator-(const Jet<T, N>& a) {
+  Jet<T, N> r;
+  r.v = -a.v;
+#pragma unroll
+  for (int k = 0; k < N; ++k) r.d[k] = -a.d[k];
+  return r;
+}
+template <class T, int N> PCEXP_DEV Jet<T, N> operator+(const Jet<T, N>& a, T b) { Jet<T, N> r = a; r.v += b; return r; }
+template <class T, int N> PCEXP_DEV Jet<T, N> operator+(T a, const Jet<T, N>& b) { Jet<T, N> r = b; r.v += a; return r; }
+template <class T, int N> PCEXP_DEV Jet<T, N> operator-(const Jet<T, N>& a, T b) { Jet<T, N> r = a; r.v -= b; return r; }
+template <class T, int N> PCEXP_DEV Jet<T, N> operator-(T a, const Jet<T, N>& b) {
+  Jet<T, N> r;
+  r.v = a - b.v;
+#pragma unroll
+  for (int k = 0; k < N; ++k) r.d[k] = -b.d[k];
+  return r;
+}
+template <class T, int N> PCEXP_DEV Jet<T, N> operator*(const Jet<T, N>& a, T b) {
+  Jet<T, N> r;
+  r.v = a.v * b;
+#pragma unroll
+  for (int k = 0; k < N; ++k) r.d[k] = a.d[k] * b;
+  return r;
+}
+template <class T, int N> PCEXP_DEV Jet<T, N> operator*(T a, const Jet<T, N>& b) { return b * a; }
+template <class T, int N> PCEXP_DEV Jet<T, N> operator/(const Jet<T, N>& a, T b) { return a * (T(1) / b); }
+template <class T, int N> PCEXP_DEV Jet<T, N> operator/(T a, const Jet<T, N>& b) {
+  Jet<T, N> r;
+  r.v = a / b.v;
+  const T f = -r.v / b.v;
+#pragma unroll
+  for (int k = 0; k < N; ++k) r.d[k] = f * b.d[k];
+  return r;
+}
+template <class T, int N> PCEXP_DEV Jet<T, N> sqrt_s(const Jet<T, N>& x) {
+  Jet<T, N> r;
+  r.v = sqrt_s(x.v);
+  const T f = T(0.5) / r.v;
+#pragma unroll
+  for (int k = 0; k < N; ++k) r.d[k] = f * x.d[k];
+  return r;
+}
+template <class T, int N> PCEXP_DEV Jet<T, N> abs_s(const Jet<T, N>& x) {
+  const T sg = x.v > T(0) ? T(1) : (x.v < T(0) ? T(-1) : T(0));
+  Jet<T, N> r;
+  r.v = sg * x.v;
+#pragma unroll
+  for (int k = 0; k < N; ++k) r.d[k] = sg * x.d[k];
+  return r;
+}
+template <class T, int N> PCEXP_DEV Jet<T, N> pow_s(const Jet<T, N>& x, T e) {
+  Jet<T, N> r;
+  r.v = pow_s(x.v, e);
+  const T f = e * r.v / x.v;
+#pragma unroll
+  for (int k = 0; k < N; ++k) r.d[k] = f * x.d[k];
+  return r;
+}
+template <class S, class T> struct Lift {
+  PCEXP_DEV static S of(T x) { return S(x); }
+};
+template <class T> struct Lift<Tangent<T>, T> {
+  PCEXP_DEV static Tangent<T> of(T x) { return {x, T(0)}; }
+};
+template <class T, int N> struct Lift<Jet<T, N>, T> {
+  PCEXP_DEV static Jet<T, N> of(T x) {
+    Jet<T, N> r;
+    r.v = x;
+#pragma unroll
+    for (int k = 0; k < N; ++k) r.d[k] = T(0);
+    return r;
+  }
+};
 
 // ---------------------------------------------------------------- free stream
 template <class T>
@@ -158,16 +258,16 @@ PCEXP_DEV void ghost_farfield(const S U[4], T nx, T ny, const Free<T>& fs, S G[4
   T cinf = sqrt_s(g * fs.p / fs.rho);
   T qinf = fs.u * nx + fs.v * ny;
   T mn = val(qn) / val(c);
-  S rp = select_s(mn > T(-1), qn + T(2) * c / gm, lift_s<S, T>(qinf + T(2) * cinf / gm));
-  S rm = select_s(mn < T(1), lift_s<S, T>(qinf - T(2) * cinf / gm), qn - T(2) * c / gm);
+  S rp = select_s(mn > T(-1), qn + T(2) * c / gm, Lift<S, T>::of(qinf + T(2) * cinf / gm));
+  S rm = select_s(mn < T(1), Lift<S, T>::of(qinf - T(2) * cinf / gm), qn - T(2) * c / gm);
   S qb = T(0.5) * (rp + rm);
   S cb = T(0.25) * gm * (rp - rm);
   bool out = val(qb) >= T(0);
   S s_in = p / pow_s(U[0], g);
   T s_inf = fs.p / pow_s(fs.rho, g);
-  S sb = select_s(out, s_in, lift_s<S, T>(s_inf));
-  S ut = select_s(out, u - qn * nx, lift_s<S, T>(fs.u - qinf * nx));
-  S vt = select_s(out, v - qn * ny, lift_s<S, T>(fs.v - qinf * ny));
+  S sb = select_s(out, s_in, Lift<S, T>::of(s_inf));
+  S ut = select_s(out, u - qn * nx, Lift<S, T>::of(fs.u - qinf * nx));
+  S vt = select_s(out, v - qn * ny, Lift<S, T>::of(fs.v - qinf * ny));
   S ub = ut + qb * nx, vb = vt + qb * ny;
   S rb = pow_s(cb * cb / (g * sb), T(1) / gm);
   S pb = rb * cb * cb / g;
