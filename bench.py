@@ -144,6 +144,56 @@ def algorithmic_bytes(kind, T, K, E, F, nfq, m):
     }.get(kind)
 
 
+FP64_PEAK_TFLOPS = 152 * 2 * 2 * 2.070e9 / 1e12  # SMs x DFMA/clk/SM x 2 flops x max SM clock
+
+
+def algorithmic_flops(kind, K, E, F, P, m):
+    """Floating-point operations per launch of a kernel class (an FMA counts 2).
+
+    jvp_elem: per element, nq points x (trace 4 nb + Jacobian 32) FMA and 4 nb outputs x
+    (volume 2 nq + lift 3 nfq) FMA; jvp_face: per face point 2 x 4 nb trace + 32 FMA;
+    CGS kernels: per unknown and column, 1 (projection) or 2 (update + projection) FMA,
+    averaged over the columns of one Arnoldi process."""
+    nb, nq, nfq = (P + 1) * (P + 2) // 2, (P + 1) ** 2, P + 1
+    nc = (m + 1) / 2.0  # mean number of basis columns per launch
+    fma = {
+        "jvp_elem": E * (nq * (4 * nb + 32) + 4 * nb * (2 * nq + 3 * nfq)),
+        "jvp_face": F * nfq * (8 * nb + 32),
+        "cgs_proj": K * (nc + 1),
+        "cgs_upd_proj": K * 2 * nc,
+        "cgs_upd_norm": K * (nc + 1),
+    }.get(kind)
+    return None if fma is None else 2.0 * fma
+
+
+def roofline_entry(prof, precision_bytes, K, E, F, hbm, peak_kind):
+    """Roofline of the dominant kernel class: FP64 kernels are bound by the FP64 pipe
+    (alu, TFLOP/s), FP32 kernels by HBM (GB/s)."""
+    dom = max(prof, key=lambda k: prof[k][1])
+    n_dom, ms_dom = prof[dom]
+    if not n_dom:
+        return None
+    sec = ms_dom / n_dom / 1e3
+    entry = {"kernel": dom, "avg_launch_us": round(sec * 1e6, 2),
+             "time_share": round(ms_dom / sum(v[1] for v in prof.values()), 4), "traffic": None}
+    ab = algorithmic_bytes(dom, precision_bytes, K, E, F, P + 1, M)
+    if ab is not None:
+        entry["algorithmic_bytes_per_launch"] = ab
+    fl = algorithmic_flops(dom, K, E, F, P, M)
+    if precision_bytes == 8 and fl is not None:
+        ach = fl / sec / 1e12
+        entry.update({"bound": "alu", "achieved": round(ach, 3), "peak": round(FP64_PEAK_TFLOPS, 3),
+                      "unit": "TFLOP/s", "frac": round(ach / FP64_PEAK_TFLOPS, 4),
+                      "peak_source": "derived: 152 SMs x 2 DFMA/clk x 2 x 2.07 GHz",
+                      "algorithmic_flops_per_launch": fl,
+                      "hbm_frac": round(ab / sec / 1e9 / hbm, 4) if ab else None})
+    elif ab is not None:
+        ach = ab / sec / 1e9
+        entry.update({"bound": "hbm", "achieved": round(ach, 1), "peak": hbm, "unit": "GB/s",
+                      "frac": round(ach / hbm, 4), "peak_source": peak_kind})
+    return entry
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -273,21 +323,13 @@ def main():
 
     # roofline of the dominant kernel class (by device time in the timed region)
     hbm, peak_kind = load_peaks()
-    E, F, nfq = case.mesh.n_elem, None, P + 1
-    from paper_1801_06300_gb300.capi import KERNEL_CLASSES  # noqa: F401
-    nfaces = (3 * E + len(case.mesh.btags)) // 2
-    F = nfaces
+    E, nfq = case.mesh.n_elem, P + 1
+    F = (3 * E + len(case.mesh.btags)) // 2
     launches = sum(v[0] for v in prof.values())
-    dom = max(prof, key=lambda k: prof[k][1])
-    n_dom, ms_dom = prof[dom]
-    ab = algorithmic_bytes(dom, 8 if args.precision == "fp64" else 4, K, E, F, nfq, M)
-    roof = None
-    if ab is not None and n_dom:
-        achieved = ab / (ms_dom / n_dom / 1e3) / 1e9
-        roof = {"kernel": dom, "bound": "hbm", "achieved": round(achieved, 1), "peak": hbm, "unit": "GB/s",
-                "frac": round(achieved / hbm, 4), "peak_source": peak_kind, "traffic": None,
-                "algorithmic_bytes_per_launch": ab, "avg_launch_us": round(ms_dom / n_dom * 1e3, 2),
-                "time_share": round(ms_dom / sum(v[1] for v in prof.values()), 4)}
+    Tb = 8 if args.precision == "fp64" else 4
+    roof = roofline_entry(prof, Tb, K, E, F, hbm, peak_kind)
+    if mixed is not None:
+        mixed["roofline"] = roofline_entry(prof32, 4, K, E, F, hbm, peak_kind)
 
     cpu = None
     if rank == 0 and world == 1 and not args.no_cpu_baseline:

@@ -6,6 +6,7 @@
 // kernels after a happy breakdown exit at once.  Only pcexp_step with a
 // non-NULL info, the steady march (one 8-byte residual read per iteration)
 // and host-pointer transfers synchronise.
+#include <algorithm>
 #include <cmath>
 #include <cstdio>
 #include <cstring>
@@ -43,6 +44,15 @@ struct pcexp_ctx {
   double* partials = nullptr;
   int cur = 0;
   std::vector<void*> allocs;
+  // CUDA graphs of whole steps, keyed by (scheme, dt mode, m, state slot)
+  struct StepGraph {
+    int scheme, dt_mode, m, cur, cur_after;
+    cudaGraphExec_t exec;
+  };
+  std::vector<StepGraph> graphs;
+  std::vector<int> seen_keys;
+  double* param = nullptr;  // dt or CFL of the step being replayed (device)
+  cudaStream_t cap_st = nullptr;  // private stream for capture (the caller's may be the legacy stream)
   // kernel-class timing
   bool prof = false;
   std::vector<cudaEvent_t> ev_pool;
@@ -325,20 +335,20 @@ int krylov_stages(pcexp_ctx* c, int scheme, const T* escale, int m) {
   return PCEXP_OK;
 }
 
+// The launch sequence of one step; reads dt (or the CFL number) from c->param so
+// that it can be captured once into a CUDA graph and replayed.
 template <class T>
-int step_impl(pcexp_ctx* c, int scheme, int dt_mode, double dt_or_cfl, int m, pcexp_step_info* info) {
+int enqueue_step(pcexp_ctx* c, int scheme, int dt_mode, int m) {
   const DGData<T> d = dgdata<T>(c);
   T* S0 = shadow<T>(c, c->cur);
   T* V = reinterpret_cast<T*>(c->V);
-  T* G = reinterpret_cast<T*>(c->G);
   T* dte = reinterpret_cast<T*>(c->dte);
   const T* escale = nullptr;
   PCEXP_CK(cudaMemsetAsync(&c->ss->err, 0, sizeof(int), c->st));
-  (void)G;
   if (dt_mode == PCEXP_DT_GIVEN) {
-    PCEXP_LAUNCH(c, PCEXP_KC_OTHER, launch_set_dt(c->ss, dt_or_cfl, c->st));
+    PCEXP_LAUNCH(c, PCEXP_KC_OTHER, launch_copy_dt(c->ss, c->param, c->st));
   } else {
-    PCEXP_LAUNCH(c, PCEXP_KC_DT, launch_local_dt<T>(d, S0, nullptr, dt_or_cfl, dte, &c->ss->dt, c->partials, &c->ss->counter, c->st));
+    PCEXP_LAUNCH(c, PCEXP_KC_DT, launch_local_dt<T>(d, S0, c->param, 0.0, dte, &c->ss->dt, c->partials, &c->ss->counter, c->st));
     if (dt_mode == PCEXP_DT_LOCAL_CFL) {
       escale = dte;
       PCEXP_LAUNCH(c, PCEXP_KC_OTHER, launch_set_dt(c->ss, 1.0, c->st));
@@ -347,7 +357,61 @@ int step_impl(pcexp_ctx* c, int scheme, int dt_mode, double dt_or_cfl, int m, pc
   PCEXP_TRY(dg_apply<T>(c, d, S0, nullptr, V, nullptr, nullptr));
   PCEXP_LAUNCH(c, PCEXP_KC_OTHER, launch_density_norm<T>(V, nullptr, c->E, c->nb, c->nv, c->volume, c->ss, c->partials, 0, c->p, 0.0, c->st));
   if (escale) PCEXP_LAUNCH(c, PCEXP_KC_OTHER, launch_scale_elements<T>(V, escale, c->E, c->nv * c->nb, c->st));
-  PCEXP_TRY(krylov_stages<T>(c, scheme, escale, m));
+  return krylov_stages<T>(c, scheme, escale, m);
+}
+
+template <class T>
+int step_impl(pcexp_ctx* c, int scheme, int dt_mode, double dt_or_cfl, int m, pcexp_step_info* info) {
+  PCEXP_CK(launch_set_param(c->param, dt_or_cfl, c->st));
+  if (c->prof) {
+    PCEXP_TRY(enqueue_step<T>(c, scheme, dt_mode, m));
+  } else {
+    // the first step of a configuration runs eagerly (it also initialises lazily
+    // cached launch parameters); the second is captured into a graph, later ones replay it
+    const int key = ((scheme * 4 + dt_mode) * 64 + m) * 2 + c->cur;
+    pcexp_ctx::StepGraph* g = nullptr;
+    for (auto& e : c->graphs)
+      if (e.scheme == scheme && e.dt_mode == dt_mode && e.m == m && e.cur == c->cur) g = &e;
+    if (g) {
+      PCEXP_CK(cudaGraphLaunch(g->exec, c->st));
+      c->cur = g->cur_after;
+    } else if (std::find(c->seen_keys.begin(), c->seen_keys.end(), key) == c->seen_keys.end()) {
+      c->seen_keys.push_back(key);
+      PCEXP_TRY(enqueue_step<T>(c, scheme, dt_mode, m));
+    } else {
+      const int cur0 = c->cur;
+      if (!c->cap_st) PCEXP_CK(cudaStreamCreateWithFlags(&c->cap_st, cudaStreamNonBlocking));
+      // capture on the private stream (nothing runs during capture), replay on the caller's
+      cudaStream_t user_st = c->st;
+      c->st = c->cap_st;
+      cudaError_t eb = cudaStreamBeginCapture(c->st, cudaStreamCaptureModeThreadLocal);
+      if (eb != cudaSuccess) {
+        c->st = user_st;
+        g_last_error = std::string("cudaStreamBeginCapture: ") + cudaGetErrorString(eb);
+        return PCEXP_ERR_CUDA;
+      }
+      const int r = enqueue_step<T>(c, scheme, dt_mode, m);
+      cudaGraph_t graph = nullptr;
+      const cudaError_t ee = cudaStreamEndCapture(c->st, &graph);
+      c->st = user_st;
+      if (r != PCEXP_OK || ee != cudaSuccess) {
+        if (graph) cudaGraphDestroy(graph);
+        c->cur = cur0;
+        g_last_error = "step capture failed: " + std::string(cudaGetErrorString(ee)) + "; " + g_last_error;
+        return r != PCEXP_OK ? r : PCEXP_ERR_CUDA;
+      }
+      cudaGraphExec_t exec = nullptr;
+      const cudaError_t ei = cudaGraphInstantiate(&exec, graph, 0);
+      cudaGraphDestroy(graph);
+      if (ei != cudaSuccess) {
+        c->cur = cur0;
+        g_last_error = std::string("cudaGraphInstantiate: ") + cudaGetErrorString(ei);
+        return PCEXP_ERR_CUDA;
+      }
+      c->graphs.push_back({scheme, dt_mode, m, cur0, c->cur, exec});
+      PCEXP_CK(cudaGraphLaunch(exec, c->st));
+    }
+  }
   if (info) {
     StepState h;
     PCEXP_CK(cudaMemcpyAsync(&h, c->ss, sizeof(h), cudaMemcpyDeviceToHost, c->st));
@@ -607,6 +671,7 @@ int create_impl(pcexp_ctx* c, const pcexp_mesh* mesh, int p, const pcexp_physics
   PCEXP_TRY(dalloc(c, &c->ks, 1));
   PCEXP_TRY(dalloc(c, &c->ss, 1));
   PCEXP_TRY(dalloc(c, &c->partials, (size_t)RED_BLOCKS * (MMAX + 2)));
+  PCEXP_TRY(dalloc(c, &c->param, 1));
   (void)es;
   PCEXP_CK(cudaStreamSynchronize(c->st));
   // free-stream initial state
@@ -666,6 +731,8 @@ int pcexp_destroy(pcexp_ctx* c) {
   cudaStreamSynchronize(c->st);
   for (void* p : c->allocs) cudaFree(p);
   for (cudaEvent_t e : c->ev_pool) cudaEventDestroy(e);
+  for (auto& g : c->graphs) cudaGraphExecDestroy(g.exec);
+  if (c->cap_st) cudaStreamDestroy(c->cap_st);
   delete c;
   return PCEXP_OK;
 }

@@ -125,5 +125,7 @@ template <class Tin, class Tout>
 cudaError_t launch_cast(const Tin* x, Tout* y, int64_t n, cudaStream_t st);
 cudaError_t launch_reset_kstate(KState* ks, cudaStream_t st);
 cudaError_t launch_set_dt(StepState* ss, double dt, cudaStream_t st);
+cudaError_t launch_set_param(double* param, double v, cudaStream_t st);
+cudaError_t launch_copy_dt(StepState* ss, const double* param, cudaStream_t st);
 
 }  // namespace pcexp

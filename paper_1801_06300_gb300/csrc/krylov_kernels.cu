@@ -66,6 +66,7 @@ template <> struct Acc<double> {
   PCEXP_DEV void add(double x) { s += x; }
   PCEXP_DEV void add_acc(const Acc& o) { s += o.s; }
   PCEXP_DEV void add_partner(int o) { s += __shfl_xor_sync(0xffffffffu, s, o); }
+  PCEXP_DEV void shfl_from(const Acc& src, int o) { s = __shfl_xor_sync(0xffffffffu, src.s, o); }
   PCEXP_DEV double value() const { return s; }
 };
 template <> struct Acc<float> {
@@ -83,9 +84,12 @@ template <> struct Acc<float> {
   }
   PCEXP_DEV void add_partner(int o) {
     Acc p;
-    p.hi = __shfl_xor_sync(0xffffffffu, hi, o);
-    p.lo = __shfl_xor_sync(0xffffffffu, lo, o);
+    p.shfl_from(*this, o);
     add_acc(p);
+  }
+  PCEXP_DEV void shfl_from(const Acc& src, int o) {
+    hi = __shfl_xor_sync(0xffffffffu, src.hi, o);
+    lo = __shfl_xor_sync(0xffffffffu, src.lo, o);
   }
   PCEXP_DEV double value() const { return (double)hi + (double)lo; }
 };
@@ -155,6 +159,41 @@ PCEXP_DEV void cgs_finalize(int mode, int j, const double* dots, KState* ks, dou
   }
 }
 
+// Warp reduction of NC accumulators at once (NC a power of two <= 32): plain
+// butterfly levels until NC values remain per lane pair group, then transpose levels
+// in which each lane keeps half of its columns and receives the partner's other half.
+// Afterwards lane l holds the warp sum of column (l mod NC): NC - 1 + (5 - log2 NC) NC
+// additions per lane instead of 5 NC.  Fixed order, so deterministic.
+template <class T, int NC, int L, int O>
+PCEXP_DEV void transpose_level(Acc<T> (&a)[NC], int lane) {
+  if constexpr (L >= 2) {
+    const bool upper = (lane & O) != 0;
+#pragma unroll
+    for (int i = 0; i < L / 2; ++i) {
+      Acc<T> send = upper ? a[i] : a[i + L / 2];
+      Acc<T> keep = upper ? a[i + L / 2] : a[i];
+      Acc<T> recv;
+      recv.shfl_from(send, O);
+      keep.add_acc(recv);
+      a[i] = keep;
+    }
+    transpose_level<T, NC, L / 2, O / 2>(a, lane);
+  }
+}
+
+template <class T, int NC>
+PCEXP_DEV Acc<T> warp_reduce_columns(Acc<T> (&a)[NC], int lane) {
+  constexpr int LOGNC = NC >= 32 ? 5 : NC >= 16 ? 4 : NC >= 8 ? 3 : NC >= 4 ? 2 : NC >= 2 ? 1 : 0;
+  static_assert((1 << LOGNC) == NC, "NC must be a power of two <= 32");
+#pragma unroll
+  for (int o = 16; o >= NC; o >>= 1) {
+#pragma unroll
+    for (int c = 0; c < NC; ++c) a[c].add_partner(o);
+  }
+  transpose_level<T, NC, NC, NC / 2>(a, lane);
+  return a[0];
+}
+
 template <class T, int NC, int MODE>
 __global__ void __launch_bounds__(256) cgs_kernel(const T* __restrict__ Z, int64_t ldz, int64_t Kp, int j,
                                                   T* __restrict__ w, T* __restrict__ out, KState* ks,
@@ -217,10 +256,19 @@ __global__ void __launch_bounds__(256) cgs_kernel(const T* __restrict__ Z, int64
   }
   // block reduction in the accumulator type (fixed order): warp tree, then over warps
   const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5, nw = blockDim.x >> 5;
+  if constexpr (MODE == CGS_NORM || MODE == CGS_UPD_NORM) {
+    for (int o = 16; o > 0; o >>= 1) acc[0].add_partner(o);
+    if (lane == 0) red[wid][0] = acc[0];
+  } else {
+    Acc<T> cols[NC];
 #pragma unroll
-  for (int c = 0; c < NACC; ++c) {
-    for (int o = 16; o > 0; o >>= 1) acc[c].add_partner(o);
-    if (lane == 0) red[wid][c] = acc[c];
+    for (int c = 0; c < NC; ++c) cols[c] = acc[c];
+    const Acc<T> mine = warp_reduce_columns<T, NC>(cols, lane);
+    if (lane < NC) red[wid][lane] = mine;
+    if constexpr (MODE == CGS_PROJ) {
+      for (int o = 16; o > 0; o >>= 1) acc[NC].add_partner(o);
+      if (lane == 0) red[wid][NC] = acc[NC];
+    }
   }
   __syncthreads();
   const int nred = (MODE == CGS_PROJ) ? nc + 1 : (MODE == CGS_UPD_PROJ ? nc : 1);
@@ -645,6 +693,16 @@ cudaError_t launch_reset_kstate(KState* ks, cudaStream_t st) {
 }
 
 __global__ void set_dt_kernel(StepState* ss, double dt) { ss->dt = dt; }
+__global__ void set_param_kernel(double* p, double v) { *p = v; }
+__global__ void copy_dt_kernel(StepState* ss, const double* p) { ss->dt = *p; }
+cudaError_t launch_set_param(double* param, double v, cudaStream_t st) {
+  set_param_kernel<<<1, 1, 0, st>>>(param, v);
+  return cudaGetLastError();
+}
+cudaError_t launch_copy_dt(StepState* ss, const double* param, cudaStream_t st) {
+  copy_dt_kernel<<<1, 1, 0, st>>>(ss, param);
+  return cudaGetLastError();
+}
 cudaError_t launch_set_dt(StepState* ss, double dt, cudaStream_t st) {
   set_dt_kernel<<<1, 1, 0, st>>>(ss, dt);
   return cudaGetLastError();

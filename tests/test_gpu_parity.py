@@ -208,6 +208,32 @@ def test_steady_local_steps_bump(capi, scheme):
     ctx.close()
 
 
+@pytest.mark.parametrize("scheme,decades,max_iter", [("exp1", 12.0, 5), ("pcexp", 12.0, 3), ("exp1", 0.25, 40)])
+def test_steady_march_matches_oracle(capi, scheme, decades, max_iter):
+    """pcexp_march_steady (local steps, CFL ramp of Eq. cfl, CFL_max 20) against the
+    oracle march: iteration count, first and last density residual norms, final state."""
+    from oracle import pcexp
+    mesh, free = W.bump_channel(24, 8, 0.15, 1), W.Freestream(0.5, 0.0)
+    dg = oracle_dg(mesh, 1, free)
+    u0 = perturbed_state(dg, 0, amp=0.0)
+    vol = float(dg.area.sum())  # |Omega| of the discrete domain, as the library takes it
+    uo, hist = pcexp.steady_march(dg, u0, 20.0, decades, max_iter, 20, vol, scheme=scheme)
+    ro_last = dg.density_residual_norm(dg.residual(uo), vol)
+    ctx = capi.Context(mesh, 1, free, capi.PCEXP_FP64, m_max=20)
+    ctx.set_state(u0)
+    sc = capi.PCEXP_SCHEME_PCEXP if scheme == "pcexp" else capi.PCEXP_SCHEME_EXP1
+    info = ctx.march_steady(sc, 20.0, decades, max_iter, 20)
+    converged_oracle = hist[-1] <= hist[0] * 10.0 ** (-decades)
+    steps_oracle = len(hist) - 1 if converged_oracle else len(hist)
+    assert info["converged"] == converged_oracle
+    assert info["iterations"] == steps_oracle
+    assert abs(info["res_first"] - hist[0]) <= 1e-12 * hist[0]
+    last = hist[-1] if converged_oracle else ro_last
+    assert abs(info["res_last"] - last) <= 1e-8 * last
+    assert rel(ctx.get_state(), uo) <= 1e-9
+    ctx.close()
+
+
 def test_freestream_step_is_identity(capi):
     """R(u_inf) = 0 on a periodic mesh: beta = 0 and the step leaves u unchanged."""
     mesh, free = MESHES["periodic"]()
