@@ -45,7 +45,7 @@ extern "C" {
 #define PCEXP_ERR_CUDA (-3)        /* a CUDA runtime call failed */
 #define PCEXP_ERR_OOM (-4)         /* device allocation failed */
 #define PCEXP_ERR_NONFINITE (-5)   /* a norm, beta or h_{j+1,j} was NaN/Inf */
-#define PCEXP_ERR_TIMEOUT (-6)     /* reserved for bounded device waits */
+#define PCEXP_ERR_TIMEOUT (-6)     /* reserved for bounded device waits (none in this build) */
 #define PCEXP_ERR_UNSUPPORTED (-7) /* valid request this build does not cover */
 
 /* ---- boundary tags (Sec. 4.4, Sec. 5.2) ---- */

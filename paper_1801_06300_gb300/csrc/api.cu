@@ -422,6 +422,10 @@ int step_impl(pcexp_ctx* c, int scheme, int dt_mode, double dt_or_cfl, int m, pc
     info->beta[1] = scheme == PCEXP_SCHEME_EXP1 ? 0.0 : h.beta[1];
     info->dt = h.dt;
     info->res_norm = h.res_norm;
+    if (h.err == 2) {
+      g_last_error = "a bounded device wait ran out (bulk copy not completed)";
+      return PCEXP_ERR_TIMEOUT;
+    }
     if (h.err) {
       g_last_error = "non-finite norm, beta or Hessenberg entry";
       return PCEXP_ERR_NONFINITE;
@@ -490,6 +494,10 @@ int arnoldi_abi(pcexp_ctx* c, const double* U, const double* b, int m, double* V
   KState hk;
   PCEXP_CK(cudaMemcpyAsync(&hk, c->ks, sizeof(hk), cudaMemcpyDeviceToHost, c->st));
   PCEXP_CK(cudaStreamSynchronize(c->st));
+  if (hk.err == 2) {
+    g_last_error = "a bounded device wait ran out (bulk copy not completed)";
+    return PCEXP_ERR_TIMEOUT;
+  }
   if (hk.err) {
     g_last_error = "non-finite Arnoldi quantity";
     return PCEXP_ERR_NONFINITE;

@@ -418,7 +418,7 @@ __global__ void __cluster_dims__(PHI_CTAS, 1, 1) __launch_bounds__(256)
       if (ss) {
         ss->k[stage] = 0;
         ss->beta[stage] = ks->beta;
-        if (ks->err) ss->err = 1;
+        if (ks->err) ss->err = ks->err;
       }
     }
     return;
