@@ -155,6 +155,16 @@ int pcexp_residual(pcexp_ctx* ctx, const double* U, double* R, int on_device);
  * matrix-free by a tangent-linear kernel. */
 int pcexp_jvp(pcexp_ctx* ctx, const double* U, const double* v, double* Jv, int on_device);
 
+/* J(U)^T w, the adjoint of pcexp_jvp (transpose of the exact Jacobian of
+ * Eq. jac1, jac2), from the same point Jacobians, in the same basis as U. */
+int pcexp_vjp(pcexp_ctx* ctx, const double* U, const double* w, double* JTw, int on_device);
+
+/* (d/dU [w^T J(U) v])^T: the adjoint, with respect to the linearisation state U,
+ * of the Jacobian-vector product (second derivatives of R; J_n = J(u_n) depends
+ * on u_n, Eq. s9/s10).  FP64 contexts only (PCEXP_ERR_UNSUPPORTED otherwise). */
+int pcexp_jvp_state_adjoint(pcexp_ctx* ctx, const double* U, const double* v, const double* w,
+                            double* out, int on_device);
+
 /* Time-step sizes of Eq. x3d at the master state: local != 0 writes n_elem
  * values dt_e, otherwise one value min_e dt_e. */
 int pcexp_compute_dt(pcexp_ctx* ctx, double cfl, int local, double* dt, int on_device);

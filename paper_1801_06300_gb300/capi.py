@@ -80,6 +80,8 @@ SIGNATURES = {
     "pcexp_project_state": (C.c_int, [_P, C.c_int, _D, C.c_int]),
     "pcexp_residual": (C.c_int, [_P, _P, _P, C.c_int]),
     "pcexp_jvp": (C.c_int, [_P, _P, _P, _P, C.c_int]),
+    "pcexp_vjp": (C.c_int, [_P, _P, _P, _P, C.c_int]),
+    "pcexp_jvp_state_adjoint": (C.c_int, [_P, _P, _P, _P, _P, C.c_int]),
     "pcexp_compute_dt": (C.c_int, [_P, C.c_double, C.c_int, _P, C.c_int]),
     "pcexp_arnoldi": (C.c_int, [_P, _P, _P, C.c_int, _P, _D, C.POINTER(C.c_int), _D, C.c_int]),
     "pcexp_phi": (C.c_int, [_P, _D, C.c_int, C.c_int, C.c_double, _D, _D]),
@@ -211,6 +213,23 @@ class Context:
         pv, _ = _ptr(v)
         po, _ = _ptr(out)
         check(self.lib.pcexp_jvp(self.ctx, pu, pv, po, dev), "pcexp_jvp")
+        return out
+
+    def vjp(self, U, w, out=None):
+        out = (np.empty(self.K) if isinstance(U, np.ndarray) else U.new_empty(self.K)) if out is None else out
+        pu, dev = _ptr(U)
+        pw, _ = _ptr(w)
+        po, _ = _ptr(out)
+        check(self.lib.pcexp_vjp(self.ctx, pu, pw, po, dev), "pcexp_vjp")
+        return out
+
+    def jvp_state_adjoint(self, U, v, w, out=None):
+        out = (np.empty(self.K) if isinstance(U, np.ndarray) else U.new_empty(self.K)) if out is None else out
+        pu, dev = _ptr(U)
+        pv, _ = _ptr(v)
+        pw, _ = _ptr(w)
+        po, _ = _ptr(out)
+        check(self.lib.pcexp_jvp_state_adjoint(self.ctx, pu, pv, pw, po, dev), "pcexp_jvp_state_adjoint")
         return out
 
     def residual_noalloc(self, U, out):

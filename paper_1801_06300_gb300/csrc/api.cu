@@ -39,6 +39,7 @@ struct pcexp_ctx {
   void *V = nullptr, *w = nullptr, *tmp = nullptr, *delta = nullptr, *G = nullptr, *dte = nullptr;
   double *io64a = nullptr, *io64b = nullptr;
   void *Avol = nullptr, *Bface = nullptr;  // point Jacobians at the linearisation state
+  void* GT = nullptr;                      // adjoint face scratch [F][nfq][8]
   KState* ks = nullptr;
   StepState* ss = nullptr;
   double* partials = nullptr;
@@ -586,6 +587,11 @@ int project_host(pcexp_ctx* c, int kind, const double* prm, int np, std::vector<
   return PCEXP_OK;
 }
 
+int UNSUPPORTED_FP32_HESS(pcexp_ctx*) {
+  g_last_error = "the second-order adjoint is provided for the FP64 form";
+  return PCEXP_ERR_UNSUPPORTED;
+}
+
 int check_ctx(const pcexp_ctx* c) {
   if (!c) {
     g_last_error = "null context";
@@ -673,6 +679,7 @@ int create_impl(pcexp_ctx* c, const pcexp_mesh* mesh, int p, const pcexp_physics
   PCEXP_TRY(valloc(&c->G, (size_t)(c->F > 0 ? c->F : 1) * c->nfq * 4));
   PCEXP_TRY(valloc(&c->dte, c->E));
   PCEXP_TRY(valloc(&c->Avol, (size_t)32 * c->E * c->nq));
+  PCEXP_TRY(valloc(&c->GT, (size_t)8 * (c->F > 0 ? c->F : 1) * c->nfq));
   PCEXP_TRY(valloc(&c->Bface, (size_t)32 * (c->F > 0 ? c->F : 1) * c->nfq));
   PCEXP_TRY(dalloc(c, &c->io64a, Kp));
   PCEXP_TRY(dalloc(c, &c->io64b, Kp));
@@ -688,6 +695,21 @@ int create_impl(pcexp_ctx* c, const pcexp_mesh* mesh, int p, const pcexp_physics
   PCEXP_CK(cudaMemcpyAsync(c->U64[0], u.data(), u.size() * 8, cudaMemcpyHostToDevice, c->st));
   PCEXP_TRY(refresh_shadow<double>(c, 0));
   PCEXP_CK(cudaStreamSynchronize(c->st));
+  return PCEXP_OK;
+}
+
+template <class T>
+int vjp_impl(pcexp_ctx* c, const double* U, const double* w, double* JTw, int on_device) {
+  T* a = reinterpret_cast<T*>(c->tmp);
+  T* b = reinterpret_cast<T*>(c->delta);
+  T* o = reinterpret_cast<T*>(c->w);
+  const DGData<T> d = dgdata<T>(c);
+  PCEXP_TRY(import_vec<T>(c, U, on_device, a));
+  PCEXP_TRY(import_vec<T>(c, w, on_device, b));
+  PCEXP_TRY(linearize<T>(c, d, a));
+  PCEXP_CK(launch_jac_adjoint<T>(d, lindata<T>(c), b, o, reinterpret_cast<T*>(c->GT), nullptr, T(1), c->st));
+  PCEXP_TRY(export_vec<T>(c, o, JTw, on_device));
+  if (on_device) PCEXP_CK(cudaStreamSynchronize(c->st));
   return PCEXP_OK;
 }
 
@@ -822,6 +844,32 @@ int pcexp_jvp(pcexp_ctx* c, const double* U, const double* v, double* Jv, int on
   }
   if (on_device) PCEXP_CK(cudaStreamSynchronize(c->st));
   return PCEXP_OK;
+}
+
+int pcexp_jvp_state_adjoint(pcexp_ctx* c, const double* U, const double* v, const double* w, double* out,
+                            int on_device) {
+  PCEXP_TRY(check_ctx(c));
+  if (!U || !v || !w || !out) return PCEXP_ERR_INVALID_ARG;
+  if (c->fp32) return UNSUPPORTED_FP32_HESS(c);
+  double* a = reinterpret_cast<double*>(c->tmp);
+  double* b = reinterpret_cast<double*>(c->delta);
+  double* ww = reinterpret_cast<double*>(c->V);  // V[0] as scratch
+  double* o = reinterpret_cast<double*>(c->w);
+  PCEXP_TRY(import_vec<double>(c, U, on_device, a));
+  PCEXP_TRY(import_vec<double>(c, v, on_device, b));
+  PCEXP_TRY(import_vec<double>(c, w, on_device, ww));
+  PCEXP_CK(launch_jvp_state_adjoint<double>(dgdata<double>(c), a, b, ww, o, reinterpret_cast<double*>(c->GT), nullptr,
+                                            1.0, c->st));
+  PCEXP_TRY(export_vec<double>(c, o, out, on_device));
+  if (on_device) PCEXP_CK(cudaStreamSynchronize(c->st));
+  return PCEXP_OK;
+}
+
+int pcexp_vjp(pcexp_ctx* c, const double* U, const double* w, double* JTw, int on_device) {
+  PCEXP_TRY(check_ctx(c));
+  if (!U || !w || !JTw) return PCEXP_ERR_INVALID_ARG;
+  if (c->fp32) return vjp_impl<float>(c, U, w, JTw, on_device);
+  return vjp_impl<double>(c, U, w, JTw, on_device);
 }
 
 int pcexp_compute_dt(pcexp_ctx* c, double cfl, int local, double* dt, int on_device) {

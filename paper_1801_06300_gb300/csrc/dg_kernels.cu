@@ -516,6 +516,389 @@ cudaError_t launch_jac_apply(const DGData<T>& d, LinData<T> lin, const T* dv, T*
   return cudaErrorInvalidValue;
 }
 
+// ------------------------------------------------------------- adjoint J^T w
+// Transpose of the point-Jacobian J v (same linearisation state).  With the output
+// factors of J v folded into w (w~ = osc * escale_e * w), the face kernel forms the
+// adjoint of the lifted face flux at every face point,
+//   Gbar = -(1/sd_L) sum_i Bf_L[i] w~_L[i] + (1/sd_R) sum_i Bf_R[i] w~_R[i],
+// and stores B_L^T Gbar and B_R^T Gbar; the element kernel applies the transposed
+// volume Jacobians to the transposed test of w~ and gathers the transposed traces
+// of its three faces.  Deterministic (no atomics).
+template <class T, int P>
+__global__ void __launch_bounds__(256) face_adjoint_kernel(DGData<T> d, const T* __restrict__ Bface,
+                                                           const T* __restrict__ w, T* __restrict__ GT,
+                                                           const T* __restrict__ escale, T osc) {
+  using O = Ord<P>;
+  constexpr int NB = O::NB, NFQ = O::NFQ;
+  __shared__ T sBf[3 * NFQ * NB];
+  for (int i = threadIdx.x; i < 3 * NFQ * NB; i += blockDim.x) sBf[i] = d.Bf[i];
+  __syncthreads();
+  const int64_t n = d.F * NFQ;
+  const int64_t idx = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (idx >= n) return;
+  const int64_t f = idx / NFQ;
+  const int q = (int)(idx - f * NFQ);
+  const int eL = d.fel[2 * f], eR = d.fel[2 * f + 1];
+  const int loc = d.floc[f];
+  const int fL = loc & 0xff, fR = loc >> 8;
+  T gb[4];
+  {
+    const T sc = -osc * (escale ? escale[eL] : T(1)) / d.geo[8 * (int64_t)eL + 4];
+#pragma unroll
+    for (int v = 0; v < 4; ++v) {
+      T a = 0;
+#pragma unroll
+      for (int i = 0; i < NB; ++i) a += sBf[(fL * NFQ + q) * NB + i] * w[(int64_t)eL * 4 * NB + v * NB + i];
+      gb[v] = sc * a;
+    }
+  }
+  if (eR >= 0) {
+    const T sc = osc * (escale ? escale[eR] : T(1)) / d.geo[8 * (int64_t)eR + 4];
+#pragma unroll
+    for (int v = 0; v < 4; ++v) {
+      T a = 0;
+#pragma unroll
+      for (int i = 0; i < NB; ++i)
+        a += sBf[(fR * NFQ + (NFQ - 1 - q)) * NB + i] * w[(int64_t)eR * 4 * NB + v * NB + i];
+      gb[v] += sc * a;
+    }
+  }
+  T* o = GT + idx * 8;
+#pragma unroll
+  for (int side = 0; side < 2; ++side)
+#pragma unroll
+    for (int c = 0; c < 4; ++c) {
+      T a = 0;
+      if (side == 0 || eR >= 0) {
+#pragma unroll
+        for (int v = 0; v < 4; ++v) a += Bface[(int64_t)(side * 16 + v * 4 + c) * n + idx] * gb[v];
+      }
+      o[side * 4 + c] = a;
+    }
+}
+
+template <class T, int P>
+__global__ void __launch_bounds__(256) elem_adjoint_kernel(DGData<T> d, const T* __restrict__ Avol,
+                                                           const T* __restrict__ w, const T* __restrict__ GT,
+                                                           T* __restrict__ out, const T* __restrict__ escale,
+                                                           T osc) {
+  using O = Ord<P>;
+  constexpr int NB = O::NB, NQ = O::NQ, NFQ = O::NFQ, ET = O::ET, NVB = 4 * NB;
+  __shared__ T sBv[NQ * NB];
+  __shared__ T sDv[2 * NQ * NB];
+  __shared__ T sBf[3 * NFQ * NB];
+  __shared__ T sw[ET * NVB];
+  __shared__ T sU[ET * NQ * 4];
+  static_assert(ET * NQ <= 256, "one volume point per thread");
+  const int64_t e0 = (int64_t)blockIdx.x * ET;
+  const int ne = (int)((d.E - e0) < ET ? (d.E - e0) : ET);
+  const int64_t n = d.E * NQ;
+  for (int i = threadIdx.x; i < NQ * NB; i += blockDim.x) sBv[i] = d.Bv[i];
+  for (int i = threadIdx.x; i < 2 * NQ * NB; i += blockDim.x) sDv[i] = d.Dv[i];
+  for (int i = threadIdx.x; i < 3 * NFQ * NB; i += blockDim.x) sBf[i] = d.Bf[i];
+  for (int i = threadIdx.x; i < ne * NVB; i += blockDim.x)
+    sw[i] = w[e0 * NVB + i] * osc * (escale ? escale[e0 + i / NVB] : T(1));
+  __syncthreads();
+  // phase 1: transposed test, then transposed volume Jacobians, at this thread's point
+  const int el1 = threadIdx.x / NQ, q1 = threadIdx.x - (threadIdx.x / NQ) * NQ;
+  if (threadIdx.x < ne * NQ) {
+    const int64_t pidx = (e0 + el1) * NQ + q1;
+    T fb[8];
+#pragma unroll
+    for (int dd = 0; dd < 2; ++dd)
+#pragma unroll
+      for (int v = 0; v < 4; ++v) {
+        T a = 0;
+#pragma unroll
+        for (int i = 0; i < NB; ++i) a += sDv[(dd * NQ + q1) * NB + i] * sw[el1 * NVB + v * NB + i];
+        fb[dd * 4 + v] = a;
+      }
+#pragma unroll
+    for (int c = 0; c < 4; ++c) {
+      T a = 0;
+#pragma unroll
+      for (int dd = 0; dd < 2; ++dd)
+#pragma unroll
+        for (int v = 0; v < 4; ++v) a += Avol[(int64_t)(dd * 16 + v * 4 + c) * n + pidx] * fb[dd * 4 + v];
+      sU[(el1 * NQ + q1) * 4 + c] = a;
+    }
+  }
+  __syncthreads();
+  // phase 2: transposed volume traces plus the transposed face traces of the 3 faces
+  for (int it = threadIdx.x; it < ne * NVB; it += blockDim.x) {
+    const int el = it / NVB, r = it - el * NVB;
+    const int c = r / NB, j = r - c * NB;
+    T acc = 0;
+#pragma unroll
+    for (int q = 0; q < NQ; ++q) acc += sBv[q * NB + j] * sU[(el * NQ + q) * 4 + c];
+    const int64_t e = e0 + el;
+#pragma unroll
+    for (int k = 0; k < 3; ++k) {
+      const int fs = d.ef[3 * e + k];
+      const int64_t face = fs >> 1;
+      const int side = fs & 1;
+      const T* gt = GT + face * NFQ * 8 + side * 4 + c;
+#pragma unroll
+      for (int q = 0; q < NFQ; ++q) {
+        const int qq = side ? (NFQ - 1 - q) : q;
+        acc += sBf[(k * NFQ + qq) * NB + j] * gt[q * 8];
+      }
+    }
+    out[e0 * NVB + it] = acc;
+  }
+}
+
+template <class T, int P>
+static cudaError_t jac_adjoint_p(const DGData<T>& d, LinData<T> lin, const T* w, T* out, T* GT, const T* escale,
+                                 T osc, cudaStream_t st) {
+  using O = Ord<P>;
+  const int64_t nf = d.F * O::NFQ;
+  if (nf > 0) face_adjoint_kernel<T, P><<<(unsigned)((nf + 255) / 256), 256, 0, st>>>(d, lin.Bface, w, GT, escale, osc);
+  const int64_t eb = (d.E + O::ET - 1) / O::ET;
+  elem_adjoint_kernel<T, P><<<(unsigned)eb, 256, 0, st>>>(d, lin.Avol, w, GT, out, escale, osc);
+  return cudaGetLastError();
+}
+
+template <class T>
+cudaError_t launch_jac_adjoint(const DGData<T>& d, LinData<T> lin, const T* w, T* out, T* GT, const T* escale, T osc,
+                               cudaStream_t st) {
+  switch (d.p) {
+    case 0: return jac_adjoint_p<T, 0>(d, lin, w, out, GT, escale, osc, st);
+    case 1: return jac_adjoint_p<T, 1>(d, lin, w, out, GT, escale, osc, st);
+    case 2: return jac_adjoint_p<T, 2>(d, lin, w, out, GT, escale, osc, st);
+    case 3: return jac_adjoint_p<T, 3>(d, lin, w, out, GT, escale, osc, st);
+  }
+  return cudaErrorInvalidValue;
+}
+
+// ------------------------------------------- second-order adjoint (d(J(u) v)/du)^T w
+// S(u) = w~^T J(u) v is differentiated with respect to the linearisation state u:
+// every flux is evaluated on hyper-dual numbers (value, 4 seeded partials, the
+// directional derivative along the traces of v, its 4 partials), contracted with the
+// transposed test (volume) or transposed lift (faces) of w~ and mapped back through the
+// transposed traces.  Same output factors and scratch layout as the adjoint kernels.
+template <class T, int P>
+__global__ void __launch_bounds__(128) face_hess_kernel(DGData<T> d, const T* __restrict__ u,
+                                                        const T* __restrict__ v, const T* __restrict__ w,
+                                                        T* __restrict__ GT, const T* __restrict__ escale, T osc) {
+  using O = Ord<P>;
+  constexpr int NB = O::NB, NFQ = O::NFQ;
+  using H = HD4<T>;
+  const int64_t n = d.F * NFQ;
+  const int64_t idx = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (idx >= n) return;
+  const int64_t f = idx / NFQ;
+  const int q = (int)(idx - f * NFQ);
+  const int eL = d.fel[2 * f], eR = d.fel[2 * f + 1];
+  const int loc = d.floc[f];
+  const int fL = loc & 0xff, fR = loc >> 8;
+  const T nx = d.fgeo[4 * f], ny = d.fgeo[4 * f + 1], len = d.fgeo[4 * f + 2];
+  const T wq = len * d.Wf[q];
+  const T sdL = d.geo[8 * (int64_t)eL + 4];
+  const T sdR = eR >= 0 ? d.geo[8 * (int64_t)eR + 4] : T(1);
+  const T* bL = d.Bf + (fL * NFQ + q) * NB;
+  const T* bR = d.Bf + (fR * NFQ + (NFQ - 1 - q)) * NB;
+  T uL[4], tL[4], uR[4], tR[4], gb[4];
+  const T scL = -osc * (escale ? escale[eL] : T(1)) / sdL;
+  const T scR = osc * (eR >= 0 && escale ? escale[eR] : T(1)) / sdR;
+#pragma unroll
+  for (int c = 0; c < 4; ++c) {
+    T a = 0, b = 0, g = 0;
+#pragma unroll
+    for (int j = 0; j < NB; ++j) {
+      const int64_t o = (int64_t)eL * 4 * NB + c * NB + j;
+      a += bL[j] * u[o];
+      b += bL[j] * v[o];
+      g += bL[j] * w[o];
+    }
+    uL[c] = a / sdL;
+    tL[c] = b / sdL;
+    gb[c] = scL * g;
+    uR[c] = tR[c] = T(0);
+  }
+  if (eR >= 0) {
+#pragma unroll
+    for (int c = 0; c < 4; ++c) {
+      T a = 0, b = 0, g = 0;
+#pragma unroll
+      for (int j = 0; j < NB; ++j) {
+        const int64_t o = (int64_t)eR * 4 * NB + c * NB + j;
+        a += bR[j] * u[o];
+        b += bR[j] * v[o];
+        g += bR[j] * w[o];
+      }
+      uR[c] = a / sdR;
+      tR[c] = b / sdR;
+      gb[c] += scR * g;
+    }
+  }
+  T* o = GT + idx * 8;
+#pragma unroll 1
+  for (int side = 0; side < 2; ++side) {
+    if (side == 1 && eR < 0) {
+#pragma unroll
+      for (int c = 0; c < 4; ++c) o[4 + c] = T(0);
+      break;
+    }
+    H L[4], R[4], F[4];
+#pragma unroll
+    for (int c = 0; c < 4; ++c) {
+      L[c].v = uL[c];
+      L[c].t = tL[c];
+#pragma unroll
+      for (int k = 0; k < 4; ++k) {
+        L[c].d[k] = (side == 0 && k == c) ? T(1) : T(0);
+        L[c].dt[k] = T(0);
+      }
+    }
+    if (eR >= 0) {
+#pragma unroll
+      for (int c = 0; c < 4; ++c) {
+        R[c].v = uR[c];
+        R[c].t = tR[c];
+#pragma unroll
+        for (int k = 0; k < 4; ++k) {
+          R[c].d[k] = (side == 1 && k == c) ? T(1) : T(0);
+          R[c].dt[k] = T(0);
+        }
+      }
+    } else if (-eR == PCEXP_BC_SLIP_WALL) {
+      ghost_slip_wall<H, T>(L, nx, ny, R);
+    } else {
+      ghost_farfield<H, T>(L, nx, ny, d.fs, R);
+    }
+    roe_flux<H, T>(L, R, nx, ny, d.fs.gamma, F);
+    const T sc = wq / (side == 0 ? sdL : sdR);
+#pragma unroll
+    for (int c = 0; c < 4; ++c) {
+      T a = 0;
+#pragma unroll
+      for (int vv = 0; vv < 4; ++vv) a += gb[vv] * F[vv].dt[c];
+      o[side * 4 + c] = sc * a;
+    }
+  }
+}
+
+template <class T, int P>
+__global__ void __launch_bounds__(256) elem_hess_kernel(DGData<T> d, const T* __restrict__ u, const T* __restrict__ v,
+                                                        const T* __restrict__ w, const T* __restrict__ GT,
+                                                        T* __restrict__ out, const T* __restrict__ escale, T osc) {
+  using O = Ord<P>;
+  constexpr int NB = O::NB, NQ = O::NQ, NFQ = O::NFQ, ET = O::ET, NVB = 4 * NB;
+  using H = HD4<T>;
+  __shared__ T sBv[NQ * NB];
+  __shared__ T sDv[2 * NQ * NB];
+  __shared__ T sBf[3 * NFQ * NB];
+  __shared__ T su[ET * NVB];
+  __shared__ T sv[ET * NVB];
+  __shared__ T sw[ET * NVB];
+  __shared__ T sU[ET * NQ * 4];
+  __shared__ T sgeo[ET * 8];
+  static_assert(ET * NQ <= 256, "one volume point per thread");
+  const int64_t e0 = (int64_t)blockIdx.x * ET;
+  const int ne = (int)((d.E - e0) < ET ? (d.E - e0) : ET);
+  for (int i = threadIdx.x; i < NQ * NB; i += blockDim.x) sBv[i] = d.Bv[i];
+  for (int i = threadIdx.x; i < 2 * NQ * NB; i += blockDim.x) sDv[i] = d.Dv[i];
+  for (int i = threadIdx.x; i < 3 * NFQ * NB; i += blockDim.x) sBf[i] = d.Bf[i];
+  for (int i = threadIdx.x; i < ne * NVB; i += blockDim.x) {
+    su[i] = u[e0 * NVB + i];
+    sv[i] = v[e0 * NVB + i];
+    sw[i] = w[e0 * NVB + i] * osc * (escale ? escale[e0 + i / NVB] : T(1));
+  }
+  for (int i = threadIdx.x; i < ne * 8; i += blockDim.x) sgeo[i] = d.geo[e0 * 8 + i];
+  __syncthreads();
+  const int el1 = threadIdx.x / NQ, q1 = threadIdx.x - (threadIdx.x / NQ) * NQ;
+  if (threadIdx.x < ne * NQ) {
+    const T* ge = sgeo + el1 * 8;
+    const T sd = ge[4];
+    H U[4];
+#pragma unroll
+    for (int c = 0; c < 4; ++c) {
+      T a = 0, b = 0;
+#pragma unroll
+      for (int j = 0; j < NB; ++j) {
+        a += sBv[q1 * NB + j] * su[el1 * NVB + c * NB + j];
+        b += sBv[q1 * NB + j] * sv[el1 * NVB + c * NB + j];
+      }
+      U[c].v = a / sd;
+      U[c].t = b;  // the sqrt(det) factors of trace and test cancel
+#pragma unroll
+      for (int k = 0; k < 4; ++k) {
+        U[c].d[k] = (k == c) ? T(1) : T(0);
+        U[c].dt[k] = T(0);
+      }
+    }
+    H Fx[4], Fy[4];
+    euler_flux<H, T>(U, d.fs.gamma, Fx, Fy);
+    T fb[8];
+#pragma unroll
+    for (int dd = 0; dd < 2; ++dd)
+#pragma unroll
+      for (int vv = 0; vv < 4; ++vv) {
+        T a = 0;
+#pragma unroll
+        for (int i = 0; i < NB; ++i) a += sDv[(dd * NQ + q1) * NB + i] * sw[el1 * NVB + vv * NB + i];
+        fb[dd * 4 + vv] = a;
+      }
+#pragma unroll
+    for (int c = 0; c < 4; ++c) {
+      T a = 0;
+#pragma unroll
+      for (int vv = 0; vv < 4; ++vv) {
+        const T f0 = ge[0] * Fx[vv].dt[c] + ge[1] * Fy[vv].dt[c];
+        const T f1 = ge[2] * Fx[vv].dt[c] + ge[3] * Fy[vv].dt[c];
+        a += fb[vv] * f0 + fb[4 + vv] * f1;
+      }
+      sU[(el1 * NQ + q1) * 4 + c] = a / sd;
+    }
+  }
+  __syncthreads();
+  for (int it = threadIdx.x; it < ne * NVB; it += blockDim.x) {
+    const int el = it / NVB, r = it - el * NVB;
+    const int c = r / NB, j = r - c * NB;
+    T acc = 0;
+#pragma unroll
+    for (int q = 0; q < NQ; ++q) acc += sBv[q * NB + j] * sU[(el * NQ + q) * 4 + c];
+    const int64_t e = e0 + el;
+#pragma unroll
+    for (int k = 0; k < 3; ++k) {
+      const int fs = d.ef[3 * e + k];
+      const int64_t face = fs >> 1;
+      const int side = fs & 1;
+      const T* gt = GT + face * NFQ * 8 + side * 4 + c;
+#pragma unroll
+      for (int q = 0; q < NFQ; ++q) {
+        const int qq = side ? (NFQ - 1 - q) : q;
+        acc += sBf[(k * NFQ + qq) * NB + j] * gt[q * 8];
+      }
+    }
+    out[e0 * NVB + it] = acc;
+  }
+}
+
+template <class T, int P>
+static cudaError_t jvp_state_adjoint_p(const DGData<T>& d, const T* u, const T* v, const T* w, T* out, T* GT,
+                                       const T* escale, T osc, cudaStream_t st) {
+  using O = Ord<P>;
+  const int64_t nf = d.F * O::NFQ;
+  if (nf > 0) face_hess_kernel<T, P><<<(unsigned)((nf + 127) / 128), 128, 0, st>>>(d, u, v, w, GT, escale, osc);
+  const int64_t eb = (d.E + O::ET - 1) / O::ET;
+  elem_hess_kernel<T, P><<<(unsigned)eb, 256, 0, st>>>(d, u, v, w, GT, out, escale, osc);
+  return cudaGetLastError();
+}
+
+template <class T>
+cudaError_t launch_jvp_state_adjoint(const DGData<T>& d, const T* u, const T* v, const T* w, T* out, T* GT,
+                                     const T* escale, T osc, cudaStream_t st) {
+  switch (d.p) {
+    case 0: return jvp_state_adjoint_p<T, 0>(d, u, v, w, out, GT, escale, osc, st);
+    case 1: return jvp_state_adjoint_p<T, 1>(d, u, v, w, out, GT, escale, osc, st);
+    case 2: return jvp_state_adjoint_p<T, 2>(d, u, v, w, out, GT, escale, osc, st);
+    case 3: return jvp_state_adjoint_p<T, 3>(d, u, v, w, out, GT, escale, osc, st);
+  }
+  return cudaErrorInvalidValue;
+}
+
 // ------------------------------------------------------------------ time step
 // dt_e = CFL h_e / ((2p+1)(|v| + c)) with v, c at the element centroid (Eq. x3d).
 template <class T, int P>
@@ -694,6 +1077,10 @@ cudaError_t launch_density_norm(const T* R, const T* s, int64_t E, int nb, int n
 }
 
 #define PCEXP_INST(T)                                                                                         \
+  template cudaError_t launch_jvp_state_adjoint<T>(const DGData<T>&, const T*, const T*, const T*, T*, T*,        \
+                                                   const T*, T, cudaStream_t);                                \
+  template cudaError_t launch_jac_adjoint<T>(const DGData<T>&, LinData<T>, const T*, T*, T*, const T*, T,        \
+                                             cudaStream_t);                                                   \
   template cudaError_t launch_linearize<T>(const DGData<T>&, const T*, LinData<T>, cudaStream_t);               \
   template cudaError_t launch_jac_apply<T>(const DGData<T>&, LinData<T>, const T*, T*, T*, const T*, const int*, \
                                            const double*, cudaStream_t, const cudaEvent_t*);                  \

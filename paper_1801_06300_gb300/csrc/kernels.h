@@ -87,6 +87,14 @@ cudaError_t launch_linearize(const DGData<T>& d, const T* u, LinData<T> lin, cud
 template <class T>
 cudaError_t launch_jac_apply(const DGData<T>& d, LinData<T> lin, const T* dv, T* out, T* G, const T* escale,
                              const int* skip, const double* oscale, cudaStream_t st, const cudaEvent_t* ev);
+// out = (osc * diag(escale) * J(u))^T w from the point Jacobians; GT is scratch [F][nfq][8].
+template <class T>
+cudaError_t launch_jac_adjoint(const DGData<T>& d, LinData<T> lin, const T* w, T* out, T* GT, const T* escale, T osc,
+                               cudaStream_t st);
+// out = (d/du [ (osc diag(escale) J(u) v)^T w ])^T, the second-order adjoint; GT scratch [F][nfq][8].
+template <class T>
+cudaError_t launch_jvp_state_adjoint(const DGData<T>& d, const T* u, const T* v, const T* w, T* out, T* GT,
+                                     const T* escale, T osc, cudaStream_t st);
 // dt_e = cfl h_e / ((2p+1)(|v_c| + c_c)) -> dte[E]; min over e -> *dtmin (last-block reduction).
 template <class T>
 cudaError_t launch_local_dt(const DGData<T>& d, const T* u, const double* cfl_dev, double cfl,

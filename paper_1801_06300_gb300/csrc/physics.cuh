@@ -170,6 +170,111 @@ template <class T, int N> struct Lift<Jet<T, N>, T> {
   }
 };
 
+// ------------------------------------------------------- hyper-dual (second order)
+// HD4<T>: value v, partials d[c] along 4 seeded directions, the directional
+// derivative t along one more direction, and the partials dt[c] of t.  Running a
+// flux on HD4 gives d/dU_c (dF/dU . t): the second-order term needed by the adjoint of
+// a Jacobian-vector product with respect to the linearisation state.
+template <class T>
+struct HD4 {
+  T v;
+  T d[4];
+  T t;
+  T dt[4];
+};
+template <class T> PCEXP_DEV T val(const HD4<T>& x) { return x.v; }
+template <class T> PCEXP_DEV HD4<T> operator+(const HD4<T>& a, const HD4<T>& b) {
+  HD4<T> r;
+  r.v = a.v + b.v;
+  r.t = a.t + b.t;
+#pragma unroll
+  for (int c = 0; c < 4; ++c) {
+    r.d[c] = a.d[c] + b.d[c];
+    r.dt[c] = a.dt[c] + b.dt[c];
+  }
+  return r;
+}
+template <class T> PCEXP_DEV HD4<T> operator-(const HD4<T>& a) {
+  HD4<T> r;
+  r.v = -a.v;
+  r.t = -a.t;
+#pragma unroll
+  for (int c = 0; c < 4; ++c) {
+    r.d[c] = -a.d[c];
+    r.dt[c] = -a.dt[c];
+  }
+  return r;
+}
+template <class T> PCEXP_DEV HD4<T> operator-(const HD4<T>& a, const HD4<T>& b) { return a + (-b); }
+template <class T> PCEXP_DEV HD4<T> operator*(const HD4<T>& a, const HD4<T>& b) {
+  HD4<T> r;
+  r.v = a.v * b.v;
+  r.t = a.t * b.v + a.v * b.t;
+#pragma unroll
+  for (int c = 0; c < 4; ++c) {
+    r.d[c] = a.d[c] * b.v + a.v * b.d[c];
+    r.dt[c] = a.dt[c] * b.v + a.t * b.d[c] + a.d[c] * b.t + a.v * b.dt[c];
+  }
+  return r;
+}
+template <class T> PCEXP_DEV HD4<T> operator*(const HD4<T>& a, T b) {
+  HD4<T> r;
+  r.v = a.v * b;
+  r.t = a.t * b;
+#pragma unroll
+  for (int c = 0; c < 4; ++c) {
+    r.d[c] = a.d[c] * b;
+    r.dt[c] = a.dt[c] * b;
+  }
+  return r;
+}
+template <class T> PCEXP_DEV HD4<T> operator*(T a, const HD4<T>& b) { return b * a; }
+template <class T> PCEXP_DEV HD4<T> operator+(const HD4<T>& a, T b) { HD4<T> r = a; r.v += b; return r; }
+template <class T> PCEXP_DEV HD4<T> operator+(T a, const HD4<T>& b) { HD4<T> r = b; r.v += a; return r; }
+template <class T> PCEXP_DEV HD4<T> operator-(const HD4<T>& a, T b) { HD4<T> r = a; r.v -= b; return r; }
+template <class T> PCEXP_DEV HD4<T> operator-(T a, const HD4<T>& b) { return (-b) + a; }
+// f(a) from f, f', f'' at a.v
+template <class T> PCEXP_DEV HD4<T> hd_apply(const HD4<T>& a, T f0, T f1, T f2) {
+  HD4<T> r;
+  r.v = f0;
+  r.t = f1 * a.t;
+#pragma unroll
+  for (int c = 0; c < 4; ++c) {
+    r.d[c] = f1 * a.d[c];
+    r.dt[c] = f1 * a.dt[c] + f2 * a.d[c] * a.t;
+  }
+  return r;
+}
+template <class T> PCEXP_DEV HD4<T> hd_inv(const HD4<T>& a) {
+  const T i = T(1) / a.v;
+  return hd_apply(a, i, -i * i, T(2) * i * i * i);
+}
+template <class T> PCEXP_DEV HD4<T> operator/(const HD4<T>& a, const HD4<T>& b) { return a * hd_inv(b); }
+template <class T> PCEXP_DEV HD4<T> operator/(const HD4<T>& a, T b) { return a * (T(1) / b); }
+template <class T> PCEXP_DEV HD4<T> operator/(T a, const HD4<T>& b) { return hd_inv(b) * a; }
+template <class T> PCEXP_DEV HD4<T> sqrt_s(const HD4<T>& a) {
+  const T s = sqrt_s(a.v);
+  return hd_apply(a, s, T(0.5) / s, T(-0.25) / (s * a.v));
+}
+template <class T> PCEXP_DEV HD4<T> abs_s(const HD4<T>& a) {
+  const T sg = a.v > T(0) ? T(1) : (a.v < T(0) ? T(-1) : T(0));
+  return hd_apply(a, sg * a.v, sg, T(0));
+}
+template <class T> PCEXP_DEV HD4<T> pow_s(const HD4<T>& a, T e) {
+  const T p = pow_s(a.v, e);
+  return hd_apply(a, p, e * p / a.v, e * (e - T(1)) * p / (a.v * a.v));
+}
+template <class T> struct Lift<HD4<T>, T> {
+  PCEXP_DEV static HD4<T> of(T x) {
+    HD4<T> r;
+    r.v = x;
+    r.t = T(0);
+#pragma unroll
+    for (int c = 0; c < 4; ++c) r.d[c] = r.dt[c] = T(0);
+    return r;
+  }
+};
+
 // ---------------------------------------------------------------- free stream
 template <class T>
 struct Free {
