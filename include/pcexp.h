@@ -184,6 +184,24 @@ int pcexp_arnoldi(pcexp_ctx* ctx, const double* U, const double* b, int m,
 int pcexp_phi(pcexp_ctx* ctx, const double* H, int k, int ldh, double dt,
               double* phi1, double* phi2);
 
+/* Adjoint of pcexp_phi: Hbar = (d y / d H)^T ybar for y = phi_1(dt H) e_1
+ * (k x k, row-major with leading dimension ldh; host arrays).  Computed on the
+ * device in FP64 as dt times the leading block of the Frechet derivative
+ * L_exp(A^T, Ybar), the top-right block of exp([[A^T, Ybar], [0, A^T]]). */
+int pcexp_phi_adjoint(pcexp_ctx* ctx, const double* H, int k, int ldh, double dt,
+                      const double* ybar, double* Hbar);
+
+/* Reverse of one PCEXP step (Eq. s9, s10) exactly as computed with the global
+ * time step dt and Krylov dimension m: given the state U = u_n (the checkpoint)
+ * and ubar_next, the adjoint of u_{n+1}, writes ubar = (du_{n+1}/du_n)^T
+ * ubar_next.  The step is recomputed from u_n; dt is held constant.  Covers the
+ * adjoint of R, of J_n (including its dependence on u_n), of the CGS2 Arnoldi
+ * processes, of phi and of both updates.  FP64 contexts only
+ * (PCEXP_ERR_UNSUPPORTED otherwise).  The first call allocates the reverse work
+ * space (about 2 (m_max + 1) + 16 state vectors). */
+int pcexp_step_backward(pcexp_ctx* ctx, const double* U, double dt, int m,
+                        const double* ubar_next, double* ubar, int on_device);
+
 /* One PCEXP (Eq. s9, s10) or EXP1 (Eq. s9) step on the master state with
  * Krylov dimension m (<= m_max).  dt_mode PCEXP_DT_*: dt_or_cfl is dt for
  * PCEXP_DT_GIVEN, else the CFL number.  info may be NULL; when given, the

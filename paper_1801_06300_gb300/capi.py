@@ -86,6 +86,8 @@ SIGNATURES = {
     "pcexp_arnoldi": (C.c_int, [_P, _P, _P, C.c_int, _P, _D, C.POINTER(C.c_int), _D, C.c_int]),
     "pcexp_phi": (C.c_int, [_P, _D, C.c_int, C.c_int, C.c_double, _D, _D]),
     "pcexp_step": (C.c_int, [_P, C.c_int, C.c_int, C.c_double, C.c_int, C.POINTER(pcexp_step_info)]),
+    "pcexp_phi_adjoint": (C.c_int, [_P, _D, C.c_int, C.c_int, C.c_double, _D, _D]),
+    "pcexp_step_backward": (C.c_int, [_P, _P, C.c_double, C.c_int, _P, _P, C.c_int]),
     "pcexp_march_steady": (C.c_int, [_P, C.c_int, C.c_double, C.c_double, C.c_int, C.c_int,
                                      C.POINTER(pcexp_steady_info)]),
     "pcexp_output": (C.c_int, [_P, C.c_int, _D]),
@@ -263,6 +265,23 @@ class Context:
         check(self.lib.pcexp_phi(self.ctx, H.ctypes.data_as(_D), k, H.shape[1], dt, p1.ctypes.data_as(_D),
                                  p2.ctypes.data_as(_D)), "pcexp_phi")
         return p1, p2
+
+    def phi_adjoint(self, H, dt: float, ybar):
+        H = np.ascontiguousarray(H, np.float64)
+        yb = np.ascontiguousarray(ybar, np.float64)
+        k = H.shape[0]
+        Hb = np.zeros_like(H)
+        check(self.lib.pcexp_phi_adjoint(self.ctx, H.ctypes.data_as(_D), k, H.shape[1], dt, yb.ctypes.data_as(_D),
+                                         Hb.ctypes.data_as(_D)), "pcexp_phi_adjoint")
+        return Hb
+
+    def step_backward(self, U, dt: float, m: int, ubar_next, out=None):
+        out = (np.empty(self.K) if isinstance(U, np.ndarray) else U.new_empty(self.K)) if out is None else out
+        pu, dev = _ptr(U)
+        pg, _ = _ptr(ubar_next)
+        po, _ = _ptr(out)
+        check(self.lib.pcexp_step_backward(self.ctx, pu, dt, m, pg, po, dev), "pcexp_step_backward")
+        return out
 
     def step(self, scheme: int, dt_mode: int, dt_or_cfl: float, m: int, info: bool = True):
         inf = pcexp_step_info()

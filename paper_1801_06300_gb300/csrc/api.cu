@@ -40,6 +40,14 @@ struct pcexp_ctx {
   double *io64a = nullptr, *io64b = nullptr;
   void *Avol = nullptr, *Bface = nullptr;  // point Jacobians at the linearisation state
   void* GT = nullptr;                      // adjoint face scratch [F][nfq][8]
+  // reverse-step work space (FP64 contexts, allocated by the first backward call)
+  double *b_un = nullptr, *b_us = nullptr, *b_dl = nullptr, *b_V1 = nullptr, *b_Vb = nullptr;
+  double *b_w1 = nullptr, *b_w0 = nullptr, *b_wb2 = nullptr, *b_wb1 = nullptr, *b_wb0 = nullptr;
+  double *b_t1 = nullptr, *b_t2 = nullptr, *b_ubn = nullptr, *b_ubs = nullptr, *b_db = nullptr, *b_bb = nullptr,
+         *b_rb = nullptr, *b_gin = nullptr;
+  double* b_small = nullptr;  // 2 MMAX^2 doubles: H and Hbar of pcexp_phi_adjoint
+  KState* b_ks1 = nullptr;
+  AdjState* b_as = nullptr;
   KState* ks = nullptr;
   StepState* ss = nullptr;
   double* partials = nullptr;
@@ -713,6 +721,149 @@ int vjp_impl(pcexp_ctx* c, const double* U, const double* w, double* JTw, int on
   return PCEXP_OK;
 }
 
+
+// ------------------------------------------------------------------ reverse step
+int alloc_backward(pcexp_ctx* c) {
+  if (c->b_un) return PCEXP_OK;
+  const size_t Kp = (size_t)c->Kp, Vn = (size_t)(c->m_max + 1) * Kp;
+  double** vecs[] = {&c->b_un, &c->b_us, &c->b_dl, &c->b_w1, &c->b_w0, &c->b_wb2, &c->b_wb1, &c->b_wb0,
+                     &c->b_t1, &c->b_t2, &c->b_ubn, &c->b_ubs, &c->b_db, &c->b_bb, &c->b_rb, &c->b_gin};
+  for (double** v : vecs) PCEXP_TRY(dalloc(c, v, Kp));
+  PCEXP_TRY(dalloc(c, &c->b_V1, Vn));
+  PCEXP_TRY(dalloc(c, &c->b_Vb, Vn));
+  PCEXP_TRY(dalloc(c, &c->b_small, (size_t)2 * MMAX * MMAX));
+  PCEXP_TRY(dalloc(c, &c->b_ks1, 1));
+  PCEXP_TRY(dalloc(c, &c->b_as, 1));
+  PCEXP_CK(cudaStreamSynchronize(c->st));
+  return PCEXP_OK;
+}
+
+// Reverse of one Arnoldi + phi + update stage; Vb holds the seeded basis adjoints.
+// Accumulates the second-order terms into b_ubn and leaves the start-vector adjoint in b_bb.
+int reverse_krylov(pcexp_ctx* c, const DGData<double>& d, const double* Z, const KState* ks, int k) {
+  const int64_t Kp = c->Kp;
+  double* G = reinterpret_cast<double*>(c->GT);
+  for (int j = k - 1; j >= 0; --j) {
+    PCEXP_CK(launch_adj_column(Z, Kp, c->b_Vb, Kp, j, j == k - 1, ks, c->b_as, c->partials, c->b_w1, c->b_w0,
+                               c->b_wb2, c->b_wb1, c->b_wb0, c->st));
+    // w0 = J_n v_j: vbar_j += J_n^T w0bar;  ubar_n += (d(J(u) v_j)/du)^T w0bar, v_j = s_j z_j
+    PCEXP_CK(launch_jac_adjoint<double>(d, lindata<double>(c), c->b_wb0, c->b_t1, G, nullptr, 1.0, c->st));
+    PCEXP_CK(launch_axpy(c->b_Vb + (int64_t)j * Kp, c->b_t1, nullptr, 1.0, Kp, c->st));
+    PCEXP_CK(launch_jvp_state_adjoint<double>(d, c->b_un, Z + (int64_t)j * Kp, c->b_wb0, c->b_t2, G, nullptr, 1.0,
+                                              c->st));
+    PCEXP_CK(launch_axpy(c->b_ubn, c->b_t2, &ks->s[j], 1.0, Kp, c->st));
+  }
+  PCEXP_CK(launch_adj_bbar(Z, c->b_Vb, c->b_bb, Kp, ks, c->b_as, c->partials, c->st));
+  return PCEXP_OK;
+}
+
+int step_backward_impl(pcexp_ctx* c, const double* U, double dt, int m, const double* ubar_next, double* ubar,
+                       int on_device) {
+  PCEXP_TRY(alloc_backward(c));
+  const DGData<double> d = dgdata<double>(c);
+  const int64_t Kp = c->Kp;
+  double* V = reinterpret_cast<double*>(c->V);
+  double* w = reinterpret_cast<double*>(c->w);
+  double* tmp = reinterpret_cast<double*>(c->tmp);
+  const size_t vbytes = (size_t)Kp * sizeof(double);
+  const bool prof = c->prof;
+  c->prof = false;
+  PCEXP_TRY(import_vec<double>(c, U, on_device, c->b_un));
+  PCEXP_TRY(import_vec<double>(c, ubar_next, on_device, c->b_gin));
+  // ---- forward recompute of the step from the checkpoint u_n (Eq. s9, s10)
+  PCEXP_CK(cudaMemsetAsync(&c->ss->err, 0, sizeof(int), c->st));
+  PCEXP_CK(launch_set_dt(c->ss, dt, c->st));
+  PCEXP_TRY(dg_apply<double>(c, d, c->b_un, nullptr, V, nullptr, nullptr));
+  PCEXP_TRY(linearize<double>(c, d, c->b_un));
+  PCEXP_TRY(arnoldi<double>(c, nullptr, m));
+  PCEXP_CK(cudaMemcpyAsync(c->b_ks1, c->ks, sizeof(KState), cudaMemcpyDeviceToDevice, c->st));
+  PCEXP_CK(cudaMemcpyAsync(c->b_V1, V, (size_t)(m + 1) * vbytes, cudaMemcpyDeviceToDevice, c->st));
+  PCEXP_CK(launch_phi(c->b_ks1, &c->ss->dt, 0.0, 1.0, c->ss, 0, c->st));
+  PCEXP_CK(launch_krylov_axpy<double>(c->b_un, c->b_us, c->b_us, c->b_dl, c->b_V1, Kp, Kp, c->b_ks1, c->st));
+  PCEXP_TRY(dg_apply<double>(c, d, c->b_us, nullptr, w, nullptr, nullptr));
+  PCEXP_TRY(jac_apply<double>(c, d, c->b_dl, tmp, nullptr, nullptr, nullptr));
+  PCEXP_CK(launch_combine_corrector<double>(V, w, tmp, Kp, c->st));
+  PCEXP_TRY(arnoldi<double>(c, nullptr, m));
+  PCEXP_CK(launch_phi(c->ks, &c->ss->dt, 0.0, 0.5, c->ss, 1, c->st));
+  KState h1, h2;
+  PCEXP_CK(cudaMemcpyAsync(&h1, c->b_ks1, sizeof(KState), cudaMemcpyDeviceToHost, c->st));
+  PCEXP_CK(cudaMemcpyAsync(&h2, c->ks, sizeof(KState), cudaMemcpyDeviceToHost, c->st));
+  PCEXP_CK(cudaStreamSynchronize(c->st));
+  if (h1.err || h2.err) {
+    c->prof = prof;
+    g_last_error = "non-finite quantity in the recomputed step";
+    return PCEXP_ERR_NONFINITE;
+  }
+  const int k1 = h1.k, k2 = h2.k;
+  // ---- reverse
+  PCEXP_CK(cudaMemsetAsync(c->b_ubn, 0, vbytes, c->st));
+  PCEXP_CK(cudaMemsetAsync(c->b_rb, 0, vbytes, c->st));
+  PCEXP_CK(cudaMemsetAsync(c->b_db, 0, vbytes, c->st));
+  PCEXP_CK(cudaMemcpyAsync(c->b_ubs, c->b_gin, vbytes, cudaMemcpyDeviceToDevice, c->st));
+  double* G = reinterpret_cast<double*>(c->GT);
+  if (k2 > 0) {
+    // u_{n+1} = u_* + dt/2 beta_2 V_2 y_2
+    PCEXP_CK(launch_adj_seed(V, Kp, c->b_Vb, c->b_gin, Kp, k2, m, 0.5 * dt, c->ks, c->b_as, c->partials, c->st));
+    PCEXP_CK(launch_phi_adjoint(c->ks->H, k2, MMAX, dt, c->b_as->ybar, c->b_as->Hbar, &c->b_as->err, c->st));
+    PCEXP_TRY(reverse_krylov(c, d, V, c->ks, k2));
+    // N_* - N_n = R(u_*) - R_n - J_n delta, with bbar_2 = b_bb
+    PCEXP_CK(launch_jac_adjoint<double>(d, lindata<double>(c), c->b_bb, c->b_t1, G, nullptr, 1.0, c->st));
+    PCEXP_CK(launch_axpy(c->b_db, c->b_t1, nullptr, -1.0, Kp, c->st));
+    PCEXP_CK(launch_jvp_state_adjoint<double>(d, c->b_un, c->b_dl, c->b_bb, c->b_t2, G, nullptr, 1.0, c->st));
+    PCEXP_CK(launch_axpy(c->b_ubn, c->b_t2, nullptr, -1.0, Kp, c->st));
+    PCEXP_CK(launch_axpy(c->b_rb, c->b_bb, nullptr, -1.0, Kp, c->st));
+    PCEXP_TRY(linearize<double>(c, d, c->b_us));
+    PCEXP_CK(launch_jac_adjoint<double>(d, lindata<double>(c), c->b_bb, c->b_t1, G, nullptr, 1.0, c->st));
+    PCEXP_CK(launch_axpy(c->b_ubs, c->b_t1, nullptr, 1.0, Kp, c->st));
+    PCEXP_TRY(linearize<double>(c, d, c->b_un));
+  }
+  // u_* = u_n + delta
+  PCEXP_CK(launch_axpy(c->b_ubn, c->b_ubs, nullptr, 1.0, Kp, c->st));
+  PCEXP_CK(launch_axpy(c->b_db, c->b_ubs, nullptr, 1.0, Kp, c->st));
+  if (k1 > 0) {
+    // delta = dt beta_1 V_1 y_1
+    PCEXP_CK(launch_adj_seed(c->b_V1, Kp, c->b_Vb, c->b_db, Kp, k1, m, dt, c->b_ks1, c->b_as, c->partials, c->st));
+    PCEXP_CK(launch_phi_adjoint(c->b_ks1->H, k1, MMAX, dt, c->b_as->ybar, c->b_as->Hbar, &c->b_as->err, c->st));
+    PCEXP_TRY(reverse_krylov(c, d, c->b_V1, c->b_ks1, k1));
+    PCEXP_CK(launch_axpy(c->b_rb, c->b_bb, nullptr, 1.0, Kp, c->st));
+  }
+  // R_n = R(u_n)
+  PCEXP_CK(launch_jac_adjoint<double>(d, lindata<double>(c), c->b_rb, c->b_t1, G, nullptr, 1.0, c->st));
+  PCEXP_CK(launch_axpy(c->b_ubn, c->b_t1, nullptr, 1.0, Kp, c->st));
+  c->prof = prof;
+  PCEXP_TRY(export_vec<double>(c, c->b_ubn, ubar, on_device));
+  int aerr = 0;
+  PCEXP_CK(cudaMemcpyAsync(&aerr, &c->b_as->err, sizeof(int), cudaMemcpyDeviceToHost, c->st));
+  PCEXP_CK(cudaStreamSynchronize(c->st));
+  if (aerr) {
+    g_last_error = "non-finite phi adjoint";
+    return PCEXP_ERR_NONFINITE;
+  }
+  return PCEXP_OK;
+}
+
+int phi_adjoint_abi(pcexp_ctx* c, const double* H, int k, int ldh, double dt, const double* ybar, double* Hbar) {
+  PCEXP_TRY(alloc_backward(c));
+  AdjState* as = c->b_as;
+  double* dH = c->b_small;  // k*k entries, leading dimension k
+  double* dHb = c->b_small + MMAX * MMAX;
+  PCEXP_CK(cudaMemsetAsync(&as->err, 0, sizeof(int), c->st));
+  std::vector<double> Hk((size_t)k * k);
+  for (int i = 0; i < k; ++i)
+    for (int j = 0; j < k; ++j) Hk[(size_t)i * k + j] = H[(size_t)i * ldh + j];
+  PCEXP_CK(cudaMemcpyAsync(dH, Hk.data(), Hk.size() * 8, cudaMemcpyHostToDevice, c->st));
+  PCEXP_CK(cudaMemcpyAsync(as->ybar, ybar, (size_t)k * 8, cudaMemcpyHostToDevice, c->st));
+  PCEXP_CK(launch_phi_adjoint(dH, k, k, dt, as->ybar, dHb, &as->err, c->st));
+  std::vector<double> out((size_t)k * k);
+  int err = 0;
+  PCEXP_CK(cudaMemcpyAsync(out.data(), dHb, out.size() * 8, cudaMemcpyDeviceToHost, c->st));
+  PCEXP_CK(cudaMemcpyAsync(&err, &as->err, sizeof(int), cudaMemcpyDeviceToHost, c->st));
+  PCEXP_CK(cudaStreamSynchronize(c->st));
+  if (err) return PCEXP_ERR_NONFINITE;
+  for (int i = 0; i < k; ++i)
+    for (int j = 0; j < k; ++j) Hbar[(size_t)i * ldh + j] = out[(size_t)i * k + j];
+  return PCEXP_OK;
+}
 }  // namespace
 
 namespace pcexp {
@@ -863,6 +1014,24 @@ int pcexp_jvp_state_adjoint(pcexp_ctx* c, const double* U, const double* v, cons
   PCEXP_TRY(export_vec<double>(c, o, out, on_device));
   if (on_device) PCEXP_CK(cudaStreamSynchronize(c->st));
   return PCEXP_OK;
+}
+
+int pcexp_step_backward(pcexp_ctx* c, const double* U, double dt, int m, const double* ubar_next, double* ubar,
+                        int on_device) {
+  PCEXP_TRY(check_ctx(c));
+  if (!U || !ubar_next || !ubar || m < 1 || m > c->m_max || !(dt > 0) || !std::isfinite(dt))
+    return PCEXP_ERR_INVALID_ARG;
+  if (c->fp32) {
+    g_last_error = "the reverse step is provided for the FP64 form";
+    return PCEXP_ERR_UNSUPPORTED;
+  }
+  return step_backward_impl(c, U, dt, m, ubar_next, ubar, on_device);
+}
+
+int pcexp_phi_adjoint(pcexp_ctx* c, const double* H, int k, int ldh, double dt, const double* ybar, double* Hbar) {
+  PCEXP_TRY(check_ctx(c));
+  if (!H || !ybar || !Hbar || k < 1 || k > PCEXP_MAX_KRYLOV || ldh < k) return PCEXP_ERR_INVALID_ARG;
+  return phi_adjoint_abi(c, H, k, ldh, dt, ybar, Hbar);
 }
 
 int pcexp_vjp(pcexp_ctx* c, const double* U, const double* w, double* JTw, int on_device) {

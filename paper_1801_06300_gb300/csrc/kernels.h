@@ -16,6 +16,7 @@ constexpr int VPAD = 64;        // vector length padding (elements)
 // v_i = s_i z_i; the Hessenberg matrix is row-major with leading dimension MMAX.
 struct KState {
   double H[(MMAX + 1) * MMAX];
+  double H1[(MMAX + 1) * MMAX];  // first Gram-Schmidt pass alone (the adjoint needs both passes)
   double s[MMAX + 1];
   double coef[MMAX + 1];   // Gram-Schmidt update coefficients in units of z_i
   double acoef[MMAX + 1];  // axpy coefficients (factor * beta * y_i * s_i)
@@ -27,6 +28,17 @@ struct KState {
   int done;
   int err;
   unsigned counter;
+};
+
+// Device-resident scalars of the reverse Krylov stage.
+struct AdjState {
+  double hb1[MMAX + 1], hb2[MMAX + 1], cb1[MMAX + 1], cb2[MMAX + 1];
+  double dots[MMAX + 2];
+  double ybar[MMAX];
+  double Hbar[(MMAX + 1) * MMAX];  // row-major, leading dimension MMAX
+  double alpha, betabar;
+  unsigned counter;
+  int err;
 };
 
 // Device-resident per-step scalars.
@@ -122,6 +134,9 @@ cudaError_t launch_cgs(int mode, const T* Z, int64_t ldz, int64_t Kp, int j, T* 
 // ks->acoef = factor * dt * beta * y_i * s_i; records k and beta into ss->k[stage], ss->beta[stage].
 cudaError_t launch_phi(KState* ks, const double* dt_dev, double dt, double factor, StepState* ss,
                        int stage, cudaStream_t st);
+// Hbar = (d y / d H)^T ybar for y = phi_1(dt H) e_1 (H, Hbar: k x k row-major, leading dim ldh; device)
+cudaError_t launch_phi_adjoint(const double* H, int k, int ldh, double dt, const double* ybar, double* Hbar, int* err,
+                               cudaStream_t st);
 // out64 = base64 + sum_i acoef_i z_i; delta = sum_i acoef_i z_i; shadow = (T) out64
 template <class T>
 cudaError_t launch_krylov_axpy(const double* base64, double* out64, T* shadow, T* delta, const T* Z,
@@ -132,6 +147,15 @@ cudaError_t launch_combine_corrector(T* a, const T* b, const T* c, int64_t Kp, c
 template <class Tin, class Tout>
 cudaError_t launch_cast(const Tin* x, Tout* y, int64_t n, cudaStream_t st);
 cudaError_t launch_reset_kstate(KState* ks, cudaStream_t st);
+// ---- reverse Krylov stage (adjoint.cu, FP64)
+cudaError_t launch_adj_seed(const double* Z, int64_t ldz, double* Vb, const double* ubar, int64_t Kp, int k, int m,
+                            double fdt, const KState* ks, AdjState* as, double* partials, cudaStream_t st);
+cudaError_t launch_adj_column(const double* Z, int64_t ldz, double* Vb, int64_t Kp, int j, int last_col,
+                              const KState* ks, AdjState* as, double* partials, double* w1, double* w0, double* wb2,
+                              double* wb1, double* wb0, cudaStream_t st);
+cudaError_t launch_adj_bbar(const double* Z, const double* Vb, double* bbar, int64_t Kp, const KState* ks,
+                            AdjState* as, double* partials, cudaStream_t st);
+cudaError_t launch_axpy(double* y, const double* x, const double* a_dev, double a_host, int64_t n, cudaStream_t st);
 cudaError_t launch_set_dt(StepState* ss, double dt, cudaStream_t st);
 cudaError_t launch_set_param(double* param, double v, cudaStream_t st);
 cudaError_t launch_copy_dt(StepState* ss, const double* param, cudaStream_t st);

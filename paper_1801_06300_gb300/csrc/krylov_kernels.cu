@@ -115,8 +115,12 @@ PCEXP_DEV void cgs_finalize(int mode, int j, const double* dots, KState* ks, dou
       const double si = ks->s[i];
       const double h = si * dots[i];
       if (!isfinite(h)) bad = 1;
-      if (mode == CGS_PROJ) ks->H[i * MMAX + j] = h;
-      else ks->H[i * MMAX + j] += h;
+      if (mode == CGS_PROJ) {
+        ks->H[i * MMAX + j] = h;
+        ks->H1[i * MMAX + j] = h;
+      } else {
+        ks->H[i * MMAX + j] += h;
+      }
       ks->coef[i] = si * h;
     }
     __syncthreads();
@@ -365,150 +369,121 @@ cudaError_t launch_cgs(int mode, const T* Z, int64_t ldz, int64_t Kp, int j, T* 
 }
 
 // ------------------------------------------------------------------ phi kernel
-// exp of the augmented matrix A = [[dt H_k, e_1, 0], [0, 0, 1], [0, 0, 0]] by
-// scaling and squaring with the [8/8] diagonal Pade approximant
+// exp(A) by scaling and squaring with the [8/8] diagonal Pade approximant
 //   r(X) = N(X) / N(-X),  N(X) = sum_j c_j X^j,  c_j = (16-j)! 8! / (16! j! (8-j)!),
-// applied to X = A / 2^s with ||X||_1 <= 1, where the Pade error is far below
-// FP64 rounding.  Column k of exp(A) holds phi_1(dt H) e_1, column k+1 phi_2(dt H) e_1.
+// applied to X = A / 2^s with ||X||_1 <= 1 (the Pade error is far below FP64 rounding).
+// For phi: A = [[dt H_k, e_1, 0], [0, 0, 1], [0, 0, 0]]; column k of exp(A) holds
+// phi_1(dt H) e_1 and column k+1 holds phi_2(dt H) e_1.
 //
 // FP64 issues at a few instructions per clock per SM on this GPU, so one CTA would
-// spend ~10 us per (m+2)^3 product.  The kernel runs as a cluster of PHI_CTAS CTAs:
-// every CTA keeps a full copy of the matrices in shared memory, computes its share of
-// the rows of each product and writes them into every CTA of the cluster (distributed
-// shared memory), then the cluster barrier publishes them.  The Pade solve factors the
-// denominator redundantly in each CTA and splits the right-hand-side columns.
-constexpr int PN = MMAX + 2;
+// spend ~10 us per (m+2)^3 product.  The kernels run as a cluster of PHI_CTAS CTAs:
+// every CTA keeps a full copy of the matrices in shared memory (5 buffers), computes
+// its share of the rows of each product and writes them into every CTA of the cluster
+// (distributed shared memory), then the cluster barrier publishes them.  The Pade solve
+// factors the denominator redundantly in each CTA and splits the right-hand-side columns.
+constexpr int PN = MMAX + 2;      // phi: (m+2) x (m+2)
+constexpr int PN2 = 2 * PN;       // phi adjoint: block-triangular 2 (m+2) x 2 (m+2)
 constexpr int PHI_CTAS = 8;
 
 namespace cg = cooperative_groups;
 
 // C = A B for rows i = rank, rank + PHI_CTAS, ... ; results broadcast to all CTAs.
+template <int LD>
 __device__ void mat_mul_cluster(cg::cluster_group& cl, const double* A, const double* B, double* C, int n) {
   const int rank = (int)cl.block_rank();
   const int nrow = (n - rank + PHI_CTAS - 1) / PHI_CTAS;
   for (int t = threadIdx.x; t < nrow * n; t += blockDim.x) {
     const int i = rank + (t / n) * PHI_CTAS, jj = t % n;
     double a = 0;
-    for (int l = 0; l < n; ++l) a = fma(A[i * PN + l], B[l * PN + jj], a);
+    for (int l = 0; l < n; ++l) a = fma(A[i * LD + l], B[l * LD + jj], a);
 #pragma unroll
-    for (int r = 0; r < PHI_CTAS; ++r) cl.map_shared_rank(C, r)[i * PN + jj] = a;
+    for (int r = 0; r < PHI_CTAS; ++r) cl.map_shared_rank(C, r)[i * LD + jj] = a;
   }
   cl.sync();
 }
 
-__global__ void __cluster_dims__(PHI_CTAS, 1, 1) __launch_bounds__(256)
-    phi_kernel(KState* ks, const double* dt_dev, double dt_host, double factor, StepState* ss, int stage) {
-  extern __shared__ double sm[];
-  double* A = sm;             // X = A / 2^s
-  double* B2 = A + PN * PN;
-  double* B4 = B2 + PN * PN;
-  double* B6 = B4 + PN * PN;
-  double* Nm = B6 + PN * PN;  // V + U, then the solution X
-  double* Dm = Nm + PN * PN;  // V - U
-  double* Tm = Dm + PN * PN;
+// exp of the n x n matrix held (identically) in buffer A of every CTA of the cluster.
+// sm holds 5 LD x LD buffers; returns the buffer with the result (same in all CTAs),
+// or nullptr if the input is not finite.  Must be called by all threads of all CTAs.
+template <int LD>
+__device__ double* expm_cluster(cg::cluster_group& cl, double* sm, int n) {
+  double* A = sm;
+  double* B2 = A + LD * LD;
+  double* B4 = B2 + LD * LD;
+  double* B6 = B4 + LD * LD;
+  double* Vb = B6 + LD * LD;
   __shared__ int s_sq;
   __shared__ int piv_row;
-  cg::cluster_group cl = cg::this_cluster();
+  __shared__ float colsum[LD];
   const int rank = (int)cl.block_rank();
-  const int k = ks->k;
-  const double dt = dt_dev ? *dt_dev : dt_host;
-  if (k == 0 || ks->err) {  // uniform across the cluster: no shared-memory traffic happens
-    if (rank == 0 && threadIdx.x == 0) {
-      for (int i = 0; i <= MMAX; ++i) ks->acoef[i] = 0.0;
-      if (ss) {
-        ss->k[stage] = 0;
-        ss->beta[stage] = ks->beta;
-        if (ks->err) ss->err = ks->err;
-      }
-    }
-    return;
-  }
-  const int n = k + 2;
-  for (int t = threadIdx.x; t < PN * PN; t += blockDim.x) A[t] = 0.0;
-  __syncthreads();
-  for (int t = threadIdx.x; t < k * k; t += blockDim.x) {
-    const int i = t / k, jj = t - i * k;
-    A[i * PN + jj] = dt * ks->H[i * MMAX + jj];
-  }
-  if (threadIdx.x == 0) {
-    A[0 * PN + k] = 1.0;
-    A[k * PN + k + 1] = 1.0;
+  // ||A||_1 from parallel column sums in FP32 (it only selects s; the same arithmetic in
+  // every CTA gives the same s)
+  for (int jj = threadIdx.x; jj < n; jj += blockDim.x) {
+    float c = 0.f;
+    for (int i = 0; i < n; ++i) c += fabsf((float)A[i * LD + jj]);
+    colsum[jj] = c;
   }
   __syncthreads();
-  // ||A||_1 from parallel column sums in FP32 (it only selects s; the same arithmetic
-  // in every CTA gives the same s), reduced by warp 0
-  {
-    __shared__ float colsum[PN];
-    for (int jj = threadIdx.x; jj < n; jj += blockDim.x) {
-      float c = 0.f;
-      for (int i = 0; i < n; ++i) c += fabsf((float)A[i * PN + jj]);
-      colsum[jj] = c;
-    }
-    __syncthreads();
-    if (threadIdx.x < 32) {
-      float m = 0.f;
-      for (int jj = threadIdx.x; jj < n; jj += 32) m = fmaxf(m, colsum[jj]);
-      for (int o = 16; o > 0; o >>= 1) m = fmaxf(m, __shfl_xor_sync(0xffffffffu, m, o));
-      if (threadIdx.x == 0) {
-        int s = 0;
-        if (m > 1.0f) s = (int)ceilf(log2f(m)) + 1;  // +1 covers the FP32 estimate
-        if (!(m <= 3.0e38f) || s > 1000) s = -1;     // NaN or overflow
-        s_sq = s;
-      }
+  if (threadIdx.x < 32) {
+    float m = 0.f;
+    for (int jj = threadIdx.x; jj < n; jj += 32) m = fmaxf(m, colsum[jj]);
+    for (int o = 16; o > 0; o >>= 1) m = fmaxf(m, __shfl_xor_sync(0xffffffffu, m, o));
+    if (threadIdx.x == 0) {
+      int s = 0;
+      if (m > 1.0f) s = (int)ceilf(log2f(m)) + 1;  // +1 covers the FP32 estimate
+      if (!(m <= 3.0e38f) || s > 1000) s = -1;     // NaN or overflow
+      s_sq = s;
     }
   }
   __syncthreads();
-  if (s_sq < 0) {
-    if (rank == 0 && threadIdx.x == 0) {
-      ks->err = 1;
-      if (ss) ss->err = 1;
-    }
-    return;
-  }
-  const double sc = ldexp(1.0, -s_sq);
-  for (int t = threadIdx.x; t < n * n; t += blockDim.x) {
-    const int i = t / n, jj = t - i * n;
-    A[i * PN + jj] *= sc;
-  }
-  // every CTA must have finished writing its own A before remote products land in B2
+  const int sq = s_sq;
+  if (sq < 0) return nullptr;  // uniform across the cluster (same data, same arithmetic)
+  const double sc = ldexp(1.0, -sq);
+  for (int t = threadIdx.x; t < n * n; t += blockDim.x) A[(t / n) * LD + t % n] *= sc;
+  // every CTA must have finished writing its own A before remote products land
   cl.sync();
   double c[9];
   c[0] = 1.0;
   for (int jj = 1; jj <= 8; ++jj) c[jj] = c[jj - 1] * (double)(8 - jj + 1) / (double)(jj * (16 - jj + 1));
-  mat_mul_cluster(cl, A, A, B2, n);
-  mat_mul_cluster(cl, B2, B2, B4, n);
-  mat_mul_cluster(cl, B4, B2, B6, n);
-  mat_mul_cluster(cl, B4, B4, Tm, n);  // B8
-  // V = c0 I + c2 B2 + c4 B4 + c6 B6 + c8 B8 -> Dm ; W = c1 I + c3 B2 + c5 B4 + c7 B6 -> Nm
+  mat_mul_cluster<LD>(cl, A, A, B2, n);
+  mat_mul_cluster<LD>(cl, B2, B2, B4, n);
+  mat_mul_cluster<LD>(cl, B4, B2, B6, n);
+  // V = c0 I + c2 B2 + c4 B4 + c6 B6 (Vb);  W = c1 I + c3 B2 + c5 B4 + c7 B6 (into B6)
   for (int t = threadIdx.x; t < n * n; t += blockDim.x) {
-    const int i = t / n, jj = t - i * n;
-    const int o = i * PN + jj;
+    const int i = t / n, jj = t - i * n, o = i * LD + jj;
     const double id = (i == jj) ? 1.0 : 0.0;
-    Dm[o] = c[0] * id + c[2] * B2[o] + c[4] * B4[o] + c[6] * B6[o] + c[8] * Tm[o];
-    Nm[o] = c[1] * id + c[3] * B2[o] + c[5] * B4[o] + c[7] * B6[o];
+    const double b2 = B2[o], b4 = B4[o], b6 = B6[o];
+    Vb[o] = c[0] * id + c[2] * b2 + c[4] * b4 + c[6] * b6;
+    B6[o] = c[1] * id + c[3] * b2 + c[5] * b4 + c[7] * b6;
   }
-  // Tm is overwritten by the next product: all CTAs must be done reading it
-  cl.sync();
-  mat_mul_cluster(cl, A, Nm, Tm, n);  // U = X W
+  cl.sync();  // B2 is overwritten remotely next
+  mat_mul_cluster<LD>(cl, B4, B4, B2, n);  // B8
   for (int t = threadIdx.x; t < n * n; t += blockDim.x) {
-    const int i = t / n, jj = t - i * n;
-    const int o = i * PN + jj;
-    const double V = Dm[o], U = Tm[o];
-    Nm[o] = V + U;
-    Dm[o] = V - U;
+    const int o = (t / n) * LD + t % n;
+    Vb[o] += c[8] * B2[o];
+  }
+  cl.sync();  // B4 is overwritten remotely next
+  mat_mul_cluster<LD>(cl, A, B6, B4, n);  // U = X W
+  // N = V + U (Vb), D = V - U (B2)
+  for (int t = threadIdx.x; t < n * n; t += blockDim.x) {
+    const int o = (t / n) * LD + t % n;
+    const double V = Vb[o], U = B4[o];
+    Vb[o] = V + U;
+    B2[o] = V - U;
   }
   __syncthreads();
-  // solve Dm X = Nm: LU with partial pivoting repeated in every CTA (identical),
-  // right-hand-side columns jj = rank, rank + PHI_CTAS, ... in this CTA
+  // solve D X = N: LU with partial pivoting repeated in every CTA (identical); this CTA
+  // keeps the right-hand-side columns jj = rank, rank + PHI_CTAS, ...
+  double* Dm = B2;
+  double* Nm = Vb;
   const int ncol = (n - rank + PHI_CTAS - 1) / PHI_CTAS;
   for (int col = 0; col < n; ++col) {
     if (threadIdx.x < 32) {
-      // partial pivoting: largest |Dm[i][col]|, i >= col, by warp argmax on the bit
-      // patterns of |x| (their integer order is the order of the magnitudes)
+      // partial pivoting by warp argmax on the bit patterns of |x|
       unsigned long long best = 0ull;
       int bi = col;
       for (int i = col + threadIdx.x; i < n; i += 32) {
-        const unsigned long long key = (unsigned long long)__double_as_longlong(Dm[i * PN + col]) & 0x7fffffffffffffffull;
+        const unsigned long long key = (unsigned long long)__double_as_longlong(Dm[i * LD + col]) & 0x7fffffffffffffffull;
         if (key > best || i == col) {
           best = key;
           bi = i;
@@ -527,68 +502,106 @@ __global__ void __cluster_dims__(PHI_CTAS, 1, 1) __launch_bounds__(256)
     __syncthreads();
     const int pr = piv_row;
     if (pr != col) {
-      // Dm is private to this CTA; of Nm only this CTA's own columns are touched
       for (int t = threadIdx.x; t < n; t += blockDim.x) {
-        double a = Dm[col * PN + t];
-        Dm[col * PN + t] = Dm[pr * PN + t];
-        Dm[pr * PN + t] = a;
+        double a = Dm[col * LD + t];
+        Dm[col * LD + t] = Dm[pr * LD + t];
+        Dm[pr * LD + t] = a;
       }
       for (int t = threadIdx.x; t < ncol; t += blockDim.x) {
         const int jj = rank + t * PHI_CTAS;
-        double b = Nm[col * PN + jj];
-        Nm[col * PN + jj] = Nm[pr * PN + jj];
-        Nm[pr * PN + jj] = b;
+        double b = Nm[col * LD + jj];
+        Nm[col * LD + jj] = Nm[pr * LD + jj];
+        Nm[pr * LD + jj] = b;
       }
       __syncthreads();
     }
-    const double piv = Dm[col * PN + col];
-    const int nr = n - col - 1, w = (n - col - 1) + ncol;  // matrix part, then own RHS columns
+    const double piv = Dm[col * LD + col];
+    const int nr = n - col - 1, w = (n - col - 1) + ncol;
     for (int t = threadIdx.x; t < nr * w; t += blockDim.x) {
       const int i = col + 1 + t / w, q = t % w;
-      const double f = Dm[i * PN + col] / piv;
+      const double f = Dm[i * LD + col] / piv;
       if (q < n - col - 1) {
         const int jj = col + 1 + q;
-        Dm[i * PN + jj] -= f * Dm[col * PN + jj];
+        Dm[i * LD + jj] -= f * Dm[col * LD + jj];
       } else {
         const int jj = rank + (q - (n - col - 1)) * PHI_CTAS;
-        Nm[i * PN + jj] -= f * Nm[col * PN + jj];
+        Nm[i * LD + jj] -= f * Nm[col * LD + jj];
       }
     }
     __syncthreads();
-    for (int t = threadIdx.x; t < nr; t += blockDim.x) Dm[(col + 1 + t) * PN + col] = 0.0;
+    for (int t = threadIdx.x; t < nr; t += blockDim.x) Dm[(col + 1 + t) * LD + col] = 0.0;
     __syncthreads();
   }
   for (int col = n - 1; col >= 0; --col) {
-    const double piv = Dm[col * PN + col];
-    for (int t = threadIdx.x; t < ncol; t += blockDim.x) Nm[col * PN + rank + t * PHI_CTAS] /= piv;
+    const double piv = Dm[col * LD + col];
+    for (int t = threadIdx.x; t < ncol; t += blockDim.x) Nm[col * LD + rank + t * PHI_CTAS] /= piv;
     __syncthreads();
     for (int t = threadIdx.x; t < col * ncol; t += blockDim.x) {
       const int i = t / ncol, jj = rank + (t % ncol) * PHI_CTAS;
-      Nm[i * PN + jj] -= Dm[i * PN + col] * Nm[col * PN + jj];
+      Nm[i * LD + jj] -= Dm[i * LD + col] * Nm[col * LD + jj];
     }
     __syncthreads();
   }
-  // publish this CTA's solution columns to the whole cluster, once every CTA has
-  // finished writing V + U into its own copy of Nm
+  // publish this CTA's solution columns once every CTA has finished its own solve
   cl.sync();
   for (int t = threadIdx.x; t < n * ncol; t += blockDim.x) {
     const int i = t / ncol, jj = rank + (t % ncol) * PHI_CTAS;
-    const double v = Nm[i * PN + jj];
+    const double v = Nm[i * LD + jj];
 #pragma unroll
     for (int r = 0; r < PHI_CTAS; ++r)
-      if (r != rank) cl.map_shared_rank(Nm, r)[i * PN + jj] = v;
+      if (r != rank) cl.map_shared_rank(Nm, r)[i * LD + jj] = v;
   }
   cl.sync();
-  // squaring
-  double* X = Nm;
-  double* Y = Tm;
-  for (int it = 0; it < s_sq; ++it) {
-    mat_mul_cluster(cl, X, X, Y, n);
+  // squaring (X in Vb, B4 as the other buffer)
+  double* X = Vb;
+  double* Y = B4;
+  for (int it = 0; it < sq; ++it) {
+    mat_mul_cluster<LD>(cl, X, X, Y, n);
     double* t = X;
     X = Y;
     Y = t;
   }
+  return X;
+}
+
+__global__ void __cluster_dims__(PHI_CTAS, 1, 1) __launch_bounds__(256)
+    phi_kernel(KState* ks, const double* dt_dev, double dt_host, double factor, StepState* ss, int stage) {
+  extern __shared__ double sm[];
+  cg::cluster_group cl = cg::this_cluster();
+  const int rank = (int)cl.block_rank();
+  const int k = ks->k;
+  const double dt = dt_dev ? *dt_dev : dt_host;
+  if (k == 0 || ks->err) {  // uniform across the cluster: no shared-memory traffic happens
+    if (rank == 0 && threadIdx.x == 0) {
+      for (int i = 0; i <= MMAX; ++i) ks->acoef[i] = 0.0;
+      if (ss) {
+        ss->k[stage] = 0;
+        ss->beta[stage] = ks->beta;
+        if (ks->err) ss->err = ks->err;
+      }
+    }
+    return;
+  }
+  const int n = k + 2;
+  double* A = sm;
+  for (int t = threadIdx.x; t < PN * PN; t += blockDim.x) A[t] = 0.0;
+  __syncthreads();
+  for (int t = threadIdx.x; t < k * k; t += blockDim.x) {
+    const int i = t / k, jj = t - i * k;
+    A[i * PN + jj] = dt * ks->H[i * MMAX + jj];
+  }
+  if (threadIdx.x == 0) {
+    A[0 * PN + k] = 1.0;
+    A[k * PN + k + 1] = 1.0;
+  }
+  __syncthreads();
+  const double* X = expm_cluster<PN>(cl, sm, n);
   if (rank == 0 && threadIdx.x == 0) {
+    if (!X) {
+      ks->err = 1;
+      if (ss) ss->err = 1;
+      return;
+    }
     const double beta = ks->beta;
     bool ok = true;
     for (int i = 0; i < k; ++i) {
@@ -608,9 +621,51 @@ __global__ void __cluster_dims__(PHI_CTAS, 1, 1) __launch_bounds__(256)
   }
 }
 
+// Adjoint of y = phi_1(dt H) e_1 (the first k entries of column k of exp(A)):
+//   Hbar = dt [L_exp(A^T, Xbar)]_{0:k,0:k},  Xbar = ybar in rows 0..k-1 of column k,
+// where L_exp(M, E), the Frechet derivative of exp, is the top-right block of
+// exp([[M, E], [0, M]]) (block-triangular identity; Najfeld & Havel 1995).
+__global__ void __cluster_dims__(PHI_CTAS, 1, 1) __launch_bounds__(256)
+    phi_adjoint_kernel(const double* __restrict__ H, int k, int ldh, double dt, const double* __restrict__ ybar,
+                       double* __restrict__ Hbar, int* __restrict__ err) {
+  extern __shared__ double sm[];
+  cg::cluster_group cl = cg::this_cluster();
+  const int rank = (int)cl.block_rank();
+  const int n0 = k + 2, n = 2 * n0;
+  double* M = sm;
+  for (int t = threadIdx.x; t < PN2 * PN2; t += blockDim.x) M[t] = 0.0;
+  __syncthreads();
+  // M = [[A^T, Xbar], [0, A^T]] with A = [[dt H, e_1, 0], [0, 0, 1], [0, 0, 0]]
+  for (int t = threadIdx.x; t < k * k; t += blockDim.x) {
+    const int i = t / k, jj = t - i * k;
+    const double a = dt * H[jj * ldh + i];  // (A^T)_{ij} = A_{ji}
+    M[i * PN2 + jj] = a;
+    M[(n0 + i) * PN2 + n0 + jj] = a;
+  }
+  for (int t = threadIdx.x; t < k; t += blockDim.x) M[t * PN2 + n0 + k] = ybar[t];
+  if (threadIdx.x == 0) {
+    M[k * PN2 + 0] = 1.0;  // (A^T)_{k,0} = A_{0,k} = 1
+    M[(k + 1) * PN2 + k] = 1.0;
+    M[(n0 + k) * PN2 + n0 + 0] = 1.0;
+    M[(n0 + k + 1) * PN2 + n0 + k] = 1.0;
+  }
+  __syncthreads();
+  const double* X = expm_cluster<PN2>(cl, sm, n);
+  if (rank == 0) {
+    if (!X) {
+      if (threadIdx.x == 0) *err = 1;
+      return;
+    }
+    for (int t = threadIdx.x; t < k * k; t += blockDim.x) {
+      const int i = t / k, jj = t - i * k;
+      Hbar[i * ldh + jj] = dt * X[i * PN2 + n0 + jj];
+    }
+  }
+}
+
 cudaError_t launch_phi(KState* ks, const double* dt_dev, double dt, double factor, StepState* ss, int stage,
                        cudaStream_t st) {
-  const size_t smem = 7 * PN * PN * sizeof(double);
+  const size_t smem = 5 * PN * PN * sizeof(double);
   static bool attr_set = false;
   if (!attr_set) {
     cudaError_t e = cudaFuncSetAttribute(phi_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
@@ -618,6 +673,20 @@ cudaError_t launch_phi(KState* ks, const double* dt_dev, double dt, double facto
     attr_set = true;
   }
   phi_kernel<<<PHI_CTAS, 256, smem, st>>>(ks, dt_dev, dt, factor, ss, stage);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_phi_adjoint(const double* H, int k, int ldh, double dt, const double* ybar, double* Hbar, int* err,
+                               cudaStream_t st) {
+  if (k < 1 || k > MMAX) return cudaErrorInvalidValue;
+  const size_t smem = 5 * PN2 * PN2 * sizeof(double);
+  static bool attr_set = false;
+  if (!attr_set) {
+    cudaError_t e = cudaFuncSetAttribute(phi_adjoint_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    if (e != cudaSuccess) return e;
+    attr_set = true;
+  }
+  phi_adjoint_kernel<<<PHI_CTAS, 256, smem, st>>>(H, k, ldh, dt, ybar, Hbar, err);
   return cudaGetLastError();
 }
 

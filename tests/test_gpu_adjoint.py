@@ -68,3 +68,103 @@ def test_jvp_state_adjoint_against_oracle_differences(capi, case):
         fd = (w @ dg.jvp(u + h * delta, v) - w @ dg.jvp(u - h * delta, v)) / (2 * h)
         assert abs(g @ delta - fd) <= 1e-6 * max(abs(fd), 1e-30) + 1e-12 * np.abs(g) @ np.abs(delta)
     ctx.close()
+
+
+@pytest.mark.parametrize("k,scale", [(1, 0.7), (6, 2.0), (20, 8.0)])
+def test_phi_adjoint_against_oracle_differences(capi, k, scale):
+    """Hbar = (dy/dH)^T ybar for y = phi_1(dt H) e_1: GPU Frechet-derivative form against
+    central differences of the oracle's Taylor/long-double phi."""
+    from oracle.krylov import phi_e1
+    rng = np.random.default_rng(k)
+    H = np.triu(rng.standard_normal((k, k)), -1) * scale / np.sqrt(k) - 0.5 * scale * np.eye(k)
+    ybar = rng.standard_normal(k)
+    dt = 0.6
+    mesh, p, free = CASES["periodic_p2"]()
+    ctx = capi.Context(mesh, 0, free, capi.PCEXP_FP64, m_max=4)
+    Hb = ctx.phi_adjoint(H, dt, ybar)
+    h = 1e-6 * scale
+    fd = np.zeros_like(H)
+    for i in range(k):
+        for j in range(k):
+            E = np.zeros_like(H)
+            E[i, j] = h
+            fd[i, j] = ybar @ (phi_e1(H + E, dt)[0] - phi_e1(H - E, dt)[0]) / (2 * h)
+    assert np.linalg.norm(Hb - fd) <= 1e-7 * np.linalg.norm(fd)
+    ctx.close()
+
+
+STEP_CASES = {
+    "vortex_p1": lambda: (W.periodic_square(4, 10.0, 0.1, 5), 1, W.Freestream(0.5, 45.0), 0.4, 8),
+    "bump_p2": lambda: (W.bump_channel(6, 3, 0.15, 1), 2, W.Freestream(0.5, 0.0), 0.02, 10),
+}
+
+
+def step_fixture(name):
+    from oracle.dg import DGOracle
+    mesh, p, free, dt, m = STEP_CASES[name]()
+    dg = DGOracle(mesh, p, free)
+    u = state(dg, 11, 0.05)
+    return dg, mesh, p, free, dt, m, u
+
+
+@pytest.mark.parametrize("name", list(STEP_CASES))
+def test_step_backward_directional_against_oracle(capi, name):
+    """delta . ubar_n equals the central difference of g . PCEXP(u_n) (oracle step, Eq. s9/s10)."""
+    from oracle import pcexp
+    dg, mesh, p, free, dt, m, u = step_fixture(name)
+    ctx = capi.Context(mesh, p, free, capi.PCEXP_FP64, m_max=m)
+    g = W.random_coeffs(12, (dg.K,))
+    ub = ctx.step_backward(u, dt, m, g)
+
+    def J(x):
+        return g @ pcexp.pcexp_step(x, dg.residual, dg.jvp, dt, m)[0]
+
+    for seed in (13, 14, 15):
+        delta = W.random_coeffs(seed, (dg.K,)) * np.abs(u)
+        h = 1e-5
+        fd = (J(u + h * delta) - J(u - h * delta)) / (2 * h)
+        got = ub @ delta
+        assert abs(got - fd) <= 1e-4 * abs(fd), (seed, got, fd)
+    ctx.close()
+
+
+def test_step_backward_full_gradient_dense(capi):
+    """Whole gradient on a tiny mesh against the oracle's finite-difference step Jacobian."""
+    from oracle import pcexp
+    from oracle.dg import DGOracle
+    mesh, p, free = W.periodic_square(3, 3.0, 0.1, 2), 0, W.Freestream(0.4, 20.0)
+    dg = DGOracle(mesh, p, free)
+    u = state(dg, 21, 0.1)
+    dt, m = 0.05, 6
+    ctx = capi.Context(mesh, p, free, capi.PCEXP_FP64, m_max=m)
+    g = W.random_coeffs(22, (dg.K,))
+    ub = ctx.step_backward(u, dt, m, g)
+    ref = np.zeros(dg.K)
+    for i in range(dg.K):
+        h = 1e-6 * max(abs(u[i]), 1.0)
+        e = np.zeros(dg.K)
+        e[i] = h
+        ref[i] = g @ (pcexp.pcexp_step(u + e, dg.residual, dg.jvp, dt, m)[0]
+                      - pcexp.pcexp_step(u - e, dg.residual, dg.jvp, dt, m)[0]) / (2 * h)
+    assert np.linalg.norm(ub - ref) <= 1e-4 * np.linalg.norm(ref)
+    ctx.close()
+
+
+@pytest.mark.parametrize("name", list(STEP_CASES))
+def test_step_backward_against_gpu_forward_differences(capi, name):
+    """Self-consistency: the reverse step against central differences of the GPU's own step."""
+    dg, mesh, p, free, dt, m, u = step_fixture(name)
+    ctx = capi.Context(mesh, p, free, capi.PCEXP_FP64, m_max=m)
+    g = W.random_coeffs(31, (dg.K,))
+    ub = ctx.step_backward(u, dt, m, g)
+
+    def J(x):
+        ctx.set_state(x)
+        ctx.step(capi.PCEXP_SCHEME_PCEXP, capi.PCEXP_DT_GIVEN, dt, m, info=False)
+        return g @ ctx.get_state()
+
+    delta = W.random_coeffs(32, (dg.K,)) * np.abs(u)
+    h = 1e-5
+    fd = (J(u + h * delta) - J(u - h * delta)) / (2 * h)
+    assert abs(ub @ delta - fd) <= 1e-5 * abs(fd)
+    ctx.close()
