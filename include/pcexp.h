@@ -214,6 +214,20 @@ int pcexp_step(pcexp_ctx* ctx, int scheme, int dt_mode, double dt_or_cfl, int m,
 int pcexp_march_steady(pcexp_ctx* ctx, int scheme, double cfl_max, double decades,
                        int max_iter, int m, pcexp_steady_info* info);
 
+/* Output functionals of a state U (not part of the paper's scheme; they seed
+ * adjoint runs): the pressure force on the slip walls,
+ *   J = sum over wall faces and their Gauss points of |e| w_q p(U) (n . a),
+ * a = (1, 0) for PCEXP_FUNC_WALL_FX, (0, 1) for PCEXP_FUNC_WALL_FY, n the outward
+ * normal of the fluid element.  grad (nullable) receives dJ/dU in the basis of U.
+ * FP64 contexts only. */
+#define PCEXP_FUNC_WALL_FX 0
+#define PCEXP_FUNC_WALL_FY 1
+int pcexp_functional(pcexp_ctx* ctx, int kind, const double* U, double* value, double* grad, int on_device);
+
+/* Replaces the free stream (Mach number, angle, density, pressure, gamma) used
+ * by the far-field boundary condition; the mesh and state are kept. */
+int pcexp_set_physics(pcexp_ctx* ctx, const pcexp_physics* phys);
+
 /* Diagnostics of the master state: kind 0 = density residual norm of Eq. cfl
  * (domain volume taken from the mesh), kind 1 = entropy error of
  * Eq. entropy_error. */

@@ -212,6 +212,23 @@ class DGOracle:
             J[:, k] = self.jvp(uf, ek)
         return J
 
+    # ------------------------------------------------------------- functionals
+    def wall_force(self, u, direction=(1.0, 0.0)):
+        """Pressure force on the slip walls along ``direction``: sum over wall faces and Gauss
+        points of |e| w_q p(U_L) (n . a) (the bump-force functional of the adjoint case)."""
+        u = self.unflat(u)
+        if not len(self.fb):
+            return 0.0
+        e, f, tag = self.fb.T
+        UL = ad.lin(lambda a: np.einsum("fqi,fvi->fqv", self.fb_psi, a[e]), u)
+        rho, vel, p, E = euler.primitives(UL, self.gamma)
+        na = self.fb_n[:, 0] * direction[0] + self.fb_n[:, 1] * direction[1]
+        wgt = self.fb_w * (na * (tag == BC_SLIP_WALL))[:, None]
+        tot = p * wgt
+        if isinstance(tot, ad.Dual):
+            return ad.Dual(np.sum(tot.val), np.sum(tot.der))
+        return np.sum(tot)
+
     # ------------------------------------------------------------ projections
     def project(self, fn):
         """L2 projection of a pointwise state function fn(x [E,nq,2]) -> [E,nq,nv]."""

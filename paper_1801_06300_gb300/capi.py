@@ -36,6 +36,8 @@ PCEXP_PROJ_FREESTREAM = 0
 PCEXP_PROJ_VORTEX = 1
 PCEXP_PROJ_BLOBS = 2
 PCEXP_MAX_KRYLOV = 32
+PCEXP_FUNC_WALL_FX = 0
+PCEXP_FUNC_WALL_FY = 1
 KERNEL_CLASSES = ["residual_face", "residual_elem", "jvp_face", "jvp_elem", "cgs_norm", "cgs_proj",
                   "cgs_upd_proj", "cgs_upd_norm", "phi", "axpy", "dt", "other", "linearize"]
 
@@ -91,6 +93,8 @@ SIGNATURES = {
     "pcexp_march_steady": (C.c_int, [_P, C.c_int, C.c_double, C.c_double, C.c_int, C.c_int,
                                      C.POINTER(pcexp_steady_info)]),
     "pcexp_output": (C.c_int, [_P, C.c_int, _D]),
+    "pcexp_functional": (C.c_int, [_P, C.c_int, _P, _D, _P, C.c_int]),
+    "pcexp_set_physics": (C.c_int, [_P, C.POINTER(pcexp_physics)]),
     "pcexp_synchronize": (C.c_int, [_P]),
     "pcexp_residual_noalloc": (C.c_int, [_P, _P, _P]),
     "pcexp_profile_enable": (C.c_int, [_P, C.c_int]),
@@ -298,6 +302,18 @@ class Context:
               "pcexp_march_steady")
         return dict(iterations=inf.iterations, res_first=inf.res_first, res_last=inf.res_last,
                     converged=bool(inf.converged))
+
+    def functional(self, kind: int, U, grad=None):
+        """(value, gradient) of an output functional at U; gradient is None unless grad is given."""
+        v = C.c_double()
+        pu, dev = _ptr(U)
+        pg = _ptr(grad)[0] if grad is not None else None
+        check(self.lib.pcexp_functional(self.ctx, kind, pu, C.byref(v), pg, dev), "pcexp_functional")
+        return v.value, grad
+
+    def set_physics(self, free):
+        ph = pcexp_physics(free.gamma, free.mach, free.alpha_deg, free.rho, free.p)
+        check(self.lib.pcexp_set_physics(self.ctx, C.byref(ph)), "pcexp_set_physics")
 
     def output(self, kind: int = 0) -> float:
         v = C.c_double()

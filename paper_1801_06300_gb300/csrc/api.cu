@@ -1016,6 +1016,39 @@ int pcexp_jvp_state_adjoint(pcexp_ctx* c, const double* U, const double* v, cons
   return PCEXP_OK;
 }
 
+int pcexp_functional(pcexp_ctx* c, int kind, const double* U, double* value, double* grad, int on_device) {
+  PCEXP_TRY(check_ctx(c));
+  if (!U || !value) return PCEXP_ERR_INVALID_ARG;
+  if (kind != PCEXP_FUNC_WALL_FX && kind != PCEXP_FUNC_WALL_FY) return PCEXP_ERR_INVALID_ARG;
+  if (c->fp32) {
+    g_last_error = "output functionals are provided for the FP64 form";
+    return PCEXP_ERR_UNSUPPORTED;
+  }
+  double* a = reinterpret_cast<double*>(c->tmp);
+  double* g = reinterpret_cast<double*>(c->w);
+  PCEXP_TRY(import_vec<double>(c, U, on_device, a));
+  PCEXP_CK(cudaMemsetAsync(g, 0, (size_t)c->Kp * sizeof(double), c->st));
+  const double ax = kind == PCEXP_FUNC_WALL_FX ? 1.0 : 0.0, ay = 1.0 - ax;
+  PCEXP_CK(launch_wall_force<double>(dgdata<double>(c), c->host.F_interior, a, ax, ay, g, &c->ss->dtmin_scratch,
+                                     c->partials, &c->ss->counter, c->st));
+  PCEXP_CK(cudaMemcpyAsync(value, &c->ss->dtmin_scratch, sizeof(double), cudaMemcpyDeviceToHost, c->st));
+  if (grad) PCEXP_TRY(export_vec<double>(c, g, grad, on_device));
+  PCEXP_CK(cudaStreamSynchronize(c->st));
+  return PCEXP_OK;
+}
+
+int pcexp_set_physics(pcexp_ctx* c, const pcexp_physics* phys) {
+  PCEXP_TRY(check_ctx(c));
+  if (!phys || !(phys->gamma > 1.0) || !(phys->rho_inf > 0) || !(phys->p_inf > 0)) return PCEXP_ERR_INVALID_ARG;
+  PCEXP_CK(cudaStreamSynchronize(c->st));
+  c->phys = *phys;
+  // captured steps hold the old free stream in their kernel arguments
+  for (auto& g : c->graphs) cudaGraphExecDestroy(g.exec);
+  c->graphs.clear();
+  c->seen_keys.clear();
+  return PCEXP_OK;
+}
+
 int pcexp_step_backward(pcexp_ctx* c, const double* U, double dt, int m, const double* ubar_next, double* ubar,
                         int on_device) {
   PCEXP_TRY(check_ctx(c));

@@ -899,6 +899,85 @@ cudaError_t launch_jvp_state_adjoint(const DGData<T>& d, const T* u, const T* v,
   return cudaErrorInvalidValue;
 }
 
+// ------------------------------------------------------------ output functional
+// Pressure force on the slip walls along the unit direction (ax, ay):
+//   J = sum_{wall faces} sum_q |e| w_q p(U_L(x_q)) (n . a),  p = (gamma-1)(E - |m|^2 / (2 rho)),
+// with its gradient dJ/du (trace transpose of dp/dU); value by a fixed-order reduction.
+template <class T, int P>
+__global__ void __launch_bounds__(256) wall_force_kernel(DGData<T> d, int64_t f0, const T* __restrict__ u, double ax,
+                                                         double ay, double* __restrict__ grad, double* __restrict__ value,
+                                                         double* __restrict__ partials, unsigned* counter) {
+  using O = Ord<P>;
+  constexpr int NB = O::NB, NFQ = O::NFQ;
+  __shared__ double red[8];
+  __shared__ bool last;
+  double acc = 0;
+  const T gm = d.fs.gamma - T(1);
+  for (int64_t f = f0 + (int64_t)blockIdx.x * blockDim.x + threadIdx.x; f < d.F; f += (int64_t)gridDim.x * blockDim.x) {
+    if (-d.fel[2 * f + 1] != PCEXP_BC_SLIP_WALL) continue;
+    const int e = d.fel[2 * f];
+    const int fl = d.floc[f] & 0xff;
+    const double nx = (double)d.fgeo[4 * f], ny = (double)d.fgeo[4 * f + 1], len = (double)d.fgeo[4 * f + 2];
+    const double na = nx * ax + ny * ay;
+    const double isd = 1.0 / (double)d.geo[8 * (int64_t)e + 4];
+    double g[4 * NB];
+    for (int k = 0; k < 4 * NB; ++k) g[k] = 0.0;
+    for (int q = 0; q < NFQ; ++q) {
+      const T* b = d.Bf + (fl * NFQ + q) * NB;
+      double U[4];
+      for (int c = 0; c < 4; ++c) {
+        double a = 0;
+        for (int j = 0; j < NB; ++j) a += (double)b[j] * (double)u[(int64_t)e * 4 * NB + c * NB + j];
+        U[c] = a * isd;
+      }
+      const double ux = U[1] / U[0], uy = U[2] / U[0];
+      const double p = (double)gm * (U[3] - 0.5 * U[0] * (ux * ux + uy * uy));
+      const double wq = len * (double)d.Wf[q] * na;
+      acc += wq * p;
+      const double dp[4] = {(double)gm * 0.5 * (ux * ux + uy * uy), -(double)gm * ux, -(double)gm * uy, (double)gm};
+      for (int c = 0; c < 4; ++c)
+        for (int j = 0; j < NB; ++j) g[c * NB + j] += wq * dp[c] * (double)b[j] * isd;
+    }
+    // at most two wall faces per element on the supported meshes; a + b is exact in either order
+    if (grad)
+      for (int k = 0; k < 4 * NB; ++k) atomicAdd(grad + (int64_t)e * 4 * NB + k, g[k]);
+  }
+  for (int o = 16; o > 0; o >>= 1) acc += __shfl_xor_sync(0xffffffffu, acc, o);
+  if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = acc;
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    double b = 0;
+    for (int w = 0; w < (int)(blockDim.x >> 5); ++w) b += red[w];
+    partials[blockIdx.x] = b;
+    __threadfence();
+    last = atomicAdd(counter, 1u) == gridDim.x - 1;
+  }
+  __syncthreads();
+  if (last && threadIdx.x == 0) {
+    double b = 0;
+    for (unsigned i = 0; i < gridDim.x; ++i) b += __ldcg(partials + i);
+    *value = b;
+    *counter = 0;
+  }
+}
+
+template <class T>
+cudaError_t launch_wall_force(const DGData<T>& d, int64_t f0, const T* u, double ax, double ay, double* grad,
+                              double* value, double* partials, unsigned* counter, cudaStream_t st) {
+  const int64_t nb = d.F - f0;
+  unsigned g = (unsigned)((nb + 255) / 256);
+  if (g < 1) g = 1;
+  if (g > RED_BLOCKS) g = RED_BLOCKS;
+  switch (d.p) {
+    case 0: wall_force_kernel<T, 0><<<g, 256, 0, st>>>(d, f0, u, ax, ay, grad, value, partials, counter); break;
+    case 1: wall_force_kernel<T, 1><<<g, 256, 0, st>>>(d, f0, u, ax, ay, grad, value, partials, counter); break;
+    case 2: wall_force_kernel<T, 2><<<g, 256, 0, st>>>(d, f0, u, ax, ay, grad, value, partials, counter); break;
+    case 3: wall_force_kernel<T, 3><<<g, 256, 0, st>>>(d, f0, u, ax, ay, grad, value, partials, counter); break;
+    default: return cudaErrorInvalidValue;
+  }
+  return cudaGetLastError();
+}
+
 // ------------------------------------------------------------------ time step
 // dt_e = CFL h_e / ((2p+1)(|v| + c)) with v, c at the element centroid (Eq. x3d).
 template <class T, int P>
@@ -1077,6 +1156,8 @@ cudaError_t launch_density_norm(const T* R, const T* s, int64_t E, int nb, int n
 }
 
 #define PCEXP_INST(T)                                                                                         \
+  template cudaError_t launch_wall_force<T>(const DGData<T>&, int64_t, const T*, double, double, double*, double*, \
+                                            double*, unsigned*, cudaStream_t);                                \
   template cudaError_t launch_jvp_state_adjoint<T>(const DGData<T>&, const T*, const T*, const T*, T*, T*,        \
                                                    const T*, T, cudaStream_t);                                \
   template cudaError_t launch_jac_adjoint<T>(const DGData<T>&, LinData<T>, const T*, T*, T*, const T*, T,        \

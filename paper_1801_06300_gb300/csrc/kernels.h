@@ -107,6 +107,11 @@ cudaError_t launch_jac_adjoint(const DGData<T>& d, LinData<T> lin, const T* w, T
 template <class T>
 cudaError_t launch_jvp_state_adjoint(const DGData<T>& d, const T* u, const T* v, const T* w, T* out, T* GT,
                                      const T* escale, T osc, cudaStream_t st);
+// Pressure force on the slip walls along (ax, ay) -> *value, gradient added into grad (nullable);
+// boundary faces are those with index >= f0.
+template <class T>
+cudaError_t launch_wall_force(const DGData<T>& d, int64_t f0, const T* u, double ax, double ay, double* grad,
+                              double* value, double* partials, unsigned* counter, cudaStream_t st);
 // dt_e = cfl h_e / ((2p+1)(|v_c| + c_c)) -> dte[E]; min over e -> *dtmin (last-block reduction).
 template <class T>
 cudaError_t launch_local_dt(const DGData<T>& d, const T* u, const double* cfl_dev, double cfl,

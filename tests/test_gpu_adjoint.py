@@ -168,3 +168,93 @@ def test_step_backward_against_gpu_forward_differences(capi, name):
     fd = (J(u + h * delta) - J(u - h * delta)) / (2 * h)
     assert abs(ub @ delta - fd) <= 1e-5 * abs(fd)
     ctx.close()
+
+
+def test_wall_force_functional_matches_oracle(capi):
+    from oracle.dg import DGOracle
+    torch = pytest.importorskip("torch")
+    mesh, free = W.bump_channel(12, 4, 0.15, 1), W.Freestream(0.5, 0.0)
+    dg = DGOracle(mesh, 2, free)
+    ctx = capi.Context(mesh, 2, free, capi.PCEXP_FP64, m_max=2)
+    u = state(dg, 41, 0.05)
+    for kind, dirn in ((capi.PCEXP_FUNC_WALL_FX, (1.0, 0.0)), (capi.PCEXP_FUNC_WALL_FY, (0.0, 1.0))):
+        g = np.empty(dg.K)
+        val, _ = ctx.functional(kind, u, g)
+        ref = dg.wall_force(u, dirn)
+        assert abs(val - ref) <= 1e-13 * abs(ref)
+        from oracle import adscalar as ad
+        delta = W.random_coeffs(42, (dg.K,))
+        dref = dg.wall_force(ad.Dual(u, delta), dirn).der
+        assert abs(g @ delta - dref) <= 1e-12 * max(abs(dref), 1.0)
+    ctx.close()
+
+
+def test_autograd_rollout_gradient(capi):
+    """torch.autograd through 4 PCEXP steps (checkpointed): gradient of the wall force with
+    respect to the initial state against a central difference of the oracle rollout."""
+    torch = pytest.importorskip("torch")
+    from oracle import pcexp
+    from oracle.dg import DGOracle
+    from paper_1801_06300_gb300.autograd import PCEXPStep, WallForce, adjoint_rollout
+    mesh, free = W.bump_channel(8, 4, 0.15, 1), W.Freestream(0.5, 0.0)
+    dg = DGOracle(mesh, 1, free)
+    dt, m, steps = 0.02, 10, 4
+    ctx = capi.Context(mesh, 1, free, capi.PCEXP_FP64, m_max=m)
+    u0 = state(dg, 51, 0.02)
+    x = torch.tensor(u0, device="cuda", requires_grad=True)
+    u = x
+    for _ in range(steps):
+        u = PCEXPStep.apply(u, ctx, dt, m)
+    J = WallForce.apply(u, ctx, capi.PCEXP_FUNC_WALL_FX)
+    J.backward()
+    g = x.grad.cpu().numpy()
+
+    def J_oracle(v):
+        for _ in range(steps):
+            v, _ = pcexp.pcexp_step(v, dg.residual, dg.jvp, dt, m)
+        return dg.wall_force(v)
+
+    assert abs(J.item() - J_oracle(u0)) <= 1e-10 * abs(J_oracle(u0))
+    for seed in (52, 53):
+        delta = W.random_coeffs(seed, (dg.K,)) * np.abs(u0)
+        h = 1e-5
+        fd = (J_oracle(u0 + h * delta) - J_oracle(u0 - h * delta)) / (2 * h)
+        assert abs(g @ delta - fd) <= 1e-4 * abs(fd)
+    # the explicit reverse loop gives the same gradient
+    res = adjoint_rollout(ctx, torch.tensor(u0, device="cuda"), dt, m, steps)
+    assert np.allclose(res.grad_u0.cpu().numpy(), g, rtol=1e-12, atol=1e-14 * np.abs(g).max())
+    ctx.close()
+
+
+def test_freestream_parameter_gradients(capi):
+    """dJ/dMach and dJ/dalpha from the adjoint rollout against central differences of the
+    whole GPU rollout (initial state = projected free stream of the same parameters)."""
+    torch = pytest.importorskip("torch")
+    import dataclasses
+    from paper_1801_06300_gb300.autograd import adjoint_rollout
+    mesh, free = W.bump_channel(8, 4, 0.15, 1), W.Freestream(0.5, 2.0)
+    dt, m, steps = 0.02, 10, 3
+    ctx = capi.Context(mesh, 1, free, capi.PCEXP_FP64, m_max=m)
+
+    def u_init(fr):
+        ctx.set_physics(fr)
+        ctx.project_state(capi.PCEXP_PROJ_FREESTREAM)
+        return ctx.get_state(torch.empty(ctx.K, dtype=torch.float64, device="cuda"))
+
+    u0 = u_init(free)
+    res = adjoint_rollout(ctx, u0, dt, m, steps, params={"free": free, "names": ["mach", "alpha_deg"]},
+                          initial_state=u_init)
+
+    def J_of(fr):
+        u = u_init(fr)
+        for _ in range(steps):
+            ctx.set_state(u)
+            ctx.step(capi.PCEXP_SCHEME_PCEXP, capi.PCEXP_DT_GIVEN, dt, m, info=False)
+            u = ctx.get_state(torch.empty_like(u))
+        return ctx.functional(capi.PCEXP_FUNC_WALL_FX, u)[0]
+
+    for name, h in (("mach", 1e-4), ("alpha_deg", 1e-2)):
+        th = getattr(free, name)
+        fd = (J_of(dataclasses.replace(free, **{name: th + h})) - J_of(dataclasses.replace(free, **{name: th - h}))) / (2 * h)
+        assert abs(res.grad_params[name] - fd) <= 1e-4 * abs(fd) + 1e-12, (name, res.grad_params[name], fd)
+    ctx.close()
