@@ -11,6 +11,12 @@ Cartesian coordinates:
     j < i, then psi_i /= ||psi_i||_E, so s_i > 0).
 
 psi_i = sum_k C[i, k] chi_k with C lower triangular.
+
+Points are passed as offsets r = x - v_0 from each element's first vertex.  The
+edge vectors v_k - v_0 are exact in floating point, so X = (r - r_c) / L keeps
+full relative precision on elements far from the origin; the same X formed from
+absolute points x would carry an error of order eps |x| / L, which on a fine
+mesh far from the origin dominates the residual of a uniform state (exactly zero).
 """
 import numpy as np
 
@@ -36,20 +42,23 @@ def n_basis(p: int, dim: int) -> int:
 class PaperBasis:
     """Per-element orthonormal basis of Eq. basis built by Algorithm 1.
 
-    verts: [E, dim+1, dim] element vertices.  xq, wq: volume quadrature points
-    [E, nq, dim] and weights [E, nq] (including the element Jacobian) used for
-    the centroid and the inner products.
+    verts: [E, dim+1, dim] element vertices.  rq, wq: volume quadrature points as
+    offsets from verts[:, 0] [E, nq, dim] and weights [E, nq] (including the
+    element Jacobian) used for the centroid and the inner products.  xc is the
+    absolute centroid, rc its offset from verts[:, 0].
     """
 
-    def __init__(self, verts: np.ndarray, p: int, xq: np.ndarray, wq: np.ndarray):
+    def __init__(self, verts: np.ndarray, p: int, rq: np.ndarray, wq: np.ndarray):
         self.p = p
         self.dim = verts.shape[2]
         self.exps = np.array(monomial_exponents(p, self.dim), dtype=np.int64)  # [N, dim]
         N = len(self.exps)
         vol = wq.sum(axis=1)
-        self.xc = np.einsum("eq,eqd->ed", wq, xq) / vol[:, None]
+        self.origin = verts[:, 0, :].copy()
+        self.rc = np.einsum("eq,eqd->ed", wq, rq) / vol[:, None]  # centroid offset
+        self.xc = self.origin + self.rc
         self.L = 0.5 * (verts.max(axis=1) - verts.min(axis=1))
-        chi = self.monomials(xq)  # [E, nq, N]
+        chi = self.monomials(rq)  # [E, nq, N]
         E = verts.shape[0]
         C = np.zeros((E, N, N))
         psi = np.zeros_like(chi)
@@ -66,20 +75,30 @@ class PaperBasis:
             C[:, i, :] = ci / nrm[:, None]
         self.C = C
 
-    def monomials(self, x: np.ndarray) -> np.ndarray:
-        """chi_k(x) for points x [E, npts, dim] -> [E, npts, N]."""
-        X = (x - self.xc[:, None, :]) / self.L[:, None, :]
-        out = np.ones(x.shape[:2] + (len(self.exps),))
+    def local(self, x: np.ndarray, rows=None) -> np.ndarray:
+        """Offsets of absolute points x [E or len(rows), npts, dim] from each element's v_0."""
+        o = self.origin if rows is None else self.origin[rows]
+        return x - o[:, None, :]
+
+    def _X(self, r, rows):
+        rc = self.rc if rows is None else self.rc[rows]
+        L = self.L if rows is None else self.L[rows]
+        return (r - rc[:, None, :]) / L[:, None, :], L
+
+    def monomials(self, r: np.ndarray, rows=None) -> np.ndarray:
+        """chi_k at local points r [E, npts, dim] -> [E, npts, N]."""
+        X, _ = self._X(r, rows)
+        out = np.ones(r.shape[:2] + (len(self.exps),))
         for k, ex in enumerate(self.exps):
             for d in range(self.dim):
                 if ex[d]:
                     out[:, :, k] *= X[:, :, d] ** ex[d]
         return out
 
-    def monomial_grads(self, x: np.ndarray) -> np.ndarray:
-        """d chi_k / d x_d for points x [E, npts, dim] -> [E, npts, N, dim]."""
-        X = (x - self.xc[:, None, :]) / self.L[:, None, :]
-        out = np.zeros(x.shape[:2] + (len(self.exps), self.dim))
+    def monomial_grads(self, r: np.ndarray) -> np.ndarray:
+        """d chi_k / d x_d at local points r [E, npts, dim] -> [E, npts, N, dim]."""
+        X, _ = self._X(r, None)
+        out = np.zeros(r.shape[:2] + (len(self.exps), self.dim))
         for k, ex in enumerate(self.exps):
             for d in range(self.dim):
                 if ex[d] == 0:
@@ -91,20 +110,14 @@ class PaperBasis:
                 out[:, :, k, d] = g
         return out
 
-    def eval(self, x: np.ndarray) -> np.ndarray:
-        """psi_i(x) -> [E, npts, N]."""
-        return np.einsum("eik,eqk->eqi", self.C, self.monomials(x))
+    def eval(self, r: np.ndarray) -> np.ndarray:
+        """psi_i at local points r [E, npts, dim] -> [E, npts, N]."""
+        return np.einsum("eik,eqk->eqi", self.C, self.monomials(r))
 
-    def grad(self, x: np.ndarray) -> np.ndarray:
-        """grad psi_i(x) -> [E, npts, N, dim]."""
-        return np.einsum("eik,eqkd->eqid", self.C, self.monomial_grads(x))
+    def grad(self, r: np.ndarray) -> np.ndarray:
+        """grad psi_i at local points r [E, npts, dim] -> [E, npts, N, dim]."""
+        return np.einsum("eik,eqkd->eqid", self.C, self.monomial_grads(r))
 
-    def eval_rows(self, rows: np.ndarray, x: np.ndarray) -> np.ndarray:
-        """psi of elements ``rows`` at points x [len(rows), npts, dim]."""
-        X = (x - self.xc[rows][:, None, :]) / self.L[rows][:, None, :]
-        chi = np.ones(x.shape[:2] + (len(self.exps),))
-        for k, ex in enumerate(self.exps):
-            for d in range(self.dim):
-                if ex[d]:
-                    chi[:, :, k] *= X[:, :, d] ** ex[d]
-        return np.einsum("eik,eqk->eqi", self.C[rows], chi)
+    def eval_rows(self, rows: np.ndarray, r: np.ndarray) -> np.ndarray:
+        """psi of elements ``rows`` at their local points r [len(rows), npts, dim]."""
+        return np.einsum("eik,eqk->eqi", self.C[rows], self.monomials(r, rows))

@@ -86,11 +86,12 @@ class DGOracle:
         if np.any(det <= 0):
             raise ValueError("elements must be positively oriented")
         self.area = 0.5 * det
-        self.xq = verts[:, 0:1, :] + np.einsum("qk,ekd->eqd", rp, Aff)
+        self.rq = np.einsum("qk,ekd->eqd", rp, Aff)  # offsets from v0 (exact edge vectors)
+        self.xq = verts[:, 0:1, :] + self.rq
         self.wq = rw[None, :] * det[:, None]
-        self.basis = PaperBasis(verts, p, self.xq, self.wq)
-        self.psi_q = self.basis.eval(self.xq)  # [E, nq, N]
-        self.gpsi_wq = self.basis.grad(self.xq) * self.wq[:, :, None, None]  # [E, nq, N, 2]
+        self.basis = PaperBasis(verts, p, self.rq, self.wq)
+        self.psi_q = self.basis.eval(self.rq)  # [E, nq, N]
+        self.gpsi_wq = self.basis.grad(self.rq) * self.wq[:, :, None, None]  # [E, nq, N, 2]
         # faces
         interior, boundary = build_faces(mesh)
         s, ws = gauss_legendre01(p + 1)
@@ -124,8 +125,9 @@ class DGOracle:
         aR, bR = self._edge(eR, fR)
         # L traverses a -> b; R traverses its copy of the edge in the opposite sense,
         # so L's point a + s (b - a) is R's point bR + s (aR - bR).
-        xL = aL[:, None, :] + self.s[None, :, None] * (bL - aL)[:, None, :]
-        xR = bR[:, None, :] + self.s[None, :, None] * (aR - bR)[:, None, :]
+        v0 = self.verts[:, 0, :]
+        xL = (aL - v0[eL])[:, None, :] + self.s[None, :, None] * (bL - aL)[:, None, :]
+        xR = (bR - v0[eR])[:, None, :] + self.s[None, :, None] * (aR - bR)[:, None, :]
         t = bL - aL
         ln = np.linalg.norm(t, axis=1)
         self.fi_n = np.stack([t[:, 1], -t[:, 0]], axis=1) / ln[:, None]
@@ -139,12 +141,13 @@ class DGOracle:
             return
         e, f, tag = faces.T
         a, b = self._edge(e, f)
+        r = (a - self.verts[e, 0, :])[:, None, :] + self.s[None, :, None] * (b - a)[:, None, :]
         x = a[:, None, :] + self.s[None, :, None] * (b - a)[:, None, :]
         t = b - a
         ln = np.linalg.norm(t, axis=1)
         self.fb_n = np.stack([t[:, 1], -t[:, 0]], axis=1) / ln[:, None]
         self.fb_w = ln[:, None] * self.ws[None, :]
-        self.fb_psi = self.basis.eval_rows(e, x)
+        self.fb_psi = self.basis.eval_rows(e, r)
         self.fb_x = x
 
     # --------------------------------------------------------------- operator
@@ -235,10 +238,10 @@ class DGOracle:
         Uq = fn(self.xq)
         return np.einsum("eq,eqi,eqv->evi", self.wq, self.psi_q, Uq)
 
-    def state_at(self, u, x):
-        """U_h at points x [E, npts, 2] of each element."""
+    def state_at(self, u, x, local=False):
+        """U_h at points x [E, npts, 2] of each element (offsets from v0 when ``local``)."""
         u = np.asarray(u).reshape(self.E, self.nv, self.N)
-        psi = self.basis.eval(x)
+        psi = self.basis.eval(x if local else self.basis.local(x))
         return np.einsum("eqi,evi->eqv", psi, u)
 
     def freestream_state(self):
@@ -250,8 +253,7 @@ class DGOracle:
     # ------------------------------------------------------------- time steps
     def local_dt(self, u, cfl):
         """Delta t_e = CFL h / ((2p+1)(|v| + c)), h = 2 d |E| / |dE| (Eq. x3d), v at the centroid."""
-        xc = self.basis.xc[:, None, :]
-        U = self.state_at(u, xc)[:, 0, :]
+        U = self.state_at(u, self.basis.rc[:, None, :], local=True)[:, 0, :]
         rho = U[:, 0]
         vel = U[:, 1:3] / rho[:, None]
         p = (self.gamma - 1.0) * (U[:, 3] - 0.5 * rho * np.sum(vel ** 2, axis=1))
@@ -266,7 +268,7 @@ class DGOracle:
 
     def entropy_error(self, u, volume):
         """E_L2(s) of Eq. entropy_error, s = p / rho^gamma, s0 of the free stream."""
-        U = self.state_at(u, self.xq)
+        U = self.state_at(u, self.rq, local=True)
         rho = U[..., 0]
         vel = U[..., 1:3] / rho[..., None]
         p = (self.gamma - 1.0) * (U[..., 3] - 0.5 * rho * np.sum(vel ** 2, axis=-1))
