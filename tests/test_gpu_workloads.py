@@ -1,0 +1,135 @@
+"""Full-size synthetic workloads on the GPU: the bump-channel adjoint case (96 x 32, P2,
+50 PCEXP steps from seeded Gaussian blobs) and the large periodic vortex (256 x 256
+jittered split quads, P3, K = 5,242,880) in the FP64 and FP32-mixed forms."""
+import dataclasses
+import time
+
+import numpy as np
+import pytest
+
+import workloads as W
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def capi():
+    from paper_1801_06300_gb300 import build
+    build()
+    from paper_1801_06300_gb300 import capi as c
+    c.load()
+    return c
+
+
+def rel(a, b):
+    return float(np.linalg.norm(np.asarray(a) - np.asarray(b)) / np.linalg.norm(b))
+
+
+def test_bump_adjoint_full_size(capi):
+    torch = pytest.importorskip("torch")
+    from oracle.cases import blob_state
+    from oracle.dg import DGOracle
+    from paper_1801_06300_gb300.autograd import adjoint_rollout
+    case = W.case_bump_adjoint()
+    mesh, free, p, m = case.mesh, case.free, case.p, case.m
+    ctx = capi.Context(mesh, p, free, capi.PCEXP_FP64, m_max=m)
+    params = [case.blob_radius, *case.blobs.ravel()]
+
+    def u_init(fr):
+        ctx.set_physics(fr)
+        ctx.project_state(capi.PCEXP_PROJ_BLOBS, params)
+        return ctx.get_state(torch.empty(ctx.K, dtype=torch.float64, device="cuda"))
+
+    u0 = u_init(free)
+    # the projection of the seeded blobs matches the oracle's
+    dg = DGOracle(mesh, p, free)
+    uo = dg.project(lambda x: blob_state(x, free, case.blobs, case.blob_radius)).reshape(-1)
+    assert rel(u0.cpu().numpy(), uo) <= 1e-13
+    ctx.set_state(u0)
+    dt = ctx.compute_dt(case.cfl)  # held constant over the run
+    steps = case.steps
+    t0 = time.time()
+    res = adjoint_rollout(ctx, u0, dt, m, steps, params={"free": free, "names": ["mach", "alpha_deg"]},
+                          initial_state=u_init)
+    t_adj = time.time() - t0
+
+    def J_of(x, fr=free):
+        ctx.set_physics(fr)
+        u = x
+        for _ in range(steps):
+            ctx.set_state(u)
+            ctx.step(capi.PCEXP_SCHEME_PCEXP, capi.PCEXP_DT_GIVEN, dt, m, info=False)
+            u = ctx.get_state(torch.empty_like(u))
+        return ctx.functional(capi.PCEXP_FUNC_WALL_FX, u)[0]
+
+    g = res.grad_u0
+    for seed in (61, 62):
+        delta = torch.tensor(W.random_coeffs(seed, (ctx.K,)), device="cuda") * u0.abs()
+        h = 1e-6
+        fd = (J_of(u0 + h * delta) - J_of(u0 - h * delta)) / (2 * h)
+        assert abs(float(torch.dot(g, delta)) - fd) <= 1e-4 * abs(fd)
+    for name, h in (("mach", 1e-4), ("alpha_deg", 1e-2)):
+        th = getattr(free, name)
+        fp, fm = (dataclasses.replace(free, **{name: th + s * h}) for s in (1, -1))
+        fd = (J_of(u_init(fp), fp) - J_of(u_init(fm), fm)) / (2 * h)
+        assert abs(res.grad_params[name] - fd) <= 1e-4 * abs(fd), (name, res.grad_params[name], fd)
+    print(f"bump adjoint 96x32 P2, {steps} steps: J = {res.value:.6e}, "
+          f"dJ/dMach = {res.grad_params['mach']:.4e}, dJ/dalpha = {res.grad_params['alpha_deg']:.4e}, "
+          f"adjoint rollout {t_adj:.2f} s")
+    ctx.close()
+
+
+@pytest.fixture(scope="module")
+def vortex_large():
+    from oracle.cases import vortex_state
+    from oracle.dg import DGOracle
+    case = W.case_vortex2d_large()
+    dg = DGOracle(case.mesh, case.p, case.free)
+    u0 = dg.project(lambda x: vortex_state(x, case.free, case.vortex, period=20.0)).reshape(-1)
+    return case, dg, u0
+
+
+def test_vortex_large_operator_parity(capi, vortex_large):
+    """R and J v at K = 5,242,880 element by element against the oracle, to the FP64 bar
+    1e-10.  Both sides' residual of the exact free stream (zero in exact arithmetic) is
+    printed: it is the round-off floor of each on this mesh (h = 0.078 on [0, 20]^2)."""
+    from oracle.cases import freestream_state
+    case, dg, u0 = vortex_large
+    ctx = capi.Context(case.mesh, case.p, case.free, capi.PCEXP_FP64, m_max=2)
+    v = W.random_coeffs(71, (dg.K,))
+    R_or = dg.residual(u0)
+    e_r = rel(ctx.residual(u0), R_or)
+    e_j = rel(ctx.jvp(u0, v), dg.jvp(u0, v))
+    uf = dg.project(lambda x: freestream_state(x, case.free)).reshape(-1)
+    f_gpu = np.linalg.norm(ctx.residual(uf)) / np.linalg.norm(R_or)
+    f_or = np.linalg.norm(dg.residual(uf)) / np.linalg.norm(R_or)
+    print(f"vortex 256x256 P3: R rel err {e_r:.2e}, J v rel err {e_j:.2e}; "
+          f"free-stream floor GPU {f_gpu:.2e}, oracle {f_or:.2e} (of ||R||)")
+    assert e_r <= 1e-10 and e_j <= 1e-10
+    assert f_gpu <= 1e-10
+    ctx.close()
+
+
+def test_vortex_large_fp32_mixed_vs_fp64(capi, vortex_large):
+    """PCEXP at CFL 20, m = 30: FP32-mixed against FP64 (which matches the oracle to 1e-10)
+    over 50 steps; the error is stated and bounded by the 1e-5 target."""
+    case, dg, u0 = vortex_large
+    steps = 50
+    out = {}
+    for prec in (capi.PCEXP_FP64, capi.PCEXP_FP32_MIXED):
+        ctx = capi.Context(case.mesh, case.p, case.free, prec, m_max=case.m)
+        ctx.set_state(u0)
+        ctx.step(capi.PCEXP_SCHEME_PCEXP, capi.PCEXP_DT_GLOBAL_CFL, case.cfl, case.m)
+        ctx.set_state(u0)
+        ctx.synchronize()
+        t0 = time.time()
+        for _ in range(steps):
+            ctx.step(capi.PCEXP_SCHEME_PCEXP, capi.PCEXP_DT_GLOBAL_CFL, case.cfl, case.m, info=False)
+        ctx.synchronize()
+        out[prec] = (ctx.get_state(), (time.time() - t0) / steps)
+        ctx.close()
+    (u64, t64), (u32, t32) = out[capi.PCEXP_FP64], out[capi.PCEXP_FP32_MIXED]
+    e = rel(u32, u64)
+    print(f"vortex 256x256 P3 m=30 CFL 20, {steps} steps: FP32-mixed state error vs FP64 {e:.2e}, "
+          f"{t64 * 1e3:.1f} ms/step FP64, {t32 * 1e3:.1f} ms/step FP32-mixed ({t64 / t32:.2f}x)")
+    assert e <= 1e-5
