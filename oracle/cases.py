@@ -7,21 +7,30 @@ vortex, not the paper's beta = 0.2, R = 0.05 form of Sec. 5.1):
   T = T_inf - (gamma - 1) eps^2 / (8 gamma pi^2) exp(1 - r^2),
   rho = rho_inf (T / T_inf)^(1 / (gamma - 1)), p = rho T  (isentropic).
 On a periodic domain the distance uses the nearest periodic image.  The
-exact solution is this field translated with the mean velocity.
+exact solution is this field translated with the mean velocity.  In 3D the same
+field lies in the x-y plane, uniform in z, with zero z-velocity (the vortex axis
+is along z); states then have 5 components (rho, rho u, rho v, rho w, rho E).
 """
 import numpy as np
 
 
-def freestream_velocity(free):
+def freestream_velocity(free, dim: int = 2):
+    """Free-stream velocity: Ma c_inf (cos alpha, sin alpha) in the x-y plane (w = 0 in 3D)."""
     c = np.sqrt(free.gamma * free.p / free.rho)
     a = np.deg2rad(free.alpha_deg)
-    return free.mach * c * np.cos(a), free.mach * c * np.sin(a)
+    vel = (free.mach * c * np.cos(a), free.mach * c * np.sin(a))
+    return vel if dim == 2 else vel + (0.0,)
+
+
+def _conservative(rho, vel, p, gamma):
+    E = p / (gamma - 1) + 0.5 * rho * sum(v * v for v in vel)
+    return np.stack([rho] + [rho * v for v in vel] + [E], axis=-1)
 
 
 def vortex_state(x, free, vortex, t: float = 0.0, period=None):
-    """Conservative state [..., 4] of the translated isentropic vortex at points x [..., 2]."""
+    """Conservative state [..., dim+2] of the translated isentropic vortex at points x [..., dim]."""
     g = free.gamma
-    u0, v0 = freestream_velocity(free)
+    u0, v0 = freestream_velocity(free)[:2]
     dx = x[..., 0] - (vortex.center[0] + u0 * t)
     dy = x[..., 1] - (vortex.center[1] + v0 * t)
     if period is not None:
@@ -36,16 +45,14 @@ def vortex_state(x, free, vortex, t: float = 0.0, period=None):
     T = Tinf - (g - 1) * eps ** 2 / (8 * g * np.pi ** 2) * np.exp(1.0 - r2)
     rho = free.rho * (T / Tinf) ** (1.0 / (g - 1))
     p = rho * T
-    E = p / (g - 1) + 0.5 * rho * (u * u + v * v)
-    return np.stack([rho, rho * u, rho * v, E], axis=-1)
+    vel = [u, v] if x.shape[-1] == 2 else [u, v, np.zeros_like(u)]
+    return _conservative(rho, vel, p, g)
 
 
 def freestream_state(x, free):
-    u0, v0 = freestream_velocity(free)
-    E = free.p / (free.gamma - 1) + 0.5 * free.rho * (u0 * u0 + v0 * v0)
-    out = np.empty(x.shape[:-1] + (4,))
-    out[...] = [free.rho, free.rho * u0, free.rho * v0, E]
-    return out
+    vel = freestream_velocity(free, x.shape[-1])
+    one = np.ones(x.shape[:-1])
+    return _conservative(free.rho * one, [v * one for v in vel], free.p * one, free.gamma)
 
 
 def blob_state(x, free, blobs, radius):

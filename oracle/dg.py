@@ -18,137 +18,167 @@ import numpy as np
 from . import adscalar as ad
 from . import euler
 from .basis import PaperBasis, n_basis
-from .quadrature import gauss_legendre01, triangle_rule
+from .cases import freestream_velocity
+from .quadrature import gauss_legendre01, tetra_rule, triangle_rule
 
 BC_SLIP_WALL = 1
 BC_FARFIELD = 2
 
 
-def build_faces(mesh):
-    """Face list of a 2D mesh by matching edges on periodic master vertices.
+def face_vertices(dim: int, f: int):
+    """Local vertices of local face f: the face opposite vertex f, listed from vertex
+    f+1 on (mod dim+1).  For a positively oriented triangle this runs counter-clockwise
+    around the element, so the edge (a, b) has outward normal (b - a) rotated by -90
+    degrees; in 3D the outward normal is fixed by the opposite vertex."""
+    return [(f + k) % (dim + 1) for k in range(1, dim + 1)]
 
-    Local face f of triangle (v0, v1, v2) runs from vertex (f+1)%3 to (f+2)%3.
-    Returns interior (incl. periodic) faces as arrays (eL, fL, eR, fR) and
-    boundary faces as (e, f, tag).
+
+def build_faces(mesh):
+    """Face list by matching element faces on periodic master vertices.
+
+    Returns interior (incl. periodic) faces as arrays (eL, fL, eR, fR) with eL the
+    element met first (the lower index), and boundary faces as (e, f, tag).
     """
     elems = mesh.elems
     master = mesh.vert_master
-    edges = {}
+    dim = mesh.dim
+    faces = {}
     for e in range(elems.shape[0]):
-        for f in range(3):
-            a = int(elems[e, (f + 1) % 3])
-            b = int(elems[e, (f + 2) % 3])
-            key = tuple(sorted((int(master[a]), int(master[b]))))
-            edges.setdefault(key, []).append((e, f))
+        for f in range(dim + 1):
+            vs = [int(elems[e, k]) for k in face_vertices(dim, f)]
+            key = tuple(sorted(int(master[v]) for v in vs))
+            faces.setdefault(key, []).append((e, f))
     btag = {}
-    for (a, b), t in zip(mesh.bfaces, mesh.btags):
-        btag[tuple(sorted((int(a), int(b))))] = int(t)
+    for verts, t in zip(mesh.bfaces, mesh.btags):
+        btag[tuple(sorted(int(v) for v in verts))] = int(t)
     interior, boundary = [], []
-    for key, lst in edges.items():
+    for key, lst in faces.items():
         if len(lst) == 2:
             (eL, fL), (eR, fR) = lst
             interior.append((eL, fL, eR, fR))
         elif len(lst) == 1:
             e, f = lst[0]
-            a = int(elems[e, (f + 1) % 3])
-            b = int(elems[e, (f + 2) % 3])
-            k2 = tuple(sorted((a, b)))
+            k2 = tuple(sorted(int(elems[e, k]) for k in face_vertices(dim, f)))
             if k2 not in btag:
-                raise ValueError(f"unmatched boundary edge {a}-{b}")
+                raise ValueError(f"unmatched boundary face {k2}")
             boundary.append((e, f, btag[k2]))
         else:
-            raise ValueError("non-conforming mesh: edge shared by more than two elements")
-    return np.array(interior, dtype=np.int64).reshape(-1, 4), np.array(boundary, dtype=np.int64).reshape(-1, 3)
+            raise ValueError("non-conforming mesh: face shared by more than two elements")
+    return (np.array(interior, dtype=np.int64).reshape(-1, 4),
+            np.array(boundary, dtype=np.int64).reshape(-1, 3))
 
 
 class DGOracle:
-    """R(u), J(u) v, time-step sizes and diagnostics on a 2D triangle mesh."""
+    """R(u), J(u) v, time-step sizes and diagnostics on a triangle or tetrahedron mesh."""
 
     def __init__(self, mesh, p: int, free):
-        if mesh.dim != 2:
-            raise NotImplementedError("oracle residual is written for triangles")
         self.mesh = mesh
         self.p = p
         self.gamma = free.gamma
         self.free = free
-        self.dim = 2
-        self.nv = 4
-        self.N = n_basis(p, 2)
+        self.dim = dim = mesh.dim
+        self.nv = dim + 2
+        self.N = n_basis(p, dim)
         self.E = mesh.n_elem
         self.K = self.E * self.nv * self.N
         X = mesh.coords
-        verts = X[mesh.elems]  # [E, 3, 2]
+        verts = X[mesh.elems]  # [E, dim+1, dim]
         self.verts = verts
-        # volume quadrature on each physical triangle
-        rp, rw = triangle_rule(p + 1)
-        Aff = verts[:, 1:, :] - verts[:, 0:1, :]  # rows: v1 - v0, v2 - v0
-        det = Aff[:, 0, 0] * Aff[:, 1, 1] - Aff[:, 0, 1] * Aff[:, 1, 0]
+        # volume quadrature on each physical simplex
+        rp, rw = triangle_rule(p + 1) if dim == 2 else tetra_rule(p + 1)
+        Aff = verts[:, 1:, :] - verts[:, 0:1, :]  # rows: v_k - v_0 (exact in floating point)
+        if dim == 2:
+            det = Aff[:, 0, 0] * Aff[:, 1, 1] - Aff[:, 0, 1] * Aff[:, 1, 0]
+        else:
+            det = np.einsum("ed,ed->e", np.cross(Aff[:, 0], Aff[:, 1]), Aff[:, 2])
         if np.any(det <= 0):
             raise ValueError("elements must be positively oriented")
-        self.area = 0.5 * det
-        self.rq = np.einsum("qk,ekd->eqd", rp, Aff)  # offsets from v0 (exact edge vectors)
+        self.area = det / (2.0 if dim == 2 else 6.0)  # element measure |E|
+        self.rq = np.einsum("qk,ekd->eqd", rp, Aff)  # offsets from v0
         self.xq = verts[:, 0:1, :] + self.rq
         self.wq = rw[None, :] * det[:, None]
         self.basis = PaperBasis(verts, p, self.rq, self.wq)
         self.psi_q = self.basis.eval(self.rq)  # [E, nq, N]
-        self.gpsi_wq = self.basis.grad(self.rq) * self.wq[:, :, None, None]  # [E, nq, N, 2]
-        # faces
+        self.gpsi_wq = self.basis.grad(self.rq) * self.wq[:, :, None, None]  # [E, nq, N, dim]
+        # face rule: Gauss-Legendre on [0, 1] (weights sum 1) or the collapsed triangle
+        # rule (weights sum 1/2); a face point has barycentrics lam over the face vertices
+        if dim == 2:
+            s, ws = gauss_legendre01(p + 1)
+            self.face_bary = np.stack([1.0 - s, s], axis=1)
+        else:
+            st, ws = triangle_rule(p + 1)
+            self.face_bary = np.stack([1.0 - st[:, 0] - st[:, 1], st[:, 0], st[:, 1]], axis=1)
+        self.ws = ws
         interior, boundary = build_faces(mesh)
-        s, ws = gauss_legendre01(p + 1)
-        self.s, self.ws = s, ws
+        self.perimeter = np.zeros(self.E)  # |dE|
+        for f in range(dim + 1):
+            _, meas = self._face_normal(np.arange(self.E), f)
+            self.perimeter += meas
         self._setup_interior(interior)
         self._setup_boundary(boundary)
-        # perimeter for h = 2 d |E| / |dE| (Eq. x3d)
-        perim = np.zeros(self.E)
-        for f in range(3):
-            a = verts[:, (f + 1) % 3]
-            b = verts[:, (f + 2) % 3]
-            perim += np.linalg.norm(b - a, axis=1)
-        self.perimeter = perim
-        # free-stream velocity
-        c_inf = np.sqrt(self.gamma * free.p / free.rho)
-        a = np.deg2rad(free.alpha_deg)
-        self.vel_inf = [free.mach * c_inf * np.cos(a), free.mach * c_inf * np.sin(a)]
+        self.vel_inf = list(freestream_velocity(free, dim))
 
     # ------------------------------------------------------------------ faces
-    def _edge(self, e, f):
-        a = self.verts[e, (f + 1) % 3]
-        b = self.verts[e, (f + 2) % 3]
-        return a, b
+    def _face_normal(self, e, f):
+        """Outward unit normal and measure of local face f of elements e."""
+        f = np.broadcast_to(np.asarray(f), np.shape(e))
+        fv = face_vertices(self.dim, f)  # arrays of local vertex indices, one per face
+        V = self.verts[e]
+        i = np.arange(len(e))
+        a = V[i, fv[0]]
+        if self.dim == 2:
+            t = V[i, fv[1]] - a
+            meas = np.linalg.norm(t, axis=1)
+            n = np.stack([t[:, 1], -t[:, 0]], axis=1) / meas[:, None]
+        else:
+            c = np.cross(V[i, fv[1]] - a, V[i, fv[2]] - a)
+            meas = 0.5 * np.linalg.norm(c, axis=1)
+            sign = np.sign(np.einsum("ed,ed->e", c, a - V[i, f]))
+            n = c * (sign / (2.0 * meas))[:, None]
+        return n, meas
+
+    def _face_points(self, e, corners):
+        """Face points as offsets from v0 of elements e, given each element's own copies of
+        the face vertices in the L element's order (corners [F, dim, dim]):
+        x = c_0 + sum_k lam_k (c_k - c_0)."""
+        r0 = corners[:, 0, :] - self.verts[e, 0, :]
+        edges = corners[:, 1:, :] - corners[:, 0:1, :]
+        return r0[:, None, :] + np.einsum("qk,fkd->fqd", self.face_bary[:, 1:], edges)
 
     def _setup_interior(self, faces):
         self.fi = faces
         if len(faces) == 0:
             return
         eL, fL, eR, fR = faces.T
-        aL, bL = self._edge(eL, fL)
-        aR, bR = self._edge(eR, fR)
-        # L traverses a -> b; R traverses its copy of the edge in the opposite sense,
-        # so L's point a + s (b - a) is R's point bR + s (aR - bR).
-        v0 = self.verts[:, 0, :]
-        xL = (aL - v0[eL])[:, None, :] + self.s[None, :, None] * (bL - aL)[:, None, :]
-        xR = (bR - v0[eR])[:, None, :] + self.s[None, :, None] * (aR - bR)[:, None, :]
-        t = bL - aL
-        ln = np.linalg.norm(t, axis=1)
-        self.fi_n = np.stack([t[:, 1], -t[:, 0]], axis=1) / ln[:, None]
-        self.fi_w = ln[:, None] * self.ws[None, :]
-        self.fi_psiL = self.basis.eval_rows(eL, xL)  # [F, nfq, N]
-        self.fi_psiR = self.basis.eval_rows(eR, xR)
+        master = self.mesh.vert_master
+        elems = self.mesh.elems
+        F = len(faces)
+        cornL = np.empty((F, self.dim, self.dim))
+        cornR = np.empty((F, self.dim, self.dim))
+        for i in range(F):
+            lv = [int(elems[eL[i], k]) for k in face_vertices(self.dim, fL[i])]
+            rloc = {int(master[elems[eR[i], k]]): k for k in face_vertices(self.dim, fR[i])}
+            for j, v in enumerate(lv):
+                cornL[i, j] = self.verts[eL[i], face_vertices(self.dim, fL[i])[j]]
+                cornR[i, j] = self.verts[eR[i], rloc[int(master[v])]]
+        n, meas = self._face_normal(eL, fL)
+        self.fi_n = n
+        self.fi_w = (meas * (2.0 if self.dim == 3 else 1.0))[:, None] * self.ws[None, :]
+        self.fi_psiL = self.basis.eval_rows(eL, self._face_points(eL, cornL))  # [F, nfq, N]
+        self.fi_psiR = self.basis.eval_rows(eR, self._face_points(eR, cornR))
 
     def _setup_boundary(self, faces):
         self.fb = faces
         if len(faces) == 0:
             return
         e, f, tag = faces.T
-        a, b = self._edge(e, f)
-        r = (a - self.verts[e, 0, :])[:, None, :] + self.s[None, :, None] * (b - a)[:, None, :]
-        x = a[:, None, :] + self.s[None, :, None] * (b - a)[:, None, :]
-        t = b - a
-        ln = np.linalg.norm(t, axis=1)
-        self.fb_n = np.stack([t[:, 1], -t[:, 0]], axis=1) / ln[:, None]
-        self.fb_w = ln[:, None] * self.ws[None, :]
+        corn = np.stack([self.verts[e[i], face_vertices(self.dim, f[i])] for i in range(len(faces))])
+        n, meas = self._face_normal(e, f)
+        self.fb_n = n
+        self.fb_w = (meas * (2.0 if self.dim == 3 else 1.0))[:, None] * self.ws[None, :]
+        r = self._face_points(e, corn)
         self.fb_psi = self.basis.eval_rows(e, r)
-        self.fb_x = x
+        self.fb_x = self.verts[e, 0, :][:, None, :] + r
 
     # --------------------------------------------------------------- operator
     def unflat(self, u):
@@ -170,7 +200,7 @@ class DGOracle:
             eL, fL, eR, fR = self.fi.T
             UL = ad.lin(lambda a: np.einsum("fqi,fvi->fqv", self.fi_psiL, a[eL]), u)
             UR = ad.lin(lambda a: np.einsum("fqi,fvi->fqv", self.fi_psiR, a[eR]), u)
-            n = np.broadcast_to(self.fi_n[:, None, :], UL.shape[:2] + (2,))
+            n = np.broadcast_to(self.fi_n[:, None, :], UL.shape[:2] + (self.dim,))
             Fn = euler.roe_flux(UL, UR, n, g)  # [F, nfq, nv]
             Fn = Fn * self.fi_w[:, :, None]
             cL = ad.lin(lambda a: np.einsum("fqi,fqv->fvi", self.fi_psiL, a), Fn)
@@ -180,7 +210,7 @@ class DGOracle:
         if faces and len(self.fb):
             e, f, tag = self.fb.T
             UL = ad.lin(lambda a: np.einsum("fqi,fvi->fqv", self.fb_psi, a[e]), u)
-            n = np.broadcast_to(self.fb_n[:, None, :], UL.shape[:2] + (2,))
+            n = np.broadcast_to(self.fb_n[:, None, :], UL.shape[:2] + (self.dim,))
             wall = (tag == BC_SLIP_WALL)[:, None]
             Ug_w = euler.ghost_slip_wall(UL, n, g)
             Ug_f = euler.ghost_farfield(UL, n, g, self.free.rho, self.vel_inf, self.free.p)
@@ -225,7 +255,7 @@ class DGOracle:
         e, f, tag = self.fb.T
         UL = ad.lin(lambda a: np.einsum("fqi,fvi->fqv", self.fb_psi, a[e]), u)
         rho, vel, p, E = euler.primitives(UL, self.gamma)
-        na = self.fb_n[:, 0] * direction[0] + self.fb_n[:, 1] * direction[1]
+        na = sum(self.fb_n[:, k] * direction[k] for k in range(self.dim))
         wgt = self.fb_w * (na * (tag == BC_SLIP_WALL))[:, None]
         tot = p * wgt
         if isinstance(tot, ad.Dual):
@@ -234,12 +264,12 @@ class DGOracle:
 
     # ------------------------------------------------------------ projections
     def project(self, fn):
-        """L2 projection of a pointwise state function fn(x [E,nq,2]) -> [E,nq,nv]."""
+        """L2 projection of a pointwise state function fn(x [E,nq,dim]) -> [E,nq,nv]."""
         Uq = fn(self.xq)
         return np.einsum("eq,eqi,eqv->evi", self.wq, self.psi_q, Uq)
 
     def state_at(self, u, x, local=False):
-        """U_h at points x [E, npts, 2] of each element (offsets from v0 when ``local``)."""
+        """U_h at points x [E, npts, dim] of each element (offsets from v0 when ``local``)."""
         u = np.asarray(u).reshape(self.E, self.nv, self.N)
         psi = self.basis.eval(x if local else self.basis.local(x))
         return np.einsum("eqi,evi->eqv", psi, u)
@@ -247,16 +277,16 @@ class DGOracle:
     def freestream_state(self):
         f = self.free
         vel = self.vel_inf
-        E = f.p / (f.gamma - 1.0) + 0.5 * f.rho * (vel[0] ** 2 + vel[1] ** 2)
-        return np.array([f.rho, f.rho * vel[0], f.rho * vel[1], E])
+        E = f.p / (f.gamma - 1.0) + 0.5 * f.rho * sum(v * v for v in vel)
+        return np.array([f.rho] + [f.rho * v for v in vel] + [E])
 
     # ------------------------------------------------------------- time steps
     def local_dt(self, u, cfl):
         """Delta t_e = CFL h / ((2p+1)(|v| + c)), h = 2 d |E| / |dE| (Eq. x3d), v at the centroid."""
         U = self.state_at(u, self.basis.rc[:, None, :], local=True)[:, 0, :]
         rho = U[:, 0]
-        vel = U[:, 1:3] / rho[:, None]
-        p = (self.gamma - 1.0) * (U[:, 3] - 0.5 * rho * np.sum(vel ** 2, axis=1))
+        vel = U[:, 1:1 + self.dim] / rho[:, None]
+        p = (self.gamma - 1.0) * (U[:, self.dim + 1] - 0.5 * rho * np.sum(vel ** 2, axis=1))
         c = np.sqrt(self.gamma * p / rho)
         h = 2.0 * self.dim * self.area / self.perimeter
         return cfl * h / ((2 * self.p + 1) * (np.linalg.norm(vel, axis=1) + c))
@@ -270,12 +300,25 @@ class DGOracle:
         """E_L2(s) of Eq. entropy_error, s = p / rho^gamma, s0 of the free stream."""
         U = self.state_at(u, self.rq, local=True)
         rho = U[..., 0]
-        vel = U[..., 1:3] / rho[..., None]
-        p = (self.gamma - 1.0) * (U[..., 3] - 0.5 * rho * np.sum(vel ** 2, axis=-1))
+        vel = U[..., 1:1 + self.dim] / rho[..., None]
+        p = (self.gamma - 1.0) * (U[..., self.dim + 1] - 0.5 * rho * np.sum(vel ** 2, axis=-1))
         s = p / rho ** self.gamma
         s0 = self.free.p / self.free.rho ** self.gamma
         val = np.sum(self.wq * (s / s0) ** 2) / volume - 1.0
         return np.sqrt(max(val, 0.0))
+
+    def l2_error(self, u, exact):
+        """||U_h - U_exact||_L2 over the domain and all conservative variables: the square
+        root of sum_e sum_q w_q sum_v (U_h - U_ex)_v^2 at the volume points, exact(x) being
+        the pointwise exact state (the vortex-error functional of the 3D case)."""
+        uu = self.unflat(u)
+        Uq = ad.lin(lambda a: np.einsum("eqi,evi->eqv", self.psi_q, a), uu)
+        D = Uq - exact(self.xq)
+        tot = (D * D) * self.wq[:, :, None]
+        if isinstance(tot, ad.Dual):
+            v = np.sqrt(np.sum(tot.val))
+            return ad.Dual(v, 0.5 * np.sum(tot.der) / v)
+        return np.sqrt(np.sum(tot))
 
 
 def _flatten(R):

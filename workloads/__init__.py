@@ -172,48 +172,71 @@ def bump_channel(nx: int, ny: int, jitter: float = 0.0, seed: int = 0,
                 name=f"bump{nx}x{ny}", volume=3.0 - 0.5 * bump_h)
 
 
-def periodic_cube_kuhn(n: int, length: float, jitter: float = 0.0, seed: int = 0) -> Mesh:
-    """n^3 cubes on the periodic cube [0, length]^3, each split into 6 Kuhn tetrahedra.
+def periodic_cube_kuhn(n: int, length: float, jitter: float = 0.0, seed: int = 0,
+                       periodic: bool = True) -> Mesh:
+    """n^3 cubes on the cube [0, length]^3, each split into 6 Kuhn tetrahedra.
 
-    The six tetrahedra share the cube's main diagonal, so neighbouring cubes
-    meet conformingly.  Vertex jitter works as in ``periodic_square``.
+    The six tetrahedra of a cube share its main diagonal, so neighbouring cubes
+    meet conformingly.  Vertex jitter works as in ``periodic_square`` (periodic
+    images share one offset).  With ``periodic=False`` the outer faces are far-field
+    boundary faces and boundary vertices are not moved.  Tetrahedra are ordered by
+    cube (x fastest) and, within a cube, by the path order of the unit steps.
     """
     h = length / n
     nv = n + 1
     idx = np.arange(nv)
     kk, jj, ii = np.meshgrid(idx, idx, idx, indexing="ij")
     ii, jj, kk = ii.ravel(), jj.ravel(), kk.ravel()
-    master = (((kk % n) * n + (jj % n)) * n + (ii % n)).astype(np.int32)
-    off = np.zeros((n ** 3, 3))
-    if jitter > 0.0:
-        off = jitter * h * uniform_pm(seed, 3 * n ** 3).reshape(n ** 3, 3)
-    coords = np.stack([ii * h + off[master, 0], jj * h + off[master, 1], kk * h + off[master, 2]], axis=1)
-    vid = lambda i, j, k: (k * nv + j) * nv + i  # noqa: E731
-    # Kuhn simplices: paths from (0,0,0) to (1,1,1) adding one unit vector at a time.
+    if periodic:
+        master = (((kk % n) * n + (jj % n)) * n + (ii % n)).astype(np.int32)
+        off = np.zeros((n ** 3, 3))
+        if jitter > 0.0:
+            off = jitter * h * uniform_pm(seed, 3 * n ** 3).reshape(n ** 3, 3)
+        off = off[master]
+    else:
+        master = np.arange(nv ** 3, dtype=np.int32)
+        off = np.zeros((nv ** 3, 3))
+        if jitter > 0.0:
+            off = jitter * h * uniform_pm(seed, 3 * nv ** 3).reshape(nv ** 3, 3)
+            inner = (ii > 0) & (ii < n) & (jj > 0) & (jj < n) & (kk > 0) & (kk < n)
+            off[~inner] = 0.0
+    coords = np.stack([ii * h + off[:, 0], jj * h + off[:, 1], kk * h + off[:, 2]], axis=1)
+    ci, cj, ck = np.meshgrid(np.arange(n), np.arange(n), np.arange(n), indexing="ij")
+    base = np.stack([ck.ravel(), cj.ravel(), ci.ravel()], axis=1)  # (i, j, k), x fastest
+    base = base[np.lexsort((base[:, 0], base[:, 1], base[:, 2]))]
+    vid = lambda p: (p[:, 2] * nv + p[:, 1]) * nv + p[:, 0]  # noqa: E731
+    # Kuhn simplices: paths from (0,0,0) to (1,1,1) adding one unit vector at a time
     perms = [(0, 1, 2), (0, 2, 1), (1, 0, 2), (1, 2, 0), (2, 0, 1), (2, 1, 0)]
-    unit = np.eye(3, dtype=int)
-    tets = np.empty((6 * n ** 3, 4), np.int32)
-    t = 0
-    for k in range(n):
-        for j in range(n):
-            for i in range(n):
-                base = np.array([i, j, k])
-                for perm in perms:
-                    p0 = base
-                    p1 = p0 + unit[perm[0]]
-                    p2 = p1 + unit[perm[1]]
-                    p3 = p2 + unit[perm[2]]
-                    vs = [vid(*p0), vid(*p1), vid(*p2), vid(*p3)]
-                    # orient positively
-                    a = coords[vs[1]] - coords[vs[0]]
-                    b = coords[vs[2]] - coords[vs[0]]
-                    c = coords[vs[3]] - coords[vs[0]]
-                    if np.dot(np.cross(a, b), c) < 0:
-                        vs[2], vs[3] = vs[3], vs[2]
-                    tets[t] = vs
-                    t += 1
-    return Mesh(dim=3, coords=coords, elems=tets, vert_master=master,
-                bfaces=np.zeros((0, 3), np.int32), btags=np.zeros(0, np.int32),
+    unit = np.eye(3, dtype=np.int64)
+    tets = np.empty((n ** 3, 6, 4), np.int32)
+    for t, perm in enumerate(perms):
+        p0 = base
+        p1 = p0 + unit[perm[0]]
+        p2 = p1 + unit[perm[1]]
+        p3 = p2 + unit[perm[2]]
+        tets[:, t] = np.stack([vid(p0), vid(p1), vid(p2), vid(p3)], axis=1)
+    tets = tets.reshape(-1, 4)
+    # orient positively
+    X = coords[tets]
+    vol = np.einsum("ed,ed->e", np.cross(X[:, 1] - X[:, 0], X[:, 2] - X[:, 0]), X[:, 3] - X[:, 0])
+    neg = vol < 0
+    tets[neg, 2], tets[neg, 3] = tets[neg, 3].copy(), tets[neg, 2].copy()
+    bfaces = np.zeros((0, 3), np.int32)
+    btags = np.zeros(0, np.int32)
+    if not periodic:
+        # faces of tetrahedra that lie on the outer boundary
+        fl = []
+        for f in range(4):
+            fv = tets[:, [(f + 1) % 4, (f + 2) % 4, (f + 3) % 4]]
+            P = np.stack([ii[fv], jj[fv], kk[fv]], axis=-1)  # [E, 3, 3] lattice indices
+            on = np.zeros(len(tets), bool)
+            for d in range(3):
+                for side in (0, n):
+                    on |= np.all(P[:, :, d] == side, axis=1)
+            fl.append(fv[on])
+        bfaces = np.concatenate(fl).astype(np.int32)
+        btags = np.full(len(bfaces), BC_FARFIELD, np.int32)
+    return Mesh(dim=3, coords=coords, elems=tets, vert_master=master, bfaces=bfaces, btags=btags,
                 name=f"kuhn{n}^3", volume=length ** 3)
 
 
@@ -294,6 +317,14 @@ def case_bump_adjoint(nx: int = 96, ny: int = 32, seed: int = 4) -> Case:
     return Case("bump2d_adjoint", bump_channel(nx, ny, 0.15, 1), p=2, m=30,
                 free=Freestream(mach=0.5, alpha_deg=0.0), cfl=5.0, steps=50,
                 blobs=blob_params(seed))
+
+
+def case_vortex3d(n: int = 48, p: int = 2, seed: int = 5) -> Case:
+    """3D isentropic vortex (axis along z) on periodic [0,10]^3: n^3 cubes as Kuhn tetrahedra
+    (6 n^3 elements, 663,552 at n = 48) with +-10% jitter, P2, m = 30, CFL 10, 50 steps."""
+    return Case(f"vortex3d_p{p}_n{n}", periodic_cube_kuhn(n, 10.0, 0.10, seed), p=p, m=30,
+                free=Freestream(mach=0.5, alpha_deg=45.0), vortex=Vortex(5.0, (5.0, 5.0)),
+                cfl=10.0, steps=50)
 
 
 def random_coeffs(seed: int, shape, scale: float = 1.0) -> np.ndarray:
