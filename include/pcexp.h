@@ -68,17 +68,21 @@ extern "C" {
                                  unit pseudo-step (reading for steady runs) */
 
 #define PCEXP_PROJ_FREESTREAM 0 /* params: none */
-#define PCEXP_PROJ_VORTEX 1     /* params: eps, xc, yc, period (0 = none) */
+#define PCEXP_PROJ_VORTEX 1     /* params: eps, xc, yc, period (0 = none); in 3D the planar
+                                   vortex, uniform in z, zero z-velocity */
 #define PCEXP_PROJ_BLOBS 2      /* params: radius, then n x (x, y, a_rho, a_p) */
 
 #define PCEXP_MAX_KRYLOV 32 /* largest supported m (the paper uses m = 30) */
 
-/* Mesh of positively oriented triangles (dim = 2).
+/* Mesh of positively oriented triangles (dim = 2, orders p = 0..3) or tetrahedra
+ * (dim = 3, p = 0..2; higher orders return PCEXP_ERR_UNSUPPORTED).
  * coords [n_vert][dim]; elem_vert [n_elem][dim+1]; vert_master [n_vert] maps
  * each vertex to its periodic master (NULL: no periodic identification);
  * bface_vert [n_bface][dim] + bface_tag [n_bface] list the tagged boundary
- * edges.  Edges are matched on master vertices; an edge with no partner and
- * no tag is a PCEXP_ERR_MESH. */
+ * faces (edges in 2D, triangles in 3D).  Faces are matched on master vertices;
+ * a face with no partner and no tag, or shared by more than two elements, is a
+ * PCEXP_ERR_MESH.  A face's quadrature points are those of its L element (the
+ * lower element index) in that element's local face-vertex order. */
 typedef struct pcexp_mesh {
   int32_t dim;
   int64_t n_vert;
@@ -215,14 +219,26 @@ int pcexp_march_steady(pcexp_ctx* ctx, int scheme, double cfl_max, double decade
                        int max_iter, int m, pcexp_steady_info* info);
 
 /* Output functionals of a state U (not part of the paper's scheme; they seed
- * adjoint runs): the pressure force on the slip walls,
- *   J = sum over wall faces and their Gauss points of |e| w_q p(U) (n . a),
- * a = (1, 0) for PCEXP_FUNC_WALL_FX, (0, 1) for PCEXP_FUNC_WALL_FY, n the outward
- * normal of the fluid element.  grad (nullable) receives dJ/dU in the basis of U.
- * FP64 contexts only. */
+ * adjoint runs):
+ *  - PCEXP_FUNC_WALL_FX / _FY / _FZ (FZ on tetrahedra only): the pressure force on
+ *    the slip walls, J = sum over wall faces and their Gauss points of
+ *    |f| w_q p(U) (n . a), a the unit axis, n the outward normal of the fluid element;
+ *  - PCEXP_FUNC_VORTEX_L2: the L2 error against the translated isentropic vortex,
+ *    J = (sum_e sum_q w_q |U_h(x_q) - U_exact(x_q)|^2)^(1/2) over all conservative
+ *    variables at the volume points; params = {eps, x_c, y_c, period (<= 0: none), t}
+ *    (the vortex of PCEXP_PROJ_VORTEX advected by the free stream for time t).
+ * grad (nullable) receives dJ/dU in the basis of U; it is computed on the device and
+ * for the vortex error divided by J (J > 0 assumed).  The wall-force gradient on an
+ * element with three or more wall faces sums its contributions in arrival order.
+ * pcexp_functional covers the kinds without parameters.  FP64 contexts only;
+ * INVALID_ARG for an unknown kind or missing parameters, UNSUPPORTED for FP32. */
 #define PCEXP_FUNC_WALL_FX 0
 #define PCEXP_FUNC_WALL_FY 1
+#define PCEXP_FUNC_VORTEX_L2 2
+#define PCEXP_FUNC_WALL_FZ 3
 int pcexp_functional(pcexp_ctx* ctx, int kind, const double* U, double* value, double* grad, int on_device);
+int pcexp_functional_params(pcexp_ctx* ctx, int kind, const double* params, int n_params, const double* U,
+                            double* value, double* grad, int on_device);
 
 /* Replaces the free stream (Mach number, angle, density, pressure, gamma) used
  * by the far-field boundary condition; the mesh and state are kept. */

@@ -38,6 +38,8 @@ PCEXP_PROJ_BLOBS = 2
 PCEXP_MAX_KRYLOV = 32
 PCEXP_FUNC_WALL_FX = 0
 PCEXP_FUNC_WALL_FY = 1
+PCEXP_FUNC_VORTEX_L2 = 2
+PCEXP_FUNC_WALL_FZ = 3
 KERNEL_CLASSES = ["residual_face", "residual_elem", "jvp_face", "jvp_elem", "cgs_norm", "cgs_proj",
                   "cgs_upd_proj", "cgs_upd_norm", "phi", "axpy", "dt", "other", "linearize"]
 
@@ -94,6 +96,7 @@ SIGNATURES = {
                                      C.POINTER(pcexp_steady_info)]),
     "pcexp_output": (C.c_int, [_P, C.c_int, _D]),
     "pcexp_functional": (C.c_int, [_P, C.c_int, _P, _D, _P, C.c_int]),
+    "pcexp_functional_params": (C.c_int, [_P, C.c_int, _D, C.c_int, _P, _D, _P, C.c_int]),
     "pcexp_set_physics": (C.c_int, [_P, C.POINTER(pcexp_physics)]),
     "pcexp_synchronize": (C.c_int, [_P]),
     "pcexp_residual_noalloc": (C.c_int, [_P, _P, _P]),
@@ -303,12 +306,18 @@ class Context:
         return dict(iterations=inf.iterations, res_first=inf.res_first, res_last=inf.res_last,
                     converged=bool(inf.converged))
 
-    def functional(self, kind: int, U, grad=None):
-        """(value, gradient) of an output functional at U; gradient is None unless grad is given."""
+    def functional(self, kind: int, U, grad=None, params=None):
+        """(value, gradient) of an output functional at U; gradient is None unless grad is given.
+        params: the functional's parameters (PCEXP_FUNC_VORTEX_L2: eps, x_c, y_c, period, t)."""
         v = C.c_double()
         pu, dev = _ptr(U)
         pg = _ptr(grad)[0] if grad is not None else None
-        check(self.lib.pcexp_functional(self.ctx, kind, pu, C.byref(v), pg, dev), "pcexp_functional")
+        if params is None:
+            check(self.lib.pcexp_functional(self.ctx, kind, pu, C.byref(v), pg, dev), "pcexp_functional")
+        else:
+            prm = np.ascontiguousarray(params, np.float64)
+            check(self.lib.pcexp_functional_params(self.ctx, kind, prm.ctypes.data_as(_D), len(prm), pu,
+                                                   C.byref(v), pg, dev), "pcexp_functional_params")
         return v.value, grad
 
     def set_physics(self, free):

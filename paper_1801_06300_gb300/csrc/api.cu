@@ -22,7 +22,7 @@ struct pcexp_ctx {
   int device = 0;
   cudaStream_t st = nullptr;
   bool fp32 = false;
-  int p = 0, nb = 0, nq = 0, nfq = 0, nv = 4;
+  int dim = 2, p = 0, nb = 0, nq = 0, nfq = 0, nv = 4;
   int64_t E = 0, F = 0, K = 0, Kp = 0;
   int m_max = 0;
   double eta = 0;
@@ -39,7 +39,8 @@ struct pcexp_ctx {
   void *V = nullptr, *w = nullptr, *tmp = nullptr, *delta = nullptr, *G = nullptr, *dte = nullptr;
   double *io64a = nullptr, *io64b = nullptr;
   void *Avol = nullptr, *Bface = nullptr;  // point Jacobians at the linearisation state
-  void* GT = nullptr;                      // adjoint face scratch [F][nfq][8]
+  void* GT = nullptr;                      // adjoint face scratch [F][nfq][2 nv]
+  double* xq = nullptr;                    // physical volume points [E][nq][dim] (first vortex functional)
   // reverse-step work space (FP64 contexts, allocated by the first backward call)
   double *b_un = nullptr, *b_us = nullptr, *b_dl = nullptr, *b_V1 = nullptr, *b_Vb = nullptr;
   double *b_w1 = nullptr, *b_w0 = nullptr, *b_wb2 = nullptr, *b_wb1 = nullptr, *b_wb0 = nullptr;
@@ -126,11 +127,13 @@ DGData<T> dgdata(const pcexp_ctx* c) {
   d.fel = c->fel;
   d.floc = c->floc;
   d.fgeo = reinterpret_cast<const T*>(c->fgeo);
+  const int D = c->dim, NF = D + 1, NPERM = D == 2 ? 2 : 6;
   d.Bv = tabs;
   d.Dv = d.Bv + nq * nb;
-  d.Bf = d.Dv + 2 * nq * nb;
-  d.Wf = d.Bf + 3 * nfq * nb;
+  d.Bf = d.Dv + D * nq * nb;
+  d.Wf = d.Bf + NF * NPERM * nfq * nb;
   d.Bc = d.Wf + nfq;
+  d.Wv = d.Bc + nb;
   d.E = c->E;
   d.F = c->F;
   const double a = c->phys.alpha_deg * M_PI / 180.0;
@@ -138,9 +141,11 @@ DGData<T> dgdata(const pcexp_ctx* c) {
   d.fs.gamma = (T)c->phys.gamma;
   d.fs.rho = (T)c->phys.rho_inf;
   d.fs.p = (T)c->phys.p_inf;
-  d.fs.u = (T)(c->phys.mach * cinf * std::cos(a));
-  d.fs.v = (T)(c->phys.mach * cinf * std::sin(a));
+  d.fs.vel[0] = (T)(c->phys.mach * cinf * std::cos(a));
+  d.fs.vel[1] = (T)(c->phys.mach * cinf * std::sin(a));
+  d.fs.vel[2] = T(0);
   d.p = c->p;
+  d.dim = D;
   return d;
 }
 
@@ -545,9 +550,11 @@ int arnoldi_abi(pcexp_ctx* c, const double* U, const double* b, int m, double* V
 }
 
 // Host L2 projection of an analytic state onto the internal basis:
-// u_j = sqrt(det) sum_q w^_q U(x_q) phi^_j(xi_q).
+// u_j = sqrt(det) sum_q w^_q U(x_q) phi^_j(xi_q).  The vortex and the blobs lie in
+// the x-y plane (z-velocity zero in 3D).
 int project_host(pcexp_ctx* c, int kind, const double* prm, int np, std::vector<double>& u) {
   const Setup& s = c->host;
+  const int D = c->dim, NV = c->nv, GEO = D == 2 ? 8 : 12;
   const double g = c->phys.gamma;
   const double a = c->phys.alpha_deg * M_PI / 180.0;
   const double cinf = std::sqrt(g * c->phys.p_inf / c->phys.rho_inf);
@@ -558,9 +565,9 @@ int project_host(pcexp_ctx* c, int kind, const double* prm, int np, std::vector<
   if (kind < 0 || kind > 2) return PCEXP_ERR_INVALID_ARG;
   u.assign(c->E * c->nv * c->nb, 0.0);
   for (int64_t e = 0; e < c->E; ++e) {
-    const double sd = s.geo[8 * e + 4];
+    const double sd = s.geo[GEO * e + D * D];
     for (int q = 0; q < c->nq; ++q) {
-      const double x = s.xqphys[(e * c->nq + q) * 2], y = s.xqphys[(e * c->nq + q) * 2 + 1];
+      const double x = s.xqphys[(e * c->nq + q) * D], y = s.xqphys[(e * c->nq + q) * D + 1];
       double rho = rinf, uu = u0, vv = v0, p = pinf;
       if (kind == PCEXP_PROJ_VORTEX) {
         const double eps = prm[0], period = prm[3];
@@ -586,8 +593,9 @@ int project_host(pcexp_ctx* c, int kind, const double* prm, int np, std::vector<
           p += bb[3] * wgt;
         }
       }
-      const double U[4] = {rho, rho * uu, rho * vv, p / (g - 1) + 0.5 * rho * (uu * uu + vv * vv)};
-      for (int v = 0; v < 4; ++v)
+      double U[5] = {rho, rho * uu, rho * vv, 0.0, 0.0};
+      U[NV - 1] = p / (g - 1) + 0.5 * rho * (uu * uu + vv * vv);
+      for (int v = 0; v < NV; ++v)
         for (int j = 0; j < c->nb; ++j)
           u[(e * c->nv + v) * c->nb + j] += sd * s.Wv[q] * U[v] * s.Bv[q * c->nb + j];
     }
@@ -621,6 +629,8 @@ int create_impl(pcexp_ctx* c, const pcexp_mesh* mesh, int p, const pcexp_physics
     return r;
   }
   const Setup& s = c->host;
+  c->dim = s.dim;
+  c->nv = s.nv;
   c->p = p;
   c->nb = s.nb;
   c->nq = s.nq;
@@ -642,6 +652,7 @@ int create_impl(pcexp_ctx* c, const pcexp_mesh* mesh, int p, const pcexp_physics
   tabs.insert(tabs.end(), s.Bf.begin(), s.Bf.end());
   tabs.insert(tabs.end(), s.Wf.begin(), s.Wf.end());
   tabs.insert(tabs.end(), s.Bc.begin(), s.Bc.end());
+  tabs.insert(tabs.end(), s.Wv.begin(), s.Wv.end());
   const size_t es = c->fp32 ? sizeof(float) : sizeof(double);
   if (c->fp32) {
     PCEXP_TRY(upload<float>(c, &c->tabs, tabs));
@@ -684,11 +695,12 @@ int create_impl(pcexp_ctx* c, const pcexp_mesh* mesh, int p, const pcexp_physics
   PCEXP_TRY(valloc(&c->w, Kp));
   PCEXP_TRY(valloc(&c->tmp, Kp));
   PCEXP_TRY(valloc(&c->delta, Kp));
-  PCEXP_TRY(valloc(&c->G, (size_t)(c->F > 0 ? c->F : 1) * c->nfq * 4));
+  const size_t nfp = (size_t)(c->F > 0 ? c->F : 1) * c->nfq, nv = (size_t)c->nv;
+  PCEXP_TRY(valloc(&c->G, nfp * nv));
   PCEXP_TRY(valloc(&c->dte, c->E));
-  PCEXP_TRY(valloc(&c->Avol, (size_t)32 * c->E * c->nq));
-  PCEXP_TRY(valloc(&c->GT, (size_t)8 * (c->F > 0 ? c->F : 1) * c->nfq));
-  PCEXP_TRY(valloc(&c->Bface, (size_t)32 * (c->F > 0 ? c->F : 1) * c->nfq));
+  PCEXP_TRY(valloc(&c->Avol, (size_t)c->dim * nv * nv * c->E * c->nq));
+  PCEXP_TRY(valloc(&c->GT, 2 * nv * nfp));
+  PCEXP_TRY(valloc(&c->Bface, 2 * nv * nv * nfp));
   PCEXP_TRY(dalloc(c, &c->io64a, Kp));
   PCEXP_TRY(dalloc(c, &c->io64b, Kp));
   PCEXP_TRY(dalloc(c, &c->ks, 1));
@@ -1016,25 +1028,48 @@ int pcexp_jvp_state_adjoint(pcexp_ctx* c, const double* U, const double* v, cons
   return PCEXP_OK;
 }
 
-int pcexp_functional(pcexp_ctx* c, int kind, const double* U, double* value, double* grad, int on_device) {
+int pcexp_functional_params(pcexp_ctx* c, int kind, const double* params, int n_params, const double* U,
+                            double* value, double* grad, int on_device) {
   PCEXP_TRY(check_ctx(c));
   if (!U || !value) return PCEXP_ERR_INVALID_ARG;
-  if (kind != PCEXP_FUNC_WALL_FX && kind != PCEXP_FUNC_WALL_FY) return PCEXP_ERR_INVALID_ARG;
+  if (kind != PCEXP_FUNC_WALL_FX && kind != PCEXP_FUNC_WALL_FY && kind != PCEXP_FUNC_WALL_FZ &&
+      kind != PCEXP_FUNC_VORTEX_L2)
+    return PCEXP_ERR_INVALID_ARG;
+  if (kind == PCEXP_FUNC_WALL_FZ && c->dim != 3) return PCEXP_ERR_INVALID_ARG;
+  if (kind == PCEXP_FUNC_VORTEX_L2 && (!params || n_params < 5)) return PCEXP_ERR_INVALID_ARG;
   if (c->fp32) {
     g_last_error = "output functionals are provided for the FP64 form";
     return PCEXP_ERR_UNSUPPORTED;
   }
   double* a = reinterpret_cast<double*>(c->tmp);
   double* g = reinterpret_cast<double*>(c->w);
+  const DGData<double> d = dgdata<double>(c);
   PCEXP_TRY(import_vec<double>(c, U, on_device, a));
-  PCEXP_CK(cudaMemsetAsync(g, 0, (size_t)c->Kp * sizeof(double), c->st));
-  const double ax = kind == PCEXP_FUNC_WALL_FX ? 1.0 : 0.0, ay = 1.0 - ax;
-  PCEXP_CK(launch_wall_force<double>(dgdata<double>(c), c->host.F_interior, a, ax, ay, g, &c->ss->dtmin_scratch,
-                                     c->partials, &c->ss->counter, c->st));
+  if (kind == PCEXP_FUNC_VORTEX_L2) {
+    if (!c->xq) {
+      PCEXP_TRY(dalloc(c, &c->xq, c->host.xqphys.size()));
+      PCEXP_CK(cudaMemcpyAsync(c->xq, c->host.xqphys.data(), c->host.xqphys.size() * sizeof(double),
+                               cudaMemcpyHostToDevice, c->st));
+    }
+    PCEXP_CK(launch_vortex_error<double>(d, a, c->xq, params, grad ? g : nullptr, &c->ss->dtmin_scratch,
+                                         c->partials, &c->ss->counter, c->st));
+    if (grad) PCEXP_CK(launch_scale_by_inverse(g, &c->ss->dtmin_scratch, c->Kp, c->st));
+  } else {
+    PCEXP_CK(cudaMemsetAsync(g, 0, (size_t)c->Kp * sizeof(double), c->st));
+    const double ax = kind == PCEXP_FUNC_WALL_FX ? 1.0 : 0.0, ay = kind == PCEXP_FUNC_WALL_FY ? 1.0 : 0.0;
+    const double az = kind == PCEXP_FUNC_WALL_FZ ? 1.0 : 0.0;
+    PCEXP_CK(launch_wall_force<double>(d, c->host.F_interior, a, ax, ay, az, g, &c->ss->dtmin_scratch, c->partials,
+                                       &c->ss->counter, c->st));
+  }
   PCEXP_CK(cudaMemcpyAsync(value, &c->ss->dtmin_scratch, sizeof(double), cudaMemcpyDeviceToHost, c->st));
   if (grad) PCEXP_TRY(export_vec<double>(c, g, grad, on_device));
   PCEXP_CK(cudaStreamSynchronize(c->st));
   return PCEXP_OK;
+}
+
+int pcexp_functional(pcexp_ctx* c, int kind, const double* U, double* value, double* grad, int on_device) {
+  if (kind == PCEXP_FUNC_VORTEX_L2) return PCEXP_ERR_INVALID_ARG;  // needs its parameters
+  return pcexp_functional_params(c, kind, nullptr, 0, U, value, grad, on_device);
 }
 
 int pcexp_set_physics(pcexp_ctx* c, const pcexp_physics* phys) {

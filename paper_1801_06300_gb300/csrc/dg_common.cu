@@ -1,0 +1,143 @@
+// Dimension-free kernels of the DG path: basis conversion at the interface,
+// per-element scaling and the density-residual norm of Eq. cfl with the CFL ramp.
+#include <cfloat>
+
+#include "kernels.h"
+
+namespace pcexp {
+
+// ------------------------------------------------------------ basis conversion
+template <class T>
+__global__ void paper_to_internal_kernel(const double* __restrict__ src, T* __restrict__ dst,
+                                         const double* __restrict__ Q, int64_t E, int nb, int nv) {
+  const int64_t n = E * nv * nb;
+  for (int64_t idx = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; idx < n; idx += (int64_t)gridDim.x * blockDim.x) {
+    const int64_t e = idx / (nv * nb);
+    const int r = (int)(idx - e * nv * nb), v = r / nb, j = r - v * nb;
+    const double* q = Q + e * nb * nb;
+    const double* s = src + e * nv * nb + v * nb;
+    double a = 0;
+    for (int i = 0; i < nb; ++i) a += q[i * nb + j] * s[i];
+    dst[idx] = (T)a;
+  }
+}
+
+template <class T>
+__global__ void internal_to_paper_kernel(const T* __restrict__ src, double* __restrict__ dst,
+                                         const double* __restrict__ Q, int64_t E, int nb, int nv) {
+  const int64_t n = E * nv * nb;
+  for (int64_t idx = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; idx < n; idx += (int64_t)gridDim.x * blockDim.x) {
+    const int64_t e = idx / (nv * nb);
+    const int r = (int)(idx - e * nv * nb), v = r / nb, i = r - v * nb;
+    const double* q = Q + e * nb * nb + i * nb;
+    const T* s = src + e * nv * nb + v * nb;
+    double a = 0;
+    for (int j = 0; j < nb; ++j) a += q[j] * (double)s[j];
+    dst[idx] = a;
+  }
+}
+
+static unsigned grid_for(int64_t n) {
+  int64_t b = (n + 255) / 256;
+  if (b > 152 * 16) b = 152 * 16;
+  return (unsigned)(b < 1 ? 1 : b);
+}
+
+template <class T>
+cudaError_t launch_paper_to_internal(const double* src, T* dst, const double* Q, int64_t E, int nb, int nv, cudaStream_t st) {
+  paper_to_internal_kernel<T><<<grid_for(E * nb * nv), 256, 0, st>>>(src, dst, Q, E, nb, nv);
+  return cudaGetLastError();
+}
+template <class T>
+cudaError_t launch_internal_to_paper(const T* src, double* dst, const double* Q, int64_t E, int nb, int nv, cudaStream_t st) {
+  internal_to_paper_kernel<T><<<grid_for(E * nb * nv), 256, 0, st>>>(src, dst, Q, E, nb, nv);
+  return cudaGetLastError();
+}
+
+template <class T>
+__global__ void scale_elements_kernel(T* __restrict__ x, const T* __restrict__ s, int64_t E, int nvb) {
+  const int64_t n = E * nvb;
+  for (int64_t idx = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; idx < n; idx += (int64_t)gridDim.x * blockDim.x)
+    x[idx] *= s[idx / nvb];
+}
+template <class T>
+cudaError_t launch_scale_elements(T* x, const T* s, int64_t E, int nvb, cudaStream_t st) {
+  scale_elements_kernel<T><<<grid_for(E * nvb), 256, 0, st>>>(x, s, E, nvb);
+  return cudaGetLastError();
+}
+
+// Density residual norm of Eq. cfl with the orthonormal basis:
+// (1/|Omega|) sqrt(sum_e sum_i (R[e][0][i] / s_e)^2); then CFL(n) of Eq. cfl.
+template <class T>
+__global__ void __launch_bounds__(256) density_norm_kernel(const T* __restrict__ R, const T* __restrict__ s,
+                                                           int64_t E, int nb, int nv, double volume,
+                                                           StepState* ss, double* __restrict__ partials,
+                                                           int ramp_n, int p, double cfl_max) {
+  __shared__ double red[8];
+  __shared__ bool last;
+  double acc = 0;
+  const int64_t n = E * nb;
+  for (int64_t idx = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; idx < n; idx += (int64_t)gridDim.x * blockDim.x) {
+    const int64_t e = idx / nb;
+    const int i = (int)(idx - e * nb);
+    double r = (double)R[e * nv * nb + i];
+    if (s) r /= (double)s[e];
+    acc += r * r;
+  }
+  for (int o = 16; o > 0; o >>= 1) acc += __shfl_xor_sync(0xffffffffu, acc, o);
+  if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = acc;
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    double b = 0;
+    for (int w = 0; w < (int)(blockDim.x >> 5); ++w) b += red[w];
+    partials[blockIdx.x] = b;
+    __threadfence();
+    last = atomicAdd(&ss->counter, 1u) == gridDim.x - 1;
+  }
+  __syncthreads();
+  if (last && threadIdx.x == 0) {
+    double b = 0;
+    for (unsigned i = 0; i < gridDim.x; ++i) b += __ldcg(partials + i);
+    const double rn = sqrt(b) / volume;
+    ss->res_norm = rn;
+    if (!isfinite(rn)) ss->err = 1;
+    if (ramp_n > 0) {
+      const double a = rn > 0 ? 1.0 / (rn * rn * rn) : DBL_MAX;
+      const double b2 = 1.0 + (double)(ramp_n - 1) / (2 * p + 1);
+      ss->cfl = fmin(cfl_max, fmax(a, b2));
+    }
+    ss->counter = 0;
+  }
+}
+
+template <class T>
+cudaError_t launch_density_norm(const T* R, const T* s, int64_t E, int nb, int nv, double volume, StepState* ss,
+                                double* partials, int ramp_n, int p, double cfl_max, cudaStream_t st) {
+  int64_t b = (E * nb + 255) / 256;
+  if (b > RED_BLOCKS) b = RED_BLOCKS;
+  density_norm_kernel<T><<<(unsigned)(b < 1 ? 1 : b), 256, 0, st>>>(R, s, E, nb, nv, volume, ss, partials, ramp_n, p, cfl_max);
+  return cudaGetLastError();
+}
+
+__global__ void scale_by_inverse_kernel(double* __restrict__ x, const double* __restrict__ s, int64_t n) {
+  const double f = 1.0 / *s;
+  for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x)
+    x[i] *= f;
+}
+cudaError_t launch_scale_by_inverse(double* x, const double* s, int64_t n, cudaStream_t st) {
+  scale_by_inverse_kernel<<<grid_for(n), 256, 0, st>>>(x, s, n);
+  return cudaGetLastError();
+}
+
+#define PCEXP_INST(T)                                                                                         \
+  template cudaError_t launch_paper_to_internal<T>(const double*, T*, const double*, int64_t, int, int,        \
+                                                   cudaStream_t);                                              \
+  template cudaError_t launch_internal_to_paper<T>(const T*, double*, const double*, int64_t, int, int,        \
+                                                   cudaStream_t);                                              \
+  template cudaError_t launch_scale_elements<T>(T*, const T*, int64_t, int, cudaStream_t);                     \
+  template cudaError_t launch_density_norm<T>(const T*, const T*, int64_t, int, int, double, StepState*,       \
+                                              double*, int, int, double, cudaStream_t);
+PCEXP_INST(double)
+PCEXP_INST(float)
+
+}  // namespace pcexp

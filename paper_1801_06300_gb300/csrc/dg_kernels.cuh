@@ -1,0 +1,1212 @@
+// DG operator kernels on triangles (D = 2) and tetrahedra (D = 3): the residual
+// R(u) of Eq. euler3 (Sec. 4.2), its tangent-linear J(u) v (the exact Jacobian of
+// Eq. jac1 / jac2, applied matrix-free), the transpose and second-order adjoints,
+// the output functionals and the element time-step rule of Eq. x3d.  Each
+// dimension is instantiated in its own translation unit (dg2d.cu, dg3d.cu).
+//
+// Basis: a reference-simplex orthonormal basis phi^_j mapped affinely and scaled
+// by |det A_e|^-1/2, so it is orthonormal on every element (the mass matrix is the
+// identity, as with the paper's basis).  With x = v0 + A xi:
+//   U(x_q)        = |det A|^-1/2 sum_j phi^_j(xi_q) u_j
+//   volume term   = |det A|^1/2 sum_q w_q sum_d' d phi^_i/d xi_d'(xi_q) Fhat_d'
+//                   with Fhat_d' = sum_d (A^-1)_{d' d} F_d(U(x_q))
+//   face term     = -|det A|^-1/2 sum_q w_q |f| phi^_i(x_q) F~_n(x_q)
+// Two launches per operator: a face kernel (one thread per face point) writes
+// |f| w_q F~_n into the face-flux buffer G; an element kernel (a tile of elements
+// per block, staged in shared memory) adds the volume term and lifts the face
+// fluxes of its D+1 faces.  Every face flux is computed once and every output is
+// written once, in a fixed order (deterministic).
+//
+// Face points are those of the face's L element (its local face-vertex order).
+// The trace tables Bf[face][perm][q][j] hold phi^_j at face point q of local face
+// `face` when the element's face vertices are the L element's permuted by `perm`
+// (perm 0 = identity; in 2D perm 1 reverses the edge).  An element's face slot
+// ef = (face index << 4) | (side << 3) | perm.
+#pragma once
+#include <cfloat>
+#include <type_traits>
+
+#include "kernels.h"
+
+namespace pcexp {
+
+template <int D, int P> struct Ord {
+  static constexpr int NV = D + 2;
+  static constexpr int NB = D == 2 ? (P + 1) * (P + 2) / 2 : (P + 1) * (P + 2) * (P + 3) / 6;
+  static constexpr int NQ = D == 2 ? (P + 1) * (P + 1) : (P + 1) * (P + 1) * (P + 1);
+  static constexpr int NFQ = D == 2 ? P + 1 : (P + 1) * (P + 1);
+  static constexpr int NF = D + 1;                  // faces per element
+  static constexpr int NPERM = D == 2 ? 2 : 6;      // vertex permutations of a face
+  static constexpr int GEO = D == 2 ? 8 : 12;       // geometry record: A^-1 (D x D), sqrt|det|, h
+  static constexpr int SD = D * D;
+  static constexpr int HE = D * D + 1;
+  static constexpr int NVB = NV * NB;
+  static constexpr int ET = (256 / NQ) > 128 ? 128 : (256 / NQ);  // elements per block
+  static constexpr int NJV = D * NV * NV;           // volume point-Jacobian entries
+  static constexpr int NJF = 2 * NV * NV;           // face point-Jacobian entries
+  static constexpr int NBF = NF * NPERM * NFQ * NB;  // trace-table entries
+  static constexpr bool SMEM_BF = D == 2;            // stage the trace tables in shared memory
+};
+
+template <class S> struct PartOf;
+template <> struct PartOf<double> { PCEXP_DEV static double get(double x) { return x; } };
+template <> struct PartOf<float> { PCEXP_DEV static float get(float x) { return x; } };
+template <class T> struct PartOf<Tangent<T>> { PCEXP_DEV static T get(Tangent<T> x) { return x.d; } };
+
+// table read: shared memory, or global memory through the read-only cache
+template <bool SMEM, class T> PCEXP_DEV T tab(const T* p) {
+  if constexpr (SMEM) return *p;
+  else return __ldg(p);
+}
+
+template <class O> PCEXP_DEV int slot_face(int fs) { return fs >> 4; }
+PCEXP_DEV int slot_side(int fs) { return (fs >> 3) & 1; }
+PCEXP_DEV int slot_perm(int fs) { return fs & 7; }
+
+// ------------------------------------------------------------------ face kernel
+template <class T, int D, int P, bool TAN>
+__global__ void __launch_bounds__(256) face_kernel(DGData<T> d, const T* __restrict__ u,
+                                                   const T* __restrict__ du, T* __restrict__ G,
+                                                   const int* __restrict__ skip) {
+  using O = Ord<D, P>;
+  constexpr int NB = O::NB, NFQ = O::NFQ, NV = O::NV, NPERM = O::NPERM, GEO = O::GEO;
+  constexpr bool SM = O::SMEM_BF;
+  using S = typename std::conditional<TAN, Tangent<T>, T>::type;
+  __shared__ T sBf[SM ? O::NBF : 1];
+  __shared__ T sWf[NFQ];
+  if (skip && *skip) return;
+  if constexpr (SM)
+    for (int i = threadIdx.x; i < O::NBF; i += blockDim.x) sBf[i] = d.Bf[i];
+  for (int i = threadIdx.x; i < NFQ; i += blockDim.x) sWf[i] = d.Wf[i];
+  __syncthreads();
+  const T* Bf = SM ? sBf : d.Bf;
+  const int64_t idx = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (idx >= d.F * NFQ) return;
+  const int64_t f = idx / NFQ;
+  const int q = (int)(idx - f * NFQ);
+  const int eL = d.fel[2 * f], eR = d.fel[2 * f + 1];
+  const int loc = d.floc[f];
+  const int fL = loc & 0xff, fR = (loc >> 8) & 0xff, pR = loc >> 16;
+  T n[D];
+#pragma unroll
+  for (int k = 0; k < D; ++k) n[k] = d.fgeo[4 * f + k];
+  const T meas = d.fgeo[4 * f + D];
+  S UL[NV], UR[NV];
+  {
+    const T isd = T(1) / d.geo[GEO * (int64_t)eL + O::SD];
+    const T* ue = u + (int64_t)eL * NV * NB;
+    const T* be = Bf + ((fL * NPERM) * NFQ + q) * NB;
+#pragma unroll
+    for (int v = 0; v < NV; ++v) {
+      T a = 0, b = 0;
+#pragma unroll
+      for (int j = 0; j < NB; ++j) {
+        const T bj = tab<SM>(be + j);
+        a += bj * ue[v * NB + j];
+        if constexpr (TAN) b += bj * du[(int64_t)eL * NV * NB + v * NB + j];
+      }
+      if constexpr (TAN) UL[v] = S{a * isd, b * isd};
+      else UL[v] = a * isd;
+    }
+  }
+  if (eR >= 0) {
+    const T isd = T(1) / d.geo[GEO * (int64_t)eR + O::SD];
+    const T* ue = u + (int64_t)eR * NV * NB;
+    const T* be = Bf + ((fR * NPERM + pR) * NFQ + q) * NB;
+#pragma unroll
+    for (int v = 0; v < NV; ++v) {
+      T a = 0, b = 0;
+#pragma unroll
+      for (int j = 0; j < NB; ++j) {
+        const T bj = tab<SM>(be + j);
+        a += bj * ue[v * NB + j];
+        if constexpr (TAN) b += bj * du[(int64_t)eR * NV * NB + v * NB + j];
+      }
+      if constexpr (TAN) UR[v] = S{a * isd, b * isd};
+      else UR[v] = a * isd;
+    }
+  } else if (-eR == PCEXP_BC_SLIP_WALL) {
+    ghost_slip_wall<D, S, T>(UL, n, UR);
+  } else {
+    ghost_farfield<D, S, T>(UL, n, d.fs, UR);
+  }
+  S Fn[NV];
+  roe_flux<D, S, T>(UL, UR, n, d.fs.gamma, Fn);
+  const T wl = meas * sWf[q];
+  T* g = G + idx * NV;
+#pragma unroll
+  for (int v = 0; v < NV; ++v) g[v] = wl * PartOf<S>::get(Fn[v]);
+}
+
+// lift of the D+1 face fluxes onto test function i of variable v of element e
+template <class T, int D, int P, bool SM>
+PCEXP_DEV T lift_faces(const DGData<T>& d, const T* Bf, const T* __restrict__ G, int64_t e, int v, int i) {
+  using O = Ord<D, P>;
+  constexpr int NB = O::NB, NFQ = O::NFQ, NV = O::NV, NPERM = O::NPERM, NF = O::NF;
+  T lift = 0;
+#pragma unroll
+  for (int k = 0; k < NF; ++k) {
+    const int fs = d.ef[NF * e + k];
+    const T* gf = G + (int64_t)slot_face<O>(fs) * NFQ * NV;
+    const T* tb = Bf + ((k * NPERM + slot_perm(fs)) * NFQ) * NB + i;
+    T a = 0;
+#pragma unroll
+    for (int q = 0; q < NFQ; ++q) a += tab<SM>(tb + q * NB) * gf[q * NV + v];
+    lift = slot_side(fs) ? lift + a : lift - a;
+  }
+  return lift;
+}
+
+// --------------------------------------------------------------- element kernel
+template <class T, int D, int P, bool TAN>
+__global__ void __launch_bounds__(256) elem_kernel(DGData<T> d, const T* __restrict__ u,
+                                                   const T* __restrict__ du, const T* __restrict__ G,
+                                                   T* __restrict__ out, const T* __restrict__ escale,
+                                                   const int* __restrict__ skip, const double* __restrict__ oscale) {
+  using O = Ord<D, P>;
+  constexpr int NB = O::NB, NQ = O::NQ, ET = O::ET, NVB = O::NVB, NV = O::NV, GEO = O::GEO, DV = D * NV;
+  constexpr bool SM = O::SMEM_BF;
+  using S = typename std::conditional<TAN, Tangent<T>, T>::type;
+  __shared__ T sBv[NQ * NB];
+  __shared__ T sDv[D * NQ * NB];
+  __shared__ T sBf[SM ? O::NBF : 1];
+  __shared__ T su[ET * NVB];
+  __shared__ T sdu[TAN ? ET * NVB : 1];
+  __shared__ T sF[ET * NQ * DV];
+  __shared__ T sgeo[ET * GEO];
+  if (skip && *skip) return;
+  const int64_t e0 = (int64_t)blockIdx.x * ET;
+  const int ne = (int)((d.E - e0) < ET ? (d.E - e0) : ET);
+  for (int i = threadIdx.x; i < NQ * NB; i += blockDim.x) sBv[i] = d.Bv[i];
+  for (int i = threadIdx.x; i < D * NQ * NB; i += blockDim.x) sDv[i] = d.Dv[i];
+  if constexpr (SM)
+    for (int i = threadIdx.x; i < O::NBF; i += blockDim.x) sBf[i] = d.Bf[i];
+  for (int i = threadIdx.x; i < ne * NVB; i += blockDim.x) {
+    su[i] = u[e0 * NVB + i];
+    if constexpr (TAN) sdu[i] = du[e0 * NVB + i];
+  }
+  for (int i = threadIdx.x; i < ne * GEO; i += blockDim.x) sgeo[i] = d.geo[e0 * GEO + i];
+  __syncthreads();
+  const T g = d.fs.gamma;
+  const T osc = oscale ? (T)*oscale : T(1);
+  // phase 1: flux at each volume point, mapped to reference directions
+  for (int it = threadIdx.x; it < ne * NQ; it += blockDim.x) {
+    const int el = it / NQ, q = it - el * NQ;
+    const T* ge = sgeo + el * GEO;
+    const T isd = T(1) / ge[O::SD];
+    S U[NV];
+#pragma unroll
+    for (int v = 0; v < NV; ++v) {
+      T a = 0, b = 0;
+#pragma unroll
+      for (int j = 0; j < NB; ++j) {
+        a += sBv[q * NB + j] * su[el * NVB + v * NB + j];
+        if constexpr (TAN) b += sBv[q * NB + j] * sdu[el * NVB + v * NB + j];
+      }
+      if constexpr (TAN) U[v] = S{a * isd, b * isd};
+      else U[v] = a * isd;
+    }
+    S F[D][NV];
+    euler_flux<D, S, T>(U, g, F);
+    T* fo = sF + (el * NQ + q) * DV;
+#pragma unroll
+    for (int v = 0; v < NV; ++v) {
+      T fk[D];
+#pragma unroll
+      for (int k = 0; k < D; ++k) fk[k] = PartOf<S>::get(F[k][v]);
+#pragma unroll
+      for (int dd = 0; dd < D; ++dd) {
+        T a = ge[dd * D] * fk[0];
+#pragma unroll
+        for (int k = 1; k < D; ++k) a += ge[dd * D + k] * fk[k];
+        fo[dd * NV + v] = a;
+      }
+    }
+  }
+  __syncthreads();
+  const T* Bf = SM ? sBf : d.Bf;
+  // phase 2: test against grad phi, lift the face fluxes
+  for (int it = threadIdx.x; it < ne * NVB; it += blockDim.x) {
+    const int el = it / NVB, r = it - el * NVB;
+    const int v = r / NB, i = r - v * NB;
+    const T sd = sgeo[el * GEO + O::SD];
+    T acc = 0;
+#pragma unroll
+    for (int q = 0; q < NQ; ++q)
+#pragma unroll
+      for (int dd = 0; dd < D; ++dd) acc += sDv[(dd * NQ + q) * NB + i] * sF[(el * NQ + q) * DV + dd * NV + v];
+    acc *= sd;
+    const int64_t e = e0 + el;
+    const T lift = lift_faces<T, D, P, SM>(d, Bf, G, e, v, i);
+    acc = (acc + lift / sd) * osc;
+    if (escale) acc *= escale[e];
+    out[e0 * NVB + it] = acc;
+  }
+}
+
+template <class T, int D, int P>
+cudaError_t dg_op_p(const DGData<T>& d, const T* u, const T* du, T* out, T* G, const T* escale, const int* skip,
+                    const double* oscale, cudaStream_t st, const cudaEvent_t* ev) {
+  using O = Ord<D, P>;
+  const int64_t nfp = d.F * O::NFQ;
+  if (ev) cudaEventRecord(ev[0], st);
+  if (nfp > 0) {
+    const int64_t nb = (nfp + 255) / 256;
+    if (du) face_kernel<T, D, P, true><<<(unsigned)nb, 256, 0, st>>>(d, u, du, G, skip);
+    else face_kernel<T, D, P, false><<<(unsigned)nb, 256, 0, st>>>(d, u, du, G, skip);
+  }
+  if (ev) cudaEventRecord(ev[1], st);
+  const int64_t eb = (d.E + O::ET - 1) / O::ET;
+  if (du) elem_kernel<T, D, P, true><<<(unsigned)eb, 256, 0, st>>>(d, u, du, G, out, escale, skip, oscale);
+  else elem_kernel<T, D, P, false><<<(unsigned)eb, 256, 0, st>>>(d, u, du, G, out, escale, skip, oscale);
+  if (ev) cudaEventRecord(ev[2], st);
+  return cudaGetLastError();
+}
+
+// ------------------------------------------------------- point Jacobians (linearisation)
+// The exact Jacobian of the scheme (Eq. jac1, jac2) is assembled point by point: the
+// volume flux Jacobians dF_d/dU and the Riemann-flux Jacobians dF~/dU_L, dF~/dU_R are
+// evaluated exactly by running the flux code on Jet<T, D+2> numbers seeded with unit
+// directions (the paper obtains the Riemann-flux Jacobians by AD as well).  Every J v
+// of a PCEXP step is taken at u_n, so the Jacobians are built once per step and each
+// of the 2m+1 products reduces to traces, small mat-vecs and the test/lift contractions.
+template <class T, int D, int P>
+__global__ void __launch_bounds__(256) linearize_vol_kernel(DGData<T> d, const T* __restrict__ u,
+                                                            T* __restrict__ Avol) {
+  using O = Ord<D, P>;
+  constexpr int NB = O::NB, NQ = O::NQ, NV = O::NV, GEO = O::GEO;
+  using J = Jet<T, NV>;
+  const int64_t n = d.E * NQ;
+  const int64_t idx = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (idx >= n) return;
+  const int64_t e = idx / NQ;
+  const int q = (int)(idx - e * NQ);
+  const T* ge = d.geo + GEO * e;
+  const T isd = T(1) / ge[O::SD];
+  J U[NV];
+#pragma unroll
+  for (int v = 0; v < NV; ++v) {
+    T a = 0;
+#pragma unroll
+    for (int j = 0; j < NB; ++j) a += __ldg(d.Bv + q * NB + j) * u[e * NV * NB + v * NB + j];
+    U[v].v = a * isd;
+#pragma unroll
+    for (int c = 0; c < NV; ++c) U[v].d[c] = (v == c) ? T(1) : T(0);
+  }
+  J F[D][NV];
+  euler_flux<D, J, T>(U, d.fs.gamma, F);
+#pragma unroll
+  for (int dd = 0; dd < D; ++dd)
+#pragma unroll
+    for (int v = 0; v < NV; ++v)
+#pragma unroll
+      for (int c = 0; c < NV; ++c) {
+        T a = ge[dd * D] * F[0][v].d[c];
+#pragma unroll
+        for (int k = 1; k < D; ++k) a += ge[dd * D + k] * F[k][v].d[c];
+        Avol[(int64_t)(dd * NV * NV + v * NV + c) * n + idx] = a;
+      }
+}
+
+template <class T, int D, int P>
+__global__ void __launch_bounds__(128) linearize_face_kernel(DGData<T> d, const T* __restrict__ u,
+                                                             T* __restrict__ Bface) {
+  using O = Ord<D, P>;
+  constexpr int NB = O::NB, NFQ = O::NFQ, NV = O::NV, NPERM = O::NPERM, GEO = O::GEO, NN = NV * NV;
+  using J = Jet<T, NV>;
+  const int64_t n = d.F * NFQ;
+  const int64_t idx = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (idx >= n) return;
+  const int64_t f = idx / NFQ;
+  const int q = (int)(idx - f * NFQ);
+  const int eL = d.fel[2 * f], eR = d.fel[2 * f + 1];
+  const int loc = d.floc[f];
+  const int fL = loc & 0xff, fR = (loc >> 8) & 0xff, pR = loc >> 16;
+  T nr[D];
+#pragma unroll
+  for (int k = 0; k < D; ++k) nr[k] = d.fgeo[4 * f + k];
+  const T wq = d.fgeo[4 * f + D] * d.Wf[q];
+  T uL[NV], uR[NV];
+  const T isdL = T(1) / d.geo[GEO * (int64_t)eL + O::SD];
+  T isdR = T(0);
+  {
+    const T* be = d.Bf + ((fL * NPERM) * NFQ + q) * NB;
+#pragma unroll
+    for (int v = 0; v < NV; ++v) {
+      T a = 0;
+#pragma unroll
+      for (int j = 0; j < NB; ++j) a += __ldg(be + j) * u[(int64_t)eL * NV * NB + v * NB + j];
+      uL[v] = a * isdL;
+    }
+  }
+  if (eR >= 0) {
+    isdR = T(1) / d.geo[GEO * (int64_t)eR + O::SD];
+    const T* be = d.Bf + ((fR * NPERM + pR) * NFQ + q) * NB;
+#pragma unroll
+    for (int v = 0; v < NV; ++v) {
+      T a = 0;
+#pragma unroll
+      for (int j = 0; j < NB; ++j) a += __ldg(be + j) * u[(int64_t)eR * NV * NB + v * NB + j];
+      uR[v] = a * isdR;
+    }
+  }
+#pragma unroll 1
+  for (int side = 0; side < 2; ++side) {
+    J L[NV], R[NV], F[NV];
+    if (side == 1 && eR < 0) {
+#pragma unroll
+      for (int k = 0; k < NN; ++k) Bface[(int64_t)(NN + k) * n + idx] = T(0);
+      break;
+    }
+#pragma unroll
+    for (int v = 0; v < NV; ++v) {
+      L[v].v = uL[v];
+#pragma unroll
+      for (int c = 0; c < NV; ++c) L[v].d[c] = (side == 0 && v == c) ? T(1) : T(0);
+    }
+    if (eR >= 0) {
+#pragma unroll
+      for (int v = 0; v < NV; ++v) {
+        R[v].v = uR[v];
+#pragma unroll
+        for (int c = 0; c < NV; ++c) R[v].d[c] = (side == 1 && v == c) ? T(1) : T(0);
+      }
+    } else if (-eR == PCEXP_BC_SLIP_WALL) {
+      ghost_slip_wall<D, J, T>(L, nr, R);
+    } else {
+      ghost_farfield<D, J, T>(L, nr, d.fs, R);
+    }
+    roe_flux<D, J, T>(L, R, nr, d.fs.gamma, F);
+    const T sc = wq * (side == 0 ? isdL : isdR);
+#pragma unroll
+    for (int v = 0; v < NV; ++v)
+#pragma unroll
+      for (int c = 0; c < NV; ++c) Bface[(int64_t)(side * NN + v * NV + c) * n + idx] = sc * F[v].d[c];
+  }
+}
+
+template <class T, int D, int P>
+__global__ void __launch_bounds__(256) face_apply_kernel(DGData<T> d, const T* __restrict__ Bface,
+                                                         const T* __restrict__ dv, T* __restrict__ G,
+                                                         const int* __restrict__ skip) {
+  using O = Ord<D, P>;
+  constexpr int NB = O::NB, NFQ = O::NFQ, NV = O::NV, NPERM = O::NPERM, NN = NV * NV;
+  constexpr bool SM = O::SMEM_BF;
+  __shared__ T sBf[SM ? O::NBF : 1];
+  if (skip && *skip) return;
+  if constexpr (SM)
+    for (int i = threadIdx.x; i < O::NBF; i += blockDim.x) sBf[i] = d.Bf[i];
+  __syncthreads();
+  const T* Bf = SM ? sBf : d.Bf;
+  const int64_t n = d.F * NFQ;
+  const int64_t idx = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (idx >= n) return;
+  const int64_t f = idx / NFQ;
+  const int q = (int)(idx - f * NFQ);
+  const int eL = d.fel[2 * f], eR = d.fel[2 * f + 1];
+  const int loc = d.floc[f];
+  const int fL = loc & 0xff, fR = (loc >> 8) & 0xff, pR = loc >> 16;
+  T B[O::NJF];
+#pragma unroll
+  for (int k = 0; k < O::NJF; ++k) B[k] = (k < NN || eR >= 0) ? Bface[(int64_t)k * n + idx] : T(0);
+  T tL[NV], tR[NV];
+  {
+    const T* be = Bf + ((fL * NPERM) * NFQ + q) * NB;
+#pragma unroll
+    for (int v = 0; v < NV; ++v) {
+      T a = 0;
+#pragma unroll
+      for (int j = 0; j < NB; ++j) a += tab<SM>(be + j) * dv[(int64_t)eL * NV * NB + v * NB + j];
+      tL[v] = a;
+    }
+  }
+  if (eR >= 0) {
+    const T* be = Bf + ((fR * NPERM + pR) * NFQ + q) * NB;
+#pragma unroll
+    for (int v = 0; v < NV; ++v) {
+      T a = 0;
+#pragma unroll
+      for (int j = 0; j < NB; ++j) a += tab<SM>(be + j) * dv[(int64_t)eR * NV * NB + v * NB + j];
+      tR[v] = a;
+    }
+  }
+  T* g = G + idx * NV;
+#pragma unroll
+  for (int v = 0; v < NV; ++v) {
+    T a = 0;
+#pragma unroll
+    for (int c = 0; c < NV; ++c) a += B[v * NV + c] * tL[c];
+    if (eR >= 0) {
+#pragma unroll
+      for (int c = 0; c < NV; ++c) a += B[NN + v * NV + c] * tR[c];
+    }
+    g[v] = a;
+  }
+}
+
+template <class T, int D, int P>
+__global__ void __launch_bounds__(256) elem_apply_kernel(DGData<T> d, const T* __restrict__ Avol,
+                                                         const T* __restrict__ dv, const T* __restrict__ G,
+                                                         T* __restrict__ out, const T* __restrict__ escale,
+                                                         const int* __restrict__ skip,
+                                                         const double* __restrict__ oscale) {
+  using O = Ord<D, P>;
+  constexpr int NB = O::NB, NQ = O::NQ, ET = O::ET, NVB = O::NVB, NV = O::NV, GEO = O::GEO, DV = D * NV;
+  constexpr int NN = NV * NV;
+  constexpr int NPRE = D == 2 ? O::NJV : NN;  // point-Jacobian entries loaded before the staging
+  constexpr bool SM = O::SMEM_BF;
+  __shared__ T sBv[NQ * NB];
+  __shared__ T sDv[D * NQ * NB];
+  __shared__ T sBf[SM ? O::NBF : 1];
+  __shared__ T sdu[ET * NVB];
+  __shared__ T sF[ET * NQ * DV];
+  __shared__ T ssd[ET];
+  static_assert(ET * NQ <= 256, "one volume point per thread");
+  if (skip && *skip) return;
+  const int64_t e0 = (int64_t)blockIdx.x * ET;
+  const int ne = (int)((d.E - e0) < ET ? (d.E - e0) : ET);
+  const int64_t n = d.E * NQ;
+  // issue this thread's point-Jacobian loads first, so they are in flight while the
+  // block stages its tile of dv in shared memory
+  const int el1 = threadIdx.x / NQ, q1 = threadIdx.x - (threadIdx.x / NQ) * NQ;
+  const bool has_pt = threadIdx.x < ne * NQ;
+  const int64_t pidx = (e0 + el1) * NQ + q1;
+  T A[NPRE];
+#pragma unroll
+  for (int k = 0; k < NPRE; ++k) A[k] = has_pt ? Avol[(int64_t)k * n + pidx] : T(0);
+  for (int i = threadIdx.x; i < NQ * NB; i += blockDim.x) sBv[i] = d.Bv[i];
+  for (int i = threadIdx.x; i < D * NQ * NB; i += blockDim.x) sDv[i] = d.Dv[i];
+  if constexpr (SM)
+    for (int i = threadIdx.x; i < O::NBF; i += blockDim.x) sBf[i] = d.Bf[i];
+  for (int i = threadIdx.x; i < ne * NVB; i += blockDim.x) sdu[i] = dv[e0 * NVB + i];
+  for (int i = threadIdx.x; i < ne; i += blockDim.x) ssd[i] = d.geo[(e0 + i) * GEO + O::SD];
+  __syncthreads();
+  const T osc = oscale ? (T)*oscale : T(1);
+  // phase 1: trace of dv at this thread's volume point, times the mapped flux Jacobians
+  if (has_pt) {
+    T t[NV];
+#pragma unroll
+    for (int v = 0; v < NV; ++v) {
+      T a = 0;
+#pragma unroll
+      for (int j = 0; j < NB; ++j) a += sBv[q1 * NB + j] * sdu[el1 * NVB + v * NB + j];
+      t[v] = a;
+    }
+    T* fo = sF + (el1 * NQ + q1) * DV;
+#pragma unroll
+    for (int dd = 0; dd < D; ++dd)
+#pragma unroll
+      for (int v = 0; v < NV; ++v) {
+        T a = 0;
+#pragma unroll
+        for (int c = 0; c < NV; ++c) {
+          const int k = dd * NN + v * NV + c;
+          const T akc = k < NPRE ? A[k < NPRE ? k : 0] : Avol[(int64_t)k * n + pidx];
+          a += akc * t[c];
+        }
+        fo[dd * NV + v] = a;
+      }
+  }
+  __syncthreads();
+  const T* Bf = SM ? sBf : d.Bf;
+  // phase 2: test against grad phi (the sqrt(det) factors cancel), lift the face terms
+  for (int it = threadIdx.x; it < ne * NVB; it += blockDim.x) {
+    const int el = it / NVB, r = it - el * NVB;
+    const int v = r / NB, i = r - v * NB;
+    T acc = 0;
+#pragma unroll
+    for (int q = 0; q < NQ; ++q)
+#pragma unroll
+      for (int dd = 0; dd < D; ++dd) acc += sDv[(dd * NQ + q) * NB + i] * sF[(el * NQ + q) * DV + dd * NV + v];
+    const int64_t e = e0 + el;
+    const T lift = lift_faces<T, D, P, SM>(d, Bf, G, e, v, i);
+    acc = (acc + lift / ssd[el]) * osc;
+    if (escale) acc *= escale[e];
+    out[e0 * NVB + it] = acc;
+  }
+}
+
+template <class T, int D, int P>
+cudaError_t linearize_p(const DGData<T>& d, const T* u, LinData<T> lin, cudaStream_t st) {
+  using O = Ord<D, P>;
+  const int64_t nv = d.E * O::NQ, nf = d.F * O::NFQ;
+  linearize_vol_kernel<T, D, P><<<(unsigned)((nv + 255) / 256), 256, 0, st>>>(d, u, lin.Avol);
+  if (nf > 0) linearize_face_kernel<T, D, P><<<(unsigned)((nf + 127) / 128), 128, 0, st>>>(d, u, lin.Bface);
+  return cudaGetLastError();
+}
+
+template <class T, int D, int P>
+cudaError_t jac_apply_p(const DGData<T>& d, LinData<T> lin, const T* dv, T* out, T* G, const T* escale,
+                        const int* skip, const double* oscale, cudaStream_t st, const cudaEvent_t* ev) {
+  using O = Ord<D, P>;
+  const int64_t nf = d.F * O::NFQ;
+  if (ev) cudaEventRecord(ev[0], st);
+  if (nf > 0) face_apply_kernel<T, D, P><<<(unsigned)((nf + 255) / 256), 256, 0, st>>>(d, lin.Bface, dv, G, skip);
+  if (ev) cudaEventRecord(ev[1], st);
+  const int64_t eb = (d.E + O::ET - 1) / O::ET;
+  elem_apply_kernel<T, D, P><<<(unsigned)eb, 256, 0, st>>>(d, lin.Avol, dv, G, out, escale, skip, oscale);
+  if (ev) cudaEventRecord(ev[2], st);
+  return cudaGetLastError();
+}
+
+// ------------------------------------------------------------- adjoint J^T w
+// Transpose of the point-Jacobian J v (same linearisation state).  With the output
+// factors of J v folded into w (w~ = osc * escale_e * w), the face kernel forms the
+// adjoint of the lifted face flux at every face point,
+//   Gbar = -(1/sd_L) sum_i Bf_L[i] w~_L[i] + (1/sd_R) sum_i Bf_R[i] w~_R[i],
+// and stores B_L^T Gbar and B_R^T Gbar; the element kernel applies the transposed
+// volume Jacobians to the transposed test of w~ and gathers the transposed traces
+// of its faces.  Deterministic (no atomics).
+template <class T, int D, int P>
+__global__ void __launch_bounds__(256) face_adjoint_kernel(DGData<T> d, const T* __restrict__ Bface,
+                                                           const T* __restrict__ w, T* __restrict__ GT,
+                                                           const T* __restrict__ escale, T osc) {
+  using O = Ord<D, P>;
+  constexpr int NB = O::NB, NFQ = O::NFQ, NV = O::NV, NPERM = O::NPERM, GEO = O::GEO, NN = NV * NV;
+  constexpr bool SM = O::SMEM_BF;
+  __shared__ T sBf[SM ? O::NBF : 1];
+  if constexpr (SM)
+    for (int i = threadIdx.x; i < O::NBF; i += blockDim.x) sBf[i] = d.Bf[i];
+  __syncthreads();
+  const T* Bf = SM ? sBf : d.Bf;
+  const int64_t n = d.F * NFQ;
+  const int64_t idx = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (idx >= n) return;
+  const int64_t f = idx / NFQ;
+  const int q = (int)(idx - f * NFQ);
+  const int eL = d.fel[2 * f], eR = d.fel[2 * f + 1];
+  const int loc = d.floc[f];
+  const int fL = loc & 0xff, fR = (loc >> 8) & 0xff, pR = loc >> 16;
+  T gb[NV];
+  {
+    const T sc = -osc * (escale ? escale[eL] : T(1)) / d.geo[GEO * (int64_t)eL + O::SD];
+    const T* be = Bf + ((fL * NPERM) * NFQ + q) * NB;
+#pragma unroll
+    for (int v = 0; v < NV; ++v) {
+      T a = 0;
+#pragma unroll
+      for (int i = 0; i < NB; ++i) a += tab<SM>(be + i) * w[(int64_t)eL * NV * NB + v * NB + i];
+      gb[v] = sc * a;
+    }
+  }
+  if (eR >= 0) {
+    const T sc = osc * (escale ? escale[eR] : T(1)) / d.geo[GEO * (int64_t)eR + O::SD];
+    const T* be = Bf + ((fR * NPERM + pR) * NFQ + q) * NB;
+#pragma unroll
+    for (int v = 0; v < NV; ++v) {
+      T a = 0;
+#pragma unroll
+      for (int i = 0; i < NB; ++i) a += tab<SM>(be + i) * w[(int64_t)eR * NV * NB + v * NB + i];
+      gb[v] += sc * a;
+    }
+  }
+  T* o = GT + idx * 2 * NV;
+#pragma unroll
+  for (int side = 0; side < 2; ++side)
+#pragma unroll
+    for (int c = 0; c < NV; ++c) {
+      T a = 0;
+      if (side == 0 || eR >= 0) {
+#pragma unroll
+        for (int v = 0; v < NV; ++v) a += Bface[(int64_t)(side * NN + v * NV + c) * n + idx] * gb[v];
+      }
+      o[side * NV + c] = a;
+    }
+}
+
+// transposed face traces of the D+1 faces for coefficient j of variable c of element e
+template <class T, int D, int P, bool SM>
+PCEXP_DEV T gather_faces_T(const DGData<T>& d, const T* Bf, const T* __restrict__ GT, int64_t e, int c, int j) {
+  using O = Ord<D, P>;
+  constexpr int NB = O::NB, NFQ = O::NFQ, NV = O::NV, NPERM = O::NPERM, NF = O::NF;
+  T acc = 0;
+#pragma unroll
+  for (int k = 0; k < NF; ++k) {
+    const int fs = d.ef[NF * e + k];
+    const T* gt = GT + (int64_t)slot_face<O>(fs) * NFQ * 2 * NV + slot_side(fs) * NV + c;
+    const T* tb = Bf + ((k * NPERM + slot_perm(fs)) * NFQ) * NB + j;
+#pragma unroll
+    for (int q = 0; q < NFQ; ++q) acc += tab<SM>(tb + q * NB) * gt[q * 2 * NV];
+  }
+  return acc;
+}
+
+template <class T, int D, int P>
+__global__ void __launch_bounds__(256) elem_adjoint_kernel(DGData<T> d, const T* __restrict__ Avol,
+                                                           const T* __restrict__ w, const T* __restrict__ GT,
+                                                           T* __restrict__ out, const T* __restrict__ escale,
+                                                           T osc) {
+  using O = Ord<D, P>;
+  constexpr int NB = O::NB, NQ = O::NQ, ET = O::ET, NVB = O::NVB, NV = O::NV, NN = NV * NV;
+  constexpr bool SM = O::SMEM_BF;
+  __shared__ T sBv[NQ * NB];
+  __shared__ T sDv[D * NQ * NB];
+  __shared__ T sBf[SM ? O::NBF : 1];
+  __shared__ T sw[ET * NVB];
+  __shared__ T sU[ET * NQ * NV];
+  static_assert(ET * NQ <= 256, "one volume point per thread");
+  const int64_t e0 = (int64_t)blockIdx.x * ET;
+  const int ne = (int)((d.E - e0) < ET ? (d.E - e0) : ET);
+  const int64_t n = d.E * NQ;
+  for (int i = threadIdx.x; i < NQ * NB; i += blockDim.x) sBv[i] = d.Bv[i];
+  for (int i = threadIdx.x; i < D * NQ * NB; i += blockDim.x) sDv[i] = d.Dv[i];
+  if constexpr (SM)
+    for (int i = threadIdx.x; i < O::NBF; i += blockDim.x) sBf[i] = d.Bf[i];
+  for (int i = threadIdx.x; i < ne * NVB; i += blockDim.x)
+    sw[i] = w[e0 * NVB + i] * osc * (escale ? escale[e0 + i / NVB] : T(1));
+  __syncthreads();
+  // phase 1: transposed test, then transposed volume Jacobians, at this thread's point
+  const int el1 = threadIdx.x / NQ, q1 = threadIdx.x - (threadIdx.x / NQ) * NQ;
+  if (threadIdx.x < ne * NQ) {
+    const int64_t pidx = (e0 + el1) * NQ + q1;
+    T fb[D * NV];
+#pragma unroll
+    for (int dd = 0; dd < D; ++dd)
+#pragma unroll
+      for (int v = 0; v < NV; ++v) {
+        T a = 0;
+#pragma unroll
+        for (int i = 0; i < NB; ++i) a += sDv[(dd * NQ + q1) * NB + i] * sw[el1 * NVB + v * NB + i];
+        fb[dd * NV + v] = a;
+      }
+#pragma unroll
+    for (int c = 0; c < NV; ++c) {
+      T a = 0;
+#pragma unroll
+      for (int dd = 0; dd < D; ++dd)
+#pragma unroll
+        for (int v = 0; v < NV; ++v) a += Avol[(int64_t)(dd * NN + v * NV + c) * n + pidx] * fb[dd * NV + v];
+      sU[(el1 * NQ + q1) * NV + c] = a;
+    }
+  }
+  __syncthreads();
+  const T* Bf = SM ? sBf : d.Bf;
+  // phase 2: transposed volume traces plus the transposed face traces
+  for (int it = threadIdx.x; it < ne * NVB; it += blockDim.x) {
+    const int el = it / NVB, r = it - el * NVB;
+    const int c = r / NB, j = r - c * NB;
+    T acc = 0;
+#pragma unroll
+    for (int q = 0; q < NQ; ++q) acc += sBv[q * NB + j] * sU[(el * NQ + q) * NV + c];
+    acc += gather_faces_T<T, D, P, SM>(d, Bf, GT, e0 + el, c, j);
+    out[e0 * NVB + it] = acc;
+  }
+}
+
+template <class T, int D, int P>
+cudaError_t jac_adjoint_p(const DGData<T>& d, LinData<T> lin, const T* w, T* out, T* GT, const T* escale, T osc,
+                          cudaStream_t st) {
+  using O = Ord<D, P>;
+  const int64_t nf = d.F * O::NFQ;
+  if (nf > 0) face_adjoint_kernel<T, D, P><<<(unsigned)((nf + 255) / 256), 256, 0, st>>>(d, lin.Bface, w, GT, escale, osc);
+  const int64_t eb = (d.E + O::ET - 1) / O::ET;
+  elem_adjoint_kernel<T, D, P><<<(unsigned)eb, 256, 0, st>>>(d, lin.Avol, w, GT, out, escale, osc);
+  return cudaGetLastError();
+}
+
+// ------------------------------------------- second-order adjoint (d(J(u) v)/du)^T w
+// S(u) = w~^T J(u) v is differentiated with respect to the linearisation state u:
+// every flux is evaluated on hyper-dual numbers (value, D+2 seeded partials, the
+// directional derivative along the traces of v, its partials), contracted with the
+// transposed test (volume) or transposed lift (faces) of w~ and mapped back through the
+// transposed traces.  Same output factors and scratch layout as the adjoint kernels.
+template <class T, int D, int P>
+__global__ void __launch_bounds__(128) face_hess_kernel(DGData<T> d, const T* __restrict__ u,
+                                                        const T* __restrict__ v, const T* __restrict__ w,
+                                                        T* __restrict__ GT, const T* __restrict__ escale, T osc) {
+  using O = Ord<D, P>;
+  constexpr int NB = O::NB, NFQ = O::NFQ, NV = O::NV, NPERM = O::NPERM, GEO = O::GEO;
+  using H = HD<T, NV>;
+  const int64_t n = d.F * NFQ;
+  const int64_t idx = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (idx >= n) return;
+  const int64_t f = idx / NFQ;
+  const int q = (int)(idx - f * NFQ);
+  const int eL = d.fel[2 * f], eR = d.fel[2 * f + 1];
+  const int loc = d.floc[f];
+  const int fL = loc & 0xff, fR = (loc >> 8) & 0xff, pR = loc >> 16;
+  T nr[D];
+#pragma unroll
+  for (int k = 0; k < D; ++k) nr[k] = d.fgeo[4 * f + k];
+  const T wq = d.fgeo[4 * f + D] * d.Wf[q];
+  const T sdL = d.geo[GEO * (int64_t)eL + O::SD];
+  const T sdR = eR >= 0 ? d.geo[GEO * (int64_t)eR + O::SD] : T(1);
+  const T* bL = d.Bf + ((fL * NPERM) * NFQ + q) * NB;
+  const T* bR = d.Bf + ((fR * NPERM + (eR >= 0 ? pR : 0)) * NFQ + q) * NB;
+  T uL[NV], tL[NV], uR[NV], tR[NV], gb[NV];
+  const T scL = -osc * (escale ? escale[eL] : T(1)) / sdL;
+  const T scR = osc * (eR >= 0 && escale ? escale[eR] : T(1)) / sdR;
+#pragma unroll
+  for (int c = 0; c < NV; ++c) {
+    T a = 0, b = 0, g = 0;
+#pragma unroll
+    for (int j = 0; j < NB; ++j) {
+      const int64_t o = (int64_t)eL * NV * NB + c * NB + j;
+      const T bj = __ldg(bL + j);
+      a += bj * u[o];
+      b += bj * v[o];
+      g += bj * w[o];
+    }
+    uL[c] = a / sdL;
+    tL[c] = b / sdL;
+    gb[c] = scL * g;
+    uR[c] = tR[c] = T(0);
+  }
+  if (eR >= 0) {
+#pragma unroll
+    for (int c = 0; c < NV; ++c) {
+      T a = 0, b = 0, g = 0;
+#pragma unroll
+      for (int j = 0; j < NB; ++j) {
+        const int64_t o = (int64_t)eR * NV * NB + c * NB + j;
+        const T bj = __ldg(bR + j);
+        a += bj * u[o];
+        b += bj * v[o];
+        g += bj * w[o];
+      }
+      uR[c] = a / sdR;
+      tR[c] = b / sdR;
+      gb[c] += scR * g;
+    }
+  }
+  T* o = GT + idx * 2 * NV;
+#pragma unroll 1
+  for (int side = 0; side < 2; ++side) {
+    if (side == 1 && eR < 0) {
+#pragma unroll
+      for (int c = 0; c < NV; ++c) o[NV + c] = T(0);
+      break;
+    }
+    H L[NV], R[NV], F[NV];
+#pragma unroll
+    for (int c = 0; c < NV; ++c) {
+      L[c].v = uL[c];
+      L[c].t = tL[c];
+#pragma unroll
+      for (int k = 0; k < NV; ++k) {
+        L[c].d[k] = (side == 0 && k == c) ? T(1) : T(0);
+        L[c].dt[k] = T(0);
+      }
+    }
+    if (eR >= 0) {
+#pragma unroll
+      for (int c = 0; c < NV; ++c) {
+        R[c].v = uR[c];
+        R[c].t = tR[c];
+#pragma unroll
+        for (int k = 0; k < NV; ++k) {
+          R[c].d[k] = (side == 1 && k == c) ? T(1) : T(0);
+          R[c].dt[k] = T(0);
+        }
+      }
+    } else if (-eR == PCEXP_BC_SLIP_WALL) {
+      ghost_slip_wall<D, H, T>(L, nr, R);
+    } else {
+      ghost_farfield<D, H, T>(L, nr, d.fs, R);
+    }
+    roe_flux<D, H, T>(L, R, nr, d.fs.gamma, F);
+    const T sc = wq / (side == 0 ? sdL : sdR);
+#pragma unroll
+    for (int c = 0; c < NV; ++c) {
+      T a = 0;
+#pragma unroll
+      for (int vv = 0; vv < NV; ++vv) a += gb[vv] * F[vv].dt[c];
+      o[side * NV + c] = sc * a;
+    }
+  }
+}
+
+template <class T, int D, int P>
+__global__ void __launch_bounds__(256) elem_hess_kernel(DGData<T> d, const T* __restrict__ u, const T* __restrict__ v,
+                                                        const T* __restrict__ w, const T* __restrict__ GT,
+                                                        T* __restrict__ out, const T* __restrict__ escale, T osc) {
+  using O = Ord<D, P>;
+  constexpr int NB = O::NB, NQ = O::NQ, ET = O::ET, NVB = O::NVB, NV = O::NV, GEO = O::GEO;
+  constexpr bool SM = O::SMEM_BF;
+  using H = HD<T, NV>;
+  __shared__ T sBv[NQ * NB];
+  __shared__ T sDv[D * NQ * NB];
+  __shared__ T sBf[SM ? O::NBF : 1];
+  __shared__ T su[ET * NVB];
+  __shared__ T sv[ET * NVB];
+  __shared__ T sw[ET * NVB];
+  __shared__ T sU[ET * NQ * NV];
+  __shared__ T sgeo[ET * GEO];
+  static_assert(ET * NQ <= 256, "one volume point per thread");
+  const int64_t e0 = (int64_t)blockIdx.x * ET;
+  const int ne = (int)((d.E - e0) < ET ? (d.E - e0) : ET);
+  for (int i = threadIdx.x; i < NQ * NB; i += blockDim.x) sBv[i] = d.Bv[i];
+  for (int i = threadIdx.x; i < D * NQ * NB; i += blockDim.x) sDv[i] = d.Dv[i];
+  if constexpr (SM)
+    for (int i = threadIdx.x; i < O::NBF; i += blockDim.x) sBf[i] = d.Bf[i];
+  for (int i = threadIdx.x; i < ne * NVB; i += blockDim.x) {
+    su[i] = u[e0 * NVB + i];
+    sv[i] = v[e0 * NVB + i];
+    sw[i] = w[e0 * NVB + i] * osc * (escale ? escale[e0 + i / NVB] : T(1));
+  }
+  for (int i = threadIdx.x; i < ne * GEO; i += blockDim.x) sgeo[i] = d.geo[e0 * GEO + i];
+  __syncthreads();
+  const int el1 = threadIdx.x / NQ, q1 = threadIdx.x - (threadIdx.x / NQ) * NQ;
+  if (threadIdx.x < ne * NQ) {
+    const T* ge = sgeo + el1 * GEO;
+    const T sd = ge[O::SD];
+    H U[NV];
+#pragma unroll
+    for (int c = 0; c < NV; ++c) {
+      T a = 0, b = 0;
+#pragma unroll
+      for (int j = 0; j < NB; ++j) {
+        a += sBv[q1 * NB + j] * su[el1 * NVB + c * NB + j];
+        b += sBv[q1 * NB + j] * sv[el1 * NVB + c * NB + j];
+      }
+      U[c].v = a / sd;
+      U[c].t = b;  // the sqrt(det) factors of trace and test cancel
+#pragma unroll
+      for (int k = 0; k < NV; ++k) {
+        U[c].d[k] = (k == c) ? T(1) : T(0);
+        U[c].dt[k] = T(0);
+      }
+    }
+    H F[D][NV];
+    euler_flux<D, H, T>(U, d.fs.gamma, F);
+    T fb[D * NV];
+#pragma unroll
+    for (int dd = 0; dd < D; ++dd)
+#pragma unroll
+      for (int vv = 0; vv < NV; ++vv) {
+        T a = 0;
+#pragma unroll
+        for (int i = 0; i < NB; ++i) a += sDv[(dd * NQ + q1) * NB + i] * sw[el1 * NVB + vv * NB + i];
+        fb[dd * NV + vv] = a;
+      }
+#pragma unroll
+    for (int c = 0; c < NV; ++c) {
+      T a = 0;
+#pragma unroll
+      for (int vv = 0; vv < NV; ++vv)
+#pragma unroll
+        for (int dd = 0; dd < D; ++dd) {
+          T fm = ge[dd * D] * F[0][vv].dt[c];
+#pragma unroll
+          for (int k = 1; k < D; ++k) fm += ge[dd * D + k] * F[k][vv].dt[c];
+          a += fb[dd * NV + vv] * fm;
+        }
+      sU[(el1 * NQ + q1) * NV + c] = a / sd;
+    }
+  }
+  __syncthreads();
+  const T* Bf = SM ? sBf : d.Bf;
+  for (int it = threadIdx.x; it < ne * NVB; it += blockDim.x) {
+    const int el = it / NVB, r = it - el * NVB;
+    const int c = r / NB, j = r - c * NB;
+    T acc = 0;
+#pragma unroll
+    for (int q = 0; q < NQ; ++q) acc += sBv[q * NB + j] * sU[(el * NQ + q) * NV + c];
+    acc += gather_faces_T<T, D, P, SM>(d, Bf, GT, e0 + el, c, j);
+    out[e0 * NVB + it] = acc;
+  }
+}
+
+template <class T, int D, int P>
+cudaError_t jvp_state_adjoint_p(const DGData<T>& d, const T* u, const T* v, const T* w, T* out, T* GT,
+                                const T* escale, T osc, cudaStream_t st) {
+  using O = Ord<D, P>;
+  const int64_t nf = d.F * O::NFQ;
+  if (nf > 0) face_hess_kernel<T, D, P><<<(unsigned)((nf + 127) / 128), 128, 0, st>>>(d, u, v, w, GT, escale, osc);
+  const int64_t eb = (d.E + O::ET - 1) / O::ET;
+  elem_hess_kernel<T, D, P><<<(unsigned)eb, 256, 0, st>>>(d, u, v, w, GT, out, escale, osc);
+  return cudaGetLastError();
+}
+
+// ------------------------------------------------------------ output functionals
+// fixed-order sum of one double per thread into *value (last-block reduction)
+PCEXP_DEV void block_sum_last(double acc, double* value, double* partials, unsigned* counter, bool sqrt_out) {
+  __shared__ double red[8];
+  __shared__ bool last;
+  for (int o = 16; o > 0; o >>= 1) acc += __shfl_xor_sync(0xffffffffu, acc, o);
+  if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = acc;
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    double b = 0;
+    for (int w = 0; w < (int)(blockDim.x >> 5); ++w) b += red[w];
+    partials[blockIdx.x] = b;
+    __threadfence();
+    last = atomicAdd(counter, 1u) == gridDim.x - 1;
+  }
+  __syncthreads();
+  if (last && threadIdx.x == 0) {
+    double b = 0;
+    for (unsigned i = 0; i < gridDim.x; ++i) b += __ldcg(partials + i);
+    *value = sqrt_out ? sqrt(b) : b;
+    *counter = 0;
+  }
+}
+
+// Pressure force on the slip walls along the unit direction a:
+//   J = sum_{wall faces} sum_q |f| w_q p(U_L(x_q)) (n . a),  p = (gamma-1)(E - |m|^2 / (2 rho)),
+// with its gradient dJ/du (trace transpose of dp/dU); value by a fixed-order reduction.
+template <class T, int D, int P>
+__global__ void __launch_bounds__(256) wall_force_kernel(DGData<T> d, int64_t f0, const T* __restrict__ u, double ax,
+                                                         double ay, double az, double* __restrict__ grad,
+                                                         double* __restrict__ value, double* __restrict__ partials,
+                                                         unsigned* counter) {
+  using O = Ord<D, P>;
+  constexpr int NB = O::NB, NFQ = O::NFQ, NV = O::NV, NPERM = O::NPERM, GEO = O::GEO;
+  const double a3[3] = {ax, ay, az};
+  double acc = 0;
+  const T gm = d.fs.gamma - T(1);
+  for (int64_t f = f0 + (int64_t)blockIdx.x * blockDim.x + threadIdx.x; f < d.F; f += (int64_t)gridDim.x * blockDim.x) {
+    if (-d.fel[2 * f + 1] != PCEXP_BC_SLIP_WALL) continue;
+    const int e = d.fel[2 * f];
+    const int fl = d.floc[f] & 0xff;
+    double na = 0;
+    for (int k = 0; k < D; ++k) na += (double)d.fgeo[4 * f + k] * a3[k];
+    const double meas = (double)d.fgeo[4 * f + D];
+    const double isd = 1.0 / (double)d.geo[GEO * (int64_t)e + O::SD];
+    double g[NV * NB];
+    for (int k = 0; k < NV * NB; ++k) g[k] = 0.0;
+    for (int q = 0; q < NFQ; ++q) {
+      const T* b = d.Bf + ((fl * NPERM) * NFQ + q) * NB;
+      double U[NV];
+      for (int c = 0; c < NV; ++c) {
+        double a = 0;
+        for (int j = 0; j < NB; ++j) a += (double)b[j] * (double)u[(int64_t)e * NV * NB + c * NB + j];
+        U[c] = a * isd;
+      }
+      double vel[D], v2 = 0;
+      for (int k = 0; k < D; ++k) {
+        vel[k] = U[1 + k] / U[0];
+        v2 += vel[k] * vel[k];
+      }
+      const double p = (double)gm * (U[NV - 1] - 0.5 * U[0] * v2);
+      const double wq = meas * (double)d.Wf[q] * na;
+      acc += wq * p;
+      double dp[NV];
+      dp[0] = (double)gm * 0.5 * v2;
+      for (int k = 0; k < D; ++k) dp[1 + k] = -(double)gm * vel[k];
+      dp[NV - 1] = (double)gm;
+      for (int c = 0; c < NV; ++c)
+        for (int j = 0; j < NB; ++j) g[c * NB + j] += wq * dp[c] * (double)b[j] * isd;
+    }
+    // on the 2D walls at most two wall faces meet in one element, and a + b is the same
+    // in either order; elements with three or more wall faces sum in arrival order
+    if (grad)
+      for (int k = 0; k < NV * NB; ++k) atomicAdd(grad + (int64_t)e * NV * NB + k, g[k]);
+  }
+  block_sum_last(acc, value, partials, counter, false);
+}
+
+// Vortex-error functional J = ||U_h - U_exact||_L2 (all conservative variables) with the
+// exact state of the translated isentropic vortex at the volume points, and the
+// unnormalised gradient sum_q w_q (U_h - U_ex)_v dU_h/du_{e,v,j} (scaled by 1/J afterwards).
+// prm: eps, x_c, y_c, period (<= 0: none), t.  The field lies in the x-y plane.
+template <class T, int D, int P>
+__global__ void __launch_bounds__(256) vortex_error_kernel(DGData<T> d, const T* __restrict__ u,
+                                                           const double* __restrict__ xq, double eps, double xc,
+                                                           double yc, double period, double t,
+                                                           double* __restrict__ grad, double* __restrict__ value,
+                                                           double* __restrict__ partials, unsigned* counter) {
+  using O = Ord<D, P>;
+  constexpr int NB = O::NB, NQ = O::NQ, NV = O::NV, GEO = O::GEO;
+  double acc = 0;
+  const double g = (double)d.fs.gamma, rinf = (double)d.fs.rho, pinf = (double)d.fs.p;
+  const double u0 = (double)d.fs.vel[0], v0 = (double)d.fs.vel[1];
+  const double Tinf = pinf / rinf, pi = 3.141592653589793238462643383279502884;
+  for (int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; e < d.E; e += (int64_t)gridDim.x * blockDim.x) {
+    const double sd = (double)d.geo[GEO * e + O::SD];
+    double ge[NV * NB];
+    for (int k = 0; k < NV * NB; ++k) ge[k] = 0.0;
+    for (int q = 0; q < NQ; ++q) {
+      double dx = xq[(e * NQ + q) * D] - (xc + u0 * t), dy = xq[(e * NQ + q) * D + 1] - (yc + v0 * t);
+      if (period > 0) {
+        dx -= period * nearbyint(dx / period);
+        dy -= period * nearbyint(dy / period);
+      }
+      const double r2 = dx * dx + dy * dy;
+      const double fe = eps / (2 * pi) * exp(0.5 * (1 - r2));
+      const double uu = u0 - fe * dy, vv = v0 + fe * dx;
+      const double Tv = Tinf - (g - 1) * eps * eps / (8 * g * pi * pi) * exp(1 - r2);
+      const double rho = rinf * pow(Tv / Tinf, 1.0 / (g - 1));
+      const double p = rho * Tv;
+      double Ue[NV];
+      Ue[0] = rho;
+      Ue[1] = rho * uu;
+      Ue[2] = rho * vv;
+      if (D == 3) Ue[3] = 0.0;
+      Ue[NV - 1] = p / (g - 1) + 0.5 * rho * (uu * uu + vv * vv);
+      const double wq = (double)d.Wv[q] * sd * sd;  // |det A| w^_q
+      for (int c = 0; c < NV; ++c) {
+        double a = 0;
+        for (int j = 0; j < NB; ++j) a += (double)d.Bv[q * NB + j] * (double)u[e * NV * NB + c * NB + j];
+        const double diff = a / sd - Ue[c];
+        acc += wq * diff * diff;
+        for (int j = 0; j < NB; ++j) ge[c * NB + j] += wq * diff * (double)d.Bv[q * NB + j] / sd;
+      }
+    }
+    if (grad)
+      for (int k = 0; k < NV * NB; ++k) grad[e * NV * NB + k] = ge[k];
+  }
+  block_sum_last(acc, value, partials, counter, true);
+}
+
+// ------------------------------------------------------------------ time step
+// dt_e = CFL h_e / ((2p+1)(|v| + c)) with v, c at the element centroid (Eq. x3d).
+template <class T, int D, int P>
+__global__ void __launch_bounds__(256) local_dt_kernel(DGData<T> d, const T* __restrict__ u,
+                                                       const double* cfl_dev, double cfl_host,
+                                                       T* __restrict__ dte, double* __restrict__ dtmin,
+                                                       double* __restrict__ partials,
+                                                       unsigned* __restrict__ counter) {
+  using O = Ord<D, P>;
+  constexpr int NB = O::NB, NV = O::NV, GEO = O::GEO;
+  __shared__ double red[8];
+  __shared__ bool last;
+  const double cfl = cfl_dev ? *cfl_dev : cfl_host;
+  double mn = DBL_MAX;
+  for (int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; e < d.E; e += (int64_t)gridDim.x * blockDim.x) {
+    const T isd = T(1) / d.geo[GEO * e + O::SD];
+    double U[NV];
+    for (int v = 0; v < NV; ++v) {
+      T a = 0;
+      for (int j = 0; j < NB; ++j) a += d.Bc[j] * u[e * NV * NB + v * NB + j];
+      U[v] = (double)(a * isd);
+    }
+    const double gam = (double)d.fs.gamma;
+    double v2 = 0;
+    for (int k = 0; k < D; ++k) v2 += (U[1 + k] / U[0]) * (U[1 + k] / U[0]);
+    const double p = (gam - 1.0) * (U[NV - 1] - 0.5 * U[0] * v2);
+    const double c = sqrt(gam * p / U[0]);
+    const double h = (double)d.geo[GEO * e + O::HE];
+    const double dt = cfl * h / ((2 * d.p + 1) * (sqrt(v2) + c));
+    if (dte) dte[e] = (T)dt;
+    mn = fmin(mn, dt);
+  }
+  for (int o = 16; o > 0; o >>= 1) mn = fmin(mn, __shfl_xor_sync(0xffffffffu, mn, o));
+  if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = mn;
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    double b = red[0];
+    for (int w = 1; w < (int)(blockDim.x >> 5); ++w) b = fmin(b, red[w]);
+    partials[blockIdx.x] = b;
+    __threadfence();
+    last = atomicAdd(counter, 1u) == gridDim.x - 1;
+  }
+  __syncthreads();
+  if (last && threadIdx.x == 0) {
+    double b = DBL_MAX;
+    for (unsigned i = 0; i < gridDim.x; ++i) b = fmin(b, __ldcg(partials + i));
+    *dtmin = b;
+    *counter = 0;
+  }
+}
+
+// ------------------------------------------------------------------ launchers
+// The launchers below dispatch on p for one dimension D; orders above PMAX<D> are
+// rejected when a context is created.
+template <int D> constexpr int PMAX = D == 2 ? 3 : 2;
+
+#define PCEXP_PSWITCH(D, CALL)                       \
+  switch (d.p) {                                     \
+    case 0: { constexpr int P_ = 0; return CALL; }   \
+    case 1: { constexpr int P_ = 1; return CALL; }   \
+    case 2: { constexpr int P_ = 2; return CALL; }   \
+    case 3: {                                        \
+      if constexpr (PMAX<D> >= 3) {                  \
+        constexpr int P_ = PMAX<D> >= 3 ? 3 : 0;     \
+        return CALL;                                 \
+      }                                              \
+      break;                                         \
+    }                                                \
+  }                                                  \
+  return cudaErrorInvalidValue;
+
+template <class T, int D>
+cudaError_t launch_dg_operator_d(const DGData<T>& d, const T* u, const T* du, T* out, T* G, const T* escale,
+                                 const int* skip, cudaStream_t st, const cudaEvent_t* ev, const double* oscale) {
+  PCEXP_PSWITCH(D, (dg_op_p<T, D, P_>(d, u, du, out, G, escale, skip, oscale, st, ev)))
+}
+template <class T, int D>
+cudaError_t launch_linearize_d(const DGData<T>& d, const T* u, LinData<T> lin, cudaStream_t st) {
+  PCEXP_PSWITCH(D, (linearize_p<T, D, P_>(d, u, lin, st)))
+}
+template <class T, int D>
+cudaError_t launch_jac_apply_d(const DGData<T>& d, LinData<T> lin, const T* dv, T* out, T* G, const T* escale,
+                               const int* skip, const double* oscale, cudaStream_t st, const cudaEvent_t* ev) {
+  PCEXP_PSWITCH(D, (jac_apply_p<T, D, P_>(d, lin, dv, out, G, escale, skip, oscale, st, ev)))
+}
+template <class T, int D>
+cudaError_t launch_jac_adjoint_d(const DGData<T>& d, LinData<T> lin, const T* w, T* out, T* GT, const T* escale,
+                                 T osc, cudaStream_t st) {
+  PCEXP_PSWITCH(D, (jac_adjoint_p<T, D, P_>(d, lin, w, out, GT, escale, osc, st)))
+}
+template <class T, int D>
+cudaError_t launch_jvp_state_adjoint_d(const DGData<T>& d, const T* u, const T* v, const T* w, T* out, T* GT,
+                                       const T* escale, T osc, cudaStream_t st) {
+  PCEXP_PSWITCH(D, (jvp_state_adjoint_p<T, D, P_>(d, u, v, w, out, GT, escale, osc, st)))
+}
+
+template <class T, int D, int P>
+cudaError_t wall_force_p(const DGData<T>& d, int64_t f0, const T* u, double ax, double ay, double az, double* grad,
+                         double* value, double* partials, unsigned* counter, cudaStream_t st) {
+  const int64_t nb = d.F - f0;
+  unsigned g = (unsigned)((nb + 255) / 256);
+  if (g < 1) g = 1;
+  if (g > RED_BLOCKS) g = RED_BLOCKS;
+  wall_force_kernel<T, D, P><<<g, 256, 0, st>>>(d, f0, u, ax, ay, az, grad, value, partials, counter);
+  return cudaGetLastError();
+}
+template <class T, int D>
+cudaError_t launch_wall_force_d(const DGData<T>& d, int64_t f0, const T* u, double ax, double ay, double az,
+                                double* grad, double* value, double* partials, unsigned* counter, cudaStream_t st) {
+  PCEXP_PSWITCH(D, (wall_force_p<T, D, P_>(d, f0, u, ax, ay, az, grad, value, partials, counter, st)))
+}
+
+template <class T, int D, int P>
+cudaError_t vortex_error_p(const DGData<T>& d, const T* u, const double* xq, const double* prm, double* grad,
+                           double* value, double* partials, unsigned* counter, cudaStream_t st) {
+  int64_t nb = (d.E + 255) / 256;
+  if (nb > RED_BLOCKS) nb = RED_BLOCKS;
+  vortex_error_kernel<T, D, P><<<(unsigned)(nb < 1 ? 1 : nb), 256, 0, st>>>(
+      d, u, xq, prm[0], prm[1], prm[2], prm[3], prm[4], grad, value, partials, counter);
+  return cudaGetLastError();
+}
+template <class T, int D>
+cudaError_t launch_vortex_error_d(const DGData<T>& d, const T* u, const double* xq, const double* prm, double* grad,
+                                  double* value, double* partials, unsigned* counter, cudaStream_t st) {
+  PCEXP_PSWITCH(D, (vortex_error_p<T, D, P_>(d, u, xq, prm, grad, value, partials, counter, st)))
+}
+
+template <class T, int D, int P>
+cudaError_t local_dt_p(const DGData<T>& d, const T* u, const double* cfl_dev, double cfl, T* dte, double* dtmin,
+                       double* partials, unsigned* counter, cudaStream_t st) {
+  int64_t nb = (d.E + 255) / 256;
+  if (nb > RED_BLOCKS) nb = RED_BLOCKS;
+  local_dt_kernel<T, D, P><<<(unsigned)nb, 256, 0, st>>>(d, u, cfl_dev, cfl, dte, dtmin, partials, counter);
+  return cudaGetLastError();
+}
+template <class T, int D>
+cudaError_t launch_local_dt_d(const DGData<T>& d, const T* u, const double* cfl_dev, double cfl, T* dte,
+                              double* dtmin, double* partials, unsigned* counter, cudaStream_t st) {
+  PCEXP_PSWITCH(D, (local_dt_p<T, D, P_>(d, u, cfl_dev, cfl, dte, dtmin, partials, counter, st)))
+}
+
+#undef PCEXP_PSWITCH
+
+#define PCEXP_INST_D(T, D)                                                                                         \
+  template cudaError_t launch_dg_operator_d<T, D>(const DGData<T>&, const T*, const T*, T*, T*, const T*,           \
+                                                  const int*, cudaStream_t, const cudaEvent_t*, const double*);    \
+  template cudaError_t launch_linearize_d<T, D>(const DGData<T>&, const T*, LinData<T>, cudaStream_t);             \
+  template cudaError_t launch_jac_apply_d<T, D>(const DGData<T>&, LinData<T>, const T*, T*, T*, const T*,          \
+                                                const int*, const double*, cudaStream_t, const cudaEvent_t*);      \
+  template cudaError_t launch_jac_adjoint_d<T, D>(const DGData<T>&, LinData<T>, const T*, T*, T*, const T*, T,     \
+                                                  cudaStream_t);                                                   \
+  template cudaError_t launch_jvp_state_adjoint_d<T, D>(const DGData<T>&, const T*, const T*, const T*, T*, T*,    \
+                                                        const T*, T, cudaStream_t);                                \
+  template cudaError_t launch_wall_force_d<T, D>(const DGData<T>&, int64_t, const T*, double, double, double,      \
+                                                 double*, double*, double*, unsigned*, cudaStream_t);              \
+  template cudaError_t launch_vortex_error_d<T, D>(const DGData<T>&, const T*, const double*, const double*,       \
+                                                   double*, double*, double*, unsigned*, cudaStream_t);            \
+  template cudaError_t launch_local_dt_d<T, D>(const DGData<T>&, const T*, const double*, double, T*, double*,     \
+                                               double*, unsigned*, cudaStream_t);
+
+}  // namespace pcexp

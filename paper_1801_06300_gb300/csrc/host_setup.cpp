@@ -1,16 +1,25 @@
 // Host preprocessing: quadrature, reference basis, paper-basis transform,
-// element geometry and the face list (Sec. 4.2-4.3 of the paper).
+// element geometry and the face list (Sec. 4.2-4.3 of the paper), for
+// triangles (dim 2) and tetrahedra (dim 3).
 //
 // Quadrature (the paper does not fix it; same reading as the documented
-// rules): Gauss-Legendre with p+1 points on edges; on triangles the collapsed
-// product rule Gauss-Legendre x Gauss-Jacobi(1,0) with p+1 points per
-// direction, mapped to the physical triangle (v0, v1, v2) by
-// x = v0 + xi (v1 - v0) + eta (v2 - v0), xi = a (1 - b), eta = b.
+// rules): p+1 Gauss points per direction.  Edges: Gauss-Legendre.  Triangles
+// (elements in 2D, faces in 3D): collapsed product rule Gauss-Legendre x
+// Gauss-Jacobi(1,0), xi = a (1 - b), eta = b.  Tetrahedra: Gauss-Legendre x
+// Gauss-Jacobi(1,0) x Gauss-Jacobi(2,0), xi = a (1-b)(1-c), eta = b (1-c),
+// zeta = c.  A simplex (v0, ..., vD) maps x = v0 + sum_k xi_k (v_k - v0).
 // Nodes are found here by bisection on sign changes of the three-term
 // recurrence, weights from the closed Christoffel form.
+//
+// Faces: local face f of an element is the face opposite vertex f, with
+// vertices f+1, ..., f+D (mod D+1).  A face's points are the face rule on its
+// L element (the lower element index) in that vertex order; the R element sees
+// the same points through the permutation of its local face vertices that
+// matches the L element's (on periodic master vertices).
 #include "host_setup.h"
 
 #include <algorithm>
+#include <array>
 #include <cmath>
 #include <unordered_map>
 
@@ -74,21 +83,59 @@ void gauss_jacobi(int n, long double a, long double b, std::vector<long double>&
   }
 }
 
-struct Poly2 {
-  int ex, ey;
+struct Mono {
+  int e[3];
 };
 
-std::vector<Poly2> graded_exponents(int p) {
-  std::vector<Poly2> e;
+// graded order: by total degree, then descending x-power, then descending y-power
+std::vector<Mono> graded_exponents(int dim, int p) {
+  std::vector<Mono> out;
   for (int deg = 0; deg <= p; ++deg)
-    for (int px = deg; px >= 0; --px) e.push_back({px, deg - px});
-  return e;
+    for (int px = deg; px >= 0; --px) {
+      if (dim == 2) {
+        out.push_back({{px, deg - px, 0}});
+      } else {
+        for (int py = deg - px; py >= 0; --py) out.push_back({{px, py, deg - px - py}});
+      }
+    }
+  return out;
 }
 
-long double ipow(long double x, int k) {
-  long double r = 1.0L;
+template <class R> R ipow(R x, int k) {
+  R r = 1;
   for (int i = 0; i < k; ++i) r *= x;
   return r;
+}
+
+// monomial k and its derivative along d at a point x (dim coordinates)
+template <class R> R mono_val(const Mono& m, const R* x, int dim) {
+  R r = 1;
+  for (int d = 0; d < dim; ++d) r *= ipow(x[d], m.e[d]);
+  return r;
+}
+template <class R> R mono_der(const Mono& m, int dd, const R* x, int dim) {
+  if (m.e[dd] == 0) return R(0);
+  R r = R(m.e[dd]) * ipow(x[dd], m.e[dd] - 1);
+  for (int d = 0; d < dim; ++d)
+    if (d != dd) r *= ipow(x[d], m.e[d]);
+  return r;
+}
+
+struct Key {
+  int64_t a, b, c;
+  bool operator==(const Key& o) const { return a == o.a && b == o.b && c == o.c; }
+};
+struct KeyHash {
+  size_t operator()(const Key& k) const {
+    uint64_t h = (uint64_t)k.a * 0x9E3779B97F4A7C15ull;
+    h ^= (uint64_t)k.b + 0x632BE59BD9B4E019ull + (h << 6) + (h >> 2);
+    h ^= (uint64_t)k.c + 0x85157AF5ull + (h << 6) + (h >> 2);
+    return (size_t)h;
+  }
+};
+Key sorted_key(int64_t* v, int n) {
+  std::sort(v, v + n);
+  return Key{v[0], v[1], n > 2 ? v[2] : -1};
 }
 
 }  // namespace
@@ -137,163 +184,263 @@ RuleTri collapsed_triangle(int n) {
   return t;
 }
 
-int n_basis_2d(int p) { return (p + 1) * (p + 2) / 2; }
+int n_basis(int dim, int p) { return dim == 2 ? (p + 1) * (p + 2) / 2 : (p + 1) * (p + 2) * (p + 3) / 6; }
+
+RuleTet collapsed_tetra(int n) {
+  Rule1D a = gauss_legendre_unit(n), b = gauss_jacobi_unit(n, 1), c = gauss_jacobi_unit(n, 2);
+  RuleTet t;
+  for (int i = 0; i < n; ++i)
+    for (int j = 0; j < n; ++j)
+      for (int k = 0; k < n; ++k) {
+        t.xi.push_back(a.x[i] * (1.0L - b.x[j]) * (1.0L - c.x[k]));
+        t.eta.push_back(b.x[j] * (1.0L - c.x[k]));
+        t.zeta.push_back(c.x[k]);
+        t.w.push_back(a.w[i] * b.w[j] * c.w[k]);
+      }
+  return t;
+}
 
 int build_setup(const pcexp_mesh& mesh, int p, Setup& s, std::string& msg) {
-  if (mesh.dim != 2) {
-    msg = "only triangle meshes (dim = 2) are supported";
+  const int D = mesh.dim;
+  if (D != 2 && D != 3) {
+    msg = "mesh dimension must be 2 (triangles) or 3 (tetrahedra)";
     return PCEXP_ERR_UNSUPPORTED;
   }
   if (p < 0 || p > 3) {
     msg = "order p must be 0..3";
     return PCEXP_ERR_INVALID_ARG;
   }
+  if (D == 3 && p > 2) {
+    msg = "tetrahedra are supported up to p = 2";
+    return PCEXP_ERR_UNSUPPORTED;
+  }
   if (mesh.n_elem <= 0 || mesh.n_vert <= 0 || !mesh.coords || !mesh.elem_vert) {
     msg = "empty mesh";
     return PCEXP_ERR_INVALID_ARG;
   }
-  const int nb = n_basis_2d(p), n1 = p + 1;
+  const int NF = D + 1, NPERM = D == 2 ? 2 : 6, GEO = D == 2 ? 8 : 12;
+  const int n1 = p + 1, nb = n_basis(D, p);
+  s.dim = D;
+  s.nv = D + 2;
   s.p = p;
   s.nb = nb;
-  s.nq = n1 * n1;
-  s.nfq = n1;
+  s.nq = D == 2 ? n1 * n1 : n1 * n1 * n1;
+  s.nfq = D == 2 ? n1 : n1 * n1;
   s.E = mesh.n_elem;
   const int64_t E = s.E;
   const int nq = s.nq, nfq = s.nfq;
 
-  // ---- reference rule and reference orthonormal basis (MGS of monomials in (xi-1/3, eta-1/3))
-  RuleTri tri = collapsed_triangle(n1);
-  Rule1D edge = gauss_legendre_unit(n1);
-  std::vector<Poly2> ex = graded_exponents(p);
-  auto mono = [&](int k, long double xi, long double eta) {
-    return ipow(xi - 1.0L / 3, ex[k].ex) * ipow(eta - 1.0L / 3, ex[k].ey);
-  };
-  auto dmono = [&](int k, int d, long double xi, long double eta) -> long double {
-    if (d == 0)
-      return ex[k].ex ? ex[k].ex * ipow(xi - 1.0L / 3, ex[k].ex - 1) * ipow(eta - 1.0L / 3, ex[k].ey) : 0.0L;
-    return ex[k].ey ? ex[k].ey * ipow(xi - 1.0L / 3, ex[k].ex) * ipow(eta - 1.0L / 3, ex[k].ey - 1) : 0.0L;
-  };
-  std::vector<long double> Cr(nb * nb, 0.0L);  // phi^_i = sum_k Cr[i][k] mono_k
+  // ---- reference rules (long double, once)
+  std::vector<std::array<long double, 3>> xr(nq);
+  std::vector<long double> wr(nq);
+  if (D == 2) {
+    RuleTri tri = collapsed_triangle(n1);
+    for (int q = 0; q < nq; ++q) {
+      xr[q] = {tri.xi[q], tri.eta[q], 0.0L};
+      wr[q] = tri.w[q];
+    }
+  } else {
+    RuleTet tet = collapsed_tetra(n1);
+    for (int q = 0; q < nq; ++q) {
+      xr[q] = {tet.xi[q], tet.eta[q], tet.zeta[q]};
+      wr[q] = tet.w[q];
+    }
+  }
+  // face rule as barycentrics over the face's D vertices, weights summing to 1 (2D) or 1/2 (3D)
+  std::vector<std::array<long double, 3>> lam(nfq);
+  std::vector<long double> wf(nfq);
+  if (D == 2) {
+    Rule1D edge = gauss_legendre_unit(n1);
+    for (int q = 0; q < nfq; ++q) {
+      lam[q] = {1.0L - edge.x[q], edge.x[q], 0.0L};
+      wf[q] = edge.w[q];
+    }
+  } else {
+    RuleTri tri = collapsed_triangle(n1);
+    for (int q = 0; q < nfq; ++q) {
+      lam[q] = {1.0L - tri.xi[q] - tri.eta[q], tri.xi[q], tri.eta[q]};
+      wf[q] = tri.w[q];
+    }
+  }
+
+  // ---- reference orthonormal basis: MGS of monomials about the reference centroid
+  const std::vector<Mono> ex = graded_exponents(D, p);
+  const long double cen = 1.0L / (D + 1);
+  std::vector<long double> Cr(nb * nb, 0.0L);  // phi^_i = sum_k Cr[i][k] mono_k(xi - cen)
   {
     std::vector<long double> vals(nb * nq), psi(nb * nq);
     for (int k = 0; k < nb; ++k)
-      for (int q = 0; q < nq; ++q) vals[k * nq + q] = mono(k, tri.xi[q], tri.eta[q]);
+      for (int q = 0; q < nq; ++q) {
+        long double y[3] = {xr[q][0] - cen, xr[q][1] - cen, xr[q][2] - cen};
+        vals[k * nq + q] = mono_val(ex[k], y, D);
+      }
     for (int i = 0; i < nb; ++i) {
       std::vector<long double> c(nb, 0.0L), v(vals.begin() + i * nq, vals.begin() + (i + 1) * nq);
       c[i] = 1.0L;
       for (int j = 0; j < i; ++j) {
         long double d = 0;
-        for (int q = 0; q < nq; ++q) d += tri.w[q] * v[q] * psi[j * nq + q];
+        for (int q = 0; q < nq; ++q) d += wr[q] * v[q] * psi[j * nq + q];
         for (int q = 0; q < nq; ++q) v[q] -= d * psi[j * nq + q];
         for (int k = 0; k < nb; ++k) c[k] -= d * Cr[j * nb + k];
       }
       long double nr = 0;
-      for (int q = 0; q < nq; ++q) nr += tri.w[q] * v[q] * v[q];
+      for (int q = 0; q < nq; ++q) nr += wr[q] * v[q] * v[q];
       nr = std::sqrt(nr);
       for (int q = 0; q < nq; ++q) psi[i * nq + q] = v[q] / nr;
       for (int k = 0; k < nb; ++k) Cr[i * nb + k] = c[k] / nr;
     }
   }
-  auto phi = [&](int i, long double xi, long double eta) {
+  auto phi = [&](int i, const long double* x) {
+    long double y[3] = {x[0] - cen, x[1] - cen, D == 3 ? x[2] - cen : 0.0L};
     long double r = 0;
-    for (int k = 0; k <= i; ++k) r += Cr[i * nb + k] * mono(k, xi, eta);
+    for (int k = 0; k <= i; ++k) r += Cr[i * nb + k] * mono_val(ex[k], y, D);
     return r;
   };
-  auto dphi = [&](int i, int d, long double xi, long double eta) {
+  auto dphi = [&](int i, int d, const long double* x) {
+    long double y[3] = {x[0] - cen, x[1] - cen, D == 3 ? x[2] - cen : 0.0L};
     long double r = 0;
-    for (int k = 0; k <= i; ++k) r += Cr[i * nb + k] * dmono(k, d, xi, eta);
+    for (int k = 0; k <= i; ++k) r += Cr[i * nb + k] * mono_der(ex[k], d, y, D);
     return r;
   };
   s.Bv.assign(nq * nb, 0);
-  s.Dv.assign(2 * nq * nb, 0);
+  s.Dv.assign(D * nq * nb, 0);
   s.Wv.assign(nq, 0);
   for (int q = 0; q < nq; ++q) {
-    s.Wv[q] = (double)tri.w[q];
+    s.Wv[q] = (double)wr[q];
     for (int j = 0; j < nb; ++j) {
-      s.Bv[q * nb + j] = (double)phi(j, tri.xi[q], tri.eta[q]);
-      for (int d = 0; d < 2; ++d)
-        s.Dv[(d * nq + q) * nb + j] = (double)(tri.w[q] * dphi(j, d, tri.xi[q], tri.eta[q]));
+      s.Bv[q * nb + j] = (double)phi(j, xr[q].data());
+      for (int d = 0; d < D; ++d) s.Dv[(d * nq + q) * nb + j] = (double)(wr[q] * dphi(j, d, xr[q].data()));
     }
   }
-  const long double VX[3] = {0, 1, 0}, VY[3] = {0, 0, 1};
-  s.Bf.assign(3 * nfq * nb, 0);
+  // reference vertices, local face vertices and face-vertex permutations
+  long double VR[4][3] = {{0, 0, 0}, {1, 0, 0}, {0, 1, 0}, {0, 0, 1}};
+  auto fv = [&](int f, int k) { return (f + 1 + k) % (D + 1); };
+  static const int PERM2[2][3] = {{0, 1, 2}, {1, 0, 2}};
+  static const int PERM3[6][3] = {{0, 1, 2}, {0, 2, 1}, {1, 0, 2}, {1, 2, 0}, {2, 0, 1}, {2, 1, 0}};
+  auto perm = [&](int pi, int k) { return D == 2 ? PERM2[pi][k] : PERM3[pi][k]; };
+  s.Bf.assign((size_t)NF * NPERM * nfq * nb, 0);
   s.Wf.assign(nfq, 0);
-  for (int q = 0; q < nfq; ++q) s.Wf[q] = (double)edge.w[q];
-  for (int f = 0; f < 3; ++f) {
-    int a = (f + 1) % 3, b = (f + 2) % 3;
-    for (int q = 0; q < nfq; ++q) {
-      long double t = edge.x[q];
-      long double xi = VX[a] + t * (VX[b] - VX[a]), eta = VY[a] + t * (VY[b] - VY[a]);
-      for (int j = 0; j < nb; ++j) s.Bf[(f * nfq + q) * nb + j] = (double)phi(j, xi, eta);
-    }
-  }
+  for (int q = 0; q < nfq; ++q) s.Wf[q] = (double)wf[q];
+  for (int f = 0; f < NF; ++f)
+    for (int pi = 0; pi < NPERM; ++pi)
+      for (int q = 0; q < nfq; ++q) {
+        long double x[3] = {0, 0, 0};
+        for (int k = 0; k < D; ++k)
+          for (int d = 0; d < 3; ++d) x[d] += lam[q][k] * VR[fv(f, perm(pi, k))][d];
+        for (int j = 0; j < nb; ++j) s.Bf[(((size_t)f * NPERM + pi) * nfq + q) * nb + j] = (double)phi(j, x);
+      }
   s.Bc.assign(nb, 0);
-  for (int j = 0; j < nb; ++j) s.Bc[j] = (double)phi(j, 1.0L / 3, 1.0L / 3);
+  {
+    long double x[3] = {cen, cen, D == 3 ? cen : 0.0L};
+    for (int j = 0; j < nb; ++j) s.Bc[j] = (double)phi(j, x);
+  }
 
-  // ---- element geometry and the paper-basis transform Q_e (Eq. basis, Algorithm 1)
+  // ---- element geometry and the paper-basis transform Q_e (Eq. basis, Algorithm 1).
+  // Per element in double on offsets from v0 (edge vectors are exact), so the
+  // centroid-scaled monomials keep full relative precision far from the origin.
   const double* X = mesh.coords;
   const int32_t* EV = mesh.elem_vert;
-  s.geo.assign(E * 8, 0.0);
-  s.xqphys.assign(E * nq * 2, 0.0);
-  s.Q.assign(E * nb * nb, 0.0);
+  s.geo.assign((size_t)E * GEO, 0.0);
+  s.xqphys.assign((size_t)E * nq * D, 0.0);
+  s.Q.assign((size_t)E * nb * nb, 0.0);
   s.volume = 0;
+  const double fact = D == 2 ? 2.0 : 6.0;
+  std::vector<double> rq(nq * 3), pw(nq), psi(nb * nq), vv(nq);
   for (int64_t e = 0; e < E; ++e) {
-    int32_t v[3] = {EV[3 * e], EV[3 * e + 1], EV[3 * e + 2]};
-    for (int k = 0; k < 3; ++k)
+    int32_t v[4];
+    for (int k = 0; k <= D; ++k) {
+      v[k] = EV[(D + 1) * e + k];
       if (v[k] < 0 || v[k] >= mesh.n_vert) {
         msg = "element vertex out of range";
         return PCEXP_ERR_MESH;
       }
-    long double x0 = X[2 * v[0]], y0 = X[2 * v[0] + 1];
-    long double x1 = X[2 * v[1]], y1 = X[2 * v[1] + 1];
-    long double x2 = X[2 * v[2]], y2 = X[2 * v[2] + 1];
-    long double A00 = x1 - x0, A01 = x2 - x0, A10 = y1 - y0, A11 = y2 - y0;
-    long double det = A00 * A11 - A01 * A10;
+    }
+    double A[3][3] = {{0, 0, 0}, {0, 0, 0}, {0, 0, 0}};  // columns: v_k - v0
+    for (int k = 0; k < D; ++k)
+      for (int d = 0; d < D; ++d) A[d][k] = X[D * v[k + 1] + d] - X[D * v[0] + d];
+    double det, Ai[3][3];
+    if (D == 2) {
+      det = A[0][0] * A[1][1] - A[0][1] * A[1][0];
+      Ai[0][0] = A[1][1] / det;
+      Ai[0][1] = -A[0][1] / det;
+      Ai[1][0] = -A[1][0] / det;
+      Ai[1][1] = A[0][0] / det;
+    } else {
+      const double c00 = A[1][1] * A[2][2] - A[1][2] * A[2][1], c01 = A[1][2] * A[2][0] - A[1][0] * A[2][2],
+                   c02 = A[1][0] * A[2][1] - A[1][1] * A[2][0];
+      det = A[0][0] * c00 + A[0][1] * c01 + A[0][2] * c02;
+      Ai[0][0] = c00 / det;
+      Ai[1][0] = c01 / det;
+      Ai[2][0] = c02 / det;
+      Ai[0][1] = (A[0][2] * A[2][1] - A[0][1] * A[2][2]) / det;
+      Ai[1][1] = (A[0][0] * A[2][2] - A[0][2] * A[2][0]) / det;
+      Ai[2][1] = (A[0][1] * A[2][0] - A[0][0] * A[2][1]) / det;
+      Ai[0][2] = (A[0][1] * A[1][2] - A[0][2] * A[1][1]) / det;
+      Ai[1][2] = (A[0][2] * A[1][0] - A[0][0] * A[1][2]) / det;
+      Ai[2][2] = (A[0][0] * A[1][1] - A[0][1] * A[1][0]) / det;
+    }
     if (!(det > 0)) {
       msg = "inverted or degenerate element " + std::to_string(e);
       return PCEXP_ERR_MESH;
     }
-    long double perim = std::hypot((double)(x1 - x0), (double)(y1 - y0)) +
-                        std::hypot((double)(x2 - x1), (double)(y2 - y1)) +
-                        std::hypot((double)(x0 - x2), (double)(y0 - y2));
-    double* g = &s.geo[8 * e];
-    g[0] = (double)(A11 / det);
-    g[1] = (double)(-A01 / det);
-    g[2] = (double)(-A10 / det);
-    g[3] = (double)(A00 / det);
-    long double sdet = std::sqrt(det);
-    g[4] = (double)sdet;
-    g[5] = (double)(2.0L * det / perim);  // h = 2 d |E| / |dE| with |E| = det / 2, d = 2
-    s.volume += (double)(0.5L * det);
-    // physical quadrature points
-    std::vector<long double> px(nq), py(nq), pw(nq);
-    long double xc = 0, yc = 0, area = 0;
-    for (int q = 0; q < nq; ++q) {
-      px[q] = x0 + tri.xi[q] * A00 + tri.eta[q] * A01;
-      py[q] = y0 + tri.xi[q] * A10 + tri.eta[q] * A11;
-      pw[q] = tri.w[q] * det;
-      xc += pw[q] * px[q];
-      yc += pw[q] * py[q];
-      area += pw[q];
-      s.xqphys[(e * nq + q) * 2] = (double)px[q];
-      s.xqphys[(e * nq + q) * 2 + 1] = (double)py[q];
+    // boundary measure |dE|
+    double bnd = 0;
+    for (int f = 0; f < NF; ++f) {
+      double P[3][3];
+      for (int k = 0; k < D; ++k)
+        for (int d = 0; d < D; ++d) P[k][d] = X[D * v[fv(f, k)] + d];
+      if (D == 2) {
+        bnd += std::hypot(P[1][0] - P[0][0], P[1][1] - P[0][1]);
+      } else {
+        const double a[3] = {P[1][0] - P[0][0], P[1][1] - P[0][1], P[1][2] - P[0][2]};
+        const double b[3] = {P[2][0] - P[0][0], P[2][1] - P[0][1], P[2][2] - P[0][2]};
+        const double cx = a[1] * b[2] - a[2] * b[1], cy = a[2] * b[0] - a[0] * b[2], cz = a[0] * b[1] - a[1] * b[0];
+        bnd += 0.5 * std::sqrt(cx * cx + cy * cy + cz * cz);
+      }
     }
-    xc /= area;
-    yc /= area;
-    long double Lx = 0.5L * (std::max({x0, x1, x2}) - std::min({x0, x1, x2}));
-    long double Ly = 0.5L * (std::max({y0, y1, y2}) - std::min({y0, y1, y2}));
+    double* g = &s.geo[(size_t)GEO * e];
+    for (int r = 0; r < D; ++r)
+      for (int c = 0; c < D; ++c) g[r * D + c] = Ai[r][c];
+    const double sdet = std::sqrt(det);
+    g[D * D] = sdet;
+    g[D * D + 1] = 2.0 * D * (det / fact) / bnd;  // h = 2 d |E| / |dE|
+    s.volume += det / fact;
+    // quadrature points as offsets from v0, weights, centroid offset and half-extents
+    double rc[3] = {0, 0, 0}, area = 0;
+    for (int q = 0; q < nq; ++q) {
+      for (int d = 0; d < D; ++d) {
+        double a = 0;
+        for (int k = 0; k < D; ++k) a += A[d][k] * (double)xr[q][k];
+        rq[q * 3 + d] = a;
+        s.xqphys[((size_t)e * nq + q) * D + d] = X[D * v[0] + d] + a;
+      }
+      pw[q] = (double)wr[q] * det;
+      for (int d = 0; d < D; ++d) rc[d] += pw[q] * rq[q * 3 + d];
+      area += pw[q];
+    }
+    double Lh[3];
+    for (int d = 0; d < D; ++d) {
+      rc[d] /= area;
+      double mn = 0, mx = 0;  // offsets of the vertices from v0 (v0 itself at 0)
+      for (int k = 0; k < D; ++k) {
+        mn = std::min(mn, A[d][k]);
+        mx = std::max(mx, A[d][k]);
+      }
+      Lh[d] = 0.5 * (mx - mn);
+    }
     // paper basis values at the points by MGS (psi_i <- chi_i; psi_i -= <psi_i,psi_j> psi_j; normalise)
-    std::vector<long double> psi(nb * nq);
     for (int i = 0; i < nb; ++i) {
-      std::vector<long double> vv(nq);
-      for (int q = 0; q < nq; ++q)
-        vv[q] = ipow((px[q] - xc) / Lx, ex[i].ex) * ipow((py[q] - yc) / Ly, ex[i].ey);
+      for (int q = 0; q < nq; ++q) {
+        double y[3];
+        for (int d = 0; d < D; ++d) y[d] = (rq[q * 3 + d] - rc[d]) / Lh[d];
+        vv[q] = mono_val(ex[i], y, D);
+      }
       for (int j = 0; j < i; ++j) {
-        long double d = 0;
+        double d = 0;
         for (int q = 0; q < nq; ++q) d += pw[q] * vv[q] * psi[j * nq + q];
         for (int q = 0; q < nq; ++q) vv[q] -= d * psi[j * nq + q];
       }
-      long double nr = 0;
+      double nr = 0;
       for (int q = 0; q < nq; ++q) nr += pw[q] * vv[q] * vv[q];
       nr = std::sqrt(nr);
       for (int q = 0; q < nq; ++q) psi[i * nq + q] = vv[q] / nr;
@@ -301,49 +448,47 @@ int build_setup(const pcexp_mesh& mesh, int p, Setup& s, std::string& msg) {
     // Q[i][j] = <psi_i, phi_j>_E, phi_j = phi^_j / sqrt(det)
     for (int i = 0; i < nb; ++i)
       for (int j = 0; j < nb; ++j) {
-        long double acc = 0;
-        for (int q = 0; q < nq; ++q) acc += pw[q] * psi[i * nq + q] * (long double)s.Bv[q * nb + j];
-        s.Q[(e * nb + i) * nb + j] = (double)(acc / sdet);
+        double acc = 0;
+        for (int q = 0; q < nq; ++q) acc += pw[q] * psi[i * nq + q] * s.Bv[q * nb + j];
+        s.Q[((size_t)e * nb + i) * nb + j] = acc / sdet;
       }
   }
 
-  // ---- faces: match edges on periodic master vertices
-  auto master = [&](int32_t v) -> int64_t { return mesh.vert_master ? mesh.vert_master[v] : v; };
-  auto key2 = [](int64_t a, int64_t b) -> uint64_t {
-    if (a > b) std::swap(a, b);
-    return ((uint64_t)a << 32) | (uint64_t)b;
-  };
-  std::unordered_map<uint64_t, int64_t> first;  // edge -> e*3+f of its first occurrence
-  first.reserve(E * 3);
-  std::unordered_map<uint64_t, int32_t> btag;
+  // ---- faces: match element faces on periodic master vertices
+  auto master = [&](int32_t vtx) -> int64_t { return mesh.vert_master ? mesh.vert_master[vtx] : vtx; };
+  std::unordered_map<Key, int64_t, KeyHash> first;  // face -> e*NF+f of its first occurrence
+  first.reserve((size_t)E * NF);
+  std::unordered_map<Key, int32_t, KeyHash> btag;
   for (int64_t i = 0; i < mesh.n_bface; ++i) {
-    int32_t a = mesh.bface_vert[2 * i], b = mesh.bface_vert[2 * i + 1];
+    int64_t vs[3] = {0, 0, 0};
+    for (int k = 0; k < D; ++k) vs[k] = mesh.bface_vert[(size_t)D * i + k];
     int32_t t = mesh.bface_tag ? mesh.bface_tag[i] : 0;
     if (t != PCEXP_BC_SLIP_WALL && t != PCEXP_BC_FARFIELD) {
       msg = "unknown boundary tag";
       return PCEXP_ERR_MESH;
     }
-    btag[key2(a, b)] = t;
+    btag[sorted_key(vs, D)] = t;
   }
-  std::vector<int64_t> partner(E * 3, -1);
+  std::vector<int64_t> partner((size_t)E * NF, -1);
   for (int64_t e = 0; e < E; ++e)
-    for (int f = 0; f < 3; ++f) {
-      int32_t a = EV[3 * e + (f + 1) % 3], b = EV[3 * e + (f + 2) % 3];
-      uint64_t k = key2(master(a), master(b));
-      auto it = first.find(k);
+    for (int f = 0; f < NF; ++f) {
+      int64_t vs[3] = {0, 0, 0};
+      for (int k = 0; k < D; ++k) vs[k] = master(EV[(D + 1) * e + fv(f, k)]);
+      const Key key = sorted_key(vs, D);
+      auto it = first.find(key);
       if (it == first.end()) {
-        first.emplace(k, e * 3 + f);
+        first.emplace(key, e * NF + f);
       } else {
         if (it->second < 0) {
-          msg = "edge shared by more than two elements";
+          msg = "face shared by more than two elements";
           return PCEXP_ERR_MESH;
         }
-        partner[it->second] = e * 3 + f;
-        partner[e * 3 + f] = it->second;
+        partner[it->second] = e * NF + f;
+        partner[e * NF + f] = it->second;
         it->second = -1;
       }
     }
-  s.ef.assign(E * 3, -1);
+  s.ef.assign((size_t)E * NF, -1);
   s.fel.clear();
   s.floc.clear();
   s.fgeo.clear();
@@ -351,40 +496,75 @@ int build_setup(const pcexp_mesh& mesh, int p, Setup& s, std::string& msg) {
   // interior faces first, in order of their L element
   for (int pass = 0; pass < 2; ++pass)
     for (int64_t e = 0; e < E; ++e)
-      for (int f = 0; f < 3; ++f) {
-        int64_t id = e * 3 + f;
+      for (int f = 0; f < NF; ++f) {
+        const int64_t id = e * NF + f;
         if (s.ef[id] >= 0) continue;
-        int64_t pr = partner[id];
+        const int64_t pr = partner[id];
         if ((pass == 0) != (pr >= 0)) continue;
-        int32_t a = EV[3 * e + (f + 1) % 3], b = EV[3 * e + (f + 2) % 3];
-        double ax = X[2 * a], ay = X[2 * a + 1], bx = X[2 * b], by = X[2 * b + 1];
-        double tx = bx - ax, ty = by - ay, len = std::hypot(tx, ty);
-        int32_t eR, fR = 0;
+        if (F >= (int64_t(1) << 27)) {
+          msg = "too many faces";
+          return PCEXP_ERR_UNSUPPORTED;
+        }
+        int32_t lv[3];
+        for (int k = 0; k < D; ++k) lv[k] = EV[(D + 1) * e + fv(f, k)];
+        double nrm[3] = {0, 0, 0}, meas;
+        if (D == 2) {
+          const double tx = X[2 * lv[1]] - X[2 * lv[0]], ty = X[2 * lv[1] + 1] - X[2 * lv[0] + 1];
+          const double len = std::hypot(tx, ty);
+          nrm[0] = ty / len;
+          nrm[1] = -tx / len;
+          meas = len;
+        } else {
+          double a[3], b[3], o[3];
+          for (int d = 0; d < 3; ++d) {
+            a[d] = X[3 * lv[1] + d] - X[3 * lv[0] + d];
+            b[d] = X[3 * lv[2] + d] - X[3 * lv[0] + d];
+            o[d] = X[3 * lv[0] + d] - X[3 * EV[4 * e + f] + d];  // from the opposite vertex
+          }
+          double c[3] = {a[1] * b[2] - a[2] * b[1], a[2] * b[0] - a[0] * b[2], a[0] * b[1] - a[1] * b[0]};
+          const double cn = std::sqrt(c[0] * c[0] + c[1] * c[1] + c[2] * c[2]);
+          const double sg = (c[0] * o[0] + c[1] * o[1] + c[2] * o[2]) < 0 ? -1.0 : 1.0;
+          for (int d = 0; d < 3; ++d) nrm[d] = sg * c[d] / cn;
+          meas = cn;  // twice the face area: the face weights sum to 1/2
+        }
+        int32_t eR, fR = 0, pR = 0;
         if (pr >= 0) {
-          eR = (int32_t)(pr / 3);
-          fR = (int)(pr % 3);
-          int32_t aR = EV[3 * eR + (fR + 1) % 3], bR = EV[3 * eR + (fR + 2) % 3];
-          if (master(aR) != master(b) || master(bR) != master(a)) {
-            msg = "neighbouring elements traverse a shared edge in the same sense";
+          eR = (int32_t)(pr / NF);
+          fR = (int)(pr % NF);
+          int pi_of[3] = {-1, -1, -1};
+          for (int k = 0; k < D; ++k)
+            for (int j = 0; j < D; ++j)
+              if (master(EV[(D + 1) * (int64_t)eR + fv(fR, j)]) == master(lv[k])) pi_of[k] = j;
+          pR = -1;
+          for (int pi = 0; pi < NPERM; ++pi) {
+            bool ok = true;
+            for (int k = 0; k < D; ++k) ok = ok && perm(pi, k) == pi_of[k];
+            if (ok) pR = pi;
+          }
+          if (pR < 0 || (D == 2 && pR != 1)) {
+            msg = D == 2 ? "neighbouring elements traverse a shared edge in the same sense"
+                         : "shared face vertices do not match";
             return PCEXP_ERR_MESH;
           }
-          s.ef[pr] = (int32_t)(F * 2 + 1);
+          s.ef[pr] = (int32_t)((F << 4) | (1 << 3) | pR);
         } else {
-          auto it = btag.find(key2(a, b));
+          int64_t vs[3] = {0, 0, 0};
+          for (int k = 0; k < D; ++k) vs[k] = lv[k];
+          auto it = btag.find(sorted_key(vs, D));
           if (it == btag.end()) {
-            msg = "boundary edge " + std::to_string(a) + "-" + std::to_string(b) + " has no tag";
+            msg = "boundary face of element " + std::to_string(e) + " has no tag";
             return PCEXP_ERR_MESH;
           }
           eR = -it->second;
         }
-        s.ef[id] = (int32_t)(F * 2);
+        s.ef[id] = (int32_t)(F << 4);
         s.fel.push_back((int32_t)e);
         s.fel.push_back(eR);
-        s.floc.push_back(f | (fR << 8));
-        s.fgeo.push_back(ty / len);
-        s.fgeo.push_back(-tx / len);
-        s.fgeo.push_back(len);
-        s.fgeo.push_back(0.0);
+        s.floc.push_back(f | (fR << 8) | (pR << 16));
+        for (int d = 0; d < 3; ++d)
+          if (d < D) s.fgeo.push_back(nrm[d]);
+        s.fgeo.push_back(meas);
+        if (D == 2) s.fgeo.push_back(0.0);
         ++F;
       }
   s.F = F;

@@ -23,29 +23,37 @@ struct RuleTri {
 };
 RuleTri collapsed_triangle(int n);
 
-int n_basis_2d(int p);
+// Reference-tetrahedron rule: collapsed product rule Gauss-Legendre x
+// Gauss-Jacobi(1,0) x Gauss-Jacobi(2,0), xi = a (1-b)(1-c), eta = b (1-c), zeta = c.
+struct RuleTet {
+  std::vector<long double> xi, eta, zeta, w;
+};
+RuleTet collapsed_tetra(int n);
 
-// Everything the device needs, built once on the host.
+int n_basis(int dim, int p);
+
+// Everything the device needs, built once on the host (D = dim, NF = D + 1 faces
+// per element, NPERM = 2 or 6 face-vertex permutations).
 struct Setup {
   int dim = 2, p = 0, nb = 0, nq = 0, nfq = 0, nv = 4;
   int64_t E = 0, F = 0, F_interior = 0;
   double volume = 0;
   // reference tables (row-major)
-  std::vector<double> Bv;  // [nq][nb]      phi^_j at volume points
-  std::vector<double> Dv;  // [2][nq][nb]   w_q d(phi^_j)/d xi_d
-  std::vector<double> Wv;  // [nq]          reference weights (sum 1/2)
-  std::vector<double> Bf;  // [3][nfq][nb]  phi^_j at face points of local face f (L order)
-  std::vector<double> Wf;  // [nfq]         edge weights on [0, 1]
-  std::vector<double> Bc;  // [nb]          phi^_j at the reference centroid
+  std::vector<double> Bv;  // [nq][nb]              phi^_j at volume points
+  std::vector<double> Dv;  // [D][nq][nb]           w_q d(phi^_j)/d xi_d
+  std::vector<double> Wv;  // [nq]                  reference weights (sum 1/2 or 1/6)
+  std::vector<double> Bf;  // [NF][NPERM][nfq][nb]  phi^_j at face points of local face f, vertices permuted
+  std::vector<double> Wf;  // [nfq]                 face weights (sum 1 on edges, 1/2 on triangles)
+  std::vector<double> Bc;  // [nb]                  phi^_j at the reference centroid
   // per element
-  std::vector<double> geo;     // [E][8]: Ainv00 Ainv01 Ainv10 Ainv11 sdet h 0 0
-  std::vector<double> xqphys;  // [E][nq][2] physical volume points (host projections)
-  std::vector<int32_t> ef;     // [E][3]  face*2 + side of local face f
+  std::vector<double> geo;     // [E][8 or 12]: A^-1 (D x D), sqrt(det A), h
+  std::vector<double> xqphys;  // [E][nq][D] physical volume points (projections, functionals)
+  std::vector<int32_t> ef;     // [E][NF] face slot (face << 4) | (side << 3) | perm
   std::vector<double> Q;       // [E][nb][nb] paper <- internal
   // per face
   std::vector<int32_t> fel;   // [F][2] eL, eR (eR = -tag for boundary faces)
-  std::vector<int32_t> floc;  // [F] fL | (fR << 8)
-  std::vector<double> fgeo;   // [F][4] nx ny len 0
+  std::vector<int32_t> floc;  // [F] fL | (fR << 8) | (permR << 16)
+  std::vector<double> fgeo;   // [F][4] unit normal (D), measure factor
 };
 
 // Returns PCEXP_OK or an error code; msg receives a description on error.

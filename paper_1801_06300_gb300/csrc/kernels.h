@@ -53,37 +53,64 @@ struct StepState {
   double dtmin_scratch;
 };
 
-// Mesh/geometry/tables on the device, for one scalar type.
+// Mesh/geometry/tables on the device, for one scalar type.  D = dim, NV = D + 2,
+// NF = D + 1 faces per element, NPERM = 2 (2D) or 6 (3D) face-vertex permutations.
 template <class T>
 struct DGData {
-  const T* geo;          // [E][8]
-  const int32_t* ef;     // [E][3]
-  const int32_t* fel;    // [F][2]
-  const int32_t* floc;   // [F]
-  const T* fgeo;         // [F][4]
+  const T* geo;          // [E][GEO]: A^-1 (D x D row-major), sqrt|det A|, h; GEO = 8 (2D) or 12 (3D)
+  const int32_t* ef;     // [E][NF]: face slot (face << 4) | (side << 3) | perm
+  const int32_t* fel;    // [F][2]: e_L, e_R (e_R = -tag on boundary faces)
+  const int32_t* floc;   // [F]: f_L | f_R << 8 | perm_R << 16
+  const T* fgeo;         // [F][4]: unit normal (D), measure factor |f| with sum_q Wf = 1 (2D) or 1/2 (3D)
   const T* Bv;           // [nq][nb]
-  const T* Dv;           // [2][nq][nb]
-  const T* Bf;           // [3][nfq][nb]
+  const T* Dv;           // [D][nq][nb]
+  const T* Bf;           // [NF][NPERM][nfq][nb]
   const T* Wf;           // [nfq]
   const T* Bc;           // [nb]
+  const T* Wv;           // [nq] reference volume weights
   int64_t E, F;
   Free<T> fs;
   int p;
+  int dim;
 };
 
 // Point Jacobians of the DG operator at a linearisation state u (structure of
-// arrays: entry k of every point is contiguous).
-//   Avol [32][E*nq]:  k = d'*16 + v*4 + c: sum_d (A^-1)_{d'd} dF_d[v]/dU[c] at volume points
-//   Bface[32][F*nfq]: k = s*16 + v*4 + c: |e| w_q / sqrt(det_s) dF~[v]/dU_s[c], s = L (0), R (1),
-//                     the ghost-state chain rule folded into s = L on boundary faces
+// arrays: entry k of every point is contiguous), NV = D + 2.
+//   Avol [D NV NV][E*nq]:  k = d'*NV*NV + v*NV + c: sum_d (A^-1)_{d'd} dF_d[v]/dU[c] at volume points
+//   Bface[2 NV NV][F*nfq]: k = s*NV*NV + v*NV + c: |f| w_q / sqrt(det_s) dF~[v]/dU_s[c], s = L (0), R (1),
+//                          the ghost-state chain rule folded into s = L on boundary faces
 template <class T>
 struct LinData {
   T* Avol;
   T* Bface;
 };
 
-// ---- DG operator (dg_kernels.cu)
-// out = R(u)  or  out = J(u) du  (du != nullptr); G is face-flux scratch [F][nfq][4].
+// ---- DG operator (dg_kernels.cuh, instantiated per dimension in dg2d.cu / dg3d.cu)
+template <class T, int D>
+cudaError_t launch_dg_operator_d(const DGData<T>& d, const T* u, const T* du, T* out, T* G, const T* escale,
+                                 const int* skip, cudaStream_t st, const cudaEvent_t* ev, const double* oscale);
+template <class T, int D>
+cudaError_t launch_linearize_d(const DGData<T>& d, const T* u, LinData<T> lin, cudaStream_t st);
+template <class T, int D>
+cudaError_t launch_jac_apply_d(const DGData<T>& d, LinData<T> lin, const T* dv, T* out, T* G, const T* escale,
+                               const int* skip, const double* oscale, cudaStream_t st, const cudaEvent_t* ev);
+template <class T, int D>
+cudaError_t launch_jac_adjoint_d(const DGData<T>& d, LinData<T> lin, const T* w, T* out, T* GT, const T* escale,
+                                 T osc, cudaStream_t st);
+template <class T, int D>
+cudaError_t launch_jvp_state_adjoint_d(const DGData<T>& d, const T* u, const T* v, const T* w, T* out, T* GT,
+                                       const T* escale, T osc, cudaStream_t st);
+template <class T, int D>
+cudaError_t launch_wall_force_d(const DGData<T>& d, int64_t f0, const T* u, double ax, double ay, double az,
+                                double* grad, double* value, double* partials, unsigned* counter, cudaStream_t st);
+template <class T, int D>
+cudaError_t launch_vortex_error_d(const DGData<T>& d, const T* u, const double* xq, const double* prm, double* grad,
+                                  double* value, double* partials, unsigned* counter, cudaStream_t st);
+template <class T, int D>
+cudaError_t launch_local_dt_d(const DGData<T>& d, const T* u, const double* cfl_dev, double cfl, T* dte,
+                              double* dtmin, double* partials, unsigned* counter, cudaStream_t st);
+
+// out = R(u)  or  out = J(u) du  (du != nullptr); G is face-flux scratch [F][nfq][NV].
 // escale (nullable): per-element output factor.  skip (nullable): device flag, nonzero = no-op.
 // ev (nullable): three events recorded before the face kernel, between the
 // two kernels and after the element kernel.  oscale (nullable, device): one
@@ -91,31 +118,60 @@ struct LinData {
 template <class T>
 cudaError_t launch_dg_operator(const DGData<T>& d, const T* u, const T* du, T* out, T* G,
                                const T* escale, const int* skip, cudaStream_t st,
-                               const cudaEvent_t* ev = nullptr, const double* oscale = nullptr);
+                               const cudaEvent_t* ev = nullptr, const double* oscale = nullptr) {
+  return d.dim == 3 ? launch_dg_operator_d<T, 3>(d, u, du, out, G, escale, skip, st, ev, oscale)
+                    : launch_dg_operator_d<T, 2>(d, u, du, out, G, escale, skip, st, ev, oscale);
+}
 // Evaluate the point Jacobians at u (once per linearisation state).
 template <class T>
-cudaError_t launch_linearize(const DGData<T>& d, const T* u, LinData<T> lin, cudaStream_t st);
+cudaError_t launch_linearize(const DGData<T>& d, const T* u, LinData<T> lin, cudaStream_t st) {
+  return d.dim == 3 ? launch_linearize_d<T, 3>(d, u, lin, st) : launch_linearize_d<T, 2>(d, u, lin, st);
+}
 // out = J(u) dv from the point Jacobians (same ev / escale / skip / oscale conventions).
 template <class T>
 cudaError_t launch_jac_apply(const DGData<T>& d, LinData<T> lin, const T* dv, T* out, T* G, const T* escale,
-                             const int* skip, const double* oscale, cudaStream_t st, const cudaEvent_t* ev);
-// out = (osc * diag(escale) * J(u))^T w from the point Jacobians; GT is scratch [F][nfq][8].
+                             const int* skip, const double* oscale, cudaStream_t st, const cudaEvent_t* ev) {
+  return d.dim == 3 ? launch_jac_apply_d<T, 3>(d, lin, dv, out, G, escale, skip, oscale, st, ev)
+                    : launch_jac_apply_d<T, 2>(d, lin, dv, out, G, escale, skip, oscale, st, ev);
+}
+// out = (osc * diag(escale) * J(u))^T w from the point Jacobians; GT is scratch [F][nfq][2 NV].
 template <class T>
 cudaError_t launch_jac_adjoint(const DGData<T>& d, LinData<T> lin, const T* w, T* out, T* GT, const T* escale, T osc,
-                               cudaStream_t st);
-// out = (d/du [ (osc diag(escale) J(u) v)^T w ])^T, the second-order adjoint; GT scratch [F][nfq][8].
+                               cudaStream_t st) {
+  return d.dim == 3 ? launch_jac_adjoint_d<T, 3>(d, lin, w, out, GT, escale, osc, st)
+                    : launch_jac_adjoint_d<T, 2>(d, lin, w, out, GT, escale, osc, st);
+}
+// out = (d/du [ (osc diag(escale) J(u) v)^T w ])^T, the second-order adjoint; GT scratch [F][nfq][2 NV].
 template <class T>
 cudaError_t launch_jvp_state_adjoint(const DGData<T>& d, const T* u, const T* v, const T* w, T* out, T* GT,
-                                     const T* escale, T osc, cudaStream_t st);
-// Pressure force on the slip walls along (ax, ay) -> *value, gradient added into grad (nullable);
-// boundary faces are those with index >= f0.
+                                     const T* escale, T osc, cudaStream_t st) {
+  return d.dim == 3 ? launch_jvp_state_adjoint_d<T, 3>(d, u, v, w, out, GT, escale, osc, st)
+                    : launch_jvp_state_adjoint_d<T, 2>(d, u, v, w, out, GT, escale, osc, st);
+}
+// Pressure force on the slip walls along (ax, ay, az) -> *value, gradient added into grad
+// (nullable); boundary faces are those with index >= f0.
 template <class T>
-cudaError_t launch_wall_force(const DGData<T>& d, int64_t f0, const T* u, double ax, double ay, double* grad,
-                              double* value, double* partials, unsigned* counter, cudaStream_t st);
+cudaError_t launch_wall_force(const DGData<T>& d, int64_t f0, const T* u, double ax, double ay, double az,
+                              double* grad, double* value, double* partials, unsigned* counter, cudaStream_t st) {
+  return d.dim == 3 ? launch_wall_force_d<T, 3>(d, f0, u, ax, ay, az, grad, value, partials, counter, st)
+                    : launch_wall_force_d<T, 2>(d, f0, u, ax, ay, az, grad, value, partials, counter, st);
+}
+// ||U_h - U_vortex||_L2 -> *value and its unnormalised gradient (times J) -> grad (nullable);
+// xq: physical volume points [E][nq][D] (FP64); prm (host): eps, x_c, y_c, period, t.
+template <class T>
+cudaError_t launch_vortex_error(const DGData<T>& d, const T* u, const double* xq, const double* prm, double* grad,
+                                double* value, double* partials, unsigned* counter, cudaStream_t st) {
+  return d.dim == 3 ? launch_vortex_error_d<T, 3>(d, u, xq, prm, grad, value, partials, counter, st)
+                    : launch_vortex_error_d<T, 2>(d, u, xq, prm, grad, value, partials, counter, st);
+}
 // dt_e = cfl h_e / ((2p+1)(|v_c| + c_c)) -> dte[E]; min over e -> *dtmin (last-block reduction).
 template <class T>
 cudaError_t launch_local_dt(const DGData<T>& d, const T* u, const double* cfl_dev, double cfl,
-                            T* dte, double* dtmin, double* partials, unsigned* counter, cudaStream_t st);
+                            T* dte, double* dtmin, double* partials, unsigned* counter, cudaStream_t st) {
+  return d.dim == 3 ? launch_local_dt_d<T, 3>(d, u, cfl_dev, cfl, dte, dtmin, partials, counter, st)
+                    : launch_local_dt_d<T, 2>(d, u, cfl_dev, cfl, dte, dtmin, partials, counter, st);
+}
+// ---- dimension-free kernels (dg_common.cu)
 // basis conversions at the interface (Q_e: paper <- internal)
 template <class T>
 cudaError_t launch_paper_to_internal(const double* src, T* dst, const double* Q, int64_t E, int nb, int nv, cudaStream_t st);
@@ -124,6 +180,8 @@ cudaError_t launch_internal_to_paper(const T* src, double* dst, const double* Q,
 // x[e][:] *= s[e] (block of nvb entries per element)
 template <class T>
 cudaError_t launch_scale_elements(T* x, const T* s, int64_t E, int nvb, cudaStream_t st);
+// x *= s (s a device scalar, n entries)
+cudaError_t launch_scale_by_inverse(double* x, const double* s, int64_t n, cudaStream_t st);
 // density residual norm sqrt(sum (R[e][0][i] / s[e])^2) / volume -> ss->res_norm, then the CFL ramp
 template <class T>
 cudaError_t launch_density_norm(const T* R, const T* s, int64_t E, int nb, int nv, double volume,

@@ -62,7 +62,7 @@ extern "C" int pcexp_residual_noalloc(pcexp_ctx* ctx, const double* U, double* R
   int r = ctx_noalloc_view(ctx, &d, &st, &nfq, &fp32, &device);
   if (r != PCEXP_OK) return r;
   if (fp32) return PCEXP_ERR_UNSUPPORTED;
-  if (d.F * nfq * 4 > NOALLOC_FACE_FLUX_DOUBLES) return PCEXP_ERR_INVALID_ARG;
+  if (d.F * nfq * (d.dim + 2) > NOALLOC_FACE_FLUX_DOUBLES) return PCEXP_ERR_INVALID_ARG;
   double* G = nullptr;
   r = scratch_address(device, &G);
   if (r != PCEXP_OK) return r;

@@ -1,6 +1,7 @@
 // Euler physics for the DG kernels (Sec. 4.1, 4.4 of the paper), written once
-// over a scalar type S that is either a real type (the residual) or Tangent<T>
-// (value + directional derivative: the tangent-linear J v kernel).
+// over the dimension D (2 or 3; D + 2 conservative variables) and over a scalar
+// type S that is a real type (the residual), Tangent<T> (value + directional
+// derivative: J v), Jet<T, N> (point Jacobians) or HD<T, N> (second order).
 //
 // Riemann flux: Roe's solver with square-root-density averages and no entropy
 // fix, F~ = 1/2 (F_n(U_L) + F_n(U_R)) - 1/2 sum_k |lambda_k| alpha_k r_k.
@@ -171,215 +172,268 @@ template <class T, int N> struct Lift<Jet<T, N>, T> {
 };
 
 // ------------------------------------------------------- hyper-dual (second order)
-// HD4<T>: value v, partials d[c] along 4 seeded directions, the directional
+// HD<T, N>: value v, partials d[c] along N seeded directions, the directional
 // derivative t along one more direction, and the partials dt[c] of t.  Running a
-// flux on HD4 gives d/dU_c (dF/dU . t): the second-order term needed by the adjoint of
+// flux on HD gives d/dU_c (dF/dU . t): the second-order term needed by the adjoint of
 // a Jacobian-vector product with respect to the linearisation state.
-template <class T>
-struct HD4 {
+template <class T, int N>
+struct HD {
   T v;
-  T d[4];
+  T d[N];
   T t;
-  T dt[4];
+  T dt[N];
 };
-template <class T> PCEXP_DEV T val(const HD4<T>& x) { return x.v; }
-template <class T> PCEXP_DEV HD4<T> operator+(const HD4<T>& a, const HD4<T>& b) {
-  HD4<T> r;
+template <class T, int N> PCEXP_DEV T val(const HD<T, N>& x) { return x.v; }
+template <class T, int N> PCEXP_DEV HD<T, N> operator+(const HD<T, N>& a, const HD<T, N>& b) {
+  HD<T, N> r;
   r.v = a.v + b.v;
   r.t = a.t + b.t;
 #pragma unroll
-  for (int c = 0; c < 4; ++c) {
+  for (int c = 0; c < N; ++c) {
     r.d[c] = a.d[c] + b.d[c];
     r.dt[c] = a.dt[c] + b.dt[c];
   }
   return r;
 }
-template <class T> PCEXP_DEV HD4<T> operator-(const HD4<T>& a) {
-  HD4<T> r;
+template <class T, int N> PCEXP_DEV HD<T, N> operator-(const HD<T, N>& a) {
+  HD<T, N> r;
   r.v = -a.v;
   r.t = -a.t;
 #pragma unroll
-  for (int c = 0; c < 4; ++c) {
+  for (int c = 0; c < N; ++c) {
     r.d[c] = -a.d[c];
     r.dt[c] = -a.dt[c];
   }
   return r;
 }
-template <class T> PCEXP_DEV HD4<T> operator-(const HD4<T>& a, const HD4<T>& b) { return a + (-b); }
-template <class T> PCEXP_DEV HD4<T> operator*(const HD4<T>& a, const HD4<T>& b) {
-  HD4<T> r;
+template <class T, int N> PCEXP_DEV HD<T, N> operator-(const HD<T, N>& a, const HD<T, N>& b) { return a + (-b); }
+template <class T, int N> PCEXP_DEV HD<T, N> operator*(const HD<T, N>& a, const HD<T, N>& b) {
+  HD<T, N> r;
   r.v = a.v * b.v;
   r.t = a.t * b.v + a.v * b.t;
 #pragma unroll
-  for (int c = 0; c < 4; ++c) {
+  for (int c = 0; c < N; ++c) {
     r.d[c] = a.d[c] * b.v + a.v * b.d[c];
     r.dt[c] = a.dt[c] * b.v + a.t * b.d[c] + a.d[c] * b.t + a.v * b.dt[c];
   }
   return r;
 }
-template <class T> PCEXP_DEV HD4<T> operator*(const HD4<T>& a, T b) {
-  HD4<T> r;
+template <class T, int N> PCEXP_DEV HD<T, N> operator*(const HD<T, N>& a, T b) {
+  HD<T, N> r;
   r.v = a.v * b;
   r.t = a.t * b;
 #pragma unroll
-  for (int c = 0; c < 4; ++c) {
+  for (int c = 0; c < N; ++c) {
     r.d[c] = a.d[c] * b;
     r.dt[c] = a.dt[c] * b;
   }
   return r;
 }
-template <class T> PCEXP_DEV HD4<T> operator*(T a, const HD4<T>& b) { return b * a; }
-template <class T> PCEXP_DEV HD4<T> operator+(const HD4<T>& a, T b) { HD4<T> r = a; r.v += b; return r; }
-template <class T> PCEXP_DEV HD4<T> operator+(T a, const HD4<T>& b) { HD4<T> r = b; r.v += a; return r; }
-template <class T> PCEXP_DEV HD4<T> operator-(const HD4<T>& a, T b) { HD4<T> r = a; r.v -= b; return r; }
-template <class T> PCEXP_DEV HD4<T> operator-(T a, const HD4<T>& b) { return (-b) + a; }
+template <class T, int N> PCEXP_DEV HD<T, N> operator*(T a, const HD<T, N>& b) { return b * a; }
+template <class T, int N> PCEXP_DEV HD<T, N> operator+(const HD<T, N>& a, T b) { HD<T, N> r = a; r.v += b; return r; }
+template <class T, int N> PCEXP_DEV HD<T, N> operator+(T a, const HD<T, N>& b) { HD<T, N> r = b; r.v += a; return r; }
+template <class T, int N> PCEXP_DEV HD<T, N> operator-(const HD<T, N>& a, T b) { HD<T, N> r = a; r.v -= b; return r; }
+template <class T, int N> PCEXP_DEV HD<T, N> operator-(T a, const HD<T, N>& b) { return (-b) + a; }
 // f(a) from f, f', f'' at a.v
-template <class T> PCEXP_DEV HD4<T> hd_apply(const HD4<T>& a, T f0, T f1, T f2) {
-  HD4<T> r;
+template <class T, int N> PCEXP_DEV HD<T, N> hd_apply(const HD<T, N>& a, T f0, T f1, T f2) {
+  HD<T, N> r;
   r.v = f0;
   r.t = f1 * a.t;
 #pragma unroll
-  for (int c = 0; c < 4; ++c) {
+  for (int c = 0; c < N; ++c) {
     r.d[c] = f1 * a.d[c];
     r.dt[c] = f1 * a.dt[c] + f2 * a.d[c] * a.t;
   }
   return r;
 }
-template <class T> PCEXP_DEV HD4<T> hd_inv(const HD4<T>& a) {
+template <class T, int N> PCEXP_DEV HD<T, N> hd_inv(const HD<T, N>& a) {
   const T i = T(1) / a.v;
   return hd_apply(a, i, -i * i, T(2) * i * i * i);
 }
-template <class T> PCEXP_DEV HD4<T> operator/(const HD4<T>& a, const HD4<T>& b) { return a * hd_inv(b); }
-template <class T> PCEXP_DEV HD4<T> operator/(const HD4<T>& a, T b) { return a * (T(1) / b); }
-template <class T> PCEXP_DEV HD4<T> operator/(T a, const HD4<T>& b) { return hd_inv(b) * a; }
-template <class T> PCEXP_DEV HD4<T> sqrt_s(const HD4<T>& a) {
+template <class T, int N> PCEXP_DEV HD<T, N> operator/(const HD<T, N>& a, const HD<T, N>& b) { return a * hd_inv(b); }
+template <class T, int N> PCEXP_DEV HD<T, N> operator/(const HD<T, N>& a, T b) { return a * (T(1) / b); }
+template <class T, int N> PCEXP_DEV HD<T, N> operator/(T a, const HD<T, N>& b) { return hd_inv(b) * a; }
+template <class T, int N> PCEXP_DEV HD<T, N> sqrt_s(const HD<T, N>& a) {
   const T s = sqrt_s(a.v);
   return hd_apply(a, s, T(0.5) / s, T(-0.25) / (s * a.v));
 }
-template <class T> PCEXP_DEV HD4<T> abs_s(const HD4<T>& a) {
+template <class T, int N> PCEXP_DEV HD<T, N> abs_s(const HD<T, N>& a) {
   const T sg = a.v > T(0) ? T(1) : (a.v < T(0) ? T(-1) : T(0));
   return hd_apply(a, sg * a.v, sg, T(0));
 }
-template <class T> PCEXP_DEV HD4<T> pow_s(const HD4<T>& a, T e) {
+template <class T, int N> PCEXP_DEV HD<T, N> pow_s(const HD<T, N>& a, T e) {
   const T p = pow_s(a.v, e);
   return hd_apply(a, p, e * p / a.v, e * (e - T(1)) * p / (a.v * a.v));
 }
-template <class T> struct Lift<HD4<T>, T> {
-  PCEXP_DEV static HD4<T> of(T x) {
-    HD4<T> r;
+template <class T, int N> struct Lift<HD<T, N>, T> {
+  PCEXP_DEV static HD<T, N> of(T x) {
+    HD<T, N> r;
     r.v = x;
     r.t = T(0);
 #pragma unroll
-    for (int c = 0; c < 4; ++c) r.d[c] = r.dt[c] = T(0);
+    for (int c = 0; c < N; ++c) r.d[c] = r.dt[c] = T(0);
     return r;
   }
 };
 
 // ---------------------------------------------------------------- free stream
+// vel holds the free-stream velocity in x, y (and z in 3D; zero in the x-y-plane cases)
 template <class T>
 struct Free {
-  T gamma, rho, u, v, p;
+  T gamma, rho, p;
+  T vel[3];
 };
 
-// ---------------------------------------------------------------- fluxes (2D, 4 variables)
-// Physical fluxes along x and y of U = (rho, rho u, rho v, rho E).
-template <class S, class T>
-PCEXP_DEV void euler_flux(const S U[4], T g, S Fx[4], S Fy[4]) {
-  S ir = T(1) / U[0];
-  S u = U[1] * ir, v = U[2] * ir;
-  S p = (g - T(1)) * (U[3] - T(0.5) * (U[1] * u + U[2] * v));
-  S e = U[3] + p;
-  Fx[0] = U[1];
-  Fx[1] = U[1] * u + p;
-  Fx[2] = U[2] * u;
-  Fx[3] = e * u;
-  Fy[0] = U[2];
-  Fy[1] = U[1] * v;
-  Fy[2] = U[2] * v + p;
-  Fy[3] = e * v;
+// ------------------------------------------------------ fluxes (D dimensions, D+2 variables)
+// Physical fluxes F[d] along the Cartesian axes of U = (rho, rho v_1..rho v_D, rho E).
+template <int D, class S, class T>
+PCEXP_DEV void euler_flux(const S (&U)[D + 2], T g, S (&F)[D][D + 2]) {
+  constexpr int NV = D + 2;
+  const S ir = T(1) / U[0];
+  S vel[D];
+#pragma unroll
+  for (int d = 0; d < D; ++d) vel[d] = U[1 + d] * ir;
+  S ke = U[1] * vel[0];
+#pragma unroll
+  for (int d = 1; d < D; ++d) ke = ke + U[1 + d] * vel[d];
+  const S p = (g - T(1)) * (U[NV - 1] - T(0.5) * ke);
+  const S e = U[NV - 1] + p;
+#pragma unroll
+  for (int d = 0; d < D; ++d) {
+    F[d][0] = U[1 + d];
+#pragma unroll
+    for (int k = 0; k < D; ++k) F[d][1 + k] = (k == d) ? U[1 + k] * vel[d] + p : U[1 + k] * vel[d];
+    F[d][NV - 1] = e * vel[d];
+  }
+}
+
+template <int D, class S, class T>
+PCEXP_DEV S dot_n(const S (&a)[D], const T (&n)[D]) {
+  S r = a[0] * n[0];
+#pragma unroll
+  for (int d = 1; d < D; ++d) r = r + a[d] * n[d];
+  return r;
 }
 
 // Roe flux F~(U_L, U_R) . n
-template <class S, class T>
-PCEXP_DEV void roe_flux(const S L[4], const S R[4], T nx, T ny, T g, S F[4]) {
+template <int D, class S, class T>
+PCEXP_DEV void roe_flux(const S (&L)[D + 2], const S (&R)[D + 2], const T (&n)[D], T g, S (&F)[D + 2]) {
+  constexpr int NV = D + 2;
   const T gm = g - T(1);
-  S rL = L[0], irL = T(1) / rL, uL = L[1] * irL, vL = L[2] * irL;
-  S pL = gm * (L[3] - T(0.5) * (L[1] * uL + L[2] * vL));
-  S rR = R[0], irR = T(1) / rR, uR = R[1] * irR, vR = R[2] * irR;
-  S pR = gm * (R[3] - T(0.5) * (R[1] * uR + R[2] * vR));
-  S qL = uL * nx + vL * ny, qR = uR * nx + vR * ny;
-  S HL = (L[3] + pL) * irL, HR = (R[3] + pR) * irR;
+  S rL = L[0], irL = T(1) / rL, rR = R[0], irR = T(1) / rR;
+  S vL[D], vR[D];
+#pragma unroll
+  for (int d = 0; d < D; ++d) {
+    vL[d] = L[1 + d] * irL;
+    vR[d] = R[1 + d] * irR;
+  }
+  S keL = L[1] * vL[0], keR = R[1] * vR[0];
+#pragma unroll
+  for (int d = 1; d < D; ++d) {
+    keL = keL + L[1 + d] * vL[d];
+    keR = keR + R[1 + d] * vR[d];
+  }
+  S pL = gm * (L[NV - 1] - T(0.5) * keL);
+  S pR = gm * (R[NV - 1] - T(0.5) * keR);
+  S qL = dot_n<D>(vL, n), qR = dot_n<D>(vR, n);
+  S HL = (L[NV - 1] + pL) * irL, HR = (R[NV - 1] + pR) * irR;
   // central part
-  S c0 = rL * qL + rR * qR;
-  S c1 = L[1] * qL + R[1] * qR + (pL + pR) * nx;
-  S c2 = L[2] * qL + R[2] * qR + (pL + pR) * ny;
-  S c3 = (L[3] + pL) * qL + (R[3] + pR) * qR;
+  S c[NV];
+  c[0] = rL * qL + rR * qR;
+#pragma unroll
+  for (int d = 0; d < D; ++d) c[1 + d] = L[1 + d] * qL + R[1 + d] * qR + (pL + pR) * n[d];
+  c[NV - 1] = (L[NV - 1] + pL) * qL + (R[NV - 1] + pR) * qR;
   // Roe averages
   S sL = sqrt_s(rL), sR = sqrt_s(rR), is = T(1) / (sL + sR);
   S rh = sL * sR;
-  S uh = (sL * uL + sR * uR) * is, vh = (sL * vL + sR * vR) * is;
+  S vh[D];
+#pragma unroll
+  for (int d = 0; d < D; ++d) vh[d] = (sL * vL[d] + sR * vR[d]) * is;
   S Hh = (sL * HL + sR * HR) * is;
-  S q2 = uh * uh + vh * vh;
+  S q2 = vh[0] * vh[0];
+#pragma unroll
+  for (int d = 1; d < D; ++d) q2 = q2 + vh[d] * vh[d];
   S cc = gm * (Hh - T(0.5) * q2);
-  S c = sqrt_s(cc);
-  S qh = uh * nx + vh * ny;
+  S cs = sqrt_s(cc);
+  S qh = dot_n<D>(vh, n);
   // jumps and wave strengths
-  S dp = pR - pL, dr = rR - rL, du = uR - uL, dv = vR - vL;
-  S dq = du * nx + dv * ny;
-  S l1 = abs_s(qh - c), l2 = abs_s(qh), l4 = abs_s(qh + c);
+  S dp = pR - pL, dr = rR - rL;
+  S dv[D];
+#pragma unroll
+  for (int d = 0; d < D; ++d) dv[d] = vR[d] - vL[d];
+  S dq = dot_n<D>(dv, n);
+  S l1 = abs_s(qh - cs), l2 = abs_s(qh), l4 = abs_s(qh + cs);
   S i2c = T(0.5) / cc;
-  S a1 = (dp - rh * c * dq) * i2c;
-  S a4 = (dp + rh * c * dq) * i2c;
+  S a1 = (dp - rh * cs * dq) * i2c;
+  S a4 = (dp + rh * cs * dq) * i2c;
   S a2 = dr - dp / cc;
   S t1 = l1 * a1, t4 = l4 * a4, t2 = l2 * a2, ts = l2 * rh;
-  S d0 = t1 + t2 + t4;
-  S d1 = t1 * (uh - c * nx) + t2 * uh + ts * (du - dq * nx) + t4 * (uh + c * nx);
-  S d2 = t1 * (vh - c * ny) + t2 * vh + ts * (dv - dq * ny) + t4 * (vh + c * ny);
-  S d3 = t1 * (Hh - c * qh) + t2 * (T(0.5) * q2) + ts * (uh * du + vh * dv - qh * dq) + t4 * (Hh + c * qh);
-  F[0] = T(0.5) * (c0 - d0);
-  F[1] = T(0.5) * (c1 - d1);
-  F[2] = T(0.5) * (c2 - d2);
-  F[3] = T(0.5) * (c3 - d3);
+  S dd[NV];
+  dd[0] = t1 + t2 + t4;
+  S vdv = vh[0] * dv[0];
+#pragma unroll
+  for (int d = 1; d < D; ++d) vdv = vdv + vh[d] * dv[d];
+#pragma unroll
+  for (int d = 0; d < D; ++d)
+    dd[1 + d] = t1 * (vh[d] - cs * n[d]) + t2 * vh[d] + ts * (dv[d] - dq * n[d]) + t4 * (vh[d] + cs * n[d]);
+  dd[NV - 1] = t1 * (Hh - cs * qh) + t2 * (T(0.5) * q2) + ts * (vdv - qh * dq) + t4 * (Hh + cs * qh);
+#pragma unroll
+  for (int v = 0; v < NV; ++v) F[v] = T(0.5) * (c[v] - dd[v]);
 }
 
-template <class S, class T>
-PCEXP_DEV void ghost_slip_wall(const S U[4], T nx, T ny, S G[4]) {
-  S ir = T(1) / U[0];
-  S qn = (U[1] * nx + U[2] * ny) * ir;  // normal velocity
+template <int D, class S, class T>
+PCEXP_DEV void ghost_slip_wall(const S (&U)[D + 2], const T (&n)[D], S (&G)[D + 2]) {
+  constexpr int NV = D + 2;
+  const S ir = T(1) / U[0];
+  S m[D];
+#pragma unroll
+  for (int d = 0; d < D; ++d) m[d] = U[1 + d];
+  const S qn = dot_n<D>(m, n) * ir;  // normal velocity
   G[0] = U[0];
-  G[1] = U[1] - T(2) * U[0] * qn * nx;
-  G[2] = U[2] - T(2) * U[0] * qn * ny;
-  G[3] = U[3];
+#pragma unroll
+  for (int d = 0; d < D; ++d) G[1 + d] = U[1 + d] - T(2) * U[0] * qn * n[d];
+  G[NV - 1] = U[NV - 1];
 }
 
-template <class S, class T>
-PCEXP_DEV void ghost_farfield(const S U[4], T nx, T ny, const Free<T>& fs, S G[4]) {
+template <int D, class S, class T>
+PCEXP_DEV void ghost_farfield(const S (&U)[D + 2], const T (&n)[D], const Free<T>& fs, S (&G)[D + 2]) {
+  constexpr int NV = D + 2;
   const T g = fs.gamma, gm = g - T(1);
-  S ir = T(1) / U[0];
-  S u = U[1] * ir, v = U[2] * ir;
-  S p = gm * (U[3] - T(0.5) * (U[1] * u + U[2] * v));
-  S c = sqrt_s(g * p * ir);
-  S qn = u * nx + v * ny;
-  T cinf = sqrt_s(g * fs.p / fs.rho);
-  T qinf = fs.u * nx + fs.v * ny;
-  T mn = val(qn) / val(c);
-  S rp = select_s(mn > T(-1), qn + T(2) * c / gm, Lift<S, T>::of(qinf + T(2) * cinf / gm));
-  S rm = select_s(mn < T(1), Lift<S, T>::of(qinf - T(2) * cinf / gm), qn - T(2) * c / gm);
-  S qb = T(0.5) * (rp + rm);
-  S cb = T(0.25) * gm * (rp - rm);
-  bool out = val(qb) >= T(0);
-  S s_in = p / pow_s(U[0], g);
-  T s_inf = fs.p / pow_s(fs.rho, g);
-  S sb = select_s(out, s_in, Lift<S, T>::of(s_inf));
-  S ut = select_s(out, u - qn * nx, Lift<S, T>::of(fs.u - qinf * nx));
-  S vt = select_s(out, v - qn * ny, Lift<S, T>::of(fs.v - qinf * ny));
-  S ub = ut + qb * nx, vb = vt + qb * ny;
-  S rb = pow_s(cb * cb / (g * sb), T(1) / gm);
-  S pb = rb * cb * cb / g;
+  const S ir = T(1) / U[0];
+  S vel[D];
+#pragma unroll
+  for (int d = 0; d < D; ++d) vel[d] = U[1 + d] * ir;
+  S ke = U[1] * vel[0];
+#pragma unroll
+  for (int d = 1; d < D; ++d) ke = ke + U[1 + d] * vel[d];
+  const S p = gm * (U[NV - 1] - T(0.5) * ke);
+  const S c = sqrt_s(g * p * ir);
+  const S qn = dot_n<D>(vel, n);
+  const T cinf = sqrt_s(g * fs.p / fs.rho);
+  T qinf = fs.vel[0] * n[0];
+#pragma unroll
+  for (int d = 1; d < D; ++d) qinf += fs.vel[d] * n[d];
+  const T mn = val(qn) / val(c);
+  const S rp = select_s(mn > T(-1), qn + T(2) * c / gm, Lift<S, T>::of(qinf + T(2) * cinf / gm));
+  const S rm = select_s(mn < T(1), Lift<S, T>::of(qinf - T(2) * cinf / gm), qn - T(2) * c / gm);
+  const S qb = T(0.5) * (rp + rm);
+  const S cb = T(0.25) * gm * (rp - rm);
+  const bool out = val(qb) >= T(0);
+  const S s_in = p / pow_s(U[0], g);
+  const T s_inf = fs.p / pow_s(fs.rho, g);
+  const S sb = select_s(out, s_in, Lift<S, T>::of(s_inf));
+  const S rb = pow_s(cb * cb / (g * sb), T(1) / gm);
+  const S pb = rb * cb * cb / g;
+  S kb = Lift<S, T>::of(T(0));
   G[0] = rb;
-  G[1] = rb * ub;
-  G[2] = rb * vb;
-  G[3] = pb / gm + T(0.5) * rb * (ub * ub + vb * vb);
+#pragma unroll
+  for (int d = 0; d < D; ++d) {
+    const S vt = select_s(out, vel[d] - qn * n[d], Lift<S, T>::of(fs.vel[d] - qinf * n[d]));
+    const S vb = vt + qb * n[d];
+    G[1 + d] = rb * vb;
+    kb = kb + vb * vb;
+  }
+  G[NV - 1] = pb / gm + T(0.5) * rb * kb;
 }
 
 }  // namespace pcexp
