@@ -117,7 +117,7 @@ def test_pcexp_steps_vortex_3d_per_step(capi, p):
 
 def test_vjp_3d_dot_product_and_dense_transpose(capi):
     mesh, free = MESHES["walls"]()
-    for p in (0, 1):
+    for p in (0, 1, 2):
         dg = oracle_dg(mesh, p, free)
         ctx = capi.Context(mesh, p, free, capi.PCEXP_FP64, m_max=2)
         u = perturbed_state(dg, 1)
@@ -132,10 +132,11 @@ def test_vjp_3d_dot_product_and_dense_transpose(capi):
         ctx.close()
 
 
-def test_jvp_state_adjoint_3d_against_oracle_differences(capi):
-    mesh, free = MESHES["walls"]()
-    dg = oracle_dg(mesh, 1, free)
-    ctx = capi.Context(mesh, 1, free, capi.PCEXP_FP64, m_max=2)
+@pytest.mark.parametrize("kind,p", [("walls", 1), ("walls", 2), ("periodic", 2)])
+def test_jvp_state_adjoint_3d_against_oracle_differences(capi, kind, p):
+    mesh, free = MESHES[kind]()
+    dg = oracle_dg(mesh, p, free)
+    ctx = capi.Context(mesh, p, free, capi.PCEXP_FP64, m_max=2)
     u = perturbed_state(dg, 4)
     v = W.random_coeffs(5, (dg.K,))
     w = W.random_coeffs(6, (dg.K,))
@@ -148,13 +149,14 @@ def test_jvp_state_adjoint_3d_against_oracle_differences(capi):
     ctx.close()
 
 
-def test_step_backward_3d_directional_against_oracle(capi):
+@pytest.mark.parametrize("p", [1, 2])
+def test_step_backward_3d_directional_against_oracle(capi, p):
     from oracle import pcexp
-    case = W.case_vortex3d(n=3, p=1)
-    dg = oracle_dg(case.mesh, 1, case.free)
+    case = W.case_vortex3d(n=3, p=p)
+    dg = oracle_dg(case.mesh, p, case.free)
     u = perturbed_state(dg, 11, 0.05)
     dt, m = 0.3, 8
-    ctx = capi.Context(case.mesh, 1, case.free, capi.PCEXP_FP64, m_max=m)
+    ctx = capi.Context(case.mesh, p, case.free, capi.PCEXP_FP64, m_max=m)
     gT = W.random_coeffs(12, (dg.K,))
     ub = ctx.step_backward(u, dt, m, gT)
 
@@ -188,4 +190,50 @@ def test_vortex_error_functional_matches_oracle(capi):
         d = W.random_coeffs(seed, (dg.K,))
         ref = dg.l2_error(Dual(u, d), ex).der
         assert abs(grad @ d - ref) <= 1e-11 * abs(ref)
+    ctx.close()
+
+
+def test_vortex3d_strength_gradient_small(capi):
+    """dJ/deps of the vortex error after 5 steps on a 4^3 Kuhn mesh (P2, m = 10) by the
+    adjoint rollout, against central differences of whole GPU rollouts."""
+    torch = pytest.importorskip("torch")
+    from paper_1801_06300_gb300.autograd import adjoint_rollout
+    case = W.case_vortex3d(n=4, p=2)
+    m, steps = 10, 5
+    ctx = capi.Context(case.mesh, 2, case.free, capi.PCEXP_FP64, m_max=m)
+    eps0, (xc, yc) = case.vortex.eps, case.vortex.center
+
+    def init(eps):
+        ctx.project_state(capi.PCEXP_PROJ_VORTEX, [eps, xc, yc, 10.0])
+        return ctx.get_state(torch.empty(ctx.K, dtype=torch.float64, device="cuda"))
+
+    u0 = init(eps0)
+    ctx.set_state(u0)
+    dt = ctx.compute_dt(case.cfl)
+    T = steps * dt
+    fparams = lambda eps: [eps, xc, yc, 10.0, T]  # noqa: E731
+    res = adjoint_rollout(ctx, u0, dt, m, steps, kind=capi.PCEXP_FUNC_VORTEX_L2,
+                          functional_params=fparams(eps0), case_params={"eps": (eps0, init, fparams)}, h=1e-5)
+
+    def J(x, eps):
+        u = x
+        for _ in range(steps):
+            ctx.set_state(u)
+            ctx.step(capi.PCEXP_SCHEME_PCEXP, capi.PCEXP_DT_GIVEN, dt, m, info=False)
+            u = ctx.get_state(torch.empty_like(u))
+        return ctx.functional(capi.PCEXP_FUNC_VORTEX_L2, u, None, params=fparams(eps))[0]
+
+    delta = torch.tensor(W.random_coeffs(41, (ctx.K,)), device="cuda") * u0.abs()
+    hu = 1e-6
+    fdu = (J(u0 + hu * delta, eps0) - J(u0 - hu * delta, eps0)) / (2 * hu)
+    gu = float(torch.dot(res.grad_u0, delta))
+    # PCEXP uses the exact Jacobian, whose Roe part holds sign(q_n): wherever a face-point
+    # wave speed crosses zero, J_n (and so the step) jumps.  The difference width is kept
+    # below the distance to the nearest crossing (h = 1e-4 already straddles one here).
+    h = 1e-6
+    fd = (J(init(eps0 + h), eps0 + h) - J(init(eps0 - h), eps0 - h)) / (2 * h)
+    print(f"small 3D: J = {res.value:.6e}; u0 direction {gu:.6e} vs {fdu:.6e}; "
+          f"eps {res.grad_params['eps']:.6e} vs {fd:.6e}")
+    assert abs(gu - fdu) <= 1e-4 * abs(fdu)
+    assert abs(res.grad_params["eps"] - fd) <= 1e-4 * abs(fd)
     ctx.close()

@@ -1,0 +1,178 @@
+"""The 3D vortex at full size: 48^3 cubes as 663,552 jittered Kuhn tetrahedra, P2
+(K = 33,177,600), m = 30, CFL 10, 50 PCEXP steps.
+
+* Operators at full size, element by element on sampled elements: the oracle runs on a
+  patch made of the sampled elements and their face neighbours (in global order, so
+  every sampled element sees its own faces, neighbours and face points).
+* The FP32-mixed form against FP64 over the 50 steps (error and speedup stated).
+* The gradient of the final vortex L2 error with respect to the vortex strength and to
+  the initial state, against central differences of whole GPU rollouts.
+"""
+import time
+
+import numpy as np
+import pytest
+
+import workloads as W
+
+pytestmark = pytest.mark.gpu
+
+
+def rel(a, b):
+    return float(np.linalg.norm(np.asarray(a) - np.asarray(b)) / np.linalg.norm(b))
+
+
+@pytest.fixture(scope="module")
+def capi():
+    from paper_1801_06300_gb300 import build
+    build()
+    from paper_1801_06300_gb300 import capi as c
+    c.load()
+    return c
+
+
+@pytest.fixture(scope="module")
+def case():
+    return W.case_vortex3d()
+
+
+def element_volumes(mesh):
+    X = mesh.coords[mesh.elems]
+    return np.einsum("ed,ed->e", np.cross(X[:, 1] - X[:, 0], X[:, 2] - X[:, 0]), X[:, 3] - X[:, 0]) / 6.0
+
+
+def face_codes(mesh, elems):
+    """Sorted master-vertex triples of the 4 faces of each element, as one integer each."""
+    fv = np.array([[(f + k) % 4 for k in (1, 2, 3)] for f in range(4)])
+    key = np.sort(mesh.vert_master[mesh.elems[elems][:, fv]].astype(np.int64), axis=2)
+    n = np.int64(mesh.vert_master.max() + 1)
+    return (key[..., 0] * n + key[..., 1]) * n + key[..., 2]
+
+
+def patch_around(mesh, sample):
+    """Mesh of the sampled elements and their face neighbours (global order kept); faces
+    left unmatched inside the patch belong to neighbours only and are tagged far field."""
+    allc = face_codes(mesh, np.arange(mesh.n_elem)).reshape(-1)
+    order = np.argsort(allc, kind="stable")
+    sc = face_codes(mesh, sample).reshape(-1)
+    lo = np.searchsorted(allc[order], sc, side="left")
+    hi = np.searchsorted(allc[order], sc, side="right")
+    nb = np.concatenate([order[a:b] // 4 for a, b in zip(lo, hi)])
+    elems = np.unique(np.concatenate([sample, nb]))
+    pc = face_codes(mesh, elems)
+    uniq, cnt = np.unique(pc.reshape(-1), return_counts=True)
+    lonely = np.isin(pc, uniq[cnt == 1])
+    fv = np.array([[(f + k) % 4 for k in (1, 2, 3)] for f in range(4)])
+    bf = mesh.elems[elems][:, fv][lonely]
+    sub = W.Mesh(dim=3, coords=mesh.coords, elems=mesh.elems[elems], vert_master=mesh.vert_master,
+                 bfaces=bf.astype(np.int32), btags=np.full(len(bf), W.BC_FARFIELD, np.int32), name="patch")
+    return sub, elems
+
+
+def test_vortex3d_full_sampled_operator_parity(capi, case):
+    from oracle.dg import DGOracle
+    mesh, p, free = case.mesh, case.p, case.free
+    ctx = capi.Context(mesh, p, free, capi.PCEXP_FP64, m_max=2)
+    E, nv, N = mesh.n_elem, 5, 10
+    assert ctx.K == E * nv * N == 33_177_600
+    # perturbed free stream in the paper basis: mode 0 of psi_1 = |E|^-1/2 carries U_inf
+    c = np.sqrt(1.4)
+    vel = 0.5 * c * np.array([np.cos(np.pi / 4), np.sin(np.pi / 4), 0.0])
+    Uinf = np.array([1.0, *vel, 1.0 / 0.4 + 0.5 * vel @ vel])
+    u = np.zeros((E, nv, N))
+    u[:, :, 0] = Uinf[None, :] * np.sqrt(element_volumes(mesh))[:, None]
+    u = (u + 0.05 * W.random_coeffs(31, u.shape) * np.abs(u[:, :, :1])).reshape(-1)
+    v = W.random_coeffs(32, (ctx.K,))
+    t0 = time.time()
+    R = ctx.residual(u).reshape(E, nv, N)
+    Jv = ctx.jvp(u, v).reshape(E, nv, N)
+    t_gpu = time.time() - t0
+    sample = np.sort(np.unique((W.uniform(33, 48) * E).astype(np.int64)))
+    sub, elems = patch_around(mesh, sample)
+    dg = DGOracle(sub, p, free)
+    up = u.reshape(E, nv, N)[elems].reshape(-1)
+    vp = v.reshape(E, nv, N)[elems].reshape(-1)
+    rows = np.searchsorted(elems, sample)
+    Ro = dg.residual(up).reshape(-1, nv, N)[rows]
+    Jo = dg.jvp(up, vp).reshape(-1, nv, N)[rows]
+    eR, eJ = rel(R[sample], Ro), rel(Jv[sample], Jo)
+    print(f"3D vortex 48^3 P2 (K = {ctx.K}): sampled R rel err {eR:.2e}, J v {eJ:.2e} "
+          f"({len(sample)} elements, patch of {len(elems)}); GPU R + J v incl. transfers {t_gpu:.2f} s")
+    assert eR <= 1e-10 and eJ <= 1e-10
+    ctx.close()
+
+
+def test_vortex3d_full_fp32_mixed_vs_fp64(capi, case):
+    """50 PCEXP steps at global CFL 10, m = 30 from the projected vortex."""
+    mesh, p, free = case.mesh, case.p, case.free
+    prm = [case.vortex.eps, *case.vortex.center, 10.0]
+    out = {}
+    for prec in (capi.PCEXP_FP64, capi.PCEXP_FP32_MIXED):
+        ctx = capi.Context(mesh, p, free, prec, m_max=case.m)
+        ctx.project_state(capi.PCEXP_PROJ_VORTEX, prm)
+        ctx.step(capi.PCEXP_SCHEME_PCEXP, capi.PCEXP_DT_GLOBAL_CFL, case.cfl, case.m)  # warm-up / capture
+        ctx.project_state(capi.PCEXP_PROJ_VORTEX, prm)
+        ctx.synchronize()
+        t0 = time.time()
+        for _ in range(case.steps):
+            ctx.step(capi.PCEXP_SCHEME_PCEXP, capi.PCEXP_DT_GLOBAL_CFL, case.cfl, case.m, info=False)
+        ctx.synchronize()
+        out[prec] = (ctx.get_state(), (time.time() - t0) / case.steps)
+        ctx.close()
+    (u64, t64), (u32, t32) = out[capi.PCEXP_FP64], out[capi.PCEXP_FP32_MIXED]
+    e = rel(u32, u64)
+    print(f"3D vortex 48^3 P2, {case.steps} steps CFL {case.cfl}: FP32-mixed vs FP64 state error {e:.2e}; "
+          f"{t64 * 1e3:.1f} ms/step FP64, {t32 * 1e3:.1f} ms/step FP32-mixed ({t64 / t32:.2f}x); "
+          f"{33_177_600 / t32:.3e} DOF-steps/s FP32-mixed")
+    assert e <= 1e-5
+
+
+GRAD_STEPS = 5  # the first 5 of the 50 steps: the reverse pass costs about 11 s per step here
+
+
+def test_vortex3d_full_strength_gradient(capi, case):
+    """dJ/deps of J = ||U_h(T) - U_exact(T; eps)|| after GRAD_STEPS steps (dt held at its
+    value at u_0), by the adjoint rollout, against central differences of whole rollouts;
+    and one initial-state direction."""
+    torch = pytest.importorskip("torch")
+    from paper_1801_06300_gb300.autograd import adjoint_rollout
+    mesh, p, free = case.mesh, case.p, case.free
+    ctx = capi.Context(mesh, p, free, capi.PCEXP_FP64, m_max=case.m)
+    eps0, (xc, yc) = case.vortex.eps, case.vortex.center
+
+    def init(eps):
+        ctx.project_state(capi.PCEXP_PROJ_VORTEX, [eps, xc, yc, 10.0])
+        return ctx.get_state(torch.empty(ctx.K, dtype=torch.float64, device="cuda"))
+
+    u0 = init(eps0)
+    ctx.set_state(u0)
+    dt = ctx.compute_dt(case.cfl)
+    steps = GRAD_STEPS
+    T = steps * dt
+    fparams = lambda eps: [eps, xc, yc, 10.0, T]  # noqa: E731
+    t0 = time.time()
+    res = adjoint_rollout(ctx, u0, dt, case.m, steps, kind=capi.PCEXP_FUNC_VORTEX_L2,
+                          functional_params=fparams(eps0), case_params={"eps": (eps0, init, fparams)}, h=1e-8)
+    t_adj = time.time() - t0
+
+    def J(x, eps):
+        u = x
+        for _ in range(steps):
+            ctx.set_state(u)
+            ctx.step(capi.PCEXP_SCHEME_PCEXP, capi.PCEXP_DT_GIVEN, dt, case.m, info=False)
+            u = ctx.get_state(torch.empty_like(u))
+        return ctx.functional(capi.PCEXP_FUNC_VORTEX_L2, u, None, params=fparams(eps))[0]
+
+    # The step map jumps where a face-point wave speed crosses zero (the exact Jacobian
+    # holds sign(q_n)); with 12M face points the widths stay below ~1e-8 relative so that
+    # no crossing falls inside the difference.
+    h = 5e-8
+    fd = (J(init(eps0 + h), eps0 + h) - J(init(eps0 - h), eps0 - h)) / (2 * h)
+    assert abs(res.grad_params["eps"] - fd) <= 1e-4 * abs(fd), (res.grad_params["eps"], fd)
+    delta = torch.tensor(W.random_coeffs(41, (ctx.K,)), device="cuda") * u0.abs()
+    hu = 1e-8
+    fdu = (J(u0 + hu * delta, eps0) - J(u0 - hu * delta, eps0)) / (2 * hu)
+    assert abs(float(torch.dot(res.grad_u0, delta)) - fdu) <= 1e-4 * abs(fdu)
+    print(f"3D vortex 48^3 P2, {steps} steps: J = {res.value:.6e}, dJ/deps = {res.grad_params['eps']:.6e} "
+          f"(central difference {fd:.6e}); adjoint rollout {t_adj:.1f} s")
+    ctx.close()
