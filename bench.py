@@ -125,17 +125,25 @@ class ClockSampler:
 
 
 # ------------------------------------------------------------ algorithmic bytes
-def algorithmic_bytes(kind, T, K, E, F, nfq, m):
-    """Minimum DRAM bytes per launch of a kernel class (per-kernel table)."""
-    nq = nfq * nfq
-    g_face = F * (4 * T + 12)  # normal, length, element and local-face ids
-    g_elem = E * (8 * T + 12)  # affine map, sqrt(det), h; face slots
-    G = F * nfq * 4 * T        # face-flux buffer
-    avg_j = (m - 1) / 2.0       # mean column index over one Arnoldi process
+def shape(dim, p):
+    """(nb, nq, nfq, nv, nf): basis size, volume and face points, variables, faces per element."""
+    if dim == 2:
+        return (p + 1) * (p + 2) // 2, (p + 1) ** 2, p + 1, 4, 3
+    return (p + 1) * (p + 2) * (p + 3) // 6, (p + 1) ** 3, (p + 1) ** 2, 5, 4
+
+
+def algorithmic_bytes(kind, T, K, E, F, dim, p, m):
+    """Minimum DRAM bytes per launch of a kernel class (per-kernel table of the design notes)."""
+    nb, nq, nfq, nv, nf = shape(dim, p)
+    geo = dim * dim + 2
+    g_face = F * ((dim + 1) * T + 12)  # normal, measure, element and local-face ids
+    g_elem = E * (geo * T + 4 * nf)    # inverse map, sqrt(det), h; face slots
+    G = F * nfq * nv * T               # face-flux buffer
+    avg_j = (m - 1) / 2.0              # mean column index over one Arnoldi process
     return {
-        # J v from the point Jacobians at u_n: read v and the 4x4 blocks, write G / Jv
-        "jvp_face": K * T + 32 * F * nfq * T + F * 12 + G,
-        "jvp_elem": 2 * K * T + 32 * E * nq * T + E * (T + 12) + G,
+        # J v from the point Jacobians at u_n: read v and the Jacobian blocks, write G / Jv
+        "jvp_face": K * T + 2 * nv * nv * F * nfq * T + F * 12 + G,
+        "jvp_elem": 2 * K * T + dim * nv * nv * E * nq * T + E * (T + 4 * nf) + G,
         "residual_face": K * T + g_face + G,
         "residual_elem": 2 * K * T + g_elem + G,
         "cgs_proj": (avg_j + 2) * K * T,
@@ -147,18 +155,18 @@ def algorithmic_bytes(kind, T, K, E, F, nfq, m):
 FP64_PEAK_TFLOPS = 152 * 2 * 2 * 2.070e9 / 1e12  # SMs x DFMA/clk/SM x 2 flops x max SM clock
 
 
-def algorithmic_flops(kind, K, E, F, P, m):
+def algorithmic_flops(kind, K, E, F, dim, p, m):
     """Floating-point operations per launch of a kernel class (an FMA counts 2).
 
-    jvp_elem: per element, nq points x (trace 4 nb + Jacobian 32) FMA and 4 nb outputs x
-    (volume 2 nq + lift 3 nfq) FMA; jvp_face: per face point 2 x 4 nb trace + 32 FMA;
+    jvp_elem: per element, nq points x (trace nv nb + Jacobian d nv^2) FMA and nv nb outputs x
+    (volume d nq + lift nf nfq) FMA; jvp_face: per face point 2 nv nb trace + 2 nv^2 FMA;
     CGS kernels: per unknown and column, 1 (projection) or 2 (update + projection) FMA,
     averaged over the columns of one Arnoldi process."""
-    nb, nq, nfq = (P + 1) * (P + 2) // 2, (P + 1) ** 2, P + 1
+    nb, nq, nfq, nv, nf = shape(dim, p)
     nc = (m + 1) / 2.0  # mean number of basis columns per launch
     fma = {
-        "jvp_elem": E * (nq * (4 * nb + 32) + 4 * nb * (2 * nq + 3 * nfq)),
-        "jvp_face": F * nfq * (8 * nb + 32),
+        "jvp_elem": E * (nq * (nv * nb + dim * nv * nv) + nv * nb * (dim * nq + nf * nfq)),
+        "jvp_face": F * nfq * (2 * nv * nb + 2 * nv * nv),
         "cgs_proj": K * (nc + 1),
         "cgs_upd_proj": K * 2 * nc,
         "cgs_upd_norm": K * (nc + 1),
@@ -166,7 +174,7 @@ def algorithmic_flops(kind, K, E, F, P, m):
     return None if fma is None else 2.0 * fma
 
 
-def roofline_entry(prof, precision_bytes, K, E, F, hbm, peak_kind):
+def roofline_entry(prof, precision_bytes, K, E, F, hbm, peak_kind, dim=2, p=2, m=30):
     """Roofline of the dominant kernel class: FP64 kernels are bound by the FP64 pipe
     (alu, TFLOP/s), FP32 kernels by HBM (GB/s)."""
     dom = max(prof, key=lambda k: prof[k][1])
@@ -176,10 +184,10 @@ def roofline_entry(prof, precision_bytes, K, E, F, hbm, peak_kind):
     sec = ms_dom / n_dom / 1e3
     entry = {"kernel": dom, "avg_launch_us": round(sec * 1e6, 2),
              "time_share": round(ms_dom / sum(v[1] for v in prof.values()), 4), "traffic": None}
-    ab = algorithmic_bytes(dom, precision_bytes, K, E, F, P + 1, M)
+    ab = algorithmic_bytes(dom, precision_bytes, K, E, F, dim, p, m)
     if ab is not None:
         entry["algorithmic_bytes_per_launch"] = ab
-    fl = algorithmic_flops(dom, K, E, F, P, M)
+    fl = algorithmic_flops(dom, K, E, F, dim, p, m)
     if precision_bytes == 8 and fl is not None:
         ach = fl / sec / 1e12
         entry.update({"bound": "alu", "achieved": round(ach, 3), "peak": round(FP64_PEAK_TFLOPS, 3),
@@ -202,6 +210,7 @@ def main():
     ap.add_argument("--impl", default="gb300", choices=["gb300", "reference"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-mixed", action="store_true", help="skip the second precision form")
+    ap.add_argument("--no-3d", action="store_true", help="skip the 3D vortex block")
     ap.add_argument("--precision", default="fp64", choices=["fp64", "fp32"],
                     help="form of the headline value (the other form is reported beside it)")
     args = ap.parse_args()
@@ -327,9 +336,15 @@ def main():
     F = (3 * E + len(case.mesh.btags)) // 2
     launches = sum(v[0] for v in prof.values())
     Tb = 8 if args.precision == "fp64" else 4
-    roof = roofline_entry(prof, Tb, K, E, F, hbm, peak_kind)
+    roof = roofline_entry(prof, Tb, K, E, F, hbm, peak_kind, 2, P, M)
     if mixed is not None:
-        mixed["roofline"] = roofline_entry(prof32, 4, K, E, F, hbm, peak_kind)
+        mixed["roofline"] = roofline_entry(prof32, 4, K, E, F, hbm, peak_kind, 2, P, M)
+    ctx64.close()
+
+    # the 3D vortex (48^3 cubes as 663,552 Kuhn tetrahedra, P2, K = 33,177,600), both forms
+    v3d = None
+    if not args.no_3d:
+        v3d = vortex3d_block(args, capi, W, torch, np, local, hbm, peak_kind)
 
     cpu = None
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
@@ -355,13 +370,58 @@ def main():
         "roofline": roof,
         "cpu_baseline": cpu,
         "fp32_mixed": mixed,
+        "vortex3d": v3d,
         "clocks": clocks,
     }
-    ctx64.close()
     if rank == 0:
         print(json.dumps(out))
     if dist:
         dist.destroy_process_group()
+
+
+def vortex3d_block(args, capi, W, torch, np, local, hbm, peak_kind):
+    """Throughput of PCEXP steps on the 3D vortex (global CFL 10, m = 30) in both forms from
+    the projected vortex, with CUDA events per step after warm-up (inputs far larger than
+    L2), the dominant kernel's roofline and the FP32-mixed state error against FP64 after
+    the same steps."""
+    case = W.case_vortex3d()
+    steps, warm = max(3, min(args.steps, 5)), 3
+    prm = [case.vortex.eps, *case.vortex.center, 10.0]
+    res, states = {}, {}
+    for name, prec in (("fp64", capi.PCEXP_FP64), ("fp32_mixed", capi.PCEXP_FP32_MIXED)):
+        ctx = capi.Context(case.mesh, case.p, case.free, prec, m_max=case.m)
+        ctx.project_state(capi.PCEXP_PROJ_VORTEX, prm)
+        for _ in range(warm):
+            ctx.step(capi.PCEXP_SCHEME_PCEXP, capi.PCEXP_DT_GLOBAL_CFL, case.cfl, case.m, info=False)
+        evs = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(steps)]
+        torch.cuda.synchronize()
+        for s in range(steps):
+            evs[s][0].record()
+            ctx.step(capi.PCEXP_SCHEME_PCEXP, capi.PCEXP_DT_GLOBAL_CFL, case.cfl, case.m, info=False)
+            evs[s][1].record()
+        torch.cuda.synchronize()
+        ms = sum(a.elapsed_time(b) for a, b in evs)
+        ctx.profile_enable(True)
+        ctx.step(capi.PCEXP_SCHEME_PCEXP, capi.PCEXP_DT_GLOBAL_CFL, case.cfl, case.m, info=False)
+        torch.cuda.synchronize()
+        prof = ctx.profile_read()
+        ctx.profile_enable(False)
+        K, E = ctx.K, case.mesh.n_elem
+        F = 2 * E  # periodic: every face interior
+        states[name] = ctx.get_state()
+        res[name] = {"value": K * steps / (ms / 1e3), "ms_per_step": ms / steps,
+                     "kernel_ms_per_step": {k: round(v[1], 3) for k, v in prof.items() if v[0]},
+                     "roofline": roofline_entry(prof, 8 if name == "fp64" else 4, K, E, F, hbm, peak_kind,
+                                                3, case.p, case.m)}
+        ctx.close()
+    a, b = states["fp64"], states["fp32_mixed"]
+    res["fp32_mixed"]["speedup_vs_fp64"] = res["fp64"]["ms_per_step"] / res["fp32_mixed"]["ms_per_step"]
+    res["fp32_mixed"]["state_rel_l2_vs_fp64"] = float(np.linalg.norm(b - a) / np.linalg.norm(a))
+    return {"workload": "vortex3d_48cubed_p2_m30_pcexp_globalcfl10",
+            "mesh": "48^3 cubes, 663,552 Kuhn tetrahedra, 10% jitter seed 5, periodic [0,10]^3",
+            "K": K, "steps": steps, "warmup": warm,
+            "note": f"state error after {warm + steps} steps from the projected vortex in both forms",
+            **res}
 
 
 def reference_arm(args, rank, world):
