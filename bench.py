@@ -154,6 +154,13 @@ def algorithmic_bytes(kind, T, K, E, F, dim, p, m):
 
 FP64_PEAK_TFLOPS = 152 * 2 * 2 * 2.070e9 / 1e12  # SMs x DFMA/clk/SM x 2 flops x max SM clock
 
+# DRAM bytes (read + write) per launch from one ncu capture of the same kernel on the same
+# workload, keyed (workload, element bytes, kernel class); an entry is dropped when its
+# kernel changes.  The summaries under profiles/ give the commands.
+NCU_TRAFFIC = {
+    ("bump2d", 8, "jvp_elem"): (67_781_376, "profiles/elem_apply_fp64_bump2d_p2.md"),
+}
+
 
 def algorithmic_flops(kind, K, E, F, dim, p, m):
     """Floating-point operations per launch of a kernel class (an FMA counts 2).
@@ -174,7 +181,7 @@ def algorithmic_flops(kind, K, E, F, dim, p, m):
     return None if fma is None else 2.0 * fma
 
 
-def roofline_entry(prof, precision_bytes, K, E, F, hbm, peak_kind, dim=2, p=2, m=30):
+def roofline_entry(prof, precision_bytes, K, E, F, hbm, peak_kind, dim=2, p=2, m=30, workload="bump2d"):
     """Roofline of the dominant kernel class: FP64 kernels are bound by the FP64 pipe
     (alu, TFLOP/s), FP32 kernels by HBM (GB/s)."""
     dom = max(prof, key=lambda k: prof[k][1])
@@ -182,8 +189,12 @@ def roofline_entry(prof, precision_bytes, K, E, F, hbm, peak_kind, dim=2, p=2, m
     if not n_dom:
         return None
     sec = ms_dom / n_dom / 1e3
+    tr = NCU_TRAFFIC.get((workload, precision_bytes, dom))
     entry = {"kernel": dom, "avg_launch_us": round(sec * 1e6, 2),
-             "time_share": round(ms_dom / sum(v[1] for v in prof.values()), 4), "traffic": None}
+             "time_share": round(ms_dom / sum(v[1] for v in prof.values()), 4),
+             "traffic": tr[0] if tr else None}
+    if tr:
+        entry["traffic_source"] = tr[1]
     ab = algorithmic_bytes(dom, precision_bytes, K, E, F, dim, p, m)
     if ab is not None:
         entry["algorithmic_bytes_per_launch"] = ab
@@ -412,7 +423,7 @@ def vortex3d_block(args, capi, W, torch, np, local, hbm, peak_kind):
         res[name] = {"value": K * steps / (ms / 1e3), "ms_per_step": ms / steps,
                      "kernel_ms_per_step": {k: round(v[1], 3) for k, v in prof.items() if v[0]},
                      "roofline": roofline_entry(prof, 8 if name == "fp64" else 4, K, E, F, hbm, peak_kind,
-                                                3, case.p, case.m)}
+                                                3, case.p, case.m, "vortex3d")}
         ctx.close()
     a, b = states["fp64"], states["fp32_mixed"]
     res["fp32_mixed"]["speedup_vs_fp64"] = res["fp64"]["ms_per_step"] / res["fp32_mixed"]["ms_per_step"]

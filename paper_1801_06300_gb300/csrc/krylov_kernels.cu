@@ -313,6 +313,152 @@ __global__ void __launch_bounds__(256) cgs_kernel(const T* __restrict__ Z, int64
   if (threadIdx.x == 0) ks->counter = 0;
 }
 
+// Per-block sums red[0..nred) -> partials; the last block to finish (atomic ticket) reduces
+// them in a fixed order and finalises the column.  Every thread of the block calls this.
+template <class T>
+PCEXP_DEV void cgs_grid_tail(const Acc<T>* red, int nred, int mode, int j, KState* ks, double* partials,
+                             double eta) {
+  __shared__ bool last;
+  __shared__ double dots[MMAX + 2];
+  Acc<T>* P = reinterpret_cast<Acc<T>*>(partials);
+  for (int c = threadIdx.x; c < nred; c += blockDim.x) P[(int64_t)c * gridDim.x + blockIdx.x] = red[c];
+  __threadfence();
+  __syncthreads();
+  if (threadIdx.x == 0) last = atomicAdd(&ks->counter, 1u) == gridDim.x - 1;
+  __syncthreads();
+  if (!last) return;
+  __threadfence();
+  const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5, nw = blockDim.x >> 5;
+  constexpr int PER_LANE = (RED_BLOCKS + 31) / 32;
+  for (int c = wid; c < nred; c += nw) {
+    const unsigned long long* pc = reinterpret_cast<const unsigned long long*>(P + (int64_t)c * gridDim.x);
+    unsigned long long pv[PER_LANE];
+#pragma unroll
+    for (int t = 0; t < PER_LANE; ++t) {
+      const unsigned b = lane + 32u * t;
+      pv[t] = b < gridDim.x ? __ldcg(pc + b) : 0ull;
+    }
+    Acc<T> a;
+    a.zero();
+#pragma unroll
+    for (int t = 0; t < PER_LANE; ++t) a.add_acc(*reinterpret_cast<const Acc<T>*>(&pv[t]));
+    for (int o = 16; o > 0; o >>= 1) a.add_partner(o);
+    if (lane == 0) dots[c] = a.value();
+  }
+  __syncthreads();
+  cgs_finalize(mode, j, dots, ks, eta);
+  if (threadIdx.x == 0) ks->counter = 0;
+}
+
+// Column-split Gram-Schmidt pass (PROJ, UPD_PROJ, UPD_NORM).  The 8 warps of a block walk
+// the same tiles of 32 x VN rows; warp w owns the columns c = w, w + 8, ... (NCW of them),
+// so a thread holds NCW accumulators instead of one per column and many blocks fit per SM
+// (more loads in flight).  Update modes: each warp forms its partial sum of coef_c z_c,
+// the partials meet in shared memory, warp 0 subtracts them in a fixed warp order, stores
+// the updated tile and publishes it, and each warp projects it on its own columns with
+// the chunks still in registers (two block barriers per tile).
+constexpr int CGS_WARPS = 8;
+
+template <class T, int NCW, int MODE>
+__global__ void __launch_bounds__(256) cgs_cs_kernel(const T* __restrict__ Z, int64_t ldz, int64_t Kp, int j,
+                                                     T* __restrict__ w, T* __restrict__ out, KState* ks,
+                                                     double* __restrict__ partials, double eta) {
+  constexpr int VN = VecN<T>::N, TR = 32 * VN;
+  __shared__ T scoef[CGS_WARPS * NCW];
+  __shared__ T part[(MODE == CGS_PROJ) ? 1 : CGS_WARPS * TR];
+  __shared__ T xs[(MODE == CGS_UPD_PROJ) ? TR : 1];
+  __shared__ Acc<T> red[CGS_WARPS * NCW + 1];
+  if (ks->done) return;  // breakdown reached earlier: uniform early exit
+  const int nc = j + 1;
+  const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+  for (int c = threadIdx.x; c < CGS_WARPS * NCW; c += blockDim.x) scoef[c] = c < nc ? (T)ks->coef[c] : T(0);
+  __syncthreads();
+  Acc<T> acc[NCW + 1];
+#pragma unroll
+  for (int k = 0; k <= NCW; ++k) acc[k].zero();
+  const int64_t ntile = (Kp + TR - 1) / TR;
+  for (int64_t t = blockIdx.x; t < ntile; t += gridDim.x) {
+    const int64_t r = t * TR + lane * VN;
+    const bool valid = r < Kp;
+    T z[NCW][VN];
+#pragma unroll
+    for (int k = 0; k < NCW; ++k) {
+      const int c = wid + CGS_WARPS * k;
+      if (valid && c < nc) load_vec<T, VN>(Z + c * ldz + r, z[k]);
+      else
+#pragma unroll
+        for (int v = 0; v < VN; ++v) z[k][v] = T(0);
+    }
+    // every warp needs the tile of w for the projection; in the update modes only warp 0
+    // (which applies the update), loading it here so the load overlaps the column loads
+    T x[VN];
+    if (valid && (MODE == CGS_PROJ || wid == 0)) load_vec<T, VN>(w + r, x);
+    else
+#pragma unroll
+      for (int v = 0; v < VN; ++v) x[v] = T(0);
+    if constexpr (MODE == CGS_PROJ) {
+#pragma unroll
+      for (int k = 0; k < NCW; ++k) acc[k].add(dot_vec<T, VN>(z[k], x));
+      if (wid == 0) acc[NCW].add(dot_vec<T, VN>(x, x));
+    } else {
+      T p[VN];
+#pragma unroll
+      for (int v = 0; v < VN; ++v) p[v] = T(0);
+#pragma unroll
+      for (int k = 0; k < NCW; ++k) {
+        const T cf = scoef[wid + CGS_WARPS * k];
+#pragma unroll
+        for (int v = 0; v < VN; ++v) p[v] = fma(cf, z[k][v], p[v]);
+      }
+#pragma unroll
+      for (int v = 0; v < VN; ++v) part[wid * TR + lane * VN + v] = p[v];
+      __syncthreads();
+      // warp 0 forms the updated tile once (fixed warp order), stores it and publishes it
+      if (wid == 0) {
+#pragma unroll
+        for (int q = 0; q < CGS_WARPS; ++q)
+#pragma unroll
+          for (int v = 0; v < VN; ++v) x[v] -= part[q * TR + lane * VN + v];
+        if (valid) store_vec<T, VN>((MODE == CGS_UPD_PROJ ? w : out) + r, x);
+        if constexpr (MODE == CGS_UPD_PROJ) {
+#pragma unroll
+          for (int v = 0; v < VN; ++v) xs[lane * VN + v] = x[v];
+        } else {
+          acc[NCW].add(dot_vec<T, VN>(x, x));
+        }
+      }
+      __syncthreads();
+      if constexpr (MODE == CGS_UPD_PROJ) {
+        T xn[VN];
+#pragma unroll
+        for (int v = 0; v < VN; ++v) xn[v] = xs[lane * VN + v];
+#pragma unroll
+        for (int k = 0; k < NCW; ++k) acc[k].add(dot_vec<T, VN>(z[k], xn));
+      }
+    }
+  }
+  // warp sums of the owned columns (fixed shuffle tree); each column has one owner warp
+  if constexpr (MODE != CGS_UPD_NORM) {
+#pragma unroll
+    for (int k = 0; k < NCW; ++k) {
+      for (int o = 16; o > 0; o >>= 1) acc[k].add_partner(o);
+      if (lane == 0) red[wid + CGS_WARPS * k] = acc[k];
+    }
+  }
+  if (MODE != CGS_UPD_PROJ && wid == 0) {
+    for (int o = 16; o > 0; o >>= 1) acc[NCW].add_partner(o);
+    if (lane == 0) red[MODE == CGS_PROJ ? CGS_WARPS * NCW : 0] = acc[NCW];
+  }
+  __syncthreads();
+  // partial-sum slots: PROJ columns 0..nc-1 and the norm at nc; UPD_PROJ columns; UPD_NORM the norm
+  __shared__ Acc<T> ordered[MMAX + 1];
+  const int nred = (MODE == CGS_PROJ) ? nc + 1 : (MODE == CGS_UPD_PROJ ? nc : 1);
+  for (int c = threadIdx.x; c < nred; c += blockDim.x)
+    ordered[c] = (MODE == CGS_PROJ && c == nc) ? red[CGS_WARPS * NCW] : red[c];
+  __syncthreads();
+  cgs_grid_tail<T>(ordered, nred, MODE, j, ks, partials, eta);
+}
+
 template <class KernelT>
 static unsigned wave_grid(KernelT kernel, int64_t chunks) {
   static int sms = 0;
@@ -344,13 +490,41 @@ static void cgs_launch(const T* Z, int64_t ldz, int64_t Kp, int j, T* w, T* out,
   cgs_kernel<T, NC, MODE><<<grid_cache, 256, 0, st>>>(Z, ldz, Kp, j, w, out, ks, partials, eta);
 }
 
+template <class T, int NCW, int MODE>
+static void cgs_cs_launch(const T* Z, int64_t ldz, int64_t Kp, int j, T* w, T* out, KState* ks, double* partials,
+                          double eta, cudaStream_t st) {
+  static unsigned grid_cache = 0;
+  static int64_t kp_cache = -1;
+  if (kp_cache != Kp) {
+    grid_cache = wave_grid(cgs_cs_kernel<T, NCW, MODE>, (Kp + 32 * VecN<T>::N - 1) / (32 * VecN<T>::N) * 256);
+    kp_cache = Kp;
+  }
+  cgs_cs_kernel<T, NCW, MODE><<<grid_cache, 256, 0, st>>>(Z, ldz, Kp, j, w, out, ks, partials, eta);
+}
+
+// Which layout serves a precision and pass: the column-split kernel (column capacity
+// 8 x NCW, NCW = 1, 2, 4) or the row kernel (every thread accumulates all columns of its
+// rows).  Measured on GB300 (C2 and the 48^3 tetrahedra): the FP32 projections gain from
+// the column split (fewer registers, more loads in flight); the FP64 passes are bound by
+// the FP64 pipe and the update-and-norm pass keeps one accumulator, so the row kernel's
+// single barrier-free sweep is faster for those.
+template <class T, int MODE> struct CgsColumnSplit {
+  static constexpr bool value = sizeof(T) == 4 && MODE != CGS_UPD_NORM;
+};
+
 template <class T, int MODE>
 static void cgs_dispatch(int nc, const T* Z, int64_t ldz, int64_t Kp, int j, T* w, T* out, KState* ks,
                          double* partials, double eta, cudaStream_t st) {
-  if (nc <= 4) cgs_launch<T, 4, MODE>(Z, ldz, Kp, j, w, out, ks, partials, eta, st);
-  else if (nc <= 8) cgs_launch<T, 8, MODE>(Z, ldz, Kp, j, w, out, ks, partials, eta, st);
-  else if (nc <= 16) cgs_launch<T, 16, MODE>(Z, ldz, Kp, j, w, out, ks, partials, eta, st);
-  else cgs_launch<T, 32, MODE>(Z, ldz, Kp, j, w, out, ks, partials, eta, st);
+  if constexpr (CgsColumnSplit<T, MODE>::value) {
+    if (nc <= CGS_WARPS) cgs_cs_launch<T, 1, MODE>(Z, ldz, Kp, j, w, out, ks, partials, eta, st);
+    else if (nc <= 2 * CGS_WARPS) cgs_cs_launch<T, 2, MODE>(Z, ldz, Kp, j, w, out, ks, partials, eta, st);
+    else cgs_cs_launch<T, 4, MODE>(Z, ldz, Kp, j, w, out, ks, partials, eta, st);
+  } else {
+    if (nc <= 4) cgs_launch<T, 4, MODE>(Z, ldz, Kp, j, w, out, ks, partials, eta, st);
+    else if (nc <= 8) cgs_launch<T, 8, MODE>(Z, ldz, Kp, j, w, out, ks, partials, eta, st);
+    else if (nc <= 16) cgs_launch<T, 16, MODE>(Z, ldz, Kp, j, w, out, ks, partials, eta, st);
+    else cgs_launch<T, 32, MODE>(Z, ldz, Kp, j, w, out, ks, partials, eta, st);
+  }
 }
 
 template <class T>
