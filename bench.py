@@ -140,10 +140,14 @@ def algorithmic_bytes(kind, T, K, E, F, dim, p, m):
     g_elem = E * (geo * T + 4 * nf)    # inverse map, sqrt(det), h; face slots
     G = F * nfq * nv * T               # face-flux buffer
     avg_j = (m - 1) / 2.0              # mean column index over one Arnoldi process
+    # J v element kernel: FP64 applies the volume point Jacobians (read v and the blocks,
+    # write Jv); FP32-mixed recomputes the flux tangents at u_n (read u_n and v, write Jv)
+    jvp_elem = (2 * K * T + dim * nv * nv * E * nq * T + E * (T + 4 * nf) + G if T == 8
+                else 3 * K * T + g_elem + G)
     return {
-        # J v from the point Jacobians at u_n: read v and the Jacobian blocks, write G / Jv
+        # face J v from the face point Jacobians: read v and the blocks, write G
         "jvp_face": K * T + 2 * nv * nv * F * nfq * T + F * 12 + G,
-        "jvp_elem": 2 * K * T + dim * nv * nv * E * nq * T + E * (T + 4 * nf) + G,
+        "jvp_elem": jvp_elem,
         "residual_face": K * T + g_face + G,
         "residual_elem": 2 * K * T + g_elem + G,
         "cgs_proj": (avg_j + 2) * K * T,
@@ -158,7 +162,7 @@ FP64_PEAK_TFLOPS = 152 * 2 * 2 * 2.070e9 / 1e12  # SMs x DFMA/clk/SM x 2 flops x
 # workload, keyed (workload, element bytes, kernel class); an entry is dropped when its
 # kernel changes.  The summaries under profiles/ give the commands.
 NCU_TRAFFIC = {
-    ("bump2d", 8, "jvp_elem"): (67_781_376, "profiles/elem_apply_fp64_bump2d_p2.md"),
+    ("bump2d", 8, "jvp_elem"): (67_718_656, "profiles/elem_apply_fp64_bump2d_p2.md"),
 }
 
 
@@ -222,6 +226,9 @@ def main():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-mixed", action="store_true", help="skip the second precision form")
     ap.add_argument("--no-3d", action="store_true", help="skip the 3D vortex block")
+    ap.add_argument("--only-3d", action="store_true",
+                    help="run the 3D vortex block alone and print it (profiling runs)")
+    ap.add_argument("--n3d", type=int, default=48, help="cubes per side of the 3D vortex block")
     ap.add_argument("--precision", default="fp64", choices=["fp64", "fp32"],
                     help="form of the headline value (the other form is reported beside it)")
     args = ap.parse_args()
@@ -249,6 +256,13 @@ def main():
     if dist:
         dist.barrier()
     capi.load()
+
+    if args.only_3d:
+        hbm, peak_kind = load_peaks()
+        v3d = vortex3d_block(args, capi, W, torch, np, local, hbm, peak_kind)
+        if rank == 0:
+            print(json.dumps({"vortex3d": v3d}))
+        return
 
     case = W.case_bump2d(NX, NY, P, SEED)
     free = case.free
@@ -395,7 +409,7 @@ def vortex3d_block(args, capi, W, torch, np, local, hbm, peak_kind):
     the projected vortex, with CUDA events per step after warm-up (inputs far larger than
     L2), the dominant kernel's roofline and the FP32-mixed state error against FP64 after
     the same steps."""
-    case = W.case_vortex3d()
+    case = W.case_vortex3d(n=args.n3d)
     steps, warm = max(3, min(args.steps, 5)), 3
     prm = [case.vortex.eps, *case.vortex.center, 10.0]
     res, states = {}, {}
@@ -428,8 +442,9 @@ def vortex3d_block(args, capi, W, torch, np, local, hbm, peak_kind):
     a, b = states["fp64"], states["fp32_mixed"]
     res["fp32_mixed"]["speedup_vs_fp64"] = res["fp64"]["ms_per_step"] / res["fp32_mixed"]["ms_per_step"]
     res["fp32_mixed"]["state_rel_l2_vs_fp64"] = float(np.linalg.norm(b - a) / np.linalg.norm(a))
-    return {"workload": "vortex3d_48cubed_p2_m30_pcexp_globalcfl10",
-            "mesh": "48^3 cubes, 663,552 Kuhn tetrahedra, 10% jitter seed 5, periodic [0,10]^3",
+    n = args.n3d
+    return {"workload": f"vortex3d_{n}cubed_p2_m30_pcexp_globalcfl10",
+            "mesh": f"{n}^3 cubes, {6 * n ** 3:,} Kuhn tetrahedra, 10% jitter seed 5, periodic [0,10]^3",
             "K": K, "steps": steps, "warmup": warm,
             "note": f"state error after {warm + steps} steps from the projected vortex in both forms",
             **res}

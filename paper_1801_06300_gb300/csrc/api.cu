@@ -39,6 +39,8 @@ struct pcexp_ctx {
   void *V = nullptr, *w = nullptr, *tmp = nullptr, *delta = nullptr, *G = nullptr, *dte = nullptr;
   double *io64a = nullptr, *io64b = nullptr;
   void *Avol = nullptr, *Bface = nullptr;  // point Jacobians at the linearisation state
+  const void* lin_state = nullptr;         // state the last linearize() recorded
+  bool jv_tangent = false;                 // volume part of J v by flux tangents (FP32-mixed)
   void* GT = nullptr;                      // adjoint face scratch [F][nfq][2 nv]
   double* xq = nullptr;                    // physical volume points [E][nq][dim] (first vortex functional)
   // reverse-step work space (FP64 contexts, allocated by the first backward call)
@@ -134,6 +136,11 @@ DGData<T> dgdata(const pcexp_ctx* c) {
   d.Wf = d.Bf + NF * NPERM * nfq * nb;
   d.Bc = d.Wf + nfq;
   d.Wv = d.Bc + nb;
+  {
+    // padded trace tables: after Wv, at the next 16-byte boundary (as laid out in create_impl)
+    const size_t vec = 16 / sizeof(T), off = (size_t)((d.Wv + nq) - tabs);
+    d.BfP = tabs + (off + vec - 1) / vec * vec;
+  }
   d.E = c->E;
   d.F = c->F;
   const double a = c->phys.alpha_deg * M_PI / 180.0;
@@ -231,19 +238,26 @@ template <class T> LinData<T> lindata(pcexp_ctx* c) {
   return LinData<T>{reinterpret_cast<T*>(c->Avol), reinterpret_cast<T*>(c->Bface)};
 }
 
+// Linearise the operator at u for the J v products that follow.  FP64 contexts build the
+// face and volume point Jacobians once; FP32-mixed contexts build the face blocks only and
+// recompute the volume flux tangents at u in every J v (reading u and dv instead of
+// D nv^2 values per volume point).  blocks = true builds both (the transpose needs them).
 template <class T>
-int linearize(pcexp_ctx* c, const DGData<T>& d, const T* u) {
-  PCEXP_LAUNCH(c, PCEXP_KC_LINEARIZE, launch_linearize<T>(d, u, lindata<T>(c), c->st));
+int linearize(pcexp_ctx* c, const DGData<T>& d, const T* u, bool blocks = false) {
+  c->lin_state = u;
+  const bool faces_only = c->jv_tangent && !blocks;
+  PCEXP_LAUNCH(c, PCEXP_KC_LINEARIZE, launch_linearize<T>(d, u, lindata<T>(c), c->st, faces_only));
   return PCEXP_OK;
 }
 
-// J(u_lin) dv from the point Jacobians (two kernels: face, element)
+// J(u_lin) dv (two kernels: face, element)
 template <class T>
 int jac_apply(pcexp_ctx* c, const DGData<T>& d, const T* dv, T* out, const T* escale, const int* skip,
               const double* oscale) {
   cudaEvent_t* ev = prof_events(c, 3);
+  const T* u_elem = c->jv_tangent ? reinterpret_cast<const T*>(c->lin_state) : nullptr;
   cudaError_t e = launch_jac_apply<T>(d, lindata<T>(c), dv, out, reinterpret_cast<T*>(c->G), escale, skip, oscale,
-                                      c->st, ev);
+                                      c->st, ev, u_elem);
   if (ev) {
     prof_note(c, PCEXP_KC_JVP_FACE, ev, 0);
     prof_note(c, PCEXP_KC_JVP_ELEM, ev, 1);
@@ -436,10 +450,6 @@ int step_impl(pcexp_ctx* c, int scheme, int dt_mode, double dt_or_cfl, int m, pc
     info->beta[1] = scheme == PCEXP_SCHEME_EXP1 ? 0.0 : h.beta[1];
     info->dt = h.dt;
     info->res_norm = h.res_norm;
-    if (h.err == 2) {
-      g_last_error = "a bounded device wait ran out (bulk copy not completed)";
-      return PCEXP_ERR_TIMEOUT;
-    }
     if (h.err) {
       g_last_error = "non-finite norm, beta or Hessenberg entry";
       return PCEXP_ERR_NONFINITE;
@@ -508,10 +518,6 @@ int arnoldi_abi(pcexp_ctx* c, const double* U, const double* b, int m, double* V
   KState hk;
   PCEXP_CK(cudaMemcpyAsync(&hk, c->ks, sizeof(hk), cudaMemcpyDeviceToHost, c->st));
   PCEXP_CK(cudaStreamSynchronize(c->st));
-  if (hk.err == 2) {
-    g_last_error = "a bounded device wait ran out (bulk copy not completed)";
-    return PCEXP_ERR_TIMEOUT;
-  }
   if (hk.err) {
     g_last_error = "non-finite Arnoldi quantity";
     return PCEXP_ERR_NONFINITE;
@@ -642,6 +648,7 @@ int create_impl(pcexp_ctx* c, const pcexp_mesh* mesh, int p, const pcexp_physics
   c->volume = s.volume;
   c->phys = *phys;
   c->fp32 = opt->precision == PCEXP_FP32_MIXED;
+  c->jv_tangent = c->fp32;
   c->m_max = opt->m_max;
   c->eta = opt->breakdown_eta > 0 ? opt->breakdown_eta : (c->fp32 ? 1e-6 : 1e-12);
   c->basis_io = opt->basis_io;
@@ -653,6 +660,15 @@ int create_impl(pcexp_ctx* c, const pcexp_mesh* mesh, int p, const pcexp_physics
   tabs.insert(tabs.end(), s.Wf.begin(), s.Wf.end());
   tabs.insert(tabs.end(), s.Bc.begin(), s.Bc.end());
   tabs.insert(tabs.end(), s.Wv.begin(), s.Wv.end());
+  {
+    // the trace tables again with each row padded to whole 16-byte vectors (4 floats or
+    // 2 doubles), the padded block itself starting on a 16-byte boundary
+    const size_t vec = c->fp32 ? 4 : 2, nbp = (s.nb + vec - 1) / vec * vec;
+    while (tabs.size() % vec) tabs.push_back(0.0);
+    const size_t rows = s.Bf.size() / s.nb;
+    for (size_t r = 0; r < rows; ++r)
+      for (size_t j = 0; j < nbp; ++j) tabs.push_back(j < (size_t)s.nb ? s.Bf[r * s.nb + j] : 0.0);
+  }
   const size_t es = c->fp32 ? sizeof(float) : sizeof(double);
   if (c->fp32) {
     PCEXP_TRY(upload<float>(c, &c->tabs, tabs));
@@ -726,7 +742,7 @@ int vjp_impl(pcexp_ctx* c, const double* U, const double* w, double* JTw, int on
   const DGData<T> d = dgdata<T>(c);
   PCEXP_TRY(import_vec<T>(c, U, on_device, a));
   PCEXP_TRY(import_vec<T>(c, w, on_device, b));
-  PCEXP_TRY(linearize<T>(c, d, a));
+  PCEXP_TRY(linearize<T>(c, d, a, true));
   PCEXP_CK(launch_jac_adjoint<T>(d, lindata<T>(c), b, o, reinterpret_cast<T*>(c->GT), nullptr, T(1), c->st));
   PCEXP_TRY(export_vec<T>(c, o, JTw, on_device));
   if (on_device) PCEXP_CK(cudaStreamSynchronize(c->st));

@@ -37,9 +37,10 @@ template <int D, int P> struct Ord {
   static constexpr int NFQ = D == 2 ? P + 1 : (P + 1) * (P + 1);
   static constexpr int NF = D + 1;                  // faces per element
   static constexpr int NPERM = D == 2 ? 2 : 6;      // vertex permutations of a face
-  static constexpr int GEO = D == 2 ? 8 : 12;       // geometry record: A^-1 (D x D), sqrt|det|, h
-  static constexpr int SD = D * D;
-  static constexpr int HE = D * D + 1;
+  static constexpr int GEO = D == 2 ? 8 : 12;       // geometry record: A^-1 (D x D), sqrt|det|, h, 1/sqrt|det|
+  static constexpr int SD = D * D;       // sqrt|det A|
+  static constexpr int HE = D * D + 1;   // h
+  static constexpr int ISD = D * D + 2;  // 1 / sqrt|det A| (multiplications instead of FP64 divisions)
   static constexpr int NVB = NV * NB;
   static constexpr int ET = (256 / NQ) > 128 ? 128 : (256 / NQ);  // elements per block
   static constexpr int NJV = D * NV * NV;           // volume point-Jacobian entries
@@ -93,7 +94,7 @@ __global__ void __launch_bounds__(256) face_kernel(DGData<T> d, const T* __restr
   const T meas = d.fgeo[4 * f + D];
   S UL[NV], UR[NV];
   {
-    const T isd = T(1) / d.geo[GEO * (int64_t)eL + O::SD];
+    const T isd = d.geo[GEO * (int64_t)eL + O::ISD];
     const T* ue = u + (int64_t)eL * NV * NB;
     const T* be = Bf + ((fL * NPERM) * NFQ + q) * NB;
 #pragma unroll
@@ -110,7 +111,7 @@ __global__ void __launch_bounds__(256) face_kernel(DGData<T> d, const T* __restr
     }
   }
   if (eR >= 0) {
-    const T isd = T(1) / d.geo[GEO * (int64_t)eR + O::SD];
+    const T isd = d.geo[GEO * (int64_t)eR + O::ISD];
     const T* ue = u + (int64_t)eR * NV * NB;
     const T* be = Bf + ((fR * NPERM + pR) * NFQ + q) * NB;
 #pragma unroll
@@ -138,6 +139,34 @@ __global__ void __launch_bounds__(256) face_kernel(DGData<T> d, const T* __restr
   for (int v = 0; v < NV; ++v) g[v] = wl * PartOf<S>::get(Fn[v]);
 }
 
+// Rows of the element kernel's tables and coefficient tiles are padded to whole 16-byte
+// vectors so that a row is read with 16-byte loads.
+template <class T> constexpr int VECW = 16 / (int)sizeof(T);
+template <class T, int N> constexpr int PADV = (N + VECW<T> - 1) / VECW<T> * VECW<T>;
+
+// r[0..N) = p[0..N) from a 16-byte-aligned row (shared memory, or global through the
+// read-only cache), N a multiple of VECW<T>
+template <class T, int N, bool GLOBAL = false>
+PCEXP_DEV void load_row(const T* p, T (&r)[N]) {
+  if constexpr (sizeof(T) == 4) {
+#pragma unroll
+    for (int k = 0; k < N / 4; ++k) {
+      const float4 a = GLOBAL ? __ldg(reinterpret_cast<const float4*>(p) + k) : reinterpret_cast<const float4*>(p)[k];
+      r[4 * k] = a.x;
+      r[4 * k + 1] = a.y;
+      r[4 * k + 2] = a.z;
+      r[4 * k + 3] = a.w;
+    }
+  } else {
+#pragma unroll
+    for (int k = 0; k < N / 2; ++k) {
+      const double2 a = GLOBAL ? __ldg(reinterpret_cast<const double2*>(p) + k) : reinterpret_cast<const double2*>(p)[k];
+      r[2 * k] = a.x;
+      r[2 * k + 1] = a.y;
+    }
+  }
+}
+
 // lift of the D+1 face fluxes onto test function i of variable v of element e
 template <class T, int D, int P, bool SM>
 PCEXP_DEV T lift_faces(const DGData<T>& d, const T* Bf, const T* __restrict__ G, int64_t e, int v, int i) {
@@ -158,32 +187,52 @@ PCEXP_DEV T lift_faces(const DGData<T>& d, const T* Bf, const T* __restrict__ G,
 }
 
 // --------------------------------------------------------------- element kernel
+// Phase 1: one thread per volume point forms the trace (and tangent) of u, the Euler flux
+// and its mapping to reference directions.  Phase 2: a group of S lanes owns one (element,
+// variable) pair and accumulates all nb test functions at once over a strided share of the
+// (point, direction) sum and of the element's faces (the lift pre-scaled by 1/|det A| so it
+// shares the accumulator); a shuffle tree combines the S shares.  Every operand row is read
+// with 16-byte loads and serves all nb accumulators.  (Staging the block's face fluxes and
+// the 3D trace tables in shared memory was measured slower on GB300: the larger footprint
+// costs more occupancy than the L1 traffic it saves.)
 template <class T, int D, int P, bool TAN>
 __global__ void __launch_bounds__(256) elem_kernel(DGData<T> d, const T* __restrict__ u,
                                                    const T* __restrict__ du, const T* __restrict__ G,
                                                    T* __restrict__ out, const T* __restrict__ escale,
                                                    const int* __restrict__ skip, const double* __restrict__ oscale) {
   using O = Ord<D, P>;
-  constexpr int NB = O::NB, NQ = O::NQ, ET = O::ET, NVB = O::NVB, NV = O::NV, GEO = O::GEO, DV = D * NV;
+  constexpr int NB = O::NB, NQ = O::NQ, NFQ = O::NFQ, ET = O::ET, NVB = O::NVB, NV = O::NV, GEO = O::GEO;
+  constexpr int DV = D * NV, NF = O::NF, NPERM = O::NPERM;
+  constexpr int NBP = PADV<T, NB>;
   constexpr bool SM = O::SMEM_BF;
-  using S = typename std::conditional<TAN, Tangent<T>, T>::type;
-  __shared__ T sBv[NQ * NB];
-  __shared__ T sDv[D * NQ * NB];
-  __shared__ T sBf[SM ? O::NBF : 1];
-  __shared__ T su[ET * NVB];
-  __shared__ T sdu[TAN ? ET * NVB : 1];
+  constexpr int NPAIR = ET * NV;
+  constexpr int S = (NPAIR * 8 <= 256) ? 8 : (NPAIR * 4 <= 256) ? 4 : (NPAIR * 2 <= 256) ? 2 : 1;
+  constexpr int ROUNDS = (NPAIR * S + 255) / 256;
+  using Sc = typename std::conditional<TAN, Tangent<T>, T>::type;
+  __shared__ __align__(16) T sBv[NQ * NBP];
+  __shared__ __align__(16) T sDv[D * NQ * NBP];
+  __shared__ __align__(16) T sBf[SM ? NF * NPERM * NFQ * NBP : 1];
+  __shared__ __align__(16) T su[ET * NV * NBP];
+  __shared__ __align__(16) T sdu[TAN ? ET * NV * NBP : 1];
   __shared__ T sF[ET * NQ * DV];
   __shared__ T sgeo[ET * GEO];
   if (skip && *skip) return;
   const int64_t e0 = (int64_t)blockIdx.x * ET;
   const int ne = (int)((d.E - e0) < ET ? (d.E - e0) : ET);
-  for (int i = threadIdx.x; i < NQ * NB; i += blockDim.x) sBv[i] = d.Bv[i];
-  for (int i = threadIdx.x; i < D * NQ * NB; i += blockDim.x) sDv[i] = d.Dv[i];
+  for (int i = threadIdx.x; i < NQ * NBP; i += blockDim.x) {
+    const int r = i / NBP, j = i - r * NBP;
+    sBv[i] = j < NB ? d.Bv[r * NB + j] : T(0);
+  }
+  for (int i = threadIdx.x; i < D * NQ * NBP; i += blockDim.x) {
+    const int r = i / NBP, j = i - r * NBP;
+    sDv[i] = j < NB ? d.Dv[r * NB + j] : T(0);
+  }
   if constexpr (SM)
-    for (int i = threadIdx.x; i < O::NBF; i += blockDim.x) sBf[i] = d.Bf[i];
-  for (int i = threadIdx.x; i < ne * NVB; i += blockDim.x) {
-    su[i] = u[e0 * NVB + i];
-    if constexpr (TAN) sdu[i] = du[e0 * NVB + i];
+    for (int i = threadIdx.x; i < NF * NPERM * NFQ * NBP; i += blockDim.x) sBf[i] = d.BfP[i];
+  for (int i = threadIdx.x; i < ne * NV * NBP; i += blockDim.x) {
+    const int r = i / NBP, j = i - r * NBP;
+    su[i] = j < NB ? u[e0 * NVB + r * NB + j] : T(0);
+    if constexpr (TAN) sdu[i] = j < NB ? du[e0 * NVB + r * NB + j] : T(0);
   }
   for (int i = threadIdx.x; i < ne * GEO; i += blockDim.x) sgeo[i] = d.geo[e0 * GEO + i];
   __syncthreads();
@@ -193,27 +242,35 @@ __global__ void __launch_bounds__(256) elem_kernel(DGData<T> d, const T* __restr
   for (int it = threadIdx.x; it < ne * NQ; it += blockDim.x) {
     const int el = it / NQ, q = it - el * NQ;
     const T* ge = sgeo + el * GEO;
-    const T isd = T(1) / ge[O::SD];
-    S U[NV];
+    const T isd = ge[O::ISD];
+    T b[NBP];
+    load_row<T, NBP>(sBv + q * NBP, b);
+    Sc U[NV];
 #pragma unroll
     for (int v = 0; v < NV; ++v) {
-      T a = 0, b = 0;
+      T c[NBP];
+      load_row<T, NBP>(su + (el * NV + v) * NBP, c);
+      T a = 0;
 #pragma unroll
-      for (int j = 0; j < NB; ++j) {
-        a += sBv[q * NB + j] * su[el * NVB + v * NB + j];
-        if constexpr (TAN) b += sBv[q * NB + j] * sdu[el * NVB + v * NB + j];
+      for (int j = 0; j < NB; ++j) a = fma(b[j], c[j], a);
+      if constexpr (TAN) {
+        load_row<T, NBP>(sdu + (el * NV + v) * NBP, c);
+        T t = 0;
+#pragma unroll
+        for (int j = 0; j < NB; ++j) t = fma(b[j], c[j], t);
+        U[v] = Sc{a * isd, t * isd};
+      } else {
+        U[v] = a * isd;
       }
-      if constexpr (TAN) U[v] = S{a * isd, b * isd};
-      else U[v] = a * isd;
     }
-    S F[D][NV];
-    euler_flux<D, S, T>(U, g, F);
+    Sc F[D][NV];
+    euler_flux<D, Sc, T>(U, g, F);
     T* fo = sF + (el * NQ + q) * DV;
 #pragma unroll
     for (int v = 0; v < NV; ++v) {
       T fk[D];
 #pragma unroll
-      for (int k = 0; k < D; ++k) fk[k] = PartOf<S>::get(F[k][v]);
+      for (int k = 0; k < D; ++k) fk[k] = PartOf<Sc>::get(F[k][v]);
 #pragma unroll
       for (int dd = 0; dd < D; ++dd) {
         T a = ge[dd * D] * fk[0];
@@ -224,23 +281,54 @@ __global__ void __launch_bounds__(256) elem_kernel(DGData<T> d, const T* __restr
     }
   }
   __syncthreads();
-  const T* Bf = SM ? sBf : d.Bf;
-  // phase 2: test against grad phi, lift the face fluxes
-  for (int it = threadIdx.x; it < ne * NVB; it += blockDim.x) {
-    const int el = it / NVB, r = it - el * NVB;
-    const int v = r / NB, i = r - v * NB;
-    const T sd = sgeo[el * GEO + O::SD];
-    T acc = 0;
+  const T* Bf = SM ? sBf : d.BfP;
+  // phase 2: S lanes per (element, variable): test against grad phi and lift the faces
+  const int ls = threadIdx.x % S;
+#pragma unroll 1
+  for (int round = 0; round < ROUNDS; ++round) {
+    const int pr = round * (256 / S) + (int)threadIdx.x / S;
+    const bool act = pr < ne * NV;
+    const int prc = act ? pr : 0;
+    const int el = prc / NV, v = prc - (prc / NV) * NV;
+    T acc[NB];
 #pragma unroll
-    for (int q = 0; q < NQ; ++q)
+    for (int i = 0; i < NB; ++i) acc[i] = T(0);
+    for (int k = ls; k < NQ * D; k += S) {
+      const int q = k / D, dd = k - (k / D) * D;
+      const T f = sF[(el * NQ + q) * DV + dd * NV + v];
+      T row[NBP];
+      load_row<T, NBP>(sDv + (dd * NQ + q) * NBP, row);
 #pragma unroll
-      for (int dd = 0; dd < D; ++dd) acc += sDv[(dd * NQ + q) * NB + i] * sF[(el * NQ + q) * DV + dd * NV + v];
-    acc *= sd;
+      for (int i = 0; i < NB; ++i) acc[i] = fma(row[i], f, acc[i]);
+    }
     const int64_t e = e0 + el;
-    const T lift = lift_faces<T, D, P, SM>(d, Bf, G, e, v, i);
-    acc = (acc + lift / sd) * osc;
-    if (escale) acc *= escale[e];
-    out[e0 * NVB + it] = acc;
+    const T isd = sgeo[el * GEO + O::ISD];
+    const T rdet = isd * isd;  // the lift carries 1/sqrt|det|, the volume term sqrt|det|
+    for (int kf = ls; kf < NF; kf += S) {
+      const int fs = d.ef[NF * e + kf];
+      const T* gf = G + (int64_t)slot_face<O>(fs) * NFQ * NV;
+      const T* tb = Bf + ((kf * NPERM + slot_perm(fs)) * NFQ) * NBP;
+      const T sg = slot_side(fs) ? rdet : -rdet;
+#pragma unroll
+      for (int q = 0; q < NFQ; ++q) {
+        const T gq = sg * gf[q * NV + v];
+        T row[NBP];
+        load_row<T, NBP, !SM>(tb + q * NBP, row);
+#pragma unroll
+        for (int i = 0; i < NB; ++i) acc[i] = fma(row[i], gq, acc[i]);
+      }
+    }
+#pragma unroll
+    for (int off = S / 2; off >= 1; off /= 2)
+#pragma unroll
+      for (int i = 0; i < NB; ++i) acc[i] += __shfl_xor_sync(0xffffffffu, acc[i], off);
+    if (act) {
+      T sc = sgeo[el * GEO + O::SD] * osc;
+      if (escale) sc *= escale[e];
+#pragma unroll
+      for (int i = 0; i < NB; ++i)
+        if (i % S == ls) out[e * NVB + v * NB + i] = acc[i] * sc;
+    }
   }
 }
 
@@ -282,7 +370,7 @@ __global__ void __launch_bounds__(256) linearize_vol_kernel(DGData<T> d, const T
   const int64_t e = idx / NQ;
   const int q = (int)(idx - e * NQ);
   const T* ge = d.geo + GEO * e;
-  const T isd = T(1) / ge[O::SD];
+  const T isd = ge[O::ISD];
   J U[NV];
 #pragma unroll
   for (int v = 0; v < NV; ++v) {
@@ -327,7 +415,7 @@ __global__ void __launch_bounds__(128) linearize_face_kernel(DGData<T> d, const 
   for (int k = 0; k < D; ++k) nr[k] = d.fgeo[4 * f + k];
   const T wq = d.fgeo[4 * f + D] * d.Wf[q];
   T uL[NV], uR[NV];
-  const T isdL = T(1) / d.geo[GEO * (int64_t)eL + O::SD];
+  const T isdL = d.geo[GEO * (int64_t)eL + O::ISD];
   T isdR = T(0);
   {
     const T* be = d.Bf + ((fL * NPERM) * NFQ + q) * NB;
@@ -340,7 +428,7 @@ __global__ void __launch_bounds__(128) linearize_face_kernel(DGData<T> d, const 
     }
   }
   if (eR >= 0) {
-    isdR = T(1) / d.geo[GEO * (int64_t)eR + O::SD];
+    isdR = d.geo[GEO * (int64_t)eR + O::ISD];
     const T* be = d.Bf + ((fR * NPERM + pR) * NFQ + q) * NB;
 #pragma unroll
     for (int v = 0; v < NV; ++v) {
@@ -479,7 +567,7 @@ __global__ void __launch_bounds__(256) elem_apply_kernel(DGData<T> d, const T* _
   if constexpr (SM)
     for (int i = threadIdx.x; i < O::NBF; i += blockDim.x) sBf[i] = d.Bf[i];
   for (int i = threadIdx.x; i < ne * NVB; i += blockDim.x) sdu[i] = dv[e0 * NVB + i];
-  for (int i = threadIdx.x; i < ne; i += blockDim.x) ssd[i] = d.geo[(e0 + i) * GEO + O::SD];
+  for (int i = threadIdx.x; i < ne; i += blockDim.x) ssd[i] = d.geo[(e0 + i) * GEO + O::ISD];
   __syncthreads();
   const T osc = oscale ? (T)*oscale : T(1);
   // phase 1: trace of dv at this thread's volume point, times the mapped flux Jacobians
@@ -520,31 +608,38 @@ __global__ void __launch_bounds__(256) elem_apply_kernel(DGData<T> d, const T* _
       for (int dd = 0; dd < D; ++dd) acc += sDv[(dd * NQ + q) * NB + i] * sF[(el * NQ + q) * DV + dd * NV + v];
     const int64_t e = e0 + el;
     const T lift = lift_faces<T, D, P, SM>(d, Bf, G, e, v, i);
-    acc = (acc + lift / ssd[el]) * osc;
+    acc = (acc + lift * ssd[el]) * osc;
     if (escale) acc *= escale[e];
     out[e0 * NVB + it] = acc;
   }
 }
 
 template <class T, int D, int P>
-cudaError_t linearize_p(const DGData<T>& d, const T* u, LinData<T> lin, cudaStream_t st) {
+cudaError_t linearize_p(const DGData<T>& d, const T* u, LinData<T> lin, bool faces_only, cudaStream_t st) {
   using O = Ord<D, P>;
   const int64_t nv = d.E * O::NQ, nf = d.F * O::NFQ;
-  linearize_vol_kernel<T, D, P><<<(unsigned)((nv + 255) / 256), 256, 0, st>>>(d, u, lin.Avol);
+  if (!faces_only) linearize_vol_kernel<T, D, P><<<(unsigned)((nv + 255) / 256), 256, 0, st>>>(d, u, lin.Avol);
   if (nf > 0) linearize_face_kernel<T, D, P><<<(unsigned)((nf + 127) / 128), 128, 0, st>>>(d, u, lin.Bface);
   return cudaGetLastError();
 }
 
+// J v from the face point Jacobians and either the volume point Jacobians (u_elem null)
+// or the volume flux tangents recomputed at u_elem (the elements then read u and dv
+// instead of D nv^2 values per volume point).
 template <class T, int D, int P>
-cudaError_t jac_apply_p(const DGData<T>& d, LinData<T> lin, const T* dv, T* out, T* G, const T* escale,
-                        const int* skip, const double* oscale, cudaStream_t st, const cudaEvent_t* ev) {
+cudaError_t jac_apply_p(const DGData<T>& d, LinData<T> lin, const T* u_elem, const T* dv, T* out, T* G,
+                        const T* escale, const int* skip, const double* oscale, cudaStream_t st,
+                        const cudaEvent_t* ev) {
   using O = Ord<D, P>;
   const int64_t nf = d.F * O::NFQ;
   if (ev) cudaEventRecord(ev[0], st);
   if (nf > 0) face_apply_kernel<T, D, P><<<(unsigned)((nf + 255) / 256), 256, 0, st>>>(d, lin.Bface, dv, G, skip);
   if (ev) cudaEventRecord(ev[1], st);
   const int64_t eb = (d.E + O::ET - 1) / O::ET;
-  elem_apply_kernel<T, D, P><<<(unsigned)eb, 256, 0, st>>>(d, lin.Avol, dv, G, out, escale, skip, oscale);
+  if (u_elem)
+    elem_kernel<T, D, P, true><<<(unsigned)eb, 256, 0, st>>>(d, u_elem, dv, G, out, escale, skip, oscale);
+  else
+    elem_apply_kernel<T, D, P><<<(unsigned)eb, 256, 0, st>>>(d, lin.Avol, dv, G, out, escale, skip, oscale);
   if (ev) cudaEventRecord(ev[2], st);
   return cudaGetLastError();
 }
@@ -579,7 +674,7 @@ __global__ void __launch_bounds__(256) face_adjoint_kernel(DGData<T> d, const T*
   const int fL = loc & 0xff, fR = (loc >> 8) & 0xff, pR = loc >> 16;
   T gb[NV];
   {
-    const T sc = -osc * (escale ? escale[eL] : T(1)) / d.geo[GEO * (int64_t)eL + O::SD];
+    const T sc = -osc * (escale ? escale[eL] : T(1)) * d.geo[GEO * (int64_t)eL + O::ISD];
     const T* be = Bf + ((fL * NPERM) * NFQ + q) * NB;
 #pragma unroll
     for (int v = 0; v < NV; ++v) {
@@ -590,7 +685,7 @@ __global__ void __launch_bounds__(256) face_adjoint_kernel(DGData<T> d, const T*
     }
   }
   if (eR >= 0) {
-    const T sc = osc * (escale ? escale[eR] : T(1)) / d.geo[GEO * (int64_t)eR + O::SD];
+    const T sc = osc * (escale ? escale[eR] : T(1)) * d.geo[GEO * (int64_t)eR + O::ISD];
     const T* be = Bf + ((fR * NPERM + pR) * NFQ + q) * NB;
 #pragma unroll
     for (int v = 0; v < NV; ++v) {
@@ -962,7 +1057,7 @@ __global__ void __launch_bounds__(256) wall_force_kernel(DGData<T> d, int64_t f0
     double na = 0;
     for (int k = 0; k < D; ++k) na += (double)d.fgeo[4 * f + k] * a3[k];
     const double meas = (double)d.fgeo[4 * f + D];
-    const double isd = 1.0 / (double)d.geo[GEO * (int64_t)e + O::SD];
+    const double isd = (double)d.geo[GEO * (int64_t)e + O::ISD];
     double g[NV * NB];
     for (int k = 0; k < NV * NB; ++k) g[k] = 0.0;
     for (int q = 0; q < NFQ; ++q) {
@@ -1064,7 +1159,7 @@ __global__ void __launch_bounds__(256) local_dt_kernel(DGData<T> d, const T* __r
   const double cfl = cfl_dev ? *cfl_dev : cfl_host;
   double mn = DBL_MAX;
   for (int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; e < d.E; e += (int64_t)gridDim.x * blockDim.x) {
-    const T isd = T(1) / d.geo[GEO * e + O::SD];
+    const T isd = d.geo[GEO * e + O::ISD];
     double U[NV];
     for (int v = 0; v < NV; ++v) {
       T a = 0;
@@ -1126,13 +1221,14 @@ cudaError_t launch_dg_operator_d(const DGData<T>& d, const T* u, const T* du, T*
   PCEXP_PSWITCH(D, (dg_op_p<T, D, P_>(d, u, du, out, G, escale, skip, oscale, st, ev)))
 }
 template <class T, int D>
-cudaError_t launch_linearize_d(const DGData<T>& d, const T* u, LinData<T> lin, cudaStream_t st) {
-  PCEXP_PSWITCH(D, (linearize_p<T, D, P_>(d, u, lin, st)))
+cudaError_t launch_linearize_d(const DGData<T>& d, const T* u, LinData<T> lin, bool faces_only, cudaStream_t st) {
+  PCEXP_PSWITCH(D, (linearize_p<T, D, P_>(d, u, lin, faces_only, st)))
 }
 template <class T, int D>
-cudaError_t launch_jac_apply_d(const DGData<T>& d, LinData<T> lin, const T* dv, T* out, T* G, const T* escale,
-                               const int* skip, const double* oscale, cudaStream_t st, const cudaEvent_t* ev) {
-  PCEXP_PSWITCH(D, (jac_apply_p<T, D, P_>(d, lin, dv, out, G, escale, skip, oscale, st, ev)))
+cudaError_t launch_jac_apply_d(const DGData<T>& d, LinData<T> lin, const T* u_elem, const T* dv, T* out, T* G,
+                               const T* escale, const int* skip, const double* oscale, cudaStream_t st,
+                               const cudaEvent_t* ev) {
+  PCEXP_PSWITCH(D, (jac_apply_p<T, D, P_>(d, lin, u_elem, dv, out, G, escale, skip, oscale, st, ev)))
 }
 template <class T, int D>
 cudaError_t launch_jac_adjoint_d(const DGData<T>& d, LinData<T> lin, const T* w, T* out, T* GT, const T* escale,
@@ -1195,9 +1291,10 @@ cudaError_t launch_local_dt_d(const DGData<T>& d, const T* u, const double* cfl_
 #define PCEXP_INST_D(T, D)                                                                                         \
   template cudaError_t launch_dg_operator_d<T, D>(const DGData<T>&, const T*, const T*, T*, T*, const T*,           \
                                                   const int*, cudaStream_t, const cudaEvent_t*, const double*);    \
-  template cudaError_t launch_linearize_d<T, D>(const DGData<T>&, const T*, LinData<T>, cudaStream_t);             \
-  template cudaError_t launch_jac_apply_d<T, D>(const DGData<T>&, LinData<T>, const T*, T*, T*, const T*,          \
-                                                const int*, const double*, cudaStream_t, const cudaEvent_t*);      \
+  template cudaError_t launch_linearize_d<T, D>(const DGData<T>&, const T*, LinData<T>, bool, cudaStream_t);       \
+  template cudaError_t launch_jac_apply_d<T, D>(const DGData<T>&, LinData<T>, const T*, const T*, T*, T*,          \
+                                                const T*, const int*, const double*, cudaStream_t,                 \
+                                                const cudaEvent_t*);                                               \
   template cudaError_t launch_jac_adjoint_d<T, D>(const DGData<T>&, LinData<T>, const T*, T*, T*, const T*, T,     \
                                                   cudaStream_t);                                                   \
   template cudaError_t launch_jvp_state_adjoint_d<T, D>(const DGData<T>&, const T*, const T*, const T*, T*, T*,    \

@@ -404,6 +404,7 @@ int build_setup(const pcexp_mesh& mesh, int p, Setup& s, std::string& msg) {
     const double sdet = std::sqrt(det);
     g[D * D] = sdet;
     g[D * D + 1] = 2.0 * D * (det / fact) / bnd;  // h = 2 d |E| / |dE|
+    g[D * D + 2] = 1.0 / sdet;                     // so the kernels multiply instead of dividing
     s.volume += det / fact;
     // quadrature points as offsets from v0, weights, centroid offset and half-extents
     double rc[3] = {0, 0, 0}, area = 0;

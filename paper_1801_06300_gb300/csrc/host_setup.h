@@ -46,7 +46,7 @@ struct Setup {
   std::vector<double> Wf;  // [nfq]                 face weights (sum 1 on edges, 1/2 on triangles)
   std::vector<double> Bc;  // [nb]                  phi^_j at the reference centroid
   // per element
-  std::vector<double> geo;     // [E][8 or 12]: A^-1 (D x D), sqrt(det A), h
+  std::vector<double> geo;     // [E][8 or 12]: A^-1 (D x D), sqrt(det A), h, 1 / sqrt(det A)
   std::vector<double> xqphys;  // [E][nq][D] physical volume points (projections, functionals)
   std::vector<int32_t> ef;     // [E][NF] face slot (face << 4) | (side << 3) | perm
   std::vector<double> Q;       // [E][nb][nb] paper <- internal

@@ -57,7 +57,7 @@ struct StepState {
 // NF = D + 1 faces per element, NPERM = 2 (2D) or 6 (3D) face-vertex permutations.
 template <class T>
 struct DGData {
-  const T* geo;          // [E][GEO]: A^-1 (D x D row-major), sqrt|det A|, h; GEO = 8 (2D) or 12 (3D)
+  const T* geo;          // [E][GEO]: A^-1 (D x D row-major), sqrt|det A|, h, 1/sqrt|det A|; GEO = 8 or 12
   const int32_t* ef;     // [E][NF]: face slot (face << 4) | (side << 3) | perm
   const int32_t* fel;    // [F][2]: e_L, e_R (e_R = -tag on boundary faces)
   const int32_t* floc;   // [F]: f_L | f_R << 8 | perm_R << 16
@@ -68,6 +68,7 @@ struct DGData {
   const T* Wf;           // [nfq]
   const T* Bc;           // [nb]
   const T* Wv;           // [nq] reference volume weights
+  const T* BfP;          // [NF][NPERM][nfq][nbp]: Bf with rows padded to whole 16-byte vectors
   int64_t E, F;
   Free<T> fs;
   int p;
@@ -90,10 +91,11 @@ template <class T, int D>
 cudaError_t launch_dg_operator_d(const DGData<T>& d, const T* u, const T* du, T* out, T* G, const T* escale,
                                  const int* skip, cudaStream_t st, const cudaEvent_t* ev, const double* oscale);
 template <class T, int D>
-cudaError_t launch_linearize_d(const DGData<T>& d, const T* u, LinData<T> lin, cudaStream_t st);
+cudaError_t launch_linearize_d(const DGData<T>& d, const T* u, LinData<T> lin, bool faces_only, cudaStream_t st);
 template <class T, int D>
-cudaError_t launch_jac_apply_d(const DGData<T>& d, LinData<T> lin, const T* dv, T* out, T* G, const T* escale,
-                               const int* skip, const double* oscale, cudaStream_t st, const cudaEvent_t* ev);
+cudaError_t launch_jac_apply_d(const DGData<T>& d, LinData<T> lin, const T* u_elem, const T* dv, T* out, T* G,
+                               const T* escale, const int* skip, const double* oscale, cudaStream_t st,
+                               const cudaEvent_t* ev);
 template <class T, int D>
 cudaError_t launch_jac_adjoint_d(const DGData<T>& d, LinData<T> lin, const T* w, T* out, T* GT, const T* escale,
                                  T osc, cudaStream_t st);
@@ -122,17 +124,23 @@ cudaError_t launch_dg_operator(const DGData<T>& d, const T* u, const T* du, T* o
   return d.dim == 3 ? launch_dg_operator_d<T, 3>(d, u, du, out, G, escale, skip, st, ev, oscale)
                     : launch_dg_operator_d<T, 2>(d, u, du, out, G, escale, skip, st, ev, oscale);
 }
-// Evaluate the point Jacobians at u (once per linearisation state).
+// Evaluate the point Jacobians at u (once per linearisation state): faces and volume, or
+// the face blocks only (faces_only, when the volume part of J v recomputes flux tangents).
 template <class T>
-cudaError_t launch_linearize(const DGData<T>& d, const T* u, LinData<T> lin, cudaStream_t st) {
-  return d.dim == 3 ? launch_linearize_d<T, 3>(d, u, lin, st) : launch_linearize_d<T, 2>(d, u, lin, st);
+cudaError_t launch_linearize(const DGData<T>& d, const T* u, LinData<T> lin, cudaStream_t st,
+                             bool faces_only = false) {
+  return d.dim == 3 ? launch_linearize_d<T, 3>(d, u, lin, faces_only, st)
+                    : launch_linearize_d<T, 2>(d, u, lin, faces_only, st);
 }
-// out = J(u) dv from the point Jacobians (same ev / escale / skip / oscale conventions).
+// out = J(u) dv from the face point Jacobians and, for the volume, the volume point
+// Jacobians (u_elem null) or the flux tangents at u_elem (same ev / escale / skip /
+// oscale conventions as the operator).
 template <class T>
 cudaError_t launch_jac_apply(const DGData<T>& d, LinData<T> lin, const T* dv, T* out, T* G, const T* escale,
-                             const int* skip, const double* oscale, cudaStream_t st, const cudaEvent_t* ev) {
-  return d.dim == 3 ? launch_jac_apply_d<T, 3>(d, lin, dv, out, G, escale, skip, oscale, st, ev)
-                    : launch_jac_apply_d<T, 2>(d, lin, dv, out, G, escale, skip, oscale, st, ev);
+                             const int* skip, const double* oscale, cudaStream_t st, const cudaEvent_t* ev,
+                             const T* u_elem = nullptr) {
+  return d.dim == 3 ? launch_jac_apply_d<T, 3>(d, lin, u_elem, dv, out, G, escale, skip, oscale, st, ev)
+                    : launch_jac_apply_d<T, 2>(d, lin, u_elem, dv, out, G, escale, skip, oscale, st, ev);
 }
 // out = (osc * diag(escale) * J(u))^T w from the point Jacobians; GT is scratch [F][nfq][2 NV].
 template <class T>

@@ -104,6 +104,19 @@ PCEXP_DEV T dot_vec(const T (&a)[VN], const T (&b)[VN]) {
   return s;
 }
 
+// acc += <a, b> over one chunk.  FP64: FMAs straight into the accumulator (one FP64
+// instruction per element; the FP64 pipe bounds these passes).  FP32: the chunk's FMA chain,
+// then one compensated addition.
+template <class T, int VN>
+PCEXP_DEV void acc_dot(Acc<T>& acc, const T (&a)[VN], const T (&b)[VN]) {
+  if constexpr (sizeof(T) == 8) {
+#pragma unroll
+    for (int v = 0; v < VN; ++v) acc.s = fma(a[v], b[v], acc.s);
+  } else {
+    acc.add(dot_vec<T, VN>(a, b));
+  }
+}
+
 // Stage logic of the last block: per-column entries in parallel, scalars on thread 0.
 PCEXP_DEV void cgs_finalize(int mode, int j, const double* dots, KState* ks, double eta) {
   __shared__ int bad;
@@ -220,17 +233,17 @@ __global__ void __launch_bounds__(256) cgs_kernel(const T* __restrict__ Z, int64
     T x[VN];
     load_vec<T, VN>(w + r, x);
     if constexpr (MODE == CGS_NORM) {
-      acc[0].add(dot_vec<T, VN>(x, x));
+      acc_dot<T, VN>(acc[0], x, x);
     } else if constexpr (MODE == CGS_PROJ) {
 #pragma unroll
       for (int c = 0; c < NC; ++c) {
         if (c < nc) {
           T z[VN];
           load_vec<T, VN>(Z + c * ldz + r, z);
-          acc[c].add(dot_vec<T, VN>(z, x));
+          acc_dot<T, VN>(acc[c], z, x);
         }
       }
-      acc[NC].add(dot_vec<T, VN>(x, x));
+      acc_dot<T, VN>(acc[NC], x, x);
     } else {
       // update pass; the projection pass below re-reads the same 16-byte chunks (L1)
 #pragma unroll
@@ -249,12 +262,12 @@ __global__ void __launch_bounds__(256) cgs_kernel(const T* __restrict__ Z, int64
           if (c < nc) {
             T z[VN];
             load_vec<T, VN>(Z + c * ldz + r, z);
-            acc[c].add(dot_vec<T, VN>(z, x));
+            acc_dot<T, VN>(acc[c], z, x);
           }
         }
       } else {
         store_vec<T, VN>(out + r, x);
-        acc[0].add(dot_vec<T, VN>(x, x));
+        acc_dot<T, VN>(acc[0], x, x);
       }
     }
   }
@@ -398,8 +411,8 @@ __global__ void __launch_bounds__(256) cgs_cs_kernel(const T* __restrict__ Z, in
       for (int v = 0; v < VN; ++v) x[v] = T(0);
     if constexpr (MODE == CGS_PROJ) {
 #pragma unroll
-      for (int k = 0; k < NCW; ++k) acc[k].add(dot_vec<T, VN>(z[k], x));
-      if (wid == 0) acc[NCW].add(dot_vec<T, VN>(x, x));
+      for (int k = 0; k < NCW; ++k) acc_dot<T, VN>(acc[k], z[k], x);
+      if (wid == 0) acc_dot<T, VN>(acc[NCW], x, x);
     } else {
       T p[VN];
 #pragma unroll
@@ -424,7 +437,7 @@ __global__ void __launch_bounds__(256) cgs_cs_kernel(const T* __restrict__ Z, in
 #pragma unroll
           for (int v = 0; v < VN; ++v) xs[lane * VN + v] = x[v];
         } else {
-          acc[NCW].add(dot_vec<T, VN>(x, x));
+          acc_dot<T, VN>(acc[NCW], x, x);
         }
       }
       __syncthreads();
@@ -433,7 +446,7 @@ __global__ void __launch_bounds__(256) cgs_cs_kernel(const T* __restrict__ Z, in
 #pragma unroll
         for (int v = 0; v < VN; ++v) xn[v] = xs[lane * VN + v];
 #pragma unroll
-        for (int k = 0; k < NCW; ++k) acc[k].add(dot_vec<T, VN>(z[k], xn));
+        for (int k = 0; k < NCW; ++k) acc_dot<T, VN>(acc[k], z[k], xn);
       }
     }
   }
