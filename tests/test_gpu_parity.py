@@ -328,3 +328,21 @@ def test_torch_device_pointers(capi):
     torch.cuda.synchronize()
     assert rel(R.cpu().numpy(), dg.residual(u)) <= 1e-12
     ctx.close()
+
+
+def test_vjp_fp32_mixed_builds_volume_blocks(capi):
+    """FP32-mixed contexts apply J v from face blocks and volume flux tangents; the transpose
+    builds the volume blocks on demand.  Dot-product consistency w.J v = (J^T w).v and the
+    oracle's dense transpose, both to FP32 accuracy."""
+    mesh, free = W.periodic_square(4, 10.0, 0.15, 3), W.Freestream(0.5, 30.0)
+    dg = oracle_dg(mesh, 1, free)
+    ctx = capi.Context(mesh, 1, free, capi.PCEXP_FP32_MIXED, m_max=2)
+    u = perturbed_state(dg, 1)
+    v = W.random_coeffs(2, (dg.K,))
+    w = W.random_coeffs(3, (dg.K,))
+    Jv = ctx.jvp(u, v)
+    JTw = ctx.vjp(u, w)
+    assert abs(w @ Jv - JTw @ v) <= 2e-6 * (np.abs(w) @ np.abs(Jv))
+    ref = dg.dense_jacobian(u).T @ w
+    assert rel(JTw, ref) <= 2e-5
+    ctx.close()
