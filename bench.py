@@ -217,6 +217,26 @@ def roofline_entry(prof, precision_bytes, K, E, F, hbm, peak_kind, dim=2, p=2, m
     return entry
 
 
+def kernel_table(prof, precision_bytes, K, E, F, hbm, dim=2, p=2, m=30):
+    """Every kernel class with a byte model: launches, mean launch time (CUDA events per
+    class over the profiled steps), algorithmic GB/s and its fraction of measured HBM; FP64
+    classes with a flop model also give TFLOP/s and the fraction of the FP64 pipe."""
+    out = {}
+    for kind, (n, ms) in prof.items():
+        ab = algorithmic_bytes(kind, precision_bytes, K, E, F, dim, p, m)
+        if not n or ab is None:
+            continue
+        sec = ms / n / 1e3
+        row = {"launches": n, "avg_launch_us": round(sec * 1e6, 2), "gbs": round(ab / sec / 1e9, 1),
+               "hbm_frac": round(ab / sec / 1e9 / hbm, 4)}
+        fl = algorithmic_flops(kind, K, E, F, dim, p, m)
+        if precision_bytes == 8 and fl is not None:
+            row["fp64_tflops"] = round(fl / sec / 1e12, 3)
+            row["fp64_frac"] = round(fl / sec / 1e12 / FP64_PEAK_TFLOPS, 4)
+        out[kind] = row
+    return out
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -362,8 +382,10 @@ def main():
     launches = sum(v[0] for v in prof.values())
     Tb = 8 if args.precision == "fp64" else 4
     roof = roofline_entry(prof, Tb, K, E, F, hbm, peak_kind, 2, P, M)
+    kernels = kernel_table(prof, Tb, K, E, F, hbm, 2, P, M)
     if mixed is not None:
         mixed["roofline"] = roofline_entry(prof32, 4, K, E, F, hbm, peak_kind, 2, P, M)
+        mixed["kernels"] = kernel_table(prof32, 4, K, E, F, hbm, 2, P, M)
     ctx64.close()
 
     # the 3D vortex (48^3 cubes as 663,552 Kuhn tetrahedra, P2, K = 33,177,600), both forms
@@ -393,6 +415,10 @@ def main():
         "ms_per_step_with_kernel_events": ms64_prof / args.steps,
         "kernel_ms_per_step": {k: round(v[1] / args.steps, 4) for k, v in prof.items() if v[0]},
         "roofline": roof,
+        "kernels": kernels,
+        "kernels_note": ("algorithmic bytes (and FP64 flops) per launch over CUDA-event time per kernel "
+                         "class; at this size a Krylov basis of 31 vectors (146 MB FP64, 73 MB FP32) is "
+                         "partly or wholly L2-resident, so Gram-Schmidt fractions of HBM can exceed 1"),
         "cpu_baseline": cpu,
         "fp32_mixed": mixed,
         "vortex3d": v3d,
@@ -437,7 +463,8 @@ def vortex3d_block(args, capi, W, torch, np, local, hbm, peak_kind):
         res[name] = {"value": K * steps / (ms / 1e3), "ms_per_step": ms / steps,
                      "kernel_ms_per_step": {k: round(v[1], 3) for k, v in prof.items() if v[0]},
                      "roofline": roofline_entry(prof, 8 if name == "fp64" else 4, K, E, F, hbm, peak_kind,
-                                                3, case.p, case.m, "vortex3d")}
+                                                3, case.p, case.m, "vortex3d"),
+                     "kernels": kernel_table(prof, 8 if name == "fp64" else 4, K, E, F, hbm, 3, case.p, case.m)}
         ctx.close()
     a, b = states["fp64"], states["fp32_mixed"]
     res["fp32_mixed"]["speedup_vs_fp64"] = res["fp64"]["ms_per_step"] / res["fp32_mixed"]["ms_per_step"]

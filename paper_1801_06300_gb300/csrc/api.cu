@@ -674,6 +674,7 @@ int create_impl(pcexp_ctx* c, const pcexp_mesh* mesh, int p, const pcexp_physics
     PCEXP_TRY(upload<float>(c, &c->tabs, tabs));
     PCEXP_TRY(upload<float>(c, &c->geo, s.geo));
     PCEXP_TRY(upload<float>(c, &c->fgeo, s.fgeo));
+    if (c->jv_tangent) PCEXP_CK(launch_tan_tables(dgdata<float>(c), c->st));
   } else {
     PCEXP_TRY(upload<double>(c, &c->tabs, tabs));
     PCEXP_TRY(upload<double>(c, &c->geo, s.geo));

@@ -351,6 +351,170 @@ cudaError_t dg_op_p(const DGData<T>& d, const T* u, const T* du, T* out, T* G, c
   return cudaGetLastError();
 }
 
+// ------------------------------------- FP32 volume J v by flux tangents, one element per lane
+// The reference tables [Bv (nq x nb) | Dv (D x nq x nb)] of one (D, p) in constant memory.
+// They depend on the reference simplex alone, so every context of that order uploads the
+// same bytes (tan_tables_p); the kernel below reads them at warp-uniform addresses, which
+// the constant cache serves as broadcasts outside the load/store pipe.
+template <int D, int P> __constant__ float c_tan[(D + 1) * Ord<D, P>::NQ * Ord<D, P>::NB];
+
+// Block = D+1 warps over 32 elements, lane l on element e0 + l.  The warps split the volume
+// points (warp w takes q = w, w + D+1, ...) and the faces (warp w takes face w), so every
+// table index is warp-uniform; an element's u, u' rows and face fluxes are staged in shared
+// memory with strides that keep the per-lane reads free of bank conflicts.  Each warp keeps
+// all nv x nb sums of its element in registers; the D+1 partial sums meet in shared memory
+// and are added in warp order (deterministic), and the outputs leave as contiguous rows.
+// Same sums as elem_kernel<float, D, P, true>, in another order.
+template <int D, int P>
+__global__ void __launch_bounds__(32 * (D + 1), D == 3 ? 4 : 1) elem_tan_kernel(DGData<float> d, const float* __restrict__ u,
+                                                                const float* __restrict__ du,
+                                                                const float* __restrict__ G, float* __restrict__ out,
+                                                                const float* __restrict__ escale,
+                                                                const int* __restrict__ skip,
+                                                                const double* __restrict__ oscale) {
+  using O = Ord<D, P>;
+  constexpr int NB = O::NB, NQ = O::NQ, NFQ = O::NFQ, NV = O::NV, NF = O::NF, NPERM = O::NPERM, GEO = O::GEO;
+  constexpr int NVB = O::NVB, QW = NF, NT = 32 * QW;
+  constexpr int NBP = PADV<float, NB>;
+  constexpr int UR0 = 2 * NV * NBP;                     // u rows, then u' rows, of one element
+  constexpr int UROW = UR0 + (36 - UR0 % 32) % 32;      // = 4 (mod 32) words: 16-byte reads of 8 lanes hit 32 banks
+  constexpr int GREC = NF * NFQ * NV;                   // face fluxes seen by one element
+  constexpr int GROW = GREC | 1;                        // odd strides: scalar reads of 32 lanes hit 32 banks
+  constexpr int PST = NVB | 1;
+  constexpr int STAGE = 32 * (UROW + GROW), PART = QW * 32 * PST;
+  constexpr bool SM = O::SMEM_BF;
+  static_assert(UROW % 32 == 4 && UROW >= UR0, "row stride");
+  __shared__ __align__(16) float sm[STAGE > PART ? STAGE : PART];
+  __shared__ __align__(16) float sBf[SM ? NF * NPERM * NFQ * NBP : 1];
+  __shared__ int sef[32 * NF];
+  __shared__ float ssd[32];
+  float* su = sm;               // [32][UROW]
+  float* sg = sm + 32 * UROW;   // [32][GROW]
+  float* part = sm;             // [QW][32][PST], after the staged rows are consumed
+  if (skip && *skip) return;
+  const int tid = threadIdx.x, lane = tid & 31, w = tid >> 5;
+  const int64_t e0 = (int64_t)blockIdx.x * 32;
+  const int ne = (int)((d.E - e0) < 32 ? (d.E - e0) : 32);
+  for (int i = tid; i < ne * NF; i += NT) sef[i] = d.ef[e0 * NF + i];
+  for (int i = tid; i < ne * NVB; i += NT) {
+    const int el = i / NVB, r = i - el * NVB, v = r / NB, j = r - v * NB;
+    su[el * UROW + v * NBP + j] = u[e0 * NVB + i];
+    su[el * UROW + (NV + v) * NBP + j] = du[e0 * NVB + i];
+  }
+  if constexpr (SM)
+    for (int i = tid; i < NF * NPERM * NFQ * NBP; i += NT) sBf[i] = d.BfP[i];
+  __syncthreads();
+  for (int i = tid; i < ne * GREC; i += NT) {
+    const int el = i / GREC, r = i - el * GREC, kf = r / (NFQ * NV), k = r - kf * (NFQ * NV);
+    sg[el * GROW + r] = G[(int64_t)slot_face<O>(sef[el * NF + kf]) * NFQ * NV + k];
+  }
+  __syncthreads();
+  const int el = lane < ne ? lane : 0;  // lanes past the last element repeat element 0; discarded
+  const float* ge = d.geo + (e0 + el) * GEO;
+  float Ai[D * D];
+#pragma unroll
+  for (int k = 0; k < D * D; ++k) Ai[k] = ge[k];
+  const float isd = ge[O::ISD];
+  if (w == 0) ssd[lane] = ge[O::SD];
+  const float g = d.fs.gamma;
+  float acc[NV][NB];
+#pragma unroll
+  for (int v = 0; v < NV; ++v)
+#pragma unroll
+    for (int i = 0; i < NB; ++i) acc[v][i] = 0.f;
+  const float* ur = su + el * UROW;
+  // volume: trace and tangent at point q, flux tangent mapped to reference directions,
+  // tested against the reference gradients
+#pragma unroll 1
+  for (int q = w; q < NQ; q += QW) {
+    const float* bq = c_tan<D, P> + q * NB;
+    Tangent<float> U[NV];
+#pragma unroll
+    for (int v = 0; v < NV; ++v) {
+      float c[NBP];
+      load_row<float, NBP>(ur + v * NBP, c);
+      float a = 0.f;
+#pragma unroll
+      for (int j = 0; j < NB; ++j) a = fmaf(bq[j], c[j], a);
+      load_row<float, NBP>(ur + (NV + v) * NBP, c);
+      float t = 0.f;
+#pragma unroll
+      for (int j = 0; j < NB; ++j) t = fmaf(bq[j], c[j], t);
+      U[v] = Tangent<float>{a * isd, t * isd};
+      asm volatile("" ::: "memory");  // one variable's rows in flight at a time (registers)
+    }
+    Tangent<float> F[D][NV];
+    euler_flux<D, Tangent<float>, float>(U, g, F);
+    const float* dq = c_tan<D, P> + NQ * NB + q * NB;
+#pragma unroll
+    for (int dd = 0; dd < D; ++dd) {
+      float fh[NV];
+#pragma unroll
+      for (int v = 0; v < NV; ++v) {
+        float a = Ai[dd * D] * F[0][v].d;
+#pragma unroll
+        for (int k = 1; k < D; ++k) a += Ai[dd * D + k] * F[k][v].d;
+        fh[v] = a;
+      }
+#pragma unroll
+      for (int i = 0; i < NB; ++i) {
+        const float t = dq[dd * NQ * NB + i];
+#pragma unroll
+        for (int v = 0; v < NV; ++v) acc[v][i] = fmaf(t, fh[v], acc[v][i]);
+      }
+    }
+  }
+  // faces: lift of the staged face fluxes, pre-scaled by 1/|det A| to share the accumulators
+  const float rdet = isd * isd;
+  const float* Bf = SM ? sBf : d.BfP;
+#pragma unroll 1
+  for (int kf = w; kf < NF; kf += QW) {
+    const int fs = sef[el * NF + kf];
+    const float sgn = slot_side(fs) ? rdet : -rdet;
+    const float* tb = Bf + ((kf * NPERM + slot_perm(fs)) * NFQ) * NBP;
+    const float* gr = sg + el * GROW + kf * NFQ * NV;
+#pragma unroll
+    for (int q = 0; q < NFQ; ++q) {
+      float row[NBP];
+      load_row<float, NBP, !SM>(tb + q * NBP, row);
+#pragma unroll
+      for (int v = 0; v < NV; ++v) {
+        const float gq = sgn * gr[q * NV + v];
+#pragma unroll
+        for (int i = 0; i < NB; ++i) acc[v][i] = fmaf(row[i], gq, acc[v][i]);
+      }
+    }
+  }
+  __syncthreads();  // the staged rows are consumed; the partial sums reuse their space
+  float* pr = part + (w * 32 + lane) * PST;
+#pragma unroll
+  for (int v = 0; v < NV; ++v)
+#pragma unroll
+    for (int i = 0; i < NB; ++i) pr[v * NB + i] = acc[v][i];
+  __syncthreads();
+  const float osc = oscale ? (float)*oscale : 1.f;
+  for (int o = tid; o < ne * NVB; o += NT) {
+    const int el2 = o / NVB, r = o - el2 * NVB;
+    float s = part[el2 * PST + r];
+#pragma unroll
+    for (int ww = 1; ww < QW; ++ww) s += part[(ww * 32 + el2) * PST + r];
+    float sc = ssd[el2] * osc;
+    if (escale) sc *= escale[e0 + el2];
+    out[e0 * NVB + o] = s * sc;
+  }
+}
+
+template <int D, int P>
+cudaError_t tan_tables_p(const DGData<float>& d, cudaStream_t st) {
+  using O = Ord<D, P>;
+  // the kernel's occupancy is bound by registers and shared memory: ask for the largest carveout
+  const cudaError_t e = cudaFuncSetAttribute(elem_tan_kernel<D, P>, cudaFuncAttributePreferredSharedMemoryCarveout,
+                                             (int)cudaSharedmemCarveoutMaxShared);
+  if (e != cudaSuccess) return e;
+  return cudaMemcpyToSymbolAsync(c_tan<D, P>, d.Bv, sizeof(float) * (D + 1) * O::NQ * O::NB, 0,
+                                 cudaMemcpyDeviceToDevice, st);
+}
+
 // ------------------------------------------------------- point Jacobians (linearisation)
 // The exact Jacobian of the scheme (Eq. jac1, jac2) is assembled point by point: the
 // volume flux Jacobians dF_d/dU and the Riemann-flux Jacobians dF~/dU_L, dF~/dU_R are
@@ -636,10 +800,17 @@ cudaError_t jac_apply_p(const DGData<T>& d, LinData<T> lin, const T* u_elem, con
   if (nf > 0) face_apply_kernel<T, D, P><<<(unsigned)((nf + 255) / 256), 256, 0, st>>>(d, lin.Bface, dv, G, skip);
   if (ev) cudaEventRecord(ev[1], st);
   const int64_t eb = (d.E + O::ET - 1) / O::ET;
-  if (u_elem)
-    elem_kernel<T, D, P, true><<<(unsigned)eb, 256, 0, st>>>(d, u_elem, dv, G, out, escale, skip, oscale);
-  else
+  if (u_elem) {
+    if constexpr (std::is_same<T, float>::value && D == 3) {
+      if (d.E > 0)
+        elem_tan_kernel<D, P><<<(unsigned)((d.E + 31) / 32), 32 * (D + 1), 0, st>>>(d, u_elem, dv, G, out, escale,
+                                                                                       skip, oscale);
+    } else {
+      elem_kernel<T, D, P, true><<<(unsigned)eb, 256, 0, st>>>(d, u_elem, dv, G, out, escale, skip, oscale);
+    }
+  } else {
     elem_apply_kernel<T, D, P><<<(unsigned)eb, 256, 0, st>>>(d, lin.Avol, dv, G, out, escale, skip, oscale);
+  }
   if (ev) cudaEventRecord(ev[2], st);
   return cudaGetLastError();
 }
@@ -1229,6 +1400,10 @@ cudaError_t launch_jac_apply_d(const DGData<T>& d, LinData<T> lin, const T* u_el
                                const T* escale, const int* skip, const double* oscale, cudaStream_t st,
                                const cudaEvent_t* ev) {
   PCEXP_PSWITCH(D, (jac_apply_p<T, D, P_>(d, lin, u_elem, dv, out, G, escale, skip, oscale, st, ev)))
+}
+template <int D>
+cudaError_t launch_tan_tables_d(const DGData<float>& d, cudaStream_t st) {
+  PCEXP_PSWITCH(D, (tan_tables_p<D, P_>(d, st)))
 }
 template <class T, int D>
 cudaError_t launch_jac_adjoint_d(const DGData<T>& d, LinData<T> lin, const T* w, T* out, T* GT, const T* escale,

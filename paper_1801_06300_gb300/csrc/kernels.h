@@ -96,6 +96,8 @@ template <class T, int D>
 cudaError_t launch_jac_apply_d(const DGData<T>& d, LinData<T> lin, const T* u_elem, const T* dv, T* out, T* G,
                                const T* escale, const int* skip, const double* oscale, cudaStream_t st,
                                const cudaEvent_t* ev);
+template <int D>
+cudaError_t launch_tan_tables_d(const DGData<float>& d, cudaStream_t st);
 template <class T, int D>
 cudaError_t launch_jac_adjoint_d(const DGData<T>& d, LinData<T> lin, const T* w, T* out, T* GT, const T* escale,
                                  T osc, cudaStream_t st);
@@ -141,6 +143,12 @@ cudaError_t launch_jac_apply(const DGData<T>& d, LinData<T> lin, const T* dv, T*
                              const T* u_elem = nullptr) {
   return d.dim == 3 ? launch_jac_apply_d<T, 3>(d, lin, u_elem, dv, out, G, escale, skip, oscale, st, ev)
                     : launch_jac_apply_d<T, 2>(d, lin, u_elem, dv, out, G, escale, skip, oscale, st, ev);
+}
+// Upload the reference tables [Bv | Dv] of the context's (D, p) to the constant-memory copy
+// read by the FP32 flux-tangent J v (device-to-device, on st; same bytes for every context
+// of that order).
+inline cudaError_t launch_tan_tables(const DGData<float>& d, cudaStream_t st) {
+  return d.dim == 3 ? launch_tan_tables_d<3>(d, st) : launch_tan_tables_d<2>(d, st);
 }
 // out = (osc * diag(escale) * J(u))^T w from the point Jacobians; GT is scratch [F][nfq][2 NV].
 template <class T>

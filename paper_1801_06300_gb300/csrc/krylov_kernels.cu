@@ -235,34 +235,49 @@ __global__ void __launch_bounds__(256) cgs_kernel(const T* __restrict__ Z, int64
     if constexpr (MODE == CGS_NORM) {
       acc_dot<T, VN>(acc[0], x, x);
     } else if constexpr (MODE == CGS_PROJ) {
+      // columns in groups of 8: a group's loads are issued together (the column index
+      // clamped to the last one, so no load waits behind a branch) before its FMAs
+      constexpr int G = NC < 8 ? NC : 8;
 #pragma unroll
-      for (int c = 0; c < NC; ++c) {
-        if (c < nc) {
-          T z[VN];
-          load_vec<T, VN>(Z + c * ldz + r, z);
-          acc_dot<T, VN>(acc[c], z, x);
+      for (int c0 = 0; c0 < NC; c0 += G) {
+        if (c0 < nc) {
+          T z[G][VN];
+#pragma unroll
+          for (int g = 0; g < G; ++g) load_vec<T, VN>(Z + (int64_t)(c0 + g < nc ? c0 + g : nc - 1) * ldz + r, z[g]);
+#pragma unroll
+          for (int g = 0; g < G; ++g)
+            if (c0 + g < nc) acc_dot<T, VN>(acc[c0 + g], z[g], x);
         }
       }
       acc_dot<T, VN>(acc[NC], x, x);
     } else {
-      // update pass; the projection pass below re-reads the same 16-byte chunks (L1)
+      // update pass in the same column groups; the projection pass of UPD_PROJ below
+      // re-reads each group's chunks (cache hits)
+      constexpr int G = NC < 8 ? NC : 8;
 #pragma unroll
-      for (int c = 0; c < NC; ++c) {
-        if (c < nc) {
-          T z[VN];
-          load_vec<T, VN>(Z + c * ldz + r, z);
+      for (int c0 = 0; c0 < NC; c0 += G) {
+        if (c0 < nc) {
+          T z[G][VN];
 #pragma unroll
-          for (int v = 0; v < VN; ++v) x[v] = fma(-scoef[c], z[v], x[v]);
+          for (int g = 0; g < G; ++g) load_vec<T, VN>(Z + (int64_t)(c0 + g < nc ? c0 + g : nc - 1) * ldz + r, z[g]);
+#pragma unroll
+          for (int g = 0; g < G; ++g)
+            if (c0 + g < nc)
+#pragma unroll
+              for (int v = 0; v < VN; ++v) x[v] = fma(-scoef[c0 + g], z[g][v], x[v]);
         }
       }
       if constexpr (MODE == CGS_UPD_PROJ) {
         store_vec<T, VN>(w + r, x);
 #pragma unroll
-        for (int c = 0; c < NC; ++c) {
-          if (c < nc) {
-            T z[VN];
-            load_vec<T, VN>(Z + c * ldz + r, z);
-            acc_dot<T, VN>(acc[c], z, x);
+        for (int c0 = 0; c0 < NC; c0 += G) {
+          if (c0 < nc) {
+            T z[G][VN];
+#pragma unroll
+            for (int g = 0; g < G; ++g) load_vec<T, VN>(Z + (int64_t)(c0 + g < nc ? c0 + g : nc - 1) * ldz + r, z[g]);
+#pragma unroll
+            for (int g = 0; g < G; ++g)
+              if (c0 + g < nc) acc_dot<T, VN>(acc[c0 + g], z[g], x);
           }
         }
       } else {

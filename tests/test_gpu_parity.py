@@ -286,6 +286,33 @@ def test_fp32_mixed_steps_vortex_error_stated(capi):
     ctx.close()
 
 
+FP32_JV_MESHES = {
+    "periodic": MESHES["periodic"],
+    "bump": MESHES["bump"],
+    "ragged50": lambda: (W.periodic_square(5, 10.0, 0.15, 22), W.Freestream(0.5, 30.0)),
+    "tiny18": lambda: (W.periodic_square(3, 10.0, 0.15, 23), W.Freestream(0.5, 30.0)),
+}
+
+
+@pytest.mark.parametrize("kind", list(FP32_JV_MESHES))
+@pytest.mark.parametrize("p", [0, 1, 2, 3])
+def test_fp32_krylov_jvp_matches_oracle(capi, kind, p):
+    """The J v inside the FP32-mixed Krylov process (face point Jacobians, volume flux
+    tangents at u recomputed per element) against the oracle's J v, on element counts that
+    fill whole 32-element blocks (288, 192), leave a ragged block (50) or one partial block
+    (18).  With m = 1 the Arnoldi relation gives J v_0 = h_00 v_0 + h_10 v_1."""
+    mesh, free = FP32_JV_MESHES[kind]()
+    dg = oracle_dg(mesh, p, free)
+    ctx = capi.Context(mesh, p, free, capi.PCEXP_FP32_MIXED, m_max=2)
+    u = perturbed_state(dg, 300 + p)
+    b = W.random_coeffs(301 + p, (dg.K,))
+    V, H, k, beta = ctx.arnoldi(u, b, 1)
+    assert k == 1
+    Jv = H[0, 0] * V[0] + H[1, 0] * V[1]
+    assert rel(Jv, dg.jvp(u, V[0])) <= 2e-5
+    ctx.close()
+
+
 def test_fp32_mixed_krylov_no_overflow_and_one_step(capi):
     """FP32-mixed Arnoldi at m = 30 on an operator with ||D J|| ~ 1e2 (stored Krylov
     vectors must not grow like ||J||^j), and one local-step PCEXP iteration against the
