@@ -4,5 +4,4 @@
 namespace pcexp {
 PCEXP_INST_D(double, 2)
 PCEXP_INST_D(float, 2)
-template cudaError_t launch_tan_tables_d<2>(const DGData<float>&, cudaStream_t);
 }  // namespace pcexp

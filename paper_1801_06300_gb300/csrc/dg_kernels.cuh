@@ -364,9 +364,12 @@ template <int D, int P> __constant__ float c_tan[(D + 1) * Ord<D, P>::NQ * Ord<D
 // memory with strides that keep the per-lane reads free of bank conflicts.  Each warp keeps
 // all nv x nb sums of its element in registers; the D+1 partial sums meet in shared memory
 // and are added in warp order (deterministic), and the outputs leave as contiguous rows.
-// Same sums as elem_kernel<float, D, P, true>, in another order.
+// Same sums as elem_kernel<float, D, P, true>, in another order.  Four blocks per SM: the
+// launch bounds hold the registers at 128 and the shared-memory carveout is set to its
+// maximum (tan_tables_p).  Used on tetrahedra; on triangles (6 x 4 sums per element,
+// 24,576 elements at 192 x 64) the tile kernel measured faster.
 template <int D, int P>
-__global__ void __launch_bounds__(32 * (D + 1), D == 3 ? 4 : 1) elem_tan_kernel(DGData<float> d, const float* __restrict__ u,
+__global__ void __launch_bounds__(32 * (D + 1), 4) elem_tan_kernel(DGData<float> d, const float* __restrict__ u,
                                                                 const float* __restrict__ du,
                                                                 const float* __restrict__ G, float* __restrict__ out,
                                                                 const float* __restrict__ escale,

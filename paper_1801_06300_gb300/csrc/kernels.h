@@ -145,10 +145,11 @@ cudaError_t launch_jac_apply(const DGData<T>& d, LinData<T> lin, const T* dv, T*
                     : launch_jac_apply_d<T, 2>(d, lin, u_elem, dv, out, G, escale, skip, oscale, st, ev);
 }
 // Upload the reference tables [Bv | Dv] of the context's (D, p) to the constant-memory copy
-// read by the FP32 flux-tangent J v (device-to-device, on st; same bytes for every context
-// of that order).
+// read by the FP32 flux-tangent J v on tetrahedra (device-to-device, on st; same bytes for
+// every context of that order).  Triangles use the tile kernel, which reads the tables from
+// global memory.
 inline cudaError_t launch_tan_tables(const DGData<float>& d, cudaStream_t st) {
-  return d.dim == 3 ? launch_tan_tables_d<3>(d, st) : launch_tan_tables_d<2>(d, st);
+  return d.dim == 3 ? launch_tan_tables_d<3>(d, st) : cudaSuccess;
 }
 // out = (osc * diag(escale) * J(u))^T w from the point Jacobians; GT is scratch [F][nfq][2 NV].
 template <class T>
