@@ -211,8 +211,11 @@ PCEXP_DEV Acc<T> warp_reduce_columns(Acc<T> (&a)[NC], int lane) {
   return a[0];
 }
 
+// Row Gram-Schmidt pass (NORM, PROJ, UPD_PROJ, UPD_NORM): every thread owns whole 16-byte
+// chunks of rows and accumulates all columns for them; the launch bounds hold it at 128
+// registers so that two blocks share an SM.
 template <class T, int NC, int MODE>
-__global__ void __launch_bounds__(256) cgs_kernel(const T* __restrict__ Z, int64_t ldz, int64_t Kp, int j,
+__global__ void __launch_bounds__(256, 2) cgs_kernel(const T* __restrict__ Z, int64_t ldz, int64_t Kp, int j,
                                                   T* __restrict__ w, T* __restrict__ out, KState* ks,
                                                   double* __restrict__ partials, double eta) {
   constexpr int VN = VecN<T>::N;
@@ -252,7 +255,7 @@ __global__ void __launch_bounds__(256) cgs_kernel(const T* __restrict__ Z, int64
       acc_dot<T, VN>(acc[NC], x, x);
     } else {
       // update pass in the same column groups; the projection pass of UPD_PROJ below
-      // re-reads each group's chunks (cache hits)
+      // re-reads each group's chunks
       constexpr int G = NC < 8 ? NC : 8;
 #pragma unroll
       for (int c0 = 0; c0 < NC; c0 += G) {
@@ -269,6 +272,9 @@ __global__ void __launch_bounds__(256) cgs_kernel(const T* __restrict__ Z, int64
       }
       if constexpr (MODE == CGS_UPD_PROJ) {
         store_vec<T, VN>(w + r, x);
+        // reload the chunks rather than keep all of them live across the store (255 -> 128
+        // registers, two blocks per SM instead of one; the reloads hit L1/L2)
+        asm volatile("" ::: "memory");
 #pragma unroll
         for (int c0 = 0; c0 < NC; c0 += G) {
           if (c0 < nc) {
