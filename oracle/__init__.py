@@ -13,7 +13,9 @@ holds no method arithmetic.
 Pinned by the ``-m "not gpu"`` tests against closed forms, library routines
 and printed values (Table 1 "timesize", Eq. grow / exp1_grow / rkgrow,
 phi_1(z) = (e^z - 1)/z, dense expm, free-stream preservation, conservation,
-complex-step derivatives and the Appendix flux Jacobian).  Parity unpinned:
-the steady bump-channel march beyond agreement with itself (no printed
-number exists for it).
+complex-step derivatives, the Appendix flux Jacobian, the inscribed-circle and
+inscribed-sphere diameters behind the element time step of Eq. x3d, and the
+exact decay of a linear system under the steady march of Eq. cfl).  Parity
+unpinned: the nonlinear bump-channel steady march beyond agreement with
+itself (no printed number exists for it).
 """
