@@ -217,6 +217,23 @@ def roofline_entry(prof, precision_bytes, K, E, F, hbm, peak_kind, dim=2, p=2, m
     return entry
 
 
+def max_over_ranks(x, dist, device="cuda"):
+    """The largest of the ranks' values of x (the slowest rank sets the job's time); x itself
+    without a process group.  The tensor lives on `device` (cuda for NCCL, cpu for gloo)."""
+    if dist is None:
+        return float(x)
+    import torch
+    t = torch.tensor([float(x)], device=device, dtype=torch.float64)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def job_throughput(units_per_rank_step, steps, world, seconds):
+    """Whole-job DOF * steps / s: every rank advances its own replica by `steps` steps of
+    `units_per_rank_step` unknowns; `seconds` is the max over ranks."""
+    return units_per_rank_step * steps * world / seconds
+
+
 def kernel_table(prof, precision_bytes, K, E, F, hbm, dim=2, p=2, m=30):
     """Every kernel class with a byte model: launches, mean launch time (CUDA events per
     class over the profiled steps), algorithmic GB/s and its fraction of measured HBM; FP64
@@ -279,7 +296,7 @@ def main():
 
     if args.only_3d:
         hbm, peak_kind = load_peaks()
-        v3d = vortex3d_block(args, capi, W, torch, np, local, hbm, peak_kind)
+        v3d = vortex3d_block(args, capi, W, torch, np, local, hbm, peak_kind, dist, world)
         if rank == 0:
             print(json.dumps({"vortex3d": v3d}))
         return
@@ -327,12 +344,8 @@ def main():
     main_prec = capi.PCEXP_FP64 if args.precision == "fp64" else capi.PCEXP_FP32_MIXED
     ctx64, ms64, ms64_prof, prof, clocks, state64 = run(main_prec)
     K = ctx64.K
-    ms_max = ms64
-    if dist:
-        t = torch.tensor([ms64], device="cuda", dtype=torch.float64)
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        ms_max = float(t.item())
-    value = K * args.steps * world / (ms_max / 1e3)
+    ms_max = max_over_ranks(ms64, dist)
+    value = job_throughput(K, args.steps, world, ms_max / 1e3)
 
     # end to end through the public API with host buffers (pinned), copies inside the timed region
     hin = torch.empty(K, dtype=torch.float64, pin_memory=True).numpy()
@@ -348,12 +361,8 @@ def main():
         ctx64.get_state(hout)
         hin, hout = hout, hin
     torch.cuda.synchronize()
-    e2e_s = time.perf_counter() - t0
-    if dist:
-        t = torch.tensor([e2e_s], device="cuda", dtype=torch.float64)
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        e2e_s = float(t.item())
-    e2e_value = K * args.steps * world / e2e_s
+    e2e_s = max_over_ranks(time.perf_counter() - t0, dist)
+    e2e_value = job_throughput(K, args.steps, world, e2e_s)
 
     # FP32-mixed form on the same workload.  Accuracy: one step from the same state in
     # both forms (the steady march at CFL 100 amplifies any 1e-7 difference to 1e-2
@@ -368,8 +377,9 @@ def main():
         ctx32.set_state(s0)
         ctx32.step(capi.PCEXP_SCHEME_PCEXP, capi.PCEXP_DT_LOCAL_CFL, CFL, M, info=False)
         b = ctx32.get_state()
-        mixed = {"value": K * args.steps * world / (ms32 / 1e3), "ms_per_step": ms32 / args.steps,
-                 "speedup_vs_fp64": ms64 / ms32,
+        ms32 = max_over_ranks(ms32, dist)
+        mixed = {"value": job_throughput(K, args.steps, world, ms32 / 1e3), "ms_per_step": ms32 / args.steps,
+                 "speedup_vs_fp64": ms_max / ms32,
                  "one_step_state_rel_l2_vs_fp64": float(np.linalg.norm(b - a) / np.linalg.norm(a)),
                  "one_step_increment_rel_l2_vs_fp64": float(np.linalg.norm((b - s0) - (a - s0)) / np.linalg.norm(a - s0)),
                  "kernel_ms_per_step": {k: round(v[1] / args.steps, 4) for k, v in prof32.items() if v[0]}}
@@ -391,7 +401,7 @@ def main():
     # the 3D vortex (48^3 cubes as 663,552 Kuhn tetrahedra, P2, K = 33,177,600), both forms
     v3d = None
     if not args.no_3d:
-        v3d = vortex3d_block(args, capi, W, torch, np, local, hbm, peak_kind)
+        v3d = vortex3d_block(args, capi, W, torch, np, local, hbm, peak_kind, dist, world)
 
     cpu = None
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
@@ -430,7 +440,7 @@ def main():
         dist.destroy_process_group()
 
 
-def vortex3d_block(args, capi, W, torch, np, local, hbm, peak_kind):
+def vortex3d_block(args, capi, W, torch, np, local, hbm, peak_kind, dist=None, world=1):
     """Throughput of PCEXP steps on the 3D vortex (global CFL 10, m = 30) in both forms from
     the projected vortex, with CUDA events per step after warm-up (inputs far larger than
     L2), the dominant kernel's roofline and the FP32-mixed state error against FP64 after
@@ -460,7 +470,8 @@ def vortex3d_block(args, capi, W, torch, np, local, hbm, peak_kind):
         K, E = ctx.K, case.mesh.n_elem
         F = 2 * E  # periodic: every face interior
         states[name] = ctx.get_state()
-        res[name] = {"value": K * steps / (ms / 1e3), "ms_per_step": ms / steps,
+        ms = max_over_ranks(ms, dist)
+        res[name] = {"value": job_throughput(K, steps, world, ms / 1e3), "ms_per_step": ms / steps,
                      "kernel_ms_per_step": {k: round(v[1], 3) for k, v in prof.items() if v[0]},
                      "roofline": roofline_entry(prof, 8 if name == "fp64" else 4, K, E, F, hbm, peak_kind,
                                                 3, case.p, case.m, "vortex3d"),
