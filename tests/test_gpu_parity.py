@@ -344,6 +344,37 @@ def test_fp32_mixed_krylov_no_overflow_and_one_step(capi):
     ctx.close()
 
 
+def test_invalid_arguments_are_rejected(capi):
+    """Degenerate inputs end in PCEXP_ERR_INVALID_ARG before any kernel runs: an empty mesh,
+    a Krylov capacity of 0 or above PCEXP_MAX_KRYLOV, an order above 3, and Krylov
+    dimensions or steps outside 1..m_max."""
+    mesh, free = MESHES["periodic"]()
+    empty = W.Mesh(dim=2, coords=mesh.coords, elems=np.zeros((0, 3), np.int32), vert_master=mesh.vert_master,
+                   bfaces=np.zeros((0, 2), np.int32), btags=np.zeros(0, np.int32), name="empty")
+    bad = [(empty, 1, 4), (mesh, 1, 0), (mesh, 1, capi.PCEXP_MAX_KRYLOV + 1), (mesh, 4, 4)]
+    for msh, p, m_max in bad:
+        with pytest.raises(capi.PcexpError) as ei:
+            capi.Context(msh, p, free, capi.PCEXP_FP64, m_max=m_max)
+        assert ei.value.code == capi.PCEXP_ERR_INVALID_ARG
+    dg = oracle_dg(mesh, 1, free)
+    ctx = capi.Context(mesh, 1, free, capi.PCEXP_FP64, m_max=4)
+    u = perturbed_state(dg, 3)
+    ctx.set_state(u)
+    s0 = ctx.get_state()  # after the basis round trip
+    for m in (0, 5):
+        with pytest.raises(capi.PcexpError) as ei:
+            ctx.arnoldi(u, dg.residual(u), m)
+        assert ei.value.code == capi.PCEXP_ERR_INVALID_ARG
+        with pytest.raises(capi.PcexpError) as ei:
+            ctx.step(capi.PCEXP_SCHEME_PCEXP, capi.PCEXP_DT_GLOBAL_CFL, 1.0, m)
+        assert ei.value.code == capi.PCEXP_ERR_INVALID_ARG
+    with pytest.raises(capi.PcexpError) as ei:
+        ctx.step(capi.PCEXP_SCHEME_PCEXP, capi.PCEXP_DT_GLOBAL_CFL, -1.0, 4)
+    assert ei.value.code == capi.PCEXP_ERR_INVALID_ARG
+    assert np.array_equal(ctx.get_state(), s0)  # rejected calls leave the state untouched
+    ctx.close()
+
+
 def test_torch_device_pointers(capi):
     torch = pytest.importorskip("torch")
     mesh, free = MESHES["periodic"]()
