@@ -244,9 +244,14 @@ int pcexp_functional_params(pcexp_ctx* ctx, int kind, const double* params, int 
  * by the far-field boundary condition; the mesh and state are kept. */
 int pcexp_set_physics(pcexp_ctx* ctx, const pcexp_physics* phys);
 
-/* Diagnostics of the master state: kind 0 = density residual norm of Eq. cfl
- * (domain volume taken from the mesh), kind 1 = entropy error of
- * Eq. entropy_error. */
+/* Diagnostics of the master state (Sec. 5):
+ *  - kind 0: density residual norm of Eq. cfl, (1/|Omega|) ||R(rho)||, |Omega| = sum_e |E|;
+ *  - kind 1: entropy error of Eq. entropy_error (Sec. 5.1),
+ *    sqrt((1/|Omega|) int (s/s0)^2 dx - 1) with s = p / rho^gamma and s0 = p_inf / rho_inf^gamma,
+ *    integrated by the volume rule in FP64 on the FP64 master state (either precision form);
+ *    a negative radicand (rounding of a free stream) gives 0.
+ * Synchronises the stream.  Errors: INVALID_ARG (kind), NONFINITE, CUDA, OOM (the first
+ * kind-1 call allocates the FP64 volume tables, nq (nb + 1) + n_elem doubles). */
 int pcexp_output(pcexp_ctx* ctx, int kind, double* value);
 
 /* ---- kernel-class timing (diagnostic) ----
@@ -271,21 +276,23 @@ int pcexp_output(pcexp_ctx* ctx, int kind, double* value);
 int pcexp_profile_enable(pcexp_ctx* ctx, int enable);
 int pcexp_profile_read(pcexp_ctx* ctx, int kernel_class, int64_t* launches, double* ms);
 
-/* R(U) exactly as pcexp_residual computes it, for callers that cannot allocate
- * device memory when they need it (inside CUDA stream capture, under a fixed
- * memory budget or a custom allocator, in loops that forbid allocator calls
- * after set-up).  The paper has no counterpart; this is an interface variant.
- * U and R are device pointers to K doubles in the library's INTERNAL basis
- * (whatever basis_io the context uses); the context must be FP64.  The call
- * only enqueues the two DG kernels on the context's stream and returns; it
- * calls no cudaMalloc/cudaFree or other allocating routine.  Its face-flux
- * scratch is a fixed 8 MiB device array inside the library (held by every GPU
- * that loads the library until the process exits): meshes needing more than
- * 2^20 doubles (faces x (p+1) x 4) get PCEXP_ERR_INVALID_ARG.  The array's
- * device address is looked up on the first call on each device, so make that
- * first call before any stream capture.  All calls share the array: calls
- * whose kernels overlap on the GPU race; calls on one stream are ordered.
- * Errors: INVALID_ARG, UNSUPPORTED (FP32-mixed context), CUDA. */
+/* R(U) exactly as pcexp_residual computes it, for callers that cannot allocate device
+ * memory when they need R(U): hosts whose own pool or caching allocator owns all device
+ * memory, hosts with a fixed memory budget reserved at start-up, and real-time loops that
+ * may not call cudaMalloc/cudaFree (which can synchronise the device) after set-up.  The
+ * paper has no counterpart; this is an interface variant.
+ * U and R are device pointers to K doubles in the library's INTERNAL basis (whatever
+ * basis_io the context uses); the context must be FP64.  The call only enqueues the two DG
+ * kernels on the context's stream and returns; it calls no cudaMalloc/cudaFree or other
+ * allocating routine.  Its face-flux scratch is a fixed 8 MiB device array inside the
+ * library (held by every GPU that loads the library until the process exits): meshes with
+ * faces x face quadrature points x (dim + 2) > 2^20 doubles get PCEXP_ERR_INVALID_ARG
+ * (face points: p + 1 on edges, (p + 1)^2 on triangular faces).  The first call on a
+ * device makes that device current and looks up the array's device address; make that
+ * first call before any stream capture.  All calls share the array, which keeps the last
+ * call's face fluxes: calls whose kernels overlap on the GPU race; calls on one stream are
+ * ordered.  Errors (with pcexp_last_error text): INVALID_ARG, UNSUPPORTED (FP32-mixed
+ * context), CUDA. */
 int pcexp_residual_noalloc(pcexp_ctx* ctx, const double* U, double* R);
 
 /* Waits for all work queued on the context's stream. */

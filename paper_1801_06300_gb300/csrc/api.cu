@@ -43,6 +43,7 @@ struct pcexp_ctx {
   bool jv_tangent = false;                 // volume part of J v by flux tangents (FP32-mixed)
   void* GT = nullptr;                      // adjoint face scratch [F][nfq][2 nv]
   double* xq = nullptr;                    // physical volume points [E][nq][dim] (first vortex functional)
+  double* diag = nullptr;                  // FP64 [Bv (nq nb) | Wv (nq) | sqrt|det A| (E)] (first entropy output)
   // reverse-step work space (FP64 contexts, allocated by the first backward call)
   double *b_un = nullptr, *b_us = nullptr, *b_dl = nullptr, *b_V1 = nullptr, *b_Vb = nullptr;
   double *b_w1 = nullptr, *b_w0 = nullptr, *b_wb2 = nullptr, *b_wb1 = nullptr, *b_wb0 = nullptr;
@@ -896,6 +897,9 @@ int phi_adjoint_abi(pcexp_ctx* c, const double* H, int k, int ldh, double dt, co
 }  // namespace
 
 namespace pcexp {
+// Sets the calling thread's pcexp_last_error() text (for entry points outside this file).
+void set_last_error(const char* msg) { g_last_error = msg ? msg : ""; }
+
 // Read-only view of a context for pcexp_residual_noalloc (noalloc.cu); makes the
 // context's device current.
 int ctx_noalloc_view(pcexp_ctx* c, DGData<double>* d, cudaStream_t* st, int* nfq, int* fp32, int* device) {
@@ -1198,7 +1202,36 @@ int pcexp_march_steady(pcexp_ctx* c, int scheme, double cfl_max, double decades,
 int pcexp_output(pcexp_ctx* c, int kind, double* value) {
   PCEXP_TRY(check_ctx(c));
   if (!value) return PCEXP_ERR_INVALID_ARG;
-  if (kind != 0) return PCEXP_ERR_UNSUPPORTED;
+  if (kind != 0 && kind != 1) return PCEXP_ERR_INVALID_ARG;
+  if (kind == 1) {
+    // entropy error of Eq. entropy_error on the FP64 master state with FP64 tables (an FP32
+    // evaluation would lose the small radicand of a near-isentropic flow to rounding)
+    const Setup& s = c->host;
+    const int GEO = c->dim == 2 ? 8 : 12;
+    if (!c->diag) {
+      std::vector<double> t(s.Bv);
+      t.insert(t.end(), s.Wv.begin(), s.Wv.end());
+      for (int64_t e = 0; e < c->E; ++e) t.push_back(s.geo[GEO * e + c->dim * c->dim]);
+      PCEXP_TRY(dalloc(c, &c->diag, t.size()));
+      PCEXP_CK(cudaMemcpyAsync(c->diag, t.data(), t.size() * sizeof(double), cudaMemcpyHostToDevice, c->st));
+    }
+    const double g = c->phys.gamma;
+    const double s0 = c->phys.p_inf / std::pow(c->phys.rho_inf, g);
+    const double* Bv = c->diag;
+    const double* Wv = Bv + (size_t)c->nq * c->nb;
+    const double* sd = Wv + c->nq;
+    PCEXP_CK(launch_entropy_sum(c->U64[c->cur], Bv, Wv, sd, c->E, c->nb, c->nq, c->nv, g, s0,
+                                &c->ss->dtmin_scratch, c->partials, &c->ss->counter, c->st));
+    double sum = 0;
+    PCEXP_CK(cudaMemcpyAsync(&sum, &c->ss->dtmin_scratch, sizeof(double), cudaMemcpyDeviceToHost, c->st));
+    PCEXP_CK(cudaStreamSynchronize(c->st));
+    if (!std::isfinite(sum)) {
+      g_last_error = "non-finite entropy integral";
+      return PCEXP_ERR_NONFINITE;
+    }
+    *value = std::sqrt(std::max(sum / c->volume - 1.0, 0.0));
+    return PCEXP_OK;
+  }
   if (c->fp32) {
     float* V = reinterpret_cast<float*>(c->V);
     PCEXP_CK(launch_dg_operator<float>(dgdata<float>(c), shadow<float>(c, c->cur), nullptr, V, reinterpret_cast<float*>(c->G),

@@ -119,6 +119,64 @@ cudaError_t launch_density_norm(const T* R, const T* s, int64_t E, int nb, int n
   return cudaGetLastError();
 }
 
+// Entropy error of Eq. entropy_error (Sec. 5.1) on the FP64 master state, before the
+// final square root: sum_e sum_q w^_q |det A_e| (s / s0)^2 with s = p / rho^gamma at the
+// volume points, U(x_q) = |det A_e|^-1/2 sum_j phi^_j(xi_q) u_j.  sd[e] = sqrt|det A_e| in
+// FP64; Bv [nq][nb] and Wv [nq] the FP64 reference tables.  Fixed-order last-block sum.
+__global__ void __launch_bounds__(256) entropy_sum_kernel(const double* __restrict__ u, const double* __restrict__ Bv,
+                                                          const double* __restrict__ Wv, const double* __restrict__ sd,
+                                                          int64_t E, int nb, int nq, int nv, double gamma,
+                                                          double s0, double* __restrict__ value,
+                                                          double* __restrict__ partials, unsigned* counter) {
+  __shared__ double red[8];
+  __shared__ bool last;
+  double acc = 0;
+  for (int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; e < E; e += (int64_t)gridDim.x * blockDim.x) {
+    const double s = sd[e], is = 1.0 / s;
+    const double* ue = u + e * nv * nb;
+    for (int q = 0; q < nq; ++q) {
+      double U[5];
+      for (int v = 0; v < nv; ++v) {
+        double a = 0;
+        for (int j = 0; j < nb; ++j) a += Bv[q * nb + j] * ue[v * nb + j];
+        U[v] = a * is;
+      }
+      double m2 = 0;
+      for (int k = 1; k < nv - 1; ++k) m2 += U[k] * U[k];
+      const double p = (gamma - 1.0) * (U[nv - 1] - 0.5 * m2 / U[0]);
+      const double r = p / pow(U[0], gamma) / s0;
+      acc += Wv[q] * s * s * r * r;
+    }
+  }
+  for (int o = 16; o > 0; o >>= 1) acc += __shfl_xor_sync(0xffffffffu, acc, o);
+  if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = acc;
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    double b = 0;
+    for (int w = 0; w < (int)(blockDim.x >> 5); ++w) b += red[w];
+    partials[blockIdx.x] = b;
+    __threadfence();
+    last = atomicAdd(counter, 1u) == gridDim.x - 1;
+  }
+  __syncthreads();
+  if (last && threadIdx.x == 0) {
+    double b = 0;
+    for (unsigned i = 0; i < gridDim.x; ++i) b += __ldcg(partials + i);
+    *value = b;
+    *counter = 0;
+  }
+}
+
+cudaError_t launch_entropy_sum(const double* u, const double* Bv, const double* Wv, const double* sd, int64_t E, int nb,
+                               int nq, int nv, double gamma, double s0, double* value, double* partials,
+                               unsigned* counter, cudaStream_t st) {
+  int64_t b = (E + 255) / 256;
+  if (b > RED_BLOCKS) b = RED_BLOCKS;
+  entropy_sum_kernel<<<(unsigned)(b < 1 ? 1 : b), 256, 0, st>>>(u, Bv, Wv, sd, E, nb, nq, nv, gamma, s0, value,
+                                                                partials, counter);
+  return cudaGetLastError();
+}
+
 __global__ void scale_by_inverse_kernel(double* __restrict__ x, const double* __restrict__ s, int64_t n) {
   const double f = 1.0 / *s;
   for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x)

@@ -199,6 +199,10 @@ template <class T>
 cudaError_t launch_scale_elements(T* x, const T* s, int64_t E, int nvb, cudaStream_t st);
 // x *= s (s a device scalar, n entries)
 cudaError_t launch_scale_by_inverse(double* x, const double* s, int64_t n, cudaStream_t st);
+// sum_e sum_q w^_q |det A_e| (s/s0)^2 of the FP64 state u (Eq. entropy_error) -> *value
+cudaError_t launch_entropy_sum(const double* u, const double* Bv, const double* Wv, const double* sd, int64_t E, int nb,
+                               int nq, int nv, double gamma, double s0, double* value, double* partials,
+                               unsigned* counter, cudaStream_t st);
 // density residual norm sqrt(sum (R[e][0][i] / s[e])^2) / volume -> ss->res_norm, then the CFL ramp
 template <class T>
 cudaError_t launch_density_norm(const T* R, const T* s, int64_t E, int nb, int nv, double volume,
