@@ -61,6 +61,8 @@ extern "C" {
 
 #define PCEXP_SCHEME_PCEXP 0 /* Eq. s9 + s10 */
 #define PCEXP_SCHEME_EXP1 1  /* Eq. s9 alone (first stage) */
+#define PCEXP_SCHEME_ETD2 2  /* Eq. s7: ETD1 + dt (dt/dt_{n-1}) phi_2(dt J_n)(N_n - N_{n-1}), history in
+                                the context; the first step after a state change is ETD1 (Eq. s8) */
 
 #define PCEXP_DT_GIVEN 0      /* global dt passed by the caller */
 #define PCEXP_DT_GLOBAL_CFL 1 /* dt = min_e dt_e(CFL), Eq. x3d */
@@ -68,8 +70,9 @@ extern "C" {
                                  unit pseudo-step (reading for steady runs) */
 
 #define PCEXP_PROJ_FREESTREAM 0 /* params: none */
-#define PCEXP_PROJ_VORTEX 1     /* params: eps, xc, yc, period (0 = none); in 3D the planar
-                                   vortex, uniform in z, zero z-velocity */
+#define PCEXP_PROJ_VORTEX 1     /* params: eps, xc, yc, period (0 = none) [, core radius R (default
+                                   1; distances in units of R)]; in 3D the planar vortex, uniform
+                                   in z, zero z-velocity */
 #define PCEXP_PROJ_BLOBS 2      /* params: radius, then n x (x, y, a_rho, a_p) */
 
 #define PCEXP_MAX_KRYLOV 32 /* largest supported m (the paper uses m = 30) */
@@ -111,6 +114,11 @@ typedef struct pcexp_options {
   double breakdown_eta; /* happy breakdown when h_{j+1,j} <= eta ||J v_j||; <=0: default
                            (1e-12 FP64, 1e-6 FP32-mixed) */
   int32_t basis_io;     /* PCEXP_BASIS_PAPER | PCEXP_BASIS_INTERNAL */
+  double krylov_tol;    /* Krylov tolerance (Sec. 5 uses 1e-5); <= 0: fixed dimension m.  > 0: in
+                           every step stage the Arnoldi process ends at the first k = 5, 10, ...
+                           (k < m) whose relative error estimate (below) is <= krylov_tol, and the
+                           steady march caps its CFL from the first stage's estimate:
+                           cap = CFL_used * clamp(0.8 (tol / est)^(1/2), 1/4, 2) */
 } pcexp_options;
 
 typedef struct pcexp_step_info {
@@ -118,6 +126,9 @@ typedef struct pcexp_step_info {
   double beta[2];        /* ||R_n|| and ||N_* - N_n|| */
   double dt;             /* dt used (1 for local pseudo-steps) */
   double res_norm;       /* density residual norm of Eq. cfl at u_n */
+  double krylov_err[2];  /* relative a-posteriori error estimate of each stage's phi product
+                            (Saad 1992, cited in Sec. 2.2): dt h_{k+1,k} |e_k^T phi_2(dt H_k) e_1|
+                            / ||phi_1(dt H_k) e_1|| at the dimension k used */
 } pcexp_step_info;
 
 typedef struct pcexp_steady_info {
@@ -206,10 +217,15 @@ int pcexp_phi_adjoint(pcexp_ctx* ctx, const double* H, int k, int ldh, double dt
 int pcexp_step_backward(pcexp_ctx* ctx, const double* U, double dt, int m,
                         const double* ubar_next, double* ubar, int on_device);
 
-/* One PCEXP (Eq. s9, s10) or EXP1 (Eq. s9) step on the master state with
- * Krylov dimension m (<= m_max).  dt_mode PCEXP_DT_*: dt_or_cfl is dt for
+/* One PCEXP (Eq. s9, s10), EXP1 (Eq. s9) or ETD2 (Eq. s7) step on the master state
+ * with Krylov dimension m (<= m_max).  dt_mode PCEXP_DT_*: dt_or_cfl is dt for
  * PCEXP_DT_GIVEN, else the CFL number.  info may be NULL; when given, the
- * call synchronises the stream to fill it. */
+ * call synchronises the stream to fill it.
+ * ETD2 keeps u_n, R(u_n) and dt of its last step in the context (the first ETD2 step
+ * allocates 3 state vectors for them) and forms N_n - N_{n-1} = R_n - R_{n-1} -
+ * J_n (u_n - u_{n-1}) with one J v; its second Krylov stage takes phi_2.  Setting or
+ * projecting the state, another scheme or a steady march clears the history, and the next
+ * ETD2 step is then ETD1 (krylov_dim[1] = 0).  ETD2 with PCEXP_DT_LOCAL_CFL is INVALID_ARG. */
 int pcexp_step(pcexp_ctx* ctx, int scheme, int dt_mode, double dt_or_cfl, int m,
                pcexp_step_info* info);
 
@@ -294,6 +310,13 @@ int pcexp_profile_read(pcexp_ctx* ctx, int kernel_class, int64_t* launches, doub
  * ordered.  Errors (with pcexp_last_error text): INVALID_ARG, UNSUPPORTED (FP32-mixed
  * context), CUDA. */
 int pcexp_residual_noalloc(pcexp_ctx* ctx, const double* U, double* R);
+
+/* Measurement aid (the paper has no counterpart): the FP64 fused multiply-add rate of
+ * the current device in TFLOP/s, from independent DFMA chains on every SM timed with CUDA
+ * events (best of three launches after a warm-up; a few milliseconds).  It is the roof of
+ * the FP64 form's compute-bound kernels.  Allocates and frees one small device buffer and
+ * a private stream.  Errors: INVALID_ARG, CUDA. */
+int pcexp_fp64_fma_rate(double* tflops);
 
 /* Waits for all work queued on the context's stream. */
 int pcexp_synchronize(pcexp_ctx* ctx);

@@ -6,7 +6,10 @@ vortex, not the paper's beta = 0.2, R = 0.05 form of Sec. 5.1):
   dv = eps / (2 pi) exp((1 - r^2) / 2) (-(y - y_c), x - x_c),
   T = T_inf - (gamma - 1) eps^2 / (8 gamma pi^2) exp(1 - r^2),
   rho = rho_inf (T / T_inf)^(1 / (gamma - 1)), p = rho T  (isentropic).
-On a periodic domain the distance uses the nearest periodic image.  The
+On a periodic domain the distance uses the nearest periodic image.  A core radius R
+measures (x - x_c, y - y_c) in units of R (the paper's vortex of Sec. 5.1, with the
+temperature perturbation read as -(beta U_inf)^2 / (2 C_p) exp(-r^2), is this vortex with
+R = 0.05 and eps = 2 pi beta U_inf exp(-1/2)).  The
 exact solution is this field translated with the mean velocity.  In 3D the same
 field lies in the x-y plane, uniform in z, with zero z-velocity (the vortex axis
 is along z); states then have 5 components (rho, rho u, rho v, rho w, rho E).
@@ -36,6 +39,8 @@ def vortex_state(x, free, vortex, t: float = 0.0, period=None):
     if period is not None:
         dx = dx - period * np.round(dx / period)
         dy = dy - period * np.round(dy / period)
+    rad = getattr(vortex, "radius", 1.0)  # core radius: distances in its units
+    dx, dy = dx / rad, dy / rad
     r2 = dx * dx + dy * dy
     eps = vortex.eps
     f = eps / (2 * np.pi) * np.exp(0.5 * (1.0 - r2))

@@ -4,8 +4,10 @@ Arnoldi (Eq. vm, vm1, vm2): J V_m = V_{m+1} H~_m with v_1 = b / ||b||.  The
 oracle orthogonalises with modified Gram-Schmidt followed by one full
 re-orthogonalisation pass; any Gram-Schmidt variant spans the same Krylov
 space and gives the same H~_m to rounding.  Reading of the paper's "Krylov
-tolerance": the dimension m is fixed; a happy breakdown at step j
-(h_{j+1,j} <= eta ||J v_j||) truncates V and H to j columns.
+tolerance" (Sec. 5, 1e-5): by default the dimension m is fixed; with a tolerance the
+process stops at the first checkpoint whose a-posteriori error estimate (Saad 1992) is
+within it.  A happy breakdown at step j (h_{j+1,j} <= eta ||J v_j||) truncates V and H
+to j columns.
 
 phi functions (Eq. Phi1, Phi2, final): phi_1(dt H) e_1 and phi_2(dt H) e_1
 are read off the exponential of the augmented matrix
@@ -20,11 +22,12 @@ import math
 import numpy as np
 
 
-def arnoldi(matvec, b, m: int, eta: float = 1e-12):
+def arnoldi(matvec, b, m: int, eta: float = 1e-12, stop=None, check: int = 5):
     """Arnoldi with MGS + one re-orthogonalisation pass.
 
     Returns (V [K, k+1], Hbar [k+1, k], k, beta, breakdown) where k <= m is the
-    dimension reached.  beta = ||b||; beta == 0 returns k = 0.
+    dimension reached.  beta = ||b||; beta == 0 returns k = 0.  stop(k, Hbar_k) (optional)
+    is asked after every ``check``-th column k < m; True ends the process at dimension k.
     """
     b = np.asarray(b, dtype=np.float64)
     beta = float(np.sqrt(np.dot(b, b)))
@@ -50,6 +53,9 @@ def arnoldi(matvec, b, m: int, eta: float = 1e-12):
             k = j + 1
             return V[:, :k], H[: k + 1, :k], k, beta, True
         V[:, j + 1] = w / hn
+        k = j + 1
+        if stop is not None and k < m and k % check == 0 and stop(k, H[: k + 1, :k]):
+            return V[:, : k + 1], H[: k + 1, :k], k, beta, False
     return V, H, m, beta, False
 
 
@@ -90,13 +96,46 @@ def phi_e1(H: np.ndarray, dt: float):
     return np.asarray(X[:k, k], dtype=np.float64), np.asarray(X[:k, k + 1], dtype=np.float64)
 
 
-def krylov_phi1(matvec, b, dt: float, m: int, eta: float = 1e-12):
+def error_estimate(Hb, dt: float):
+    """Relative a-posteriori error of the Krylov phi_1 product of dimension k (Saad 1992,
+    cited in Sec. 2.2; the leading term of the error expansion of Eq. final):
+
+        ||phi_1(dt J) b - beta V_k phi_1(dt H_k) e_1|| / ||beta V_k phi_1(dt H_k) e_1||
+          ~= dt h_{k+1,k} |e_k^T phi_2(dt H_k) e_1| / ||phi_1(dt H_k) e_1||,
+
+    from Hbar [k+1, k] (row k holds h_{k+1,k}).  Both phi columns come from one augmented
+    exponential (Eq. Phi1, Phi2)."""
+    k = Hb.shape[1]
+    y1, y2 = phi_e1(Hb[:k, :k], dt)
+    return float(dt * abs(Hb[k, k - 1]) * abs(y2[k - 1]) / np.linalg.norm(y1))
+
+
+def krylov_phi1(matvec, b, dt: float, m: int, eta: float = 1e-12, tol: float = 0.0, check: int = 5):
     """phi_1(dt J) b ~= ||b|| V_k phi_1(dt H_k) e_1 (Eq. final).
 
-    Returns (x, info) with info = dict(k=..., beta=..., breakdown=...).
+    tol > 0 reads the paper's Krylov tolerance (Sec. 5) as an adaptive dimension: the
+    Arnoldi process stops at the first k (a multiple of ``check``, k < m) whose relative
+    error estimate (``error_estimate``) is <= tol; otherwise k = m (or the breakdown
+    dimension).  Returns (x, info) with info = dict(k, beta, breakdown, H, err) where err is
+    the estimate at the dimension used.
     """
+    stop = (lambda k, Hk: error_estimate(Hk, dt) <= tol) if tol > 0 else None
+    V, Hb, k, beta, brk = arnoldi(matvec, b, m, eta, stop, check)
+    if k == 0:
+        return np.zeros_like(np.asarray(b, np.float64)), dict(k=0, beta=0.0, breakdown=True, err=0.0)
+    y, _ = phi_e1(Hb[:k, :k], dt)
+    err = error_estimate(Hb[: k + 1, :k], dt)
+    return beta * (V[:, :k] @ y), dict(k=k, beta=beta, breakdown=brk, H=Hb, err=err)
+
+
+def krylov_phi2(matvec, b, dt: float, m: int, eta: float = 1e-12):
+    """phi_2(dt J) b ~= ||b|| V_k phi_2(dt H_k) e_1 (Eq. Phi2 through the projection of
+    Eq. final; the second phi column of the same augmented exponential).
+
+    Returns (x, info) as ``krylov_phi1``."""
     V, Hb, k, beta, brk = arnoldi(matvec, b, m, eta)
     if k == 0:
         return np.zeros_like(np.asarray(b, np.float64)), dict(k=0, beta=0.0, breakdown=True)
-    y, _ = phi_e1(Hb[:k, :k], dt)
-    return beta * (V[:, :k] @ y), dict(k=k, beta=beta, breakdown=brk, H=Hb)
+    _, y2 = phi_e1(Hb[:k, :k], dt)
+    return beta * (V[:, :k] @ y2), dict(k=k, beta=beta, breakdown=brk, H=Hb)
+

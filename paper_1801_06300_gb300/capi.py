@@ -29,6 +29,7 @@ PCEXP_BASIS_PAPER = 0
 PCEXP_BASIS_INTERNAL = 1
 PCEXP_SCHEME_PCEXP = 0
 PCEXP_SCHEME_EXP1 = 1
+PCEXP_SCHEME_ETD2 = 2
 PCEXP_DT_GIVEN = 0
 PCEXP_DT_GLOBAL_CFL = 1
 PCEXP_DT_LOCAL_CFL = 2
@@ -58,12 +59,12 @@ class pcexp_physics(C.Structure):
 
 class pcexp_options(C.Structure):
     _fields_ = [("precision", C.c_int32), ("m_max", C.c_int32), ("breakdown_eta", C.c_double),
-                ("basis_io", C.c_int32)]
+                ("basis_io", C.c_int32), ("krylov_tol", C.c_double)]
 
 
 class pcexp_step_info(C.Structure):
     _fields_ = [("krylov_dim", C.c_int32 * 2), ("beta", C.c_double * 2), ("dt", C.c_double),
-                ("res_norm", C.c_double)]
+                ("res_norm", C.c_double), ("krylov_err", C.c_double * 2)]
 
 
 class pcexp_steady_info(C.Structure):
@@ -102,6 +103,7 @@ SIGNATURES = {
     "pcexp_residual_noalloc": (C.c_int, [_P, _P, _P]),
     "pcexp_profile_enable": (C.c_int, [_P, C.c_int]),
     "pcexp_profile_read": (C.c_int, [_P, C.c_int, C.POINTER(C.c_int64), _D]),
+    "pcexp_fp64_fma_rate": (C.c_int, [_D]),
     "pcexp_status_string": (C.c_char_p, [C.c_int]),
     "pcexp_last_error": (C.c_char_p, []),
 }
@@ -126,6 +128,14 @@ def load(path: str | None = None):
         fn.argtypes = args
     _lib = lib
     return lib
+
+
+def fp64_fma_rate() -> float:
+    """FP64 FMA rate of the current device in TFLOP/s (DFMA chains on every SM)."""
+    lib = load()
+    v = C.c_double()
+    check(lib.pcexp_fp64_fma_rate(C.byref(v)), "pcexp_fp64_fma_rate")
+    return v.value
 
 
 class PcexpError(RuntimeError):
@@ -155,7 +165,7 @@ class Context:
     """Owns one pcexp_ctx; each method is one C call with its arguments marshalled."""
 
     def __init__(self, mesh, p: int, free, precision: int = PCEXP_FP64, m_max: int = 30,
-                 eta: float = 0.0, basis_io: int = PCEXP_BASIS_PAPER, stream=None):
+                 eta: float = 0.0, basis_io: int = PCEXP_BASIS_PAPER, stream=None, krylov_tol: float = 0.0):
         lib = load()
         self._keep = []
         coords = np.ascontiguousarray(mesh.coords, np.float64)
@@ -168,7 +178,7 @@ class Context:
         m = pcexp_mesh(mesh.dim, coords.shape[0], coords.ctypes.data_as(_D), elems.shape[0], ip(elems),
                        ip(master), btag.shape[0], ip(bfv) if bfv.size else None, ip(btag) if btag.size else None)
         ph = pcexp_physics(free.gamma, free.mach, free.alpha_deg, free.rho, free.p)
-        op = pcexp_options(precision, m_max, eta, basis_io)
+        op = pcexp_options(precision, m_max, eta, basis_io, krylov_tol)
         if stream is None:
             try:
                 import torch
@@ -297,7 +307,7 @@ class Context:
         if not info:
             return None
         return dict(k=(inf.krylov_dim[0], inf.krylov_dim[1]), beta=(inf.beta[0], inf.beta[1]), dt=inf.dt,
-                    res_norm=inf.res_norm)
+                    res_norm=inf.res_norm, err=(inf.krylov_err[0], inf.krylov_err[1]))
 
     def march_steady(self, scheme: int, cfl_max: float, decades: float, max_iter: int, m: int):
         inf = pcexp_steady_info()

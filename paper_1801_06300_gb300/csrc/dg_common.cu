@@ -187,6 +187,54 @@ cudaError_t launch_scale_by_inverse(double* x, const double* s, int64_t n, cudaS
   return cudaGetLastError();
 }
 
+// FP64 FMA throughput of this GPU: NCH independent DFMA chains per thread on every SM, no
+// memory traffic.  The result depends on the inputs only through the final store, which a
+// comparison that never holds keeps alive.
+constexpr int FMA_CHAINS = 8;
+__global__ void __launch_bounds__(256) dfma_chain_kernel(double* out, int iters, double a, double b) {
+  double x[FMA_CHAINS];
+#pragma unroll
+  for (int k = 0; k < FMA_CHAINS; ++k) x[k] = 1e-3 * (threadIdx.x + k);
+  for (int i = 0; i < iters; ++i)
+#pragma unroll
+    for (int k = 0; k < FMA_CHAINS; ++k) x[k] = fma(x[k], a, b);
+  double s = 0;
+#pragma unroll
+  for (int k = 0; k < FMA_CHAINS; ++k) s += x[k];
+  if (s == -1.0) out[blockIdx.x] = s;
+}
+
+cudaError_t measure_fp64_fma_rate(double* tflops) {
+  int dev = 0, sms = 0;
+  cudaError_t e = cudaGetDevice(&dev);
+  if (e == cudaSuccess) e = cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+  if (e != cudaSuccess) return e;
+  cudaStream_t st = nullptr;
+  cudaEvent_t e0 = nullptr, e1 = nullptr;
+  double* out = nullptr;
+  if ((e = cudaStreamCreateWithFlags(&st, cudaStreamNonBlocking)) != cudaSuccess) return e;
+  e = cudaEventCreate(&e0);
+  if (e == cudaSuccess) e = cudaEventCreate(&e1);
+  if (e == cudaSuccess) e = cudaMalloc(&out, sizeof(double) * sms * 8);
+  const int iters = 1 << 14, blocks = sms * 8, threads = 256;
+  float best = 1e30f;
+  for (int rep = 0; e == cudaSuccess && rep < 4; ++rep) {
+    cudaEventRecord(e0, st);
+    dfma_chain_kernel<<<blocks, threads, 0, st>>>(out, iters, 0.9999999, 1e-7);
+    cudaEventRecord(e1, st);
+    e = cudaEventSynchronize(e1);
+    float ms = 0;
+    if (e == cudaSuccess) e = cudaEventElapsedTime(&ms, e0, e1);
+    if (e == cudaSuccess && rep > 0 && ms < best) best = ms;  // the first launch is a warm-up
+  }
+  if (e == cudaSuccess) *tflops = 2.0 * FMA_CHAINS * (double)iters * blocks * threads / (best * 1e-3) / 1e12;
+  if (out) cudaFree(out);
+  if (e0) cudaEventDestroy(e0);
+  if (e1) cudaEventDestroy(e1);
+  cudaStreamDestroy(st);
+  return e;
+}
+
 #define PCEXP_INST(T)                                                                                         \
   template cudaError_t launch_paper_to_internal<T>(const double*, T*, const double*, int64_t, int, int,        \
                                                    cudaStream_t);                                              \

@@ -793,14 +793,23 @@ cudaError_t linearize_p(const DGData<T>& d, const T* u, LinData<T> lin, bool fac
 // J v from the face point Jacobians and either the volume point Jacobians (u_elem null)
 // or the volume flux tangents recomputed at u_elem (the elements then read u and dv
 // instead of D nv^2 values per volume point).
+//
+// face_tan: the face part recomputes the Riemann-flux tangent at every face point from the
+// traces of u_elem and dv (face_kernel<TAN>) instead of applying the stored face point
+// Jacobians (it then reads u_n and dv instead of 2 nv^2 values per face point).
 template <class T, int D, int P>
 cudaError_t jac_apply_p(const DGData<T>& d, LinData<T> lin, const T* u_elem, const T* dv, T* out, T* G,
                         const T* escale, const int* skip, const double* oscale, cudaStream_t st,
-                        const cudaEvent_t* ev) {
+                        const cudaEvent_t* ev, bool face_tan) {
   using O = Ord<D, P>;
   const int64_t nf = d.F * O::NFQ;
   if (ev) cudaEventRecord(ev[0], st);
-  if (nf > 0) face_apply_kernel<T, D, P><<<(unsigned)((nf + 255) / 256), 256, 0, st>>>(d, lin.Bface, dv, G, skip);
+  if (nf > 0) {
+    if (face_tan && u_elem)
+      face_kernel<T, D, P, true><<<(unsigned)((nf + 255) / 256), 256, 0, st>>>(d, u_elem, dv, G, skip);
+    else
+      face_apply_kernel<T, D, P><<<(unsigned)((nf + 255) / 256), 256, 0, st>>>(d, lin.Bface, dv, G, skip);
+  }
   if (ev) cudaEventRecord(ev[1], st);
   const int64_t eb = (d.E + O::ET - 1) / O::ET;
   if (u_elem) {
@@ -1401,8 +1410,8 @@ cudaError_t launch_linearize_d(const DGData<T>& d, const T* u, LinData<T> lin, b
 template <class T, int D>
 cudaError_t launch_jac_apply_d(const DGData<T>& d, LinData<T> lin, const T* u_elem, const T* dv, T* out, T* G,
                                const T* escale, const int* skip, const double* oscale, cudaStream_t st,
-                               const cudaEvent_t* ev) {
-  PCEXP_PSWITCH(D, (jac_apply_p<T, D, P_>(d, lin, u_elem, dv, out, G, escale, skip, oscale, st, ev)))
+                               const cudaEvent_t* ev, bool face_tan) {
+  PCEXP_PSWITCH(D, (jac_apply_p<T, D, P_>(d, lin, u_elem, dv, out, G, escale, skip, oscale, st, ev, face_tan)))
 }
 template <int D>
 cudaError_t launch_tan_tables_d(const DGData<float>& d, cudaStream_t st) {
@@ -1472,7 +1481,7 @@ cudaError_t launch_local_dt_d(const DGData<T>& d, const T* u, const double* cfl_
   template cudaError_t launch_linearize_d<T, D>(const DGData<T>&, const T*, LinData<T>, bool, cudaStream_t);       \
   template cudaError_t launch_jac_apply_d<T, D>(const DGData<T>&, LinData<T>, const T*, const T*, T*, T*,          \
                                                 const T*, const int*, const double*, cudaStream_t,                 \
-                                                const cudaEvent_t*);                                               \
+                                                const cudaEvent_t*, bool);                                         \
   template cudaError_t launch_jac_adjoint_d<T, D>(const DGData<T>&, LinData<T>, const T*, T*, T*, const T*, T,     \
                                                   cudaStream_t);                                                   \
   template cudaError_t launch_jvp_state_adjoint_d<T, D>(const DGData<T>&, const T*, const T*, const T*, T*, T*,    \

@@ -24,6 +24,7 @@ struct KState {
   double y2[MMAX];         // phi_2(dt H_k) e_1
   double beta;
   double wnorm0;
+  double err_est;          // relative a-posteriori error estimate of the last phi evaluation
   int k;
   int done;
   int err;
@@ -51,6 +52,8 @@ struct StepState {
   int err;
   unsigned counter;
   double dtmin_scratch;
+  double dt_prev;  // dt of the previous ETD2 step (its divided difference of N)
+  double kerr[2];  // Krylov error estimates of the two stages
 };
 
 // Mesh/geometry/tables on the device, for one scalar type.  D = dim, NV = D + 2,
@@ -95,7 +98,7 @@ cudaError_t launch_linearize_d(const DGData<T>& d, const T* u, LinData<T> lin, b
 template <class T, int D>
 cudaError_t launch_jac_apply_d(const DGData<T>& d, LinData<T> lin, const T* u_elem, const T* dv, T* out, T* G,
                                const T* escale, const int* skip, const double* oscale, cudaStream_t st,
-                               const cudaEvent_t* ev);
+                               const cudaEvent_t* ev, bool face_tan);
 template <int D>
 cudaError_t launch_tan_tables_d(const DGData<float>& d, cudaStream_t st);
 template <class T, int D>
@@ -134,15 +137,16 @@ cudaError_t launch_linearize(const DGData<T>& d, const T* u, LinData<T> lin, cud
   return d.dim == 3 ? launch_linearize_d<T, 3>(d, u, lin, faces_only, st)
                     : launch_linearize_d<T, 2>(d, u, lin, faces_only, st);
 }
-// out = J(u) dv from the face point Jacobians and, for the volume, the volume point
-// Jacobians (u_elem null) or the flux tangents at u_elem (same ev / escale / skip /
-// oscale conventions as the operator).
+// out = J(u) dv: the face part from the face point Jacobians, or (face_tan, with u_elem) from
+// Riemann-flux tangents recomputed at u_elem; the volume part from the volume point
+// Jacobians (u_elem null) or the flux tangents at u_elem (same ev / escale / skip / oscale
+// conventions as the operator).
 template <class T>
 cudaError_t launch_jac_apply(const DGData<T>& d, LinData<T> lin, const T* dv, T* out, T* G, const T* escale,
                              const int* skip, const double* oscale, cudaStream_t st, const cudaEvent_t* ev,
-                             const T* u_elem = nullptr) {
-  return d.dim == 3 ? launch_jac_apply_d<T, 3>(d, lin, u_elem, dv, out, G, escale, skip, oscale, st, ev)
-                    : launch_jac_apply_d<T, 2>(d, lin, u_elem, dv, out, G, escale, skip, oscale, st, ev);
+                             const T* u_elem = nullptr, bool face_tan = false) {
+  return d.dim == 3 ? launch_jac_apply_d<T, 3>(d, lin, u_elem, dv, out, G, escale, skip, oscale, st, ev, face_tan)
+                    : launch_jac_apply_d<T, 2>(d, lin, u_elem, dv, out, G, escale, skip, oscale, st, ev, face_tan);
 }
 // Upload the reference tables [Bv | Dv] of the context's (D, p) to the constant-memory copy
 // read by the FP32 flux-tangent J v on tetrahedra (device-to-device, on st; same bytes for
@@ -199,6 +203,8 @@ template <class T>
 cudaError_t launch_scale_elements(T* x, const T* s, int64_t E, int nvb, cudaStream_t st);
 // x *= s (s a device scalar, n entries)
 cudaError_t launch_scale_by_inverse(double* x, const double* s, int64_t n, cudaStream_t st);
+// FP64 FMA rate of the current device (TFLOP/s) from DFMA chains on every SM
+cudaError_t measure_fp64_fma_rate(double* tflops);
 // sum_e sum_q w^_q |det A_e| (s/s0)^2 of the FP64 state u (Eq. entropy_error) -> *value
 cudaError_t launch_entropy_sum(const double* u, const double* Bv, const double* Wv, const double* sd, int64_t E, int nb,
                                int nq, int nv, double gamma, double s0, double* value, double* partials,
@@ -215,9 +221,14 @@ template <class T>
 cudaError_t launch_cgs(int mode, const T* Z, int64_t ldz, int64_t Kp, int j, T* w, T* out,
                        KState* ks, double* partials, double eta, cudaStream_t st);
 // phi_1/phi_2 of dt H_k (dt from *dt_dev when non-null, else dt) -> ks->y, ks->y2,
-// ks->acoef = factor * dt * beta * y_i * s_i; records k and beta into ss->k[stage], ss->beta[stage].
+// ks->acoef = factor * dt * beta * y_i * s_i (which = 1) or factor * dt * beta * y2_i * s_i (which = 2),
+// times dt / *dt_prev when dt_prev is non-null; records k and beta into ss->k[stage], ss->beta[stage].
 cudaError_t launch_phi(KState* ks, const double* dt_dev, double dt, double factor, StepState* ss,
-                       int stage, cudaStream_t st);
+                       int stage, cudaStream_t st, int which = 1, const double* dt_prev = nullptr);
+// Checkpoint of the adaptive Krylov dimension: the error estimate of phi_1(dt H_k) e_1 at the
+// current dimension k -> ks->err_est, and ks->done = 1 (the remaining columns are skipped)
+// when it is <= tol.  No update coefficients are written.
+cudaError_t launch_phi_check(KState* ks, const double* dt_dev, double tol, cudaStream_t st);
 // Hbar = (d y / d H)^T ybar for y = phi_1(dt H) e_1 (H, Hbar: k x k row-major, leading dim ldh; device)
 cudaError_t launch_phi_adjoint(const double* H, int k, int ldh, double dt, const double* ybar, double* Hbar, int* err,
                                cudaStream_t st);
@@ -230,6 +241,13 @@ template <class T>
 cudaError_t launch_combine_corrector(T* a, const T* b, const T* c, int64_t Kp, cudaStream_t st);
 template <class Tin, class Tout>
 cudaError_t launch_cast(const Tin* x, Tout* y, int64_t n, cudaStream_t st);
+// out = x - y - z (z nullable)
+template <class T>
+cudaError_t launch_lincomb3(T* out, const T* x, const T* y, const T* z, int64_t Kp, cudaStream_t st);
+// ss->dt_prev = ss->dt
+cudaError_t launch_keep_dt(StepState* ss, cudaStream_t st);
+// ss->cfl = min(ss->cfl, cap) (the Krylov-error cap of the steady march)
+cudaError_t launch_cap_cfl(StepState* ss, double cap, cudaStream_t st);
 cudaError_t launch_reset_kstate(KState* ks, cudaStream_t st);
 // ---- reverse Krylov stage (adjoint.cu, FP64)
 cudaError_t launch_adj_seed(const double* Z, int64_t ldz, double* Vb, const double* ubar, int64_t Kp, int k, int m,

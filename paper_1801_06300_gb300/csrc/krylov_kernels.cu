@@ -772,13 +772,23 @@ __device__ double* expm_cluster(cg::cluster_group& cl, double* sm, int n) {
   return X;
 }
 
+// which = 1: the update coefficients use phi_1(dt H) e_1 (Eq. s8, s9, s10); which = 2: they use
+// phi_2(dt H) e_1 (the ETD2 term of Eq. s7), times dt / *dt_prev when dt_prev is given.
+//
+// Every evaluation also forms the relative a-posteriori error estimate of the Krylov phi_1
+// product (Saad 1992, the leading term of the error of Eq. final),
+//   est = dt h_{k+1,k} |e_k^T phi_2(dt H_k) e_1| / ||phi_1(dt H_k) e_1||,
+// from the phi_2 column of the same exponential.  check_tol > 0 is a checkpoint of the
+// adaptive dimension: only est is formed, and ks->done is raised when est <= check_tol.
 __global__ void __cluster_dims__(PHI_CTAS, 1, 1) __launch_bounds__(256)
-    phi_kernel(KState* ks, const double* dt_dev, double dt_host, double factor, StepState* ss, int stage) {
+    phi_kernel(KState* ks, const double* dt_dev, double dt_host, double factor, StepState* ss, int stage, int which,
+               const double* dt_prev, double check_tol) {
   extern __shared__ double sm[];
   cg::cluster_group cl = cg::this_cluster();
   const int rank = (int)cl.block_rank();
   const int k = ks->k;
   const double dt = dt_dev ? *dt_dev : dt_host;
+  if (check_tol > 0.0 && (k == 0 || ks->err || ks->done)) return;  // uniform across the cluster
   if (k == 0 || ks->err) {  // uniform across the cluster: no shared-memory traffic happens
     if (rank == 0 && threadIdx.x == 0) {
       for (int i = 0; i <= MMAX; ++i) ks->acoef[i] = 0.0;
@@ -810,13 +820,22 @@ __global__ void __cluster_dims__(PHI_CTAS, 1, 1) __launch_bounds__(256)
       if (ss) ss->err = 1;
       return;
     }
+    double n1 = 0.0;
+    for (int i = 0; i < k; ++i) n1 += X[i * PN + k] * X[i * PN + k];
+    const double est = dt * fabs(ks->H[k * MMAX + k - 1]) * fabs(X[(k - 1) * PN + k + 1]) / sqrt(n1);
+    ks->err_est = est;
+    if (check_tol > 0.0) {
+      if (est <= check_tol) ks->done = 1;  // the estimate may be NaN: then the process goes on
+      return;
+    }
     const double beta = ks->beta;
+    const double f = dt_prev ? factor * dt / *dt_prev : factor;
     bool ok = true;
     for (int i = 0; i < k; ++i) {
       const double y1 = X[i * PN + k], y2 = X[i * PN + k + 1];
       ks->y[i] = y1;
       ks->y2[i] = y2;
-      ks->acoef[i] = factor * dt * beta * y1 * ks->s[i];
+      ks->acoef[i] = f * dt * beta * (which == 2 ? y2 : y1) * ks->s[i];
       ok = ok && isfinite(ks->acoef[i]);
     }
     for (int i = k; i <= MMAX; ++i) ks->acoef[i] = 0.0;
@@ -824,6 +843,7 @@ __global__ void __cluster_dims__(PHI_CTAS, 1, 1) __launch_bounds__(256)
     if (ss) {
       ss->k[stage] = k;
       ss->beta[stage] = beta;
+      ss->kerr[stage] = est;
       if (!ok) ss->err = 1;
     }
   }
@@ -871,16 +891,30 @@ __global__ void __cluster_dims__(PHI_CTAS, 1, 1) __launch_bounds__(256)
   }
 }
 
-cudaError_t launch_phi(KState* ks, const double* dt_dev, double dt, double factor, StepState* ss, int stage,
-                       cudaStream_t st) {
-  const size_t smem = 5 * PN * PN * sizeof(double);
+static cudaError_t phi_smem_attr(size_t smem) {
   static bool attr_set = false;
   if (!attr_set) {
     cudaError_t e = cudaFuncSetAttribute(phi_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     if (e != cudaSuccess) return e;
     attr_set = true;
   }
-  phi_kernel<<<PHI_CTAS, 256, smem, st>>>(ks, dt_dev, dt, factor, ss, stage);
+  return cudaSuccess;
+}
+
+cudaError_t launch_phi(KState* ks, const double* dt_dev, double dt, double factor, StepState* ss, int stage,
+                       cudaStream_t st, int which, const double* dt_prev) {
+  const size_t smem = 5 * PN * PN * sizeof(double);
+  cudaError_t e = phi_smem_attr(smem);
+  if (e != cudaSuccess) return e;
+  phi_kernel<<<PHI_CTAS, 256, smem, st>>>(ks, dt_dev, dt, factor, ss, stage, which, dt_prev, 0.0);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_phi_check(KState* ks, const double* dt_dev, double tol, cudaStream_t st) {
+  const size_t smem = 5 * PN * PN * sizeof(double);
+  cudaError_t e = phi_smem_attr(smem);
+  if (e != cudaSuccess) return e;
+  phi_kernel<<<PHI_CTAS, 256, smem, st>>>(ks, dt_dev, 1.0, 1.0, nullptr, 0, 1, nullptr, tol);
   return cudaGetLastError();
 }
 
@@ -941,6 +975,21 @@ cudaError_t launch_combine_corrector(T* a, const T* b, const T* c, int64_t Kp, c
   return cudaGetLastError();
 }
 
+// out = x - y - z (z nullable)
+template <class T>
+__global__ void lincomb3_kernel(T* __restrict__ out, const T* __restrict__ x, const T* __restrict__ y,
+                                const T* __restrict__ z, int64_t n) {
+  for (int64_t r = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; r < n; r += (int64_t)gridDim.x * blockDim.x)
+    out[r] = z ? x[r] - y[r] - z[r] : x[r] - y[r];
+}
+template <class T>
+cudaError_t launch_lincomb3(T* out, const T* x, const T* y, const T* z, int64_t Kp, cudaStream_t st) {
+  int64_t g = (Kp + 255) / 256;
+  if (g > 152 * 8) g = 152 * 8;
+  lincomb3_kernel<T><<<(unsigned)(g < 1 ? 1 : g), 256, 0, st>>>(out, x, y, z, Kp);
+  return cudaGetLastError();
+}
+
 template <class Tin, class Tout>
 __global__ void cast_kernel(const Tin* __restrict__ x, Tout* __restrict__ y, int64_t n) {
   for (int64_t r = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; r < n; r += (int64_t)gridDim.x * blockDim.x)
@@ -961,6 +1010,7 @@ __global__ void reset_kstate_kernel(KState* ks) {
     ks->err = 0;
     ks->counter = 0;
     ks->beta = 0;
+    ks->err_est = 0;
   }
   for (int i = threadIdx.x; i < (MMAX + 1) * MMAX; i += blockDim.x) ks->H[i] = 0.0;
 }
@@ -970,6 +1020,16 @@ cudaError_t launch_reset_kstate(KState* ks, cudaStream_t st) {
 }
 
 __global__ void set_dt_kernel(StepState* ss, double dt) { ss->dt = dt; }
+__global__ void keep_dt_kernel(StepState* ss) { ss->dt_prev = ss->dt; }
+__global__ void cap_cfl_kernel(StepState* ss, double cap) { ss->cfl = fmin(ss->cfl, cap); }
+cudaError_t launch_cap_cfl(StepState* ss, double cap, cudaStream_t st) {
+  cap_cfl_kernel<<<1, 1, 0, st>>>(ss, cap);
+  return cudaGetLastError();
+}
+cudaError_t launch_keep_dt(StepState* ss, cudaStream_t st) {
+  keep_dt_kernel<<<1, 1, 0, st>>>(ss);
+  return cudaGetLastError();
+}
 __global__ void set_param_kernel(double* p, double v) { *p = v; }
 __global__ void copy_dt_kernel(StepState* ss, const double* p) { ss->dt = *p; }
 cudaError_t launch_set_param(double* param, double v, cudaStream_t st) {
@@ -993,6 +1053,9 @@ template cudaError_t launch_krylov_axpy<double>(const double*, double*, double*,
                                                 int64_t, const KState*, cudaStream_t);
 template cudaError_t launch_krylov_axpy<float>(const double*, double*, float*, float*, const float*, int64_t,
                                                int64_t, const KState*, cudaStream_t);
+template cudaError_t launch_lincomb3<double>(double*, const double*, const double*, const double*, int64_t,
+                                             cudaStream_t);
+template cudaError_t launch_lincomb3<float>(float*, const float*, const float*, const float*, int64_t, cudaStream_t);
 template cudaError_t launch_combine_corrector<double>(double*, const double*, const double*, int64_t, cudaStream_t);
 template cudaError_t launch_combine_corrector<float>(float*, const float*, const float*, int64_t, cudaStream_t);
 template cudaError_t launch_cast<double, float>(const double*, float*, int64_t, cudaStream_t);

@@ -172,6 +172,26 @@ def bump_channel(nx: int, ny: int, jitter: float = 0.0, seed: int = 0,
                 name=f"bump{nx}x{ny}", volume=3.0 - 0.5 * bump_h)
 
 
+def stretched_periodic_square(n: int, length: float, power: int = 3) -> Mesh:
+    """The paper's stiff vortex mesh (Sec. 5.1): node j = 1..n+1 of each direction at
+    x_j = (1 - xi_j^p) x_L / 2 + (1 + xi_j^p) x_R / 2, xi_j = 2 (j - 1) / n - 1 (x_L = 0,
+    x_R = length, p = 3), clustered about the centre; n x n quads, each split into 2
+    triangles, periodic in both directions (node n+1 is node 1's periodic image)."""
+    j = np.arange(1, n + 2)
+    xi = 2.0 * (j - 1) / n - 1.0
+    xs = 0.5 * (1.0 - xi ** power) * 0.0 + 0.5 * (1.0 + xi ** power) * length
+    nv = n + 1
+    ii, jj = np.meshgrid(np.arange(nv), np.arange(nv), indexing="xy")
+    ii = ii.ravel()
+    jj = jj.ravel()
+    master = ((jj % n) * n + (ii % n)).astype(np.int32)
+    coords = np.stack([xs[ii], xs[jj]], axis=1)
+    elems = _split_quads(n, n, lambda i, k: k * nv + i)
+    return Mesh(dim=2, coords=coords, elems=elems, vert_master=master,
+                bfaces=np.zeros((0, 2), np.int32), btags=np.zeros(0, np.int32),
+                name=f"stretched{n}x{n}", volume=length * length)
+
+
 def periodic_cube_kuhn(n: int, length: float, jitter: float = 0.0, seed: int = 0,
                        periodic: bool = True) -> Mesh:
     """n^3 cubes on the cube [0, length]^3, each split into 6 Kuhn tetrahedra.
@@ -260,10 +280,12 @@ class Freestream:
 
 @dataclasses.dataclass
 class Vortex:
-    """Isentropic vortex of strength ``eps`` centred at ``center``, carried by the free stream."""
+    """Isentropic vortex of strength ``eps`` centred at ``center``, carried by the free stream;
+    ``radius`` is the core radius (the length unit of its profile)."""
 
     eps: float = 5.0
     center: tuple = (5.0, 5.0)
+    radius: float = 1.0
 
 
 @dataclasses.dataclass
@@ -325,6 +347,19 @@ def case_vortex3d(n: int = 48, p: int = 2, seed: int = 5) -> Case:
     return Case(f"vortex3d_p{p}_n{n}", periodic_cube_kuhn(n, 10.0, 0.10, seed), p=p, m=30,
                 free=Freestream(mach=0.5, alpha_deg=45.0), vortex=Vortex(5.0, (5.0, 5.0)),
                 cfl=10.0, steps=50)
+
+
+def case_vortex_stretched(n: int = 24, p: int = 1) -> Case:
+    """The paper's stiff vortex case (Sec. 5.1): periodic [0, 0.1]^2 on the stretched n x n
+    mesh (minimum spacing 2.9e-5, maximum 0.0115 at n = 24), Ma 0.5 along x, vortex with
+    beta = 0.2 and core radius R = 0.05 at (0.05, 0.05), PCEXP at CFL 1000, m = 30, one
+    period T = 0.1 / U_inf.  With rho_inf = p_inf = 1 the paper's vortex is the isentropic
+    vortex of core radius R and strength eps = 2 pi beta U_inf exp(-1/2)."""
+    free = Freestream(mach=0.5, alpha_deg=0.0)
+    u_inf = vortex_speed(free)
+    eps = 2.0 * math.pi * 0.2 * u_inf * math.exp(-0.5)
+    return Case(f"vortex_stretched_p{p}_n{n}", stretched_periodic_square(n, 0.1), p=p, m=30, free=free,
+                vortex=Vortex(eps, (0.05, 0.05), 0.05), cfl=1000.0, steps=0)
 
 
 def random_coeffs(seed: int, shape, scale: float = 1.0) -> np.ndarray:
