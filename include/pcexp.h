@@ -209,13 +209,27 @@ int pcexp_phi_adjoint(pcexp_ctx* ctx, const double* H, int k, int ldh, double dt
 /* Reverse of one PCEXP step (Eq. s9, s10) exactly as computed with the global
  * time step dt and Krylov dimension m: given the state U = u_n (the checkpoint)
  * and ubar_next, the adjoint of u_{n+1}, writes ubar = (du_{n+1}/du_n)^T
- * ubar_next.  The step is recomputed from u_n; dt is held constant.  Covers the
+ * ubar_next and, when theta_bar (host, 2 doubles) is not NULL, the adjoint of the
+ * free-stream parameters theta = (Mach number, flow angle in degrees) of the step,
+ * theta_bar = (du_{n+1}/dtheta)^T ubar_next (theta enters through the far-field ghost
+ * state of every R and J v of the step; the mixed second derivatives of J_n are
+ * included).  The step is recomputed from u_n; dt is held constant.  Covers the
  * adjoint of R, of J_n (including its dependence on u_n), of the CGS2 Arnoldi
  * processes, of phi and of both updates.  FP64 contexts only
  * (PCEXP_ERR_UNSUPPORTED otherwise).  The first call allocates the reverse work
  * space (about 2 (m_max + 1) + 16 state vectors). */
 int pcexp_step_backward(pcexp_ctx* ctx, const double* U, double dt, int m,
-                        const double* ubar_next, double* ubar, int on_device);
+                        const double* ubar_next, double* ubar, double* theta_bar, int on_device);
+
+/* Adjoint of pcexp_project_state: theta_bar = (d u_0 / d theta)^T ubar0 for the projected
+ * state u_0 of kind (PCEXP_PROJ_*) and params, with theta = (Mach, alpha in degrees) and,
+ * for PCEXP_PROJ_VORTEX, the vortex strength eps as a third entry (theta_bar holds 2 or 3
+ * doubles, host).  ubar0 has K entries in the context's basis (host or device).  The
+ * derivative of the pointwise state is exact (forward-mode dual numbers through the same
+ * state formulas) and is projected with the volume rule; host computation.  FP64 contexts.
+ * Errors: INVALID_ARG, UNSUPPORTED (FP32-mixed), CUDA. */
+int pcexp_project_state_adjoint(pcexp_ctx* ctx, int kind, const double* params, int n_params,
+                                const double* ubar0, double* theta_bar, int on_device);
 
 /* One PCEXP (Eq. s9, s10), EXP1 (Eq. s9) or ETD2 (Eq. s7) step on the master state
  * with Krylov dimension m (<= m_max).  dt_mode PCEXP_DT_*: dt_or_cfl is dt for
@@ -255,6 +269,14 @@ int pcexp_march_steady(pcexp_ctx* ctx, int scheme, double cfl_max, double decade
 int pcexp_functional(pcexp_ctx* ctx, int kind, const double* U, double* value, double* grad, int on_device);
 int pcexp_functional_params(pcexp_ctx* ctx, int kind, const double* params, int n_params, const double* U,
                             double* value, double* grad, int on_device);
+/* Partial derivatives of an output functional with respect to its parameters at a fixed
+ * state U: dJ[0..2] = dJ/d(Mach, alpha in degrees, eps).  The wall forces depend on U alone
+ * (all zero); the vortex error depends on the exact translated vortex, whose mean velocity
+ * is the free stream's (Mach, alpha) and whose strength is eps:
+ * dJ/dtheta = -(1/J) sum w_q (U_h - U_ex) . dU_ex/dtheta, on the device (dual numbers through
+ * the exact state).  Same parameters as pcexp_functional_params.  FP64 contexts. */
+int pcexp_functional_param_grad(pcexp_ctx* ctx, int kind, const double* params, int n_params, const double* U,
+                                double* dJ, int on_device);
 
 /* Replaces the free stream (Mach number, angle, density, pressure, gamma) used
  * by the far-field boundary condition; the mesh and state are kept. */

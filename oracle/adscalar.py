@@ -20,8 +20,9 @@ class Dual:
     __array_priority__ = 100.0
 
     def __init__(self, val, der):
-        self.val = np.asarray(val, dtype=np.float64)
-        self.der = np.asarray(der, dtype=np.float64)
+        # float64, or complex128 when a complex step runs through dual numbers
+        self.val = np.asarray(val, dtype=np.result_type(val, np.float64))
+        self.der = np.asarray(der, dtype=np.result_type(der, np.float64))
 
     @staticmethod
     def _split(o):
@@ -91,8 +92,8 @@ def sqrt(x):
 def absval(x):
     """|x| with derivative sign(x) (sign(0) = 0); complex continuation x sign(Re x)."""
     if isinstance(x, Dual):
-        sg = np.sign(x.val)
-        return Dual(np.abs(x.val), sg * x.der)
+        sg = np.sign(np.real(x.val))
+        return Dual(x.val * sg, sg * x.der)
     if np.iscomplexobj(x):
         return x * np.sign(x.real)
     return np.abs(x)
@@ -131,7 +132,7 @@ def stack(xs, axis=-1):
 def zeros_like_var(x, shape):
     """A zero array of ``shape`` with the scalar type of ``x``."""
     if isinstance(x, Dual):
-        return Dual(np.zeros(shape), np.zeros(shape))
+        return Dual(np.zeros(shape, dtype=x.val.dtype), np.zeros(shape, dtype=np.result_type(x.val, x.der)))
     return np.zeros(shape, dtype=np.result_type(x, np.float64))
 
 

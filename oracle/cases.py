@@ -20,7 +20,7 @@ import numpy as np
 def freestream_velocity(free, dim: int = 2):
     """Free-stream velocity: Ma c_inf (cos alpha, sin alpha) in the x-y plane (w = 0 in 3D)."""
     c = np.sqrt(free.gamma * free.p / free.rho)
-    a = np.deg2rad(free.alpha_deg)
+    a = free.alpha_deg * (np.pi / 180.0)  # the deg2rad constant; also takes a complex step
     vel = (free.mach * c * np.cos(a), free.mach * c * np.sin(a))
     return vel if dim == 2 else vel + (0.0,)
 

@@ -224,8 +224,8 @@ class DGOracle:
 
     def jvp(self, u, v, **kw):
         """J(u) v by forward-mode dual numbers through ``residual`` (Eq. jac1, jac2)."""
-        ud = ad.Dual(np.asarray(u, np.float64).reshape(self.E, self.nv, self.N),
-                     np.asarray(v, np.float64).reshape(self.E, self.nv, self.N))
+        ud = ad.Dual(np.asarray(u).reshape(self.E, self.nv, self.N),
+                     np.asarray(v).reshape(self.E, self.nv, self.N))
         r = self.residual(ud, **kw)
         return r.der.reshape(np.shape(u))
 

@@ -29,27 +29,30 @@ def arnoldi(matvec, b, m: int, eta: float = 1e-12, stop=None, check: int = 5):
     dimension reached.  beta = ||b||; beta == 0 returns k = 0.  stop(k, Hbar_k) (optional)
     is asked after every ``check``-th column k < m; True ends the process at dimension k.
     """
-    b = np.asarray(b, dtype=np.float64)
-    beta = float(np.sqrt(np.dot(b, b)))
+    # real (FP64) or complex (a complex step through the whole process: dot products without
+    # conjugation, decisions on real parts)
+    ty = np.result_type(b, np.float64)
+    b = np.asarray(b, dtype=ty)
+    beta = np.sqrt(np.dot(b, b))
     K = b.shape[0]
     if beta == 0.0:
-        return np.zeros((K, 1)), np.zeros((1, 0)), 0, 0.0, True
-    V = np.zeros((K, m + 1))
-    H = np.zeros((m + 1, m))
+        return np.zeros((K, 1), ty), np.zeros((1, 0), ty), 0, 0.0, True
+    V = np.zeros((K, m + 1), ty)
+    H = np.zeros((m + 1, m), ty)
     V[:, 0] = b / beta
     for j in range(m):
-        w = np.asarray(matvec(V[:, j]), dtype=np.float64).copy()
-        w0 = float(np.sqrt(np.dot(w, w)))
+        w = np.asarray(matvec(V[:, j]), dtype=ty).copy()
+        w0 = np.sqrt(np.dot(w, w))
         for _ in range(2):
             for i in range(j + 1):
-                h = float(np.dot(V[:, i], w))
+                h = np.dot(V[:, i], w)
                 H[i, j] += h
                 w -= h * V[:, i]
-        hn = float(np.sqrt(np.dot(w, w)))
+        hn = np.sqrt(np.dot(w, w))
         H[j + 1, j] = hn
         if not np.isfinite(hn):
             raise FloatingPointError("non-finite Arnoldi norm")
-        if hn <= eta * w0:
+        if np.real(hn) <= eta * np.real(w0):
             k = j + 1
             return V[:, :k], H[: k + 1, :k], k, beta, True
         V[:, j + 1] = w / hn
@@ -62,9 +65,10 @@ def arnoldi(matvec, b, m: int, eta: float = 1e-12, stop=None, check: int = 5):
 def expm_taylor(A: np.ndarray) -> np.ndarray:
     """exp(A) by Taylor series after scaling A / 2^s to 1-norm <= 1/2, then squaring.
 
-    Runs in numpy longdouble (80-bit on x86-64, 128-bit on AArch64).
+    Runs in numpy longdouble (80-bit on x86-64, 128-bit on AArch64), complex longdouble for
+    complex input.
     """
-    A = np.asarray(A, dtype=np.longdouble)
+    A = np.asarray(A, dtype=np.clongdouble if np.iscomplexobj(A) else np.longdouble)
     n = A.shape[0]
     nrm = float(np.max(np.sum(np.abs(A), axis=0))) if n else 0.0
     s = 0
@@ -72,8 +76,8 @@ def expm_taylor(A: np.ndarray) -> np.ndarray:
         s = int(math.ceil(math.log2(nrm / 0.5)))
     B = A / np.longdouble(2.0) ** s
     eps = np.finfo(np.longdouble).eps
-    T = np.eye(n, dtype=np.longdouble)
-    term = np.eye(n, dtype=np.longdouble)
+    T = np.eye(n, dtype=A.dtype)
+    term = np.eye(n, dtype=A.dtype)
     for k in range(1, 80):
         term = term @ B / np.longdouble(k)
         T = T + term
@@ -87,13 +91,15 @@ def expm_taylor(A: np.ndarray) -> np.ndarray:
 def phi_e1(H: np.ndarray, dt: float):
     """(phi_1(dt H) e_1, phi_2(dt H) e_1) for square H [k, k] via the augmented exponential."""
     k = H.shape[0]
-    A = np.zeros((k + 2, k + 2), dtype=np.longdouble)
-    A[:k, :k] = np.asarray(H, dtype=np.longdouble) * np.longdouble(dt)
+    cx = np.iscomplexobj(H)
+    A = np.zeros((k + 2, k + 2), dtype=np.clongdouble if cx else np.longdouble)
+    A[:k, :k] = np.asarray(H, dtype=A.dtype) * np.longdouble(dt)
     if k:
         A[0, k] = 1.0
     A[k, k + 1] = 1.0
     X = expm_taylor(A)
-    return np.asarray(X[:k, k], dtype=np.float64), np.asarray(X[:k, k + 1], dtype=np.float64)
+    out = np.complex128 if cx else np.float64
+    return np.asarray(X[:k, k], dtype=out), np.asarray(X[:k, k + 1], dtype=out)
 
 
 def error_estimate(Hb, dt: float):
@@ -122,9 +128,10 @@ def krylov_phi1(matvec, b, dt: float, m: int, eta: float = 1e-12, tol: float = 0
     stop = (lambda k, Hk: error_estimate(Hk, dt) <= tol) if tol > 0 else None
     V, Hb, k, beta, brk = arnoldi(matvec, b, m, eta, stop, check)
     if k == 0:
-        return np.zeros_like(np.asarray(b, np.float64)), dict(k=0, beta=0.0, breakdown=True, err=0.0)
+        return np.zeros_like(np.asarray(b, np.result_type(b, np.float64))), dict(k=0, beta=0.0, breakdown=True,
+                                                                                  err=0.0)
     y, _ = phi_e1(Hb[:k, :k], dt)
-    err = error_estimate(Hb[: k + 1, :k], dt)
+    err = error_estimate(np.real(Hb[: k + 1, :k]), dt)
     return beta * (V[:, :k] @ y), dict(k=k, beta=beta, breakdown=brk, H=Hb, err=err)
 
 
@@ -135,7 +142,7 @@ def krylov_phi2(matvec, b, dt: float, m: int, eta: float = 1e-12):
     Returns (x, info) as ``krylov_phi1``."""
     V, Hb, k, beta, brk = arnoldi(matvec, b, m, eta)
     if k == 0:
-        return np.zeros_like(np.asarray(b, np.float64)), dict(k=0, beta=0.0, breakdown=True)
+        return np.zeros_like(np.asarray(b, np.result_type(b, np.float64))), dict(k=0, beta=0.0, breakdown=True)
     _, y2 = phi_e1(Hb[:k, :k], dt)
     return beta * (V[:, :k] @ y2), dict(k=k, beta=beta, breakdown=brk, H=Hb)
 

@@ -23,7 +23,7 @@ def pcexp_step(u, R, jvp, dt: float, m: int, eta: float = 1e-12, scheme: str = "
     (``krylov.krylov_phi1``).  Returns (u_{n+1}, info); info err1, err2 are the Krylov
     error estimates of the two stages.
     """
-    u = np.asarray(u, dtype=np.float64)
+    u = np.asarray(u, dtype=np.result_type(u, np.float64))  # complex for a complex step
     Rn = R(u)
     x1, i1 = krylov.krylov_phi1(lambda v: jvp(u, v), Rn, dt, m, eta, tol)
     u_star = u + dt * x1

@@ -1,41 +1,73 @@
 """Gradients through PCEXP steps with torch.autograd (argument marshalling only).
 
-``PCEXPStep.apply(u_n, solver, dt, m)`` runs one PCEXP step (Eq. s9, s10) of the CUDA
-library and, in backward, its exact reverse (``pcexp_step_backward``): the step is
-recomputed from the saved u_n (per-step checkpointing) and the Krylov bases are rebuilt.
-``WallForce.apply(u, solver, kind)`` is the slip-wall pressure force and its gradient;
-``VortexError.apply(u, solver, params)`` the L2 error against the translated vortex.
-``adjoint_rollout`` chains N steps and returns the functional, its gradient with respect
-to the initial state and, optionally, with respect to free-stream parameters and to
-parameters of the initial state and the functional (the vortex strength).
+``PCEXPStep.apply(u_n, theta, solver, dt, m)`` runs one PCEXP step (Eq. s9, s10) of the CUDA
+library with the free-stream parameters theta = (Mach number, flow angle in degrees) and, in
+backward, its exact reverse (``pcexp_step_backward``): the step is recomputed from the saved
+u_n (per-step checkpointing), the Krylov bases are rebuilt, and the adjoints of u_n and of
+theta come back from the library.  ``ProjectedState.apply(theta, solver, kind, params)`` is
+the projected initial state (``pcexp_project_state``) with its exact adjoint;
+``WallForce.apply(u, solver, kind)`` the slip-wall pressure force and ``VortexError.apply(u,
+solver, params)`` the L2 error against the translated vortex, each with its gradient from
+the library.  ``adjoint_rollout`` chains N steps without autograd and returns the functional
+and its gradients with respect to the initial state, (Mach, alpha) and the vortex strength.
 
-States are CUDA float64 tensors of K coefficients in the context's basis.
+States are CUDA float64 tensors of K coefficients in the context's basis; theta is a float64
+tensor of 2 entries.  Every derivative is computed by the library; this module only moves
+arguments and results.
 """
 from __future__ import annotations
 
 import dataclasses
 
+import numpy as np
 import torch
 
 from . import capi
 
 
+def _free_with(solver_free, theta):
+    return dataclasses.replace(solver_free, mach=float(theta[0]), alpha_deg=float(theta[1]))
+
+
 class PCEXPStep(torch.autograd.Function):
     @staticmethod
-    def forward(ctx, u, solver, dt, m):
+    def forward(ctx, u, theta, solver, free, dt, m):
         u = u.detach().contiguous()
+        fr = _free_with(free, theta.detach().cpu())
+        solver.set_physics(fr)
         solver.set_state(u)
         solver.step(capi.PCEXP_SCHEME_PCEXP, capi.PCEXP_DT_GIVEN, float(dt), int(m), info=False)
         out = solver.get_state(torch.empty_like(u))
-        ctx.save_for_backward(u)
-        ctx.solver, ctx.dt, ctx.m = solver, float(dt), int(m)
+        ctx.save_for_backward(u, theta.detach())
+        ctx.solver, ctx.free, ctx.dt, ctx.m = solver, free, float(dt), int(m)
         return out
 
     @staticmethod
     def backward(ctx, g):
-        (u,) = ctx.saved_tensors
-        ub = ctx.solver.step_backward(u, ctx.dt, ctx.m, g.contiguous())
-        return ub, None, None, None
+        u, theta = ctx.saved_tensors
+        ctx.solver.set_physics(_free_with(ctx.free, theta.cpu()))
+        ub, th = ctx.solver.step_backward(u, ctx.dt, ctx.m, g.contiguous(), with_theta=True)
+        return ub, torch.tensor(th, dtype=theta.dtype, device=theta.device), None, None, None, None
+
+
+class ProjectedState(torch.autograd.Function):
+    """u_0 = projection of the analytic state `kind` with params, under free stream theta."""
+
+    @staticmethod
+    def forward(ctx, theta, solver, free, kind, params):
+        solver.set_physics(_free_with(free, theta.detach().cpu()))
+        solver.project_state(kind, params)
+        u0 = solver.get_state(torch.empty(solver.K, dtype=torch.float64, device="cuda"))
+        ctx.save_for_backward(theta.detach())
+        ctx.solver, ctx.free, ctx.kind, ctx.params = solver, free, kind, list(params)
+        return u0
+
+    @staticmethod
+    def backward(ctx, g):
+        (theta,) = ctx.saved_tensors
+        ctx.solver.set_physics(_free_with(ctx.free, theta.cpu()))
+        th = ctx.solver.project_state_adjoint(ctx.kind, ctx.params, g.contiguous())
+        return torch.tensor(th[:2], dtype=theta.dtype, device=theta.device), None, None, None, None
 
 
 class WallForce(torch.autograd.Function):
@@ -68,11 +100,11 @@ class VortexError(torch.autograd.Function):
         return g * grad, None, None
 
 
-def rollout(u0, solver, dt, m, steps):
-    """u_N after ``steps`` PCEXP steps, differentiable with respect to u0."""
+def rollout(u0, theta, solver, free, dt, m, steps):
+    """u_N after ``steps`` PCEXP steps, differentiable with respect to u0 and theta."""
     u = u0
     for _ in range(steps):
-        u = PCEXPStep.apply(u, solver, dt, m)
+        u = PCEXPStep.apply(u, theta, solver, free, dt, m)
     return u
 
 
@@ -83,23 +115,18 @@ class AdjointResult:
     grad_params: dict
 
 
-def adjoint_rollout(solver, u0, dt, m, steps, kind=capi.PCEXP_FUNC_WALL_FX, params=None, initial_state=None,
-                    h=1e-6, functional_params=None, case_params=None):
-    """Value and gradients of J(u_N), u_{n+1} = PCEXP(u_n; theta).
+def adjoint_rollout(solver, u0, dt, m, steps, kind=capi.PCEXP_FUNC_WALL_FX, functional_params=None,
+                    initial=None):
+    """Value and gradients of J(u_N), u_{n+1} = PCEXP(u_n; theta), theta = (Mach, alpha).
 
-    grad_u0 is exact (reverse of every step).  For each free-stream parameter name in
-    ``params`` (attributes of the Freestream passed as ``params[name] = freestream``),
-    dJ/dtheta = sum_n ubar_{n+1} . dF/dtheta (u_n) + ubar_0 . du_0/dtheta, where the
-    partial of one step (and of the initial state ``initial_state(free)``) with respect
-    to theta is taken by a central difference of width h at fixed u_n.
-
-    ``functional_params`` are passed to the functional (PCEXP_FUNC_VORTEX_L2).
-    ``case_params`` = {name: (theta, init(theta) -> u0, fparams(theta) -> functional
-    parameters)} lists parameters that enter the initial state and the functional but
-    not the step map (the vortex strength): dJ/dtheta = ubar_0 . du_0/dtheta +
-    dJ/dtheta at fixed u_N, both partials by central differences of width h (relative
-    to max(1, |theta|)).
-    """
+    Forward steps keep their checkpoints u_n; the reverse sweep calls pcexp_step_backward
+    per step, which returns ubar_n and the step's adjoint of theta.  grad_params holds
+      mach, alpha_deg:  sum_n theta_bar_n (+ the initial state's and the functional's share),
+      eps (vortex functional and vortex initial state): the initial state's share plus the
+           functional's partial at fixed u_N.
+    ``initial`` = (kind, params) of the projected initial state u0 (its adjoint then
+    contributes); None leaves u0 as given.  ``functional_params`` are passed to the
+    functional (PCEXP_FUNC_VORTEX_L2)."""
     checkpoints = [u0.detach().contiguous()]
     u = checkpoints[0]
     for _ in range(steps):
@@ -109,34 +136,21 @@ def adjoint_rollout(solver, u0, dt, m, steps, kind=capi.PCEXP_FUNC_WALL_FX, para
         checkpoints.append(u)
     grad = torch.empty_like(u)
     value, _ = solver.functional(kind, u, grad, params=functional_params)
-    ubars = [None] * (steps + 1)
-    ubars[steps] = grad
+    theta = np.zeros(2)
+    ub = grad
     for n in range(steps - 1, -1, -1):
-        ubars[n] = solver.step_backward(checkpoints[n], float(dt), int(m), ubars[n + 1].contiguous())
+        ub, th = solver.step_backward(checkpoints[n], float(dt), int(m), ub.contiguous(), with_theta=True)
+        theta += th
     gp = {}
-    if params:
-        base_free = params["free"]
-        for name in params["names"]:
-            theta = getattr(base_free, name)
-            total = 0.0
-            for n in range(steps):
-                outs = []
-                for sgn in (1.0, -1.0):
-                    solver.set_physics(dataclasses.replace(base_free, **{name: theta + sgn * h}))
-                    solver.set_state(checkpoints[n])
-                    solver.step(capi.PCEXP_SCHEME_PCEXP, capi.PCEXP_DT_GIVEN, float(dt), int(m), info=False)
-                    outs.append(solver.get_state(torch.empty_like(u)))
-                total += float(torch.dot(ubars[n + 1], (outs[0] - outs[1]) / (2 * h)))
-            if initial_state is not None:
-                up = initial_state(dataclasses.replace(base_free, **{name: theta + h}))
-                um = initial_state(dataclasses.replace(base_free, **{name: theta - h}))
-                total += float(torch.dot(ubars[0], (up - um) / (2 * h)))
-            solver.set_physics(base_free)
-            gp[name] = total
-    for name, (theta, init, fparams) in (case_params or {}).items():
-        hh = h * max(1.0, abs(theta))
-        du0 = (init(theta + hh) - init(theta - hh)) / (2 * hh)
-        jp, _ = solver.functional(kind, u, None, params=fparams(theta + hh))
-        jm, _ = solver.functional(kind, u, None, params=fparams(theta - hh))
-        gp[name] = float(torch.dot(ubars[0], du0)) + (jp - jm) / (2 * hh)
-    return AdjointResult(value=value, grad_u0=ubars[0], grad_params=gp)
+    dJ = solver.functional_param_grad(kind, u, functional_params)
+    theta += dJ[:2]
+    eps = dJ[2]
+    if initial is not None:
+        t0 = solver.project_state_adjoint(initial[0], initial[1], ub.contiguous())
+        theta += t0[:2]
+        if len(t0) > 2:
+            eps += t0[2]
+    gp["mach"], gp["alpha_deg"] = float(theta[0]), float(theta[1])
+    if kind == capi.PCEXP_FUNC_VORTEX_L2 or (initial is not None and initial[0] == capi.PCEXP_PROJ_VORTEX):
+        gp["eps"] = float(eps)
+    return AdjointResult(value=value, grad_u0=ub, grad_params=gp)

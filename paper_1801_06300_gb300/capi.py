@@ -92,7 +92,9 @@ SIGNATURES = {
     "pcexp_phi": (C.c_int, [_P, _D, C.c_int, C.c_int, C.c_double, _D, _D]),
     "pcexp_step": (C.c_int, [_P, C.c_int, C.c_int, C.c_double, C.c_int, C.POINTER(pcexp_step_info)]),
     "pcexp_phi_adjoint": (C.c_int, [_P, _D, C.c_int, C.c_int, C.c_double, _D, _D]),
-    "pcexp_step_backward": (C.c_int, [_P, _P, C.c_double, C.c_int, _P, _P, C.c_int]),
+    "pcexp_step_backward": (C.c_int, [_P, _P, C.c_double, C.c_int, _P, _P, _D, C.c_int]),
+    "pcexp_project_state_adjoint": (C.c_int, [_P, C.c_int, _D, C.c_int, _P, _D, C.c_int]),
+    "pcexp_functional_param_grad": (C.c_int, [_P, C.c_int, _D, C.c_int, _P, _D, C.c_int]),
     "pcexp_march_steady": (C.c_int, [_P, C.c_int, C.c_double, C.c_double, C.c_int, C.c_int,
                                      C.POINTER(pcexp_steady_info)]),
     "pcexp_output": (C.c_int, [_P, C.c_int, _D]),
@@ -292,13 +294,37 @@ class Context:
                                          Hb.ctypes.data_as(_D)), "pcexp_phi_adjoint")
         return Hb
 
-    def step_backward(self, U, dt: float, m: int, ubar_next, out=None):
+    def step_backward(self, U, dt: float, m: int, ubar_next, out=None, with_theta: bool = False):
+        """ubar_n = (du_{n+1}/du_n)^T ubar_next; with_theta also returns the adjoint of
+        (Mach, alpha in degrees) of the step as a numpy array of 2."""
         out = (np.empty(self.K) if isinstance(U, np.ndarray) else U.new_empty(self.K)) if out is None else out
         pu, dev = _ptr(U)
         pg, _ = _ptr(ubar_next)
         po, _ = _ptr(out)
-        check(self.lib.pcexp_step_backward(self.ctx, pu, dt, m, pg, po, dev), "pcexp_step_backward")
-        return out
+        th = np.zeros(2)
+        check(self.lib.pcexp_step_backward(self.ctx, pu, dt, m, pg, po, th.ctypes.data_as(_D) if with_theta else None,
+                                           dev), "pcexp_step_backward")
+        return (out, th) if with_theta else out
+
+    def project_state_adjoint(self, kind: int, params, ubar0):
+        """(du_0/dtheta)^T ubar0 for theta = (Mach, alpha in degrees[, eps for the vortex])."""
+        prm = np.ascontiguousarray(params, np.float64)
+        pu, dev = _ptr(ubar0)
+        th = np.zeros(3)
+        check(self.lib.pcexp_project_state_adjoint(self.ctx, kind, prm.ctypes.data_as(_D) if prm.size else None,
+                                                   prm.size, pu, th.ctypes.data_as(_D), dev),
+              "pcexp_project_state_adjoint")
+        return th if kind == PCEXP_PROJ_VORTEX else th[:2]
+
+    def functional_param_grad(self, kind: int, U, params=None):
+        """dJ/d(Mach, alpha in degrees, eps) of an output functional at a fixed state U."""
+        prm = np.ascontiguousarray(params if params is not None else [], np.float64)
+        pu, dev = _ptr(U)
+        dj = np.zeros(3)
+        check(self.lib.pcexp_functional_param_grad(self.ctx, kind, prm.ctypes.data_as(_D) if prm.size else None,
+                                                   prm.size, pu, dj.ctypes.data_as(_D), dev),
+              "pcexp_functional_param_grad")
+        return dj
 
     def step(self, scheme: int, dt_mode: int, dt_or_cfl: float, m: int, info: bool = True):
         inf = pcexp_step_info()

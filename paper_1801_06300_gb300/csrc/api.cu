@@ -46,6 +46,7 @@ struct pcexp_ctx {
   void* GT = nullptr;                      // adjoint face scratch [F][nfq][2 nv]
   double* xq = nullptr;                    // physical volume points [E][nq][dim] (first vortex functional)
   double* diag = nullptr;                  // FP64 [Bv (nq nb) | Wv (nq) | sqrt|det A| (E)] (first entropy output)
+  double* pgrad = nullptr;                 // 4 doubles: sums of the functional-parameter gradient
   // ETD2 history (first ETD2 step): u_{n-1}, R_{n-1}, and R_n of the step in progress
   void *h_u = nullptr, *h_R = nullptr, *h_Rc = nullptr;
   bool etd2_prev = false;  // the history holds the previous ETD2 step of the current state
@@ -55,6 +56,7 @@ struct pcexp_ctx {
   double *b_t1 = nullptr, *b_t2 = nullptr, *b_ubn = nullptr, *b_ubs = nullptr, *b_db = nullptr, *b_bb = nullptr,
          *b_rb = nullptr, *b_gin = nullptr;
   double* b_small = nullptr;  // 2 MMAX^2 doubles: H and Hbar of pcexp_phi_adjoint
+  double* b_theta = nullptr;  // adjoint of (Mach, alpha in degrees) of the reverse step (2 doubles)
   KState* b_ks1 = nullptr;
   AdjState* b_as = nullptr;
   KState* ks = nullptr;
@@ -698,6 +700,90 @@ int project_host(pcexp_ctx* c, int kind, const double* prm, int np, std::vector<
   return PCEXP_OK;
 }
 
+// Forward-mode number with three derivative directions (Mach, alpha in degrees, eps) for the
+// exact derivative of the projected analytic states (host).
+struct Dual3 {
+  double v, d[3];
+};
+Dual3 dc(double x) { return {x, {0.0, 0.0, 0.0}}; }
+Dual3 operator+(Dual3 a, Dual3 b) { return {a.v + b.v, {a.d[0] + b.d[0], a.d[1] + b.d[1], a.d[2] + b.d[2]}}; }
+Dual3 operator-(Dual3 a, Dual3 b) { return {a.v - b.v, {a.d[0] - b.d[0], a.d[1] - b.d[1], a.d[2] - b.d[2]}}; }
+Dual3 operator*(Dual3 a, Dual3 b) {
+  return {a.v * b.v, {a.d[0] * b.v + a.v * b.d[0], a.d[1] * b.v + a.v * b.d[1], a.d[2] * b.v + a.v * b.d[2]}};
+}
+Dual3 operator*(double a, Dual3 b) { return {a * b.v, {a * b.d[0], a * b.d[1], a * b.d[2]}}; }
+Dual3 dpow(Dual3 x, double e) {
+  const double pv = std::pow(x.v, e), f = e * pv / x.v;
+  return {pv, {f * x.d[0], f * x.d[1], f * x.d[2]}};
+}
+
+// theta_bar = (du_0/dtheta)^T ubar for the states of project_host, theta = (Mach, alpha in
+// degrees, eps): the pointwise state formulas of project_host on Dual3 numbers, projected with
+// the same volume rule; ubar in the internal basis.
+int project_adjoint_host(pcexp_ctx* c, int kind, const double* prm, int np, const std::vector<double>& ubar,
+                         double tb[3]) {
+  const Setup& s = c->host;
+  const int D = c->dim, NV = c->nv;
+  const double g = c->phys.gamma;
+  const double cinf = std::sqrt(g * c->phys.p_inf / c->phys.rho_inf);
+  const Dual3 mach{c->phys.mach, {1.0, 0.0, 0.0}};
+  const Dual3 alpha{c->phys.alpha_deg * M_PI / 180.0, {0.0, M_PI / 180.0, 0.0}};
+  const Dual3 ca{std::cos(alpha.v), {0.0, -std::sin(alpha.v) * alpha.d[1], 0.0}};
+  const Dual3 sa{std::sin(alpha.v), {0.0, std::cos(alpha.v) * alpha.d[1], 0.0}};
+  const Dual3 u0 = cinf * (mach * ca), v0 = cinf * (mach * sa);
+  const double rinf = c->phys.rho_inf, pinf = c->phys.p_inf;
+  if (kind == PCEXP_PROJ_VORTEX && (np < 4 || (np >= 5 && !(prm[4] > 0)))) return PCEXP_ERR_INVALID_ARG;
+  if (kind == PCEXP_PROJ_BLOBS && (np < 1 || (np - 1) % 4)) return PCEXP_ERR_INVALID_ARG;
+  if (kind < 0 || kind > 2) return PCEXP_ERR_INVALID_ARG;
+  double acc[3] = {0.0, 0.0, 0.0};
+  for (int64_t e = 0; e < c->E; ++e) {
+    const double sd = s.geo[(D == 2 ? 8 : 12) * e + D * D];
+    for (int q = 0; q < c->nq; ++q) {
+      const double x = s.xqphys[(e * c->nq + q) * D], y = s.xqphys[(e * c->nq + q) * D + 1];
+      Dual3 rho = dc(rinf), uu = u0, vv = v0, p = dc(pinf);
+      if (kind == PCEXP_PROJ_VORTEX) {
+        const Dual3 eps{prm[0], {0.0, 0.0, 1.0}};
+        const double period = prm[3], rad = np >= 5 ? prm[4] : 1.0;
+        double dx = x - prm[1], dy = y - prm[2];
+        if (period > 0) {
+          dx -= period * std::nearbyint(dx / period);
+          dy -= period * std::nearbyint(dy / period);
+        }
+        dx /= rad;
+        dy /= rad;
+        const double r2 = dx * dx + dy * dy;
+        const Dual3 f = (std::exp(0.5 * (1 - r2)) / (2 * M_PI)) * eps;
+        uu = u0 - dy * f;
+        vv = v0 + dx * f;
+        const double Tinf = pinf / rinf;
+        const Dual3 T = dc(Tinf) - ((g - 1) / (8 * g * M_PI * M_PI) * std::exp(1 - r2)) * (eps * eps);
+        rho = rinf * dpow((1.0 / Tinf) * T, 1.0 / (g - 1));
+        p = rho * T;
+      } else if (kind == PCEXP_PROJ_BLOBS) {
+        const double R = prm[0];
+        double r = rinf, pp = pinf;
+        for (int b = 0; b < (np - 1) / 4; ++b) {
+          const double* bb = prm + 1 + 4 * b;
+          const double wgt = std::exp(-((x - bb[0]) * (x - bb[0]) + (y - bb[1]) * (y - bb[1])) / (R * R));
+          r += bb[2] * wgt;
+          pp += bb[3] * wgt;
+        }
+        rho = dc(r);
+        p = dc(pp);
+      }
+      Dual3 U[5] = {rho, rho * uu, rho * vv, dc(0.0), dc(0.0)};
+      U[NV - 1] = (1.0 / (g - 1)) * p + 0.5 * (rho * (uu * uu + vv * vv));
+      for (int v = 0; v < NV; ++v)
+        for (int j = 0; j < c->nb; ++j) {
+          const double w = sd * s.Wv[q] * s.Bv[q * c->nb + j] * ubar[(e * c->nv + v) * c->nb + j];
+          for (int k = 0; k < 3; ++k) acc[k] += w * U[v].d[k];
+        }
+    }
+  }
+  for (int k = 0; k < 3; ++k) tb[k] = acc[k];
+  return PCEXP_OK;
+}
+
 int UNSUPPORTED_FP32_HESS(pcexp_ctx*) {
   g_last_error = "the second-order adjoint is provided for the FP64 form";
   return PCEXP_ERR_UNSUPPORTED;
@@ -855,9 +941,31 @@ int alloc_backward(pcexp_ctx* c) {
   PCEXP_TRY(dalloc(c, &c->b_V1, Vn));
   PCEXP_TRY(dalloc(c, &c->b_Vb, Vn));
   PCEXP_TRY(dalloc(c, &c->b_small, (size_t)2 * MMAX * MMAX));
+  PCEXP_TRY(dalloc(c, &c->b_theta, 2));
   PCEXP_TRY(dalloc(c, &c->b_ks1, 1));
   PCEXP_TRY(dalloc(c, &c->b_as, 1));
   PCEXP_CK(cudaStreamSynchronize(c->st));
+  return PCEXP_OK;
+}
+
+// d(free-stream velocity)/d(Mach) and d/d(alpha in degrees), x and y components: the velocity
+// Ma c_inf (cos alpha, sin alpha) is the only place the two parameters enter the operator.
+void freestream_velocity_derivatives(const pcexp_physics& ph, double dvel[4]) {
+  const double a = ph.alpha_deg * M_PI / 180.0, cinf = std::sqrt(ph.gamma * ph.p_inf / ph.rho_inf);
+  dvel[0] = cinf * std::cos(a);
+  dvel[1] = cinf * std::sin(a);
+  dvel[2] = -ph.mach * cinf * std::sin(a) * M_PI / 180.0;
+  dvel[3] = ph.mach * cinf * std::cos(a) * M_PI / 180.0;
+}
+
+// theta_bar += (d(...)/dtheta)^T w for the reverse step: order 1 with u (R(u)), order 2 with
+// u and t (J(u) t), scaled by osc (and *osc_dev)
+int param_adjoint(pcexp_ctx* c, const DGData<double>& d, int order, const double* u, const double* t, const double* w,
+                  double osc, const double* osc_dev) {
+  double dvel[4];
+  freestream_velocity_derivatives(c->phys, dvel);
+  PCEXP_CK(launch_param_adjoint<double>(d, c->host.F_interior, order, u, t, w, osc, osc_dev, dvel, c->b_theta,
+                                        c->partials, &c->b_as->counter, c->st));
   return PCEXP_OK;
 }
 
@@ -875,13 +983,15 @@ int reverse_krylov(pcexp_ctx* c, const DGData<double>& d, const double* Z, const
     PCEXP_CK(launch_jvp_state_adjoint<double>(d, c->b_un, Z + (int64_t)j * Kp, c->b_wb0, c->b_t2, G, nullptr, 1.0,
                                               c->st));
     PCEXP_CK(launch_axpy(c->b_ubn, c->b_t2, &ks->s[j], 1.0, Kp, c->st));
+    // theta_bar += s_j (d(J(u_n; theta) z_j)/dtheta)^T w0bar
+    PCEXP_TRY(param_adjoint(c, d, 2, c->b_un, Z + (int64_t)j * Kp, c->b_wb0, 1.0, &ks->s[j]));
   }
   PCEXP_CK(launch_adj_bbar(Z, c->b_Vb, c->b_bb, Kp, ks, c->b_as, c->partials, c->st));
   return PCEXP_OK;
 }
 
 int step_backward_impl(pcexp_ctx* c, const double* U, double dt, int m, const double* ubar_next, double* ubar,
-                       int on_device) {
+                       double* theta_bar, int on_device) {
   PCEXP_TRY(alloc_backward(c));
   const DGData<double> d = dgdata<double>(c);
   const int64_t Kp = c->Kp;
@@ -919,6 +1029,7 @@ int step_backward_impl(pcexp_ctx* c, const double* U, double dt, int m, const do
   }
   const int k1 = h1.k, k2 = h2.k;
   // ---- reverse
+  PCEXP_CK(cudaMemsetAsync(c->b_theta, 0, 2 * sizeof(double), c->st));
   PCEXP_CK(cudaMemsetAsync(c->b_ubn, 0, vbytes, c->st));
   PCEXP_CK(cudaMemsetAsync(c->b_rb, 0, vbytes, c->st));
   PCEXP_CK(cudaMemsetAsync(c->b_db, 0, vbytes, c->st));
@@ -935,6 +1046,9 @@ int step_backward_impl(pcexp_ctx* c, const double* U, double dt, int m, const do
     PCEXP_CK(launch_jvp_state_adjoint<double>(d, c->b_un, c->b_dl, c->b_bb, c->b_t2, G, nullptr, 1.0, c->st));
     PCEXP_CK(launch_axpy(c->b_ubn, c->b_t2, nullptr, -1.0, Kp, c->st));
     PCEXP_CK(launch_axpy(c->b_rb, c->b_bb, nullptr, -1.0, Kp, c->st));
+    // theta_bar -= (d(J(u_n; theta) delta)/dtheta)^T bbar_2;  += (dR(u_*; theta)/dtheta)^T bbar_2
+    PCEXP_TRY(param_adjoint(c, d, 2, c->b_un, c->b_dl, c->b_bb, -1.0, nullptr));
+    PCEXP_TRY(param_adjoint(c, d, 1, c->b_us, nullptr, c->b_bb, 1.0, nullptr));
     PCEXP_TRY(linearize<double>(c, d, c->b_us));
     PCEXP_CK(launch_jac_adjoint<double>(d, lindata<double>(c), c->b_bb, c->b_t1, G, nullptr, 1.0, c->st));
     PCEXP_CK(launch_axpy(c->b_ubs, c->b_t1, nullptr, 1.0, Kp, c->st));
@@ -953,11 +1067,18 @@ int step_backward_impl(pcexp_ctx* c, const double* U, double dt, int m, const do
   // R_n = R(u_n)
   PCEXP_CK(launch_jac_adjoint<double>(d, lindata<double>(c), c->b_rb, c->b_t1, G, nullptr, 1.0, c->st));
   PCEXP_CK(launch_axpy(c->b_ubn, c->b_t1, nullptr, 1.0, Kp, c->st));
+  PCEXP_TRY(param_adjoint(c, d, 1, c->b_un, nullptr, c->b_rb, 1.0, nullptr));
   c->prof = prof;
   PCEXP_TRY(export_vec<double>(c, c->b_ubn, ubar, on_device));
   int aerr = 0;
+  double th[2] = {0.0, 0.0};
   PCEXP_CK(cudaMemcpyAsync(&aerr, &c->b_as->err, sizeof(int), cudaMemcpyDeviceToHost, c->st));
+  PCEXP_CK(cudaMemcpyAsync(th, c->b_theta, sizeof(th), cudaMemcpyDeviceToHost, c->st));
   PCEXP_CK(cudaStreamSynchronize(c->st));
+  if (theta_bar) {
+    theta_bar[0] = th[0];
+    theta_bar[1] = th[1];
+  }
   if (aerr) {
     g_last_error = "non-finite phi adjoint";
     return PCEXP_ERR_NONFINITE;
@@ -1183,6 +1304,65 @@ int pcexp_functional_params(pcexp_ctx* c, int kind, const double* params, int n_
   return PCEXP_OK;
 }
 
+int pcexp_functional_param_grad(pcexp_ctx* c, int kind, const double* params, int n_params, const double* U,
+                                double* dJ, int on_device) {
+  PCEXP_TRY(check_ctx(c));
+  if (!U || !dJ) return PCEXP_ERR_INVALID_ARG;
+  if (kind != PCEXP_FUNC_WALL_FX && kind != PCEXP_FUNC_WALL_FY && kind != PCEXP_FUNC_WALL_FZ &&
+      kind != PCEXP_FUNC_VORTEX_L2)
+    return PCEXP_ERR_INVALID_ARG;
+  if (kind == PCEXP_FUNC_VORTEX_L2 && (!params || n_params < 5)) return PCEXP_ERR_INVALID_ARG;
+  if (c->fp32) {
+    g_last_error = "output functionals are provided for the FP64 form";
+    return PCEXP_ERR_UNSUPPORTED;
+  }
+  dJ[0] = dJ[1] = dJ[2] = 0.0;
+  if (kind != PCEXP_FUNC_VORTEX_L2) return PCEXP_OK;  // the wall forces depend on U alone
+  double* a = reinterpret_cast<double*>(c->tmp);
+  const DGData<double> d = dgdata<double>(c);
+  PCEXP_TRY(import_vec<double>(c, U, on_device, a));
+  if (!c->xq) {
+    PCEXP_TRY(dalloc(c, &c->xq, c->host.xqphys.size()));
+    PCEXP_CK(cudaMemcpyAsync(c->xq, c->host.xqphys.data(), c->host.xqphys.size() * sizeof(double),
+                             cudaMemcpyHostToDevice, c->st));
+  }
+  if (!c->pgrad) PCEXP_TRY(dalloc(c, &c->pgrad, 4));
+  double dvel[4];
+  freestream_velocity_derivatives(c->phys, dvel);
+  PCEXP_CK(launch_vortex_param_grad<double>(d, a, c->xq, params, dvel, c->pgrad, c->partials, &c->ss->counter, c->st));
+  double out[4];
+  PCEXP_CK(cudaMemcpyAsync(out, c->pgrad, sizeof(out), cudaMemcpyDeviceToHost, c->st));
+  PCEXP_CK(cudaStreamSynchronize(c->st));
+  const double J = std::sqrt(out[0]);
+  if (!(J > 0)) {
+    g_last_error = "the vortex error is zero: its gradient is not defined";
+    return PCEXP_ERR_NONFINITE;
+  }
+  for (int k = 0; k < 3; ++k) dJ[k] = -out[1 + k] / J;
+  return PCEXP_OK;
+}
+
+int pcexp_project_state_adjoint(pcexp_ctx* c, int kind, const double* params, int n_params, const double* ubar0,
+                                double* theta_bar, int on_device) {
+  PCEXP_TRY(check_ctx(c));
+  if (!ubar0 || !theta_bar || (n_params > 0 && !params)) return PCEXP_ERR_INVALID_ARG;
+  if (c->fp32) {
+    g_last_error = "the projection adjoint is provided for the FP64 form";
+    return PCEXP_ERR_UNSUPPORTED;
+  }
+  double* a = reinterpret_cast<double*>(c->tmp);
+  PCEXP_TRY(import_vec<double>(c, ubar0, on_device, a));
+  std::vector<double> ub((size_t)c->K);
+  PCEXP_CK(cudaMemcpyAsync(ub.data(), a, c->K * sizeof(double), cudaMemcpyDeviceToHost, c->st));
+  PCEXP_CK(cudaStreamSynchronize(c->st));
+  double tb[3];
+  PCEXP_TRY(project_adjoint_host(c, kind, params, n_params, ub, tb));
+  theta_bar[0] = tb[0];
+  theta_bar[1] = tb[1];
+  if (kind == PCEXP_PROJ_VORTEX) theta_bar[2] = tb[2];
+  return PCEXP_OK;
+}
+
 int pcexp_functional(pcexp_ctx* c, int kind, const double* U, double* value, double* grad, int on_device) {
   if (kind == PCEXP_FUNC_VORTEX_L2) return PCEXP_ERR_INVALID_ARG;  // needs its parameters
   return pcexp_functional_params(c, kind, nullptr, 0, U, value, grad, on_device);
@@ -1201,7 +1381,7 @@ int pcexp_set_physics(pcexp_ctx* c, const pcexp_physics* phys) {
 }
 
 int pcexp_step_backward(pcexp_ctx* c, const double* U, double dt, int m, const double* ubar_next, double* ubar,
-                        int on_device) {
+                        double* theta_bar, int on_device) {
   PCEXP_TRY(check_ctx(c));
   if (!U || !ubar_next || !ubar || m < 1 || m > c->m_max || !(dt > 0) || !std::isfinite(dt))
     return PCEXP_ERR_INVALID_ARG;
@@ -1209,7 +1389,7 @@ int pcexp_step_backward(pcexp_ctx* c, const double* U, double dt, int m, const d
     g_last_error = "the reverse step is provided for the FP64 form";
     return PCEXP_ERR_UNSUPPORTED;
   }
-  return step_backward_impl(c, U, dt, m, ubar_next, ubar, on_device);
+  return step_backward_impl(c, U, dt, m, ubar_next, ubar, theta_bar, on_device);
 }
 
 int pcexp_phi_adjoint(pcexp_ctx* c, const double* H, int k, int ldh, double dt, const double* ybar, double* Hbar) {

@@ -507,13 +507,231 @@ __global__ void __launch_bounds__(32 * (D + 1), 4) elem_tan_kernel(DGData<float>
   }
 }
 
+// ---------------------------------- the same J v volume part as a pipelined persistent kernel
+// cp.async copies (global -> shared, no register staging), 4 or 16 bytes
+PCEXP_DEV void cp_async4(void* dst, const void* src) {
+  asm volatile("cp.async.ca.shared.global [%0], [%1], 4;" ::"r"((uint32_t)__cvta_generic_to_shared(dst)), "l"(src)
+               : "memory");
+}
+PCEXP_DEV void cp_async16(void* dst, const void* src) {
+  asm volatile("cp.async.cg.shared.global [%0], [%1], 16;" ::"r"((uint32_t)__cvta_generic_to_shared(dst)),
+               "l"(src)
+               : "memory");
+}
+PCEXP_DEV void cp_async_commit() { asm volatile("cp.async.commit_group;" ::: "memory"); }
+PCEXP_DEV void cp_async_wait_all() { asm volatile("cp.async.wait_all;" ::: "memory"); }
+
+// Shared-memory words of one stage of elem_tan_pipe_kernel<D, P>: u, u' rows, face fluxes,
+// geometry records and face slots of 32 elements.
+template <int D, int P> struct TanPipe {
+  using O = Ord<D, P>;
+  static constexpr int NBP = PADV<float, O::NB>;
+  static constexpr int UR0 = 2 * O::NV * NBP;
+  static constexpr int UROW = UR0 + (36 - UR0 % 32) % 32;
+  static constexpr int GREC = O::NF * O::NFQ * O::NV;
+  static constexpr int GROW = GREC | 1;
+  static constexpr int PST = O::NVB | 1;
+  static constexpr int SU = 32 * UROW, SG = 32 * GROW, SGEO = 32 * O::GEO, SEF = 32 * O::NF;
+  static constexpr int STAGE = SU + SG + SGEO + SEF;  // words (SGEO and SU keep 16-byte alignment)
+  static constexpr int PART = O::NF * 32 * PST;
+  static_assert(PART <= SU + SG, "partial sums reuse the consumed rows, not the geometry records");
+  static_assert(SU % 4 == 0 && SG % 4 == 0, "16-byte alignment of the geometry records");
+  static constexpr size_t BYTES = 2 * (size_t)STAGE * 4;
+};
+
+// Persistent form of elem_tan_kernel: a block of D+1 warps loops over tiles of 32 elements
+// (one per lane, same point and face split, same sums in the same order, so the results are
+// bit-identical).  While tile t is computed, tile t + gridDim.x is copied into the other
+// shared-memory stage by cp.async: its u, u' rows and geometry records at the start of the
+// tile, its face fluxes (gathered through its face slots, which are loaded into a register at
+// the start and are needed only then) after the volume loop.  The staging latency that stalls
+// the one-shot kernel is hidden behind a tile of compute.
+template <int D, int P>
+__global__ void __launch_bounds__(32 * (D + 1), 2) elem_tan_pipe_kernel(DGData<float> d, const float* __restrict__ u,
+                                                                     const float* __restrict__ du,
+                                                                     const float* __restrict__ G, float* __restrict__ out,
+                                                                     const float* __restrict__ escale,
+                                                                     const int* __restrict__ skip,
+                                                                     const double* __restrict__ oscale, int64_t ntiles) {
+  using O = Ord<D, P>;
+  using L = TanPipe<D, P>;
+  constexpr int NB = O::NB, NQ = O::NQ, NFQ = O::NFQ, NV = O::NV, NF = O::NF, NPERM = O::NPERM, GEO = O::GEO;
+  constexpr int NVB = O::NVB, QW = NF, NT = 32 * QW;
+  constexpr int NBP = L::NBP, UROW = L::UROW, GROW = L::GROW, PST = L::PST;
+  static_assert(!O::SMEM_BF, "tetrahedra read the trace tables through the read-only cache");
+  extern __shared__ __align__(16) float dsm[];
+  if (skip && *skip) return;
+  const int tid = threadIdx.x, lane = tid & 31, w = tid >> 5;
+  int64_t t = blockIdx.x;
+  if (t >= ntiles) return;
+  const float g = d.fs.gamma;
+  const float osc = oscale ? (float)*oscale : 1.f;
+
+  // copies of tile tt into stage S: u, u' rows (4-byte copies into padded rows), geometry
+  // records (16-byte copies); the face fluxes follow once the face slots are known
+  auto stage_rows = [&](int64_t tt, float* S) {
+    const int64_t e0 = tt * 32;
+    const int ne = (int)((d.E - e0) < 32 ? (d.E - e0) : 32);
+    float* su = S;
+    float* sgeo = S + L::SU + L::SG;
+    for (int i = tid; i < ne * NVB; i += NT) {
+      const int el = i / NVB, r = i - el * NVB, v = r / NB, j = r - v * NB;
+      cp_async4(su + el * UROW + v * NBP + j, u + e0 * NVB + i);
+      cp_async4(su + el * UROW + (NV + v) * NBP + j, du + e0 * NVB + i);
+    }
+    for (int i = tid; i < ne * (GEO / 4); i += NT) cp_async16(sgeo + 4 * i, d.geo + e0 * GEO + 4 * i);
+  };
+  auto stage_faces = [&](int64_t tt, float* S, int fs) {
+    const int64_t e0 = tt * 32;
+    const int ne = (int)((d.E - e0) < 32 ? (d.E - e0) : 32);
+    if (tid < ne * NF) {
+      int* sef = reinterpret_cast<int*>(S + L::SU + L::SG + L::SGEO);
+      sef[tid] = fs;
+      const int el = tid / NF, kf = tid - el * NF;
+      float* dst = S + L::SU + el * GROW + kf * NFQ * NV;
+      const float* src = G + (int64_t)slot_face<O>(fs) * NFQ * NV;
+#pragma unroll 5
+      for (int k = 0; k < NFQ * NV; ++k) cp_async4(dst + k, src + k);
+    }
+  };
+
+  // prologue: tile t into stage 0
+  {
+    stage_rows(t, dsm);
+    const int64_t e0 = t * 32;
+    const int ne = (int)((d.E - e0) < 32 ? (d.E - e0) : 32);
+    const int fs = tid < ne * NF ? d.ef[e0 * NF + tid] : 0;
+    stage_faces(t, dsm, fs);
+    cp_async_commit();
+    cp_async_wait_all();
+    __syncthreads();
+  }
+  for (int it = 0; t < ntiles; ++it, t += gridDim.x) {
+    float* S = dsm + (it & 1) * L::STAGE;
+    float* N = dsm + ((it & 1) ^ 1) * L::STAGE;
+    const int64_t e0 = t * 32;
+    const int ne = (int)((d.E - e0) < 32 ? (d.E - e0) : 32);
+    const int64_t tn = t + gridDim.x;
+    const bool has_next = tn < ntiles;
+    int fs_next = 0;
+    if (has_next) {
+      stage_rows(tn, N);
+      const int64_t en0 = tn * 32;
+      const int nen = (int)((d.E - en0) < 32 ? (d.E - en0) : 32);
+      if (tid < nen * NF) fs_next = d.ef[en0 * NF + tid];
+    }
+    const float* su = S;
+    const float* sg = S + L::SU;
+    const float* sgeo = S + L::SU + L::SG;
+    const int* sef = reinterpret_cast<const int*>(S + L::SU + L::SG + L::SGEO);
+    const int el = lane < ne ? lane : 0;  // lanes past the last element repeat element 0; discarded
+    const float* ge = sgeo + el * GEO;
+    float Ai[D * D];
+#pragma unroll
+    for (int k = 0; k < D * D; ++k) Ai[k] = ge[k];
+    const float isd = ge[O::ISD];
+    float acc[NV][NB];
+#pragma unroll
+    for (int v = 0; v < NV; ++v)
+#pragma unroll
+      for (int i = 0; i < NB; ++i) acc[v][i] = 0.f;
+    const float* ur = su + el * UROW;
+#pragma unroll 1
+    for (int q = w; q < NQ; q += QW) {
+      const float* bq = c_tan<D, P> + q * NB;
+      Tangent<float> U[NV];
+#pragma unroll
+      for (int v = 0; v < NV; ++v) {
+        float c[NBP];
+        load_row<float, NBP>(ur + v * NBP, c);
+        float a = 0.f;
+#pragma unroll
+        for (int j = 0; j < NB; ++j) a = fmaf(bq[j], c[j], a);
+        load_row<float, NBP>(ur + (NV + v) * NBP, c);
+        float tt = 0.f;
+#pragma unroll
+        for (int j = 0; j < NB; ++j) tt = fmaf(bq[j], c[j], tt);
+        U[v] = Tangent<float>{a * isd, tt * isd};
+        asm volatile("" ::: "memory");  // one variable's rows in flight at a time (registers)
+      }
+      Tangent<float> F[D][NV];
+      euler_flux<D, Tangent<float>, float>(U, g, F);
+      const float* dq = c_tan<D, P> + NQ * NB + q * NB;
+#pragma unroll
+      for (int dd = 0; dd < D; ++dd) {
+        float fh[NV];
+#pragma unroll
+        for (int v = 0; v < NV; ++v) {
+          float a = Ai[dd * D] * F[0][v].d;
+#pragma unroll
+          for (int k = 1; k < D; ++k) a += Ai[dd * D + k] * F[k][v].d;
+          fh[v] = a;
+        }
+#pragma unroll
+        for (int i = 0; i < NB; ++i) {
+          const float tq = dq[dd * NQ * NB + i];
+#pragma unroll
+          for (int v = 0; v < NV; ++v) acc[v][i] = fmaf(tq, fh[v], acc[v][i]);
+        }
+      }
+    }
+    // the next tile's face fluxes, now that its face slots have arrived
+    if (has_next) stage_faces(tn, N, fs_next);
+    cp_async_commit();
+    // faces: lift of the staged face fluxes, pre-scaled by 1/|det A| to share the accumulators
+    const float rdet = isd * isd;
+#pragma unroll 1
+    for (int kf = w; kf < NF; kf += QW) {
+      const int fs = sef[el * NF + kf];
+      const float sgn = slot_side(fs) ? rdet : -rdet;
+      const float* tb = d.BfP + ((kf * NPERM + slot_perm(fs)) * NFQ) * NBP;
+      const float* gr = sg + el * GROW + kf * NFQ * NV;
+#pragma unroll
+      for (int q = 0; q < NFQ; ++q) {
+        float row[NBP];
+        load_row<float, NBP, true>(tb + q * NBP, row);
+#pragma unroll
+        for (int v = 0; v < NV; ++v) {
+          const float gq = sgn * gr[q * NV + v];
+#pragma unroll
+          for (int i = 0; i < NB; ++i) acc[v][i] = fmaf(row[i], gq, acc[v][i]);
+        }
+      }
+    }
+    __syncthreads();  // the stage is consumed; the partial sums reuse it
+    float* part = S;
+    float* pr = part + (w * 32 + lane) * PST;
+#pragma unroll
+    for (int v = 0; v < NV; ++v)
+#pragma unroll
+      for (int i = 0; i < NB; ++i) pr[v * NB + i] = acc[v][i];
+    __syncthreads();
+    for (int o = tid; o < ne * NVB; o += NT) {
+      const int el2 = o / NVB, r = o - el2 * NVB;
+      float s = part[el2 * PST + r];
+#pragma unroll
+      for (int ww = 1; ww < QW; ++ww) s += part[(ww * 32 + el2) * PST + r];
+      float sc = sgeo[el2 * GEO + O::SD] * osc;
+      if (escale) sc *= escale[e0 + el2];
+      out[e0 * NVB + o] = s * sc;
+    }
+    cp_async_wait_all();
+    __syncthreads();  // next stage landed; this stage's partial sums are read
+  }
+}
+
 template <int D, int P>
 cudaError_t tan_tables_p(const DGData<float>& d, cudaStream_t st) {
   using O = Ord<D, P>;
-  // the kernel's occupancy is bound by registers and shared memory: ask for the largest carveout
-  const cudaError_t e = cudaFuncSetAttribute(elem_tan_kernel<D, P>, cudaFuncAttributePreferredSharedMemoryCarveout,
-                                             (int)cudaSharedmemCarveoutMaxShared);
+  // the kernels' occupancy is bound by registers and shared memory: ask for the largest carveout
+  cudaError_t e = cudaFuncSetAttribute(elem_tan_kernel<D, P>, cudaFuncAttributePreferredSharedMemoryCarveout,
+                                       (int)cudaSharedmemCarveoutMaxShared);
   if (e != cudaSuccess) return e;
+  if constexpr (D == 3) {
+    e = cudaFuncSetAttribute(elem_tan_pipe_kernel<D, P>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                             (int)TanPipe<D, P>::BYTES);
+    if (e != cudaSuccess) return e;
+  }
   return cudaMemcpyToSymbolAsync(c_tan<D, P>, d.Bv, sizeof(float) * (D + 1) * O::NQ * O::NB, 0,
                                  cudaMemcpyDeviceToDevice, st);
 }
@@ -814,9 +1032,19 @@ cudaError_t jac_apply_p(const DGData<T>& d, LinData<T> lin, const T* u_elem, con
   const int64_t eb = (d.E + O::ET - 1) / O::ET;
   if (u_elem) {
     if constexpr (std::is_same<T, float>::value && D == 3) {
-      if (d.E > 0)
-        elem_tan_kernel<D, P><<<(unsigned)((d.E + 31) / 32), 32 * (D + 1), 0, st>>>(d, u_elem, dv, G, out, escale,
-                                                                                       skip, oscale);
+      if (d.E > 0) {
+        // persistent: two blocks per SM (two 42 KB stages each), tiles of 32 elements
+        static int nsm = 0;
+        if (!nsm) {
+          int dev = 0;
+          cudaGetDevice(&dev);
+          if (cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess || nsm < 1) nsm = 152;
+        }
+        const int64_t ntiles = (d.E + 31) / 32;
+        const int64_t grid = ntiles < 2 * (int64_t)nsm ? ntiles : 2 * (int64_t)nsm;
+        elem_tan_pipe_kernel<D, P><<<(unsigned)grid, 32 * (D + 1), TanPipe<D, P>::BYTES, st>>>(
+            d, u_elem, dv, G, out, escale, skip, oscale, ntiles);
+      }
     } else {
       elem_kernel<T, D, P, true><<<(unsigned)eb, 256, 0, st>>>(d, u_elem, dv, G, out, escale, skip, oscale);
     }
@@ -1196,6 +1424,151 @@ cudaError_t jvp_state_adjoint_p(const DGData<T>& d, const T* u, const T* v, cons
   return cudaGetLastError();
 }
 
+// ------------------------------------------- adjoint with respect to the free stream
+// theta = (Mach number, flow angle in degrees) enters the operator only through the
+// free-stream velocity of the far-field ghost state.  For the far-field faces (indices >= f0)
+// this kernel adds to acc[0..1]
+//   order 1:  sum_q sum_v gbar_q[v] dF~_v/dtheta_k                       ((dR/dtheta)^T w)
+//   order 2:  sum_q sum_v gbar_q[v] d/dtheta_k (dF~_v/dU_L . t_L)          ((d(J t)/dtheta)^T w)
+// with gbar_q[v] = -osc |f| w_q / sqrt|det A_L| sum_i phi_i(x_q) w[e_L][v][i] (the transposed lift
+// of w, the face term of R at the L element) and t_L the trace of t.  Jet numbers seeded on
+// the velocity give the first derivatives, hyper-dual numbers (velocity seeds, tangent t_L)
+// the mixed second ones.  dvel = {dvel/dMach (D), dvel/dalpha (D)}.  osc_dev (nullable)
+// multiplies osc.  Fixed-order sum: per-block partials, the last block adds them to acc.
+template <class T, int D, int P, int ORDER>
+__global__ void __launch_bounds__(128) param_adjoint_kernel(DGData<T> d, int64_t f0, const T* __restrict__ u,
+                                                            const T* __restrict__ t, const T* __restrict__ w,
+                                                            double osc, const double* __restrict__ osc_dev,
+                                                            double dvm0, double dvm1, double dva0, double dva1,
+                                                            double* __restrict__ acc, double* __restrict__ partials,
+                                                            unsigned* counter) {
+  using O = Ord<D, P>;
+  constexpr int NB = O::NB, NFQ = O::NFQ, NV = O::NV, NPERM = O::NPERM, GEO = O::GEO;
+  __shared__ double red[2][4];
+  __shared__ bool last;
+  double a0 = 0.0, a1 = 0.0;
+  const double os = osc * (osc_dev ? *osc_dev : 1.0);
+  const int64_t n = (d.F - f0) * NFQ;
+  for (int64_t idx = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; idx < n; idx += (int64_t)gridDim.x * blockDim.x) {
+    const int64_t f = f0 + idx / NFQ;
+    const int q = (int)(idx % NFQ);
+    if (-d.fel[2 * f + 1] != PCEXP_BC_FARFIELD) continue;
+    const int eL = d.fel[2 * f];
+    const int fL = d.floc[f] & 0xff;
+    T nr[D];
+#pragma unroll
+    for (int k = 0; k < D; ++k) nr[k] = d.fgeo[4 * f + k];
+    const T isd = d.geo[GEO * (int64_t)eL + O::ISD];
+    const T* be = d.Bf + ((fL * NPERM) * NFQ + q) * NB;
+    const T wl = d.fgeo[4 * f + D] * d.Wf[q];
+    T uL[NV], tL[NV], gb[NV];
+#pragma unroll
+    for (int v = 0; v < NV; ++v) {
+      T a = 0, b = 0, c = 0;
+#pragma unroll
+      for (int j = 0; j < NB; ++j) {
+        const T bj = __ldg(be + j);
+        const int64_t o = (int64_t)eL * NV * NB + v * NB + j;
+        a += bj * u[o];
+        if (ORDER == 2) b += bj * t[o];
+        c += bj * w[o];
+      }
+      uL[v] = a * isd;
+      tL[v] = b * isd;
+      gb[v] = (T)(-os) * wl * isd * c;
+    }
+    const double dm[3] = {dvm0, dvm1, 0.0}, da[3] = {dva0, dva1, 0.0};
+    if constexpr (ORDER == 1) {
+      using J = Jet<T, 2>;
+      J L[NV], R[NV], F[NV], vi[3];
+#pragma unroll
+      for (int v = 0; v < NV; ++v) L[v] = Lift<J, T>::of(uL[v]);
+#pragma unroll
+      for (int k = 0; k < 3; ++k) {
+        vi[k].v = d.fs.vel[k];
+        vi[k].d[0] = (T)dm[k];
+        vi[k].d[1] = (T)da[k];
+      }
+      ghost_farfield_v<D, J, T>(L, nr, d.fs.gamma, d.fs.rho, d.fs.p, vi, R);
+      roe_flux<D, J, T>(L, R, nr, d.fs.gamma, F);
+#pragma unroll
+      for (int v = 0; v < NV; ++v) {
+        a0 += (double)gb[v] * (double)F[v].d[0];
+        a1 += (double)gb[v] * (double)F[v].d[1];
+      }
+    } else {
+      using H = HD<T, 2>;
+      H L[NV], R[NV], F[NV], vi[3];
+#pragma unroll
+      for (int v = 0; v < NV; ++v) {
+        L[v] = Lift<H, T>::of(uL[v]);
+        L[v].t = tL[v];
+      }
+#pragma unroll
+      for (int k = 0; k < 3; ++k) {
+        vi[k] = Lift<H, T>::of(d.fs.vel[k]);
+        vi[k].d[0] = (T)dm[k];
+        vi[k].d[1] = (T)da[k];
+      }
+      ghost_farfield_v<D, H, T>(L, nr, d.fs.gamma, d.fs.rho, d.fs.p, vi, R);
+      roe_flux<D, H, T>(L, R, nr, d.fs.gamma, F);
+#pragma unroll
+      for (int v = 0; v < NV; ++v) {
+        a0 += (double)gb[v] * (double)F[v].dt[0];
+        a1 += (double)gb[v] * (double)F[v].dt[1];
+      }
+    }
+  }
+  for (int o = 16; o > 0; o >>= 1) {
+    a0 += __shfl_xor_sync(0xffffffffu, a0, o);
+    a1 += __shfl_xor_sync(0xffffffffu, a1, o);
+  }
+  if ((threadIdx.x & 31) == 0) {
+    red[0][threadIdx.x >> 5] = a0;
+    red[1][threadIdx.x >> 5] = a1;
+  }
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    double b0 = 0, b1 = 0;
+    for (int ww = 0; ww < (int)(blockDim.x >> 5); ++ww) {
+      b0 += red[0][ww];
+      b1 += red[1][ww];
+    }
+    partials[2 * blockIdx.x] = b0;
+    partials[2 * blockIdx.x + 1] = b1;
+    __threadfence();
+    last = atomicAdd(counter, 1u) == gridDim.x - 1;
+  }
+  __syncthreads();
+  if (last && threadIdx.x == 0) {
+    double b0 = 0, b1 = 0;
+    for (unsigned i = 0; i < gridDim.x; ++i) {
+      b0 += __ldcg(partials + 2 * i);
+      b1 += __ldcg(partials + 2 * i + 1);
+    }
+    acc[0] += b0;
+    acc[1] += b1;
+    *counter = 0;
+  }
+}
+
+template <class T, int D, int P>
+cudaError_t param_adjoint_p(const DGData<T>& d, int64_t f0, int order, const T* u, const T* t, const T* w, double osc,
+                            const double* osc_dev, const double* dvel, double* acc, double* partials,
+                            unsigned* counter, cudaStream_t st) {
+  const int64_t n = (d.F - f0) * Ord<D, P>::NFQ;
+  if (n <= 0) return cudaSuccess;
+  int64_t g = (n + 127) / 128;
+  if (g > RED_BLOCKS) g = RED_BLOCKS;
+  if (order == 1)
+    param_adjoint_kernel<T, D, P, 1><<<(unsigned)g, 128, 0, st>>>(d, f0, u, t, w, osc, osc_dev, dvel[0], dvel[1],
+                                                                   dvel[2], dvel[3], acc, partials, counter);
+  else
+    param_adjoint_kernel<T, D, P, 2><<<(unsigned)g, 128, 0, st>>>(d, f0, u, t, w, osc, osc_dev, dvel[0], dvel[1],
+                                                                   dvel[2], dvel[3], acc, partials, counter);
+  return cudaGetLastError();
+}
+
 // ------------------------------------------------------------ output functionals
 // fixed-order sum of one double per thread into *value (last-block reduction)
 PCEXP_DEV void block_sum_last(double acc, double* value, double* partials, unsigned* counter, bool sqrt_out) {
@@ -1327,6 +1700,104 @@ __global__ void __launch_bounds__(256) vortex_error_kernel(DGData<T> d, const T*
   block_sum_last(acc, value, partials, counter, true);
 }
 
+// Partials of the vortex-error functional with respect to theta = (Mach, alpha in degrees,
+// eps) at a fixed state: out[0] = sum w_q |U_h - U_ex|^2 (= J^2), out[1 + k] = sum w_q
+// (U_h - U_ex) . dU_ex/dtheta_k, so dJ/dtheta_k = -out[1 + k] / J.  The exact state is
+// evaluated on Jet numbers seeded with the free-stream velocity derivatives (dvel: d/dMach
+// x, y, then d/dalpha x, y) and with eps.  Fixed-order last-block sums.
+template <class T, int D, int P>
+__global__ void __launch_bounds__(256) vortex_param_grad_kernel(DGData<T> d, const T* __restrict__ u,
+                                                                const double* __restrict__ xq, double eps, double xc,
+                                                                double yc, double period, double t, double dvm0,
+                                                                double dvm1, double dva0, double dva1,
+                                                                double* __restrict__ out, double* __restrict__ partials,
+                                                                unsigned* counter) {
+  using O = Ord<D, P>;
+  constexpr int NB = O::NB, NQ = O::NQ, NV = O::NV, GEO = O::GEO;
+  using J = Jet<double, 3>;
+  __shared__ double red[4][8];
+  __shared__ bool last;
+  double acc[4] = {0, 0, 0, 0};
+  const double g = (double)d.fs.gamma, rinf = (double)d.fs.rho, pinf = (double)d.fs.p;
+  const double Tinf = pinf / rinf, pi = 3.141592653589793238462643383279502884;
+  J u0, v0, ep;
+  u0.v = (double)d.fs.vel[0];
+  u0.d[0] = dvm0;
+  u0.d[1] = dva0;
+  u0.d[2] = 0.0;
+  v0.v = (double)d.fs.vel[1];
+  v0.d[0] = dvm1;
+  v0.d[1] = dva1;
+  v0.d[2] = 0.0;
+  ep.v = eps;
+  ep.d[0] = ep.d[1] = 0.0;
+  ep.d[2] = 1.0;
+  for (int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; e < d.E; e += (int64_t)gridDim.x * blockDim.x) {
+    const double sd = (double)d.geo[GEO * e + O::SD];
+    for (int q = 0; q < NQ; ++q) {
+      J dx = (xq[(e * NQ + q) * D] - xc) - u0 * t;
+      J dy = (xq[(e * NQ + q) * D + 1] - yc) - v0 * t;
+      if (period > 0) {
+        dx = dx - period * nearbyint(dx.v / period);
+        dy = dy - period * nearbyint(dy.v / period);
+      }
+      const J r2 = dx * dx + dy * dy;
+      const J fe = ep * (1.0 / (2 * pi)) * exp_s(0.5 * (1.0 - r2));
+      const J uu = u0 - fe * dy, vv = v0 + fe * dx;
+      const J Tv = Tinf - ((g - 1) / (8 * g * pi * pi)) * (ep * ep) * exp_s(1.0 - r2);
+      const J rho = rinf * pow_s(Tv * (1.0 / Tinf), 1.0 / (g - 1));
+      const J p = rho * Tv;
+      J Ue[NV];
+      Ue[0] = rho;
+      Ue[1] = rho * uu;
+      Ue[2] = rho * vv;
+      if (D == 3) Ue[3] = Lift<J, double>::of(0.0);
+      Ue[NV - 1] = p * (1.0 / (g - 1)) + 0.5 * rho * (uu * uu + vv * vv);
+      const double wq = (double)d.Wv[q] * sd * sd;
+      for (int c = 0; c < NV; ++c) {
+        double a = 0;
+        for (int j = 0; j < NB; ++j) a += (double)d.Bv[q * NB + j] * (double)u[e * NV * NB + c * NB + j];
+        const double diff = a / sd - Ue[c].v;
+        acc[0] += wq * diff * diff;
+        for (int k = 0; k < 3; ++k) acc[1 + k] += wq * diff * Ue[c].d[k];
+      }
+    }
+  }
+  for (int k = 0; k < 4; ++k) {
+    for (int o = 16; o > 0; o >>= 1) acc[k] += __shfl_xor_sync(0xffffffffu, acc[k], o);
+    if ((threadIdx.x & 31) == 0) red[k][threadIdx.x >> 5] = acc[k];
+  }
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    for (int k = 0; k < 4; ++k) {
+      double b = 0;
+      for (int w = 0; w < (int)(blockDim.x >> 5); ++w) b += red[k][w];
+      partials[4 * blockIdx.x + k] = b;
+    }
+    __threadfence();
+    last = atomicAdd(counter, 1u) == gridDim.x - 1;
+  }
+  __syncthreads();
+  if (last && threadIdx.x == 0) {
+    for (int k = 0; k < 4; ++k) {
+      double b = 0;
+      for (unsigned i = 0; i < gridDim.x; ++i) b += __ldcg(partials + 4 * i + k);
+      out[k] = b;
+    }
+    *counter = 0;
+  }
+}
+
+template <class T, int D, int P>
+cudaError_t vortex_param_grad_p(const DGData<T>& d, const T* u, const double* xq, const double* prm, const double* dvel,
+                                double* out, double* partials, unsigned* counter, cudaStream_t st) {
+  int64_t nb = (d.E + 255) / 256;
+  if (nb > RED_BLOCKS / 2) nb = RED_BLOCKS / 2;
+  vortex_param_grad_kernel<T, D, P><<<(unsigned)(nb < 1 ? 1 : nb), 256, 0, st>>>(
+      d, u, xq, prm[0], prm[1], prm[2], prm[3], prm[4], dvel[0], dvel[1], dvel[2], dvel[3], out, partials, counter);
+  return cudaGetLastError();
+}
+
 // ------------------------------------------------------------------ time step
 // dt_e = CFL h_e / ((2p+1)(|v| + c)) with v, c at the element centroid (Eq. x3d).
 template <class T, int D, int P>
@@ -1428,6 +1899,13 @@ cudaError_t launch_jvp_state_adjoint_d(const DGData<T>& d, const T* u, const T* 
   PCEXP_PSWITCH(D, (jvp_state_adjoint_p<T, D, P_>(d, u, v, w, out, GT, escale, osc, st)))
 }
 
+template <class T, int D>
+cudaError_t launch_param_adjoint_d(const DGData<T>& d, int64_t f0, int order, const T* u, const T* t, const T* w,
+                                   double osc, const double* osc_dev, const double* dvel, double* acc,
+                                   double* partials, unsigned* counter, cudaStream_t st) {
+  PCEXP_PSWITCH(D, (param_adjoint_p<T, D, P_>(d, f0, order, u, t, w, osc, osc_dev, dvel, acc, partials, counter, st)))
+}
+
 template <class T, int D, int P>
 cudaError_t wall_force_p(const DGData<T>& d, int64_t f0, const T* u, double ax, double ay, double az, double* grad,
                          double* value, double* partials, unsigned* counter, cudaStream_t st) {
@@ -1457,6 +1935,13 @@ template <class T, int D>
 cudaError_t launch_vortex_error_d(const DGData<T>& d, const T* u, const double* xq, const double* prm, double* grad,
                                   double* value, double* partials, unsigned* counter, cudaStream_t st) {
   PCEXP_PSWITCH(D, (vortex_error_p<T, D, P_>(d, u, xq, prm, grad, value, partials, counter, st)))
+}
+
+template <class T, int D>
+cudaError_t launch_vortex_param_grad_d(const DGData<T>& d, const T* u, const double* xq, const double* prm,
+                                       const double* dvel, double* out, double* partials, unsigned* counter,
+                                       cudaStream_t st) {
+  PCEXP_PSWITCH(D, (vortex_param_grad_p<T, D, P_>(d, u, xq, prm, dvel, out, partials, counter, st)))
 }
 
 template <class T, int D, int P>
@@ -1491,6 +1976,11 @@ cudaError_t launch_local_dt_d(const DGData<T>& d, const T* u, const double* cfl_
   template cudaError_t launch_vortex_error_d<T, D>(const DGData<T>&, const T*, const double*, const double*,       \
                                                    double*, double*, double*, unsigned*, cudaStream_t);            \
   template cudaError_t launch_local_dt_d<T, D>(const DGData<T>&, const T*, const double*, double, T*, double*,     \
-                                               double*, unsigned*, cudaStream_t);
+                                               double*, unsigned*, cudaStream_t);                                  \
+  template cudaError_t launch_vortex_param_grad_d<T, D>(const DGData<T>&, const T*, const double*, const double*,   \
+                                                        const double*, double*, double*, unsigned*, cudaStream_t); \
+  template cudaError_t launch_param_adjoint_d<T, D>(const DGData<T>&, int64_t, int, const T*, const T*, const T*,  \
+                                                    double, const double*, const double*, double*, double*,        \
+                                                    unsigned*, cudaStream_t);
 
 }  // namespace pcexp

@@ -114,6 +114,14 @@ template <class T, int D>
 cudaError_t launch_vortex_error_d(const DGData<T>& d, const T* u, const double* xq, const double* prm, double* grad,
                                   double* value, double* partials, unsigned* counter, cudaStream_t st);
 template <class T, int D>
+cudaError_t launch_param_adjoint_d(const DGData<T>& d, int64_t f0, int order, const T* u, const T* t, const T* w,
+                                   double osc, const double* osc_dev, const double* dvel, double* acc,
+                                   double* partials, unsigned* counter, cudaStream_t st);
+template <class T, int D>
+cudaError_t launch_vortex_param_grad_d(const DGData<T>& d, const T* u, const double* xq, const double* prm,
+                                       const double* dvel, double* out, double* partials, unsigned* counter,
+                                       cudaStream_t st);
+template <class T, int D>
 cudaError_t launch_local_dt_d(const DGData<T>& d, const T* u, const double* cfl_dev, double cfl, T* dte,
                               double* dtmin, double* partials, unsigned* counter, cudaStream_t st);
 
@@ -191,6 +199,25 @@ cudaError_t launch_local_dt(const DGData<T>& d, const T* u, const double* cfl_de
                             T* dte, double* dtmin, double* partials, unsigned* counter, cudaStream_t st) {
   return d.dim == 3 ? launch_local_dt_d<T, 3>(d, u, cfl_dev, cfl, dte, dtmin, partials, counter, st)
                     : launch_local_dt_d<T, 2>(d, u, cfl_dev, cfl, dte, dtmin, partials, counter, st);
+}
+// acc[0..1] += adjoint with respect to (Mach, alpha in degrees) of the far-field faces (index >= f0):
+// order 1: (dR(u)/dtheta)^T w; order 2: (d(J(u) t)/dtheta)^T w; both times osc (and *osc_dev).
+// dvel: d(free-stream velocity)/dMach (x, y), then d/dalpha (x, y).
+template <class T>
+cudaError_t launch_param_adjoint(const DGData<T>& d, int64_t f0, int order, const T* u, const T* t, const T* w,
+                                 double osc, const double* osc_dev, const double* dvel, double* acc, double* partials,
+                                 unsigned* counter, cudaStream_t st) {
+  return d.dim == 3 ? launch_param_adjoint_d<T, 3>(d, f0, order, u, t, w, osc, osc_dev, dvel, acc, partials, counter, st)
+                    : launch_param_adjoint_d<T, 2>(d, f0, order, u, t, w, osc, osc_dev, dvel, acc, partials, counter, st);
+}
+// out[0] = sum w |U_h - U_ex|^2, out[1..3] = sum w (U_h - U_ex) . dU_ex/d(Mach, alpha, eps) for the
+// vortex-error functional (prm: eps, x_c, y_c, period, t; dvel as for launch_param_adjoint)
+template <class T>
+cudaError_t launch_vortex_param_grad(const DGData<T>& d, const T* u, const double* xq, const double* prm,
+                                     const double* dvel, double* out, double* partials, unsigned* counter,
+                                     cudaStream_t st) {
+  return d.dim == 3 ? launch_vortex_param_grad_d<T, 3>(d, u, xq, prm, dvel, out, partials, counter, st)
+                    : launch_vortex_param_grad_d<T, 2>(d, u, xq, prm, dvel, out, partials, counter, st);
 }
 // ---- dimension-free kernels (dg_common.cu)
 // basis conversions at the interface (Q_e: paper <- internal)

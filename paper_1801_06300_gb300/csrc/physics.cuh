@@ -155,6 +155,14 @@ template <class T, int N> PCEXP_DEV Jet<T, N> pow_s(const Jet<T, N>& x, T e) {
   for (int k = 0; k < N; ++k) r.d[k] = f * x.d[k];
   return r;
 }
+PCEXP_DEV double exp_s(double x) { return exp(x); }
+template <class T, int N> PCEXP_DEV Jet<T, N> exp_s(const Jet<T, N>& x) {
+  Jet<T, N> r;
+  r.v = exp(x.v);
+#pragma unroll
+  for (int k = 0; k < N; ++k) r.d[k] = r.v * x.d[k];
+  return r;
+}
 template <class S, class T> struct Lift {
   PCEXP_DEV static S of(T x) { return S(x); }
 };
@@ -429,6 +437,52 @@ PCEXP_DEV void ghost_farfield(const S (&U)[D + 2], const T (&n)[D], const Free<T
 #pragma unroll
   for (int d = 0; d < D; ++d) {
     const S vt = select_s(out, vel[d] - qn * n[d], Lift<S, T>::of(fs.vel[d] - qinf * n[d]));
+    const S vb = vt + qb * n[d];
+    G[1 + d] = rb * vb;
+    kb = kb + vb * vb;
+  }
+  G[NV - 1] = pb / gm + T(0.5) * rb * kb;
+}
+
+// The far-field ghost state of ghost_farfield with the free-stream velocity as a scalar of
+// type S, for derivatives with respect to the free stream (the Mach number and the flow
+// angle enter the scheme only through this velocity).  Same arithmetic, operation by
+// operation, as ghost_farfield.
+template <int D, class S, class T>
+PCEXP_DEV void ghost_farfield_v(const S (&U)[D + 2], const T (&n)[D], T g, T rho_inf, T p_inf, const S (&vinf)[3],
+                                S (&G)[D + 2]) {
+  constexpr int NV = D + 2;
+  const T gm = g - T(1);
+  const S ir = T(1) / U[0];
+  S vel[D];
+#pragma unroll
+  for (int d = 0; d < D; ++d) vel[d] = U[1 + d] * ir;
+  S ke = U[1] * vel[0];
+#pragma unroll
+  for (int d = 1; d < D; ++d) ke = ke + U[1 + d] * vel[d];
+  const S p = gm * (U[NV - 1] - T(0.5) * ke);
+  const S c = sqrt_s(g * p * ir);
+  const S qn = dot_n<D>(vel, n);
+  const T cinf = sqrt_s(g * p_inf / rho_inf);
+  S qinf = vinf[0] * n[0];
+#pragma unroll
+  for (int d = 1; d < D; ++d) qinf = qinf + vinf[d] * n[d];
+  const T mn = val(qn) / val(c);
+  const S rp = select_s(mn > T(-1), qn + T(2) * c / gm, qinf + T(2) * cinf / gm);
+  const S rm = select_s(mn < T(1), qinf - T(2) * cinf / gm, qn - T(2) * c / gm);
+  const S qb = T(0.5) * (rp + rm);
+  const S cb = T(0.25) * gm * (rp - rm);
+  const bool out = val(qb) >= T(0);
+  const S s_in = p / pow_s(U[0], g);
+  const T s_inf = p_inf / pow_s(rho_inf, g);
+  const S sb = select_s(out, s_in, Lift<S, T>::of(s_inf));
+  const S rb = pow_s(cb * cb / (g * sb), T(1) / gm);
+  const S pb = rb * cb * cb / g;
+  S kb = Lift<S, T>::of(T(0));
+  G[0] = rb;
+#pragma unroll
+  for (int d = 0; d < D; ++d) {
+    const S vt = select_s(out, vel[d] - qn * n[d], vinf[d] - qinf * n[d]);
     const S vb = vt + qb * n[d];
     G[1 + d] = rb * vb;
     kb = kb + vb * vb;

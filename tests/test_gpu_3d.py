@@ -232,7 +232,7 @@ def test_vortex3d_strength_gradient_small(capi):
     T = steps * dt
     fparams = lambda eps: [eps, xc, yc, 10.0, T]  # noqa: E731
     res = adjoint_rollout(ctx, u0, dt, m, steps, kind=capi.PCEXP_FUNC_VORTEX_L2,
-                          functional_params=fparams(eps0), case_params={"eps": (eps0, init, fparams)}, h=1e-5)
+                          functional_params=fparams(eps0), initial=(capi.PCEXP_PROJ_VORTEX, [eps0, xc, yc, 10.0]))
 
     def J(x, eps):
         u = x

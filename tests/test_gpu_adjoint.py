@@ -202,9 +202,10 @@ def test_autograd_rollout_gradient(capi):
     ctx = capi.Context(mesh, 1, free, capi.PCEXP_FP64, m_max=m)
     u0 = state(dg, 51, 0.02)
     x = torch.tensor(u0, device="cuda", requires_grad=True)
+    theta = torch.tensor([free.mach, free.alpha_deg], dtype=torch.float64, device="cuda")
     u = x
     for _ in range(steps):
-        u = PCEXPStep.apply(u, ctx, dt, m)
+        u = PCEXPStep.apply(u, theta, ctx, free, dt, m)
     J = WallForce.apply(u, ctx, capi.PCEXP_FUNC_WALL_FX)
     J.backward()
     g = x.grad.cpu().numpy()
@@ -227,11 +228,12 @@ def test_autograd_rollout_gradient(capi):
 
 
 def test_freestream_parameter_gradients(capi):
-    """dJ/dMach and dJ/dalpha from the adjoint rollout against central differences of the
-    whole GPU rollout (initial state = projected free stream of the same parameters)."""
+    """dJ/dMach and dJ/dalpha from the adjoint rollout (library reverse steps with their
+    theta adjoint, the projection adjoint of the initial state) against central differences
+    of the whole GPU rollout, and the same gradient through torch.autograd."""
     torch = pytest.importorskip("torch")
     import dataclasses
-    from paper_1801_06300_gb300.autograd import adjoint_rollout
+    from paper_1801_06300_gb300.autograd import PCEXPStep, ProjectedState, WallForce, adjoint_rollout
     mesh, free = W.bump_channel(8, 4, 0.15, 1), W.Freestream(0.5, 2.0)
     dt, m, steps = 0.02, 10, 3
     ctx = capi.Context(mesh, 1, free, capi.PCEXP_FP64, m_max=m)
@@ -242,8 +244,7 @@ def test_freestream_parameter_gradients(capi):
         return ctx.get_state(torch.empty(ctx.K, dtype=torch.float64, device="cuda"))
 
     u0 = u_init(free)
-    res = adjoint_rollout(ctx, u0, dt, m, steps, params={"free": free, "names": ["mach", "alpha_deg"]},
-                          initial_state=u_init)
+    res = adjoint_rollout(ctx, u0, dt, m, steps, initial=(capi.PCEXP_PROJ_FREESTREAM, []))
 
     def J_of(fr):
         u = u_init(fr)
@@ -257,4 +258,53 @@ def test_freestream_parameter_gradients(capi):
         th = getattr(free, name)
         fd = (J_of(dataclasses.replace(free, **{name: th + h})) - J_of(dataclasses.replace(free, **{name: th - h}))) / (2 * h)
         assert abs(res.grad_params[name] - fd) <= 1e-4 * abs(fd) + 1e-12, (name, res.grad_params[name], fd)
+    # torch.autograd: theta as a leaf through the projection, the steps and the functional
+    theta = torch.tensor([free.mach, free.alpha_deg], dtype=torch.float64, device="cuda", requires_grad=True)
+    u = ProjectedState.apply(theta, ctx, free, capi.PCEXP_PROJ_FREESTREAM, [])
+    for _ in range(steps):
+        u = PCEXPStep.apply(u, theta, ctx, free, dt, m)
+    WallForce.apply(u, ctx, capi.PCEXP_FUNC_WALL_FX).backward()
+    g = theta.grad.cpu().numpy()
+    assert abs(g[0] - res.grad_params["mach"]) <= 1e-10 * abs(g[0])
+    assert abs(g[1] - res.grad_params["alpha_deg"]) <= 1e-10 * abs(g[1])
+    ctx.close()
+
+
+def test_rollout_gradients_match_oracle_complex_step(capi):
+    """The whole gradient of J(u_N) (wall force after 3 PCEXP steps on a 8 x 4 bump, P1,
+    m = 10, from the projected free stream plus a fixed perturbation) against the oracle's
+    complex step through the same rollout: a state direction of u_0, the Mach number and the
+    flow angle (the far-field ghost state in every R and J v, and the initial state)."""
+    torch = pytest.importorskip("torch")
+    import dataclasses
+    from oracle import pcexp
+    from oracle.cases import freestream_state
+    from oracle.dg import DGOracle
+    from paper_1801_06300_gb300.autograd import adjoint_rollout
+    mesh, free = W.bump_channel(8, 4, 0.15, 1), W.Freestream(0.5, 2.0)
+    dt, m, steps = 0.02, 10, 3
+    pert = 0.03 * W.random_coeffs(5, (mesh.n_elem * 4 * 3,))
+
+    def J_oracle(fr, du=None):
+        dg = DGOracle(mesh, 1, fr)
+        u = dg.project(lambda x: freestream_state(x, fr)).reshape(-1) + pert
+        if du is not None:
+            u = u + du
+        for _ in range(steps):
+            u, _ = pcexp.pcexp_step(u, dg.residual, dg.jvp, dt, m)
+        return dg.wall_force(u, (1.0, 0.0))
+
+    ctx = capi.Context(mesh, 1, free, capi.PCEXP_FP64, m_max=m)
+    ctx.project_state(capi.PCEXP_PROJ_FREESTREAM)
+    u0 = ctx.get_state(torch.empty(ctx.K, dtype=torch.float64, device="cuda")) + torch.tensor(pert, device="cuda")
+    res = adjoint_rollout(ctx, u0, dt, m, steps, initial=(capi.PCEXP_PROJ_FREESTREAM, []))
+    assert abs(res.value - float(np.real(J_oracle(free)))) <= 1e-10 * abs(res.value)
+    h = 1e-30
+    delta = W.random_coeffs(6, (ctx.K,))
+    cs_u = np.imag(J_oracle(free, 1j * h * delta)) / h
+    assert abs(float(torch.dot(res.grad_u0, torch.tensor(delta, device="cuda"))) - cs_u) <= 1e-8 * abs(cs_u)
+    for name in ("mach", "alpha_deg"):
+        th = getattr(free, name)
+        cs = np.imag(J_oracle(dataclasses.replace(free, **{name: th + 1j * h}))) / h
+        assert abs(res.grad_params[name] - cs) <= 1e-8 * abs(cs), (name, res.grad_params[name], cs)
     ctx.close()

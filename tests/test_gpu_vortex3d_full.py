@@ -152,7 +152,7 @@ def test_vortex3d_full_strength_gradient(capi, case):
     fparams = lambda eps: [eps, xc, yc, 10.0, T]  # noqa: E731
     t0 = time.time()
     res = adjoint_rollout(ctx, u0, dt, case.m, steps, kind=capi.PCEXP_FUNC_VORTEX_L2,
-                          functional_params=fparams(eps0), case_params={"eps": (eps0, init, fparams)}, h=1e-8)
+                          functional_params=fparams(eps0), initial=(capi.PCEXP_PROJ_VORTEX, [eps0, xc, yc, 10.0]))
     t_adj = time.time() - t0
 
     def J(x, eps):

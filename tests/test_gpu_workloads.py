@@ -49,8 +49,8 @@ def test_bump_adjoint_full_size(capi):
     dt = ctx.compute_dt(case.cfl)  # held constant over the run
     steps = case.steps
     t0 = time.time()
-    res = adjoint_rollout(ctx, u0, dt, m, steps, params={"free": free, "names": ["mach", "alpha_deg"]},
-                          initial_state=u_init)
+    ctx.set_physics(free)
+    res = adjoint_rollout(ctx, u0, dt, m, steps, initial=(capi.PCEXP_PROJ_BLOBS, params))
     t_adj = time.time() - t0
 
     def J_of(x, fr=free):
