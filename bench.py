@@ -171,17 +171,22 @@ def algorithmic_bytes(kind, T, K, E, F, dim, p, m, face_jacobians=True):
     }.get(kind)
 
 
-def algorithmic_flops(kind, K, E, F, dim, p, m):
+def algorithmic_flops(kind, K, E, F, dim, p, m, T=8):
     """Floating-point operations per launch of a kernel class (an FMA counts 2).
 
-    jvp_elem: per element, nq points x (trace nv nb + Jacobian d nv^2) FMA and nv nb outputs x
-    (volume d nq + lift nf nfq) FMA; jvp_face: per face point 2 nv nb trace + 2 nv^2 FMA;
-    CGS kernels: per unknown and column, 1 (projection) or 2 (update + projection) FMA,
-    averaged over the columns of one Arnoldi process."""
+    jvp_elem, FP64 (stored point Jacobians): per element, nq points x (trace nv nb + Jacobian
+    d nv^2) FMA and nv nb outputs x (volume d nq + lift nf nfq) FMA.  FP32-mixed (flux
+    tangents): nq points x (traces of u_n and v, 2 nv nb; mapping of the flux tangent to
+    reference directions, d^2 nv) FMA and the same test and lift; the Euler-flux tangent itself
+    (a few hundred operations per point) is not counted, so the fraction is a lower bound.
+    jvp_face: per face point 2 nv nb trace + 2 nv^2 FMA; CGS kernels: per unknown and column,
+    1 (projection) or 2 (update + projection) FMA, averaged over the columns of one Arnoldi
+    process."""
     nb, nq, nfq, nv, nf = shape(dim, p)
     nc = (m + 1) / 2.0
+    vol = nq * (nv * nb + dim * nv * nv) if T == 8 else nq * (2 * nv * nb + dim * dim * nv)
     fma = {
-        "jvp_elem": E * (nq * (nv * nb + dim * nv * nv) + nv * nb * (dim * nq + nf * nfq)),
+        "jvp_elem": E * (vol + nv * nb * (dim * nq + nf * nfq)),
         "jvp_face": F * nfq * (2 * nv * nb + 2 * nv * nv),
         "cgs_proj": K * (nc + 1),
         "cgs_upd_proj": K * 2 * nc,
@@ -204,11 +209,21 @@ def fp64_peak(capi):
         return 152 * 2 * 2 * 2.070e9 / 1e12, "derived: 152 SMs x 2 DFMA/clk x 2 x 2.07 GHz"
 
 
-def roofline_entry(prof, T, K, E, F, hbm, peak_kind, dim, p, m, workload, fp64=None, face_jacobians=True):
-    """Roofline of the dominant kernel class by device time.  FP32 kernels against the
-    measured HBM copy rate (GB/s); FP64 kernels against the FP64 pipe (alu, TFLOP/s) with
-    their HBM fraction beside it.  Adds the whole J v application (face + element time)
-    against the three-K-pass minimum."""
+def fp32_peak(capi):
+    """Measured FP32 FMA rate (TFLOP/s) of this GPU from the library's FFMA-chain kernel."""
+    try:
+        return capi.fp32_fma_rate(), "measured: FFMA chains on every SM, CUDA events"
+    except Exception:
+        return 152 * 128 * 2 * 2.070e9 / 1e12, "derived: 152 SMs x 128 FFMA/clk x 2 x 2.07 GHz"
+
+
+def roofline_entry(prof, T, K, E, F, hbm, peak_kind, dim, p, m, workload, fp64=None, face_jacobians=True,
+                   fp32=None):
+    """Roofline of the dominant kernel class by device time, against the roof that bounds it:
+    the one with the longer minimum time, algorithmic bytes at the measured HBM copy rate or
+    algorithmic flops at the measured FMA rate of its precision (FP64 pipe for FP64 kernels,
+    FP32 FMA for FP32 ones).  Both fractions are given.  Adds the whole J v application
+    (face + element time) against the three-K-pass minimum."""
     dom = max(prof, key=lambda k: prof[k][1])
     n_dom, ms_dom = prof[dom]
     if not n_dom:
@@ -223,17 +238,23 @@ def roofline_entry(prof, T, K, E, F, hbm, peak_kind, dim, p, m, workload, fp64=N
     ab = algorithmic_bytes(dom, T, K, E, F, dim, p, m, face_jacobians)
     if ab is not None:
         entry["algorithmic_bytes_per_launch"] = ab
-    fl = algorithmic_flops(dom, K, E, F, dim, p, m)
-    if T == 8 and fl is not None and fp64 is not None:
+    fl = algorithmic_flops(dom, K, E, F, dim, p, m, T)
+    alu = fp64 if T == 8 else fp32
+    t_alu = fl / (alu[0] * 1e12) if fl is not None and alu is not None else 0.0
+    t_hbm = ab / (hbm * 1e9) if ab is not None else 0.0
+    if t_alu > t_hbm:
         ach = fl / sec / 1e12
-        entry.update({"bound": "alu", "achieved": round(ach, 3), "peak": round(fp64[0], 3),
-                      "unit": "TFLOP/s", "frac": round(ach / fp64[0], 4), "peak_source": fp64[1],
+        entry.update({"bound": "alu", "achieved": round(ach, 3), "peak": round(alu[0], 3),
+                      "unit": "TFLOP/s", "frac": round(ach / alu[0], 4),
+                      "peak_source": ("FP64 FMA " if T == 8 else "FP32 FMA ") + alu[1],
                       "algorithmic_flops_per_launch": fl,
                       "hbm_frac": round(ab / sec / 1e9 / hbm, 4) if ab else None})
     elif ab is not None:
         ach = ab / sec / 1e9
         entry.update({"bound": "hbm", "achieved": round(ach, 1), "peak": hbm, "unit": "GB/s",
                       "frac": round(ach / hbm, 4), "peak_source": peak_kind})
+        if t_alu:
+            entry["alu_frac"] = round(fl / sec / 1e12 / alu[0], 4)
     nf_, tf_ = prof.get("jvp_face", (0, 0.0))
     ne_, te_ = prof.get("jvp_elem", (0, 0.0))
     if ne_:
@@ -244,10 +265,11 @@ def roofline_entry(prof, T, K, E, F, hbm, peak_kind, dim, p, m, workload, fp64=N
     return entry
 
 
-def kernel_table(prof, T, K, E, F, hbm, dim, p, m, fp64=None, face_jacobians=True):
+def kernel_table(prof, T, K, E, F, hbm, dim, p, m, fp64=None, face_jacobians=True, fp32=None):
     """Every kernel class with a byte model: launches, mean launch time (CUDA events per
-    class over the profiled steps), algorithmic GB/s and its fraction of measured HBM; FP64
-    classes with a flop model also give TFLOP/s and the fraction of the FP64 pipe."""
+    class over the profiled steps), algorithmic GB/s and its fraction of measured HBM;
+    classes with a flop model also give TFLOP/s and the fraction of the measured FMA rate of
+    their precision."""
     out = {}
     for kind, (n, ms) in prof.items():
         ab = algorithmic_bytes(kind, T, K, E, F, dim, p, m, face_jacobians)
@@ -256,10 +278,13 @@ def kernel_table(prof, T, K, E, F, hbm, dim, p, m, fp64=None, face_jacobians=Tru
         sec = ms / n / 1e3
         row = {"launches": n, "avg_launch_us": round(sec * 1e6, 2), "gbs": round(ab / sec / 1e9, 1),
                "hbm_frac": round(ab / sec / 1e9 / hbm, 4)}
-        fl = algorithmic_flops(kind, K, E, F, dim, p, m)
+        fl = algorithmic_flops(kind, K, E, F, dim, p, m, T)
         if T == 8 and fl is not None and fp64 is not None:
             row["fp64_tflops"] = round(fl / sec / 1e12, 3)
             row["fp64_frac"] = round(fl / sec / 1e12 / fp64[0], 4)
+        elif T == 4 and fl is not None and fp32 is not None:
+            row["fp32_tflops"] = round(fl / sec / 1e12, 3)
+            row["fp32_frac"] = round(fl / sec / 1e12 / fp32[0], 4)
         out[kind] = row
     return out
 
@@ -318,6 +343,7 @@ def main():
     capi.load()
     hbm, peak_kind = load_peaks()
     fp64 = fp64_peak(capi)
+    fp32 = fp32_peak(capi)
 
     case = W.case_vortex3d(n=args.n3d)
     prm = [case.vortex.eps, *case.vortex.center, 10.0]
@@ -379,8 +405,9 @@ def main():
             "value": job_throughput(ctx.K, args.steps, world, ms / 1e3), "ms_per_step": ms / args.steps,
             "state": state, "clocks": clocks, "prof": prof,
             "kernel_ms_per_step": {k: round(v[1], 4) for k, v in prof.items() if v[0]},
-            "roofline": roofline_entry(prof, T, ctx.K, E, F, hbm, peak_kind, 3, case.p, case.m, "vortex3d", fp64),
-            "kernels": kernel_table(prof, T, ctx.K, E, F, hbm, 3, case.p, case.m, fp64),
+            "roofline": roofline_entry(prof, T, ctx.K, E, F, hbm, peak_kind, 3, case.p, case.m, "vortex3d", fp64,
+                                       fp32=fp32),
+            "kernels": kernel_table(prof, T, ctx.K, E, F, hbm, 3, case.p, case.m, fp64, fp32=fp32),
         }
         if name == "fp32_mixed":
             ctx32 = ctx
@@ -413,7 +440,7 @@ def main():
         a, b = forms["fp64"]["state"], head["state"]
         err = float(np.linalg.norm(b - a) / np.linalg.norm(a))
 
-    side = None if args.no_2d else bump2d_block(args, capi, W, torch, np, hbm, peak_kind, fp64, dist)
+    side = None if args.no_2d else bump2d_block(args, capi, W, torch, np, hbm, peak_kind, fp64, dist, fp32)
 
     cpu = None
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
@@ -444,6 +471,8 @@ def main():
                 "h2d_bytes_per_step": K * 8, "d2h_bytes_per_step": K * 8},
         "gpu_launches": int(launches_per_step * args.steps),
         "roofline": head["roofline"],
+        "fma_peaks": {"fp64_tflops": round(fp64[0], 3), "fp64_source": fp64[1],
+                      "fp32_tflops": round(fp32[0], 2), "fp32_source": fp32[1]},
         "kernel_ms_per_step": head["kernel_ms_per_step"],
         "kernels": head["kernels"],
         "fp64": strip(forms["fp64"]) if "fp64" in forms else None,
@@ -458,7 +487,7 @@ def main():
         dist.destroy_process_group()
 
 
-def bump2d_block(args, capi, W, torch, np, hbm, peak_kind, fp64, dist=None):
+def bump2d_block(args, capi, W, torch, np, hbm, peak_kind, fp64, dist=None, fp32=None):
     """Side block: the steady bump channel (192 x 64 split quads, 24,576 triangles, P2, local
     CFL 100, m = 30) in both forms, with a 256 MB L2 flush before each step (its vectors are
     L2-sized) outside the step's CUDA events."""
@@ -488,7 +517,8 @@ def bump2d_block(args, capi, W, torch, np, hbm, peak_kind, fp64, dist=None):
         T = 8 if name == "fp64" else 4
         res[name] = {"value": ctx.K * steps / (ms / 1e3), "ms_per_step": ms / steps,
                      "kernel_ms_per_step": {k: round(v[1], 4) for k, v in prof.items() if v[0]},
-                     "roofline": roofline_entry(prof, T, ctx.K, E, F, hbm, peak_kind, 2, P2D, M2D, "bump2d", fp64)}
+                     "roofline": roofline_entry(prof, T, ctx.K, E, F, hbm, peak_kind, 2, P2D, M2D, "bump2d", fp64,
+                                                fp32=fp32)}
         ctx.close()
     res["fp32_mixed"]["speedup_vs_fp64"] = res["fp64"]["ms_per_step"] / res["fp32_mixed"]["ms_per_step"]
     return {"workload": f"bump2d_{NX}x{NY}_p{P2D}_m{M2D}_pcexp_localcfl100", "steps": steps, **res}

@@ -45,12 +45,14 @@ extern "C" {
 #define PCEXP_ERR_CUDA (-3)        /* a CUDA runtime call failed */
 #define PCEXP_ERR_OOM (-4)         /* device allocation failed */
 #define PCEXP_ERR_NONFINITE (-5)   /* a norm, beta or h_{j+1,j} was NaN/Inf */
-#define PCEXP_ERR_TIMEOUT (-6)     /* reserved for bounded device waits (none in this build) */
+#define PCEXP_ERR_TIMEOUT (-6)     /* a partition of a group missed a rendezvous (failed or stalled) */
 #define PCEXP_ERR_UNSUPPORTED (-7) /* valid request this build does not cover */
 
 /* ---- boundary tags (Sec. 4.4, Sec. 5.2) ---- */
-#define PCEXP_BC_SLIP_WALL 1 /* ghost state mirrors the normal velocity */
+#define PCEXP_BC_SLIP_WALL 1 /* ghost state mirrors the normal velocity (relative to the frame) */
 #define PCEXP_BC_FARFIELD 2  /* characteristic (Riemann-invariant) ghost state */
+#define PCEXP_BC_SYMMETRY 3  /* symmetry plane (Sec. 5.2, sphere case): the slip-wall ghost state of
+                                inviscid flow; not part of the wall-force functionals */
 
 /* ---- options ---- */
 #define PCEXP_FP64 0       /* every vector, flux and reduction in FP64 */
@@ -99,13 +101,22 @@ typedef struct pcexp_mesh {
 } pcexp_mesh;
 
 /* Free stream (nondimensional): gamma (7/5 in the paper, Sec. 4.1), Mach
- * number, flow angle in degrees, density and pressure. */
+ * number, flow angle in degrees, density and pressure; and the angular velocity omega
+ * of a rotating frame of reference (Sec. 4.1, Eq. euler; zero: a fixed frame).  With
+ * omega != 0 the flux is F_abs - U v_r^T, v_r = omega x x, the source -rho omega x v is
+ * added, the Roe waves move with the frame and the slip wall mirrors the velocity relative
+ * to it; the mesh must have no periodic identification and no far-field faces, and in 2D
+ * only omega[2] may be nonzero (otherwise PCEXP_ERR_INVALID_ARG).  The steps' local time
+ * steps use the velocity relative to the frame at the centroid.  The adjoint entry points
+ * (pcexp_step_backward, pcexp_jvp_state_adjoint) return PCEXP_ERR_UNSUPPORTED in a
+ * rotating frame. */
 typedef struct pcexp_physics {
   double gamma;
   double mach;
   double alpha_deg;
   double rho_inf;
   double p_inf;
+  double omega[3];
 } pcexp_physics;
 
 typedef struct pcexp_options {
@@ -279,7 +290,8 @@ int pcexp_functional_param_grad(pcexp_ctx* ctx, int kind, const double* params, 
                                 double* dJ, int on_device);
 
 /* Replaces the free stream (Mach number, angle, density, pressure, gamma) used
- * by the far-field boundary condition; the mesh and state are kept. */
+ * by the far-field boundary condition; the mesh and state are kept.  omega must equal
+ * the context's (INVALID_ARG otherwise): the frame's arrays are built at creation. */
 int pcexp_set_physics(pcexp_ctx* ctx, const pcexp_physics* phys);
 
 /* Diagnostics of the master state (Sec. 5):
@@ -340,8 +352,84 @@ int pcexp_residual_noalloc(pcexp_ctx* ctx, const double* U, double* R);
  * a private stream.  Errors: INVALID_ARG, CUDA. */
 int pcexp_fp64_fma_rate(double* tflops);
 
+/* The same for FP32 fused multiply-adds (the roof of the FP32-mixed form's arithmetic-bound
+ * kernels, e.g. the element J v on tetrahedra).  Errors: INVALID_ARG, CUDA. */
+int pcexp_fp32_fma_rate(double* tflops);
+
 /* Waits for all work queued on the context's stream. */
 int pcexp_synchronize(pcexp_ctx* ctx);
+
+/* ---- partitioned runs (an element decomposition; the paper runs on one processor)
+ *
+ * The operator of Sec. 4.3 (Eq. euler3) couples an element only to the elements across its
+ * faces.  A partition therefore computes its own elements' rows of R(u) and J v (Sec. 4.4)
+ * from its own elements and a one-element halo (the other partitions' elements that share a
+ * face with one of its own), and the rest of the Krylov step (Sec. 2.2, Eq. s9/s10: the
+ * Gram-Schmidt inner products and norms of the Arnoldi process, the axpys) is arithmetic on
+ * its own rows plus sums over partitions.  A group holds one context per partition, each on
+ * its own device (or all on one) and stream.  In a step, each operator pass first gathers
+ * the halo rows of its input vector from the owning partitions' device buffers (peer reads),
+ * each Gram-Schmidt pass sums its (j + 2) partial sums over the partitions in partition
+ * order (every partition obtains the same Hessenberg matrix, bit for bit), and the global
+ * dt of PCEXP_DT_GLOBAL_CFL is the minimum over partitions.  The results equal those of one
+ * context on the whole mesh up to the summation order of the inner products.  A group call
+ * drives each partition from a host thread of its own; the partitions meet at host
+ * rendezvous points, the ordering between their streams is by CUDA events, and no kernel
+ * waits on another.  A group is not thread-safe; one group call at a time.
+ *
+ * Global state-shaped arrays are host arrays of the whole mesh (layout and basis as for one
+ * context).  After a failed group call the state is undefined until the next set/project. */
+typedef struct pcexp_group pcexp_group;
+
+/* part[e] in [0, n_parts) for every element (n_parts <= 16, n_elem >= n_parts): recursive
+ * coordinate bisection of the element centroids (each set of elements going to n parts is
+ * split at the floor(n/2)/n quantile along its axis of largest extent; ties by element
+ * index).  Host only.  Errors: INVALID_ARG. */
+int pcexp_partition(const pcexp_mesh* mesh, int n_parts, int32_t* part);
+
+/* The elements partition k computes with: *n_owned of its own (ascending element index),
+ * then its halo (ascending), *n_total in all; elems (NULL: sizes only) receives them and must
+ * hold n_elem entries.  Host only.  Errors: INVALID_ARG, MESH. */
+int pcexp_partition_halo(const pcexp_mesh* mesh, const int32_t* part, int n_parts, int k,
+                         int64_t* n_owned, int64_t* n_total, int64_t* elems);
+
+/* Creates a group of n_parts contexts (1..16), partition k on device devices[k] (NULL: all
+ * on the current device), each with the submesh of its own and halo elements: a face keeps
+ * the quadrature points of the whole mesh's L element; halo faces with no partner in the
+ * submesh get the symmetry-plane ghost state, whose halo rows are discarded.  Devices of
+ * different partitions must allow peer access (else UNSUPPORTED).  The state starts at the
+ * free stream.  Errors: INVALID_ARG (bad option, index out of range, empty partition),
+ * MESH, CUDA, OOM, UNSUPPORTED. */
+int pcexp_group_create(pcexp_group** out, const pcexp_mesh* mesh, const int32_t* part, int n_parts,
+                       const int32_t* devices, int p, const pcexp_physics* phys,
+                       const pcexp_options* opt);
+int pcexp_group_destroy(pcexp_group* group);
+
+/* Own and halo element counts of partition k. */
+int pcexp_group_sizes(const pcexp_group* group, int k, int64_t* n_owned, int64_t* n_halo);
+
+/* State of the whole mesh (host, K doubles), scattered to / gathered from the partitions. */
+int pcexp_group_set_state(pcexp_group* group, const double* U);
+int pcexp_group_get_state(pcexp_group* group, double* U);
+int pcexp_group_project_state(pcexp_group* group, int kind, const double* params, int n_params);
+
+/* R(U) and J(U) v of the whole mesh (host arrays).  Each partition receives only its own rows
+ * of U and v; the halo rows come from the exchange of the operator pass, as in a step. */
+int pcexp_group_residual(pcexp_group* group, const double* U, double* R);
+int pcexp_group_jvp(pcexp_group* group, const double* U, const double* v, double* Jv);
+
+/* Arnoldi process of pcexp_arnoldi (J at U, start vector b; host arrays) with the partitioned
+ * Gram-Schmidt sums: H [(m+1) x m] row-major, *k, *beta as for pcexp_arnoldi.  The call
+ * checks that every partition holds the same H (else CUDA). */
+int pcexp_group_arnoldi(pcexp_group* group, const double* U, const double* b, int m, double* H,
+                        int* k, double* beta);
+
+/* One step of pcexp_step on the group's state: schemes PCEXP, EXP1, ETD2; dt_mode GIVEN or
+ * GLOBAL_CFL (LOCAL_CFL: UNSUPPORTED).  info as for pcexp_step, res_norm over the whole mesh.
+ * Steps run eagerly (no CUDA graph).  Errors: those of pcexp_step, TIMEOUT (a partition missed
+ * a rendezvous for 120 s: it failed or stalled). */
+int pcexp_group_step(pcexp_group* group, int scheme, int dt_mode, double dt_or_cfl, int m,
+                     pcexp_step_info* info);
 
 /* Static description of a status code. */
 const char* pcexp_status_string(int status);

@@ -13,9 +13,15 @@ holds no method arithmetic.
 Pinned by the ``-m "not gpu"`` tests against closed forms, library routines
 and printed values (Table 1 "timesize", Eq. grow / exp1_grow / rkgrow,
 phi_1(z) = (e^z - 1)/z, dense expm, free-stream preservation, conservation,
-complex-step derivatives, the Appendix flux Jacobian, the inscribed-circle and
-inscribed-sphere diameters behind the element time step of Eq. x3d, and the
-exact decay of a linear system under the steady march of Eq. cfl).  Parity
-unpinned: the nonlinear bump-channel steady march beyond agreement with
-itself (no printed number exists for it).
+complex-step derivatives, the Appendix flux Jacobian (also with the rotating-frame
+terms of Eq. dfdu), the inscribed-circle and inscribed-sphere diameters behind the
+element time step of Eq. x3d, and the exact decay of a linear system under the
+steady march of Eq. cfl); ETD2 against the scalar phi_1/phi_2 closed forms, exact
+affine flows and second-order convergence; the Krylov error estimate against the
+true error from a dense exponential; the stretched mesh against the spacings the
+paper prints; the wall force, entropy error and density norm against trapezoid,
+shoelace and closed-form integrals; the exact translation of the isentropic vortex;
+the rotating-frame source of a uniform state.  Parity unpinned: the nonlinear
+bump-channel steady march beyond agreement with itself (no printed number exists
+for it).
 """

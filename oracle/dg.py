@@ -23,6 +23,7 @@ from .quadrature import gauss_legendre01, tetra_rule, triangle_rule
 
 BC_SLIP_WALL = 1
 BC_FARFIELD = 2
+BC_SYMMETRY = 3  # symmetry plane: the slip-wall ghost state (inviscid), not part of the wall force
 
 
 def face_vertices(dim: int, f: int):
@@ -69,9 +70,14 @@ def build_faces(mesh):
 
 
 class DGOracle:
-    """R(u), J(u) v, time-step sizes and diagnostics on a triangle or tetrahedron mesh."""
+    """R(u), J(u) v, time-step sizes and diagnostics on a triangle or tetrahedron mesh.
 
-    def __init__(self, mesh, p: int, free):
+    omega (optional, 3 components; only omega_z in 2D): angular velocity of a rotating
+    frame of reference (Eq. euler): frame velocity v_r = omega x x in the fluxes and the
+    source -rho omega x v.  v_r depends on position, so a rotating frame needs a mesh
+    without periodic faces, and far-field faces are not defined for it."""
+
+    def __init__(self, mesh, p: int, free, omega=None):
         self.mesh = mesh
         self.p = p
         self.gamma = free.gamma
@@ -117,6 +123,29 @@ class DGOracle:
         self._setup_interior(interior)
         self._setup_boundary(boundary)
         self.vel_inf = list(freestream_velocity(free, dim))
+        self.omega = None
+        if omega is not None and np.any(np.asarray(omega) != 0.0):
+            om = np.asarray(omega, dtype=np.float64)
+            if dim == 2 and (om[0] != 0.0 or om[1] != 0.0):
+                raise ValueError("in 2D the frame rotates about z: omega = (0, 0, omega_z)")
+            if np.any(mesh.vert_master != np.arange(mesh.n_vert)):
+                raise ValueError("a rotating frame needs a mesh without periodic faces")
+            if len(self.fb) and np.any(self.fb[:, 2] == BC_FARFIELD):
+                raise ValueError("far-field faces are not defined in a rotating frame")
+            self.omega = om
+            self.vr_q = self.frame_velocity(self.xq)      # [E, nq, dim]
+            if len(self.fi):
+                self.vrn_i = np.einsum("fqd,fd->fq", self.frame_velocity(self.fi_x), self.fi_n)
+            if len(self.fb):
+                self.vrn_b = np.einsum("fqd,fd->fq", self.frame_velocity(self.fb_x), self.fb_n)
+
+    def frame_velocity(self, x):
+        """v_r = omega x x at points x [..., dim] (the x-y components in 2D)."""
+        om = self.omega
+        X = np.zeros(x.shape[:-1] + (3,))
+        X[..., : self.dim] = x
+        vr = np.cross(np.broadcast_to(om, X.shape), X)
+        return vr[..., : self.dim]
 
     # ------------------------------------------------------------------ faces
     def _face_normal(self, e, f):
@@ -164,7 +193,9 @@ class DGOracle:
         n, meas = self._face_normal(eL, fL)
         self.fi_n = n
         self.fi_w = (meas * (2.0 if self.dim == 3 else 1.0))[:, None] * self.ws[None, :]
-        self.fi_psiL = self.basis.eval_rows(eL, self._face_points(eL, cornL))  # [F, nfq, N]
+        rL = self._face_points(eL, cornL)
+        self.fi_x = self.verts[eL, 0, :][:, None, :] + rL  # face points (the L element's copy)
+        self.fi_psiL = self.basis.eval_rows(eL, rL)  # [F, nfq, N]
         self.fi_psiR = self.basis.eval_rows(eR, self._face_points(eR, cornR))
 
     def _setup_boundary(self, faces):
@@ -191,17 +222,26 @@ class DGOracle:
         u = self.unflat(u)
         g = self.gamma
         R = ad.zeros_like_var(u, (self.E, self.nv, self.N))
+        rot = self.omega is not None
         if volume:
             Uq = ad.lin(lambda a: np.einsum("eqi,evi->eqv", self.psi_q, a), u)
             for k in range(self.dim):
-                Fk = ad.stack(euler.flux_dir(Uq, k, g))  # [E, nq, nv]
+                Fk = ad.stack(euler.flux_dir(Uq, k, g, self.vr_q[..., k] if rot else None))  # [E, nq, nv]
                 R = R + ad.lin(lambda a, k=k: np.einsum("eqi,eqv->evi", self.gpsi_wq[:, :, :, k], a), Fk)
+            if rot:
+                # int_E psi_i S(U_h) dx, S = (0, -omega x (rho v), 0) (Eq. euler3)
+                om = self.omega
+                m = [Uq[..., 1 + k] for k in range(self.dim)] + ([0.0 * Uq[..., 0]] if self.dim == 2 else [])
+                cross = [om[1] * m[2] - om[2] * m[1], om[2] * m[0] - om[0] * m[2], om[0] * m[1] - om[1] * m[0]]
+                zero = 0.0 * Uq[..., 0]
+                Sq = ad.stack([zero] + [-cross[k] for k in range(self.dim)] + [zero])
+                R = R + ad.lin(lambda a: np.einsum("eq,eqi,eqv->evi", self.wq, self.psi_q, a), Sq)
         if faces and len(self.fi):
             eL, fL, eR, fR = self.fi.T
             UL = ad.lin(lambda a: np.einsum("fqi,fvi->fqv", self.fi_psiL, a[eL]), u)
             UR = ad.lin(lambda a: np.einsum("fqi,fvi->fqv", self.fi_psiR, a[eR]), u)
             n = np.broadcast_to(self.fi_n[:, None, :], UL.shape[:2] + (self.dim,))
-            Fn = euler.roe_flux(UL, UR, n, g)  # [F, nfq, nv]
+            Fn = euler.roe_flux(UL, UR, n, g, self.vrn_i if rot else None)  # [F, nfq, nv]
             Fn = Fn * self.fi_w[:, :, None]
             cL = ad.lin(lambda a: np.einsum("fqi,fqv->fvi", self.fi_psiL, a), Fn)
             cR = ad.lin(lambda a: np.einsum("fqi,fqv->fvi", self.fi_psiR, a), Fn)
@@ -211,11 +251,14 @@ class DGOracle:
             e, f, tag = self.fb.T
             UL = ad.lin(lambda a: np.einsum("fqi,fvi->fqv", self.fb_psi, a[e]), u)
             n = np.broadcast_to(self.fb_n[:, None, :], UL.shape[:2] + (self.dim,))
-            wall = (tag == BC_SLIP_WALL)[:, None]
-            Ug_w = euler.ghost_slip_wall(UL, n, g)
-            Ug_f = euler.ghost_farfield(UL, n, g, self.free.rho, self.vel_inf, self.free.p)
-            Ug = ad.where(wall[:, :, None], Ug_w, Ug_f)
-            Fn = euler.roe_flux(UL, Ug, n, g) * self.fb_w[:, :, None]
+            wall = ((tag == BC_SLIP_WALL) | (tag == BC_SYMMETRY))[:, None]
+            Ug_w = euler.ghost_slip_wall(UL, n, g, self.vrn_b if rot else None)
+            if rot:
+                Ug = Ug_w  # only slip walls and symmetry planes in a rotating frame
+            else:
+                Ug_f = euler.ghost_farfield(UL, n, g, self.free.rho, self.vel_inf, self.free.p)
+                Ug = ad.where(wall[:, :, None], Ug_w, Ug_f)
+            Fn = euler.roe_flux(UL, Ug, n, g, self.vrn_b if rot else None) * self.fb_w[:, :, None]
             c = ad.lin(lambda a: np.einsum("fqi,fqv->fvi", self.fb_psi, a), Fn)
             R = ad.add_at(R, e, -c)
         if flat:
@@ -289,6 +332,9 @@ class DGOracle:
         p = (self.gamma - 1.0) * (U[:, self.dim + 1] - 0.5 * rho * np.sum(vel ** 2, axis=1))
         c = np.sqrt(self.gamma * p / rho)
         h = 2.0 * self.dim * self.area / self.perimeter
+        if self.omega is not None:
+            # reading: in a rotating frame the waves travel with the velocity relative to it
+            vel = vel - self.frame_velocity(self.verts.mean(axis=1))
         return cfl * h / ((2 * self.p + 1) * (np.linalg.norm(vel, axis=1) + c))
 
     def density_residual_norm(self, R, volume):

@@ -1,8 +1,13 @@
 """Euler fluxes, Roe's Riemann flux and ghost states for the oracle.
 
-Sec. 4.1 (Eq. euler) with a non-rotating frame (omega = 0, so v_r = 0 and
-S = 0): U = (rho, rho v, rho E), F = (rho v, rho v v^T + p I, rho H v),
-p = (gamma - 1) rho e, E = e + |v|^2 / 2, H = E + p / rho.
+Sec. 4.1 (Eq. euler): U = (rho, rho v, rho E) with the absolute velocity v,
+p = (gamma - 1) rho e, E = e + |v|^2 / 2, H = E + p / rho.  In a frame rotating with
+angular velocity omega the flux is F = F_abs - U v_r^T with v_r = omega x x (reading:
+the mass row rho (v - v_r), the momentum rows rho v (v - v_r)^T + p I and the energy
+row rho H v - rho E v_r, the form whose Jacobian is the Appendix's Eq. dfdu -- the
+printed energy row rho H (v - v_r) would give gamma (B_1 - B_2) on its diagonal where
+Eq. dfdu has gamma B_1 - B_2).  The source S = (0, -rho omega x v, 0) enters the DG
+residual in ``dg``.  omega = 0 gives the fixed-frame equations.
 
 Riemann flux (Sec. 4.2, after Eq. euler3): Roe's approximate solver with
 square-root-density averages and no entropy fix (the paper names none):
@@ -31,8 +36,9 @@ def primitives(U, gamma):
     return rho, vel, p, E
 
 
-def flux_dir(U, k, gamma):
-    """Physical flux component along Cartesian axis k -> list of nv arrays."""
+def flux_dir(U, k, gamma, vr=None):
+    """Flux component along Cartesian axis k -> list of nv arrays; with the frame velocity
+    component vr_k (array, rotating frame) the relative part -U vr_k is included."""
     rho, vel, p, E = primitives(U, gamma)
     dim = len(vel)
     vk = vel[k]
@@ -43,6 +49,8 @@ def flux_dir(U, k, gamma):
             f = f + p
         out.append(f)
     out.append((E + p) * vk)
+    if vr is not None:
+        out = [out[j] - U[..., j] * vr for j in range(len(out))]
     return out
 
 
@@ -58,8 +66,10 @@ def flux_normal(U, n, gamma):
     return out
 
 
-def roe_dissipation(UL, UR, n, gamma):
-    """|A_roe| (U_R - U_L) written as the sum over waves |lambda_k| alpha_k r_k."""
+def roe_dissipation(UL, UR, n, gamma, vrn=None):
+    """|A_roe| (U_R - U_L) written as the sum over waves |lambda_k| alpha_k r_k.  In a
+    rotating frame the normal flux Jacobian is A_n - (v_r . n) I: same waves, eigenvalues
+    shifted by -vrn."""
     rL, vL, pL, EL = primitives(UL, gamma)
     rR, vR, pR, ER = primitives(UR, gamma)
     dim = len(vL)
@@ -79,9 +89,10 @@ def roe_dissipation(UL, UR, n, gamma):
     drho = rR - rL
     dvel = [vR[k] - vL[k] for k in range(dim)]
     dqn = sum(dvel[k] * n[..., k] for k in range(dim))
-    l1 = ad.absval(qn - c)
-    l2 = ad.absval(qn)
-    l4 = ad.absval(qn + c)
+    qs = qn if vrn is None else qn - vrn  # the waves' speeds relative to the frame
+    l1 = ad.absval(qs - c)
+    l2 = ad.absval(qs)
+    l4 = ad.absval(qs + c)
     a1 = (dp - rho_h * c * dqn) / (2.0 * c2)
     a4 = (dp + rho_h * c * dqn) / (2.0 * c2)
     a2 = drho - dp / c2
@@ -97,11 +108,15 @@ def roe_dissipation(UL, UR, n, gamma):
     return d
 
 
-def roe_flux(UL, UR, n, gamma):
-    """Roe's Riemann flux F~(U_L, U_R) . n -> stacked [..., nv]."""
+def roe_flux(UL, UR, n, gamma, vrn=None):
+    """Roe's Riemann flux F~(U_L, U_R) . n -> stacked [..., nv]; vrn = v_r . n at the face
+    points in a rotating frame (F . n = F_abs . n - vrn U)."""
     fL = flux_normal(UL, n, gamma)
     fR = flux_normal(UR, n, gamma)
-    dis = roe_dissipation(UL, UR, n, gamma)
+    if vrn is not None:
+        fL = [fL[v] - vrn * UL[..., v] for v in range(len(fL))]
+        fR = [fR[v] - vrn * UR[..., v] for v in range(len(fR))]
+    dis = roe_dissipation(UL, UR, n, gamma, vrn)
     return ad.stack([0.5 * (fL[v] + fR[v]) - 0.5 * dis[v] for v in range(len(fL))])
 
 
@@ -111,11 +126,14 @@ def conservative(rho, vel, p, gamma):
     return ad.stack([rho] + [rho * v for v in vel] + [p / (gamma - 1.0) + rho * ke])
 
 
-def ghost_slip_wall(UL, n, gamma):
-    """Mirror state: v_g = v - 2 (v . n) n, same density and pressure."""
+def ghost_slip_wall(UL, n, gamma, vrn=None):
+    """Mirror state: v_g = v - 2 ((v - v_r) . n) n (the velocity relative to the wall, which
+    moves with the frame, is mirrored), same density and pressure.  Also the symmetry plane."""
     rho, vel, p, E = primitives(UL, gamma)
     dim = len(vel)
     qn = sum(vel[k] * n[..., k] for k in range(dim))
+    if vrn is not None:
+        qn = qn - vrn
     velg = [vel[k] - 2.0 * qn * n[..., k] for k in range(dim)]
     return conservative(rho, velg, p, gamma)
 

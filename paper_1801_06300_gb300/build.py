@@ -16,7 +16,7 @@ CSRC = os.path.join(HERE, "csrc")
 ROOT = os.path.dirname(HERE)
 BUILD = os.path.join(HERE, "_build")
 LIB = os.path.join(HERE, "libpcexp.so")
-SOURCES = ["host_setup.cpp", "dg2d.cu", "dg3d.cu", "dg_common.cu", "krylov_kernels.cu", "adjoint.cu", "api.cu", "noalloc.cu"]
+SOURCES = ["host_setup.cpp", "partition.cpp", "dg2d.cu", "dg3d.cu", "dg_common.cu", "krylov_kernels.cu", "adjoint.cu", "api.cu", "noalloc.cu"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 FLAGS = ARCH + ["-O3", "-lineinfo", "-std=c++17", "-Xcompiler", "-fPIC", "-Xcompiler", "-O2",
                 "-I", os.path.join(ROOT, "include")]

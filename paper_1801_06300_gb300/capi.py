@@ -23,6 +23,7 @@ PCEXP_ERR_TIMEOUT = -6
 PCEXP_ERR_UNSUPPORTED = -7
 PCEXP_BC_SLIP_WALL = 1
 PCEXP_BC_FARFIELD = 2
+PCEXP_BC_SYMMETRY = 3
 PCEXP_FP64 = 0
 PCEXP_FP32_MIXED = 1
 PCEXP_BASIS_PAPER = 0
@@ -54,7 +55,12 @@ class pcexp_mesh(C.Structure):
 
 class pcexp_physics(C.Structure):
     _fields_ = [("gamma", C.c_double), ("mach", C.c_double), ("alpha_deg", C.c_double),
-                ("rho_inf", C.c_double), ("p_inf", C.c_double)]
+                ("rho_inf", C.c_double), ("p_inf", C.c_double), ("omega", C.c_double * 3)]
+
+
+def _physics(free, omega):
+    om = (C.c_double * 3)(*(omega if omega is not None else (0.0, 0.0, 0.0)))
+    return pcexp_physics(free.gamma, free.mach, free.alpha_deg, free.rho, free.p, om)
 
 
 class pcexp_options(C.Structure):
@@ -106,6 +112,21 @@ SIGNATURES = {
     "pcexp_profile_enable": (C.c_int, [_P, C.c_int]),
     "pcexp_profile_read": (C.c_int, [_P, C.c_int, C.POINTER(C.c_int64), _D]),
     "pcexp_fp64_fma_rate": (C.c_int, [_D]),
+    "pcexp_fp32_fma_rate": (C.c_int, [_D]),
+    "pcexp_partition": (C.c_int, [C.POINTER(pcexp_mesh), C.c_int, _P]),
+    "pcexp_partition_halo": (C.c_int, [C.POINTER(pcexp_mesh), _P, C.c_int, C.c_int, C.POINTER(C.c_int64),
+                                       C.POINTER(C.c_int64), _P]),
+    "pcexp_group_create": (C.c_int, [C.POINTER(_P), C.POINTER(pcexp_mesh), _P, C.c_int, _P, C.c_int,
+                                     C.POINTER(pcexp_physics), C.POINTER(pcexp_options)]),
+    "pcexp_group_destroy": (C.c_int, [_P]),
+    "pcexp_group_sizes": (C.c_int, [_P, C.c_int, C.POINTER(C.c_int64), C.POINTER(C.c_int64)]),
+    "pcexp_group_set_state": (C.c_int, [_P, _P]),
+    "pcexp_group_get_state": (C.c_int, [_P, _P]),
+    "pcexp_group_project_state": (C.c_int, [_P, C.c_int, _D, C.c_int]),
+    "pcexp_group_residual": (C.c_int, [_P, _P, _P]),
+    "pcexp_group_jvp": (C.c_int, [_P, _P, _P, _P]),
+    "pcexp_group_arnoldi": (C.c_int, [_P, _P, _P, C.c_int, _D, C.POINTER(C.c_int), _D]),
+    "pcexp_group_step": (C.c_int, [_P, C.c_int, C.c_int, C.c_double, C.c_int, C.POINTER(pcexp_step_info)]),
     "pcexp_status_string": (C.c_char_p, [C.c_int]),
     "pcexp_last_error": (C.c_char_p, []),
 }
@@ -140,6 +161,14 @@ def fp64_fma_rate() -> float:
     return v.value
 
 
+def fp32_fma_rate() -> float:
+    """FP32 FMA rate of the current device in TFLOP/s (FFMA chains on every SM)."""
+    lib = load()
+    v = C.c_double()
+    check(lib.pcexp_fp32_fma_rate(C.byref(v)), "pcexp_fp32_fma_rate")
+    return v.value
+
+
 class PcexpError(RuntimeError):
     def __init__(self, code: int, where: str):
         lib = load()
@@ -163,23 +192,133 @@ def _ptr(x):
     return C.c_void_p(x.data_ptr()), 1 if x.is_cuda else 0
 
 
+def _mesh_struct(mesh):
+    """(pcexp_mesh, arrays it points into): keep the arrays alive while the struct is used."""
+    coords = np.ascontiguousarray(mesh.coords, np.float64)
+    elems = np.ascontiguousarray(mesh.elems, np.int32)
+    master = np.ascontiguousarray(mesh.vert_master, np.int32)
+    bfv = np.ascontiguousarray(mesh.bfaces, np.int32).reshape(-1)
+    btag = np.ascontiguousarray(mesh.btags, np.int32)
+    ip = lambda a: a.ctypes.data_as(C.POINTER(C.c_int32))  # noqa: E731
+    m = pcexp_mesh(mesh.dim, coords.shape[0], coords.ctypes.data_as(_D), elems.shape[0], ip(elems),
+                   ip(master), btag.shape[0], ip(bfv) if bfv.size else None, ip(btag) if btag.size else None)
+    return m, [coords, elems, master, bfv, btag]
+
+
+def partition(mesh, n_parts: int) -> np.ndarray:
+    """pcexp_partition: int32 partition index of every element (host only)."""
+    lib = load()
+    m, keep = _mesh_struct(mesh)
+    part = np.empty(len(mesh.elems), np.int32)
+    check(lib.pcexp_partition(C.byref(m), n_parts, part.ctypes.data_as(_P)), "pcexp_partition")
+    return part
+
+
+def partition_halo(mesh, part, k: int):
+    """pcexp_partition_halo: (own elements, halo elements) of partition k (host only)."""
+    lib = load()
+    m, keep = _mesh_struct(mesh)
+    part = np.ascontiguousarray(part, np.int32)
+    el = np.empty(len(mesh.elems), np.int64)
+    no, nt = C.c_int64(), C.c_int64()
+    check(lib.pcexp_partition_halo(C.byref(m), part.ctypes.data_as(_P), int(part.max()) + 1, k, C.byref(no),
+                                   C.byref(nt), el.ctypes.data_as(_P)), "pcexp_partition_halo")
+    return el[:no.value].copy(), el[no.value:nt.value].copy()
+
+
+class Group:
+    """Owns one pcexp_group (a partitioned run, host arrays of the whole mesh)."""
+
+    def __init__(self, mesh, part, p: int, free, precision: int = PCEXP_FP64, m_max: int = 30,
+                 eta: float = 0.0, basis_io: int = PCEXP_BASIS_PAPER, devices=None, omega=None):
+        lib = load()
+        m, self._keep = _mesh_struct(mesh)
+        part = np.ascontiguousarray(part, np.int32)
+        self.n = int(part.max()) + 1
+        dev = None if devices is None else np.ascontiguousarray(devices, np.int32)
+        ph = _physics(free, omega)
+        op = pcexp_options(precision, m_max, eta, basis_io, 0.0)
+        self.g = C.c_void_p()
+        check(lib.pcexp_group_create(C.byref(self.g), C.byref(m), part.ctypes.data_as(_P), self.n,
+                                     dev.ctypes.data_as(_P) if dev is not None else None, p, C.byref(ph),
+                                     C.byref(op)), "pcexp_group_create")
+        self.lib = lib
+        nv = mesh.dim + 2
+        nb = {2: (p + 1) * (p + 2) // 2, 3: (p + 1) * (p + 2) * (p + 3) // 6}[mesh.dim]
+        self.K = len(mesh.elems) * nv * nb
+
+    def sizes(self, k: int):
+        a, b = C.c_int64(), C.c_int64()
+        check(self.lib.pcexp_group_sizes(self.g, k, C.byref(a), C.byref(b)), "pcexp_group_sizes")
+        return a.value, b.value
+
+    def close(self):
+        if getattr(self, "g", None) is not None and self.g.value:
+            self.lib.pcexp_group_destroy(self.g)
+            self.g = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def _host(self, x):
+        x = np.ascontiguousarray(x, np.float64)
+        assert x.size == self.K
+        return x
+
+    def set_state(self, U):
+        U = self._host(U)
+        check(self.lib.pcexp_group_set_state(self.g, U.ctypes.data_as(_P)), "pcexp_group_set_state")
+
+    def get_state(self):
+        out = np.empty(self.K)
+        check(self.lib.pcexp_group_get_state(self.g, out.ctypes.data_as(_P)), "pcexp_group_get_state")
+        return out
+
+    def project_state(self, kind: int, params=()):
+        prm = np.ascontiguousarray(params, np.float64)
+        check(self.lib.pcexp_group_project_state(self.g, kind, prm.ctypes.data_as(_D) if prm.size else None,
+                                                 prm.size), "pcexp_group_project_state")
+
+    def residual(self, U):
+        U, out = self._host(U), np.empty(self.K)
+        check(self.lib.pcexp_group_residual(self.g, U.ctypes.data_as(_P), out.ctypes.data_as(_P)),
+              "pcexp_group_residual")
+        return out
+
+    def jvp(self, U, v):
+        U, v, out = self._host(U), self._host(v), np.empty(self.K)
+        check(self.lib.pcexp_group_jvp(self.g, U.ctypes.data_as(_P), v.ctypes.data_as(_P), out.ctypes.data_as(_P)),
+              "pcexp_group_jvp")
+        return out
+
+    def arnoldi(self, U, b, m: int):
+        U, b = self._host(U), self._host(b)
+        H = np.zeros((m + 1) * m)
+        k, beta = C.c_int(), C.c_double()
+        check(self.lib.pcexp_group_arnoldi(self.g, U.ctypes.data_as(_P), b.ctypes.data_as(_P), m,
+                                           H.ctypes.data_as(_D), C.byref(k), C.byref(beta)), "pcexp_group_arnoldi")
+        return H.reshape(m + 1, m), k.value, beta.value
+
+    def step(self, scheme: int, dt_mode: int, dt_or_cfl: float, m: int):
+        inf = pcexp_step_info()
+        check(self.lib.pcexp_group_step(self.g, scheme, dt_mode, dt_or_cfl, m, C.byref(inf)), "pcexp_group_step")
+        return dict(k=(inf.krylov_dim[0], inf.krylov_dim[1]), beta=(inf.beta[0], inf.beta[1]), dt=inf.dt,
+                    res_norm=inf.res_norm, err=(inf.krylov_err[0], inf.krylov_err[1]))
+
+
 class Context:
     """Owns one pcexp_ctx; each method is one C call with its arguments marshalled."""
 
     def __init__(self, mesh, p: int, free, precision: int = PCEXP_FP64, m_max: int = 30,
-                 eta: float = 0.0, basis_io: int = PCEXP_BASIS_PAPER, stream=None, krylov_tol: float = 0.0):
+                 eta: float = 0.0, basis_io: int = PCEXP_BASIS_PAPER, stream=None, krylov_tol: float = 0.0,
+                 omega=None):
         lib = load()
-        self._keep = []
-        coords = np.ascontiguousarray(mesh.coords, np.float64)
-        elems = np.ascontiguousarray(mesh.elems, np.int32)
-        master = np.ascontiguousarray(mesh.vert_master, np.int32)
-        bfv = np.ascontiguousarray(mesh.bfaces, np.int32).reshape(-1)
-        btag = np.ascontiguousarray(mesh.btags, np.int32)
-        self._keep += [coords, elems, master, bfv, btag]
-        ip = lambda a: a.ctypes.data_as(C.POINTER(C.c_int32))  # noqa: E731
-        m = pcexp_mesh(mesh.dim, coords.shape[0], coords.ctypes.data_as(_D), elems.shape[0], ip(elems),
-                       ip(master), btag.shape[0], ip(bfv) if bfv.size else None, ip(btag) if btag.size else None)
-        ph = pcexp_physics(free.gamma, free.mach, free.alpha_deg, free.rho, free.p)
+        m, self._keep = _mesh_struct(mesh)
+        ph = _physics(free, omega)
+        self.omega = omega
         op = pcexp_options(precision, m_max, eta, basis_io, krylov_tol)
         if stream is None:
             try:
@@ -357,7 +496,7 @@ class Context:
         return v.value, grad
 
     def set_physics(self, free):
-        ph = pcexp_physics(free.gamma, free.mach, free.alpha_deg, free.rho, free.p)
+        ph = _physics(free, self.omega)
         check(self.lib.pcexp_set_physics(self.ctx, C.byref(ph)), "pcexp_set_physics")
 
     def output(self, kind: int = 0) -> float:

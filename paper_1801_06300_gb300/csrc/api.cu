@@ -7,14 +7,19 @@
 // non-NULL info, the steady march (one 8-byte residual read per iteration)
 // and host-pointer transfers synchronise.
 #include <algorithm>
+#include <chrono>
 #include <cmath>
+#include <condition_variable>
 #include <cstdio>
 #include <cstring>
+#include <mutex>
 #include <string>
+#include <thread>
 #include <vector>
 
 #include "host_setup.h"
 #include "kernels.h"
+#include "partition.h"
 
 using namespace pcexp;
 
@@ -47,6 +52,10 @@ struct pcexp_ctx {
   double* xq = nullptr;                    // physical volume points [E][nq][dim] (first vortex functional)
   double* diag = nullptr;                  // FP64 [Bv (nq nb) | Wv (nq) | sqrt|det A| (E)] (first entropy output)
   double* pgrad = nullptr;                 // 4 doubles: sums of the functional-parameter gradient
+  // rotating frame: v_r at volume points, v_r . n at face points, v_r at centroids (precision of
+  // the DG kernels); allocated when omega != 0
+  void *vrq = nullptr, *vrn = nullptr, *vrc = nullptr;
+  bool rot = false;
   // ETD2 history (first ETD2 step): u_{n-1}, R_{n-1}, and R_n of the step in progress
   void *h_u = nullptr, *h_R = nullptr, *h_Rc = nullptr;
   bool etd2_prev = false;  // the history holds the previous ETD2 step of the current state
@@ -80,6 +89,41 @@ struct pcexp_ctx {
   std::vector<int> ev_rec;  // (class, start, end) triples of indices into ev_pool
   double prof_ms[PCEXP_KC_COUNT] = {};
   int64_t prof_n[PCEXP_KC_COUNT] = {};
+  // partition of a group (pcexp_group_create): the first n_local elements are its own, the
+  // n_ghost after them its halo, whose rows are gathered from the owning partitions
+  pcexp_group* grp = nullptr;
+  int part = -1;
+  int64_t n_local = 0, n_ghost = 0;
+  int32_t *g_src_part = nullptr, *g_src_elem = nullptr;  // [n_ghost] owning partition, its local index
+};
+
+// A partitioned run: one context per partition, each on its own device and stream, driven by
+// one host thread per partition during a group call.  The partitions meet in rounds: each
+// publishes a device pointer and records an event, all meet at a host barrier, each makes its
+// stream wait for the others' events and enqueues the work that reads their data, records a
+// second event, meets them again and waits for theirs.  So the data a round reads is complete
+// before it is read and is not overwritten before every partition has read it, with no device-side
+// wait between kernels.
+struct pcexp_group {
+  int n = 0;
+  std::vector<pcexp_ctx*> ctx;
+  std::vector<int> dev;
+  std::vector<cudaStream_t> st;
+  std::vector<std::vector<int64_t>> elems;  // per partition: global element of each local element
+  std::vector<double> own_volume;           // per partition: measure of its own elements
+  int64_t E = 0;
+  int nb = 0, nv = 0;
+  double volume = 0;
+  int fp32 = 0;
+  // rendezvous
+  std::mutex mu;
+  std::condition_variable cv;
+  int arrived = 0;
+  uint64_t gen = 0;
+  bool abort = false;
+  std::vector<const void*> pub;
+  std::vector<cudaEvent_t> ev_ready, ev_done;
+  std::vector<std::string> errs;
 };
 
 namespace {
@@ -150,6 +194,7 @@ DGData<T> dgdata(const pcexp_ctx* c) {
     d.BfP = tabs + (off + vec - 1) / vec * vec;
   }
   d.E = c->E;
+  d.E_loc = c->grp ? c->n_local : c->E;
   d.F = c->F;
   const double a = c->phys.alpha_deg * M_PI / 180.0;
   const double cinf = std::sqrt(c->phys.gamma * c->phys.p_inf / c->phys.rho_inf);
@@ -161,6 +206,11 @@ DGData<T> dgdata(const pcexp_ctx* c) {
   d.fs.vel[2] = T(0);
   d.p = c->p;
   d.dim = D;
+  d.rot = c->rot ? 1 : 0;
+  d.vrq = reinterpret_cast<const T*>(c->vrq);
+  d.vrn = reinterpret_cast<const T*>(c->vrn);
+  d.vrc = reinterpret_cast<const T*>(c->vrc);
+  for (int k = 0; k < 3; ++k) d.om[k] = (T)c->phys.omega[k];
   return d;
 }
 
@@ -225,10 +275,111 @@ void prof_note(pcexp_ctx* c, int cls, cudaEvent_t* e0, int offset) {
     }                                                              \
   } while (0)
 
+// ---- partitioned runs (pcexp_group): rendezvous, halo exchange, split reductions
+constexpr int GROUP_WAIT_S = 120;  // a partition not at a rendezvous by then has failed
+
+int group_barrier(pcexp_group* g) {
+  std::unique_lock<std::mutex> lk(g->mu);
+  if (g->abort) {
+    g_last_error = "another partition of the group failed";
+    return PCEXP_ERR_TIMEOUT;
+  }
+  const uint64_t my = g->gen;
+  if (++g->arrived == g->n) {
+    g->arrived = 0;
+    ++g->gen;
+    g->cv.notify_all();
+    return PCEXP_OK;
+  }
+  const auto until = std::chrono::steady_clock::now() + std::chrono::seconds(GROUP_WAIT_S);
+  while (g->gen == my && !g->abort)
+    if (g->cv.wait_until(lk, until) == std::cv_status::timeout && g->gen == my) {
+      g->abort = true;
+      g->cv.notify_all();
+      g_last_error = "partition rendezvous timed out";
+      return PCEXP_ERR_TIMEOUT;
+    }
+  if (g->gen == my) {
+    g_last_error = "another partition of the group failed";
+    return PCEXP_ERR_TIMEOUT;
+  }
+  return PCEXP_OK;
+}
+
+// One round: publish `mine`, then consume(pointers of all partitions) on every partition's
+// stream once every partition's work so far is complete; later work on any stream starts after
+// every partition's consume.
+template <class F>
+int group_round(pcexp_ctx* c, const void* mine, F&& consume) {
+  pcexp_group* g = c->grp;
+  const int me = c->part;
+  g->pub[me] = mine;
+  PCEXP_CK(cudaEventRecord(g->ev_ready[me], c->st));
+  PCEXP_TRY(group_barrier(g));
+  PartPtrs pp{};
+  for (int q = 0; q < g->n; ++q) {
+    pp.p[q] = g->pub[q];
+    if (q != me) PCEXP_CK(cudaStreamWaitEvent(c->st, g->ev_ready[q], 0));
+  }
+  PCEXP_TRY(consume(pp));
+  PCEXP_CK(cudaEventRecord(g->ev_done[me], c->st));
+  PCEXP_TRY(group_barrier(g));
+  for (int q = 0; q < g->n; ++q)
+    if (q != me) PCEXP_CK(cudaStreamWaitEvent(c->st, g->ev_done[q], 0));
+  return PCEXP_OK;
+}
+
+// Halo rows of x (a state-shaped vector of the partition) <- the owners' rows of the same vector.
+template <class T>
+int group_exchange(pcexp_ctx* c, const T* x) {
+  if (!c->grp) return PCEXP_OK;
+  T* xm = const_cast<T*>(x);  // the context's own buffer; only its halo rows are written
+  return group_round(c, x, [&](const PartPtrs& pp) -> int {
+    PCEXP_CK(launch_gather_ghosts<T>(xm, pp, c->g_src_part, c->g_src_elem, c->n_local, c->n_ghost,
+                                     c->nv * c->nb, c->st));
+    return PCEXP_OK;
+  });
+}
+
+// Halo rows of x <- 0: operator outputs and Krylov vectors carry zero halo rows, so that the
+// inner products over all local rows are sums over the own elements.
+template <class T>
+int group_zero_halo(pcexp_ctx* c, T* x) {
+  if (!c->grp) return PCEXP_OK;
+  const int64_t nvb = (int64_t)c->nv * c->nb;
+  PCEXP_CK(launch_zero_range<T>(x, c->n_local * nvb, (c->n_local + c->n_ghost) * nvb, c->st));
+  return PCEXP_OK;
+}
+
+template <class T> double* dev_field(T* base, size_t off) {
+  return reinterpret_cast<double*>(reinterpret_cast<char*>(base) + off);
+}
+
+// A Gram-Schmidt pass of a partitioned run left this partition's sums in ks->gsum: sum them
+// over the partitions (partition order, the same on every partition) and finalise the column.
+int group_cgs(pcexp_ctx* c, int mode, int j) {
+  if (!c->grp) return PCEXP_OK;
+  return group_round(c, dev_field(c->ks, offsetof(KState, gsum)), [&](const PartPtrs& pp) -> int {
+    PCEXP_CK(launch_group_reduce(pp, c->grp->n, MMAX + 2, dev_field(c->ks, offsetof(KState, gtot)), 0, c->st));
+    PCEXP_CK(launch_cgs_group_finalize(mode, j, c->ks, c->eta, c->st));
+    return PCEXP_OK;
+  });
+}
+
+// ss->dt <- the minimum over the partitions of their ss->dtmin_scratch (Eq. x3d over all elements)
+int group_min_dt(pcexp_ctx* c) {
+  return group_round(c, dev_field(c->ss, offsetof(StepState, dtmin_scratch)), [&](const PartPtrs& pp) -> int {
+    PCEXP_CK(launch_group_reduce(pp, c->grp->n, 1, dev_field(c->ss, offsetof(StepState, dt)), 1, c->st));
+    return PCEXP_OK;
+  });
+}
+
 // the two kernels of one DG operator application (face, element)
 template <class T>
 int dg_apply(pcexp_ctx* c, const DGData<T>& d, const T* u, const T* du, T* out, const T* escale, const int* skip,
              const double* oscale = nullptr) {
+  PCEXP_TRY(group_exchange<T>(c, u));
+  if (du) PCEXP_TRY(group_exchange<T>(c, du));
   cudaEvent_t* ev = prof_events(c, 3);
   cudaError_t e = launch_dg_operator<T>(d, u, du, out, reinterpret_cast<T*>(c->G), escale, skip, c->st, ev, oscale);
   if (ev) {
@@ -239,7 +390,7 @@ int dg_apply(pcexp_ctx* c, const DGData<T>& d, const T* u, const T* du, T* out, 
     g_last_error = std::string("DG operator launch: ") + cudaGetErrorString(e);
     return PCEXP_ERR_CUDA;
   }
-  return PCEXP_OK;
+  return group_zero_halo<T>(c, out);
 }
 
 template <class T> LinData<T> lindata(pcexp_ctx* c) {
@@ -263,6 +414,7 @@ int linearize(pcexp_ctx* c, const DGData<T>& d, const T* u, bool blocks = false)
 template <class T>
 int jac_apply(pcexp_ctx* c, const DGData<T>& d, const T* dv, T* out, const T* escale, const int* skip,
               const double* oscale) {
+  PCEXP_TRY(group_exchange<T>(c, dv));
   cudaEvent_t* ev = prof_events(c, 3);
   const T* u_elem = c->jv_tangent ? reinterpret_cast<const T*>(c->lin_state) : nullptr;
   cudaError_t e = launch_jac_apply<T>(d, lindata<T>(c), dv, out, reinterpret_cast<T*>(c->G), escale, skip, oscale,
@@ -275,7 +427,12 @@ int jac_apply(pcexp_ctx* c, const DGData<T>& d, const T* dv, T* out, const T* es
     g_last_error = std::string("Jacobian apply launch: ") + cudaGetErrorString(e);
     return PCEXP_ERR_CUDA;
   }
-  return PCEXP_OK;
+  if (c->grp) {
+    // a Krylov vector gets its zero halo rows back (the Gram-Schmidt sums run over all rows)
+    const T* V = reinterpret_cast<const T*>(c->V);
+    if (dv >= V && dv < V + (int64_t)(c->m_max + 1) * c->Kp) PCEXP_TRY(group_zero_halo<T>(c, const_cast<T*>(dv)));
+  }
+  return group_zero_halo<T>(c, out);
 }
 
 template <class T> T* Vcol(pcexp_ctx* c, int j) { return reinterpret_cast<T*>(c->V) + (int64_t)j * c->Kp; }
@@ -330,13 +487,17 @@ int arnoldi(pcexp_ctx* c, const T* escale, int m, const double* dt_dev = nullptr
   (void)G;
   PCEXP_LAUNCH(c, PCEXP_KC_OTHER, launch_reset_kstate(c->ks, c->st));
   PCEXP_LAUNCH(c, PCEXP_KC_CGS_NORM, launch_cgs<T>(CGS_NORM, V, c->Kp, c->Kp, 0, V, nullptr, c->ks, c->partials, c->eta, c->st));
+  PCEXP_TRY(group_cgs(c, CGS_NORM, 0));
   for (int j = 0; j < m; ++j) {
     // w = J v_j = s_j J z_j: the basis scale is applied to the output, so every
     // stored vector stays of the size of ||J|| (no growth like ||J||^j)
     PCEXP_TRY(jac_apply<T>(c, d, Vcol<T>(c, j), w, escale, &c->ks->done, &c->ks->s[j]));
     PCEXP_LAUNCH(c, PCEXP_KC_CGS_PROJ, launch_cgs<T>(CGS_PROJ, V, c->Kp, c->Kp, j, w, nullptr, c->ks, c->partials, c->eta, c->st));
+    PCEXP_TRY(group_cgs(c, CGS_PROJ, j));
     PCEXP_LAUNCH(c, PCEXP_KC_CGS_UPD_PROJ, launch_cgs<T>(CGS_UPD_PROJ, V, c->Kp, c->Kp, j, w, nullptr, c->ks, c->partials, c->eta, c->st));
+    PCEXP_TRY(group_cgs(c, CGS_UPD_PROJ, j));
     PCEXP_LAUNCH(c, PCEXP_KC_CGS_UPD_NORM, launch_cgs<T>(CGS_UPD_NORM, V, c->Kp, c->Kp, j, w, Vcol<T>(c, j + 1), c->ks, c->partials, c->eta, c->st));
+    PCEXP_TRY(group_cgs(c, CGS_UPD_NORM, j));
     if (c->ktol > 0 && dt_dev && (j + 1) % KRYLOV_CHECK == 0 && j + 1 < m)
       PCEXP_LAUNCH(c, PCEXP_KC_PHI, launch_phi_check(c->ks, dt_dev, c->ktol, c->st));
   }
@@ -433,6 +594,10 @@ int enqueue_step(pcexp_ctx* c, int scheme, int dt_mode, int m) {
   PCEXP_CK(cudaMemsetAsync(&c->ss->err, 0, sizeof(int), c->st));
   if (dt_mode == PCEXP_DT_GIVEN) {
     PCEXP_LAUNCH(c, PCEXP_KC_OTHER, launch_copy_dt(c->ss, c->param, c->st));
+  } else if (c->grp) {
+    // the minimum over the own elements, then over the partitions
+    PCEXP_LAUNCH(c, PCEXP_KC_DT, launch_local_dt<T>(d, S0, c->param, 0.0, dte, &c->ss->dtmin_scratch, c->partials, &c->ss->counter, c->st));
+    PCEXP_TRY(group_min_dt(c));
   } else {
     PCEXP_LAUNCH(c, PCEXP_KC_DT, launch_local_dt<T>(d, S0, c->param, 0.0, dte, &c->ss->dt, c->partials, &c->ss->counter, c->st));
     if (dt_mode == PCEXP_DT_LOCAL_CFL) {
@@ -462,8 +627,10 @@ int step_impl(pcexp_ctx* c, int scheme, int dt_mode, double dt_or_cfl, int m, pc
     c->h_Rc = r;
   }
   PCEXP_CK(launch_set_param(c->param, dt_or_cfl, c->st));
-  // an ETD2 step without history (ETD1) runs eagerly: its graph would differ from the others
-  if (c->prof || etd1_start) {
+  // an ETD2 step without history (ETD1) runs eagerly: its graph would differ from the others;
+  // so do the steps of a partition (their rounds synchronise with the other partitions' host
+  // threads)
+  if (c->prof || etd1_start || c->grp) {
     PCEXP_TRY(enqueue_step<T>(c, scheme, dt_mode, m));
   } else {
     // the first step of a configuration runs eagerly (it also initialises lazily
@@ -784,6 +951,83 @@ int project_adjoint_host(pcexp_ctx* c, int kind, const double* prm, int np, cons
   return PCEXP_OK;
 }
 
+// Checks omega against the mesh (no periodic faces, no far-field faces, rotation about z in
+// 2D) and uploads the frame arrays: v_r = omega x x at the volume points, v_r . n at the face
+// points of each face (its L element's points, the face rule over its local vertices), v_r at
+// the element centroids.
+int setup_rotation(pcexp_ctx* c, const pcexp_mesh* mesh) {
+  const double* om = c->phys.omega;
+  c->rot = om[0] != 0.0 || om[1] != 0.0 || om[2] != 0.0;
+  if (!c->rot) return PCEXP_OK;
+  const Setup& s = c->host;
+  const int D = c->dim;
+  if (D == 2 && (om[0] != 0.0 || om[1] != 0.0)) {
+    g_last_error = "in 2D the frame rotates about z: omega = (0, 0, omega_z)";
+    return PCEXP_ERR_INVALID_ARG;
+  }
+  if (!mesh || !mesh->coords) {
+    g_last_error = "the rotating frame is set up when the context is created";
+    return PCEXP_ERR_INVALID_ARG;
+  }
+  if (mesh->vert_master)
+    for (int64_t v = 0; v < mesh->n_vert; ++v)
+      if (mesh->vert_master[v] != v) {
+        g_last_error = "a rotating frame needs a mesh without periodic faces (v_r depends on position)";
+        return PCEXP_ERR_INVALID_ARG;
+      }
+  for (int64_t f = 0; f < s.F; ++f)
+    if (s.fel[2 * f + 1] == -PCEXP_BC_FARFIELD) {
+      g_last_error = "far-field faces are not defined in a rotating frame";
+      return PCEXP_ERR_INVALID_ARG;
+    }
+  auto vr_at = [&](const double* x, double* out) {  // omega x x (x-y components in 2D)
+    const double X[3] = {x[0], x[1], D == 3 ? x[2] : 0.0};
+    const double r[3] = {om[1] * X[2] - om[2] * X[1], om[2] * X[0] - om[0] * X[2], om[0] * X[1] - om[1] * X[0]};
+    for (int k = 0; k < D; ++k) out[k] = r[k];
+  };
+  std::vector<double> vq((size_t)c->E * c->nq * D), vn((size_t)(s.F > 0 ? s.F : 1) * c->nfq, 0.0),
+      vc((size_t)c->E * D);
+  for (int64_t i = 0; i < c->E * c->nq; ++i) vr_at(&s.xqphys[(size_t)i * D], &vq[(size_t)i * D]);
+  const int NF = D + 1;
+  for (int64_t e = 0; e < c->E; ++e) {
+    double x[3] = {0, 0, 0};
+    for (int k = 0; k <= D; ++k)
+      for (int d = 0; d < D; ++d) x[d] += mesh->coords[(size_t)D * mesh->elem_vert[(size_t)(D + 1) * e + k] + d];
+    for (int d = 0; d < D; ++d) x[d] /= (D + 1);
+    vr_at(x, &vc[(size_t)e * D]);
+  }
+  for (int64_t f = 0; f < s.F; ++f) {
+    const int64_t eL = s.fel[2 * f];
+    const int fL = s.floc[f] & 0xff;
+    for (int q = 0; q < c->nfq; ++q) {
+      double x[3] = {0, 0, 0}, v[3];
+      for (int k = 0; k < D; ++k) {
+        const int32_t vtx = mesh->elem_vert[(size_t)(D + 1) * eL + (fL + 1 + k) % NF];
+        for (int d = 0; d < D; ++d) x[d] += s.flam[(size_t)q * D + k] * mesh->coords[(size_t)D * vtx + d];
+      }
+      vr_at(x, v);
+      double a = 0;
+      for (int d = 0; d < D; ++d) a += v[d] * s.fgeo[4 * f + d];
+      vn[(size_t)f * c->nfq + q] = a;
+    }
+  }
+  if (c->fp32) {
+    PCEXP_TRY(upload<float>(c, &c->vrq, vq));
+    PCEXP_TRY(upload<float>(c, &c->vrn, vn));
+    PCEXP_TRY(upload<float>(c, &c->vrc, vc));
+  } else {
+    PCEXP_TRY(upload<double>(c, &c->vrq, vq));
+    PCEXP_TRY(upload<double>(c, &c->vrn, vn));
+    PCEXP_TRY(upload<double>(c, &c->vrc, vc));
+  }
+  return PCEXP_OK;
+}
+
+int UNSUPPORTED_ROTATING(const char* what) {
+  g_last_error = std::string(what) + " is not provided in a rotating frame";
+  return PCEXP_ERR_UNSUPPORTED;
+}
+
 int UNSUPPORTED_FP32_HESS(pcexp_ctx*) {
   g_last_error = "the second-order adjoint is provided for the FP64 form";
   return PCEXP_ERR_UNSUPPORTED;
@@ -802,9 +1046,10 @@ int check_ctx(const pcexp_ctx* c) {
   return PCEXP_OK;
 }
 
-int create_impl(pcexp_ctx* c, const pcexp_mesh* mesh, int p, const pcexp_physics* phys, const pcexp_options* opt) {
+int create_impl(pcexp_ctx* c, const pcexp_mesh* mesh, int p, const pcexp_physics* phys, const pcexp_options* opt,
+                const int64_t* elem_key = nullptr) {
   std::string msg;
-  int r = build_setup(*mesh, p, c->host, msg);
+  int r = build_setup(*mesh, p, c->host, msg, elem_key);
   if (r != PCEXP_OK) {
     g_last_error = msg;
     return r;
@@ -906,6 +1151,7 @@ int create_impl(pcexp_ctx* c, const pcexp_mesh* mesh, int p, const pcexp_physics
   PCEXP_TRY(dalloc(c, &c->param, 1));
   (void)es;
   PCEXP_CK(cudaStreamSynchronize(c->st));
+  PCEXP_TRY(setup_rotation(c, mesh));
   // free-stream initial state
   std::vector<double> u;
   PCEXP_TRY(project_host(c, PCEXP_PROJ_FREESTREAM, nullptr, 0, u));
@@ -1251,6 +1497,7 @@ int pcexp_jvp_state_adjoint(pcexp_ctx* c, const double* U, const double* v, cons
   PCEXP_TRY(check_ctx(c));
   if (!U || !v || !w || !out) return PCEXP_ERR_INVALID_ARG;
   if (c->fp32) return UNSUPPORTED_FP32_HESS(c);
+  if (c->rot) return UNSUPPORTED_ROTATING("the second-order adjoint");
   double* a = reinterpret_cast<double*>(c->tmp);
   double* b = reinterpret_cast<double*>(c->delta);
   double* ww = reinterpret_cast<double*>(c->V);  // V[0] as scratch
@@ -1371,6 +1618,11 @@ int pcexp_functional(pcexp_ctx* c, int kind, const double* U, double* value, dou
 int pcexp_set_physics(pcexp_ctx* c, const pcexp_physics* phys) {
   PCEXP_TRY(check_ctx(c));
   if (!phys || !(phys->gamma > 1.0) || !(phys->rho_inf > 0) || !(phys->p_inf > 0)) return PCEXP_ERR_INVALID_ARG;
+  for (int k = 0; k < 3; ++k)
+    if (phys->omega[k] != c->phys.omega[k]) {
+      g_last_error = "omega is fixed when the context is created (its frame arrays depend on the mesh)";
+      return PCEXP_ERR_INVALID_ARG;
+    }
   PCEXP_CK(cudaStreamSynchronize(c->st));
   c->phys = *phys;
   // captured steps hold the old free stream in their kernel arguments
@@ -1389,6 +1641,7 @@ int pcexp_step_backward(pcexp_ctx* c, const double* U, double dt, int m, const d
     g_last_error = "the reverse step is provided for the FP64 form";
     return PCEXP_ERR_UNSUPPORTED;
   }
+  if (c->rot) return UNSUPPORTED_ROTATING("the reverse step");
   return step_backward_impl(c, U, dt, m, ubar_next, ubar, theta_bar, on_device);
 }
 
@@ -1562,6 +1815,12 @@ int pcexp_fp64_fma_rate(double* tflops) {
   return PCEXP_OK;
 }
 
+int pcexp_fp32_fma_rate(double* tflops) {
+  if (!tflops) return PCEXP_ERR_INVALID_ARG;
+  PCEXP_CK(measure_fp32_fma_rate(tflops));
+  return PCEXP_OK;
+}
+
 const char* pcexp_last_error(void) { return g_last_error.c_str(); }
 
 const char* pcexp_status_string(int status) {
@@ -1572,10 +1831,440 @@ const char* pcexp_status_string(int status) {
     case PCEXP_ERR_CUDA: return "CUDA error";
     case PCEXP_ERR_OOM: return "out of device memory";
     case PCEXP_ERR_NONFINITE: return "non-finite value";
-    case PCEXP_ERR_TIMEOUT: return "device wait timed out";
+    case PCEXP_ERR_TIMEOUT: return "wait timed out (partition rendezvous)";
     case PCEXP_ERR_UNSUPPORTED: return "unsupported request";
   }
   return "unknown status";
+}
+
+}  // extern "C"
+
+// ================================================================ partitioned runs
+namespace {
+
+int check_opts(const pcexp_physics* phys, const pcexp_options* opt) {
+  if (opt->m_max < 1 || opt->m_max > PCEXP_MAX_KRYLOV) return PCEXP_ERR_INVALID_ARG;
+  if (opt->precision != PCEXP_FP64 && opt->precision != PCEXP_FP32_MIXED) return PCEXP_ERR_INVALID_ARG;
+  if (opt->basis_io != PCEXP_BASIS_PAPER && opt->basis_io != PCEXP_BASIS_INTERNAL) return PCEXP_ERR_INVALID_ARG;
+  if (!(phys->gamma > 1.0) || !(phys->rho_inf > 0) || !(phys->p_inf > 0)) return PCEXP_ERR_INVALID_ARG;
+  return PCEXP_OK;
+}
+
+// Runs fn(k) for every partition, each on a host thread of its own with its device current.
+// The first failure that is not another partition's failure seen at a rendezvous is reported.
+template <class F>
+int group_run(pcexp_group* g, F&& fn) {
+  {
+    std::lock_guard<std::mutex> lk(g->mu);
+    g->abort = false;
+    g->arrived = 0;
+  }
+  std::vector<int> rc((size_t)g->n, PCEXP_OK);
+  std::vector<std::string> err((size_t)g->n);
+  auto body = [&](int k) {
+    if (cudaSetDevice(g->dev[(size_t)k]) != cudaSuccess) {
+      rc[(size_t)k] = PCEXP_ERR_CUDA;
+      err[(size_t)k] = "cudaSetDevice failed";
+    } else {
+      rc[(size_t)k] = fn(k);
+      if (rc[(size_t)k] != PCEXP_OK) err[(size_t)k] = g_last_error;
+    }
+    if (rc[(size_t)k] != PCEXP_OK) {
+      std::lock_guard<std::mutex> lk(g->mu);
+      g->abort = true;
+      g->cv.notify_all();
+    }
+  };
+  if (g->n == 1) {
+    body(0);
+  } else {
+    std::vector<std::thread> th;
+    for (int k = 0; k < g->n; ++k) th.emplace_back(body, k);
+    for (auto& t : th) t.join();
+  }
+  for (int pass = 0; pass < 2; ++pass)
+    for (int k = 0; k < g->n; ++k)
+      if (rc[(size_t)k] != PCEXP_OK && (pass == 1 || rc[(size_t)k] != PCEXP_ERR_TIMEOUT)) {
+        g_last_error = "partition " + std::to_string(k) + ": " + err[(size_t)k];
+        return rc[(size_t)k];
+      }
+  return PCEXP_OK;
+}
+
+int check_group(pcexp_group* g) {
+  if (!g) {
+    g_last_error = "null group";
+    return PCEXP_ERR_INVALID_ARG;
+  }
+  return PCEXP_OK;
+}
+
+// local vector of partition k (its elements' rows of a global state-shaped host array); halo rows
+// are left zero when `halo` is false
+void gather_local(const pcexp_group* g, int k, const double* U, std::vector<double>& loc, bool halo) {
+  const int64_t nvb = (int64_t)g->nv * g->nb;
+  const auto& el = g->elems[(size_t)k];
+  const int64_t n = halo ? (int64_t)el.size() : g->ctx[(size_t)k]->n_local;
+  loc.assign(el.size() * (size_t)nvb, 0.0);
+  for (int64_t e = 0; e < n; ++e) std::memcpy(&loc[(size_t)(e * nvb)], U + el[(size_t)e] * nvb, (size_t)nvb * 8);
+}
+
+void scatter_owned(const pcexp_group* g, int k, const std::vector<double>& loc, double* U) {
+  const int64_t nvb = (int64_t)g->nv * g->nb;
+  const auto& el = g->elems[(size_t)k];
+  for (int64_t e = 0; e < g->ctx[(size_t)k]->n_local; ++e)
+    std::memcpy(U + el[(size_t)e] * nvb, &loc[(size_t)(e * nvb)], (size_t)nvb * 8);
+}
+
+// R (and J v with v) of a partition whose inputs carry only their own rows: the halo rows come
+// from the exchange of the operator passes
+template <class T>
+int group_operator_part(pcexp_ctx* c, const std::vector<double>& u, const std::vector<double>* v, std::vector<double>& out) {
+  const DGData<T> d = dgdata<T>(c);
+  T* a = reinterpret_cast<T*>(c->tmp);
+  T* b = reinterpret_cast<T*>(c->delta);
+  T* o = reinterpret_cast<T*>(c->w);
+  PCEXP_TRY(import_vec<T>(c, u.data(), 0, a));
+  if (!v) {
+    PCEXP_TRY(dg_apply<T>(c, d, a, nullptr, o, nullptr, nullptr));
+  } else {
+    PCEXP_TRY(import_vec<T>(c, v->data(), 0, b));
+    PCEXP_TRY(group_exchange<T>(c, a));
+    PCEXP_TRY(linearize<T>(c, d, a));
+    PCEXP_TRY(jac_apply<T>(c, d, b, o, nullptr, nullptr, nullptr));
+  }
+  out.assign((size_t)c->K, 0.0);
+  return export_vec<T>(c, o, out.data(), 0);
+}
+
+template <class T>
+int group_arnoldi_part(pcexp_ctx* c, const std::vector<double>& u, const std::vector<double>& b, int m, KState* hk) {
+  const DGData<T> d = dgdata<T>(c);
+  T* lin = reinterpret_cast<T*>(c->delta);
+  PCEXP_TRY(import_vec<T>(c, u.data(), 0, lin));
+  PCEXP_TRY(import_vec<T>(c, b.data(), 0, Vcol<T>(c, 0)));
+  PCEXP_TRY(group_exchange<T>(c, lin));
+  PCEXP_TRY(linearize<T>(c, d, lin));
+  PCEXP_TRY(arnoldi<T>(c, nullptr, m, nullptr));
+  PCEXP_CK(cudaMemcpyAsync(hk, c->ks, sizeof(KState), cudaMemcpyDeviceToHost, c->st));
+  PCEXP_CK(cudaStreamSynchronize(c->st));
+  return PCEXP_OK;
+}
+
+}  // namespace
+
+extern "C" {
+
+int pcexp_partition(const pcexp_mesh* mesh, int n_parts, int32_t* part) {
+  if (!mesh || !part || n_parts < 1 || n_parts > MAX_PARTS || mesh->n_elem < n_parts ||
+      (mesh->dim != 2 && mesh->dim != 3)) {
+    g_last_error = "invalid partition request";
+    return PCEXP_ERR_INVALID_ARG;
+  }
+  rcb_partition(*mesh, n_parts, part);
+  return PCEXP_OK;
+}
+
+int pcexp_partition_halo(const pcexp_mesh* mesh, const int32_t* part, int n_parts, int k, int64_t* n_owned,
+                         int64_t* n_total, int64_t* elems) {
+  if (!mesh || !part || n_parts < 1 || k < 0 || k >= n_parts || !n_owned || !n_total) return PCEXP_ERR_INVALID_ARG;
+  for (int64_t e = 0; e < mesh->n_elem; ++e)
+    if (part[e] < 0 || part[e] >= n_parts) {
+      g_last_error = "partition index out of range";
+      return PCEXP_ERR_INVALID_ARG;
+    }
+  std::vector<int64_t> nbr;
+  std::string msg;
+  int r = face_neighbours(*mesh, nbr, msg);
+  if (r != PCEXP_OK) {
+    g_last_error = msg;
+    return r;
+  }
+  Halo h;
+  build_halo(*mesh, nbr, part, k, h);
+  *n_owned = h.n_owned;
+  *n_total = (int64_t)h.elems.size();
+  if (elems) std::memcpy(elems, h.elems.data(), h.elems.size() * sizeof(int64_t));
+  return PCEXP_OK;
+}
+
+int pcexp_group_destroy(pcexp_group* g) {
+  if (!g) return PCEXP_OK;
+  for (int k = 0; k < g->n; ++k) {
+    cudaSetDevice(g->dev[(size_t)k]);
+    if (k < (int)g->ctx.size() && g->ctx[(size_t)k]) pcexp_destroy(g->ctx[(size_t)k]);
+    if (k < (int)g->ev_ready.size() && g->ev_ready[(size_t)k]) cudaEventDestroy(g->ev_ready[(size_t)k]);
+    if (k < (int)g->ev_done.size() && g->ev_done[(size_t)k]) cudaEventDestroy(g->ev_done[(size_t)k]);
+    if (k < (int)g->st.size() && g->st[(size_t)k]) cudaStreamDestroy(g->st[(size_t)k]);
+  }
+  delete g;
+  return PCEXP_OK;
+}
+
+int pcexp_group_create(pcexp_group** out, const pcexp_mesh* mesh, const int32_t* part, int n_parts,
+                       const int32_t* devices, int p, const pcexp_physics* phys, const pcexp_options* opt) {
+  if (!out) return PCEXP_ERR_INVALID_ARG;
+  *out = nullptr;
+  if (!mesh || !part || !phys || !opt || n_parts < 1 || n_parts > MAX_PARTS) return PCEXP_ERR_INVALID_ARG;
+  PCEXP_TRY(check_opts(phys, opt));
+  std::vector<int64_t> count((size_t)n_parts, 0);
+  for (int64_t e = 0; e < mesh->n_elem; ++e) {
+    if (part[e] < 0 || part[e] >= n_parts) {
+      g_last_error = "partition index out of range";
+      return PCEXP_ERR_INVALID_ARG;
+    }
+    ++count[(size_t)part[e]];
+  }
+  for (int64_t c : count)
+    if (c == 0) {
+      g_last_error = "empty partition";
+      return PCEXP_ERR_INVALID_ARG;
+    }
+  int dev0 = 0;
+  cudaGetDevice(&dev0);
+  std::vector<int64_t> nbr;
+  std::string msg;
+  int r = face_neighbours(*mesh, nbr, msg);
+  if (r != PCEXP_OK) {
+    g_last_error = msg;
+    return r;
+  }
+  pcexp_group* g = new pcexp_group();
+  g->n = n_parts;
+  g->E = mesh->n_elem;
+  g->ctx.assign((size_t)n_parts, nullptr);
+  g->st.assign((size_t)n_parts, nullptr);
+  g->ev_ready.assign((size_t)n_parts, nullptr);
+  g->ev_done.assign((size_t)n_parts, nullptr);
+  g->pub.assign((size_t)n_parts, nullptr);
+  g->elems.resize((size_t)n_parts);
+  g->own_volume.assign((size_t)n_parts, 0.0);
+  g->fp32 = opt->precision == PCEXP_FP32_MIXED;
+  for (int k = 0; k < n_parts; ++k) g->dev.push_back(devices ? devices[k] : dev0);
+  auto fail = [&](int code) {
+    const std::string keep = g_last_error;
+    pcexp_group_destroy(g);
+    cudaSetDevice(dev0);
+    g_last_error = keep;
+    return code;
+  };
+  std::vector<int64_t> n_owned((size_t)n_parts);
+  for (int k = 0; k < n_parts; ++k) {
+    Halo h;
+    build_halo(*mesh, nbr, part, k, h);
+    Submesh sm;
+    if ((r = build_submesh(*mesh, h, sm, msg)) != PCEXP_OK) {
+      g_last_error = msg;
+      return fail(r);
+    }
+    if (cudaSetDevice(g->dev[(size_t)k]) != cudaSuccess ||
+        cudaStreamCreateWithFlags(&g->st[(size_t)k], cudaStreamNonBlocking) != cudaSuccess ||
+        cudaEventCreateWithFlags(&g->ev_ready[(size_t)k], cudaEventDisableTiming) != cudaSuccess ||
+        cudaEventCreateWithFlags(&g->ev_done[(size_t)k], cudaEventDisableTiming) != cudaSuccess) {
+      g_last_error = "stream or event creation failed on the partition's device";
+      return fail(PCEXP_ERR_CUDA);
+    }
+    pcexp_ctx* c = new pcexp_ctx();
+    g->ctx[(size_t)k] = c;
+    c->device = g->dev[(size_t)k];
+    c->st = g->st[(size_t)k];
+    const pcexp_mesh mv = sm.view();
+    if ((r = create_impl(c, &mv, p, phys, opt, h.elems.data())) != PCEXP_OK) return fail(r);
+    c->grp = g;
+    c->part = k;
+    c->n_local = h.n_owned;
+    c->n_ghost = (int64_t)h.elems.size() - h.n_owned;
+    // own measure: sqrt|det A| is entry D^2 of an element's geometry row; |E| = |det A| / D!
+    const int D = c->dim, G = D == 2 ? 8 : 12;
+    for (int64_t e = 0; e < h.n_owned; ++e) {
+      const double sd = c->host.geo[(size_t)(e * G + D * D)];
+      g->own_volume[(size_t)k] += sd * sd / (D == 2 ? 2.0 : 6.0);
+    }
+    g->nb = c->nb;
+    g->nv = c->nv;
+    n_owned[(size_t)k] = h.n_owned;
+    g->elems[(size_t)k] = std::move(h.elems);
+  }
+  for (double v : g->own_volume) g->volume += v;
+  // halo maps: owning partition and its local index of every halo element
+  for (int k = 0; k < n_parts; ++k) {
+    pcexp_ctx* c = g->ctx[(size_t)k];
+    cudaSetDevice(c->device);
+    const auto& el = g->elems[(size_t)k];
+    std::vector<int32_t> sp((size_t)c->n_ghost + 1, 0), se((size_t)c->n_ghost + 1, 0);
+    for (int64_t i = 0; i < c->n_ghost; ++i) {
+      const int64_t ge = el[(size_t)(c->n_local + i)];
+      const int q = part[ge];
+      const auto& eq = g->elems[(size_t)q];
+      const auto it = std::lower_bound(eq.begin(), eq.begin() + n_owned[(size_t)q], ge);
+      sp[(size_t)i] = q;
+      se[(size_t)i] = (int32_t)(it - eq.begin());
+    }
+    if (dalloc(c, &c->g_src_part, sp.size()) != PCEXP_OK || dalloc(c, &c->g_src_elem, se.size()) != PCEXP_OK)
+      return fail(PCEXP_ERR_OOM);
+    const int group_flag = 1;
+    if (cudaMemcpyAsync(c->g_src_part, sp.data(), sp.size() * 4, cudaMemcpyHostToDevice, c->st) != cudaSuccess ||
+        cudaMemcpyAsync(c->g_src_elem, se.data(), se.size() * 4, cudaMemcpyHostToDevice, c->st) != cudaSuccess ||
+        cudaMemcpyAsync(reinterpret_cast<char*>(c->ks) + offsetof(KState, group), &group_flag, sizeof(int),
+                        cudaMemcpyHostToDevice, c->st) != cudaSuccess ||
+        cudaStreamSynchronize(c->st) != cudaSuccess) {
+      g_last_error = "upload of the halo maps failed";
+      return fail(PCEXP_ERR_CUDA);
+    }
+    // the halo gather reads the other partitions' buffers directly
+    for (int q = 0; q < n_parts; ++q) {
+      const int dq = g->dev[(size_t)q];
+      if (dq == c->device) continue;
+      int can = 0;
+      cudaDeviceCanAccessPeer(&can, c->device, dq);
+      if (!can) {
+        g_last_error = "partitions on devices without peer access";
+        return fail(PCEXP_ERR_UNSUPPORTED);
+      }
+      const cudaError_t pe = cudaDeviceEnablePeerAccess(dq, 0);
+      if (pe != cudaSuccess && pe != cudaErrorPeerAccessAlreadyEnabled) {
+        g_last_error = std::string("cudaDeviceEnablePeerAccess: ") + cudaGetErrorString(pe);
+        return fail(PCEXP_ERR_CUDA);
+      }
+      cudaGetLastError();  // clear an already-enabled status
+    }
+  }
+  cudaSetDevice(dev0);
+  *out = g;
+  return PCEXP_OK;
+}
+
+int pcexp_group_sizes(const pcexp_group* g, int k, int64_t* n_owned, int64_t* n_halo) {
+  if (!g || k < 0 || k >= g->n) return PCEXP_ERR_INVALID_ARG;
+  if (n_owned) *n_owned = g->ctx[(size_t)k]->n_local;
+  if (n_halo) *n_halo = g->ctx[(size_t)k]->n_ghost;
+  return PCEXP_OK;
+}
+
+int pcexp_group_set_state(pcexp_group* g, const double* U) {
+  PCEXP_TRY(check_group(g));
+  if (!U) return PCEXP_ERR_INVALID_ARG;
+  int dev0 = 0;
+  cudaGetDevice(&dev0);
+  std::vector<double> loc;
+  for (int k = 0; k < g->n; ++k) {
+    gather_local(g, k, U, loc, true);
+    const int r = pcexp_set_state(g->ctx[(size_t)k], loc.data(), 0);
+    if (r != PCEXP_OK) return r;
+  }
+  cudaSetDevice(dev0);
+  return PCEXP_OK;
+}
+
+int pcexp_group_get_state(pcexp_group* g, double* U) {
+  PCEXP_TRY(check_group(g));
+  if (!U) return PCEXP_ERR_INVALID_ARG;
+  int dev0 = 0;
+  cudaGetDevice(&dev0);
+  std::vector<double> loc;
+  for (int k = 0; k < g->n; ++k) {
+    loc.assign((size_t)g->ctx[(size_t)k]->K, 0.0);
+    const int r = pcexp_get_state(g->ctx[(size_t)k], loc.data(), 0);
+    if (r != PCEXP_OK) return r;
+    scatter_owned(g, k, loc, U);
+  }
+  cudaSetDevice(dev0);
+  return PCEXP_OK;
+}
+
+int pcexp_group_project_state(pcexp_group* g, int kind, const double* params, int n_params) {
+  PCEXP_TRY(check_group(g));
+  int dev0 = 0;
+  cudaGetDevice(&dev0);
+  for (int k = 0; k < g->n; ++k) {
+    const int r = pcexp_project_state(g->ctx[(size_t)k], kind, params, n_params);
+    if (r != PCEXP_OK) return r;
+  }
+  cudaSetDevice(dev0);
+  return PCEXP_OK;
+}
+
+static int group_operator(pcexp_group* g, const double* U, const double* v, double* out) {
+  PCEXP_TRY(check_group(g));
+  if (!U || !out) return PCEXP_ERR_INVALID_ARG;
+  std::vector<std::vector<double>> res((size_t)g->n);
+  PCEXP_TRY(group_run(g, [&](int k) -> int {
+    pcexp_ctx* c = g->ctx[(size_t)k];
+    std::vector<double> u, dv;
+    gather_local(g, k, U, u, false);
+    if (v) gather_local(g, k, v, dv, false);
+    return c->fp32 ? group_operator_part<float>(c, u, v ? &dv : nullptr, res[(size_t)k])
+                   : group_operator_part<double>(c, u, v ? &dv : nullptr, res[(size_t)k]);
+  }));
+  for (int k = 0; k < g->n; ++k) scatter_owned(g, k, res[(size_t)k], out);
+  return PCEXP_OK;
+}
+
+int pcexp_group_residual(pcexp_group* g, const double* U, double* R) { return group_operator(g, U, nullptr, R); }
+
+int pcexp_group_jvp(pcexp_group* g, const double* U, const double* v, double* Jv) {
+  if (!v) return PCEXP_ERR_INVALID_ARG;
+  return group_operator(g, U, v, Jv);
+}
+
+int pcexp_group_arnoldi(pcexp_group* g, const double* U, const double* b, int m, double* H, int* k, double* beta) {
+  PCEXP_TRY(check_group(g));
+  if (!U || !b || m < 1 || m > g->ctx[0]->m_max) return PCEXP_ERR_INVALID_ARG;
+  std::vector<KState> hk((size_t)g->n);
+  PCEXP_TRY(group_run(g, [&](int q) -> int {
+    pcexp_ctx* c = g->ctx[(size_t)q];
+    std::vector<double> u, bb;
+    gather_local(g, q, U, u, false);
+    gather_local(g, q, b, bb, false);
+    return c->fp32 ? group_arnoldi_part<float>(c, u, bb, m, &hk[(size_t)q])
+                   : group_arnoldi_part<double>(c, u, bb, m, &hk[(size_t)q]);
+  }));
+  for (int q = 1; q < g->n; ++q)
+    if (hk[(size_t)q].k != hk[0].k ||
+        std::memcmp(hk[(size_t)q].H, hk[0].H, sizeof(double) * (MMAX + 1) * MMAX) != 0) {
+      g_last_error = "partitions disagree on the Hessenberg matrix";
+      return PCEXP_ERR_CUDA;
+    }
+  if (hk[0].err) {
+    g_last_error = "non-finite Arnoldi quantity";
+    return PCEXP_ERR_NONFINITE;
+  }
+  const int kk = hk[0].k;
+  if (k) *k = kk;
+  if (beta) *beta = hk[0].beta;
+  if (H)
+    for (int i = 0; i <= m; ++i)
+      for (int j = 0; j < m; ++j) H[i * m + j] = (i <= kk && j < kk) ? hk[0].H[i * MMAX + j] : 0.0;
+  return PCEXP_OK;
+}
+
+int pcexp_group_step(pcexp_group* g, int scheme, int dt_mode, double dt_or_cfl, int m, pcexp_step_info* info) {
+  PCEXP_TRY(check_group(g));
+  if (scheme != PCEXP_SCHEME_PCEXP && scheme != PCEXP_SCHEME_EXP1 && scheme != PCEXP_SCHEME_ETD2)
+    return PCEXP_ERR_INVALID_ARG;
+  if (dt_mode == PCEXP_DT_LOCAL_CFL) {
+    g_last_error = "local time steps are not available in a partitioned run";
+    return PCEXP_ERR_UNSUPPORTED;
+  }
+  if (dt_mode != PCEXP_DT_GIVEN && dt_mode != PCEXP_DT_GLOBAL_CFL) return PCEXP_ERR_INVALID_ARG;
+  if (m < 1 || m > g->ctx[0]->m_max || !(dt_or_cfl > 0)) return PCEXP_ERR_INVALID_ARG;
+  std::vector<pcexp_step_info> inf((size_t)g->n);
+  PCEXP_TRY(group_run(g, [&](int k) -> int {
+    pcexp_ctx* c = g->ctx[(size_t)k];
+    return c->fp32 ? step_impl<float>(c, scheme, dt_mode, dt_or_cfl, m, &inf[(size_t)k])
+                   : step_impl<double>(c, scheme, dt_mode, dt_or_cfl, m, &inf[(size_t)k]);
+  }));
+  if (info) {
+    *info = inf[0];
+    // each partition's norm is (its sum of squares)^(1/2) / its measure (own and halo elements)
+    double s2 = 0;
+    for (int k = 0; k < g->n; ++k) {
+      const double a = inf[(size_t)k].res_norm * g->ctx[(size_t)k]->volume;
+      s2 += a * a;
+    }
+    info->res_norm = std::sqrt(s2) / g->volume;
+  }
+  return PCEXP_OK;
 }
 
 }  // extern "C"

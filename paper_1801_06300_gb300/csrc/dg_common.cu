@@ -191,36 +191,41 @@ cudaError_t launch_scale_by_inverse(double* x, const double* s, int64_t n, cudaS
 // memory traffic.  The result depends on the inputs only through the final store, which a
 // comparison that never holds keeps alive.
 constexpr int FMA_CHAINS = 8;
-__global__ void __launch_bounds__(256) dfma_chain_kernel(double* out, int iters, double a, double b) {
-  double x[FMA_CHAINS];
+template <class T>
+__global__ void __launch_bounds__(256) fma_chain_kernel(T* out, int iters, T a, T b) {
+  T x[FMA_CHAINS];
 #pragma unroll
-  for (int k = 0; k < FMA_CHAINS; ++k) x[k] = 1e-3 * (threadIdx.x + k);
+  for (int k = 0; k < FMA_CHAINS; ++k) x[k] = T(1e-3) * (T)(threadIdx.x + k);
   for (int i = 0; i < iters; ++i)
 #pragma unroll
     for (int k = 0; k < FMA_CHAINS; ++k) x[k] = fma(x[k], a, b);
-  double s = 0;
+  T s = 0;
 #pragma unroll
   for (int k = 0; k < FMA_CHAINS; ++k) s += x[k];
-  if (s == -1.0) out[blockIdx.x] = s;
+  if (s == T(-1)) out[blockIdx.x] = s;
 }
 
-cudaError_t measure_fp64_fma_rate(double* tflops) {
+// FMA rate (TFLOP/s, an FMA counts 2) of the current device in FP64 or FP32: independent
+// chains on 8 blocks of 256 threads per SM, best of three timed launches after a warm-up.
+template <class T>
+cudaError_t measure_fma_rate(double* tflops) {
   int dev = 0, sms = 0;
   cudaError_t e = cudaGetDevice(&dev);
   if (e == cudaSuccess) e = cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
   if (e != cudaSuccess) return e;
   cudaStream_t st = nullptr;
   cudaEvent_t e0 = nullptr, e1 = nullptr;
-  double* out = nullptr;
+  T* out = nullptr;
   if ((e = cudaStreamCreateWithFlags(&st, cudaStreamNonBlocking)) != cudaSuccess) return e;
   e = cudaEventCreate(&e0);
   if (e == cudaSuccess) e = cudaEventCreate(&e1);
-  if (e == cudaSuccess) e = cudaMalloc(&out, sizeof(double) * sms * 8);
-  const int iters = 1 << 14, blocks = sms * 8, threads = 256;
+  if (e == cudaSuccess) e = cudaMalloc(&out, sizeof(T) * sms * 8);
+  // FP32 FMAs issue far faster than FP64 ones: more iterations keep the launch near 10 ms
+  const int iters = sizeof(T) == 8 ? 1 << 14 : 1 << 17, blocks = sms * 8, threads = 256;
   float best = 1e30f;
   for (int rep = 0; e == cudaSuccess && rep < 4; ++rep) {
     cudaEventRecord(e0, st);
-    dfma_chain_kernel<<<blocks, threads, 0, st>>>(out, iters, 0.9999999, 1e-7);
+    fma_chain_kernel<T><<<blocks, threads, 0, st>>>(out, iters, T(0.9999999), T(1e-7));
     cudaEventRecord(e1, st);
     e = cudaEventSynchronize(e1);
     float ms = 0;
@@ -234,6 +239,39 @@ cudaError_t measure_fp64_fma_rate(double* tflops) {
   cudaStreamDestroy(st);
   return e;
 }
+cudaError_t measure_fp64_fma_rate(double* tflops) { return measure_fma_rate<double>(tflops); }
+cudaError_t measure_fp32_fma_rate(double* tflops) { return measure_fma_rate<float>(tflops); }
+
+// ---- partitioned runs: ghost element rows from the owning partitions
+template <class T>
+__global__ void gather_ghosts_kernel(T* __restrict__ x, PartPtrs srcs, const int32_t* __restrict__ src_part,
+                                     const int32_t* __restrict__ src_elem, int64_t n_local, int64_t n_ghost, int nvb) {
+  const int64_t n = n_ghost * nvb;
+  for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) {
+    const int64_t g = i / nvb;
+    const int k = (int)(i - g * nvb);
+    const T* src = reinterpret_cast<const T*>(srcs.p[src_part[g]]);
+    x[(n_local + g) * nvb + k] = src[(int64_t)src_elem[g] * nvb + k];
+  }
+}
+template <class T>
+cudaError_t launch_gather_ghosts(T* x, PartPtrs srcs, const int32_t* src_part, const int32_t* src_elem, int64_t n_local,
+                                 int64_t n_ghost, int nvb, cudaStream_t st) {
+  if (n_ghost <= 0) return cudaSuccess;
+  gather_ghosts_kernel<T><<<grid_for(n_ghost * nvb), 256, 0, st>>>(x, srcs, src_part, src_elem, n_local, n_ghost, nvb);
+  return cudaGetLastError();
+}
+template <class T>
+__global__ void zero_range_kernel(T* __restrict__ x, int64_t from, int64_t to) {
+  for (int64_t i = from + (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < to; i += (int64_t)gridDim.x * blockDim.x)
+    x[i] = T(0);
+}
+template <class T>
+cudaError_t launch_zero_range(T* x, int64_t from, int64_t to, cudaStream_t st) {
+  if (to <= from) return cudaSuccess;
+  zero_range_kernel<T><<<grid_for(to - from), 256, 0, st>>>(x, from, to);
+  return cudaGetLastError();
+}
 
 #define PCEXP_INST(T)                                                                                         \
   template cudaError_t launch_paper_to_internal<T>(const double*, T*, const double*, int64_t, int, int,        \
@@ -241,6 +279,9 @@ cudaError_t measure_fp64_fma_rate(double* tflops) {
   template cudaError_t launch_internal_to_paper<T>(const T*, double*, const double*, int64_t, int, int,        \
                                                    cudaStream_t);                                              \
   template cudaError_t launch_scale_elements<T>(T*, const T*, int64_t, int, cudaStream_t);                     \
+  template cudaError_t launch_gather_ghosts<T>(T*, PartPtrs, const int32_t*, const int32_t*, int64_t, int64_t,  \
+                                               int, cudaStream_t);                                              \
+  template cudaError_t launch_zero_range<T>(T*, int64_t, int64_t, cudaStream_t);                                \
   template cudaError_t launch_density_norm<T>(const T*, const T*, int64_t, int, int, double, StepState*,       \
                                               double*, int, int, double, cudaStream_t);
 PCEXP_INST(double)

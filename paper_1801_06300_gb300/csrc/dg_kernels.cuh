@@ -60,6 +60,19 @@ template <bool SMEM, class T> PCEXP_DEV T tab(const T* p) {
   else return __ldg(p);
 }
 
+// slip wall or symmetry plane: both take the slip-wall ghost state
+PCEXP_DEV bool mirror_bc(int eR) { return -eR == PCEXP_BC_SLIP_WALL || -eR == PCEXP_BC_SYMMETRY; }
+
+// Source term of a rotating frame on the orthonormal basis: S = -omega x m is linear in U, so
+// int_E phi_i S(U_h) dx = -(omega x m_i) coefficient-wise (m_i the momentum coefficients of
+// test function i).  Returns component k (0..D-1) given the D momentum coefficients m.
+template <class T, int D>
+PCEXP_DEV T rot_source(const T* om, const T (&m)[D], int k) {
+  const T mx = m[0], my = m[1], mz = D == 3 ? m[D - 1] : T(0);
+  const T c = k == 0 ? om[1] * mz - om[2] * my : (k == 1 ? om[2] * mx - om[0] * mz : om[0] * my - om[1] * mx);
+  return -c;
+}
+
 template <class O> PCEXP_DEV int slot_face(int fs) { return fs >> 4; }
 PCEXP_DEV int slot_side(int fs) { return (fs >> 3) & 1; }
 PCEXP_DEV int slot_perm(int fs) { return fs & 7; }
@@ -126,13 +139,13 @@ __global__ void __launch_bounds__(256) face_kernel(DGData<T> d, const T* __restr
       if constexpr (TAN) UR[v] = S{a * isd, b * isd};
       else UR[v] = a * isd;
     }
-  } else if (-eR == PCEXP_BC_SLIP_WALL) {
-    ghost_slip_wall<D, S, T>(UL, n, UR);
+  } else if (mirror_bc(eR)) {
+    ghost_slip_wall<D, S, T>(UL, n, UR, d.rot ? d.vrn[idx] : T(0));
   } else {
     ghost_farfield<D, S, T>(UL, n, d.fs, UR);
   }
   S Fn[NV];
-  roe_flux<D, S, T>(UL, UR, n, d.fs.gamma, Fn);
+  roe_flux<D, S, T>(UL, UR, n, d.fs.gamma, Fn, d.rot ? d.vrn[idx] : T(0));
   const T wl = meas * sWf[q];
   T* g = G + idx * NV;
 #pragma unroll
@@ -265,6 +278,13 @@ __global__ void __launch_bounds__(256) elem_kernel(DGData<T> d, const T* __restr
     }
     Sc F[D][NV];
     euler_flux<D, Sc, T>(U, g, F);
+    if (d.rot) {  // rotating frame: F - U v_r^T at the point
+      const T* vr = d.vrq + ((e0 + el) * NQ + q) * D;
+#pragma unroll
+      for (int k = 0; k < D; ++k)
+#pragma unroll
+        for (int v = 0; v < NV; ++v) F[k][v] = F[k][v] - U[v] * vr[k];
+    }
     T* fo = sF + (el * NQ + q) * DV;
 #pragma unroll
     for (int v = 0; v < NV; ++v) {
@@ -323,11 +343,22 @@ __global__ void __launch_bounds__(256) elem_kernel(DGData<T> d, const T* __restr
 #pragma unroll
       for (int i = 0; i < NB; ++i) acc[i] += __shfl_xor_sync(0xffffffffu, acc[i], off);
     if (act) {
-      T sc = sgeo[el * GEO + O::SD] * osc;
-      if (escale) sc *= escale[e];
+      const T es = escale ? escale[e] : T(1);
+      const T sc = sgeo[el * GEO + O::SD] * osc * es;
+      const bool src = d.rot && v >= 1 && v <= D;
 #pragma unroll
       for (int i = 0; i < NB; ++i)
-        if (i % S == ls) out[e * NVB + v * NB + i] = acc[i] * sc;
+        if (i % S == ls) {
+          T o = acc[i] * sc;
+          if (src) {  // the rotating frame's source, on the coefficients of u (R) or du (J v)
+            const T* xr = (TAN ? sdu : su) + el * NV * NBP + i;
+            T m[D];
+#pragma unroll
+            for (int k = 0; k < D; ++k) m[k] = xr[(1 + k) * NBP];
+            o += rot_source<T, D>(d.om, m, v - 1) * osc * es;
+          }
+          out[e * NVB + v * NB + i] = o;
+        }
     }
   }
 }
@@ -358,155 +389,6 @@ cudaError_t dg_op_p(const DGData<T>& d, const T* u, const T* du, T* out, T* G, c
 // the constant cache serves as broadcasts outside the load/store pipe.
 template <int D, int P> __constant__ float c_tan[(D + 1) * Ord<D, P>::NQ * Ord<D, P>::NB];
 
-// Block = D+1 warps over 32 elements, lane l on element e0 + l.  The warps split the volume
-// points (warp w takes q = w, w + D+1, ...) and the faces (warp w takes face w), so every
-// table index is warp-uniform; an element's u, u' rows and face fluxes are staged in shared
-// memory with strides that keep the per-lane reads free of bank conflicts.  Each warp keeps
-// all nv x nb sums of its element in registers; the D+1 partial sums meet in shared memory
-// and are added in warp order (deterministic), and the outputs leave as contiguous rows.
-// Same sums as elem_kernel<float, D, P, true>, in another order.  Four blocks per SM: the
-// launch bounds hold the registers at 128 and the shared-memory carveout is set to its
-// maximum (tan_tables_p).  Used on tetrahedra; on triangles (6 x 4 sums per element,
-// 24,576 elements at 192 x 64) the tile kernel measured faster.
-template <int D, int P>
-__global__ void __launch_bounds__(32 * (D + 1), 4) elem_tan_kernel(DGData<float> d, const float* __restrict__ u,
-                                                                const float* __restrict__ du,
-                                                                const float* __restrict__ G, float* __restrict__ out,
-                                                                const float* __restrict__ escale,
-                                                                const int* __restrict__ skip,
-                                                                const double* __restrict__ oscale) {
-  using O = Ord<D, P>;
-  constexpr int NB = O::NB, NQ = O::NQ, NFQ = O::NFQ, NV = O::NV, NF = O::NF, NPERM = O::NPERM, GEO = O::GEO;
-  constexpr int NVB = O::NVB, QW = NF, NT = 32 * QW;
-  constexpr int NBP = PADV<float, NB>;
-  constexpr int UR0 = 2 * NV * NBP;                     // u rows, then u' rows, of one element
-  constexpr int UROW = UR0 + (36 - UR0 % 32) % 32;      // = 4 (mod 32) words: 16-byte reads of 8 lanes hit 32 banks
-  constexpr int GREC = NF * NFQ * NV;                   // face fluxes seen by one element
-  constexpr int GROW = GREC | 1;                        // odd strides: scalar reads of 32 lanes hit 32 banks
-  constexpr int PST = NVB | 1;
-  constexpr int STAGE = 32 * (UROW + GROW), PART = QW * 32 * PST;
-  constexpr bool SM = O::SMEM_BF;
-  static_assert(UROW % 32 == 4 && UROW >= UR0, "row stride");
-  __shared__ __align__(16) float sm[STAGE > PART ? STAGE : PART];
-  __shared__ __align__(16) float sBf[SM ? NF * NPERM * NFQ * NBP : 1];
-  __shared__ int sef[32 * NF];
-  __shared__ float ssd[32];
-  float* su = sm;               // [32][UROW]
-  float* sg = sm + 32 * UROW;   // [32][GROW]
-  float* part = sm;             // [QW][32][PST], after the staged rows are consumed
-  if (skip && *skip) return;
-  const int tid = threadIdx.x, lane = tid & 31, w = tid >> 5;
-  const int64_t e0 = (int64_t)blockIdx.x * 32;
-  const int ne = (int)((d.E - e0) < 32 ? (d.E - e0) : 32);
-  for (int i = tid; i < ne * NF; i += NT) sef[i] = d.ef[e0 * NF + i];
-  for (int i = tid; i < ne * NVB; i += NT) {
-    const int el = i / NVB, r = i - el * NVB, v = r / NB, j = r - v * NB;
-    su[el * UROW + v * NBP + j] = u[e0 * NVB + i];
-    su[el * UROW + (NV + v) * NBP + j] = du[e0 * NVB + i];
-  }
-  if constexpr (SM)
-    for (int i = tid; i < NF * NPERM * NFQ * NBP; i += NT) sBf[i] = d.BfP[i];
-  __syncthreads();
-  for (int i = tid; i < ne * GREC; i += NT) {
-    const int el = i / GREC, r = i - el * GREC, kf = r / (NFQ * NV), k = r - kf * (NFQ * NV);
-    sg[el * GROW + r] = G[(int64_t)slot_face<O>(sef[el * NF + kf]) * NFQ * NV + k];
-  }
-  __syncthreads();
-  const int el = lane < ne ? lane : 0;  // lanes past the last element repeat element 0; discarded
-  const float* ge = d.geo + (e0 + el) * GEO;
-  float Ai[D * D];
-#pragma unroll
-  for (int k = 0; k < D * D; ++k) Ai[k] = ge[k];
-  const float isd = ge[O::ISD];
-  if (w == 0) ssd[lane] = ge[O::SD];
-  const float g = d.fs.gamma;
-  float acc[NV][NB];
-#pragma unroll
-  for (int v = 0; v < NV; ++v)
-#pragma unroll
-    for (int i = 0; i < NB; ++i) acc[v][i] = 0.f;
-  const float* ur = su + el * UROW;
-  // volume: trace and tangent at point q, flux tangent mapped to reference directions,
-  // tested against the reference gradients
-#pragma unroll 1
-  for (int q = w; q < NQ; q += QW) {
-    const float* bq = c_tan<D, P> + q * NB;
-    Tangent<float> U[NV];
-#pragma unroll
-    for (int v = 0; v < NV; ++v) {
-      float c[NBP];
-      load_row<float, NBP>(ur + v * NBP, c);
-      float a = 0.f;
-#pragma unroll
-      for (int j = 0; j < NB; ++j) a = fmaf(bq[j], c[j], a);
-      load_row<float, NBP>(ur + (NV + v) * NBP, c);
-      float t = 0.f;
-#pragma unroll
-      for (int j = 0; j < NB; ++j) t = fmaf(bq[j], c[j], t);
-      U[v] = Tangent<float>{a * isd, t * isd};
-      asm volatile("" ::: "memory");  // one variable's rows in flight at a time (registers)
-    }
-    Tangent<float> F[D][NV];
-    euler_flux<D, Tangent<float>, float>(U, g, F);
-    const float* dq = c_tan<D, P> + NQ * NB + q * NB;
-#pragma unroll
-    for (int dd = 0; dd < D; ++dd) {
-      float fh[NV];
-#pragma unroll
-      for (int v = 0; v < NV; ++v) {
-        float a = Ai[dd * D] * F[0][v].d;
-#pragma unroll
-        for (int k = 1; k < D; ++k) a += Ai[dd * D + k] * F[k][v].d;
-        fh[v] = a;
-      }
-#pragma unroll
-      for (int i = 0; i < NB; ++i) {
-        const float t = dq[dd * NQ * NB + i];
-#pragma unroll
-        for (int v = 0; v < NV; ++v) acc[v][i] = fmaf(t, fh[v], acc[v][i]);
-      }
-    }
-  }
-  // faces: lift of the staged face fluxes, pre-scaled by 1/|det A| to share the accumulators
-  const float rdet = isd * isd;
-  const float* Bf = SM ? sBf : d.BfP;
-#pragma unroll 1
-  for (int kf = w; kf < NF; kf += QW) {
-    const int fs = sef[el * NF + kf];
-    const float sgn = slot_side(fs) ? rdet : -rdet;
-    const float* tb = Bf + ((kf * NPERM + slot_perm(fs)) * NFQ) * NBP;
-    const float* gr = sg + el * GROW + kf * NFQ * NV;
-#pragma unroll
-    for (int q = 0; q < NFQ; ++q) {
-      float row[NBP];
-      load_row<float, NBP, !SM>(tb + q * NBP, row);
-#pragma unroll
-      for (int v = 0; v < NV; ++v) {
-        const float gq = sgn * gr[q * NV + v];
-#pragma unroll
-        for (int i = 0; i < NB; ++i) acc[v][i] = fmaf(row[i], gq, acc[v][i]);
-      }
-    }
-  }
-  __syncthreads();  // the staged rows are consumed; the partial sums reuse their space
-  float* pr = part + (w * 32 + lane) * PST;
-#pragma unroll
-  for (int v = 0; v < NV; ++v)
-#pragma unroll
-    for (int i = 0; i < NB; ++i) pr[v * NB + i] = acc[v][i];
-  __syncthreads();
-  const float osc = oscale ? (float)*oscale : 1.f;
-  for (int o = tid; o < ne * NVB; o += NT) {
-    const int el2 = o / NVB, r = o - el2 * NVB;
-    float s = part[el2 * PST + r];
-#pragma unroll
-    for (int ww = 1; ww < QW; ++ww) s += part[(ww * 32 + el2) * PST + r];
-    float sc = ssd[el2] * osc;
-    if (escale) sc *= escale[e0 + el2];
-    out[e0 * NVB + o] = s * sc;
-  }
-}
-
 // ---------------------------------- the same J v volume part as a pipelined persistent kernel
 // cp.async copies (global -> shared, no register staging), 4 or 16 bytes
 PCEXP_DEV void cp_async4(void* dst, const void* src) {
@@ -533,21 +415,25 @@ template <int D, int P> struct TanPipe {
   static constexpr int PST = O::NVB | 1;
   static constexpr int SU = 32 * UROW, SG = 32 * GROW, SGEO = 32 * O::GEO, SEF = 32 * O::NF;
   static constexpr int STAGE = SU + SG + SGEO + SEF;  // words (SGEO and SU keep 16-byte alignment)
-  static constexpr int PART = O::NF * 32 * PST;
+  // warps per block: with two 42 KB stages two blocks fit an SM (P2); six warps each keep the
+  // registers of 2 x 192 threads within the SM's file and split the 27 points 5/5/5/4/4/4
+  static constexpr int WARPS = D == 3 ? 6 : O::NF;
+  static constexpr int PART = WARPS * 32 * PST;
   static_assert(PART <= SU + SG, "partial sums reuse the consumed rows, not the geometry records");
   static_assert(SU % 4 == 0 && SG % 4 == 0, "16-byte alignment of the geometry records");
   static constexpr size_t BYTES = 2 * (size_t)STAGE * 4;
 };
 
-// Persistent form of elem_tan_kernel: a block of D+1 warps loops over tiles of 32 elements
-// (one per lane, same point and face split, same sums in the same order, so the results are
-// bit-identical).  While tile t is computed, tile t + gridDim.x is copied into the other
+// Persistent element kernel of the FP32 J v on tetrahedra: a block of six warps loops over
+// tiles of 32 elements (one element per lane; the warps split the volume points and the
+// faces, so every reference-table index is warp-uniform and the tables are read from constant
+// memory).  While tile t is computed, tile t + gridDim.x is copied into the other
 // shared-memory stage by cp.async: its u, u' rows and geometry records at the start of the
 // tile, its face fluxes (gathered through its face slots, which are loaded into a register at
-// the start and are needed only then) after the volume loop.  The staging latency that stalls
-// the one-shot kernel is hidden behind a tile of compute.
+// the start and are needed only then) after the volume loop.  The staging latency is hidden
+// behind a tile of compute.
 template <int D, int P>
-__global__ void __launch_bounds__(32 * (D + 1), 2) elem_tan_pipe_kernel(DGData<float> d, const float* __restrict__ u,
+__global__ void __launch_bounds__(32 * TanPipe<D, P>::WARPS, 2) elem_tan_pipe_kernel(DGData<float> d, const float* __restrict__ u,
                                                                      const float* __restrict__ du,
                                                                      const float* __restrict__ G, float* __restrict__ out,
                                                                      const float* __restrict__ escale,
@@ -556,7 +442,8 @@ __global__ void __launch_bounds__(32 * (D + 1), 2) elem_tan_pipe_kernel(DGData<f
   using O = Ord<D, P>;
   using L = TanPipe<D, P>;
   constexpr int NB = O::NB, NQ = O::NQ, NFQ = O::NFQ, NV = O::NV, NF = O::NF, NPERM = O::NPERM, GEO = O::GEO;
-  constexpr int NVB = O::NVB, QW = NF, NT = 32 * QW;
+  constexpr int NVB = O::NVB, QW = L::WARPS, NT = 32 * QW;
+  static_assert(NT >= 32 * NF, "one thread per (element, face) slot of a tile");
   constexpr int NBP = L::NBP, UROW = L::UROW, GROW = L::GROW, PST = L::PST;
   static_assert(!O::SMEM_BF, "tetrahedra read the trace tables through the read-only cache");
   extern __shared__ __align__(16) float dsm[];
@@ -678,10 +565,11 @@ __global__ void __launch_bounds__(32 * (D + 1), 2) elem_tan_pipe_kernel(DGData<f
     // the next tile's face fluxes, now that its face slots have arrived
     if (has_next) stage_faces(tn, N, fs_next);
     cp_async_commit();
-    // faces: lift of the staged face fluxes, pre-scaled by 1/|det A| to share the accumulators
+    // faces: lift of the staged face fluxes, pre-scaled by 1/|det A| to share the accumulators;
+    // face kf goes to warp QW - 1 - kf (the warps with fewer volume points)
     const float rdet = isd * isd;
 #pragma unroll 1
-    for (int kf = w; kf < NF; kf += QW) {
+    for (int kf = QW - 1 - w; kf >= 0 && kf < NF; kf += QW) {
       const int fs = sef[el * NF + kf];
       const float sgn = slot_side(fs) ? rdet : -rdet;
       const float* tb = d.BfP + ((kf * NPERM + slot_perm(fs)) * NFQ) * NBP;
@@ -723,10 +611,7 @@ __global__ void __launch_bounds__(32 * (D + 1), 2) elem_tan_pipe_kernel(DGData<f
 template <int D, int P>
 cudaError_t tan_tables_p(const DGData<float>& d, cudaStream_t st) {
   using O = Ord<D, P>;
-  // the kernels' occupancy is bound by registers and shared memory: ask for the largest carveout
-  cudaError_t e = cudaFuncSetAttribute(elem_tan_kernel<D, P>, cudaFuncAttributePreferredSharedMemoryCarveout,
-                                       (int)cudaSharedmemCarveoutMaxShared);
-  if (e != cudaSuccess) return e;
+  cudaError_t e = cudaSuccess;
   if constexpr (D == 3) {
     e = cudaFuncSetAttribute(elem_tan_pipe_kernel<D, P>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                              (int)TanPipe<D, P>::BYTES);
@@ -768,6 +653,13 @@ __global__ void __launch_bounds__(256) linearize_vol_kernel(DGData<T> d, const T
   }
   J F[D][NV];
   euler_flux<D, J, T>(U, d.fs.gamma, F);
+  if (d.rot) {
+    const T* vr = d.vrq + idx * D;
+#pragma unroll
+    for (int k = 0; k < D; ++k)
+#pragma unroll
+      for (int v = 0; v < NV; ++v) F[k][v] = F[k][v] - U[v] * vr[k];
+  }
 #pragma unroll
   for (int dd = 0; dd < D; ++dd)
 #pragma unroll
@@ -844,12 +736,12 @@ __global__ void __launch_bounds__(128) linearize_face_kernel(DGData<T> d, const 
 #pragma unroll
         for (int c = 0; c < NV; ++c) R[v].d[c] = (side == 1 && v == c) ? T(1) : T(0);
       }
-    } else if (-eR == PCEXP_BC_SLIP_WALL) {
-      ghost_slip_wall<D, J, T>(L, nr, R);
+    } else if (mirror_bc(eR)) {
+      ghost_slip_wall<D, J, T>(L, nr, R, d.rot ? d.vrn[idx] : T(0));
     } else {
       ghost_farfield<D, J, T>(L, nr, d.fs, R);
     }
-    roe_flux<D, J, T>(L, R, nr, d.fs.gamma, F);
+    roe_flux<D, J, T>(L, R, nr, d.fs.gamma, F, d.rot ? d.vrn[idx] : T(0));
     const T sc = wq * (side == 0 ? isdL : isdR);
 #pragma unroll
     for (int v = 0; v < NV; ++v)
@@ -993,7 +885,14 @@ __global__ void __launch_bounds__(256) elem_apply_kernel(DGData<T> d, const T* _
       for (int dd = 0; dd < D; ++dd) acc += sDv[(dd * NQ + q) * NB + i] * sF[(el * NQ + q) * DV + dd * NV + v];
     const int64_t e = e0 + el;
     const T lift = lift_faces<T, D, P, SM>(d, Bf, G, e, v, i);
-    acc = (acc + lift * ssd[el]) * osc;
+    acc = acc + lift * ssd[el];
+    if (d.rot && v >= 1 && v <= D) {  // the rotating frame's source on the coefficients of dv
+      T m[D];
+#pragma unroll
+      for (int k = 0; k < D; ++k) m[k] = sdu[el * NVB + (1 + k) * NB + i];
+      acc += rot_source<T, D>(d.om, m, v - 1);
+    }
+    acc *= osc;
     if (escale) acc *= escale[e];
     out[e0 * NVB + it] = acc;
   }
@@ -1032,7 +931,9 @@ cudaError_t jac_apply_p(const DGData<T>& d, LinData<T> lin, const T* u_elem, con
   const int64_t eb = (d.E + O::ET - 1) / O::ET;
   if (u_elem) {
     if constexpr (std::is_same<T, float>::value && D == 3) {
-      if (d.E > 0) {
+      if (d.rot) {  // the frame terms live in the tile kernel
+        elem_kernel<T, D, P, true><<<(unsigned)eb, 256, 0, st>>>(d, u_elem, dv, G, out, escale, skip, oscale);
+      } else if (d.E > 0) {
         // persistent: two blocks per SM (two 42 KB stages each), tiles of 32 elements
         static int nsm = 0;
         if (!nsm) {
@@ -1042,7 +943,7 @@ cudaError_t jac_apply_p(const DGData<T>& d, LinData<T> lin, const T* u_elem, con
         }
         const int64_t ntiles = (d.E + 31) / 32;
         const int64_t grid = ntiles < 2 * (int64_t)nsm ? ntiles : 2 * (int64_t)nsm;
-        elem_tan_pipe_kernel<D, P><<<(unsigned)grid, 32 * (D + 1), TanPipe<D, P>::BYTES, st>>>(
+        elem_tan_pipe_kernel<D, P><<<(unsigned)grid, 32 * TanPipe<D, P>::WARPS, TanPipe<D, P>::BYTES, st>>>(
             d, u_elem, dv, G, out, escale, skip, oscale, ntiles);
       }
     } else {
@@ -1195,6 +1096,12 @@ __global__ void __launch_bounds__(256) elem_adjoint_kernel(DGData<T> d, const T*
 #pragma unroll
     for (int q = 0; q < NQ; ++q) acc += sBv[q * NB + j] * sU[(el * NQ + q) * NV + c];
     acc += gather_faces_T<T, D, P, SM>(d, Bf, GT, e0 + el, c, j);
+    if (d.rot && c >= 1 && c <= D) {  // transpose of the source -omega x: +omega x w~ (antisymmetric)
+      T m[D];
+#pragma unroll
+      for (int k = 0; k < D; ++k) m[k] = sw[el * NVB + (1 + k) * NB + j];
+      acc -= rot_source<T, D>(d.om, m, c - 1);
+    }
     out[e0 * NVB + it] = acc;
   }
 }
@@ -1305,7 +1212,7 @@ __global__ void __launch_bounds__(128) face_hess_kernel(DGData<T> d, const T* __
           R[c].dt[k] = T(0);
         }
       }
-    } else if (-eR == PCEXP_BC_SLIP_WALL) {
+    } else if (mirror_bc(eR)) {
       ghost_slip_wall<D, H, T>(L, nr, R);
     } else {
       ghost_farfield<D, H, T>(L, nr, d.fs, R);
@@ -1812,7 +1719,7 @@ __global__ void __launch_bounds__(256) local_dt_kernel(DGData<T> d, const T* __r
   __shared__ bool last;
   const double cfl = cfl_dev ? *cfl_dev : cfl_host;
   double mn = DBL_MAX;
-  for (int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; e < d.E; e += (int64_t)gridDim.x * blockDim.x) {
+  for (int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; e < d.E_loc; e += (int64_t)gridDim.x * blockDim.x) {
     const T isd = d.geo[GEO * e + O::ISD];
     double U[NV];
     for (int v = 0; v < NV; ++v) {
@@ -1825,6 +1732,13 @@ __global__ void __launch_bounds__(256) local_dt_kernel(DGData<T> d, const T* __r
     for (int k = 0; k < D; ++k) v2 += (U[1 + k] / U[0]) * (U[1 + k] / U[0]);
     const double p = (gam - 1.0) * (U[NV - 1] - 0.5 * U[0] * v2);
     const double c = sqrt(gam * p / U[0]);
+    if (d.rot) {  // the velocity relative to the rotating frame carries the waves
+      v2 = 0;
+      for (int k = 0; k < D; ++k) {
+        const double vk = U[1 + k] / U[0] - (double)d.vrc[e * D + k];
+        v2 += vk * vk;
+      }
+    }
     const double h = (double)d.geo[GEO * e + O::HE];
     const double dt = cfl * h / ((2 * d.p + 1) * (sqrt(v2) + c));
     if (dte) dte[e] = (T)dt;

@@ -200,7 +200,7 @@ RuleTet collapsed_tetra(int n) {
   return t;
 }
 
-int build_setup(const pcexp_mesh& mesh, int p, Setup& s, std::string& msg) {
+int build_setup(const pcexp_mesh& mesh, int p, Setup& s, std::string& msg, const int64_t* elem_key) {
   const int D = mesh.dim;
   if (D != 2 && D != 3) {
     msg = "mesh dimension must be 2 (triangles) or 3 (tetrahedra)";
@@ -262,6 +262,9 @@ int build_setup(const pcexp_mesh& mesh, int p, Setup& s, std::string& msg) {
       wf[q] = tri.w[q];
     }
   }
+  s.flam.assign((size_t)nfq * D, 0.0);
+  for (int q = 0; q < nfq; ++q)
+    for (int k = 0; k < D; ++k) s.flam[(size_t)q * D + k] = (double)lam[q][k];
 
   // ---- reference orthonormal basis: MGS of monomials about the reference centroid
   const std::vector<Mono> ex = graded_exponents(D, p);
@@ -464,7 +467,7 @@ int build_setup(const pcexp_mesh& mesh, int p, Setup& s, std::string& msg) {
     int64_t vs[3] = {0, 0, 0};
     for (int k = 0; k < D; ++k) vs[k] = mesh.bface_vert[(size_t)D * i + k];
     int32_t t = mesh.bface_tag ? mesh.bface_tag[i] : 0;
-    if (t != PCEXP_BC_SLIP_WALL && t != PCEXP_BC_FARFIELD) {
+    if (t != PCEXP_BC_SLIP_WALL && t != PCEXP_BC_FARFIELD && t != PCEXP_BC_SYMMETRY) {
       msg = "unknown boundary tag";
       return PCEXP_ERR_MESH;
     }
@@ -495,9 +498,16 @@ int build_setup(const pcexp_mesh& mesh, int p, Setup& s, std::string& msg) {
   s.fgeo.clear();
   int64_t F = 0;
   // interior faces first, in order of their L element
+  // elements in increasing key order (their index without keys): the element of a face met
+  // first is its L element, whose face points the face uses
+  std::vector<int64_t> order((size_t)E);
+  for (int64_t e = 0; e < E; ++e) order[(size_t)e] = e;
+  if (elem_key)
+    std::stable_sort(order.begin(), order.end(), [&](int64_t a, int64_t b) { return elem_key[a] < elem_key[b]; });
   for (int pass = 0; pass < 2; ++pass)
-    for (int64_t e = 0; e < E; ++e)
+    for (int64_t oe = 0; oe < E; ++oe)
       for (int f = 0; f < NF; ++f) {
+        const int64_t e = order[(size_t)oe];
         const int64_t id = e * NF + f;
         if (s.ef[id] >= 0) continue;
         const int64_t pr = partner[id];

@@ -45,6 +45,7 @@ struct Setup {
   std::vector<double> Bf;  // [NF][NPERM][nfq][nb]  phi^_j at face points of local face f, vertices permuted
   std::vector<double> Wf;  // [nfq]                 face weights (sum 1 on edges, 1/2 on triangles)
   std::vector<double> Bc;  // [nb]                  phi^_j at the reference centroid
+  std::vector<double> flam;  // [nfq][D]            face-rule barycentrics over a face's local vertices
   // per element
   std::vector<double> geo;     // [E][8 or 12]: A^-1 (D x D), sqrt(det A), h, 1 / sqrt(det A)
   std::vector<double> xqphys;  // [E][nq][D] physical volume points (projections, functionals)
@@ -56,7 +57,10 @@ struct Setup {
   std::vector<double> fgeo;   // [F][4] unit normal (D), measure factor
 };
 
-// Returns PCEXP_OK or an error code; msg receives a description on error.
-int build_setup(const pcexp_mesh& mesh, int p, Setup& s, std::string& msg);
+// Returns PCEXP_OK or an error code; msg receives a description on error.  elem_key
+// (nullable, one per element) orders the elements for the choice of a face's L element (the
+// lower key): a partition's submesh passes the global element indices, so that every face
+// keeps the L element, and hence the quadrature points, it has in the whole mesh.
+int build_setup(const pcexp_mesh& mesh, int p, Setup& s, std::string& msg, const int64_t* elem_key = nullptr);
 
 }  // namespace pcexp

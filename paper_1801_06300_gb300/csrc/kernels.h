@@ -25,10 +25,13 @@ struct KState {
   double beta;
   double wnorm0;
   double err_est;          // relative a-posteriori error estimate of the last phi evaluation
+  double gsum[MMAX + 2];   // partitioned runs: this partition's sums of the last Gram-Schmidt pass
+  double gtot[MMAX + 2];   // partitioned runs: the sums over all partitions
   int k;
   int done;
   int err;
   unsigned counter;
+  int group;               // partitioned run: the passes leave their sums in gsum, unfinalised
 };
 
 // Device-resident scalars of the reverse Krylov stage.
@@ -72,7 +75,15 @@ struct DGData {
   const T* Bc;           // [nb]
   const T* Wv;           // [nq] reference volume weights
   const T* BfP;          // [NF][NPERM][nfq][nbp]: Bf with rows padded to whole 16-byte vectors
+  // rotating frame (rot != 0): v_r = omega x x at the volume points [E][nq][D], v_r . n at the
+  // face points [F][nfq] (the L element's), v_r at the element centroids [E][D]; null otherwise
+  const T* vrq;
+  const T* vrn;
+  const T* vrc;
+  T om[3];
+  int rot;
   int64_t E, F;
+  int64_t E_loc;         // elements owned by this partition (E without partitions; ghosts follow)
   Free<T> fs;
   int p;
   int dim;
@@ -232,6 +243,7 @@ cudaError_t launch_scale_elements(T* x, const T* s, int64_t E, int nvb, cudaStre
 cudaError_t launch_scale_by_inverse(double* x, const double* s, int64_t n, cudaStream_t st);
 // FP64 FMA rate of the current device (TFLOP/s) from DFMA chains on every SM
 cudaError_t measure_fp64_fma_rate(double* tflops);
+cudaError_t measure_fp32_fma_rate(double* tflops);
 // sum_e sum_q w^_q |det A_e| (s/s0)^2 of the FP64 state u (Eq. entropy_error) -> *value
 cudaError_t launch_entropy_sum(const double* u, const double* Bv, const double* Wv, const double* sd, int64_t E, int nb,
                                int nq, int nv, double gamma, double s0, double* value, double* partials,
@@ -273,6 +285,26 @@ template <class T>
 cudaError_t launch_lincomb3(T* out, const T* x, const T* y, const T* z, int64_t Kp, cudaStream_t st);
 // ss->dt_prev = ss->dt
 cudaError_t launch_keep_dt(StepState* ss, cudaStream_t st);
+// ---- partitioned runs (several contexts, one per partition)
+constexpr int MAX_PARTS = 16;
+struct PartPtrs {
+  const void* p[MAX_PARTS];
+};
+// Gram-Schmidt pass of a partition: apply the pass's scalar step (breakdown test, H entries,
+// scales) to the partition-summed ks->gtot (mode, column j as for launch_cgs)
+cudaError_t launch_cgs_group_finalize(int mode, int j, KState* ks, double eta, cudaStream_t st);
+// out[i] = sum over q < nparts of slots.p[q][i] (doubles, i < n), in partition order; op 1: min
+cudaError_t launch_group_reduce(PartPtrs slots, int nparts, int n, double* out, int op, cudaStream_t st);
+// *dst = *src (one double)
+cudaError_t launch_copy_double(double* dst, const double* src, cudaStream_t st);
+// ghost rows of a partition's vector x (element rows n_local .. n_local + n_ghost): row g from
+// element src_elem[g] of partition src_part[g]'s copy srcs.p[src_part[g]] (nvb entries per row)
+template <class T>
+cudaError_t launch_gather_ghosts(T* x, PartPtrs srcs, const int32_t* src_part, const int32_t* src_elem,
+                                 int64_t n_local, int64_t n_ghost, int nvb, cudaStream_t st);
+// x[from, to) = 0
+template <class T>
+cudaError_t launch_zero_range(T* x, int64_t from, int64_t to, cudaStream_t st);
 // ss->cfl = min(ss->cfl, cap) (the Krylov-error cap of the steady march)
 cudaError_t launch_cap_cfl(StepState* ss, double cap, cudaStream_t st);
 cudaError_t launch_reset_kstate(KState* ks, cudaStream_t st);

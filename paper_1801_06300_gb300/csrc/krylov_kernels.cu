@@ -343,6 +343,11 @@ __global__ void __launch_bounds__(256, 2) cgs_kernel(const T* __restrict__ Z, in
     if (lane == 0) dots[c] = a.value();
   }
   __syncthreads();
+  if (ks->group) {  // partitioned: the sums over all partitions are finalised afterwards
+    for (int c = threadIdx.x; c < nred; c += blockDim.x) ks->gsum[c] = dots[c];
+    if (threadIdx.x == 0) ks->counter = 0;
+    return;
+  }
   cgs_finalize(MODE, j, dots, ks, eta);
   if (threadIdx.x == 0) ks->counter = 0;
 }
@@ -380,6 +385,11 @@ PCEXP_DEV void cgs_grid_tail(const Acc<T>* red, int nred, int mode, int j, KStat
     if (lane == 0) dots[c] = a.value();
   }
   __syncthreads();
+  if (ks->group) {
+    for (int c = threadIdx.x; c < nred; c += blockDim.x) ks->gsum[c] = dots[c];
+    if (threadIdx.x == 0) ks->counter = 0;
+    return;
+  }
   cgs_finalize(mode, j, dots, ks, eta);
   if (threadIdx.x == 0) ks->counter = 0;
 }
@@ -573,6 +583,39 @@ cudaError_t launch_cgs(int mode, const T* Z, int64_t ldz, int64_t Kp, int j, T* 
     case CGS_UPD_NORM: cgs_dispatch<T, CGS_UPD_NORM>(nc, Z, ldz, Kp, j, w, out, ks, partials, eta, st); break;
     default: return cudaErrorInvalidValue;
   }
+  return cudaGetLastError();
+}
+
+// ------------------------------------------------ Gram-Schmidt of a partitioned run
+__global__ void __launch_bounds__(256) cgs_group_finalize_kernel(int mode, int j, KState* ks, double eta) {
+  __shared__ double dots[MMAX + 2];
+  if (ks->done) return;  // the pass did not run (uniform)
+  for (int c = threadIdx.x; c < MMAX + 2; c += blockDim.x) dots[c] = ks->gtot[c];
+  __syncthreads();
+  cgs_finalize(mode, j, dots, ks, eta);
+}
+cudaError_t launch_cgs_group_finalize(int mode, int j, KState* ks, double eta, cudaStream_t st) {
+  cgs_group_finalize_kernel<<<1, 256, 0, st>>>(mode, j, ks, eta);
+  return cudaGetLastError();
+}
+
+__global__ void group_reduce_kernel(PartPtrs slots, int nparts, int n, double* out, int op) {
+  for (int i = threadIdx.x; i < n; i += blockDim.x) {
+    double a = reinterpret_cast<const double*>(slots.p[0])[i];
+    for (int q = 1; q < nparts; ++q) {
+      const double b = reinterpret_cast<const double*>(slots.p[q])[i];
+      a = op == 1 ? fmin(a, b) : a + b;
+    }
+    out[i] = a;
+  }
+}
+cudaError_t launch_group_reduce(PartPtrs slots, int nparts, int n, double* out, int op, cudaStream_t st) {
+  group_reduce_kernel<<<1, 64, 0, st>>>(slots, nparts, n, out, op);
+  return cudaGetLastError();
+}
+__global__ void copy_double_kernel(double* dst, const double* src) { *dst = *src; }
+cudaError_t launch_copy_double(double* dst, const double* src, cudaStream_t st) {
+  copy_double_kernel<<<1, 1, 0, st>>>(dst, src);
   return cudaGetLastError();
 }
 

@@ -323,9 +323,12 @@ PCEXP_DEV S dot_n(const S (&a)[D], const T (&n)[D]) {
   return r;
 }
 
-// Roe flux F~(U_L, U_R) . n
+// Roe flux F~(U_L, U_R) . n.  vrn = v_r . n, the normal velocity of a rotating frame at the
+// face point (Sec. 4.1): F . n = F_abs . n - vrn U and the waves' speeds are shifted by -vrn
+// (vrn = 0: the fixed frame, the same operations as without it).
 template <int D, class S, class T>
-PCEXP_DEV void roe_flux(const S (&L)[D + 2], const S (&R)[D + 2], const T (&n)[D], T g, S (&F)[D + 2]) {
+PCEXP_DEV void roe_flux(const S (&L)[D + 2], const S (&R)[D + 2], const T (&n)[D], T g, S (&F)[D + 2],
+                        T vrn = T(0)) {
   constexpr int NV = D + 2;
   const T gm = g - T(1);
   S rL = L[0], irL = T(1) / rL, rR = R[0], irR = T(1) / rR;
@@ -370,7 +373,8 @@ PCEXP_DEV void roe_flux(const S (&L)[D + 2], const S (&R)[D + 2], const T (&n)[D
 #pragma unroll
   for (int d = 0; d < D; ++d) dv[d] = vR[d] - vL[d];
   S dq = dot_n<D>(dv, n);
-  S l1 = abs_s(qh - cs), l2 = abs_s(qh), l4 = abs_s(qh + cs);
+  const S qs = vrn != T(0) ? qh - vrn : qh;  // wave speeds relative to the frame
+  S l1 = abs_s(qs - cs), l2 = abs_s(qs), l4 = abs_s(qs + cs);
   S i2c = T(0.5) / cc;
   S a1 = (dp - rh * cs * dq) * i2c;
   S a4 = (dp + rh * cs * dq) * i2c;
@@ -385,22 +389,32 @@ PCEXP_DEV void roe_flux(const S (&L)[D + 2], const S (&R)[D + 2], const T (&n)[D
   for (int d = 0; d < D; ++d)
     dd[1 + d] = t1 * (vh[d] - cs * n[d]) + t2 * vh[d] + ts * (dv[d] - dq * n[d]) + t4 * (vh[d] + cs * n[d]);
   dd[NV - 1] = t1 * (Hh - cs * qh) + t2 * (T(0.5) * q2) + ts * (vdv - qh * dq) + t4 * (Hh + cs * qh);
+  if (vrn != T(0)) {
+#pragma unroll
+    for (int v = 0; v < NV; ++v) c[v] = c[v] - vrn * (L[v] + R[v]);
+  }
 #pragma unroll
   for (int v = 0; v < NV; ++v) F[v] = T(0.5) * (c[v] - dd[v]);
 }
 
+// Slip wall and symmetry plane: the velocity relative to the wall (which moves with a
+// rotating frame: vrn = v_r . n) has its normal component mirrored; density and pressure are
+// kept.  v_g = v - 2 q n with q = v . n - vrn, so |v_g|^2 = |v|^2 - 4 q vrn and the ghost's
+// total energy is rho E - 2 rho q vrn (unchanged in a fixed frame).
 template <int D, class S, class T>
-PCEXP_DEV void ghost_slip_wall(const S (&U)[D + 2], const T (&n)[D], S (&G)[D + 2]) {
+PCEXP_DEV void ghost_slip_wall(const S (&U)[D + 2], const T (&n)[D], S (&G)[D + 2], T vrn = T(0)) {
   constexpr int NV = D + 2;
   const S ir = T(1) / U[0];
   S m[D];
 #pragma unroll
   for (int d = 0; d < D; ++d) m[d] = U[1 + d];
-  const S qn = dot_n<D>(m, n) * ir;  // normal velocity
+  S qn = dot_n<D>(m, n) * ir;  // normal velocity
+  if (vrn != T(0)) qn = qn - vrn;
   G[0] = U[0];
 #pragma unroll
   for (int d = 0; d < D; ++d) G[1 + d] = U[1 + d] - T(2) * U[0] * qn * n[d];
   G[NV - 1] = U[NV - 1];
+  if (vrn != T(0)) G[NV - 1] = G[NV - 1] - T(2) * vrn * (U[0] * qn);
 }
 
 template <int D, class S, class T>

@@ -1,0 +1,137 @@
+"""Partitioned runs on the GPU (pcexp_group_*): 2 and 3 partitions of one mesh, all on device 0,
+against one context on the whole mesh.
+
+* R(u) and J(u) v: each partition receives only its own rows; the halo rows come from the
+  exchange kernel reading the owners' buffers.  A face keeps the whole mesh's L element and
+  an element sums its faces in the same order, so the own rows equal the single context's
+  bit for bit.
+* Arnoldi: the Gram-Schmidt sums are split over the partitions (partition order), so H matches
+  to round-off (1e-13 relative) and every partition holds the same H (checked by the call).
+* Steps (PCEXP at the global CFL dt, ETD2, EXP1): the same Krylov dimensions, dt to the last
+  bit or two, and states within 1e-11 (FP64) after three steps; FP32-mixed within 1e-6 of the single FP32 context
+  (the FP32 basis vectors round differently once the projections differ in their last bits).
+"""
+import numpy as np
+import pytest
+
+import workloads as W
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def capi():
+    from paper_1801_06300_gb300 import build
+    build()
+    from paper_1801_06300_gb300 import capi as c
+    c.load()
+    return c
+
+
+CASES = {
+    "vortex2d": lambda: (W.periodic_square(16, 10.0, 0.15, 3), 1, W.Freestream(0.5, 45.0)),
+    "bump2d": lambda: (W.bump_channel(24, 8, 0.1, 2), 2, W.Freestream(0.5, 0.0)),
+    "cube3d": lambda: (W.periodic_cube_kuhn(4, 2.0, 0.1, 4), 2, W.Freestream(0.5, 30.0)),
+}
+
+
+def _state(ctx, seed):
+    u = ctx.get_state().reshape(ctx.E, ctx.nv, ctx.nb)
+    u = u + 0.03 * W.random_coeffs(seed, u.shape) * np.abs(u[:, :, :1])
+    return u.reshape(-1)
+
+
+def rel(a, b):
+    return float(np.linalg.norm(a - b) / np.linalg.norm(b))
+
+
+@pytest.mark.parametrize("name,n", [("vortex2d", 2), ("bump2d", 3), ("cube3d", 2), ("cube3d", 3)])
+def test_group_operator_and_arnoldi(capi, name, n):
+    mesh, p, free = CASES[name]()
+    part = capi.partition(mesh, n)
+    one = capi.Context(mesh, p, free, capi.PCEXP_FP64, m_max=12)
+    grp = capi.Group(mesh, part, p, free, capi.PCEXP_FP64, m_max=12)
+    for k in range(n):
+        own, halo = grp.sizes(k)
+        assert own == int((part == k).sum()) and halo > 0
+    u = _state(one, 1)
+    v = W.random_coeffs(2, u.size)
+    R1, Rg = one.residual(u), grp.residual(u)
+    assert np.abs(Rg - R1).max() <= 1e-15 * np.abs(R1).max()
+    J1, Jg = one.jvp(u, v), grp.jvp(u, v)
+    assert np.abs(Jg - J1).max() <= 1e-15 * np.abs(J1).max()
+    m = 10
+    H1 = one.arnoldi(u, v, m, want_V=False)
+    Hg, kg, bg = grp.arnoldi(u, v, m)
+    assert kg == H1[2] == m
+    assert abs(bg - H1[3]) <= 1e-14 * H1[3]
+    assert np.abs(Hg - H1[1]).max() <= 1e-13 * np.abs(H1[1]).max()
+    one.close()
+    grp.close()
+
+
+@pytest.mark.parametrize("name,n,scheme", [("vortex2d", 2, "PCEXP"), ("bump2d", 3, "PCEXP"), ("cube3d", 3, "PCEXP"),
+                                           ("vortex2d", 3, "ETD2"), ("bump2d", 2, "EXP1")])
+def test_group_steps_match_one_context(capi, name, n, scheme):
+    mesh, p, free = CASES[name]()
+    sc = getattr(capi, f"PCEXP_SCHEME_{scheme}")
+    part = capi.partition(mesh, n)
+    one = capi.Context(mesh, p, free, capi.PCEXP_FP64, m_max=12)
+    grp = capi.Group(mesh, part, p, free, capi.PCEXP_FP64, m_max=12)
+    u = _state(one, 3)
+    one.set_state(u)
+    grp.set_state(u)
+    assert np.array_equal(grp.get_state(), one.get_state())
+    for _ in range(3):
+        a = one.step(sc, capi.PCEXP_DT_GLOBAL_CFL, 2.0, 12)
+        b = grp.step(sc, capi.PCEXP_DT_GLOBAL_CFL, 2.0, 12)
+        # dt: equal at the first step; later steps start from states that differ by the
+        # rounding of the split Gram-Schmidt sums, so dt may differ in its last bits
+        assert a["k"] == b["k"] and abs(a["dt"] - b["dt"]) <= 4e-16 * a["dt"]
+        assert abs(a["res_norm"] - b["res_norm"]) <= 1e-12 * a["res_norm"]
+        assert abs(a["beta"][0] - b["beta"][0]) <= 1e-13 * a["beta"][0]
+    s1, sg = one.get_state(), grp.get_state()
+    assert rel(s1, u) > 1e-5  # the steps move the state
+    assert rel(sg, s1) <= 1e-11
+    one.close()
+    grp.close()
+
+
+def test_group_fp32_mixed_step(capi):
+    mesh, p, free = CASES["cube3d"]()
+    part = capi.partition(mesh, 2)
+    one = capi.Context(mesh, p, free, capi.PCEXP_FP32_MIXED, m_max=12)
+    grp = capi.Group(mesh, part, p, free, capi.PCEXP_FP32_MIXED, m_max=12)
+    u = _state(one, 4)
+    one.set_state(u)
+    grp.set_state(u)
+    for _ in range(2):
+        a = one.step(capi.PCEXP_SCHEME_PCEXP, capi.PCEXP_DT_GLOBAL_CFL, 2.0, 12)
+        b = grp.step(capi.PCEXP_SCHEME_PCEXP, capi.PCEXP_DT_GLOBAL_CFL, 2.0, 12)
+        assert a["k"] == b["k"] and abs(a["dt"] - b["dt"]) <= 1e-7 * a["dt"]
+    s1, sg = one.get_state(), grp.get_state()
+    assert rel(s1, u) > 1e-5
+    assert rel(sg, s1) <= 1e-6
+    one.close()
+    grp.close()
+
+
+def test_group_projection_and_unsupported_modes(capi):
+    mesh = W.periodic_square(12, 10.0, 0.1, 5)
+    free = W.Freestream(0.5, 45.0)
+    part = capi.partition(mesh, 2)
+    one = capi.Context(mesh, 2, free, capi.PCEXP_FP64, m_max=8)
+    grp = capi.Group(mesh, part, 2, free, capi.PCEXP_FP64, m_max=8)
+    prm = [5.0, 5.0, 5.0, 0.0]
+    one.project_state(capi.PCEXP_PROJ_VORTEX, prm)
+    grp.project_state(capi.PCEXP_PROJ_VORTEX, prm)
+    assert np.array_equal(grp.get_state(), one.get_state())
+    with pytest.raises(capi.PcexpError) as e:
+        grp.step(capi.PCEXP_SCHEME_PCEXP, capi.PCEXP_DT_LOCAL_CFL, 10.0, 8)
+    assert e.value.code == capi.PCEXP_ERR_UNSUPPORTED
+    # a failed call leaves the group usable
+    grp.step(capi.PCEXP_SCHEME_PCEXP, capi.PCEXP_DT_GIVEN, 0.01, 8)
+    one.step(capi.PCEXP_SCHEME_PCEXP, capi.PCEXP_DT_GIVEN, 0.01, 8)
+    assert rel(grp.get_state(), one.get_state()) <= 1e-12
+    one.close()
+    grp.close()
