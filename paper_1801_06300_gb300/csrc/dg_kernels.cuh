@@ -180,6 +180,23 @@ PCEXP_DEV void load_row(const T* p, T (&r)[N]) {
   }
 }
 
+// c[0..N) = p[0..N), coefficients of one variable of an element (read-only in the kernel):
+// 8-byte loads of FP32 pairs when N is even (rows then start on 8-byte boundaries)
+template <class T, int N>
+PCEXP_DEV void load_coeffs(const T* __restrict__ p, T (&c)[N]) {
+  if constexpr (sizeof(T) == 4 && N % 2 == 0) {
+#pragma unroll
+    for (int k = 0; k < N / 2; ++k) {
+      const float2 a = __ldg(reinterpret_cast<const float2*>(p) + k);
+      c[2 * k] = a.x;
+      c[2 * k + 1] = a.y;
+    }
+  } else {
+#pragma unroll
+    for (int k = 0; k < N; ++k) c[k] = __ldg(p + k);
+  }
+}
+
 // lift of the D+1 face fluxes onto test function i of variable v of element e
 template <class T, int D, int P, bool SM>
 PCEXP_DEV T lift_faces(const DGData<T>& d, const T* Bf, const T* __restrict__ G, int64_t e, int v, int i) {
@@ -523,24 +540,8 @@ __global__ void __launch_bounds__(32 * TanPipe<D, P>::WARPS, 2) elem_tan_pipe_ke
 #pragma unroll
       for (int i = 0; i < NB; ++i) acc[v][i] = 0.f;
     const float* ur = su + el * UROW;
-#pragma unroll 1
-    for (int q = w; q < NQ; q += QW) {
-      const float* bq = c_tan<D, P> + q * NB;
-      Tangent<float> U[NV];
-#pragma unroll
-      for (int v = 0; v < NV; ++v) {
-        float c[NBP];
-        load_row<float, NBP>(ur + v * NBP, c);
-        float a = 0.f;
-#pragma unroll
-        for (int j = 0; j < NB; ++j) a = fmaf(bq[j], c[j], a);
-        load_row<float, NBP>(ur + (NV + v) * NBP, c);
-        float tt = 0.f;
-#pragma unroll
-        for (int j = 0; j < NB; ++j) tt = fmaf(bq[j], c[j], tt);
-        U[v] = Tangent<float>{a * isd, tt * isd};
-        asm volatile("" ::: "memory");  // one variable's rows in flight at a time (registers)
-      }
+    // flux tangent at volume point q mapped to reference directions, tested (accumulated)
+    auto point = [&](int q, const Tangent<float>(&U)[NV]) {
       Tangent<float> F[D][NV];
       euler_flux<D, Tangent<float>, float>(U, g, F);
       const float* dq = c_tan<D, P> + NQ * NB + q * NB;
@@ -561,6 +562,39 @@ __global__ void __launch_bounds__(32 * TanPipe<D, P>::WARPS, 2) elem_tan_pipe_ke
           for (int v = 0; v < NV; ++v) acc[v][i] = fmaf(tq, fh[v], acc[v][i]);
         }
       }
+    };
+    // two of the warp's points per pass: each u, u' row read from shared memory serves both
+    // traces (the rows are the kernel's main shared-memory traffic)
+#pragma unroll 1
+    for (int q0 = w; q0 < NQ; q0 += 2 * QW) {
+      const int q1 = q0 + QW;
+      const bool two = q1 < NQ;  // warp-uniform
+      const float* b0 = c_tan<D, P> + q0 * NB;
+      const float* b1 = c_tan<D, P> + (two ? q1 : q0) * NB;
+      Tangent<float> U0[NV], U1[NV];
+#pragma unroll
+      for (int v = 0; v < NV; ++v) {
+        float c[NBP];
+        load_row<float, NBP>(ur + v * NBP, c);
+        float a0 = 0.f, a1 = 0.f;
+#pragma unroll
+        for (int j = 0; j < NB; ++j) {
+          a0 = fmaf(b0[j], c[j], a0);
+          a1 = fmaf(b1[j], c[j], a1);
+        }
+        load_row<float, NBP>(ur + (NV + v) * NBP, c);
+        float t0 = 0.f, t1 = 0.f;
+#pragma unroll
+        for (int j = 0; j < NB; ++j) {
+          t0 = fmaf(b0[j], c[j], t0);
+          t1 = fmaf(b1[j], c[j], t1);
+        }
+        U0[v] = Tangent<float>{a0 * isd, t0 * isd};
+        U1[v] = Tangent<float>{a1 * isd, t1 * isd};
+        asm volatile("" ::: "memory");  // one variable's rows in flight at a time (registers)
+      }
+      point(q0, U0);
+      if (two) point(q1, U1);
     }
     // the next tile's face fluxes, now that its face slots have arrived
     if (has_next) stage_faces(tn, N, fs_next);
@@ -774,27 +808,33 @@ __global__ void __launch_bounds__(256) face_apply_kernel(DGData<T> d, const T* _
   T B[O::NJF];
 #pragma unroll
   for (int k = 0; k < O::NJF; ++k) B[k] = (k < NN || eR >= 0) ? Bface[(int64_t)k * n + idx] : T(0);
+  // traces of dv at the point from each side: the table row (shared memory in 2D; in 3D the
+  // padded copy, 16-byte loads) and the element's rows of dv (8-byte loads when nb is even:
+  // the kernel is bound by its load instructions as much as by its bytes)
+  constexpr int NBP = PADV<T, NB>;
+  auto trace = [&](int64_t e, int fl, int pm, T(&t)[NV]) {
+    T b[NBP];
+    if constexpr (SM) {
+      const T* be = Bf + ((fl * NPERM + pm) * NFQ + q) * NB;
+#pragma unroll
+      for (int j = 0; j < NB; ++j) b[j] = be[j];
+    } else {
+      load_row<T, NBP, true>(d.BfP + ((fl * NPERM + pm) * NFQ + q) * NBP, b);
+    }
+    const T* ve = dv + e * NV * NB;
+#pragma unroll
+    for (int v = 0; v < NV; ++v) {
+      T c[NB];
+      load_coeffs<T, NB>(ve + v * NB, c);
+      T a = 0;
+#pragma unroll
+      for (int j = 0; j < NB; ++j) a += b[j] * c[j];
+      t[v] = a;
+    }
+  };
   T tL[NV], tR[NV];
-  {
-    const T* be = Bf + ((fL * NPERM) * NFQ + q) * NB;
-#pragma unroll
-    for (int v = 0; v < NV; ++v) {
-      T a = 0;
-#pragma unroll
-      for (int j = 0; j < NB; ++j) a += tab<SM>(be + j) * dv[(int64_t)eL * NV * NB + v * NB + j];
-      tL[v] = a;
-    }
-  }
-  if (eR >= 0) {
-    const T* be = Bf + ((fR * NPERM + pR) * NFQ + q) * NB;
-#pragma unroll
-    for (int v = 0; v < NV; ++v) {
-      T a = 0;
-#pragma unroll
-      for (int j = 0; j < NB; ++j) a += tab<SM>(be + j) * dv[(int64_t)eR * NV * NB + v * NB + j];
-      tR[v] = a;
-    }
-  }
+  trace(eL, fL, 0, tL);
+  if (eR >= 0) trace(eR, fR, pR, tR);
   T* g = G + idx * NV;
 #pragma unroll
   for (int v = 0; v < NV; ++v) {
