@@ -600,16 +600,27 @@ __global__ void __launch_bounds__(32 * TanPipe<D, P>::WARPS, 2) elem_tan_pipe_ke
     if (has_next) stage_faces(tn, N, fs_next);
     cp_async_commit();
     // faces: lift of the staged face fluxes, pre-scaled by 1/|det A| to share the accumulators;
-    // face kf goes to warp QW - 1 - kf (the warps with fewer volume points)
+    // faces 0..NF-2 go whole to the last warps (warp QW - 1 - kf, which have fewer volume
+    // points); the points of face NF-1 are split between warps 0 and 1, so that no warp waits
+    // at the tile's barriers for one that has a whole face more
+    static_assert(QW - (NF - 1) >= 2, "two warps share the last face");
     const float rdet = isd * isd;
-#pragma unroll 1
-    for (int kf = QW - 1 - w; kf >= 0 && kf < NF; kf += QW) {
+    int kf = -1, qa = 0, qb = NFQ;
+    if (w >= QW - (NF - 1)) {
+      kf = QW - 1 - w;
+    } else if (w < 2) {
+      kf = NF - 1;
+      qa = w == 0 ? 0 : (NFQ + 1) / 2;
+      qb = w == 0 ? (NFQ + 1) / 2 : NFQ;
+    }
+    if (kf >= 0) {  // warp-uniform
       const int fs = sef[el * NF + kf];
       const float sgn = slot_side(fs) ? rdet : -rdet;
       const float* tb = d.BfP + ((kf * NPERM + slot_perm(fs)) * NFQ) * NBP;
       const float* gr = sg + el * GROW + kf * NFQ * NV;
 #pragma unroll
       for (int q = 0; q < NFQ; ++q) {
+        if (q < qa || q >= qb) continue;  // warp-uniform
         float row[NBP];
         load_row<float, NBP, true>(tb + q * NBP, row);
 #pragma unroll
