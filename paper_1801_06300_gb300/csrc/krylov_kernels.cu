@@ -409,8 +409,7 @@ __global__ void __launch_bounds__(256) cgs_cs_kernel(const T* __restrict__ Z, in
                                                      double* __restrict__ partials, double eta) {
   constexpr int VN = VecN<T>::N, TR = 32 * VN;
   __shared__ T scoef[CGS_WARPS * NCW];
-  // UPD_PROJ: two buffers, alternating by tile, so a tile needs one block barrier
-  __shared__ T part[(MODE == CGS_PROJ) ? 1 : (MODE == CGS_UPD_PROJ ? 2 : 1) * CGS_WARPS * TR];
+  __shared__ T part[(MODE == CGS_PROJ) ? 1 : CGS_WARPS * TR];
   __shared__ T xs[(MODE == CGS_UPD_PROJ) ? TR : 1];
   __shared__ Acc<T> red[CGS_WARPS * NCW + 1];
   if (ks->done) return;  // breakdown reached earlier: uniform early exit
@@ -422,8 +421,7 @@ __global__ void __launch_bounds__(256) cgs_cs_kernel(const T* __restrict__ Z, in
 #pragma unroll
   for (int k = 0; k <= NCW; ++k) acc[k].zero();
   const int64_t ntile = (Kp + TR - 1) / TR;
-  int it = 0;
-  for (int64_t t = blockIdx.x; t < ntile; t += gridDim.x, ++it) {
+  for (int64_t t = blockIdx.x; t < ntile; t += gridDim.x) {
     const int64_t r = t * TR + lane * VN;
     const bool valid = r < Kp;
     T z[NCW][VN];
@@ -435,11 +433,10 @@ __global__ void __launch_bounds__(256) cgs_cs_kernel(const T* __restrict__ Z, in
 #pragma unroll
         for (int v = 0; v < VN; ++v) z[k][v] = T(0);
     }
-    // the tile of w: every warp needs it for the projection, and in UPD_PROJ every warp forms
-    // the updated tile itself; in UPD_NORM only warp 0 (which applies the update).  Loaded
-    // here so the load overlaps the column loads
+    // every warp needs the tile of w for the projection; in the update modes only warp 0
+    // (which applies the update), loading it here so the load overlaps the column loads
     T x[VN];
-    if (valid && (MODE != CGS_UPD_NORM || wid == 0)) load_vec<T, VN>(w + r, x);
+    if (valid && (MODE == CGS_PROJ || wid == 0)) load_vec<T, VN>(w + r, x);
     else
 #pragma unroll
       for (int v = 0; v < VN; ++v) x[v] = T(0);
@@ -456,24 +453,6 @@ __global__ void __launch_bounds__(256) cgs_cs_kernel(const T* __restrict__ Z, in
         const T cf = scoef[wid + CGS_WARPS * k];
 #pragma unroll
         for (int v = 0; v < VN; ++v) p[v] = fma(cf, z[k][v], p[v]);
-      }
-      if constexpr (MODE == CGS_UPD_PROJ) {
-        // every warp forms the updated tile from the warps' partial updates (the same fixed
-        // warp order in each, so all hold the same values), warp 0 stores it, and each
-        // projects it on its own columns: one barrier per tile; the other buffer is free
-        // again for tile + 2 once every warp has passed the next tile's barrier
-        T* pb = part + (it & 1) * CGS_WARPS * TR;
-#pragma unroll
-        for (int v = 0; v < VN; ++v) pb[wid * TR + lane * VN + v] = p[v];
-        __syncthreads();
-#pragma unroll
-        for (int q = 0; q < CGS_WARPS; ++q)
-#pragma unroll
-          for (int v = 0; v < VN; ++v) x[v] -= pb[q * TR + lane * VN + v];
-        if (wid == 0 && valid) store_vec<T, VN>(w + r, x);
-#pragma unroll
-        for (int k = 0; k < NCW; ++k) acc_dot<T, VN>(acc[k], z[k], x);
-        continue;
       }
 #pragma unroll
       for (int v = 0; v < VN; ++v) part[wid * TR + lane * VN + v] = p[v];
