@@ -198,7 +198,10 @@ def algorithmic_flops(kind, K, E, F, dim, p, m, T=8):
 # DRAM bytes (read + write) per launch from one ncu capture of the same kernel on the same
 # workload, keyed (workload, element bytes, kernel class); an entry is dropped when its
 # kernel changes.  The summaries under profiles/ give the commands.
-NCU_TRAFFIC = {}
+NCU_TRAFFIC = {
+    ("vortex3d", 4, "jvp_elem"): (663010475, "profiles/traffic_vortex3d_48_p2_m30_fp32.md"),
+    ("vortex3d", 4, "jvp_face"): (2769932160, "profiles/traffic_vortex3d_48_p2_m30_fp32.md"),
+}
 
 
 def fp64_peak(capi):
