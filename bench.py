@@ -142,7 +142,7 @@ def algorithmic_bytes(kind, T, K, E, F, dim, p, m, face_jacobians=True):
     output written once (T = 4 or 8 bytes per value).  G is the face-flux buffer
     [F][nfq][nv] between the face and element kernels of one operator application.
 
-    jvp: one whole J v application (face + element kernels), SURVEY's minimum of three
+    jvp: one whole J v application (face + element kernels) at its minimum of three
     K-vector passes (read v, read the linearisation state, write J v) plus the element
     geometry, the figure a fused J v would move."""
     nb, nq, nfq, nv, nf = shape(dim, p)

@@ -403,6 +403,16 @@ PCEXP_DEV void cgs_grid_tail(const Acc<T>* red, int nred, int mode, int j, KStat
 // the chunks still in registers (two block barriers per tile).
 constexpr int CGS_WARPS = 8;
 
+// 16-byte asynchronous copy global -> shared (bypassing L1), and its group fences
+PCEXP_DEV void cgs_cp16(void* dst, const void* src) {
+  asm volatile("cp.async.cg.shared.global [%0], [%1], 16;" ::"r"((uint32_t)__cvta_generic_to_shared(dst)),
+               "l"(src)
+               : "memory");
+}
+PCEXP_DEV void cgs_cp_commit() { asm volatile("cp.async.commit_group;" ::: "memory"); }
+PCEXP_DEV void cgs_cp_wait_prev() { asm volatile("cp.async.wait_group 1;" ::: "memory"); }
+PCEXP_DEV void cgs_cp_wait_all() { asm volatile("cp.async.wait_all;" ::: "memory"); }
+
 template <class T, int NCW, int MODE>
 __global__ void __launch_bounds__(256) cgs_cs_kernel(const T* __restrict__ Z, int64_t ldz, int64_t Kp, int j,
                                                      T* __restrict__ w, T* __restrict__ out, KState* ks,
@@ -421,25 +431,67 @@ __global__ void __launch_bounds__(256) cgs_cs_kernel(const T* __restrict__ Z, in
 #pragma unroll
   for (int k = 0; k <= NCW; ++k) acc[k].zero();
   const int64_t ntile = (Kp + TR - 1) / TR;
-  for (int64_t t = blockIdx.x; t < ntile; t += gridDim.x) {
+  // FP32 update-and-projection pass: each thread copies its own chunks of the block's next
+  // tile into its own shared-memory slots with cp.async while it works on the current tile
+  // (two stages), so the next tile's loads are in flight across this tile's two block
+  // barriers without holding registers; no other thread reads a thread's slots, so the copies
+  // need no barrier of their own.  (C5: 29.5 -> 26.4 ms per step; the projection pass, which
+  // has no barriers, measured slower staged: 24.6 against 22.3 ms.)
+  constexpr bool STAGED = MODE == CGS_UPD_PROJ && sizeof(T) == 4;
+  constexpr int SLOTS = NCW + 1;  // the thread's column chunks, then its chunk of w
+  __shared__ __align__(16) T stg[STAGED ? 2 * CGS_WARPS * SLOTS * TR : 1];
+  auto slot = [&](int buf, int k) { return stg + ((buf * CGS_WARPS + wid) * SLOTS + k) * TR + lane * VN; };
+  auto issue = [&](int64_t t, int buf) {
+    const int64_t r = t * TR + lane * VN;
+    if (r >= Kp) return;
+#pragma unroll
+    for (int k = 0; k < NCW; ++k)
+      if (wid + CGS_WARPS * k < nc) cgs_cp16(slot(buf, k), Z + (wid + CGS_WARPS * k) * ldz + r);
+    if (MODE == CGS_PROJ || wid == 0) cgs_cp16(slot(buf, NCW), w + r);
+  };
+  if constexpr (STAGED) {
+    if ((int64_t)blockIdx.x < ntile) issue(blockIdx.x, 0);
+    cgs_cp_commit();
+  }
+  int it = 0;
+  for (int64_t t = blockIdx.x; t < ntile; t += gridDim.x, ++it) {
     const int64_t r = t * TR + lane * VN;
     const bool valid = r < Kp;
+    if constexpr (STAGED) {
+      if (t + gridDim.x < ntile) issue(t + gridDim.x, (it & 1) ^ 1);
+      cgs_cp_commit();
+      cgs_cp_wait_prev();  // this tile's copies (all but the group just committed) have landed
+    }
     T z[NCW][VN];
 #pragma unroll
     for (int k = 0; k < NCW; ++k) {
       const int c = wid + CGS_WARPS * k;
-      if (valid && c < nc) load_vec<T, VN>(Z + c * ldz + r, z[k]);
-      else
+      if (valid && c < nc) {
+        if constexpr (STAGED) {
+#pragma unroll
+          for (int v = 0; v < VN; ++v) z[k][v] = slot(it & 1, k)[v];
+        } else {
+          load_vec<T, VN>(Z + c * ldz + r, z[k]);
+        }
+      } else {
 #pragma unroll
         for (int v = 0; v < VN; ++v) z[k][v] = T(0);
+      }
     }
     // every warp needs the tile of w for the projection; in the update modes only warp 0
     // (which applies the update), loading it here so the load overlaps the column loads
     T x[VN];
-    if (valid && (MODE == CGS_PROJ || wid == 0)) load_vec<T, VN>(w + r, x);
-    else
+    if (valid && (MODE == CGS_PROJ || wid == 0)) {
+      if constexpr (STAGED) {
+#pragma unroll
+        for (int v = 0; v < VN; ++v) x[v] = slot(it & 1, NCW)[v];
+      } else {
+        load_vec<T, VN>(w + r, x);
+      }
+    } else {
 #pragma unroll
       for (int v = 0; v < VN; ++v) x[v] = T(0);
+    }
     if constexpr (MODE == CGS_PROJ) {
 #pragma unroll
       for (int k = 0; k < NCW; ++k) acc_dot<T, VN>(acc[k], z[k], x);
@@ -481,6 +533,7 @@ __global__ void __launch_bounds__(256) cgs_cs_kernel(const T* __restrict__ Z, in
       }
     }
   }
+  if constexpr (STAGED) cgs_cp_wait_all();  // no copy outlives the block
   // warp sums of the owned columns (fixed shuffle tree); each column has one owner warp
   if constexpr (MODE != CGS_UPD_NORM) {
 #pragma unroll

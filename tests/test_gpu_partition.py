@@ -97,8 +97,9 @@ def test_group_steps_match_one_context(capi, name, n, scheme):
     grp.close()
 
 
-def test_group_fp32_mixed_step(capi):
-    mesh, p, free = CASES["cube3d"]()
+@pytest.mark.parametrize("name", ["cube3d", "bump2d"])
+def test_group_fp32_mixed_step(capi, name):
+    mesh, p, free = CASES[name]()
     part = capi.partition(mesh, 2)
     one = capi.Context(mesh, p, free, capi.PCEXP_FP32_MIXED, m_max=12)
     grp = capi.Group(mesh, part, p, free, capi.PCEXP_FP32_MIXED, m_max=12)
