@@ -318,6 +318,8 @@ def main():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-fp64", action="store_true", help="skip the FP64 form of the headline workload")
     ap.add_argument("--no-2d", action="store_true", help="skip the 2D bump-channel side block")
+    ap.add_argument("--no-partitioned", action="store_true",
+                    help="skip the side block of the headline workload split into element partitions")
     ap.add_argument("--n3d", type=int, default=N3D, help="cubes per side of the 3D vortex (profiling runs)")
     args = ap.parse_args()
     args.warmup = max(args.warmup, 3)
@@ -444,6 +446,7 @@ def main():
         err = float(np.linalg.norm(b - a) / np.linalg.norm(a))
 
     side = None if args.no_2d else bump2d_block(args, capi, W, torch, np, hbm, peak_kind, fp64, dist, fp32)
+    parted = None if (args.no_partitioned or world > 1) else partitioned_block(args, capi, case, prm, np, torch)
 
     cpu = None
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
@@ -482,12 +485,47 @@ def main():
         "speedup_fp32_mixed_vs_fp64": (forms["fp64"]["ms_per_step"] / head["ms_per_step"]) if "fp64" in forms else None,
         "cpu_baseline": cpu,
         "bump2d": side,
+        "partitioned": parted,
         "clocks": head["clocks"],
     }
     if rank == 0:
         print(json.dumps(out))
     if dist:
         dist.destroy_process_group()
+
+
+def partitioned_block(args, capi, case, prm, np, torch, n_parts=2, steps=5, warm=2):
+    """Side block: the headline workload split into n_parts element partitions (recursive
+    coordinate bisection, one-element halos), all on this GPU, FP32-mixed, against one context
+    on the whole mesh, both driven through the public API with per-step host synchronisation
+    (step info read back) and timed by the wall clock over the same steps.  Reports both times
+    and the relative state difference after the same steps (the partitions' split
+    Gram-Schmidt sums round differently)."""
+    part = capi.partition(case.mesh, n_parts)
+
+    def run(make):
+        obj = make()
+        obj.project_state(capi.PCEXP_PROJ_VORTEX, prm)
+        for _ in range(warm):
+            obj.step(capi.PCEXP_SCHEME_PCEXP, capi.PCEXP_DT_GLOBAL_CFL, case.cfl, case.m)
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        for _ in range(steps):
+            obj.step(capi.PCEXP_SCHEME_PCEXP, capi.PCEXP_DT_GLOBAL_CFL, case.cfl, case.m)
+        torch.cuda.synchronize()
+        sec = (time.perf_counter() - t0) / steps
+        u = obj.get_state()
+        obj.close()
+        return sec, u
+
+    t_g, u_g = run(lambda: capi.Group(case.mesh, part, case.p, case.free, capi.PCEXP_FP32_MIXED, m_max=case.m))
+    t_1, u_1 = run(lambda: capi.Context(case.mesh, case.p, case.free, capi.PCEXP_FP32_MIXED, m_max=case.m))
+    K = u_1.size
+    return {"parts": n_parts, "devices": [0] * n_parts, "steps": steps, "warmup": warm,
+            "ms_per_step": t_g * 1e3, "value": K / t_g, "unit": UNIT,
+            "single_context_ms_per_step": t_1 * 1e3, "time_vs_single_context": t_g / t_1,
+            "state_rel_diff_vs_single_context": float(np.linalg.norm(u_g - u_1) / np.linalg.norm(u_1)),
+            "timing": "wall clock, per-step host synchronisation, the same for both"}
 
 
 def bump2d_block(args, capi, W, torch, np, hbm, peak_kind, fp64, dist=None, fp32=None):
