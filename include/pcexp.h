@@ -424,12 +424,21 @@ int pcexp_group_jvp(pcexp_group* group, const double* U, const double* v, double
 int pcexp_group_arnoldi(pcexp_group* group, const double* U, const double* b, int m, double* H,
                         int* k, double* beta);
 
-/* One step of pcexp_step on the group's state: schemes PCEXP, EXP1, ETD2; dt_mode GIVEN or
- * GLOBAL_CFL (LOCAL_CFL: UNSUPPORTED).  info as for pcexp_step, res_norm over the whole mesh.
- * Steps run eagerly (no CUDA graph).  Errors: those of pcexp_step, TIMEOUT (a partition missed
- * a rendezvous for 120 s: it failed or stalled). */
+/* One step of pcexp_step on the group's state (schemes, dt modes and their rules as there;
+ * the global dt of GLOBAL_CFL is the minimum over all partitions' elements, LOCAL_CFL scales
+ * each partition's own rows by its own elements' steps).  info as for pcexp_step, res_norm
+ * over the whole mesh.  Steps run eagerly (no CUDA graph).  Errors: those of pcexp_step,
+ * TIMEOUT (a partition missed a rendezvous for 120 s: it failed or stalled). */
 int pcexp_group_step(pcexp_group* group, int scheme, int dt_mode, double dt_or_cfl, int m,
                      pcexp_step_info* info);
+
+/* pcexp_march_steady on the group's state (Sec. 5.2, Eq. cfl): each iteration's density
+ * residual norm is summed over the partitions on the host (partition order) before the stop
+ * test and the CFL ramp, so every partition takes the same decisions; the Krylov-error cap
+ * (krylov_tol of the options) uses the estimate every partition shares.  info as for
+ * pcexp_march_steady.  Errors: those of pcexp_march_steady, TIMEOUT. */
+int pcexp_group_march_steady(pcexp_group* group, int scheme, double cfl_max, double decades,
+                             int max_iter, int m, pcexp_steady_info* info);
 
 /* Static description of a status code. */
 const char* pcexp_status_string(int status);

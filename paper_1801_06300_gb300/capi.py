@@ -127,6 +127,8 @@ SIGNATURES = {
     "pcexp_group_jvp": (C.c_int, [_P, _P, _P, _P]),
     "pcexp_group_arnoldi": (C.c_int, [_P, _P, _P, C.c_int, _D, C.POINTER(C.c_int), _D]),
     "pcexp_group_step": (C.c_int, [_P, C.c_int, C.c_int, C.c_double, C.c_int, C.POINTER(pcexp_step_info)]),
+    "pcexp_group_march_steady": (C.c_int, [_P, C.c_int, C.c_double, C.c_double, C.c_int, C.c_int,
+                                           C.POINTER(pcexp_steady_info)]),
     "pcexp_status_string": (C.c_char_p, [C.c_int]),
     "pcexp_last_error": (C.c_char_p, []),
 }
@@ -230,14 +232,15 @@ class Group:
     """Owns one pcexp_group (a partitioned run, host arrays of the whole mesh)."""
 
     def __init__(self, mesh, part, p: int, free, precision: int = PCEXP_FP64, m_max: int = 30,
-                 eta: float = 0.0, basis_io: int = PCEXP_BASIS_PAPER, devices=None, omega=None):
+                 eta: float = 0.0, basis_io: int = PCEXP_BASIS_PAPER, devices=None, omega=None,
+                 krylov_tol: float = 0.0):
         lib = load()
         m, self._keep = _mesh_struct(mesh)
         part = np.ascontiguousarray(part, np.int32)
         self.n = int(part.max()) + 1
         dev = None if devices is None else np.ascontiguousarray(devices, np.int32)
         ph = _physics(free, omega)
-        op = pcexp_options(precision, m_max, eta, basis_io, 0.0)
+        op = pcexp_options(precision, m_max, eta, basis_io, krylov_tol)
         self.g = C.c_void_p()
         check(lib.pcexp_group_create(C.byref(self.g), C.byref(m), part.ctypes.data_as(_P), self.n,
                                      dev.ctypes.data_as(_P) if dev is not None else None, p, C.byref(ph),
@@ -301,6 +304,13 @@ class Group:
         check(self.lib.pcexp_group_arnoldi(self.g, U.ctypes.data_as(_P), b.ctypes.data_as(_P), m,
                                            H.ctypes.data_as(_D), C.byref(k), C.byref(beta)), "pcexp_group_arnoldi")
         return H.reshape(m + 1, m), k.value, beta.value
+
+    def march_steady(self, scheme: int, cfl_max: float, decades: float, max_iter: int, m: int):
+        inf = pcexp_steady_info()
+        check(self.lib.pcexp_group_march_steady(self.g, scheme, cfl_max, decades, max_iter, m, C.byref(inf)),
+              "pcexp_group_march_steady")
+        return dict(iterations=inf.iterations, res_first=inf.res_first, res_last=inf.res_last,
+                    converged=bool(inf.converged))
 
     def step(self, scheme: int, dt_mode: int, dt_or_cfl: float, m: int):
         inf = pcexp_step_info()

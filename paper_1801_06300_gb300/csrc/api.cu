@@ -7,6 +7,7 @@
 // non-NULL info, the steady march (one 8-byte residual read per iteration)
 // and host-pointer transfers synchronise.
 #include <algorithm>
+#include <cfloat>
 #include <chrono>
 #include <cmath>
 #include <condition_variable>
@@ -122,6 +123,7 @@ struct pcexp_group {
   uint64_t gen = 0;
   bool abort = false;
   std::vector<const void*> pub;
+  std::vector<double> hostval;  // per partition: a host scalar being summed (steady march)
   std::vector<cudaEvent_t> ev_ready, ev_done;
   std::vector<std::string> errs;
 };
@@ -366,6 +368,18 @@ int group_cgs(pcexp_ctx* c, int mode, int j) {
   });
 }
 
+// Sum over the partitions of a host scalar, in partition order (the same on every partition).
+int group_host_sum(pcexp_ctx* c, double x, double* sum) {
+  pcexp_group* g = c->grp;
+  g->hostval[(size_t)c->part] = x;
+  PCEXP_TRY(group_barrier(g));
+  double s = 0;
+  for (int q = 0; q < g->n; ++q) s += g->hostval[(size_t)q];
+  PCEXP_TRY(group_barrier(g));  // no partition writes its next value before all have read
+  *sum = s;
+  return PCEXP_OK;
+}
+
 // ss->dt <- the minimum over the partitions of their ss->dtmin_scratch (Eq. x3d over all elements)
 int group_min_dt(pcexp_ctx* c) {
   return group_round(c, dev_field(c->ss, offsetof(StepState, dtmin_scratch)), [&](const PartPtrs& pp) -> int {
@@ -595,9 +609,15 @@ int enqueue_step(pcexp_ctx* c, int scheme, int dt_mode, int m) {
   if (dt_mode == PCEXP_DT_GIVEN) {
     PCEXP_LAUNCH(c, PCEXP_KC_OTHER, launch_copy_dt(c->ss, c->param, c->st));
   } else if (c->grp) {
-    // the minimum over the own elements, then over the partitions
+    // the own elements' steps; the global one is their minimum over the partitions (the halo
+    // elements' local steps are not formed: their rows of every scaled vector are zero)
     PCEXP_LAUNCH(c, PCEXP_KC_DT, launch_local_dt<T>(d, S0, c->param, 0.0, dte, &c->ss->dtmin_scratch, c->partials, &c->ss->counter, c->st));
-    PCEXP_TRY(group_min_dt(c));
+    if (dt_mode == PCEXP_DT_LOCAL_CFL) {
+      escale = dte;
+      PCEXP_LAUNCH(c, PCEXP_KC_OTHER, launch_set_dt(c->ss, 1.0, c->st));
+    } else {
+      PCEXP_TRY(group_min_dt(c));
+    }
   } else {
     PCEXP_LAUNCH(c, PCEXP_KC_DT, launch_local_dt<T>(d, S0, c->param, 0.0, dte, &c->ss->dt, c->partials, &c->ss->counter, c->st));
     if (dt_mode == PCEXP_DT_LOCAL_CFL) {
@@ -725,6 +745,18 @@ int march_impl(pcexp_ctx* c, int scheme, double cfl_max, double decades, int max
     PCEXP_CK(cudaMemcpyAsync(&h, c->ss, sizeof(h), cudaMemcpyDeviceToHost, c->st));
     PCEXP_CK(cudaStreamSynchronize(c->st));
     rn = h.res_norm;
+    if (c->grp) {
+      // the norm over the whole mesh from the partitions' sums of squares (each partition's norm
+      // is over its own rows, divided by its submesh's measure), and the ramp of Eq. cfl from it
+      const double a = rn * c->volume;
+      double s2 = 0;
+      PCEXP_TRY(group_host_sum(c, a * a, &s2));
+      rn = std::sqrt(s2) / c->grp->volume;
+      const double ra = rn > 0 ? 1.0 / (rn * rn * rn) : DBL_MAX;
+      const double rb = 1.0 + (double)(n - 1) / (2 * c->p + 1);
+      h.cfl = std::fmin(cfl_max, std::fmax(ra, rb));
+      PCEXP_LAUNCH(c, PCEXP_KC_OTHER, launch_set_cfl(c->ss, h.cfl, c->st));
+    }
     if (!std::isfinite(rn)) {
       g_last_error = "non-finite residual norm";
       return PCEXP_ERR_NONFINITE;
@@ -2037,6 +2069,7 @@ int pcexp_group_create(pcexp_group** out, const pcexp_mesh* mesh, const int32_t*
   g->ev_ready.assign((size_t)n_parts, nullptr);
   g->ev_done.assign((size_t)n_parts, nullptr);
   g->pub.assign((size_t)n_parts, nullptr);
+  g->hostval.assign((size_t)n_parts, 0.0);
   g->elems.resize((size_t)n_parts);
   g->own_volume.assign((size_t)n_parts, 0.0);
   g->fp32 = opt->precision == PCEXP_FP32_MIXED;
@@ -2238,15 +2271,30 @@ int pcexp_group_arnoldi(pcexp_group* g, const double* U, const double* b, int m,
   return PCEXP_OK;
 }
 
+int pcexp_group_march_steady(pcexp_group* g, int scheme, double cfl_max, double decades, int max_iter, int m,
+                             pcexp_steady_info* info) {
+  PCEXP_TRY(check_group(g));
+  if (scheme != PCEXP_SCHEME_PCEXP && scheme != PCEXP_SCHEME_EXP1) return PCEXP_ERR_INVALID_ARG;
+  if (m < 1 || m > g->ctx[0]->m_max || !(cfl_max > 0) || !(decades > 0) || max_iter < 0) return PCEXP_ERR_INVALID_ARG;
+  std::vector<pcexp_steady_info> inf((size_t)g->n);
+  PCEXP_TRY(group_run(g, [&](int k) -> int {
+    pcexp_ctx* c = g->ctx[(size_t)k];
+    return c->fp32 ? march_impl<float>(c, scheme, cfl_max, decades, max_iter, m, &inf[(size_t)k])
+                   : march_impl<double>(c, scheme, cfl_max, decades, max_iter, m, &inf[(size_t)k]);
+  }));
+  if (info) *info = inf[0];  // every partition took the same decisions from the same norms
+  return PCEXP_OK;
+}
+
 int pcexp_group_step(pcexp_group* g, int scheme, int dt_mode, double dt_or_cfl, int m, pcexp_step_info* info) {
   PCEXP_TRY(check_group(g));
   if (scheme != PCEXP_SCHEME_PCEXP && scheme != PCEXP_SCHEME_EXP1 && scheme != PCEXP_SCHEME_ETD2)
     return PCEXP_ERR_INVALID_ARG;
-  if (dt_mode == PCEXP_DT_LOCAL_CFL) {
-    g_last_error = "local time steps are not available in a partitioned run";
-    return PCEXP_ERR_UNSUPPORTED;
+  if (dt_mode < PCEXP_DT_GIVEN || dt_mode > PCEXP_DT_LOCAL_CFL) return PCEXP_ERR_INVALID_ARG;
+  if (scheme == PCEXP_SCHEME_ETD2 && dt_mode == PCEXP_DT_LOCAL_CFL) {
+    g_last_error = "ETD2 is a time-accurate scheme: give dt or a global CFL number";
+    return PCEXP_ERR_INVALID_ARG;
   }
-  if (dt_mode != PCEXP_DT_GIVEN && dt_mode != PCEXP_DT_GLOBAL_CFL) return PCEXP_ERR_INVALID_ARG;
   if (m < 1 || m > g->ctx[0]->m_max || !(dt_or_cfl > 0)) return PCEXP_ERR_INVALID_ARG;
   std::vector<pcexp_step_info> inf((size_t)g->n);
   PCEXP_TRY(group_run(g, [&](int k) -> int {

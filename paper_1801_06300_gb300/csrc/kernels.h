@@ -318,6 +318,7 @@ cudaError_t launch_adj_bbar(const double* Z, const double* Vb, double* bbar, int
                             AdjState* as, double* partials, cudaStream_t st);
 cudaError_t launch_axpy(double* y, const double* x, const double* a_dev, double a_host, int64_t n, cudaStream_t st);
 cudaError_t launch_set_dt(StepState* ss, double dt, cudaStream_t st);
+cudaError_t launch_set_cfl(StepState* ss, double cfl, cudaStream_t st);
 cudaError_t launch_set_param(double* param, double v, cudaStream_t st);
 cudaError_t launch_copy_dt(StepState* ss, const double* param, cudaStream_t st);
 

@@ -1116,6 +1116,11 @@ cudaError_t launch_reset_kstate(KState* ks, cudaStream_t st) {
 }
 
 __global__ void set_dt_kernel(StepState* ss, double dt) { ss->dt = dt; }
+__global__ void set_cfl_kernel(StepState* ss, double cfl) { ss->cfl = cfl; }
+cudaError_t launch_set_cfl(StepState* ss, double cfl, cudaStream_t st) {
+  set_cfl_kernel<<<1, 1, 0, st>>>(ss, cfl);
+  return cudaGetLastError();
+}
 __global__ void keep_dt_kernel(StepState* ss) { ss->dt_prev = ss->dt; }
 __global__ void cap_cfl_kernel(StepState* ss, double cap) { ss->cfl = fmin(ss->cfl, cap); }
 cudaError_t launch_cap_cfl(StepState* ss, double cap, cudaStream_t st) {

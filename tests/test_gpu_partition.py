@@ -117,7 +117,7 @@ def test_group_fp32_mixed_step(capi, name):
     grp.close()
 
 
-def test_group_projection_and_unsupported_modes(capi):
+def test_group_projection_and_rejected_modes(capi):
     mesh = W.periodic_square(12, 10.0, 0.1, 5)
     free = W.Freestream(0.5, 45.0)
     part = capi.partition(mesh, 2)
@@ -128,11 +128,50 @@ def test_group_projection_and_unsupported_modes(capi):
     grp.project_state(capi.PCEXP_PROJ_VORTEX, prm)
     assert np.array_equal(grp.get_state(), one.get_state())
     with pytest.raises(capi.PcexpError) as e:
-        grp.step(capi.PCEXP_SCHEME_PCEXP, capi.PCEXP_DT_LOCAL_CFL, 10.0, 8)
-    assert e.value.code == capi.PCEXP_ERR_UNSUPPORTED
+        grp.step(capi.PCEXP_SCHEME_ETD2, capi.PCEXP_DT_LOCAL_CFL, 10.0, 8)
+    assert e.value.code == capi.PCEXP_ERR_INVALID_ARG
     # a failed call leaves the group usable
     grp.step(capi.PCEXP_SCHEME_PCEXP, capi.PCEXP_DT_GIVEN, 0.01, 8)
     one.step(capi.PCEXP_SCHEME_PCEXP, capi.PCEXP_DT_GIVEN, 0.01, 8)
     assert rel(grp.get_state(), one.get_state()) <= 1e-12
+    one.close()
+    grp.close()
+
+
+@pytest.mark.parametrize("n,tol", [(2, 0.0), (3, 1e-5)])
+def test_group_local_steps_and_steady_march(capi, n, tol):
+    """Local time steps (each partition scales its own rows by its own elements' steps) and the
+    steady march (norms summed over the partitions before the stop test and the CFL ramp; with
+    a Krylov tolerance, the error cap from the shared estimate) against one context.  The march
+    amplifies the rounding of the split Gram-Schmidt sums (7e-8 in the residual norm after 40
+    iterations; with a Krylov tolerance a checkpoint decision can flip), so the comparison is
+    tight over the first iterations: the same iterations and norms, states within 1e-10 after 5;
+    without a tolerance the norms stay within 1e-6 over 40."""
+    mesh, p, free = CASES["bump2d"]()
+    part = capi.partition(mesh, n)
+    one = capi.Context(mesh, p, free, capi.PCEXP_FP64, m_max=12, krylov_tol=tol)
+    grp = capi.Group(mesh, part, p, free, capi.PCEXP_FP64, m_max=12, krylov_tol=tol)
+    u = _state(one, 5)
+    one.set_state(u)
+    grp.set_state(u)
+    a = one.step(capi.PCEXP_SCHEME_PCEXP, capi.PCEXP_DT_LOCAL_CFL, 10.0, 12)
+    b = grp.step(capi.PCEXP_SCHEME_PCEXP, capi.PCEXP_DT_LOCAL_CFL, 10.0, 12)
+    assert a["k"] == b["k"] and b["dt"] == 1.0
+    s1 = one.get_state()
+    assert rel(s1, u) > 1e-6 and rel(grp.get_state(), s1) <= 1e-12
+    one.project_state(capi.PCEXP_PROJ_FREESTREAM, [])
+    grp.project_state(capi.PCEXP_PROJ_FREESTREAM, [])
+    m1 = one.march_steady(capi.PCEXP_SCHEME_PCEXP, 10.0, 10.0, 5, 12)
+    mg = grp.march_steady(capi.PCEXP_SCHEME_PCEXP, 10.0, 10.0, 5, 12)
+    assert mg["iterations"] == m1["iterations"] == 5
+    assert abs(mg["res_first"] - m1["res_first"]) <= 1e-13 * m1["res_first"]
+    assert abs(mg["res_last"] - m1["res_last"]) <= 1e-10 * m1["res_last"]
+    assert m1["res_last"] != m1["res_first"]
+    assert rel(grp.get_state(), one.get_state()) <= 1e-10
+    if tol == 0.0:
+        m1 = one.march_steady(capi.PCEXP_SCHEME_PCEXP, 10.0, 10.0, 35, 12)
+        mg = grp.march_steady(capi.PCEXP_SCHEME_PCEXP, 10.0, 10.0, 35, 12)
+        assert mg["iterations"] == m1["iterations"] == 35
+        assert abs(mg["res_last"] - m1["res_last"]) <= 1e-6 * m1["res_last"]
     one.close()
     grp.close()
