@@ -1923,6 +1923,14 @@ int group_run(pcexp_group* g, F&& fn) {
   return PCEXP_OK;
 }
 
+// restores the calling thread's current device when a group call returns (the per-partition
+// calls it makes switch to each partition's device)
+struct DeviceGuard {
+  int dev = 0;
+  DeviceGuard() { cudaGetDevice(&dev); }
+  ~DeviceGuard() { cudaSetDevice(dev); }
+};
+
 int check_group(pcexp_group* g) {
   if (!g) {
     g_last_error = "null group";
@@ -2177,23 +2185,20 @@ int pcexp_group_sizes(const pcexp_group* g, int k, int64_t* n_owned, int64_t* n_
 int pcexp_group_set_state(pcexp_group* g, const double* U) {
   PCEXP_TRY(check_group(g));
   if (!U) return PCEXP_ERR_INVALID_ARG;
-  int dev0 = 0;
-  cudaGetDevice(&dev0);
+  DeviceGuard keep;
   std::vector<double> loc;
   for (int k = 0; k < g->n; ++k) {
     gather_local(g, k, U, loc, true);
     const int r = pcexp_set_state(g->ctx[(size_t)k], loc.data(), 0);
     if (r != PCEXP_OK) return r;
   }
-  cudaSetDevice(dev0);
   return PCEXP_OK;
 }
 
 int pcexp_group_get_state(pcexp_group* g, double* U) {
   PCEXP_TRY(check_group(g));
   if (!U) return PCEXP_ERR_INVALID_ARG;
-  int dev0 = 0;
-  cudaGetDevice(&dev0);
+  DeviceGuard keep;
   std::vector<double> loc;
   for (int k = 0; k < g->n; ++k) {
     loc.assign((size_t)g->ctx[(size_t)k]->K, 0.0);
@@ -2201,19 +2206,16 @@ int pcexp_group_get_state(pcexp_group* g, double* U) {
     if (r != PCEXP_OK) return r;
     scatter_owned(g, k, loc, U);
   }
-  cudaSetDevice(dev0);
   return PCEXP_OK;
 }
 
 int pcexp_group_project_state(pcexp_group* g, int kind, const double* params, int n_params) {
   PCEXP_TRY(check_group(g));
-  int dev0 = 0;
-  cudaGetDevice(&dev0);
+  DeviceGuard keep;
   for (int k = 0; k < g->n; ++k) {
     const int r = pcexp_project_state(g->ctx[(size_t)k], kind, params, n_params);
     if (r != PCEXP_OK) return r;
   }
-  cudaSetDevice(dev0);
   return PCEXP_OK;
 }
 
