@@ -796,35 +796,20 @@ __global__ void __launch_bounds__(128) linearize_face_kernel(DGData<T> d, const 
 }
 
 template <class T, int D, int P>
-__global__ void __launch_bounds__(256, sizeof(T) == 4 ? 3 : 1) face_apply_kernel(DGData<T> d, const T* __restrict__ Bface,
+__global__ void __launch_bounds__(256) face_apply_kernel(DGData<T> d, const T* __restrict__ Bface,
                                                          const T* __restrict__ dv, T* __restrict__ G,
                                                          const int* __restrict__ skip) {
   using O = Ord<D, P>;
   constexpr int NB = O::NB, NFQ = O::NFQ, NV = O::NV, NPERM = O::NPERM, NN = NV * NV;
   constexpr bool SM = O::SMEM_BF;
   __shared__ T sBf[SM ? O::NBF : 1];
-  // 3D: the element rows of dv of the block's faces, staged once (a face's nfq points, on
-  // consecutive threads, all read both of its elements' rows)
-  constexpr int NVB = NV * NB, MAXF = 256 / NFQ + 2;
-  __shared__ __align__(16) T srow[SM ? 1 : MAXF * 2 * NVB];
   if (skip && *skip) return;
-  const int64_t n = d.F * NFQ;
-  const int64_t p0 = (int64_t)blockIdx.x * blockDim.x;
-  const int64_t f0 = p0 / NFQ;
-  if constexpr (SM) {
+  if constexpr (SM)
     for (int i = threadIdx.x; i < O::NBF; i += blockDim.x) sBf[i] = d.Bf[i];
-  } else {
-    const int64_t pl = (p0 + blockDim.x < n ? p0 + blockDim.x : n) - 1;
-    const int nfb = (int)(pl / NFQ - f0 + 1);
-    for (int i = threadIdx.x; i < nfb * 2 * NVB; i += blockDim.x) {
-      const int fl = i / (2 * NVB), r = i - fl * 2 * NVB, side = r / NVB, k = r - side * NVB;
-      const int e = d.fel[2 * (f0 + fl) + side];
-      srow[i] = e >= 0 ? __ldg(dv + (int64_t)e * NVB + k) : T(0);
-    }
-  }
   __syncthreads();
   const T* Bf = SM ? sBf : d.Bf;
-  const int64_t idx = p0 + threadIdx.x;
+  const int64_t n = d.F * NFQ;
+  const int64_t idx = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
   if (idx >= n) return;
   const int64_t f = idx / NFQ;
   const int q = (int)(idx - f * NFQ);
@@ -838,7 +823,7 @@ __global__ void __launch_bounds__(256, sizeof(T) == 4 ? 3 : 1) face_apply_kernel
   // padded copy, 16-byte loads) and the element's rows of dv (8-byte loads when nb is even:
   // the kernel is bound by its load instructions as much as by its bytes)
   constexpr int NBP = PADV<T, NB>;
-  auto trace = [&](int64_t e, int side, int fl, int pm, T(&t)[NV]) {
+  auto trace = [&](int64_t e, int fl, int pm, T(&t)[NV]) {
     T b[NBP];
     if constexpr (SM) {
       const T* be = Bf + ((fl * NPERM + pm) * NFQ + q) * NB;
@@ -847,16 +832,11 @@ __global__ void __launch_bounds__(256, sizeof(T) == 4 ? 3 : 1) face_apply_kernel
     } else {
       load_row<T, NBP, true>(d.BfP + ((fl * NPERM + pm) * NFQ + q) * NBP, b);
     }
-    const T* ve = SM ? dv + e * NV * NB : srow + ((f - f0) * 2 + side) * NVB;
+    const T* ve = dv + e * NV * NB;
 #pragma unroll
     for (int v = 0; v < NV; ++v) {
       T c[NB];
-      if constexpr (SM) {
-        load_coeffs<T, NB>(ve + v * NB, c);
-      } else {
-#pragma unroll
-        for (int j = 0; j < NB; ++j) c[j] = ve[v * NB + j];
-      }
+      load_coeffs<T, NB>(ve + v * NB, c);
       T a = 0;
 #pragma unroll
       for (int j = 0; j < NB; ++j) a += b[j] * c[j];
@@ -864,8 +844,8 @@ __global__ void __launch_bounds__(256, sizeof(T) == 4 ? 3 : 1) face_apply_kernel
     }
   };
   T tL[NV], tR[NV];
-  trace(eL, 0, fL, 0, tL);
-  if (eR >= 0) trace(eR, 1, fR, pR, tR);
+  trace(eL, fL, 0, tL);
+  if (eR >= 0) trace(eR, fR, pR, tR);
   T* g = G + idx * NV;
 #pragma unroll
   for (int v = 0; v < NV; ++v) {
