@@ -418,6 +418,15 @@ int pcexp_group_project_state(pcexp_group* group, int kind, const double* params
 int pcexp_group_residual(pcexp_group* group, const double* U, double* R);
 int pcexp_group_jvp(pcexp_group* group, const double* U, const double* v, double* Jv);
 
+/* The adjoint operator passes of the reverse step on the whole mesh (host arrays): J(U)^T w as
+ * pcexp_vjp, and (d(J(U) v)/dU)^T w as pcexp_jvp_state_adjoint (FP64 groups; UNSUPPORTED in
+ * FP32-mixed groups and rotating frames).  Each partition receives only its own rows; the halo
+ * rows of U, v and w come from the exchange (an own element's transposed face terms need w on
+ * the neighbouring halo element), and each partition returns its own rows. */
+int pcexp_group_vjp(pcexp_group* group, const double* U, const double* w, double* JTw);
+int pcexp_group_jvp_state_adjoint(pcexp_group* group, const double* U, const double* v,
+                                  const double* w, double* out);
+
 /* Arnoldi process of pcexp_arnoldi (J at U, start vector b; host arrays) with the partitioned
  * Gram-Schmidt sums: H [(m+1) x m] row-major, *k, *beta as for pcexp_arnoldi.  The call
  * checks that every partition holds the same H (else CUDA). */

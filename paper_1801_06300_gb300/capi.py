@@ -126,6 +126,8 @@ SIGNATURES = {
     "pcexp_group_residual": (C.c_int, [_P, _P, _P]),
     "pcexp_group_jvp": (C.c_int, [_P, _P, _P, _P]),
     "pcexp_group_arnoldi": (C.c_int, [_P, _P, _P, C.c_int, _D, C.POINTER(C.c_int), _D]),
+    "pcexp_group_vjp": (C.c_int, [_P, _P, _P, _P]),
+    "pcexp_group_jvp_state_adjoint": (C.c_int, [_P, _P, _P, _P, _P]),
     "pcexp_group_step": (C.c_int, [_P, C.c_int, C.c_int, C.c_double, C.c_int, C.POINTER(pcexp_step_info)]),
     "pcexp_group_march_steady": (C.c_int, [_P, C.c_int, C.c_double, C.c_double, C.c_int, C.c_int,
                                            C.POINTER(pcexp_steady_info)]),
@@ -295,6 +297,19 @@ class Group:
         U, v, out = self._host(U), self._host(v), np.empty(self.K)
         check(self.lib.pcexp_group_jvp(self.g, U.ctypes.data_as(_P), v.ctypes.data_as(_P), out.ctypes.data_as(_P)),
               "pcexp_group_jvp")
+        return out
+
+    def vjp(self, U, w):
+        U, w, out = self._host(U), self._host(w), np.empty(self.K)
+        check(self.lib.pcexp_group_vjp(self.g, U.ctypes.data_as(_P), w.ctypes.data_as(_P), out.ctypes.data_as(_P)),
+              "pcexp_group_vjp")
+        return out
+
+    def jvp_state_adjoint(self, U, v, w):
+        U, v, w, out = self._host(U), self._host(v), self._host(w), np.empty(self.K)
+        check(self.lib.pcexp_group_jvp_state_adjoint(self.g, U.ctypes.data_as(_P), v.ctypes.data_as(_P),
+                                                     w.ctypes.data_as(_P), out.ctypes.data_as(_P)),
+              "pcexp_group_jvp_state_adjoint")
         return out
 
     def arnoldi(self, U, b, m: int):

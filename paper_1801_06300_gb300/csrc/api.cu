@@ -1977,6 +1977,38 @@ int group_operator_part(pcexp_ctx* c, const std::vector<double>& u, const std::v
   return export_vec<T>(c, o, out.data(), 0);
 }
 
+// J(U)^T w (adj = 1) or (d(J(U) v)/dU)^T w (adj = 2) of a partition whose inputs carry only
+// their own rows: the halo rows of U, v and w come from the exchange (the transposed face terms
+// of an own element need w on the neighbouring halo element), the output keeps its own rows
+template <class T>
+int group_adjoint_part(pcexp_ctx* c, int adj, const std::vector<double>& u, const std::vector<double>* v,
+                       const std::vector<double>& w, std::vector<double>& out) {
+  const DGData<T> d = dgdata<T>(c);
+  T* a = reinterpret_cast<T*>(c->tmp);
+  T* b = reinterpret_cast<T*>(c->delta);
+  T* ww = reinterpret_cast<T*>(c->V);  // V[0] as scratch
+  T* o = reinterpret_cast<T*>(c->w);
+  PCEXP_TRY(import_vec<T>(c, u.data(), 0, a));
+  PCEXP_TRY(import_vec<T>(c, w.data(), 0, ww));
+  PCEXP_TRY(group_exchange<T>(c, a));
+  PCEXP_TRY(group_exchange<T>(c, ww));
+  if (adj == 1) {
+    PCEXP_TRY(linearize<T>(c, d, a, true));
+    PCEXP_CK(launch_jac_adjoint<T>(d, lindata<T>(c), ww, o, reinterpret_cast<T*>(c->GT), nullptr, T(1), c->st));
+  } else {
+    if constexpr (std::is_same<T, double>::value) {
+      PCEXP_TRY(import_vec<T>(c, v->data(), 0, b));
+      PCEXP_TRY(group_exchange<T>(c, b));
+      PCEXP_CK(launch_jvp_state_adjoint<double>(d, a, b, ww, o, reinterpret_cast<double*>(c->GT), nullptr, 1.0, c->st));
+    } else {
+      return UNSUPPORTED_FP32_HESS(c);
+    }
+  }
+  PCEXP_TRY(group_zero_halo<T>(c, o));
+  out.assign((size_t)c->K, 0.0);
+  return export_vec<T>(c, o, out.data(), 0);
+}
+
 template <class T>
 int group_arnoldi_part(pcexp_ctx* c, const std::vector<double>& u, const std::vector<double>& b, int m, KState* hk) {
   const DGData<T> d = dgdata<T>(c);
@@ -2236,6 +2268,39 @@ static int group_operator(pcexp_group* g, const double* U, const double* v, doub
 }
 
 int pcexp_group_residual(pcexp_group* g, const double* U, double* R) { return group_operator(g, U, nullptr, R); }
+
+static int group_adjoint(pcexp_group* g, int adj, const double* U, const double* v, const double* w, double* out) {
+  PCEXP_TRY(check_group(g));
+  if (!U || !w || !out || (adj == 2 && !v)) return PCEXP_ERR_INVALID_ARG;
+  if (adj == 2 && g->fp32) {
+    g_last_error = "the second-order adjoint is provided for the FP64 form";
+    return PCEXP_ERR_UNSUPPORTED;
+  }
+  if (adj == 2 && g->ctx[0]->rot) {
+    g_last_error = "the second-order adjoint is not provided in a rotating frame";
+    return PCEXP_ERR_UNSUPPORTED;
+  }
+  std::vector<std::vector<double>> res((size_t)g->n);
+  PCEXP_TRY(group_run(g, [&](int k) -> int {
+    pcexp_ctx* c = g->ctx[(size_t)k];
+    std::vector<double> uu, vv, wl;
+    gather_local(g, k, U, uu, false);
+    gather_local(g, k, w, wl, false);
+    if (v) gather_local(g, k, v, vv, false);
+    return c->fp32 ? group_adjoint_part<float>(c, adj, uu, v ? &vv : nullptr, wl, res[(size_t)k])
+                   : group_adjoint_part<double>(c, adj, uu, v ? &vv : nullptr, wl, res[(size_t)k]);
+  }));
+  for (int k = 0; k < g->n; ++k) scatter_owned(g, k, res[(size_t)k], out);
+  return PCEXP_OK;
+}
+
+int pcexp_group_vjp(pcexp_group* g, const double* U, const double* w, double* JTw) {
+  return group_adjoint(g, 1, U, nullptr, w, JTw);
+}
+
+int pcexp_group_jvp_state_adjoint(pcexp_group* g, const double* U, const double* v, const double* w, double* out) {
+  return group_adjoint(g, 2, U, v, w, out);
+}
 
 int pcexp_group_jvp(pcexp_group* g, const double* U, const double* v, double* Jv) {
   if (!v) return PCEXP_ERR_INVALID_ARG;

@@ -295,8 +295,6 @@ struct PartPtrs {
 cudaError_t launch_cgs_group_finalize(int mode, int j, KState* ks, double eta, cudaStream_t st);
 // out[i] = sum over q < nparts of slots.p[q][i] (doubles, i < n), in partition order; op 1: min
 cudaError_t launch_group_reduce(PartPtrs slots, int nparts, int n, double* out, int op, cudaStream_t st);
-// *dst = *src (one double)
-cudaError_t launch_copy_double(double* dst, const double* src, cudaStream_t st);
 // ghost rows of a partition's vector x (element rows n_local .. n_local + n_ghost): row g from
 // element src_elem[g] of partition src_part[g]'s copy srcs.p[src_part[g]] (nvb entries per row)
 template <class T>

@@ -666,11 +666,6 @@ cudaError_t launch_group_reduce(PartPtrs slots, int nparts, int n, double* out, 
   group_reduce_kernel<<<1, 64, 0, st>>>(slots, nparts, n, out, op);
   return cudaGetLastError();
 }
-__global__ void copy_double_kernel(double* dst, const double* src) { *dst = *src; }
-cudaError_t launch_copy_double(double* dst, const double* src, cudaStream_t st) {
-  copy_double_kernel<<<1, 1, 0, st>>>(dst, src);
-  return cudaGetLastError();
-}
 
 // ------------------------------------------------------------------ phi kernel
 // exp(A) by scaling and squaring with the [8/8] diagonal Pade approximant

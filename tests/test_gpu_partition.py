@@ -1,10 +1,11 @@
 """Partitioned runs on the GPU (pcexp_group_*): 2 and 3 partitions of one mesh, all on device 0,
 against one context on the whole mesh.
 
-* R(u) and J(u) v: each partition receives only its own rows; the halo rows come from the
-  exchange kernel reading the owners' buffers.  A face keeps the whole mesh's L element and
-  an element sums its faces in the same order, so the own rows equal the single context's
-  bit for bit.
+* R(u), J(u) v, and the adjoint passes J(u)^T w and (d(J(u) v)/du)^T w: each partition
+  receives only its own rows; the halo rows come from the exchange kernel reading the owners'
+  buffers.  A face keeps the whole mesh's L element and an element sums its faces in the same
+  order, so R and J v equal the single context's bit for bit, the adjoint passes to 1e-14
+  (their face terms are gathered per element in the submesh's face order).
 * Arnoldi: the Gram-Schmidt sums are split over the partitions (partition order), so H matches
   to round-off (1e-13 relative) and every partition holds the same H (checked by the call).
 * Steps (PCEXP at the global CFL dt, ETD2, EXP1): the same Krylov dimensions, dt to the last
@@ -60,6 +61,11 @@ def test_group_operator_and_arnoldi(capi, name, n):
     assert np.abs(Rg - R1).max() <= 1e-15 * np.abs(R1).max()
     J1, Jg = one.jvp(u, v), grp.jvp(u, v)
     assert np.abs(Jg - J1).max() <= 1e-15 * np.abs(J1).max()
+    w = W.random_coeffs(3, u.size)
+    A1, Ag = one.vjp(u, w), grp.vjp(u, w)
+    assert np.abs(Ag - A1).max() <= 1e-14 * np.abs(A1).max()
+    S1, Sg = one.jvp_state_adjoint(u, v, w), grp.jvp_state_adjoint(u, v, w)
+    assert np.abs(Sg - S1).max() <= 1e-14 * np.abs(S1).max()
     m = 10
     H1 = one.arnoldi(u, v, m, want_V=False)
     Hg, kg, bg = grp.arnoldi(u, v, m)
