@@ -427,6 +427,15 @@ int pcexp_group_vjp(pcexp_group* group, const double* U, const double* w, double
 int pcexp_group_jvp_state_adjoint(pcexp_group* group, const double* U, const double* v,
                                   const double* w, double* out);
 
+/* pcexp_step_backward on the whole mesh (host arrays; FP64, fixed frame): the forward step is
+ * recomputed partitioned from U, and its reverse runs partitioned too.  Every reduction of the
+ * reverse Gram-Schmidt is summed over the partitions (partition order) before its finishing
+ * step, the adjoint operator passes exchange their inputs' halo rows, and theta_bar (NULL:
+ * not returned) is the sum of the partitions' sums over their own elements.  Errors: those of
+ * pcexp_step_backward, TIMEOUT. */
+int pcexp_group_step_backward(pcexp_group* group, const double* U, double dt, int m,
+                              const double* ubar_next, double* ubar, double* theta_bar);
+
 /* Arnoldi process of pcexp_arnoldi (J at U, start vector b; host arrays) with the partitioned
  * Gram-Schmidt sums: H [(m+1) x m] row-major, *k, *beta as for pcexp_arnoldi.  The call
  * checks that every partition holds the same H (else CUDA). */

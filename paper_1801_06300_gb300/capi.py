@@ -127,6 +127,7 @@ SIGNATURES = {
     "pcexp_group_jvp": (C.c_int, [_P, _P, _P, _P]),
     "pcexp_group_arnoldi": (C.c_int, [_P, _P, _P, C.c_int, _D, C.POINTER(C.c_int), _D]),
     "pcexp_group_vjp": (C.c_int, [_P, _P, _P, _P]),
+    "pcexp_group_step_backward": (C.c_int, [_P, _P, C.c_double, C.c_int, _P, _P, _D]),
     "pcexp_group_jvp_state_adjoint": (C.c_int, [_P, _P, _P, _P, _P]),
     "pcexp_group_step": (C.c_int, [_P, C.c_int, C.c_int, C.c_double, C.c_int, C.POINTER(pcexp_step_info)]),
     "pcexp_group_march_steady": (C.c_int, [_P, C.c_int, C.c_double, C.c_double, C.c_int, C.c_int,
@@ -298,6 +299,15 @@ class Group:
         check(self.lib.pcexp_group_jvp(self.g, U.ctypes.data_as(_P), v.ctypes.data_as(_P), out.ctypes.data_as(_P)),
               "pcexp_group_jvp")
         return out
+
+    def step_backward(self, U, dt: float, m: int, ubar_next):
+        """(ubar_n, theta_bar = d/d(Mach, alpha in degrees)) of one PCEXP step at fixed dt."""
+        U, ub, out = self._host(U), self._host(ubar_next), np.empty(self.K)
+        th = np.zeros(2)
+        check(self.lib.pcexp_group_step_backward(self.g, U.ctypes.data_as(_P), dt, m, ub.ctypes.data_as(_P),
+                                                 out.ctypes.data_as(_P), th.ctypes.data_as(_D)),
+              "pcexp_group_step_backward")
+        return out, th
 
     def vjp(self, U, w):
         U, w, out = self._host(U), self._host(w), np.empty(self.K)

@@ -53,15 +53,50 @@ __device__ bool reduce_last(double (&acc)[NACC], int nred, double* partials, Adj
   __syncthreads();
   if (!last) return false;
   __threadfence();
+  // a partition of a partitioned run leaves its sums for the sum over the partitions, and the
+  // reduction is finished afterwards (launch_adj_finish)
+  double* dst = as->group ? as->gsum : as->dots;
   for (int c = wid; c < nred; c += 8) {
     double a = 0;
     for (unsigned b = lane; b < gridDim.x; b += 32) a += __ldcg(partials + (int64_t)c * gridDim.x + b);
     a = warp_sum(a);
-    if (lane == 0) as->dots[c] = a;
+    if (lane == 0) dst[c] = a;
   }
   __syncthreads();
   if (threadIdx.x == 0) as->counter = 0;
-  return true;
+  return !as->group;
+}
+
+// The finishing steps of the reductions, from the summed as->dots (called by the last block of
+// the reduction, or by the finishing kernel of a partitioned run)
+PCEXP_DEV void finish_alpha(int j, const KState* ks, AdjState* as) {
+  if (threadIdx.x == 0) as->alpha = ks->s[j + 1] * as->dots[0];
+}
+PCEXP_DEV void finish_upd(int mode, int j, const KState* ks, AdjState* as) {
+  for (int i = threadIdx.x; i <= j; i += blockDim.x) {
+    const double hb = as->Hbar[i * MMAX + j] - ks->s[i] * as->dots[i];
+    if (mode == 0) {
+      as->hb2[i] = hb;
+      as->cb2[i] = hb * ks->s[i];
+    } else {
+      as->hb1[i] = hb;
+      as->cb1[i] = hb * ks->s[i];
+    }
+  }
+}
+PCEXP_DEV void finish_ybar(int k, double fdt, const KState* ks, AdjState* as) {
+  if (threadIdx.x != 0) return;
+  double bb = 0;
+  for (int i = 0; i < k; ++i) {
+    const double yb = fdt * ks->beta * ks->s[i] * as->dots[i];
+    as->ybar[i] = yb;
+    bb += ks->y[i] * yb;
+  }
+  as->betabar = bb / ks->beta;
+  for (int i = 0; i < MMAX * (MMAX + 1); ++i) as->Hbar[i] = 0.0;
+}
+PCEXP_DEV void finish_b0(AdjState* as) {
+  if (threadIdx.x == 0) as->alpha = as->dots[0];
 }
 
 // w1 = z_{j+1} + sum_i h2_i s_i z_i,  w0 = w1 + sum_i h1_i s_i z_i
@@ -94,7 +129,7 @@ __global__ void __launch_bounds__(256) alpha_kernel(const double* __restrict__ Z
   double acc[1] = {0.0};
   for (int64_t r = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; r < Kp; r += (int64_t)gridDim.x * blockDim.x)
     acc[0] = fma(Z[(int64_t)(j + 1) * ldz + r], Vb[(int64_t)(j + 1) * ldz + r], acc[0]);
-  if (reduce_last<1>(acc, 1, partials, as) && threadIdx.x == 0) as->alpha = ks->s[j + 1] * as->dots[0];
+  if (reduce_last<1>(acc, 1, partials, as)) finish_alpha(j, ks, as);
 }
 
 // mode 0 (W2): wb = vbar_{j+1}/eta + (etabar - alpha/eta) s_{j+1} z_{j+1}   (zero when last)
@@ -140,18 +175,7 @@ __global__ void __launch_bounds__(256) upd_proj_kernel(int mode, const double* _
     for (int c = 0; c < NC; ++c)
       if (c < nc) acc[c] = fma(Z[(int64_t)c * ldz + r], x, acc[c]);
   }
-  if (reduce_last<NC>(acc, nc, partials, as)) {
-    for (int i = threadIdx.x; i < nc; i += blockDim.x) {
-      const double hb = as->Hbar[i * MMAX + j] - ks->s[i] * as->dots[i];
-      if (mode == 0) {
-        as->hb2[i] = hb;
-        as->cb2[i] = hb * ks->s[i];
-      } else {
-        as->hb1[i] = hb;
-        as->cb1[i] = hb * ks->s[i];
-      }
-    }
-  }
+  if (reduce_last<NC>(acc, nc, partials, as)) finish_upd(mode, j, ks, as);
 }
 
 // Vbar_i += w1 hb2_i - wb2 h2_i + w0 hb1_i - wb1 h1_i (i <= j);  wb0 = wb1 + sum_i cb1_i z_i
@@ -205,16 +229,7 @@ __global__ void __launch_bounds__(256) ybar_kernel(const double* __restrict__ Z,
     for (int c = 0; c < NC; ++c)
       if (c < k) acc[c] = fma(Z[(int64_t)c * ldz + r], x, acc[c]);
   }
-  if (reduce_last<NC>(acc, k, partials, as) && threadIdx.x == 0) {
-    double bb = 0;
-    for (int i = 0; i < k; ++i) {
-      const double yb = fdt * ks->beta * ks->s[i] * as->dots[i];
-      as->ybar[i] = yb;
-      bb += ks->y[i] * yb;
-    }
-    as->betabar = bb / ks->beta;
-    for (int i = 0; i < MMAX * (MMAX + 1); ++i) as->Hbar[i] = 0.0;
-  }
+  if (reduce_last<NC>(acc, k, partials, as)) finish_ybar(k, fdt, ks, as);
 }
 
 // Vbar_i = factor dt beta y_i ubar for i < k, zero for k <= i <= m
@@ -232,7 +247,16 @@ __global__ void __launch_bounds__(256) b0dot_kernel(const double* __restrict__ Z
   double acc[1] = {0.0};
   for (int64_t r = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; r < Kp; r += (int64_t)gridDim.x * blockDim.x)
     acc[0] = fma(Z[r], Vb[r], acc[0]);
-  if (reduce_last<1>(acc, 1, partials, as) && threadIdx.x == 0) as->alpha = as->dots[0];
+  if (reduce_last<1>(acc, 1, partials, as)) finish_b0(as);
+}
+
+__global__ void finish_kernel(int kind, int mode, int j, int k, double fdt, const KState* ks, AdjState* as) {
+  switch (kind) {
+    case ADJ_YBAR: finish_ybar(k, fdt, ks, as); break;
+    case ADJ_ALPHA: finish_alpha(j, ks, as); break;
+    case ADJ_B0: finish_b0(as); break;
+    default: finish_upd(mode, j, ks, as); break;
+  }
 }
 __global__ void bbar_kernel(const double* __restrict__ Z, const double* __restrict__ Vb, double* __restrict__ bbar,
                             int64_t Kp, const KState* ks, const AdjState* as) {
@@ -250,38 +274,67 @@ void launch_upd(int mode, const double* Z, int64_t ldz, const double* Vb, const 
 
 }  // namespace
 
-cudaError_t launch_adj_seed(const double* Z, int64_t ldz, double* Vb, const double* ubar, int64_t Kp, int k, int m,
-                            double fdt, const KState* ks, AdjState* as, double* partials, cudaStream_t st) {
+cudaError_t launch_adj_ybar(const double* Z, int64_t ldz, const double* ubar, int64_t Kp, int k, double fdt,
+                            const KState* ks, AdjState* as, double* partials, cudaStream_t st) {
   if (k < 1 || k > MMAX) return cudaErrorInvalidValue;
   if (k <= 8) ybar_kernel<8><<<AB, 256, 0, st>>>(Z, ldz, ubar, Kp, k, fdt, ks, as, partials);
   else if (k <= 16) ybar_kernel<16><<<AB, 256, 0, st>>>(Z, ldz, ubar, Kp, k, fdt, ks, as, partials);
   else ybar_kernel<32><<<AB, 256, 0, st>>>(Z, ldz, ubar, Kp, k, fdt, ks, as, partials);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_adj_vbar_init(double* Vb, int64_t ldz, const double* ubar, int64_t Kp, int k, int m, double fdt,
+                                 const KState* ks, cudaStream_t st) {
   vbar_init_kernel<<<AB, 256, 0, st>>>(Vb, ldz, ubar, Kp, k, m, fdt, ks);
   return cudaGetLastError();
 }
 
-cudaError_t launch_adj_column(const double* Z, int64_t ldz, double* Vb, int64_t Kp, int j, int last_col,
-                              const KState* ks, AdjState* as, double* partials, double* w1, double* w0, double* wb2,
-                              double* wb1, double* wb0, cudaStream_t st) {
+cudaError_t launch_adj_recompute(const double* Z, int64_t ldz, int64_t Kp, int j, const KState* ks, double* w1,
+                                 double* w0, cudaStream_t st) {
+  if (j + 1 > MMAX) return cudaErrorInvalidValue;
+  recompute_kernel<<<AB, 256, 0, st>>>(Z, ldz, Kp, j, ks, w1, w0);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_adj_alpha(const double* Z, int64_t ldz, const double* Vb, int64_t Kp, int j, const KState* ks,
+                             AdjState* as, double* partials, cudaStream_t st) {
+  alpha_kernel<<<AB, 256, 0, st>>>(Z, ldz, Vb, Kp, j, ks, as, partials);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_adj_upd(int mode, const double* Z, int64_t ldz, const double* Vb, const double* win, double* wb,
+                           int64_t Kp, int j, int last_col, const KState* ks, AdjState* as, double* partials,
+                           cudaStream_t st) {
   const int nc = j + 1;
   if (nc > MMAX) return cudaErrorInvalidValue;
-  recompute_kernel<<<AB, 256, 0, st>>>(Z, ldz, Kp, j, ks, w1, w0);
-  if (!last_col) alpha_kernel<<<AB, 256, 0, st>>>(Z, ldz, Vb, Kp, j, ks, as, partials);
-  for (int mode = 0; mode < 2; ++mode) {
-    double* out = mode == 0 ? wb2 : wb1;
-    const double* win = mode == 0 ? nullptr : wb2;
-    if (nc <= 8) launch_upd<8>(mode, Z, ldz, Vb, win, out, Kp, j, last_col, ks, as, partials, st);
-    else if (nc <= 16) launch_upd<16>(mode, Z, ldz, Vb, win, out, Kp, j, last_col, ks, as, partials, st);
-    else launch_upd<32>(mode, Z, ldz, Vb, win, out, Kp, j, last_col, ks, as, partials, st);
-  }
+  if (nc <= 8) launch_upd<8>(mode, Z, ldz, Vb, win, wb, Kp, j, last_col, ks, as, partials, st);
+  else if (nc <= 16) launch_upd<16>(mode, Z, ldz, Vb, win, wb, Kp, j, last_col, ks, as, partials, st);
+  else launch_upd<32>(mode, Z, ldz, Vb, win, wb, Kp, j, last_col, ks, as, partials, st);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_adj_rank(const double* Z, int64_t ldz, double* Vb, const double* w1, const double* w0,
+                            const double* wb2, const double* wb1, double* wb0, int64_t Kp, int j, const KState* ks,
+                            const AdjState* as, cudaStream_t st) {
   rank_kernel<<<AB, 256, 0, st>>>(Z, ldz, Vb, w1, w0, wb2, wb1, wb0, Kp, j, ks, as);
   return cudaGetLastError();
 }
 
-cudaError_t launch_adj_bbar(const double* Z, const double* Vb, double* bbar, int64_t Kp, const KState* ks,
-                            AdjState* as, double* partials, cudaStream_t st) {
+cudaError_t launch_adj_b0dot(const double* Z, const double* Vb, int64_t Kp, AdjState* as, double* partials,
+                             cudaStream_t st) {
   b0dot_kernel<<<AB, 256, 0, st>>>(Z, Vb, Kp, as, partials);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_adj_bbar_from(const double* Z, const double* Vb, double* bbar, int64_t Kp, const KState* ks,
+                                 const AdjState* as, cudaStream_t st) {
   bbar_kernel<<<AB, 256, 0, st>>>(Z, Vb, bbar, Kp, ks, as);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_adj_finish(int kind, int mode, int j, int k, double fdt, const KState* ks, AdjState* as,
+                              cudaStream_t st) {
+  finish_kernel<<<1, 256, 0, st>>>(kind, mode, j, k, fdt, ks, as);
   return cudaGetLastError();
 }
 

@@ -7,6 +7,7 @@
 // non-NULL info, the steady march (one 8-byte residual read per iteration)
 // and host-pointer transfers synchronise.
 #include <algorithm>
+#include <array>
 #include <cfloat>
 #include <chrono>
 #include <cmath>
@@ -1222,6 +1223,11 @@ int alloc_backward(pcexp_ctx* c) {
   PCEXP_TRY(dalloc(c, &c->b_theta, 2));
   PCEXP_TRY(dalloc(c, &c->b_ks1, 1));
   PCEXP_TRY(dalloc(c, &c->b_as, 1));
+  if (c->grp) {  // partition of a group: the reverse reductions are summed over the partitions
+    const int one = 1;
+    PCEXP_CK(cudaMemcpyAsync(reinterpret_cast<char*>(c->b_as) + offsetof(AdjState, group), &one, sizeof(int),
+                             cudaMemcpyHostToDevice, c->st));
+  }
   PCEXP_CK(cudaStreamSynchronize(c->st));
   return PCEXP_OK;
 }
@@ -1247,24 +1253,83 @@ int param_adjoint(pcexp_ctx* c, const DGData<double>& d, int order, const double
   return PCEXP_OK;
 }
 
+// A reduction of the reverse Krylov stage in a partitioned run: the partitions' sums (left in
+// b_as->gsum) summed in partition order into b_as->dots, then the reduction's finishing step.
+int adj_round(pcexp_ctx* c, int kind, int mode, int j, int k, double fdt, const KState* ks) {
+  if (!c->grp) return PCEXP_OK;
+  AdjState* as = c->b_as;
+  return group_round(c, dev_field(as, offsetof(AdjState, gsum)), [&](const PartPtrs& pp) -> int {
+    PCEXP_CK(launch_group_reduce(pp, c->grp->n, MMAX + 2, dev_field(as, offsetof(AdjState, dots)), 0, c->st));
+    PCEXP_CK(launch_adj_finish(kind, mode, j, k, fdt, ks, as, c->st));
+    return PCEXP_OK;
+  });
+}
+
+// Seeding of a stage's reverse from the adjoint ubar of u_out = u_base + fdt beta V_k y
+int adj_seed(pcexp_ctx* c, const double* Z, const double* ubar, int k, int m, double fdt, const KState* ks) {
+  PCEXP_CK(launch_adj_ybar(Z, c->Kp, ubar, c->Kp, k, fdt, ks, c->b_as, c->partials, c->st));
+  PCEXP_TRY(adj_round(c, ADJ_YBAR, 0, 0, k, fdt, ks));
+  PCEXP_CK(launch_adj_vbar_init(c->b_Vb, c->Kp, ubar, c->Kp, k, m, fdt, ks, c->st));
+  return PCEXP_OK;
+}
+
+// Reverse of Gram-Schmidt column j (its w0 bar ends in b_wb0)
+int adj_column(pcexp_ctx* c, const double* Z, int j, bool last_col, const KState* ks) {
+  const int64_t Kp = c->Kp;
+  PCEXP_CK(launch_adj_recompute(Z, Kp, Kp, j, ks, c->b_w1, c->b_w0, c->st));
+  if (!last_col) {
+    PCEXP_CK(launch_adj_alpha(Z, Kp, c->b_Vb, Kp, j, ks, c->b_as, c->partials, c->st));
+    PCEXP_TRY(adj_round(c, ADJ_ALPHA, 0, j, 0, 0.0, ks));
+  }
+  for (int mode = 0; mode < 2; ++mode) {
+    PCEXP_CK(launch_adj_upd(mode, Z, Kp, c->b_Vb, mode == 0 ? nullptr : c->b_wb2, mode == 0 ? c->b_wb2 : c->b_wb1,
+                            Kp, j, last_col ? 1 : 0, ks, c->b_as, c->partials, c->st));
+    PCEXP_TRY(adj_round(c, mode == 0 ? ADJ_UPD0 : ADJ_UPD1, mode, j, 0, 0.0, ks));
+  }
+  PCEXP_CK(launch_adj_rank(Z, Kp, c->b_Vb, c->b_w1, c->b_w0, c->b_wb2, c->b_wb1, c->b_wb0, Kp, j, ks, c->b_as,
+                           c->st));
+  return PCEXP_OK;
+}
+
+// out = J_n^T w (w's halo rows from the owners in a partitioned run; own rows of out kept)
+int adj_jt(pcexp_ctx* c, const DGData<double>& d, double* w, double* out) {
+  PCEXP_TRY(group_exchange<double>(c, w));
+  PCEXP_CK(launch_jac_adjoint<double>(d, lindata<double>(c), w, out, reinterpret_cast<double*>(c->GT), nullptr, 1.0,
+                                      c->st));
+  return group_zero_halo<double>(c, out);
+}
+
+// out = (d(J(u) v)/du)^T w at u = b_un (v's and w's halo rows from the owners; v's restored to
+// zero when it is a Krylov vector)
+int adj_hess(pcexp_ctx* c, const DGData<double>& d, double* v, bool v_krylov, double* w, double* out) {
+  PCEXP_TRY(group_exchange<double>(c, v));
+  PCEXP_TRY(group_exchange<double>(c, w));
+  PCEXP_CK(launch_jvp_state_adjoint<double>(d, c->b_un, v, w, out, reinterpret_cast<double*>(c->GT), nullptr, 1.0,
+                                            c->st));
+  if (v_krylov) PCEXP_TRY(group_zero_halo<double>(c, v));
+  return group_zero_halo<double>(c, out);
+}
+
 // Reverse of one Arnoldi + phi + update stage; Vb holds the seeded basis adjoints.
 // Accumulates the second-order terms into b_ubn and leaves the start-vector adjoint in b_bb.
-int reverse_krylov(pcexp_ctx* c, const DGData<double>& d, const double* Z, const KState* ks, int k) {
+// In a partitioned run every vector here keeps zero halo rows except while an adjoint operator
+// pass reads them (the parameter adjoint then counts each boundary face in its own partition).
+int reverse_krylov(pcexp_ctx* c, const DGData<double>& d, double* Z, const KState* ks, int k) {
   const int64_t Kp = c->Kp;
-  double* G = reinterpret_cast<double*>(c->GT);
   for (int j = k - 1; j >= 0; --j) {
-    PCEXP_CK(launch_adj_column(Z, Kp, c->b_Vb, Kp, j, j == k - 1, ks, c->b_as, c->partials, c->b_w1, c->b_w0,
-                               c->b_wb2, c->b_wb1, c->b_wb0, c->st));
+    PCEXP_TRY(adj_column(c, Z, j, j == k - 1, ks));
     // w0 = J_n v_j: vbar_j += J_n^T w0bar;  ubar_n += (d(J(u) v_j)/du)^T w0bar, v_j = s_j z_j
-    PCEXP_CK(launch_jac_adjoint<double>(d, lindata<double>(c), c->b_wb0, c->b_t1, G, nullptr, 1.0, c->st));
+    PCEXP_TRY(adj_jt(c, d, c->b_wb0, c->b_t1));
     PCEXP_CK(launch_axpy(c->b_Vb + (int64_t)j * Kp, c->b_t1, nullptr, 1.0, Kp, c->st));
-    PCEXP_CK(launch_jvp_state_adjoint<double>(d, c->b_un, Z + (int64_t)j * Kp, c->b_wb0, c->b_t2, G, nullptr, 1.0,
-                                              c->st));
+    PCEXP_TRY(adj_hess(c, d, Z + (int64_t)j * Kp, true, c->b_wb0, c->b_t2));
     PCEXP_CK(launch_axpy(c->b_ubn, c->b_t2, &ks->s[j], 1.0, Kp, c->st));
+    PCEXP_TRY(group_zero_halo<double>(c, c->b_wb0));
     // theta_bar += s_j (d(J(u_n; theta) z_j)/dtheta)^T w0bar
     PCEXP_TRY(param_adjoint(c, d, 2, c->b_un, Z + (int64_t)j * Kp, c->b_wb0, 1.0, &ks->s[j]));
   }
-  PCEXP_CK(launch_adj_bbar(Z, c->b_Vb, c->b_bb, Kp, ks, c->b_as, c->partials, c->st));
+  PCEXP_CK(launch_adj_b0dot(Z, c->b_Vb, Kp, c->b_as, c->partials, c->st));
+  PCEXP_TRY(adj_round(c, ADJ_B0, 0, 0, 0, 0.0, ks));
+  PCEXP_CK(launch_adj_bbar_from(Z, c->b_Vb, c->b_bb, Kp, ks, c->b_as, c->st));
   return PCEXP_OK;
 }
 
@@ -1312,23 +1377,23 @@ int step_backward_impl(pcexp_ctx* c, const double* U, double dt, int m, const do
   PCEXP_CK(cudaMemsetAsync(c->b_rb, 0, vbytes, c->st));
   PCEXP_CK(cudaMemsetAsync(c->b_db, 0, vbytes, c->st));
   PCEXP_CK(cudaMemcpyAsync(c->b_ubs, c->b_gin, vbytes, cudaMemcpyDeviceToDevice, c->st));
-  double* G = reinterpret_cast<double*>(c->GT);
   if (k2 > 0) {
     // u_{n+1} = u_* + dt/2 beta_2 V_2 y_2
-    PCEXP_CK(launch_adj_seed(V, Kp, c->b_Vb, c->b_gin, Kp, k2, m, 0.5 * dt, c->ks, c->b_as, c->partials, c->st));
+    PCEXP_TRY(adj_seed(c, V, c->b_gin, k2, m, 0.5 * dt, c->ks));
     PCEXP_CK(launch_phi_adjoint(c->ks->H, k2, MMAX, dt, c->b_as->ybar, c->b_as->Hbar, &c->b_as->err, c->st));
     PCEXP_TRY(reverse_krylov(c, d, V, c->ks, k2));
     // N_* - N_n = R(u_*) - R_n - J_n delta, with bbar_2 = b_bb
-    PCEXP_CK(launch_jac_adjoint<double>(d, lindata<double>(c), c->b_bb, c->b_t1, G, nullptr, 1.0, c->st));
+    PCEXP_TRY(adj_jt(c, d, c->b_bb, c->b_t1));
     PCEXP_CK(launch_axpy(c->b_db, c->b_t1, nullptr, -1.0, Kp, c->st));
-    PCEXP_CK(launch_jvp_state_adjoint<double>(d, c->b_un, c->b_dl, c->b_bb, c->b_t2, G, nullptr, 1.0, c->st));
+    PCEXP_TRY(adj_hess(c, d, c->b_dl, false, c->b_bb, c->b_t2));
     PCEXP_CK(launch_axpy(c->b_ubn, c->b_t2, nullptr, -1.0, Kp, c->st));
+    PCEXP_TRY(group_zero_halo<double>(c, c->b_bb));
     PCEXP_CK(launch_axpy(c->b_rb, c->b_bb, nullptr, -1.0, Kp, c->st));
     // theta_bar -= (d(J(u_n; theta) delta)/dtheta)^T bbar_2;  += (dR(u_*; theta)/dtheta)^T bbar_2
     PCEXP_TRY(param_adjoint(c, d, 2, c->b_un, c->b_dl, c->b_bb, -1.0, nullptr));
     PCEXP_TRY(param_adjoint(c, d, 1, c->b_us, nullptr, c->b_bb, 1.0, nullptr));
     PCEXP_TRY(linearize<double>(c, d, c->b_us));
-    PCEXP_CK(launch_jac_adjoint<double>(d, lindata<double>(c), c->b_bb, c->b_t1, G, nullptr, 1.0, c->st));
+    PCEXP_TRY(adj_jt(c, d, c->b_bb, c->b_t1));
     PCEXP_CK(launch_axpy(c->b_ubs, c->b_t1, nullptr, 1.0, Kp, c->st));
     PCEXP_TRY(linearize<double>(c, d, c->b_un));
   }
@@ -1337,14 +1402,15 @@ int step_backward_impl(pcexp_ctx* c, const double* U, double dt, int m, const do
   PCEXP_CK(launch_axpy(c->b_db, c->b_ubs, nullptr, 1.0, Kp, c->st));
   if (k1 > 0) {
     // delta = dt beta_1 V_1 y_1
-    PCEXP_CK(launch_adj_seed(c->b_V1, Kp, c->b_Vb, c->b_db, Kp, k1, m, dt, c->b_ks1, c->b_as, c->partials, c->st));
+    PCEXP_TRY(adj_seed(c, c->b_V1, c->b_db, k1, m, dt, c->b_ks1));
     PCEXP_CK(launch_phi_adjoint(c->b_ks1->H, k1, MMAX, dt, c->b_as->ybar, c->b_as->Hbar, &c->b_as->err, c->st));
     PCEXP_TRY(reverse_krylov(c, d, c->b_V1, c->b_ks1, k1));
     PCEXP_CK(launch_axpy(c->b_rb, c->b_bb, nullptr, 1.0, Kp, c->st));
   }
   // R_n = R(u_n)
-  PCEXP_CK(launch_jac_adjoint<double>(d, lindata<double>(c), c->b_rb, c->b_t1, G, nullptr, 1.0, c->st));
+  PCEXP_TRY(adj_jt(c, d, c->b_rb, c->b_t1));
   PCEXP_CK(launch_axpy(c->b_ubn, c->b_t1, nullptr, 1.0, Kp, c->st));
+  PCEXP_TRY(group_zero_halo<double>(c, c->b_rb));
   PCEXP_TRY(param_adjoint(c, d, 1, c->b_un, nullptr, c->b_rb, 1.0, nullptr));
   c->prof = prof;
   PCEXP_TRY(export_vec<double>(c, c->b_ubn, ubar, on_device));
@@ -2335,6 +2401,40 @@ int pcexp_group_arnoldi(pcexp_group* g, const double* U, const double* b, int m,
   if (H)
     for (int i = 0; i <= m; ++i)
       for (int j = 0; j < m; ++j) H[i * m + j] = (i <= kk && j < kk) ? hk[0].H[i * MMAX + j] : 0.0;
+  return PCEXP_OK;
+}
+
+int pcexp_group_step_backward(pcexp_group* g, const double* U, double dt, int m, const double* ubar_next,
+                              double* ubar, double* theta_bar) {
+  PCEXP_TRY(check_group(g));
+  if (!U || !ubar_next || !ubar || m < 1 || m > g->ctx[0]->m_max || !(dt > 0) || !std::isfinite(dt))
+    return PCEXP_ERR_INVALID_ARG;
+  if (g->fp32) {
+    g_last_error = "the reverse step is provided for the FP64 form";
+    return PCEXP_ERR_UNSUPPORTED;
+  }
+  if (g->ctx[0]->rot) {
+    g_last_error = "the reverse step is not provided in a rotating frame";
+    return PCEXP_ERR_UNSUPPORTED;
+  }
+  std::vector<std::vector<double>> res((size_t)g->n);
+  std::vector<std::array<double, 2>> th((size_t)g->n, std::array<double, 2>{0.0, 0.0});
+  PCEXP_TRY(group_run(g, [&](int k) -> int {
+    pcexp_ctx* c = g->ctx[(size_t)k];
+    std::vector<double> u, ub;
+    gather_local(g, k, U, u, false);
+    gather_local(g, k, ubar_next, ub, false);
+    res[(size_t)k].assign((size_t)c->K, 0.0);
+    return step_backward_impl(c, u.data(), dt, m, ub.data(), res[(size_t)k].data(), th[(size_t)k].data(), 0);
+  }));
+  for (int k = 0; k < g->n; ++k) scatter_owned(g, k, res[(size_t)k], ubar);
+  if (theta_bar) {  // each partition's sums cover the boundary faces of its own elements
+    theta_bar[0] = theta_bar[1] = 0.0;
+    for (int k = 0; k < g->n; ++k) {
+      theta_bar[0] += th[(size_t)k][0];
+      theta_bar[1] += th[(size_t)k][1];
+    }
+  }
   return PCEXP_OK;
 }
 

@@ -41,8 +41,10 @@ struct AdjState {
   double ybar[MMAX];
   double Hbar[(MMAX + 1) * MMAX];  // row-major, leading dimension MMAX
   double alpha, betabar;
+  double gsum[MMAX + 2];  // partitioned runs: this partition's sums of the last reduction
   unsigned counter;
   int err;
+  int group;              // partitioned run: reductions leave their sums in gsum, unfinished
 };
 
 // Device-resident per-step scalars.
@@ -307,13 +309,31 @@ cudaError_t launch_zero_range(T* x, int64_t from, int64_t to, cudaStream_t st);
 cudaError_t launch_cap_cfl(StepState* ss, double cap, cudaStream_t st);
 cudaError_t launch_reset_kstate(KState* ks, cudaStream_t st);
 // ---- reverse Krylov stage (adjoint.cu, FP64)
-cudaError_t launch_adj_seed(const double* Z, int64_t ldz, double* Vb, const double* ubar, int64_t Kp, int k, int m,
-                            double fdt, const KState* ks, AdjState* as, double* partials, cudaStream_t st);
-cudaError_t launch_adj_column(const double* Z, int64_t ldz, double* Vb, int64_t Kp, int j, int last_col,
-                              const KState* ks, AdjState* as, double* partials, double* w1, double* w0, double* wb2,
-                              double* wb1, double* wb0, cudaStream_t st);
-cudaError_t launch_adj_bbar(const double* Z, const double* Vb, double* bbar, int64_t Kp, const KState* ks,
-                            AdjState* as, double* partials, cudaStream_t st);
+// Reverse of the Krylov stage, step by step.  Each reduction (ybar, alpha, upd, b0dot) leaves
+// its sums in as->dots and finishes in its last block; in a partitioned run (as->group) it
+// leaves them in as->gsum instead, and launch_adj_finish(kind, ...) finishes from as->dots once
+// they are summed over the partitions.
+enum AdjReduction { ADJ_YBAR = 0, ADJ_ALPHA = 1, ADJ_UPD0 = 2, ADJ_UPD1 = 3, ADJ_B0 = 4 };
+cudaError_t launch_adj_ybar(const double* Z, int64_t ldz, const double* ubar, int64_t Kp, int k, double fdt,
+                            const KState* ks, AdjState* as, double* partials, cudaStream_t st);
+cudaError_t launch_adj_vbar_init(double* Vb, int64_t ldz, const double* ubar, int64_t Kp, int k, int m, double fdt,
+                                 const KState* ks, cudaStream_t st);
+cudaError_t launch_adj_recompute(const double* Z, int64_t ldz, int64_t Kp, int j, const KState* ks, double* w1,
+                                 double* w0, cudaStream_t st);
+cudaError_t launch_adj_alpha(const double* Z, int64_t ldz, const double* Vb, int64_t Kp, int j, const KState* ks,
+                             AdjState* as, double* partials, cudaStream_t st);
+cudaError_t launch_adj_upd(int mode, const double* Z, int64_t ldz, const double* Vb, const double* win, double* wb,
+                           int64_t Kp, int j, int last_col, const KState* ks, AdjState* as, double* partials,
+                           cudaStream_t st);
+cudaError_t launch_adj_rank(const double* Z, int64_t ldz, double* Vb, const double* w1, const double* w0,
+                            const double* wb2, const double* wb1, double* wb0, int64_t Kp, int j, const KState* ks,
+                            const AdjState* as, cudaStream_t st);
+cudaError_t launch_adj_b0dot(const double* Z, const double* Vb, int64_t Kp, AdjState* as, double* partials,
+                             cudaStream_t st);
+cudaError_t launch_adj_bbar_from(const double* Z, const double* Vb, double* bbar, int64_t Kp, const KState* ks,
+                                 const AdjState* as, cudaStream_t st);
+cudaError_t launch_adj_finish(int kind, int mode, int j, int k, double fdt, const KState* ks, AdjState* as,
+                              cudaStream_t st);
 cudaError_t launch_axpy(double* y, const double* x, const double* a_dev, double a_host, int64_t n, cudaStream_t st);
 cudaError_t launch_set_dt(StepState* ss, double dt, cudaStream_t st);
 cudaError_t launch_set_cfl(StepState* ss, double cfl, cudaStream_t st);

@@ -181,3 +181,29 @@ def test_group_local_steps_and_steady_march(capi, n, tol):
         assert abs(mg["res_last"] - m1["res_last"]) <= 1e-6 * m1["res_last"]
     one.close()
     grp.close()
+
+
+@pytest.mark.parametrize("name,n", [("bump2d", 2), ("bump2d", 3), ("cube3d", 2)])
+def test_group_step_backward_matches_one_context(capi, name, n):
+    """The reverse step partitioned (the forward step recomputed partitioned, every reduction of
+    the reverse Gram-Schmidt summed over the partitions before its finishing step, the adjoint
+    operator passes with exchanged inputs, theta_bar summed over the partitions' own elements)
+    against one context: ubar_n within 1e-11 and the free-stream parameter adjoint within
+    1e-11 relative (far-field faces in the channel; none in the periodic cube)."""
+    mesh, p, free = CASES[name]()
+    part = capi.partition(mesh, n)
+    one = capi.Context(mesh, p, free, capi.PCEXP_FP64, m_max=8)
+    grp = capi.Group(mesh, part, p, free, capi.PCEXP_FP64, m_max=8)
+    u = _state(one, 7)
+    ub = W.random_coeffs(8, u.size)
+    dt = 0.002
+    a, ta = one.step_backward(u, dt, 8, ub, with_theta=True)
+    b, tb = grp.step_backward(u, dt, 8, ub)
+    assert rel(b, a) <= 1e-11
+    if name == "bump2d":
+        assert np.all(np.abs(ta) > 0)
+        assert np.abs(tb - ta).max() <= 1e-11 * np.abs(ta).max()
+    else:
+        assert np.abs(tb).max() <= 1e-14 and np.abs(ta).max() <= 1e-14
+    one.close()
+    grp.close()
