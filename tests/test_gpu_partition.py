@@ -207,3 +207,24 @@ def test_group_step_backward_matches_one_context(capi, name, n):
         assert np.abs(tb).max() <= 1e-14 and np.abs(ta).max() <= 1e-14
     one.close()
     grp.close()
+
+
+def test_group_of_one_partition_is_the_single_context(capi):
+    """A group of one partition (no halo, no exchange partner) reproduces the single context
+    exactly: the same mesh order, the same kernels, sums over one partition."""
+    mesh, p, free = CASES["vortex2d"]()
+    part = np.zeros(mesh.n_elem, np.int32)
+    one = capi.Context(mesh, p, free, capi.PCEXP_FP64, m_max=8)
+    grp = capi.Group(mesh, part, p, free, capi.PCEXP_FP64, m_max=8)
+    assert grp.sizes(0) == (mesh.n_elem, 0)
+    u = _state(one, 9)
+    one.set_state(u)
+    grp.set_state(u)
+    assert np.array_equal(grp.residual(u), one.residual(u))
+    for _ in range(2):
+        a = one.step(capi.PCEXP_SCHEME_PCEXP, capi.PCEXP_DT_GLOBAL_CFL, 2.0, 8)
+        b = grp.step(capi.PCEXP_SCHEME_PCEXP, capi.PCEXP_DT_GLOBAL_CFL, 2.0, 8)
+        assert a["k"] == b["k"] and a["dt"] == b["dt"]
+    assert rel(grp.get_state(), one.get_state()) <= 1e-14
+    one.close()
+    grp.close()
