@@ -19,7 +19,7 @@ from . import adscalar as ad
 from . import euler
 from .basis import PaperBasis, n_basis
 from .cases import freestream_velocity
-from .quadrature import gauss_legendre01, tetra_rule, triangle_rule
+from .quadrature import face_rule, volume_rule
 
 BC_SLIP_WALL = 1
 BC_FARFIELD = 2
@@ -91,7 +91,7 @@ class DGOracle:
         verts = X[mesh.elems]  # [E, dim+1, dim]
         self.verts = verts
         # volume quadrature on each physical simplex
-        rp, rw = triangle_rule(p + 1) if dim == 2 else tetra_rule(p + 1)
+        rp, rw = volume_rule(dim, p)
         Aff = verts[:, 1:, :] - verts[:, 0:1, :]  # rows: v_k - v_0 (exact in floating point)
         if dim == 2:
             det = Aff[:, 0, 0] * Aff[:, 1, 1] - Aff[:, 0, 1] * Aff[:, 1, 0]
@@ -106,14 +106,9 @@ class DGOracle:
         self.basis = PaperBasis(verts, p, self.rq, self.wq)
         self.psi_q = self.basis.eval(self.rq)  # [E, nq, N]
         self.gpsi_wq = self.basis.grad(self.rq) * self.wq[:, :, None, None]  # [E, nq, N, dim]
-        # face rule: Gauss-Legendre on [0, 1] (weights sum 1) or the collapsed triangle
-        # rule (weights sum 1/2); a face point has barycentrics lam over the face vertices
-        if dim == 2:
-            s, ws = gauss_legendre01(p + 1)
-            self.face_bary = np.stack([1.0 - s, s], axis=1)
-        else:
-            st, ws = triangle_rule(p + 1)
-            self.face_bary = np.stack([1.0 - st[:, 0] - st[:, 1], st[:, 0], st[:, 1]], axis=1)
+        # face rule: Gauss-Legendre on [0, 1] (weights sum 1) or a triangle rule (weights
+        # sum 1/2); a face point has barycentrics lam over the face vertices
+        self.face_bary, ws = face_rule(dim, p)
         self.ws = ws
         interior, boundary = build_faces(mesh)
         self.perimeter = np.zeros(self.E)  # |dE|
