@@ -134,6 +134,8 @@ def shape(dim, p):
     """(nb, nq, nfq, nv, nf): basis size, volume and face points, variables, faces per element."""
     if dim == 2:
         return (p + 1) * (p + 2) // 2, (p + 1) ** 2, p + 1, 4, 3
+    if p == 2:  # the symmetric rules of tetrahedra at p = 2
+        return 10, 14, 7, 5, 4
     return (p + 1) * (p + 2) * (p + 3) // 6, (p + 1) ** 3, (p + 1) ** 2, 5, 4
 
 
@@ -199,8 +201,8 @@ def algorithmic_flops(kind, K, E, F, dim, p, m, T=8):
 # workload, keyed (workload, element bytes, kernel class); an entry is dropped when its
 # kernel changes.  The summaries under profiles/ give the commands.
 NCU_TRAFFIC = {
-    ("vortex3d", 4, "jvp_elem"): (663010475, "profiles/traffic_vortex3d_48_p2_m30_fp32.md"),
-    ("vortex3d", 4, "jvp_face"): (2769932160, "profiles/traffic_vortex3d_48_p2_m30_fp32.md"),
+    ("vortex3d", 4, "jvp_elem"): (608250112, "profiles/traffic_vortex3d_48_p2_m30_fp32.md"),
+    ("vortex3d", 4, "jvp_face"): (2185546880, "profiles/traffic_vortex3d_48_p2_m30_fp32.md"),
 }
 
 

@@ -87,7 +87,10 @@ extern "C" {
  * faces (edges in 2D, triangles in 3D).  Faces are matched on master vertices;
  * a face with no partner and no tag, or shared by more than two elements, is a
  * PCEXP_ERR_MESH.  A face's quadrature points are those of its L element (the
- * lower element index) in that element's local face-vertex order. */
+ * lower element index) in that element's local face-vertex order.  Quadrature (the
+ * paper leaves it open): Gauss rules with p + 1 points per direction (collapsed on
+ * triangles and tetrahedra), except tetrahedra at p = 2, which take fully symmetric
+ * rules of the same degree 5 with 14 volume and 7 face points. */
 typedef struct pcexp_mesh {
   int32_t dim;
   int64_t n_vert;
@@ -337,7 +340,7 @@ int pcexp_profile_read(pcexp_ctx* ctx, int kernel_class, int64_t* launches, doub
  * allocating routine.  Its face-flux scratch is a fixed 8 MiB device array inside the
  * library (held by every GPU that loads the library until the process exits): meshes with
  * faces x face quadrature points x (dim + 2) > 2^20 doubles get PCEXP_ERR_INVALID_ARG
- * (face points: p + 1 on edges, (p + 1)^2 on triangular faces).  The first call on a
+ * (face points: p + 1 on edges, (p + 1)^2 on triangular faces, 7 at p = 2).  The first call on a
  * device makes that device current and looks up the array's device address; make that
  * first call before any stream capture.  All calls share the array, which keeps the last
  * call's face fluxes: calls whose kernels overlap on the GPU race; calls on one stream are

@@ -33,8 +33,10 @@ namespace pcexp {
 template <int D, int P> struct Ord {
   static constexpr int NV = D + 2;
   static constexpr int NB = D == 2 ? (P + 1) * (P + 2) / 2 : (P + 1) * (P + 2) * (P + 3) / 6;
-  static constexpr int NQ = D == 2 ? (P + 1) * (P + 1) : (P + 1) * (P + 1) * (P + 1);
-  static constexpr int NFQ = D == 2 ? P + 1 : (P + 1) * (P + 1);
+  // volume and face points: collapsed rules with p + 1 points per direction, except
+  // tetrahedra at p = 2 (the symmetric 14-point volume and 7-point face rules)
+  static constexpr int NQ = D == 2 ? (P + 1) * (P + 1) : P == 2 ? 14 : (P + 1) * (P + 1) * (P + 1);
+  static constexpr int NFQ = D == 2 ? P + 1 : P == 2 ? 7 : (P + 1) * (P + 1);
   static constexpr int NF = D + 1;                  // faces per element
   static constexpr int NPERM = D == 2 ? 2 : 6;      // vertex permutations of a face
   static constexpr int GEO = D == 2 ? 8 : 12;       // geometry record: A^-1 (D x D), sqrt|det|, h, 1/sqrt|det|
@@ -42,7 +44,9 @@ template <int D, int P> struct Ord {
   static constexpr int HE = D * D + 1;   // h
   static constexpr int ISD = D * D + 2;  // 1 / sqrt|det A| (multiplications instead of FP64 divisions)
   static constexpr int NVB = NV * NB;
-  static constexpr int ET = (256 / NQ) > 128 ? 128 : (256 / NQ);  // elements per block
+  // elements per block (tetrahedra: at most 16, which keeps the FP64 tile within 48 KB)
+  static constexpr int ET0 = (256 / NQ) > 128 ? 128 : (256 / NQ);
+  static constexpr int ET = (D == 3 && ET0 > 16) ? 16 : ET0;
   static constexpr int NJV = D * NV * NV;           // volume point-Jacobian entries
   static constexpr int NJF = 2 * NV * NV;           // face point-Jacobian entries
   static constexpr int NBF = NF * NPERM * NFQ * NB;  // trace-table entries
@@ -431,13 +435,14 @@ template <int D, int P> struct TanPipe {
   static constexpr int GROW = GREC | 1;
   static constexpr int PST = O::NVB | 1;
   static constexpr int SU = 32 * UROW, SG = 32 * GROW, SGEO = 32 * O::GEO, SEF = 32 * O::NF;
-  static constexpr int STAGE = SU + SG + SGEO + SEF;  // words (SGEO and SU keep 16-byte alignment)
-  // warps per block: with two 42 KB stages two blocks fit an SM (P2); six warps each keep the
-  // registers of 2 x 192 threads within the SM's file and split the 27 points 5/5/5/4/4/4
+  // warps per block: with two 41 KB stages two blocks fit an SM (P2); six warps each keep the
+  // registers of 2 x 192 threads within the SM's file and split the 14 points 3/3/2/2/2/2
   static constexpr int WARPS = D == 3 ? 6 : O::NF;
   static constexpr int PART = WARPS * 32 * PST;
-  static_assert(PART <= SU + SG, "partial sums reuse the consumed rows, not the geometry records");
-  static_assert(SU % 4 == 0 && SG % 4 == 0, "16-byte alignment of the geometry records");
+  // the partial sums reuse the consumed rows and face fluxes (not the geometry records)
+  static constexpr int SROWS = ((SU + SG > PART ? SU + SG : PART) + 3) / 4 * 4;
+  static constexpr int STAGE = SROWS + SGEO + SEF;  // words (SGEO and SU keep 16-byte alignment)
+  static_assert(SU % 4 == 0, "16-byte alignment of the face fluxes");
   static constexpr size_t BYTES = 2 * (size_t)STAGE * 4;
 };
 
@@ -477,7 +482,7 @@ __global__ void __launch_bounds__(32 * TanPipe<D, P>::WARPS, 2) elem_tan_pipe_ke
     const int64_t e0 = tt * 32;
     const int ne = (int)((d.E - e0) < 32 ? (d.E - e0) : 32);
     float* su = S;
-    float* sgeo = S + L::SU + L::SG;
+    float* sgeo = S + L::SROWS;
     for (int i = tid; i < ne * NVB; i += NT) {
       const int el = i / NVB, r = i - el * NVB, v = r / NB, j = r - v * NB;
       cp_async4(su + el * UROW + v * NBP + j, u + e0 * NVB + i);
@@ -489,7 +494,7 @@ __global__ void __launch_bounds__(32 * TanPipe<D, P>::WARPS, 2) elem_tan_pipe_ke
     const int64_t e0 = tt * 32;
     const int ne = (int)((d.E - e0) < 32 ? (d.E - e0) : 32);
     if (tid < ne * NF) {
-      int* sef = reinterpret_cast<int*>(S + L::SU + L::SG + L::SGEO);
+      int* sef = reinterpret_cast<int*>(S + L::SROWS + L::SGEO);
       sef[tid] = fs;
       const int el = tid / NF, kf = tid - el * NF;
       float* dst = S + L::SU + el * GROW + kf * NFQ * NV;
@@ -526,8 +531,8 @@ __global__ void __launch_bounds__(32 * TanPipe<D, P>::WARPS, 2) elem_tan_pipe_ke
     }
     const float* su = S;
     const float* sg = S + L::SU;
-    const float* sgeo = S + L::SU + L::SG;
-    const int* sef = reinterpret_cast<const int*>(S + L::SU + L::SG + L::SGEO);
+    const float* sgeo = S + L::SROWS;
+    const int* sef = reinterpret_cast<const int*>(S + L::SROWS + L::SGEO);
     const int el = lane < ne ? lane : 0;  // lanes past the last element repeat element 0; discarded
     const float* ge = sgeo + el * GEO;
     float Ai[D * D];
@@ -603,15 +608,22 @@ __global__ void __launch_bounds__(32 * TanPipe<D, P>::WARPS, 2) elem_tan_pipe_ke
     // faces 0..NF-2 go whole to the last warps (warp QW - 1 - kf, which have fewer volume
     // points); the points of face NF-1 are split between warps 0 and 1, so that no warp waits
     // at the tile's barriers for one that has a whole face more
+    // (with 14 points, 3/3/2/2/2/2 over six warps, the four warps of two points take one whole
+    // face each instead)
     static_assert(QW - (NF - 1) >= 2, "two warps share the last face");
+    constexpr bool FACE_PER_LIGHT_WARP = QW - NQ % QW == NF;
     const float rdet = isd * isd;
     int kf = -1, qa = 0, qb = NFQ;
-    if (w >= QW - (NF - 1)) {
-      kf = QW - 1 - w;
-    } else if (w < 2) {
-      kf = NF - 1;
-      qa = w == 0 ? 0 : (NFQ + 1) / 2;
-      qb = w == 0 ? (NFQ + 1) / 2 : NFQ;
+    if constexpr (FACE_PER_LIGHT_WARP) {
+      if (w >= QW - NF) kf = QW - 1 - w;
+    } else {
+      if (w >= QW - (NF - 1)) {
+        kf = QW - 1 - w;
+      } else if (w < 2) {
+        kf = NF - 1;
+        qa = w == 0 ? 0 : (NFQ + 1) / 2;
+        qb = w == 0 ? (NFQ + 1) / 2 : NFQ;
+      }
     }
     if (kf >= 0) {  // warp-uniform
       const int fs = sef[el * NF + kf];

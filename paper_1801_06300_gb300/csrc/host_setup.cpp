@@ -2,14 +2,16 @@
 // element geometry and the face list (Sec. 4.2-4.3 of the paper), for
 // triangles (dim 2) and tetrahedra (dim 3).
 //
-// Quadrature (the paper does not fix it; same reading as the documented
-// rules): p+1 Gauss points per direction.  Edges: Gauss-Legendre.  Triangles
-// (elements in 2D, faces in 3D): collapsed product rule Gauss-Legendre x
-// Gauss-Jacobi(1,0), xi = a (1 - b), eta = b.  Tetrahedra: Gauss-Legendre x
-// Gauss-Jacobi(1,0) x Gauss-Jacobi(2,0), xi = a (1-b)(1-c), eta = b (1-c),
-// zeta = c.  A simplex (v0, ..., vD) maps x = v0 + sum_k xi_k (v_k - v0).
-// Nodes are found here by bisection on sign changes of the three-term
-// recurrence, weights from the closed Christoffel form.
+// Quadrature (the paper does not fix it): p+1 Gauss points per direction.
+// Edges: Gauss-Legendre.  Triangles (elements in 2D, faces in 3D): collapsed
+// product rule Gauss-Legendre x Gauss-Jacobi(1,0), xi = a (1 - b), eta = b.
+// Tetrahedra: Gauss-Legendre x Gauss-Jacobi(1,0) x Gauss-Jacobi(2,0),
+// xi = a (1-b)(1-c), eta = b (1-c), zeta = c.  A simplex (v0, ..., vD) maps
+// x = v0 + sum_k xi_k (v_k - v0).  Nodes are found here by bisection on sign
+// changes of the three-term recurrence, weights from the closed Christoffel
+// form.  Tetrahedra at p = 2 instead take fully symmetric rules of the same
+// degree (5): 14 volume points (instead of 27) and Radon's 7 face points
+// (instead of 9).
 //
 // Faces: local face f of an element is the face opposite vertex f, with
 // vertices f+1, ..., f+D (mod D+1).  A face's points are the face rule on its
@@ -200,6 +202,144 @@ RuleTet collapsed_tetra(int n) {
   return t;
 }
 
+// Radon's rule of degree 5 on the reference triangle (area 1/2), in closed form: the centroid
+// with weight 9/40 of the area, and the two orbits (a, a, 1 - 2a) of the barycentric
+// coordinates, a = (6 -+ sqrt 15)/21, with weights (155 -+ sqrt 15)/1200 of the area.
+RuleTri radon_triangle() {
+  RuleTri t;
+  auto add = [&](long double l1, long double l2, long double w) {
+    t.xi.push_back(l1);
+    t.eta.push_back(l2);
+    t.w.push_back(w);
+  };
+  add(1.0L / 3.0L, 1.0L / 3.0L, 9.0L / 80.0L);
+  const long double r = std::sqrt(15.0L);
+  for (int s = -1; s <= 1; s += 2) {
+    const long double a = (6.0L + s * r) / 21.0L, w = (155.0L + s * r) / 2400.0L;
+    add(a, a, w);
+    add(a, 1.0L - 2.0L * a, w);
+    add(1.0L - 2.0L * a, a, w);
+  }
+  return t;
+}
+
+// Fully symmetric 14-point rule of degree 5 on the reference tetrahedron (volume 1/6): two
+// orbits of four points, barycentric coordinates (a, a, a, 1 - 3a), and one orbit of six,
+// (b, b, 1/2 - b, 1/2 - b), each orbit with one weight.  The six parameters
+// x = (a1, w1, a2, w2, b, w3) make every monomial xi^i eta^j zeta^k of degree <= 5 integrate to
+// i! j! k! / (i + j + k + 3)!: 56 consistent equations, solved by Gauss-Newton (normal
+// equations, Gaussian elimination) in long double from a rough starting point.
+RuleTet symmetric_tetra14() {
+  // each point: coordinates c0 + x[par] * dir (reference coordinates xi, eta, zeta), weight x[wi]
+  struct Pt {
+    int par, wi;
+    long double c0[3], dir[3];
+  };
+  std::vector<Pt> pts;
+  for (int o = 0; o < 2; ++o) {  // (a, a, a, 1 - 3a): lam_0 = 1 - 3a, or one of lam_1..3 is
+    pts.push_back({2 * o, 2 * o + 1, {0, 0, 0}, {1, 1, 1}});
+    for (int k = 0; k < 3; ++k) {
+      Pt q{2 * o, 2 * o + 1, {0, 0, 0}, {1, 1, 1}};
+      q.c0[k] = 1.0L;
+      q.dir[k] = -3.0L;
+      pts.push_back(q);
+    }
+  }
+  // (b, b, 1/2 - b, 1/2 - b): of lam_1..3, the ones equal to b are those of the pair holding b
+  // that lie among them (lam_0 = b for the pairs {0, k}, lam_0 = 1/2 - b otherwise)
+  for (int i = 0; i < 4; ++i)
+    for (int j = i + 1; j < 4; ++j) {
+      Pt q{4, 5, {0.5L, 0.5L, 0.5L}, {-1, -1, -1}};
+      for (int k = 1; k <= 3; ++k)
+        if (k == i || k == j) {
+          q.c0[k - 1] = 0.0L;
+          q.dir[k - 1] = 1.0L;
+        }
+      pts.push_back(q);
+    }
+  std::vector<std::array<int, 3>> mono;
+  for (int i = 0; i <= 5; ++i)
+    for (int j = 0; i + j <= 5; ++j)
+      for (int k = 0; i + j + k <= 5; ++k) mono.push_back({i, j, k});
+  auto fact = [](int n) {
+    long double f = 1.0L;
+    for (int i = 2; i <= n; ++i) f *= i;
+    return f;
+  };
+  auto ipow = [](long double v, int e) {
+    long double r = 1.0L;
+    for (int i = 0; i < e; ++i) r *= v;
+    return r;
+  };
+  long double x[6] = {0.1L, 0.01L, 0.3L, 0.02L, 0.05L, 0.007L};
+  const int M = (int)mono.size();
+  long double rlast = 1.0L;
+  for (int it = 0; it < 100; ++it) {
+    long double JtJ[6][7] = {};
+    long double rmax = 0.0L;
+    for (int m = 0; m < M; ++m) {
+      const int* e = mono[m].data();
+      long double r = -fact(e[0]) * fact(e[1]) * fact(e[2]) / fact(e[0] + e[1] + e[2] + 3);
+      long double J[6] = {};
+      for (const Pt& q : pts) {
+        long double c[3], f = 1.0L, df = 0.0L;
+        for (int d = 0; d < 3; ++d) c[d] = q.c0[d] + x[q.par] * q.dir[d];
+        for (int d = 0; d < 3; ++d) f *= ipow(c[d], e[d]);
+        for (int d = 0; d < 3; ++d) {
+          if (e[d] == 0 || q.dir[d] == 0.0L) continue;
+          long double g = e[d] * ipow(c[d], e[d] - 1) * q.dir[d];
+          for (int d2 = 0; d2 < 3; ++d2)
+            if (d2 != d) g *= ipow(c[d2], e[d2]);
+          df += g;
+        }
+        r += x[q.wi] * f;
+        J[q.wi] += f;
+        J[q.par] += x[q.wi] * df;
+      }
+      rmax = std::max(rmax, std::fabs(r));
+      for (int a = 0; a < 6; ++a) {
+        for (int b = 0; b < 6; ++b) JtJ[a][b] += J[a] * J[b];
+        JtJ[a][6] -= J[a] * r;
+      }
+    }
+    rlast = rmax;
+    if (rmax < 1e-18L) break;
+    // Gaussian elimination with partial pivoting on [JtJ | -Jt r]
+    for (int c = 0; c < 6; ++c) {
+      int piv = c;
+      for (int rr = c + 1; rr < 6; ++rr)
+        if (std::fabs(JtJ[rr][c]) > std::fabs(JtJ[piv][c])) piv = rr;
+      if (JtJ[piv][c] == 0.0L) return RuleTet{};
+      for (int k = 0; k < 7; ++k) std::swap(JtJ[c][k], JtJ[piv][k]);
+      for (int rr = c + 1; rr < 6; ++rr) {
+        const long double f = JtJ[rr][c] / JtJ[c][c];
+        for (int k = c; k < 7; ++k) JtJ[rr][k] -= f * JtJ[c][k];
+      }
+    }
+    long double dx[6];
+    for (int c = 5; c >= 0; --c) {
+      long double s = JtJ[c][6];
+      for (int k = c + 1; k < 6; ++k) s -= JtJ[c][k] * dx[k];
+      dx[c] = s / JtJ[c][c];
+    }
+    long double step = 0.0L;
+    for (int a = 0; a < 6; ++a) {
+      x[a] += dx[a];
+      step = std::max(step, std::fabs(dx[a]));
+    }
+    if (step < 1e-19L) break;
+  }
+  RuleTet t;
+  if (!(rlast < 1e-15L)) return t;
+  for (const Pt& q : pts) {
+    t.xi.push_back(q.c0[0] + x[q.par] * q.dir[0]);
+    t.eta.push_back(q.c0[1] + x[q.par] * q.dir[1]);
+    t.zeta.push_back(q.c0[2] + x[q.par] * q.dir[2]);
+    t.w.push_back(x[q.wi]);
+  }
+  return t;
+}
+
 int build_setup(const pcexp_mesh& mesh, int p, Setup& s, std::string& msg, const int64_t* elem_key) {
   const int D = mesh.dim;
   if (D != 2 && D != 3) {
@@ -224,8 +364,9 @@ int build_setup(const pcexp_mesh& mesh, int p, Setup& s, std::string& msg, const
   s.nv = D + 2;
   s.p = p;
   s.nb = nb;
-  s.nq = D == 2 ? n1 * n1 : n1 * n1 * n1;
-  s.nfq = D == 2 ? n1 : n1 * n1;
+  const bool sym = D == 3 && p == 2;  // symmetric rules (14 volume, 7 face points)
+  s.nq = D == 2 ? n1 * n1 : sym ? 14 : n1 * n1 * n1;
+  s.nfq = D == 2 ? n1 : sym ? 7 : n1 * n1;
   s.E = mesh.n_elem;
   const int64_t E = s.E;
   const int nq = s.nq, nfq = s.nfq;
@@ -240,7 +381,11 @@ int build_setup(const pcexp_mesh& mesh, int p, Setup& s, std::string& msg, const
       wr[q] = tri.w[q];
     }
   } else {
-    RuleTet tet = collapsed_tetra(n1);
+    RuleTet tet = sym ? symmetric_tetra14() : collapsed_tetra(n1);
+    if ((int)tet.w.size() != nq) {
+      msg = "volume quadrature rule construction failed";
+      return PCEXP_ERR_INVALID_ARG;
+    }
     for (int q = 0; q < nq; ++q) {
       xr[q] = {tet.xi[q], tet.eta[q], tet.zeta[q]};
       wr[q] = tet.w[q];
@@ -256,7 +401,7 @@ int build_setup(const pcexp_mesh& mesh, int p, Setup& s, std::string& msg, const
       wf[q] = edge.w[q];
     }
   } else {
-    RuleTri tri = collapsed_triangle(n1);
+    RuleTri tri = sym ? radon_triangle() : collapsed_triangle(n1);
     for (int q = 0; q < nfq; ++q) {
       lam[q] = {1.0L - tri.xi[q] - tri.eta[q], tri.xi[q], tri.eta[q]};
       wf[q] = tri.w[q];

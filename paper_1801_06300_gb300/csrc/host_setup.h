@@ -30,6 +30,12 @@ struct RuleTet {
 };
 RuleTet collapsed_tetra(int n);
 
+// Tetrahedra at p = 2 use fully symmetric rules of the collapsed rules' degree (5) with fewer
+// points: Radon's 7-point rule on each face and a 14-point rule in the volume.
+RuleTri radon_triangle();
+// Empty on failure (the orbit parameters did not converge).
+RuleTet symmetric_tetra14();
+
 int n_basis(int dim, int p);
 
 // Everything the device needs, built once on the host (D = dim, NF = D + 1 faces
