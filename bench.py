@@ -139,14 +139,26 @@ def shape(dim, p):
     return (p + 1) * (p + 2) * (p + 3) // 6, (p + 1) ** 3, (p + 1) ** 2, 5, 4
 
 
-def algorithmic_bytes(kind, T, K, E, F, dim, p, m, face_jacobians=True):
+def second_pass_columns(masks, m):
+    """(fraction of the Gram-Schmidt update-and-norm launches that ran, mean column index of
+    those that ran) from the step infos' reorth_cols bit masks (bit j: column j of a stage ran
+    the second pass; the other launches of the class leave at once)."""
+    ran = [j for mk in masks for j in range(m) if (mk >> j) & 1]
+    if not masks:
+        return 1.0, (m - 1) / 2.0
+    return len(ran) / (m * len(masks)), (sum(ran) / len(ran) if ran else 0.0)
+
+
+def algorithmic_bytes(kind, T, K, E, F, dim, p, m, face_jacobians=True, gs=None):
     """DRAM bytes per launch of a kernel class: every input it needs read once and every
     output written once (T = 4 or 8 bytes per value).  G is the face-flux buffer
     [F][nfq][nv] between the face and element kernels of one operator application.
 
     jvp: one whole J v application (face + element kernels) at its minimum of three
     K-vector passes (read v, read the linearisation state, write J v) plus the element
-    geometry, the figure a fused J v would move."""
+    geometry, the figure a fused J v would move.  gs = second_pass_columns(...): the
+    update-and-norm class counts the columns that ran the second pass only (averaged over
+    the class's launches)."""
     nb, nq, nfq, nv, nf = shape(dim, p)
     geo = dim * dim + 3
     g_face = F * ((dim + 1) * T + 12)  # normal, measure, element and local-face ids
@@ -169,11 +181,11 @@ def algorithmic_bytes(kind, T, K, E, F, dim, p, m, face_jacobians=True):
         "residual_elem": 2 * K * T + g_elem + G,
         "cgs_proj": (avg_j + 2) * K * T,
         "cgs_upd_proj": (avg_j + 3) * K * T,
-        "cgs_upd_norm": (avg_j + 3) * K * T,
+        "cgs_upd_norm": (gs[0] * (gs[1] + 3) if gs else avg_j + 3) * K * T,
     }.get(kind)
 
 
-def algorithmic_flops(kind, K, E, F, dim, p, m, T=8):
+def algorithmic_flops(kind, K, E, F, dim, p, m, T=8, gs=None):
     """Floating-point operations per launch of a kernel class (an FMA counts 2).
 
     jvp_elem, FP64 (stored point Jacobians): per element, nq points x (trace nv nb + Jacobian
@@ -192,7 +204,7 @@ def algorithmic_flops(kind, K, E, F, dim, p, m, T=8):
         "jvp_face": F * nfq * (2 * nv * nb + 2 * nv * nv),
         "cgs_proj": K * (nc + 1),
         "cgs_upd_proj": K * 2 * nc,
-        "cgs_upd_norm": K * (nc + 1),
+        "cgs_upd_norm": K * (gs[0] * (gs[1] + 2) if gs else nc + 1),
     }.get(kind)
     return None if fma is None else 2.0 * fma
 
@@ -223,7 +235,7 @@ def fp32_peak(capi):
 
 
 def roofline_entry(prof, T, K, E, F, hbm, peak_kind, dim, p, m, workload, fp64=None, face_jacobians=True,
-                   fp32=None):
+                   fp32=None, gs=None):
     """Roofline of the dominant kernel class by device time, against the roof that bounds it:
     the one with the longer minimum time, algorithmic bytes at the measured HBM copy rate or
     algorithmic flops at the measured FMA rate of its precision (FP64 pipe for FP64 kernels,
@@ -240,10 +252,10 @@ def roofline_entry(prof, T, K, E, F, hbm, peak_kind, dim, p, m, workload, fp64=N
              "traffic": tr[0] if tr else None}
     if tr:
         entry["traffic_source"] = tr[1]
-    ab = algorithmic_bytes(dom, T, K, E, F, dim, p, m, face_jacobians)
+    ab = algorithmic_bytes(dom, T, K, E, F, dim, p, m, face_jacobians, gs)
     if ab is not None:
         entry["algorithmic_bytes_per_launch"] = ab
-    fl = algorithmic_flops(dom, K, E, F, dim, p, m, T)
+    fl = algorithmic_flops(dom, K, E, F, dim, p, m, T, gs)
     alu = fp64 if T == 8 else fp32
     t_alu = fl / (alu[0] * 1e12) if fl is not None and alu is not None else 0.0
     t_hbm = ab / (hbm * 1e9) if ab is not None else 0.0
@@ -270,20 +282,22 @@ def roofline_entry(prof, T, K, E, F, hbm, peak_kind, dim, p, m, workload, fp64=N
     return entry
 
 
-def kernel_table(prof, T, K, E, F, hbm, dim, p, m, fp64=None, face_jacobians=True, fp32=None):
+def kernel_table(prof, T, K, E, F, hbm, dim, p, m, fp64=None, face_jacobians=True, fp32=None, gs=None):
     """Every kernel class with a byte model: launches, mean launch time (CUDA events per
     class over the profiled steps), algorithmic GB/s and its fraction of measured HBM;
     classes with a flop model also give TFLOP/s and the fraction of the measured FMA rate of
     their precision."""
     out = {}
     for kind, (n, ms) in prof.items():
-        ab = algorithmic_bytes(kind, T, K, E, F, dim, p, m, face_jacobians)
+        ab = algorithmic_bytes(kind, T, K, E, F, dim, p, m, face_jacobians, gs)
         if not n or ab is None:
             continue
         sec = ms / n / 1e3
         row = {"launches": n, "avg_launch_us": round(sec * 1e6, 2), "gbs": round(ab / sec / 1e9, 1),
                "hbm_frac": round(ab / sec / 1e9 / hbm, 4)}
-        fl = algorithmic_flops(kind, K, E, F, dim, p, m, T)
+        if kind == "cgs_upd_norm" and gs:
+            row["ran"] = round(gs[0], 4)  # share of the launches that ran the second pass
+        fl = algorithmic_flops(kind, K, E, F, dim, p, m, T, gs)
         if T == 8 and fl is not None and fp64 is not None:
             row["fp64_tflops"] = round(fl / sec / 1e12, 3)
             row["fp64_frac"] = round(fl / sec / 1e12 / fp64[0], 4)
@@ -320,6 +334,8 @@ def main():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-fp64", action="store_true", help="skip the FP64 form of the headline workload")
     ap.add_argument("--no-2d", action="store_true", help="skip the 2D bump-channel side block")
+    ap.add_argument("--no-two-pass", action="store_true",
+                    help="skip the FP32-mixed run with both Gram-Schmidt passes on every column")
     ap.add_argument("--no-partitioned", action="store_true",
                     help="skip the side block of the headline workload split into element partitions")
     ap.add_argument("--n3d", type=int, default=N3D, help="cubes per side of the 3D vortex (profiling runs)")
@@ -382,15 +398,16 @@ def main():
         return sum(a.elapsed_time(b) for a, b in evs), ck
 
     def profiled(ctx, steps):
+        """Per-class CUDA-event times of `steps` steps, and the steps' second-pass column masks."""
         ctx.profile_enable(True)
-        t0 = time.perf_counter()
+        masks = []
         for _ in range(steps):
-            step(ctx)
+            info = ctx.step(capi.PCEXP_SCHEME_PCEXP, capi.PCEXP_DT_GLOBAL_CFL, case.cfl, case.m)
+            masks += list(info["reorth_cols"])
         torch.cuda.synchronize()
-        wall = time.perf_counter() - t0
         prof = ctx.profile_read()
         ctx.profile_enable(False)
-        return prof, wall
+        return prof, masks
 
     forms = {}
     order = [("fp32_mixed", capi.PCEXP_FP32_MIXED)] + ([] if args.no_fp64 else [("fp64", capi.PCEXP_FP64)])
@@ -404,17 +421,21 @@ def main():
         ms, clocks = timed(ctx, args.steps, clocks=True)
         ms = max_over_ranks(ms, dist)
         state = ctx.get_state()
-        prof, _ = profiled(ctx, 1 if name == "fp64" else 2)
         nprof = 1 if name == "fp64" else 2
+        prof, masks = profiled(ctx, nprof)
         prof = {k: (v[0] / nprof, v[1] / nprof) for k, v in prof.items()}  # per step
+        gs = second_pass_columns(masks, case.m)
         T = 4 if name == "fp32_mixed" else 8
         forms[name] = {
             "value": job_throughput(ctx.K, args.steps, world, ms / 1e3), "ms_per_step": ms / args.steps,
             "state": state, "clocks": clocks, "prof": prof,
             "kernel_ms_per_step": {k: round(v[1], 4) for k, v in prof.items() if v[0]},
             "roofline": roofline_entry(prof, T, ctx.K, E, F, hbm, peak_kind, 3, case.p, case.m, "vortex3d", fp64,
-                                       fp32=fp32),
-            "kernels": kernel_table(prof, T, ctx.K, E, F, hbm, 3, case.p, case.m, fp64, fp32=fp32),
+                                       fp32=fp32, gs=gs),
+            "kernels": kernel_table(prof, T, ctx.K, E, F, hbm, 3, case.p, case.m, fp64, fp32=fp32, gs=gs),
+            "gram_schmidt": {"reorth": "selective" if T == 4 else "always",
+                             "second_pass_columns": f"{sum(bin(x).count('1') for x in masks)} of "
+                                                    f"{case.m * len(masks)} (profiled steps)"},
         }
         if name == "fp32_mixed":
             ctx32 = ctx
@@ -423,6 +444,27 @@ def main():
     K = ctx32.K
     head = forms["fp32_mixed"]
     launches_per_step = sum(v[0] for v in head["prof"].values())
+
+    # the FP32-mixed form with both Gram-Schmidt passes on every column (CGS2), the same steps
+    two_pass = None
+    if not args.no_two_pass:
+        ctx = capi.Context(case.mesh, case.p, case.free, capi.PCEXP_FP32_MIXED, m_max=case.m,
+                           reorth=capi.PCEXP_REORTH_ALWAYS)
+        ctx.project_state(capi.PCEXP_PROJ_VORTEX, prm)
+        for _ in range(args.warmup):
+            step(ctx)
+        torch.cuda.synchronize()
+        ms2, _ = timed(ctx, args.steps)
+        ms2 = max_over_ranks(ms2, dist)
+        u2 = ctx.get_state()
+        ctx.close()
+        two_pass = {"ms_per_step": ms2 / args.steps, "value": job_throughput(K, args.steps, world, ms2 / 1e3),
+                    "selective_speedup": ms2 / args.steps / head["ms_per_step"],
+                    "state_rel_diff_vs_selective": float(np.linalg.norm(u2 - head["state"]) /
+                                                         np.linalg.norm(head["state"]))}
+        if "fp64" in forms:
+            a = forms["fp64"]["state"]
+            two_pass["state_rel_l2_vs_fp64"] = float(np.linalg.norm(u2 - a) / np.linalg.norm(a))
 
     # end to end through the public API with host buffers: every step copies the state in from
     # pinned host memory, steps, and copies it back out (copies inside the timed region)
@@ -485,6 +527,8 @@ def main():
         "kernels": head["kernels"],
         "fp64": strip(forms["fp64"]) if "fp64" in forms else None,
         "speedup_fp32_mixed_vs_fp64": (forms["fp64"]["ms_per_step"] / head["ms_per_step"]) if "fp64" in forms else None,
+        "gram_schmidt": head["gram_schmidt"],
+        "fp32_mixed_two_pass": two_pass,
         "cpu_baseline": cpu,
         "bump2d": side,
         "partitioned": parted,
@@ -554,14 +598,16 @@ def bump2d_block(args, capi, W, torch, np, hbm, peak_kind, fp64, dist=None, fp32
         torch.cuda.synchronize()
         ms = max_over_ranks(sum(a.elapsed_time(b) for a, b in evs), dist)
         ctx.profile_enable(True)
-        ctx.step(capi.PCEXP_SCHEME_PCEXP, capi.PCEXP_DT_LOCAL_CFL, CFL2D, M2D, info=False)
+        info = ctx.step(capi.PCEXP_SCHEME_PCEXP, capi.PCEXP_DT_LOCAL_CFL, CFL2D, M2D)
         prof = ctx.profile_read()
         ctx.profile_enable(False)
+        gs = second_pass_columns(list(info["reorth_cols"]), M2D)
         T = 8 if name == "fp64" else 4
         res[name] = {"value": ctx.K * steps / (ms / 1e3), "ms_per_step": ms / steps,
                      "kernel_ms_per_step": {k: round(v[1], 4) for k, v in prof.items() if v[0]},
                      "roofline": roofline_entry(prof, T, ctx.K, E, F, hbm, peak_kind, 2, P2D, M2D, "bump2d", fp64,
-                                                fp32=fp32)}
+                                                fp32=fp32, gs=gs),
+                     "second_pass_ran": round(gs[0], 4)}
         ctx.close()
     res["fp32_mixed"]["speedup_vs_fp64"] = res["fp64"]["ms_per_step"] / res["fp32_mixed"]["ms_per_step"]
     return {"workload": f"bump2d_{NX}x{NY}_p{P2D}_m{M2D}_pcexp_localcfl100", "steps": steps, **res}

@@ -61,6 +61,21 @@ extern "C" {
 #define PCEXP_BASIS_PAPER 0
 #define PCEXP_BASIS_INTERNAL 1
 
+/* Re-orthogonalisation of the Arnoldi process (Sec. 2.2, Eq. vm-vm2; the paper names the
+ * classical Arnoldi process and no Gram-Schmidt variant).  Every column j first projects
+ * w = J v_j on v_1..v_j and subtracts (one classical Gram-Schmidt pass, w_1 = w - V h).
+ * ALWAYS: a second pass projects and subtracts again (CGS2).  SELECTIVE: the second pass
+ * runs only when the first cancelled much of w, ||w_1|| < ||w|| / sqrt(2) (the criterion of
+ * Daniel, Gragg, Kaufman and Stewart, 1976); otherwise v_{j+1} = w_1 / ||w_1|| and column j
+ * of H is the first pass's.  The decision is taken on the device per column, from the FP64
+ * sums.  AUTO (0): ALWAYS for PCEXP_FP64 contexts (the form whose reverse step replays both
+ * passes) and SELECTIVE for PCEXP_FP32_MIXED, where the basis is stored in FP32 and a second
+ * pass after a first without cancellation changes it by FP32 rounding only.  SELECTIVE is
+ * not offered for PCEXP_FP64 contexts (UNSUPPORTED). */
+#define PCEXP_REORTH_AUTO 0
+#define PCEXP_REORTH_ALWAYS 1
+#define PCEXP_REORTH_SELECTIVE 2
+
 #define PCEXP_SCHEME_PCEXP 0 /* Eq. s9 + s10 */
 #define PCEXP_SCHEME_EXP1 1  /* Eq. s9 alone (first stage) */
 #define PCEXP_SCHEME_ETD2 2  /* Eq. s7: ETD1 + dt (dt/dt_{n-1}) phi_2(dt J_n)(N_n - N_{n-1}), history in
@@ -133,6 +148,7 @@ typedef struct pcexp_options {
                            (k < m) whose relative error estimate (below) is <= krylov_tol, and the
                            steady march caps its CFL from the first stage's estimate:
                            cap = CFL_used * clamp(0.8 (tol / est)^(1/2), 1/4, 2) */
+  int32_t reorth;       /* PCEXP_REORTH_AUTO | PCEXP_REORTH_ALWAYS | PCEXP_REORTH_SELECTIVE */
 } pcexp_options;
 
 typedef struct pcexp_step_info {
@@ -143,6 +159,8 @@ typedef struct pcexp_step_info {
   double krylov_err[2];  /* relative a-posteriori error estimate of each stage's phi product
                             (Saad 1992, cited in Sec. 2.2): dt h_{k+1,k} |e_k^T phi_2(dt H_k) e_1|
                             / ||phi_1(dt H_k) e_1|| at the dimension k used */
+  uint32_t reorth_cols[2]; /* bit j set: Arnoldi column j of the stage ran the second
+                              Gram-Schmidt pass (all columns under PCEXP_REORTH_ALWAYS) */
 } pcexp_step_info;
 
 typedef struct pcexp_steady_info {
@@ -200,8 +218,9 @@ int pcexp_compute_dt(pcexp_ctx* ctx, double cfl, int local, double* dt, int on_d
 
 /* Arnoldi process (Eq. vm-vm2) for J(U) started from b: V [m+1][K] (column j
  * = v_{j+1}, same basis as U), H [(m+1) * m] row-major Hessenberg H~_m,
- * *k = dimension reached (< m on happy breakdown), *beta = ||b||.  Uses
- * classical Gram-Schmidt run twice (CGS2).  V may be NULL. */
+ * *k = dimension reached (< m on happy breakdown), *beta = ||b||.  Classical
+ * Gram-Schmidt with the context's re-orthogonalisation (PCEXP_REORTH_*: two passes, or the
+ * second pass only where the first cancelled).  V may be NULL. */
 int pcexp_arnoldi(pcexp_ctx* ctx, const double* U, const double* b, int m,
                   double* V, double* H, int* k, double* beta, int on_device);
 

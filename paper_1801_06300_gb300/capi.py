@@ -28,6 +28,9 @@ PCEXP_FP64 = 0
 PCEXP_FP32_MIXED = 1
 PCEXP_BASIS_PAPER = 0
 PCEXP_BASIS_INTERNAL = 1
+PCEXP_REORTH_AUTO = 0
+PCEXP_REORTH_ALWAYS = 1
+PCEXP_REORTH_SELECTIVE = 2
 PCEXP_SCHEME_PCEXP = 0
 PCEXP_SCHEME_EXP1 = 1
 PCEXP_SCHEME_ETD2 = 2
@@ -65,12 +68,12 @@ def _physics(free, omega):
 
 class pcexp_options(C.Structure):
     _fields_ = [("precision", C.c_int32), ("m_max", C.c_int32), ("breakdown_eta", C.c_double),
-                ("basis_io", C.c_int32), ("krylov_tol", C.c_double)]
+                ("basis_io", C.c_int32), ("krylov_tol", C.c_double), ("reorth", C.c_int32)]
 
 
 class pcexp_step_info(C.Structure):
     _fields_ = [("krylov_dim", C.c_int32 * 2), ("beta", C.c_double * 2), ("dt", C.c_double),
-                ("res_norm", C.c_double), ("krylov_err", C.c_double * 2)]
+                ("res_norm", C.c_double), ("krylov_err", C.c_double * 2), ("reorth_cols", C.c_uint32 * 2)]
 
 
 class pcexp_steady_info(C.Structure):
@@ -236,14 +239,14 @@ class Group:
 
     def __init__(self, mesh, part, p: int, free, precision: int = PCEXP_FP64, m_max: int = 30,
                  eta: float = 0.0, basis_io: int = PCEXP_BASIS_PAPER, devices=None, omega=None,
-                 krylov_tol: float = 0.0):
+                 krylov_tol: float = 0.0, reorth: int = 0):
         lib = load()
         m, self._keep = _mesh_struct(mesh)
         part = np.ascontiguousarray(part, np.int32)
         self.n = int(part.max()) + 1
         dev = None if devices is None else np.ascontiguousarray(devices, np.int32)
         ph = _physics(free, omega)
-        op = pcexp_options(precision, m_max, eta, basis_io, krylov_tol)
+        op = pcexp_options(precision, m_max, eta, basis_io, krylov_tol, reorth)
         self.g = C.c_void_p()
         check(lib.pcexp_group_create(C.byref(self.g), C.byref(m), part.ctypes.data_as(_P), self.n,
                                      dev.ctypes.data_as(_P) if dev is not None else None, p, C.byref(ph),
@@ -341,7 +344,8 @@ class Group:
         inf = pcexp_step_info()
         check(self.lib.pcexp_group_step(self.g, scheme, dt_mode, dt_or_cfl, m, C.byref(inf)), "pcexp_group_step")
         return dict(k=(inf.krylov_dim[0], inf.krylov_dim[1]), beta=(inf.beta[0], inf.beta[1]), dt=inf.dt,
-                    res_norm=inf.res_norm, err=(inf.krylov_err[0], inf.krylov_err[1]))
+                    res_norm=inf.res_norm, err=(inf.krylov_err[0], inf.krylov_err[1]),
+                    reorth_cols=(int(inf.reorth_cols[0]), int(inf.reorth_cols[1])))
 
 
 class Context:
@@ -349,12 +353,12 @@ class Context:
 
     def __init__(self, mesh, p: int, free, precision: int = PCEXP_FP64, m_max: int = 30,
                  eta: float = 0.0, basis_io: int = PCEXP_BASIS_PAPER, stream=None, krylov_tol: float = 0.0,
-                 omega=None):
+                 omega=None, reorth: int = 0):
         lib = load()
         m, self._keep = _mesh_struct(mesh)
         ph = _physics(free, omega)
         self.omega = omega
-        op = pcexp_options(precision, m_max, eta, basis_io, krylov_tol)
+        op = pcexp_options(precision, m_max, eta, basis_io, krylov_tol, reorth)
         if stream is None:
             try:
                 import torch
@@ -507,7 +511,8 @@ class Context:
         if not info:
             return None
         return dict(k=(inf.krylov_dim[0], inf.krylov_dim[1]), beta=(inf.beta[0], inf.beta[1]), dt=inf.dt,
-                    res_norm=inf.res_norm, err=(inf.krylov_err[0], inf.krylov_err[1]))
+                    res_norm=inf.res_norm, err=(inf.krylov_err[0], inf.krylov_err[1]),
+                    reorth_cols=(int(inf.reorth_cols[0]), int(inf.reorth_cols[1])))
 
     def march_steady(self, scheme: int, cfl_max: float, decades: float, max_iter: int, m: int):
         inf = pcexp_steady_info()

@@ -34,6 +34,7 @@ struct pcexp_ctx {
   int m_max = 0;
   double eta = 0;
   double ktol = 0;  // Krylov tolerance of the adaptive dimension (<= 0: fixed dimension)
+  bool selective = false;  // Arnoldi: second Gram-Schmidt pass only after a cancelling first pass
   int basis_io = PCEXP_BASIS_PAPER;
   double volume = 0;
   pcexp_physics phys{};
@@ -500,7 +501,7 @@ int arnoldi(pcexp_ctx* c, const T* escale, int m, const double* dt_dev = nullptr
   T* G = reinterpret_cast<T*>(c->G);
   T* V = reinterpret_cast<T*>(c->V);
   (void)G;
-  PCEXP_LAUNCH(c, PCEXP_KC_OTHER, launch_reset_kstate(c->ks, c->st));
+  PCEXP_LAUNCH(c, PCEXP_KC_OTHER, launch_reset_kstate(c->ks, c->selective ? 1 : 0, c->st));
   PCEXP_LAUNCH(c, PCEXP_KC_CGS_NORM, launch_cgs<T>(CGS_NORM, V, c->Kp, c->Kp, 0, V, nullptr, c->ks, c->partials, c->eta, c->st));
   PCEXP_TRY(group_cgs(c, CGS_NORM, 0));
   for (int j = 0; j < m; ++j) {
@@ -509,9 +510,12 @@ int arnoldi(pcexp_ctx* c, const T* escale, int m, const double* dt_dev = nullptr
     PCEXP_TRY(jac_apply<T>(c, d, Vcol<T>(c, j), w, escale, &c->ks->done, &c->ks->s[j]));
     PCEXP_LAUNCH(c, PCEXP_KC_CGS_PROJ, launch_cgs<T>(CGS_PROJ, V, c->Kp, c->Kp, j, w, nullptr, c->ks, c->partials, c->eta, c->st));
     PCEXP_TRY(group_cgs(c, CGS_PROJ, j));
-    PCEXP_LAUNCH(c, PCEXP_KC_CGS_UPD_PROJ, launch_cgs<T>(CGS_UPD_PROJ, V, c->Kp, c->Kp, j, w, nullptr, c->ks, c->partials, c->eta, c->st));
+    // selective re-orthogonalisation: the first pass writes w_1 straight into z_{j+1}, which
+    // stays there when the second pass is not needed and is updated in place when it is
+    T* z1 = Vcol<T>(c, j + 1);
+    PCEXP_LAUNCH(c, PCEXP_KC_CGS_UPD_PROJ, launch_cgs<T>(CGS_UPD_PROJ, V, c->Kp, c->Kp, j, w, c->selective ? z1 : nullptr, c->ks, c->partials, c->eta, c->st));
     PCEXP_TRY(group_cgs(c, CGS_UPD_PROJ, j));
-    PCEXP_LAUNCH(c, PCEXP_KC_CGS_UPD_NORM, launch_cgs<T>(CGS_UPD_NORM, V, c->Kp, c->Kp, j, w, Vcol<T>(c, j + 1), c->ks, c->partials, c->eta, c->st));
+    PCEXP_LAUNCH(c, PCEXP_KC_CGS_UPD_NORM, launch_cgs<T>(CGS_UPD_NORM, V, c->Kp, c->Kp, j, c->selective ? z1 : w, z1, c->ks, c->partials, c->eta, c->st));
     PCEXP_TRY(group_cgs(c, CGS_UPD_NORM, j));
     if (c->ktol > 0 && dt_dev && (j + 1) % KRYLOV_CHECK == 0 && j + 1 < m)
       PCEXP_LAUNCH(c, PCEXP_KC_PHI, launch_phi_check(c->ks, dt_dev, c->ktol, c->st));
@@ -714,6 +718,8 @@ int step_impl(pcexp_ctx* c, int scheme, int dt_mode, double dt_or_cfl, int m, pc
     info->res_norm = h.res_norm;
     info->krylov_err[0] = h.kerr[0];
     info->krylov_err[1] = one_stage ? 0.0 : h.kerr[1];
+    info->reorth_cols[0] = h.pass2[0];
+    info->reorth_cols[1] = one_stage ? 0u : h.pass2[1];
     if (h.err) {
       g_last_error = "non-finite norm, beta or Hessenberg entry";
       return PCEXP_ERR_NONFINITE;
@@ -1066,6 +1072,21 @@ int UNSUPPORTED_FP32_HESS(pcexp_ctx*) {
   return PCEXP_ERR_UNSUPPORTED;
 }
 
+// The re-orthogonalisation option: FP64 contexts keep both Gram-Schmidt passes (their
+// reverse step replays the two-pass process as computed).
+int check_reorth(const pcexp_options* opt) {
+  if (opt->reorth != PCEXP_REORTH_AUTO && opt->reorth != PCEXP_REORTH_ALWAYS &&
+      opt->reorth != PCEXP_REORTH_SELECTIVE) {
+    g_last_error = "reorth: PCEXP_REORTH_AUTO, PCEXP_REORTH_ALWAYS or PCEXP_REORTH_SELECTIVE";
+    return PCEXP_ERR_INVALID_ARG;
+  }
+  if (opt->reorth == PCEXP_REORTH_SELECTIVE && opt->precision == PCEXP_FP64) {
+    g_last_error = "selective re-orthogonalisation is provided for the FP32-mixed form";
+    return PCEXP_ERR_UNSUPPORTED;
+  }
+  return PCEXP_OK;
+}
+
 int check_ctx(const pcexp_ctx* c) {
   if (!c) {
     g_last_error = "null context";
@@ -1109,6 +1130,7 @@ int create_impl(pcexp_ctx* c, const pcexp_mesh* mesh, int p, const pcexp_physics
   c->m_max = opt->m_max;
   c->eta = opt->breakdown_eta > 0 ? opt->breakdown_eta : (c->fp32 ? 1e-6 : 1e-12);
   c->ktol = opt->krylov_tol > 0 ? opt->krylov_tol : 0.0;
+  c->selective = opt->reorth == PCEXP_REORTH_SELECTIVE || (opt->reorth == PCEXP_REORTH_AUTO && c->fp32);
   c->basis_io = opt->basis_io;
   // tables
   std::vector<double> tabs;
@@ -1483,6 +1505,7 @@ int pcexp_create(pcexp_ctx** out, const pcexp_mesh* mesh, int p, const pcexp_phy
   if (opt->precision != PCEXP_FP64 && opt->precision != PCEXP_FP32_MIXED) return PCEXP_ERR_INVALID_ARG;
   if (opt->basis_io != PCEXP_BASIS_PAPER && opt->basis_io != PCEXP_BASIS_INTERNAL) return PCEXP_ERR_INVALID_ARG;
   if (!(phys->gamma > 1.0) || !(phys->rho_inf > 0) || !(phys->p_inf > 0)) return PCEXP_ERR_INVALID_ARG;
+  PCEXP_TRY(check_reorth(opt));
   pcexp_ctx* c = new pcexp_ctx();
   cudaGetDevice(&c->device);
   c->st = reinterpret_cast<cudaStream_t>(cuda_stream);
@@ -1945,7 +1968,7 @@ int check_opts(const pcexp_physics* phys, const pcexp_options* opt) {
   if (opt->precision != PCEXP_FP64 && opt->precision != PCEXP_FP32_MIXED) return PCEXP_ERR_INVALID_ARG;
   if (opt->basis_io != PCEXP_BASIS_PAPER && opt->basis_io != PCEXP_BASIS_INTERNAL) return PCEXP_ERR_INVALID_ARG;
   if (!(phys->gamma > 1.0) || !(phys->rho_inf > 0) || !(phys->p_inf > 0)) return PCEXP_ERR_INVALID_ARG;
-  return PCEXP_OK;
+  return check_reorth(opt);
 }
 
 // Runs fn(k) for every partition, each on a host thread of its own with its device current.

@@ -32,6 +32,9 @@ struct KState {
   int err;
   unsigned counter;
   int group;               // partitioned run: the passes leave their sums in gsum, unfinalised
+  int selective;           // second Gram-Schmidt pass only after a first pass that cancelled
+  int skip2;               // the current column's second pass is not needed (selective)
+  unsigned pass2;          // bit j: column j ran the second pass
 };
 
 // Device-resident scalars of the reverse Krylov stage.
@@ -59,6 +62,7 @@ struct StepState {
   double dtmin_scratch;
   double dt_prev;  // dt of the previous ETD2 step (its divided difference of N)
   double kerr[2];  // Krylov error estimates of the two stages
+  unsigned pass2[2];  // columns of each stage that ran the second Gram-Schmidt pass (bit j)
 };
 
 // Mesh/geometry/tables on the device, for one scalar type.  D = dim, NV = D + 2,
@@ -307,7 +311,7 @@ template <class T>
 cudaError_t launch_zero_range(T* x, int64_t from, int64_t to, cudaStream_t st);
 // ss->cfl = min(ss->cfl, cap) (the Krylov-error cap of the steady march)
 cudaError_t launch_cap_cfl(StepState* ss, double cap, cudaStream_t st);
-cudaError_t launch_reset_kstate(KState* ks, cudaStream_t st);
+cudaError_t launch_reset_kstate(KState* ks, int selective, cudaStream_t st);
 // ---- reverse Krylov stage (adjoint.cu, FP64)
 // Reverse of the Krylov stage, step by step.  Each reduction (ybar, alpha, upd, b0dot) leaves
 // its sums in as->dots and finishes in its last block; in a partitioned run (as->group) it

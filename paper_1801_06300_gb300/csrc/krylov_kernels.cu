@@ -117,12 +117,22 @@ PCEXP_DEV void acc_dot(Acc<T>& acc, const T (&a)[VN], const T (&b)[VN]) {
   }
 }
 
+// Selective re-orthogonalisation (Daniel, Gragg, Kaufman & Stewart 1976): the first pass
+// is kept alone when ||w_1|| >= ||w|| / sqrt(2), i.e. when it cancelled less than that.
+constexpr double DGKS_KAPPA = 0.70710678118654752440;
+
 // Stage logic of the last block: per-column entries in parallel, scalars on thread 0.
 PCEXP_DEV void cgs_finalize(int mode, int j, const double* dots, KState* ks, double eta) {
   __shared__ int bad;
   if (threadIdx.x == 0) bad = 0;
   __syncthreads();
   if (mode == CGS_PROJ || mode == CGS_UPD_PROJ) {
+    // selective: UPD_PROJ also summed ||w_1||^2 (slot j + 1); every thread takes the same
+    // decision from the same values.  A non-finite or zero norm takes the second pass, whose
+    // norm test reports it.
+    const double n1 = (mode == CGS_UPD_PROJ && ks->selective) ? sqrt(dots[j + 1]) : 0.0;
+    const bool keep1 = mode == CGS_UPD_PROJ && ks->selective && isfinite(n1) && n1 > 0.0 &&
+                       n1 >= DGKS_KAPPA * ks->wnorm0;
     // w = J v_j is already normalised by s_j (applied by the J v kernel)
     for (int i = threadIdx.x; i <= j; i += blockDim.x) {
       const double si = ks->s[i];
@@ -131,7 +141,7 @@ PCEXP_DEV void cgs_finalize(int mode, int j, const double* dots, KState* ks, dou
       if (mode == CGS_PROJ) {
         ks->H[i * MMAX + j] = h;
         ks->H1[i * MMAX + j] = h;
-      } else {
+      } else if (!keep1) {
         ks->H[i * MMAX + j] += h;
       }
       ks->coef[i] = si * h;
@@ -139,6 +149,14 @@ PCEXP_DEV void cgs_finalize(int mode, int j, const double* dots, KState* ks, dou
     __syncthreads();
     if (threadIdx.x == 0) {
       if (mode == CGS_PROJ) ks->wnorm0 = sqrt(dots[j + 1]);
+      if (mode == CGS_UPD_PROJ) {
+        ks->skip2 = keep1 ? 1 : 0;
+        if (keep1) {  // z_{j+1} = w_1 (written by the pass); n1 > eta ||w||: no breakdown
+          ks->H[(j + 1) * MMAX + j] = n1;
+          ks->k = j + 1;
+          ks->s[j + 1] = 1.0 / n1;
+        }
+      }
       if (bad) {
         ks->err = 1;
         ks->done = 1;
@@ -164,6 +182,7 @@ PCEXP_DEV void cgs_finalize(int mode, int j, const double* dots, KState* ks, dou
   }
   // CGS_UPD_NORM
   const double hn = sqrt(dots[0]);
+  ks->pass2 |= 1u << j;
   ks->H[(j + 1) * MMAX + j] = hn;
   ks->k = j + 1;
   if (!isfinite(hn)) {
@@ -214,9 +233,11 @@ PCEXP_DEV Acc<T> warp_reduce_columns(Acc<T> (&a)[NC], int lane) {
 // Row Gram-Schmidt pass (NORM, PROJ, UPD_PROJ, UPD_NORM): every thread owns whole 16-byte
 // chunks of rows and accumulates all columns for them; the launch bounds hold it at 128
 // registers so that two blocks share an SM.
+// In the selective form UPD_NORM runs in place (w == out == z_{j+1}, each element read and
+// then written by the same thread), so w and out are not restrict-qualified.
 template <class T, int NC, int MODE>
 __global__ void __launch_bounds__(256, 2) cgs_kernel(const T* __restrict__ Z, int64_t ldz, int64_t Kp, int j,
-                                                  T* __restrict__ w, T* __restrict__ out, KState* ks,
+                                                  T* w, T* out, KState* ks,
                                                   double* __restrict__ partials, double eta) {
   constexpr int VN = VecN<T>::N;
   constexpr int NACC = (MODE == CGS_PROJ) ? NC + 1 : (MODE == CGS_UPD_PROJ ? NC : 1);
@@ -224,6 +245,7 @@ __global__ void __launch_bounds__(256, 2) cgs_kernel(const T* __restrict__ Z, in
   __shared__ Acc<T> red[8][NACC];
   __shared__ bool last;
   if (ks->done) return;  // breakdown reached earlier: uniform early exit
+  if (MODE == CGS_UPD_NORM && ks->skip2) return;  // selective: the first pass was kept
   const int nc = (MODE == CGS_NORM) ? 0 : j + 1;
   if (MODE == CGS_UPD_PROJ || MODE == CGS_UPD_NORM)
     for (int c = threadIdx.x; c < nc; c += blockDim.x) scoef[c] = (T)ks->coef[c];
@@ -271,7 +293,7 @@ __global__ void __launch_bounds__(256, 2) cgs_kernel(const T* __restrict__ Z, in
         }
       }
       if constexpr (MODE == CGS_UPD_PROJ) {
-        store_vec<T, VN>(w + r, x);
+        store_vec<T, VN>((out ? out : w) + r, x);
         // reload the chunks rather than keep all of them live across the store (255 -> 128
         // registers, two blocks per SM instead of one; the reloads hit L1/L2)
         asm volatile("" ::: "memory");
@@ -423,6 +445,10 @@ __global__ void __launch_bounds__(256) cgs_cs_kernel(const T* __restrict__ Z, in
   __shared__ T xs[(MODE == CGS_UPD_PROJ) ? TR : 1];
   __shared__ Acc<T> red[CGS_WARPS * NCW + 1];
   if (ks->done) return;  // breakdown reached earlier: uniform early exit
+  if (MODE == CGS_UPD_NORM && ks->skip2) return;  // selective: the first pass was kept
+  // selective form: the update-and-projection pass also sums ||w_1||^2 for the decision
+  const bool unorm = MODE == CGS_UPD_PROJ && ks->selective;
+  T* const wout = (MODE == CGS_UPD_PROJ && out) ? out : (MODE == CGS_UPD_PROJ ? w : out);
   const int nc = j + 1;
   const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
   for (int c = threadIdx.x; c < CGS_WARPS * NCW; c += blockDim.x) scoef[c] = c < nc ? (T)ks->coef[c] : T(0);
@@ -515,10 +541,11 @@ __global__ void __launch_bounds__(256) cgs_cs_kernel(const T* __restrict__ Z, in
         for (int q = 0; q < CGS_WARPS; ++q)
 #pragma unroll
           for (int v = 0; v < VN; ++v) x[v] -= part[q * TR + lane * VN + v];
-        if (valid) store_vec<T, VN>((MODE == CGS_UPD_PROJ ? w : out) + r, x);
+        if (valid) store_vec<T, VN>(wout + r, x);
         if constexpr (MODE == CGS_UPD_PROJ) {
 #pragma unroll
           for (int v = 0; v < VN; ++v) xs[lane * VN + v] = x[v];
+          if (unorm) acc_dot<T, VN>(acc[NCW], x, x);
         } else {
           acc_dot<T, VN>(acc[NCW], x, x);
         }
@@ -542,16 +569,18 @@ __global__ void __launch_bounds__(256) cgs_cs_kernel(const T* __restrict__ Z, in
       if (lane == 0) red[wid + CGS_WARPS * k] = acc[k];
     }
   }
-  if (MODE != CGS_UPD_PROJ && wid == 0) {
+  if ((MODE != CGS_UPD_PROJ || unorm) && wid == 0) {
     for (int o = 16; o > 0; o >>= 1) acc[NCW].add_partner(o);
-    if (lane == 0) red[MODE == CGS_PROJ ? CGS_WARPS * NCW : 0] = acc[NCW];
+    if (lane == 0) red[MODE == CGS_UPD_NORM ? 0 : CGS_WARPS * NCW] = acc[NCW];
   }
   __syncthreads();
-  // partial-sum slots: PROJ columns 0..nc-1 and the norm at nc; UPD_PROJ columns; UPD_NORM the norm
-  __shared__ Acc<T> ordered[MMAX + 1];
-  const int nred = (MODE == CGS_PROJ) ? nc + 1 : (MODE == CGS_UPD_PROJ ? nc : 1);
+  // partial-sum slots: PROJ columns 0..nc-1 and the norm at nc; UPD_PROJ columns (and, in the
+  // selective form, the norm at nc); UPD_NORM the norm
+  __shared__ Acc<T> ordered[MMAX + 2];
+  const bool has_norm = MODE == CGS_PROJ || unorm;
+  const int nred = (MODE == CGS_UPD_NORM) ? 1 : nc + (has_norm ? 1 : 0);
   for (int c = threadIdx.x; c < nred; c += blockDim.x)
-    ordered[c] = (MODE == CGS_PROJ && c == nc) ? red[CGS_WARPS * NCW] : red[c];
+    ordered[c] = (has_norm && c == nc) ? red[CGS_WARPS * NCW] : red[c];
   __syncthreads();
   cgs_grid_tail<T>(ordered, nred, MODE, j, ks, partials, eta);
 }
@@ -643,6 +672,7 @@ cudaError_t launch_cgs(int mode, const T* Z, int64_t ldz, int64_t Kp, int j, T* 
 __global__ void __launch_bounds__(256) cgs_group_finalize_kernel(int mode, int j, KState* ks, double eta) {
   __shared__ double dots[MMAX + 2];
   if (ks->done) return;  // the pass did not run (uniform)
+  if (mode == CGS_UPD_NORM && ks->skip2) return;  // selective: the first pass was kept
   for (int c = threadIdx.x; c < MMAX + 2; c += blockDim.x) dots[c] = ks->gtot[c];
   __syncthreads();
   cgs_finalize(mode, j, dots, ks, eta);
@@ -886,6 +916,7 @@ __global__ void __cluster_dims__(PHI_CTAS, 1, 1) __launch_bounds__(256)
       if (ss) {
         ss->k[stage] = 0;
         ss->beta[stage] = ks->beta;
+        ss->pass2[stage] = ks->pass2;
         if (ks->err) ss->err = ks->err;
       }
     }
@@ -935,6 +966,7 @@ __global__ void __cluster_dims__(PHI_CTAS, 1, 1) __launch_bounds__(256)
       ss->k[stage] = k;
       ss->beta[stage] = beta;
       ss->kerr[stage] = est;
+      ss->pass2[stage] = ks->pass2;
       if (!ok) ss->err = 1;
     }
   }
@@ -1094,7 +1126,7 @@ cudaError_t launch_cast(const Tin* x, Tout* y, int64_t n, cudaStream_t st) {
   return cudaGetLastError();
 }
 
-__global__ void reset_kstate_kernel(KState* ks) {
+__global__ void reset_kstate_kernel(KState* ks, int selective) {
   if (threadIdx.x == 0) {
     ks->k = 0;
     ks->done = 0;
@@ -1102,11 +1134,14 @@ __global__ void reset_kstate_kernel(KState* ks) {
     ks->counter = 0;
     ks->beta = 0;
     ks->err_est = 0;
+    ks->selective = selective;
+    ks->skip2 = 0;
+    ks->pass2 = 0u;
   }
   for (int i = threadIdx.x; i < (MMAX + 1) * MMAX; i += blockDim.x) ks->H[i] = 0.0;
 }
-cudaError_t launch_reset_kstate(KState* ks, cudaStream_t st) {
-  reset_kstate_kernel<<<1, 256, 0, st>>>(ks);
+cudaError_t launch_reset_kstate(KState* ks, int selective, cudaStream_t st) {
+  reset_kstate_kernel<<<1, 256, 0, st>>>(ks, selective);
   return cudaGetLastError();
 }
 

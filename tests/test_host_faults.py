@@ -78,11 +78,21 @@ def test_vertex_out_of_range_is_a_mesh_error():
     assert e.code == capi.PCEXP_ERR_MESH
 
 
-@pytest.mark.parametrize("kw", [dict(m_max=0), dict(m_max=33), dict(precision=7), dict(basis_io=5)])
+@pytest.mark.parametrize("kw", [dict(m_max=0), dict(m_max=33), dict(precision=7), dict(basis_io=5),
+                                dict(reorth=3), dict(reorth=-1)])
 def test_invalid_options_are_rejected(kw):
     capi = _lib_or_skip()
     e = _create_error(capi, W.periodic_square(3, 1.0), **kw)
     assert e.code == capi.PCEXP_ERR_INVALID_ARG
+
+
+def test_selective_reorthogonalisation_is_not_offered_in_fp64():
+    """The FP64 form keeps both Gram-Schmidt passes (its reverse step replays them)."""
+    capi = _lib_or_skip()
+    e = _create_error(capi, W.periodic_square(3, 1.0), precision=capi.PCEXP_FP64,
+                      reorth=capi.PCEXP_REORTH_SELECTIVE)
+    assert e.code == capi.PCEXP_ERR_UNSUPPORTED
+    assert "FP32-mixed" in str(e)
 
 
 def test_order_beyond_support_is_rejected():
