@@ -54,8 +54,8 @@ def test_residual_noalloc_matches_residual_two_calls():
 
 
 def test_residual_noalloc_matches_residual_tetrahedra():
-    """Tetrahedra: (p + 1)^2 face points and 5 variables per face point in the size check and
-    the scratch layout; 12^3 Kuhn cubes at P2 (20,736 faces x 9 x 5 doubles) fit."""
+    """Tetrahedra: the face rule's points (7 at P2) and 5 variables per face point in the size
+    check and the scratch layout; 12^3 Kuhn cubes at P2 (20,736 faces x 7 x 5 doubles) fit."""
     pytest.importorskip("torch")
     from paper_1801_06300_gb300 import build
     build()
