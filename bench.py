@@ -182,6 +182,8 @@ def algorithmic_bytes(kind, T, K, E, F, dim, p, m, face_jacobians=True, gs=None)
         "cgs_proj": (avg_j + 2) * K * T,
         "cgs_upd_proj": (avg_j + 3) * K * T,
         "cgs_upd_norm": (gs[0] * (gs[1] + 3) if gs else avg_j + 3) * K * T,
+        "cgs_upd1": (avg_j + 3) * K * T,
+        "cgs_proj2": (gs[0] * (gs[1] + 2) if gs else avg_j + 2) * K * T,
     }.get(kind)
 
 
@@ -205,6 +207,8 @@ def algorithmic_flops(kind, K, E, F, dim, p, m, T=8, gs=None):
         "cgs_proj": K * (nc + 1),
         "cgs_upd_proj": K * 2 * nc,
         "cgs_upd_norm": K * (gs[0] * (gs[1] + 2) if gs else nc + 1),
+        "cgs_upd1": K * (nc + 1),
+        "cgs_proj2": K * (gs[0] * (gs[1] + 2) if gs else nc + 1),
     }.get(kind)
     return None if fma is None else 2.0 * fma
 
@@ -295,7 +299,7 @@ def kernel_table(prof, T, K, E, F, hbm, dim, p, m, fp64=None, face_jacobians=Tru
         sec = ms / n / 1e3
         row = {"launches": n, "avg_launch_us": round(sec * 1e6, 2), "gbs": round(ab / sec / 1e9, 1),
                "hbm_frac": round(ab / sec / 1e9 / hbm, 4)}
-        if kind == "cgs_upd_norm" and gs:
+        if kind in ("cgs_upd_norm", "cgs_proj2") and gs:
             row["ran"] = round(gs[0], 4)  # share of the launches that ran the second pass
         fl = algorithmic_flops(kind, K, E, F, dim, p, m, T, gs)
         if T == 8 and fl is not None and fp64 is not None:

@@ -338,13 +338,16 @@ int pcexp_output(pcexp_ctx* ctx, int kind, double* value);
 #define PCEXP_KC_CGS_NORM 4      /* ||b|| of the Krylov start vector */
 #define PCEXP_KC_CGS_PROJ 5      /* h = V^T w, ||w|| */
 #define PCEXP_KC_CGS_UPD_PROJ 6  /* w -= V h; h2 = V^T w */
-#define PCEXP_KC_CGS_UPD_NORM 7  /* v_{j+1} = w - V h2; ||v_{j+1}|| */
+#define PCEXP_KC_CGS_UPD_NORM 7  /* v_{j+1} = w - V h2; ||v_{j+1}|| (selective form: only where
+                                    the first pass cancelled; the other launches leave at once) */
 #define PCEXP_KC_PHI 8           /* phi of the Hessenberg matrix */
 #define PCEXP_KC_AXPY 9          /* u + sum_i c_i v_i */
 #define PCEXP_KC_DT 10           /* element time steps */
 #define PCEXP_KC_OTHER 11        /* small bookkeeping kernels */
 #define PCEXP_KC_LINEARIZE 12    /* point Jacobians at u_n (once per step) */
-#define PCEXP_KC_COUNT 13
+#define PCEXP_KC_CGS_UPD1 13     /* selective form: w_1 = w - V h; ||w_1|| and the decision */
+#define PCEXP_KC_CGS_PROJ2 14    /* selective form: h2 = V^T w_1 where the first pass cancelled */
+#define PCEXP_KC_COUNT 15
 int pcexp_profile_enable(pcexp_ctx* ctx, int enable);
 int pcexp_profile_read(pcexp_ctx* ctx, int kernel_class, int64_t* launches, double* ms);
 

@@ -46,7 +46,8 @@ PCEXP_FUNC_WALL_FY = 1
 PCEXP_FUNC_VORTEX_L2 = 2
 PCEXP_FUNC_WALL_FZ = 3
 KERNEL_CLASSES = ["residual_face", "residual_elem", "jvp_face", "jvp_elem", "cgs_norm", "cgs_proj",
-                  "cgs_upd_proj", "cgs_upd_norm", "phi", "axpy", "dt", "other", "linearize"]
+                  "cgs_upd_proj", "cgs_upd_norm", "phi", "axpy", "dt", "other", "linearize", "cgs_upd1",
+                  "cgs_proj2"]
 
 
 class pcexp_mesh(C.Structure):

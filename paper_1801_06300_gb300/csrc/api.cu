@@ -501,7 +501,7 @@ int arnoldi(pcexp_ctx* c, const T* escale, int m, const double* dt_dev = nullptr
   T* G = reinterpret_cast<T*>(c->G);
   T* V = reinterpret_cast<T*>(c->V);
   (void)G;
-  PCEXP_LAUNCH(c, PCEXP_KC_OTHER, launch_reset_kstate(c->ks, c->selective ? 1 : 0, c->st));
+  PCEXP_LAUNCH(c, PCEXP_KC_OTHER, launch_reset_kstate(c->ks, c->st));
   PCEXP_LAUNCH(c, PCEXP_KC_CGS_NORM, launch_cgs<T>(CGS_NORM, V, c->Kp, c->Kp, 0, V, nullptr, c->ks, c->partials, c->eta, c->st));
   PCEXP_TRY(group_cgs(c, CGS_NORM, 0));
   for (int j = 0; j < m; ++j) {
@@ -510,13 +510,23 @@ int arnoldi(pcexp_ctx* c, const T* escale, int m, const double* dt_dev = nullptr
     PCEXP_TRY(jac_apply<T>(c, d, Vcol<T>(c, j), w, escale, &c->ks->done, &c->ks->s[j]));
     PCEXP_LAUNCH(c, PCEXP_KC_CGS_PROJ, launch_cgs<T>(CGS_PROJ, V, c->Kp, c->Kp, j, w, nullptr, c->ks, c->partials, c->eta, c->st));
     PCEXP_TRY(group_cgs(c, CGS_PROJ, j));
-    // selective re-orthogonalisation: the first pass writes w_1 straight into z_{j+1}, which
-    // stays there when the second pass is not needed and is updated in place when it is
-    T* z1 = Vcol<T>(c, j + 1);
-    PCEXP_LAUNCH(c, PCEXP_KC_CGS_UPD_PROJ, launch_cgs<T>(CGS_UPD_PROJ, V, c->Kp, c->Kp, j, w, c->selective ? z1 : nullptr, c->ks, c->partials, c->eta, c->st));
-    PCEXP_TRY(group_cgs(c, CGS_UPD_PROJ, j));
-    PCEXP_LAUNCH(c, PCEXP_KC_CGS_UPD_NORM, launch_cgs<T>(CGS_UPD_NORM, V, c->Kp, c->Kp, j, c->selective ? z1 : w, z1, c->ks, c->partials, c->eta, c->st));
-    PCEXP_TRY(group_cgs(c, CGS_UPD_NORM, j));
+    if (c->selective) {
+      // the first update alone, w_1 = w - V h straight into z_{j+1}, with ||w_1||; where it
+      // cancelled, the second projection and update follow (in place on z_{j+1}), otherwise
+      // those two passes leave at once
+      T* z1 = Vcol<T>(c, j + 1);
+      PCEXP_LAUNCH(c, PCEXP_KC_CGS_UPD1, launch_cgs<T>(CGS_UPD1, V, c->Kp, c->Kp, j, w, z1, c->ks, c->partials, c->eta, c->st));
+      PCEXP_TRY(group_cgs(c, CGS_UPD1, j));
+      PCEXP_LAUNCH(c, PCEXP_KC_CGS_PROJ2, launch_cgs<T>(CGS_PROJ2, V, c->Kp, c->Kp, j, z1, nullptr, c->ks, c->partials, c->eta, c->st));
+      PCEXP_TRY(group_cgs(c, CGS_PROJ2, j));
+      PCEXP_LAUNCH(c, PCEXP_KC_CGS_UPD_NORM, launch_cgs<T>(CGS_UPD_NORM, V, c->Kp, c->Kp, j, z1, z1, c->ks, c->partials, c->eta, c->st));
+      PCEXP_TRY(group_cgs(c, CGS_UPD_NORM, j));
+    } else {
+      PCEXP_LAUNCH(c, PCEXP_KC_CGS_UPD_PROJ, launch_cgs<T>(CGS_UPD_PROJ, V, c->Kp, c->Kp, j, w, nullptr, c->ks, c->partials, c->eta, c->st));
+      PCEXP_TRY(group_cgs(c, CGS_UPD_PROJ, j));
+      PCEXP_LAUNCH(c, PCEXP_KC_CGS_UPD_NORM, launch_cgs<T>(CGS_UPD_NORM, V, c->Kp, c->Kp, j, w, Vcol<T>(c, j + 1), c->ks, c->partials, c->eta, c->st));
+      PCEXP_TRY(group_cgs(c, CGS_UPD_NORM, j));
+    }
     if (c->ktol > 0 && dt_dev && (j + 1) % KRYLOV_CHECK == 0 && j + 1 < m)
       PCEXP_LAUNCH(c, PCEXP_KC_PHI, launch_phi_check(c->ks, dt_dev, c->ktol, c->st));
   }

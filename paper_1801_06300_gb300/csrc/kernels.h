@@ -32,8 +32,7 @@ struct KState {
   int err;
   unsigned counter;
   int group;               // partitioned run: the passes leave their sums in gsum, unfinalised
-  int selective;           // second Gram-Schmidt pass only after a first pass that cancelled
-  int skip2;               // the current column's second pass is not needed (selective)
+  int skip2;               // selective form: the current column keeps its first pass
   unsigned pass2;          // bit j: column j ran the second pass
 };
 
@@ -261,7 +260,9 @@ cudaError_t launch_density_norm(const T* R, const T* s, int64_t E, int nb, int n
                                 cudaStream_t st);
 
 // ---- Krylov (krylov_kernels.cu)
-enum CgsMode { CGS_PROJ = 0, CGS_UPD_PROJ = 1, CGS_UPD_NORM = 2, CGS_NORM = 3 };
+// Gram-Schmidt passes.  UPD1 streams like UPD_NORM (update and norm) and PROJ2 like PROJ;
+// they differ in what the last block does with the sums (cgs_finalize).
+enum CgsMode { CGS_PROJ = 0, CGS_UPD_PROJ = 1, CGS_UPD_NORM = 2, CGS_NORM = 3, CGS_UPD1 = 4, CGS_PROJ2 = 5 };
 template <class T>
 cudaError_t launch_cgs(int mode, const T* Z, int64_t ldz, int64_t Kp, int j, T* w, T* out,
                        KState* ks, double* partials, double eta, cudaStream_t st);
@@ -311,7 +312,7 @@ template <class T>
 cudaError_t launch_zero_range(T* x, int64_t from, int64_t to, cudaStream_t st);
 // ss->cfl = min(ss->cfl, cap) (the Krylov-error cap of the steady march)
 cudaError_t launch_cap_cfl(StepState* ss, double cap, cudaStream_t st);
-cudaError_t launch_reset_kstate(KState* ks, int selective, cudaStream_t st);
+cudaError_t launch_reset_kstate(KState* ks, cudaStream_t st);
 // ---- reverse Krylov stage (adjoint.cu, FP64)
 // Reverse of the Krylov stage, step by step.  Each reduction (ybar, alpha, upd, b0dot) leaves
 // its sums in as->dots and finishes in its last block; in a partitioned run (as->group) it

@@ -122,17 +122,18 @@ PCEXP_DEV void acc_dot(Acc<T>& acc, const T (&a)[VN], const T (&b)[VN]) {
 constexpr double DGKS_KAPPA = 0.70710678118654752440;
 
 // Stage logic of the last block: per-column entries in parallel, scalars on thread 0.
+//   PROJ      h = V^T w: column j of H (and of H1), update coefficients, ||w||
+//   UPD_PROJ  h2 = V^T w_1 after the update: added to column j, new coefficients
+//   PROJ2     the same for the selective form's separate second projection
+//   UPD1      the selective form's first update w_1 = w - V h alone, with ||w_1||: keep it as
+//             z_{j+1} (skip2) when it cancelled less than DGKS_KAPPA, else leave the column
+//             to PROJ2 + UPD_NORM
+//   UPD_NORM  z_{j+1} = w_1 - V h2, h_{j+1,j} = ||z_{j+1}||, breakdown test
 PCEXP_DEV void cgs_finalize(int mode, int j, const double* dots, KState* ks, double eta) {
   __shared__ int bad;
   if (threadIdx.x == 0) bad = 0;
   __syncthreads();
-  if (mode == CGS_PROJ || mode == CGS_UPD_PROJ) {
-    // selective: UPD_PROJ also summed ||w_1||^2 (slot j + 1); every thread takes the same
-    // decision from the same values.  A non-finite or zero norm takes the second pass, whose
-    // norm test reports it.
-    const double n1 = (mode == CGS_UPD_PROJ && ks->selective) ? sqrt(dots[j + 1]) : 0.0;
-    const bool keep1 = mode == CGS_UPD_PROJ && ks->selective && isfinite(n1) && n1 > 0.0 &&
-                       n1 >= DGKS_KAPPA * ks->wnorm0;
+  if (mode == CGS_PROJ || mode == CGS_UPD_PROJ || mode == CGS_PROJ2) {
     // w = J v_j is already normalised by s_j (applied by the J v kernel)
     for (int i = threadIdx.x; i <= j; i += blockDim.x) {
       const double si = ks->s[i];
@@ -141,7 +142,7 @@ PCEXP_DEV void cgs_finalize(int mode, int j, const double* dots, KState* ks, dou
       if (mode == CGS_PROJ) {
         ks->H[i * MMAX + j] = h;
         ks->H1[i * MMAX + j] = h;
-      } else if (!keep1) {
+      } else {
         ks->H[i * MMAX + j] += h;
       }
       ks->coef[i] = si * h;
@@ -149,14 +150,6 @@ PCEXP_DEV void cgs_finalize(int mode, int j, const double* dots, KState* ks, dou
     __syncthreads();
     if (threadIdx.x == 0) {
       if (mode == CGS_PROJ) ks->wnorm0 = sqrt(dots[j + 1]);
-      if (mode == CGS_UPD_PROJ) {
-        ks->skip2 = keep1 ? 1 : 0;
-        if (keep1) {  // z_{j+1} = w_1 (written by the pass); n1 > eta ||w||: no breakdown
-          ks->H[(j + 1) * MMAX + j] = n1;
-          ks->k = j + 1;
-          ks->s[j + 1] = 1.0 / n1;
-        }
-      }
       if (bad) {
         ks->err = 1;
         ks->done = 1;
@@ -180,6 +173,19 @@ PCEXP_DEV void cgs_finalize(int mode, int j, const double* dots, KState* ks, dou
     }
     return;
   }
+  if (mode == CGS_UPD1) {
+    // a non-finite or zero norm takes the second pass, whose norm test reports it; a kept
+    // first pass has ||w_1|| >= ||w|| / sqrt(2) > eta ||w||, so it needs no breakdown test
+    const double n1 = sqrt(dots[0]);
+    const bool keep1 = isfinite(n1) && n1 > 0.0 && n1 >= DGKS_KAPPA * ks->wnorm0;
+    ks->skip2 = keep1 ? 1 : 0;
+    if (keep1) {
+      ks->H[(j + 1) * MMAX + j] = n1;
+      ks->k = j + 1;
+      ks->s[j + 1] = 1.0 / n1;
+    }
+    return;
+  }
   // CGS_UPD_NORM
   const double hn = sqrt(dots[0]);
   ks->pass2 |= 1u << j;
@@ -193,6 +199,12 @@ PCEXP_DEV void cgs_finalize(int mode, int j, const double* dots, KState* ks, dou
   } else {
     ks->s[j + 1] = 1.0 / hn;
   }
+}
+
+// The passes that belong to a column's second Gram-Schmidt pass leave at once when the
+// selective form kept the first pass.
+PCEXP_DEV bool cgs_skipped(int fmode, const KState* ks) {
+  return (fmode == CGS_PROJ2 || fmode == CGS_UPD_NORM) && ks->skip2;
 }
 
 // Warp reduction of NC accumulators at once (NC a power of two <= 32): plain
@@ -233,19 +245,20 @@ PCEXP_DEV Acc<T> warp_reduce_columns(Acc<T> (&a)[NC], int lane) {
 // Row Gram-Schmidt pass (NORM, PROJ, UPD_PROJ, UPD_NORM): every thread owns whole 16-byte
 // chunks of rows and accumulates all columns for them; the launch bounds hold it at 128
 // registers so that two blocks share an SM.
-// In the selective form UPD_NORM runs in place (w == out == z_{j+1}, each element read and
-// then written by the same thread), so w and out are not restrict-qualified.
+// MODE is how the pass streams; fmode (CgsMode) what its last block does with the sums.  In
+// the selective form the second pass's UPD_NORM runs in place (w == out == z_{j+1}, each
+// element read and then written by the same thread), so w and out are not restrict-qualified.
 template <class T, int NC, int MODE>
 __global__ void __launch_bounds__(256, 2) cgs_kernel(const T* __restrict__ Z, int64_t ldz, int64_t Kp, int j,
                                                   T* w, T* out, KState* ks,
-                                                  double* __restrict__ partials, double eta) {
+                                                  double* __restrict__ partials, double eta, int fmode) {
   constexpr int VN = VecN<T>::N;
   constexpr int NACC = (MODE == CGS_PROJ) ? NC + 1 : (MODE == CGS_UPD_PROJ ? NC : 1);
   __shared__ T scoef[NC > 0 ? NC : 1];
   __shared__ Acc<T> red[8][NACC];
   __shared__ bool last;
   if (ks->done) return;  // breakdown reached earlier: uniform early exit
-  if (MODE == CGS_UPD_NORM && ks->skip2) return;  // selective: the first pass was kept
+  if (cgs_skipped(fmode, ks)) return;
   const int nc = (MODE == CGS_NORM) ? 0 : j + 1;
   if (MODE == CGS_UPD_PROJ || MODE == CGS_UPD_NORM)
     for (int c = threadIdx.x; c < nc; c += blockDim.x) scoef[c] = (T)ks->coef[c];
@@ -293,7 +306,7 @@ __global__ void __launch_bounds__(256, 2) cgs_kernel(const T* __restrict__ Z, in
         }
       }
       if constexpr (MODE == CGS_UPD_PROJ) {
-        store_vec<T, VN>((out ? out : w) + r, x);
+        store_vec<T, VN>(w + r, x);
         // reload the chunks rather than keep all of them live across the store (255 -> 128
         // registers, two blocks per SM instead of one; the reloads hit L1/L2)
         asm volatile("" ::: "memory");
@@ -370,7 +383,7 @@ __global__ void __launch_bounds__(256, 2) cgs_kernel(const T* __restrict__ Z, in
     if (threadIdx.x == 0) ks->counter = 0;
     return;
   }
-  cgs_finalize(MODE, j, dots, ks, eta);
+  cgs_finalize(fmode, j, dots, ks, eta);
   if (threadIdx.x == 0) ks->counter = 0;
 }
 
@@ -438,17 +451,14 @@ PCEXP_DEV void cgs_cp_wait_all() { asm volatile("cp.async.wait_all;" ::: "memory
 template <class T, int NCW, int MODE>
 __global__ void __launch_bounds__(256) cgs_cs_kernel(const T* __restrict__ Z, int64_t ldz, int64_t Kp, int j,
                                                      T* __restrict__ w, T* __restrict__ out, KState* ks,
-                                                     double* __restrict__ partials, double eta) {
+                                                     double* __restrict__ partials, double eta, int fmode) {
   constexpr int VN = VecN<T>::N, TR = 32 * VN;
   __shared__ T scoef[CGS_WARPS * NCW];
   __shared__ T part[(MODE == CGS_PROJ) ? 1 : CGS_WARPS * TR];
   __shared__ T xs[(MODE == CGS_UPD_PROJ) ? TR : 1];
   __shared__ Acc<T> red[CGS_WARPS * NCW + 1];
   if (ks->done) return;  // breakdown reached earlier: uniform early exit
-  if (MODE == CGS_UPD_NORM && ks->skip2) return;  // selective: the first pass was kept
-  // selective form: the update-and-projection pass also sums ||w_1||^2 for the decision
-  const bool unorm = MODE == CGS_UPD_PROJ && ks->selective;
-  T* const wout = (MODE == CGS_UPD_PROJ && out) ? out : (MODE == CGS_UPD_PROJ ? w : out);
+  if (cgs_skipped(fmode, ks)) return;
   const int nc = j + 1;
   const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
   for (int c = threadIdx.x; c < CGS_WARPS * NCW; c += blockDim.x) scoef[c] = c < nc ? (T)ks->coef[c] : T(0);
@@ -541,11 +551,10 @@ __global__ void __launch_bounds__(256) cgs_cs_kernel(const T* __restrict__ Z, in
         for (int q = 0; q < CGS_WARPS; ++q)
 #pragma unroll
           for (int v = 0; v < VN; ++v) x[v] -= part[q * TR + lane * VN + v];
-        if (valid) store_vec<T, VN>(wout + r, x);
+        if (valid) store_vec<T, VN>((MODE == CGS_UPD_PROJ ? w : out) + r, x);
         if constexpr (MODE == CGS_UPD_PROJ) {
 #pragma unroll
           for (int v = 0; v < VN; ++v) xs[lane * VN + v] = x[v];
-          if (unorm) acc_dot<T, VN>(acc[NCW], x, x);
         } else {
           acc_dot<T, VN>(acc[NCW], x, x);
         }
@@ -569,20 +578,18 @@ __global__ void __launch_bounds__(256) cgs_cs_kernel(const T* __restrict__ Z, in
       if (lane == 0) red[wid + CGS_WARPS * k] = acc[k];
     }
   }
-  if ((MODE != CGS_UPD_PROJ || unorm) && wid == 0) {
+  if (MODE != CGS_UPD_PROJ && wid == 0) {
     for (int o = 16; o > 0; o >>= 1) acc[NCW].add_partner(o);
-    if (lane == 0) red[MODE == CGS_UPD_NORM ? 0 : CGS_WARPS * NCW] = acc[NCW];
+    if (lane == 0) red[MODE == CGS_PROJ ? CGS_WARPS * NCW : 0] = acc[NCW];
   }
   __syncthreads();
-  // partial-sum slots: PROJ columns 0..nc-1 and the norm at nc; UPD_PROJ columns (and, in the
-  // selective form, the norm at nc); UPD_NORM the norm
-  __shared__ Acc<T> ordered[MMAX + 2];
-  const bool has_norm = MODE == CGS_PROJ || unorm;
-  const int nred = (MODE == CGS_UPD_NORM) ? 1 : nc + (has_norm ? 1 : 0);
+  // partial-sum slots: PROJ columns 0..nc-1 and the norm at nc; UPD_PROJ columns; UPD_NORM the norm
+  __shared__ Acc<T> ordered[MMAX + 1];
+  const int nred = (MODE == CGS_PROJ) ? nc + 1 : (MODE == CGS_UPD_PROJ ? nc : 1);
   for (int c = threadIdx.x; c < nred; c += blockDim.x)
-    ordered[c] = (has_norm && c == nc) ? red[CGS_WARPS * NCW] : red[c];
+    ordered[c] = (MODE == CGS_PROJ && c == nc) ? red[CGS_WARPS * NCW] : red[c];
   __syncthreads();
-  cgs_grid_tail<T>(ordered, nred, MODE, j, ks, partials, eta);
+  cgs_grid_tail<T>(ordered, nred, fmode, j, ks, partials, eta);
 }
 
 template <class KernelT>
@@ -606,26 +613,26 @@ static unsigned wave_grid(KernelT kernel, int64_t chunks) {
 
 template <class T, int NC, int MODE>
 static void cgs_launch(const T* Z, int64_t ldz, int64_t Kp, int j, T* w, T* out, KState* ks, double* partials,
-                       double eta, cudaStream_t st) {
+                       double eta, int fmode, cudaStream_t st) {
   static unsigned grid_cache = 0;
   static int64_t kp_cache = -1;
   if (kp_cache != Kp) {
     grid_cache = wave_grid(cgs_kernel<T, NC, MODE>, Kp / VecN<T>::N);
     kp_cache = Kp;
   }
-  cgs_kernel<T, NC, MODE><<<grid_cache, 256, 0, st>>>(Z, ldz, Kp, j, w, out, ks, partials, eta);
+  cgs_kernel<T, NC, MODE><<<grid_cache, 256, 0, st>>>(Z, ldz, Kp, j, w, out, ks, partials, eta, fmode);
 }
 
 template <class T, int NCW, int MODE>
 static void cgs_cs_launch(const T* Z, int64_t ldz, int64_t Kp, int j, T* w, T* out, KState* ks, double* partials,
-                          double eta, cudaStream_t st) {
+                          double eta, int fmode, cudaStream_t st) {
   static unsigned grid_cache = 0;
   static int64_t kp_cache = -1;
   if (kp_cache != Kp) {
     grid_cache = wave_grid(cgs_cs_kernel<T, NCW, MODE>, (Kp + 32 * VecN<T>::N - 1) / (32 * VecN<T>::N) * 256);
     kp_cache = Kp;
   }
-  cgs_cs_kernel<T, NCW, MODE><<<grid_cache, 256, 0, st>>>(Z, ldz, Kp, j, w, out, ks, partials, eta);
+  cgs_cs_kernel<T, NCW, MODE><<<grid_cache, 256, 0, st>>>(Z, ldz, Kp, j, w, out, ks, partials, eta, fmode);
 }
 
 // Which layout serves a precision and pass: the column-split kernel (column capacity
@@ -640,16 +647,16 @@ template <class T, int MODE> struct CgsColumnSplit {
 
 template <class T, int MODE>
 static void cgs_dispatch(int nc, const T* Z, int64_t ldz, int64_t Kp, int j, T* w, T* out, KState* ks,
-                         double* partials, double eta, cudaStream_t st) {
+                         double* partials, double eta, int fmode, cudaStream_t st) {
   if constexpr (CgsColumnSplit<T, MODE>::value) {
-    if (nc <= CGS_WARPS) cgs_cs_launch<T, 1, MODE>(Z, ldz, Kp, j, w, out, ks, partials, eta, st);
-    else if (nc <= 2 * CGS_WARPS) cgs_cs_launch<T, 2, MODE>(Z, ldz, Kp, j, w, out, ks, partials, eta, st);
-    else cgs_cs_launch<T, 4, MODE>(Z, ldz, Kp, j, w, out, ks, partials, eta, st);
+    if (nc <= CGS_WARPS) cgs_cs_launch<T, 1, MODE>(Z, ldz, Kp, j, w, out, ks, partials, eta, fmode, st);
+    else if (nc <= 2 * CGS_WARPS) cgs_cs_launch<T, 2, MODE>(Z, ldz, Kp, j, w, out, ks, partials, eta, fmode, st);
+    else cgs_cs_launch<T, 4, MODE>(Z, ldz, Kp, j, w, out, ks, partials, eta, fmode, st);
   } else {
-    if (nc <= 4) cgs_launch<T, 4, MODE>(Z, ldz, Kp, j, w, out, ks, partials, eta, st);
-    else if (nc <= 8) cgs_launch<T, 8, MODE>(Z, ldz, Kp, j, w, out, ks, partials, eta, st);
-    else if (nc <= 16) cgs_launch<T, 16, MODE>(Z, ldz, Kp, j, w, out, ks, partials, eta, st);
-    else cgs_launch<T, 32, MODE>(Z, ldz, Kp, j, w, out, ks, partials, eta, st);
+    if (nc <= 4) cgs_launch<T, 4, MODE>(Z, ldz, Kp, j, w, out, ks, partials, eta, fmode, st);
+    else if (nc <= 8) cgs_launch<T, 8, MODE>(Z, ldz, Kp, j, w, out, ks, partials, eta, fmode, st);
+    else if (nc <= 16) cgs_launch<T, 16, MODE>(Z, ldz, Kp, j, w, out, ks, partials, eta, fmode, st);
+    else cgs_launch<T, 32, MODE>(Z, ldz, Kp, j, w, out, ks, partials, eta, fmode, st);
   }
 }
 
@@ -659,10 +666,12 @@ cudaError_t launch_cgs(int mode, const T* Z, int64_t ldz, int64_t Kp, int j, T* 
   const int nc = j + 1;
   if (nc > MMAX) return cudaErrorInvalidValue;
   switch (mode) {
-    case CGS_NORM: cgs_launch<T, 0, CGS_NORM>(Z, ldz, Kp, j, w, out, ks, partials, eta, st); break;
-    case CGS_PROJ: cgs_dispatch<T, CGS_PROJ>(nc, Z, ldz, Kp, j, w, out, ks, partials, eta, st); break;
-    case CGS_UPD_PROJ: cgs_dispatch<T, CGS_UPD_PROJ>(nc, Z, ldz, Kp, j, w, out, ks, partials, eta, st); break;
-    case CGS_UPD_NORM: cgs_dispatch<T, CGS_UPD_NORM>(nc, Z, ldz, Kp, j, w, out, ks, partials, eta, st); break;
+    case CGS_NORM: cgs_launch<T, 0, CGS_NORM>(Z, ldz, Kp, j, w, out, ks, partials, eta, mode, st); break;
+    case CGS_PROJ:
+    case CGS_PROJ2: cgs_dispatch<T, CGS_PROJ>(nc, Z, ldz, Kp, j, w, out, ks, partials, eta, mode, st); break;
+    case CGS_UPD_PROJ: cgs_dispatch<T, CGS_UPD_PROJ>(nc, Z, ldz, Kp, j, w, out, ks, partials, eta, mode, st); break;
+    case CGS_UPD_NORM:
+    case CGS_UPD1: cgs_dispatch<T, CGS_UPD_NORM>(nc, Z, ldz, Kp, j, w, out, ks, partials, eta, mode, st); break;
     default: return cudaErrorInvalidValue;
   }
   return cudaGetLastError();
@@ -672,7 +681,7 @@ cudaError_t launch_cgs(int mode, const T* Z, int64_t ldz, int64_t Kp, int j, T* 
 __global__ void __launch_bounds__(256) cgs_group_finalize_kernel(int mode, int j, KState* ks, double eta) {
   __shared__ double dots[MMAX + 2];
   if (ks->done) return;  // the pass did not run (uniform)
-  if (mode == CGS_UPD_NORM && ks->skip2) return;  // selective: the first pass was kept
+  if (cgs_skipped(mode, ks)) return;  // the pass did not run (uniform)
   for (int c = threadIdx.x; c < MMAX + 2; c += blockDim.x) dots[c] = ks->gtot[c];
   __syncthreads();
   cgs_finalize(mode, j, dots, ks, eta);
@@ -1126,7 +1135,7 @@ cudaError_t launch_cast(const Tin* x, Tout* y, int64_t n, cudaStream_t st) {
   return cudaGetLastError();
 }
 
-__global__ void reset_kstate_kernel(KState* ks, int selective) {
+__global__ void reset_kstate_kernel(KState* ks) {
   if (threadIdx.x == 0) {
     ks->k = 0;
     ks->done = 0;
@@ -1134,14 +1143,13 @@ __global__ void reset_kstate_kernel(KState* ks, int selective) {
     ks->counter = 0;
     ks->beta = 0;
     ks->err_est = 0;
-    ks->selective = selective;
     ks->skip2 = 0;
     ks->pass2 = 0u;
   }
   for (int i = threadIdx.x; i < (MMAX + 1) * MMAX; i += blockDim.x) ks->H[i] = 0.0;
 }
-cudaError_t launch_reset_kstate(KState* ks, int selective, cudaStream_t st) {
-  reset_kstate_kernel<<<1, 256, 0, st>>>(ks, selective);
+cudaError_t launch_reset_kstate(KState* ks, cudaStream_t st) {
+  reset_kstate_kernel<<<1, 256, 0, st>>>(ks);
   return cudaGetLastError();
 }
 
