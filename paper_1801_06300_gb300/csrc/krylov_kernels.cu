@@ -11,7 +11,11 @@
 //   UP  : w   -= sum_i s_i^2 <z_i,w> z_i; h2_i = s_i <z_i, w>  (read V_j, w; write w)
 //   UN  : z_{j+1} = w - sum_i s_i^2 <z_i,w> z_i; h_{j+1,j} = ||z_{j+1}||, s_{j+1} = 1/h_{j+1,j}
 // so every stored z_i has the size of ||J|| (no growth like ||J||^i, which would
-// overflow FP32 storage).
+// overflow FP32 storage).  The selective form (FP32-mixed default) runs a column as
+//   P, U1: z_{j+1} = w - sum_i s_i^2 <z_i,w> z_i, ||z_{j+1}||       (read V_j, w; write z_{j+1})
+// and keeps that first update when ||z_{j+1}|| >= ||w|| / sqrt(2); otherwise the second
+// pass follows, P2 (h2 = V_j^T z_{j+1}) and UN in place on z_{j+1}.  The second pass's
+// launches leave at once in the columns that keep their first update.
 // Each streaming kernel writes per-block partial sums; the last block to
 // finish (atomic ticket) reduces them in a fixed order and applies the scalar
 // update, so results are deterministic and no extra launch is needed.
