@@ -777,7 +777,7 @@ __global__ void __launch_bounds__(128) linearize_face_kernel(DGData<T> d, const 
     J L[NV], R[NV], F[NV];
     if (side == 1 && eR < 0) {
 #pragma unroll
-      for (int k = 0; k < NN; ++k) Bface[(int64_t)(NN + k) * n + idx] = T(0);
+      for (int k = 0; k < NN; ++k) Bface[bface_at<T, 2 * NN>(NN + k, idx, n)] = T(0);
       break;
     }
 #pragma unroll
@@ -803,7 +803,7 @@ __global__ void __launch_bounds__(128) linearize_face_kernel(DGData<T> d, const 
 #pragma unroll
     for (int v = 0; v < NV; ++v)
 #pragma unroll
-      for (int c = 0; c < NV; ++c) Bface[(int64_t)(side * NN + v * NV + c) * n + idx] = sc * F[v].d[c];
+      for (int c = 0; c < NV; ++c) Bface[bface_at<T, 2 * NN>(side * NN + v * NV + c, idx, n)] = sc * F[v].d[c];
   }
 }
 
@@ -828,9 +828,32 @@ __global__ void __launch_bounds__(256) face_apply_kernel(DGData<T> d, const T* _
   const int eL = d.fel[2 * f], eR = d.fel[2 * f + 1];
   const int loc = d.floc[f];
   const int fL = loc & 0xff, fR = (loc >> 8) & 0xff, pR = loc >> 16;
+  // the point's block in 16-byte vectors (bface_at); chunks wholly on the R side are not
+  // loaded on boundary faces (the linearisation stores zeros there)
   T B[O::NJF];
+  {
+    constexpr int VEC = 16 / (int)sizeof(T), NCH = O::NJF / VEC, R = O::NJF % VEC;
+    const bool two = eR >= 0;
 #pragma unroll
-  for (int k = 0; k < O::NJF; ++k) B[k] = (k < NN || eR >= 0) ? Bface[(int64_t)k * n + idx] : T(0);
+    for (int c = 0; c < NCH; ++c) {
+      if (c * VEC < NN || two) {
+        T x[VEC];
+        load_row<T, VEC, true>(Bface + ((int64_t)c * n + idx) * VEC, x);
+#pragma unroll
+        for (int i = 0; i < VEC; ++i) B[c * VEC + i] = x[i];
+      } else {
+#pragma unroll
+        for (int i = 0; i < VEC; ++i) B[c * VEC + i] = T(0);
+      }
+    }
+    if constexpr (R > 0) {
+      static_assert(R == 2 && sizeof(T) == 4, "the remainder of a point's block is one float pair");
+      const float2 x = two ? __ldg(reinterpret_cast<const float2*>(Bface + (int64_t)NCH * VEC * n + idx * R))
+                           : make_float2(0.f, 0.f);
+      B[NCH * VEC] = x.x;
+      B[NCH * VEC + 1] = x.y;
+    }
+  }
   // traces of dv at the point from each side: the table row (shared memory in 2D; in 3D the
   // padded copy, 16-byte loads) and the element's rows of dv (8-byte loads when nb is even:
   // the kernel is bound by its load instructions as much as by its bytes)
@@ -1078,7 +1101,7 @@ __global__ void __launch_bounds__(256) face_adjoint_kernel(DGData<T> d, const T*
       T a = 0;
       if (side == 0 || eR >= 0) {
 #pragma unroll
-        for (int v = 0; v < NV; ++v) a += Bface[(int64_t)(side * NN + v * NV + c) * n + idx] * gb[v];
+        for (int v = 0; v < NV; ++v) a += Bface[bface_at<T, 2 * NN>(side * NN + v * NV + c, idx, n)] * gb[v];
       }
       o[side * NV + c] = a;
     }

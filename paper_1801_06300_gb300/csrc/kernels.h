@@ -94,11 +94,23 @@ struct DGData {
   int dim;
 };
 
-// Point Jacobians of the DG operator at a linearisation state u (structure of
-// arrays: entry k of every point is contiguous), NV = D + 2.
+// Point Jacobians of the DG operator at a linearisation state u, NV = D + 2.
 //   Avol [D NV NV][E*nq]:  k = d'*NV*NV + v*NV + c: sum_d (A^-1)_{d'd} dF_d[v]/dU[c] at volume points
-//   Bface[2 NV NV][F*nfq]: k = s*NV*NV + v*NV + c: |f| w_q / sqrt(det_s) dF~[v]/dU_s[c], s = L (0), R (1),
-//                          the ghost-state chain rule folded into s = L on boundary faces
+//                          (structure of arrays: entry k of every point is contiguous)
+//   Bface, NJF = 2 NV NV entries per face point: k = s*NV*NV + v*NV + c: |f| w_q / sqrt(det_s)
+//                          dF~[v]/dU_s[c], s = L (0), R (1), the ghost-state chain rule folded into
+//                          s = L on boundary faces; in 16-byte chunks of VEC = 16 / sizeof(T)
+//                          entries, [NJF / VEC][F*nfq][VEC], the NJF % VEC left over in
+//                          [F*nfq][NJF % VEC] after them (bface_at), so a point's block loads as
+//                          16-byte vectors
+// Index of entry k of face point idx (of n) in Bface.
+template <class T, int NJF>
+__host__ __device__ __forceinline__ int64_t bface_at(int k, int64_t idx, int64_t n) {
+  constexpr int VEC = 16 / (int)sizeof(T), NCH = NJF / VEC, R = NJF % VEC;
+  return k < NCH * VEC ? ((int64_t)(k / VEC) * n + idx) * VEC + k % VEC
+                       : (int64_t)NCH * VEC * n + idx * R + (k - NCH * VEC);
+}
+
 template <class T>
 struct LinData {
   T* Avol;
