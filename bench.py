@@ -218,7 +218,6 @@ def algorithmic_flops(kind, K, E, F, dim, p, m, T=8, gs=None):
 # kernel changes.  The summaries under profiles/ give the commands.
 NCU_TRAFFIC = {
     ("vortex3d", 4, "jvp_elem"): (608250112, "profiles/traffic_vortex3d_48_p2_m30_fp32.md"),
-    ("vortex3d", 4, "jvp_face"): (2185546880, "profiles/traffic_vortex3d_48_p2_m30_fp32.md"),
 }
 
 
