@@ -485,6 +485,16 @@ def main():
         hin, hout = hout, hin
     torch.cuda.synchronize()
     e2e_s = max_over_ranks(time.perf_counter() - t0, dist)
+    # the state transfer alone (copy in from pinned host memory with the basis conversion, and
+    # out again), by the wall clock around the synchronising calls
+    t0 = time.perf_counter()
+    for _ in range(5):
+        ctx32.set_state(hin)
+    set_ms = (time.perf_counter() - t0) / 5 * 1e3
+    t0 = time.perf_counter()
+    for _ in range(5):
+        ctx32.get_state(hout)
+    get_ms = (time.perf_counter() - t0) / 5 * 1e3
     ctx32.close()
 
     err = None
@@ -521,7 +531,8 @@ def main():
         "fp32_error_note": (f"relative L2 difference of the FP32-mixed and FP64 states after the same "
                             f"{args.warmup + args.steps} steps from the projected vortex"),
         "e2e": {"value": job_throughput(K, args.steps, world, e2e_s), "unit": UNIT,
-                "h2d_bytes_per_step": K * 8, "d2h_bytes_per_step": K * 8},
+                "h2d_bytes_per_step": K * 8, "d2h_bytes_per_step": K * 8,
+                "ms_per_step": e2e_s / args.steps * 1e3, "set_state_ms": set_ms, "get_state_ms": get_ms},
         "gpu_launches": int(launches_per_step * args.steps),
         "roofline": head["roofline"],
         "fma_peaks": {"fp64_tflops": round(fp64[0], 3), "fp64_source": fp64[1],
