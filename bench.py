@@ -311,6 +311,20 @@ def kernel_table(prof, T, K, E, F, hbm, dim, p, m, fp64=None, face_jacobians=Tru
     return out
 
 
+def step_hbm(prof, T, K, E, F, hbm, dim, p, m, ms_per_step, face_jacobians=True, gs=None):
+    """The whole step against the HBM copy rate: the algorithmic bytes of every kernel class
+    with a byte model, times its launches per step, over the device-timed step.  Classes bound
+    by arithmetic (the element J v in FP32-mixed, the FP64 form) keep the step below 1."""
+    total = 0.0
+    for kind, (n, _ms) in prof.items():
+        ab = algorithmic_bytes(kind, T, K, E, F, dim, p, m, face_jacobians, gs)
+        if n and ab is not None:
+            total += n * ab
+    gbs = total / (ms_per_step / 1e3) / 1e9
+    return {"algorithmic_bytes_per_step": total, "gbs": round(gbs, 1), "peak": hbm, "unit": "GB/s",
+            "frac": round(gbs / hbm, 4)}
+
+
 def max_over_ranks(x, dist, device="cuda"):
     """The largest of the ranks' values of x (the slowest rank sets the job's time); x itself
     without a process group.  The tensor lives on `device` (cuda for NCCL, cpu for gloo)."""
@@ -436,6 +450,7 @@ def main():
             "roofline": roofline_entry(prof, T, ctx.K, E, F, hbm, peak_kind, 3, case.p, case.m, "vortex3d", fp64,
                                        fp32=fp32, gs=gs),
             "kernels": kernel_table(prof, T, ctx.K, E, F, hbm, 3, case.p, case.m, fp64, fp32=fp32, gs=gs),
+            "step_hbm": step_hbm(prof, T, ctx.K, E, F, hbm, 3, case.p, case.m, ms / args.steps, gs=gs),
             "gram_schmidt": {"reorth": "selective" if T == 4 else "always",
                              "second_pass_columns": f"{sum(bin(x).count('1') for x in masks)} of "
                                                     f"{case.m * len(masks)} (profiled steps)"},
@@ -539,6 +554,7 @@ def main():
                       "fp32_tflops": round(fp32[0], 2), "fp32_source": fp32[1]},
         "kernel_ms_per_step": head["kernel_ms_per_step"],
         "kernels": head["kernels"],
+        "step_hbm": head["step_hbm"],
         "fp64": strip(forms["fp64"]) if "fp64" in forms else None,
         "speedup_fp32_mixed_vs_fp64": (forms["fp64"]["ms_per_step"] / head["ms_per_step"]) if "fp64" in forms else None,
         "gram_schmidt": head["gram_schmidt"],

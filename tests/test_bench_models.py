@@ -40,3 +40,12 @@ def test_flop_model_of_the_selective_passes():
     assert fl("cgs_upd1") == 2 * K * (nc + 1)          # update (j + 1 FMA) and norm per unknown
     gs = (0.1, 5.0)
     assert abs(fl("cgs_proj2", gs) - 2 * K * 0.1 * 7.0) <= 1e-9 * K  # (j + 2) FMA where it ran
+
+
+def test_step_hbm_sums_the_classes_over_the_step():
+    prof = {"cgs_upd1": (2, 1.0), "cgs_proj": (2, 1.0), "phi": (2, 0.5)}  # phi has no byte model
+    r = bench.step_hbm(prof, T, K, 1, 1, 1000.0, 3, 2, M, 10.0)
+    avg_j = (M - 1) / 2
+    want = 2 * (avg_j + 3) * K * T + 2 * (avg_j + 2) * K * T
+    assert abs(r["algorithmic_bytes_per_step"] - want) <= 1e-9 * want
+    assert abs(r["gbs"] - round(want / 1e-2 / 1e9, 1)) <= 0.05 and r["peak"] == 1000.0
